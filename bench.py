@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the SSLBM hot path on GB300 (one JSON line on stdout).
+
+Workload: the 8192 x 8192 no-flux multi-seed SEIRD grid (64 Gaussian infected seeds,
+d^S = d^E = d^R = 0.05, d^I = 0.01, beta = 0.5, sigma = 0.2, gamma = 0.1, mu = 0.01), FP32
+fields.  One benchmark step = 100 SSLBM lattice steps (temporal-blocked launches) followed
+by the FP64 diagnostics reduction (total population, peak infected); with the default
+103 steps the run covers the workload's 10,000 lattice steps.  The 1.34 GB state is far
+larger than the 129 MB L2, so no flush is needed between steps.
+
+value: GLUPS (billion lattice-cell updates per second) over all ranks, device-timed
+with CUDA events on the solver's stream.  e2e: the same metric through the public API
+with pinned host buffers (initial state in, final state out) inside the timed region.
+roofline: the blocked SSLBM kernel's algorithmic bytes per launch (40 B per cell: read
+and write five FP32 planes) over its event-timed average launch duration, against the
+measured HBM copy bandwidth.  cpu_baseline: the FP64 CPU oracle on the host cores, on a
+bounded sample of the same grid.  Multi-GPU runs are independent replicas (weak scaling).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this method) on the
+same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SSLBM GLUPS & % HBM roofline; ensemble scenario-steps/s vs FP64 at fixed L2 err"
+UNIT = "GLUPS"
+NX = NY = 8192
+LATTICE_STEPS_PER_STEP = 100
+BYTES_PER_CELL_FP32 = 40  # read + write of five FP32 planes per launch
+BYTES_PER_CELL_FP64 = 80
+BGK_BYTES_PER_CELL_FP32 = 168  # 20 populations + D, read and write
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if n_gpus > 1 and world != n_gpus:
+        raise SystemExit(f"--gpus {n_gpus} must be launched with torchrun (WORLD_SIZE={world})")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_glups(state64, wl, budget_s: float = 12.0, rows: int | None = None):
+    """GLUPS of the FP64 oracle on a band of the grid (rows x 8192, no-flux band edges)."""
+    import oracle
+    tau = [oracle.tau_from_d(v) for v in wl["d"][:4]]
+    band = np.ascontiguousarray(state64[:, : (rows or state64.shape[1]), :])
+    scratch = np.empty_like(band)
+    t0 = time.perf_counter()
+    oracle.sslbm_run_inplace(band, scratch, tau, wl["rates"].as_tuple(), 1.0, wl["bc"], 1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.sslbm_run_inplace(band, scratch, tau, wl["rates"].as_tuple(), 1.0, wl["bc"], steps)
+    el = time.perf_counter() - t0
+    cells = band.shape[1] * band.shape[2]
+    return cells * steps / el / 1e9, steps, band.shape, el
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2603_19789_gb300 import inputs
+    oracle.build()
+    wl = inputs.roofline_workload(NX, NY)
+    tau = [oracle.tau_from_d(v) for v in wl["d"][:4]]
+    rows = 1024
+    band = np.ascontiguousarray(wl["state"][:, :rows, :])
+    scratch = np.empty_like(band)
+    for _ in range(args.warmup):
+        oracle.sslbm_run_inplace(band, scratch, tau, wl["rates"].as_tuple(), 1.0, wl["bc"], 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sslbm_run_inplace(band, scratch, tau, wl["rates"].as_tuple(), 1.0, wl["bc"], 1)
+    el = time.perf_counter() - t0
+    cells = rows * NX
+    value = cells * args.steps / el / 1e9
+    sample = (f"one FP64 oracle lattice step per benchmark step on a {NX}x{rows} band of the "
+              f"{NX}x{NY} grid (no-flux band edges)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "nx": NX, "ny": NY, "band_rows": rows,
+                       "lattice_steps_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def timed_steps(solver, n_lat, steps, stream, diag=True):
+    """Run `steps` benchmark steps; returns (total ms, kernel ms) from CUDA events."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(steps):
+        starts[i].record(stream)
+        solver.step(n_lat)
+        ends[i].record(stream)
+        if diag:
+            solver.diagnostics()
+    t1.record(stream)
+    t1.synchronize()
+    total = t0.elapsed_time(t1)
+    kern = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    return total, kern
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=103)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--depth", type=int, default=0, help="temporal-blocking depth (0 = default)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary variant timings")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_2603_19789_gb300 import build as libbuild
+    from paper_2603_19789_gb300 import inputs
+    from paper_2603_19789_gb300 import sslbm as L
+
+    rank, world, local = dist_setup(args.gpus)
+    libbuild.build()
+    L.load()
+    stream = torch.cuda.current_stream()
+    wl = inputs.roofline_workload(NX, NY)
+    state64 = wl["state"]
+    state32 = np.ascontiguousarray(state64.astype(np.float32))
+    rates = wl["rates"].as_tuple()
+
+    s = L.Solver(NX, NY, rates, d=wl["d"], bc=wl["bc"], precision=L.FP32)
+    if args.depth:
+        s.set_blocking(args.depth)
+    depth, seg = s.get_blocking()
+    s.write(state32)
+    for _ in range(args.warmup):
+        s.step(LATTICE_STEPS_PER_STEP)
+        s.diagnostics()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms, kern_ms = timed_steps(s, LATTICE_STEPS_PER_STEP, args.steps, stream)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    barrier(world)
+    total_ms = max_over_ranks(total_ms, world)
+    cells = NX * NY
+    value = world * cells * LATTICE_STEPS_PER_STEP * args.steps / (total_ms * 1e-3) / 1e9
+    launches_per_step = math.ceil(LATTICE_STEPS_PER_STEP / depth) + 2  # blocked launches + 2 diagnostics kernels
+    launch_ms = kern_ms / (args.steps * math.ceil(LATTICE_STEPS_PER_STEP / depth))
+    hbm, peak_kind = load_peaks()
+    achieved = BYTES_PER_CELL_FP32 * cells / (launch_ms * 1e-3) / 1e9
+    tot, peak_I = s.diagnostics()
+
+    extras = {}
+    if not args.no_extras:
+        extras = secondary_timings(L, wl, state64, state32, stream, hbm)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_timing(L, torch, s, state32, stream, world)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        g, steps_cpu, shape, el = cpu_oracle_glups(state64, wl, budget_s=10.0, rows=2048)
+        import oracle
+        cpu = {"value": g, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{steps_cpu} FP64 oracle lattice steps on a {shape[2]}x{shape[1]} band of the "
+                         f"{NX}x{NY} grid ({el:.1f} s)"}
+    s.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "nx": NX, "ny": NY, "bc": "no-flux",
+                       "precision": "fp32", "lattice_steps_per_step": LATTICE_STEPS_PER_STEP,
+                       "temporal_block_depth": depth, "seg_rows": seg or "auto",
+                       "l2": "state 1.34 GB > 129 MB L2 (no flush needed)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": f"blocked_kernel<fp32, K={depth}>",
+                         "bytes_per_launch": BYTES_PER_CELL_FP32 * cells,
+                         "launch_ms": launch_ms,
+                         "cell_updates_per_launch": cells * depth},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "diagnostics": {"total_population": float(tot.sum()), "peak_I": peak_I},
+            "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e_timing(L, torch, s, state32, stream, world, steps=3):
+    """IC in from pinned host memory, 100 lattice steps, diagnostics, final state out."""
+    host_in = torch.from_numpy(state32).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    L.sslbm_write(s.h, L.SCHEME_SSLBM, L.ALL, host_in)
+    s.step(LATTICE_STEPS_PER_STEP)
+    L.sslbm_read(s.h, L.SCHEME_SSLBM, L.ALL, host_out)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        L.sslbm_write(s.h, L.SCHEME_SSLBM, L.ALL, host_in)
+        s.step(LATTICE_STEPS_PER_STEP)
+        s.diagnostics()
+        L.sslbm_read(s.h, L.SCHEME_SSLBM, L.ALL, host_out)
+    torch.cuda.synchronize()
+    el = max_over_ranks(time.perf_counter() - t0, world)
+    v = world * NX * NY * LATTICE_STEPS_PER_STEP * steps / el / 1e9
+    nbytes = host_in.numel() * host_in.element_size()
+    return {"value": v, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 48,
+            "steps": steps, "ms_per_step": el / steps * 1e3}
+
+
+def secondary_timings(L, wl, state64, state32, stream, hbm):
+    """Other variants on the same grid: FP64, deviation-S, Kahan, depth sweep, BGK."""
+    import torch
+    out = {}
+    rates = wl["rates"].as_tuple()
+    cells = NX * NY
+
+    def glups_of(precision, n_lat, reps, depth=None, schemes=L.WANT_SSLBM, bgk=False):
+        s = L.Solver(NX, NY, rates, d=wl["d"], bc=wl["bc"], precision=precision, schemes=schemes)
+        if depth:
+            s.set_blocking(depth)
+        if bgk:
+            s.write(state64, scheme=L.SCHEME_BGK)
+        else:
+            s.write(state32 if precision != L.FP64 else state64)
+        run = s.bgk_step if bgk else s.step
+        run(n_lat)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            run(n_lat)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+        return cells * n_lat * reps / (ms * 1e-3) / 1e9, ms / (n_lat * reps)
+
+    for k in (1, 2, 3, 4):
+        g, ms = glups_of(L.FP32, 48, 4, depth=k)
+        out[f"fp32_depth{k}_glups"] = g
+        if k == 1:
+            out["fp32_depth1_hbm_frac"] = BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm
+    g, _ = glups_of(L.FP32_DEV, 48, 4)
+    out["fp32_dev_glups"] = g
+    g, _ = glups_of(L.FP32_KAHAN, 20, 2)
+    out["fp32_kahan_glups"] = g
+    g, ms = glups_of(L.FP64, 20, 2)
+    out["fp64_glups"] = g
+    out["fp64_hbm_frac"] = BYTES_PER_CELL_FP64 * cells / (ms * 1e-3) / 1e9 / hbm
+    g, ms = glups_of(L.FP32, 20, 2, schemes=L.WANT_BGK, bgk=True)
+    out["bgk_fp32_glups"] = g
+    out["bgk_fp32_hbm_frac"] = BGK_BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm
+    return out
+
+
+if __name__ == "__main__":
+    main()

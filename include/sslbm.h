@@ -1,0 +1,198 @@
+/*
+ * sslbm.h -- C ABI of libsslbm.so, the GB300 (sm_103a) solver for the 2D SEIRD
+ * reaction-diffusion model of De Rosis, "A distribution-free lattice Boltzmann
+ * method for compartmental reaction-diffusion systems with application to epidemic
+ * modelling" (arXiv 2603.19789).
+ *
+ * Two schemes advance the same problem:
+ *   - the single-step simplified lattice Boltzmann method (SSLBM), Sec. II.C,
+ *     Eq. (sslbm_final_clean) for S, E, I, R and the explicit update of Eq. (rhoD)
+ *     for D -- the hot path;
+ *   - the BGK lattice Boltzmann scheme of Sec. II.B, Eq. (pdf), on the D2Q5
+ *     lattice with one population set per mobile compartment -- the comparison.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returning int returns SSLBM_OK (0) or a negative status
+ *     (SSLBM_ERR_*); sslbm_strerror() names it and sslbm_last_error() gives the
+ *     detail of the last failure on the calling thread.  No function aborts the
+ *     process or traps on the device.
+ *   - Fields are 2D planes of ny rows by nx cells, row-major with x fastest
+ *     (cell (x, y) at index y*nx + x), in the compartment order S, E, I, R, D
+ *     (SSLBM_S .. SSLBM_D).  The paper's lattice is D2Q5 with dx in the lattice's
+ *     length unit and dt in its time unit; densities are per cell.
+ *   - Memory: the caller owns all device memory.  sslbm_workspace_bytes() says how
+ *     much one solver needs; the caller allocates it (e.g. with PyTorch) and passes
+ *     it to sslbm_create(); the library never allocates device memory.  The handle
+ *     itself is a small host object owned by the library until sslbm_destroy().
+ *   - Streams: all device work of a handle is ordered on the CUDA stream given at
+ *     creation (or sslbm_set_stream()).  sslbm_step / bgk_step only enqueue work.
+ *     Calls that return data to the host (sslbm_read to a host pointer,
+ *     sslbm_diagnostics) synchronise that stream before returning.
+ *   - A handle is not thread-safe: one thread drives it at a time.
+ */
+#ifndef SSLBM_H
+#define SSLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define SSLBM_OK 0
+#define SSLBM_ERR_BAD_ARG (-1)     /* null pointer, bad enum, non-positive size ... */
+#define SSLBM_ERR_UNSTABLE (-2)    /* parameters outside the scheme's stability range */
+#define SSLBM_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define SSLBM_ERR_TIMEOUT (-4)     /* a bounded device wait ran out (ensemble barrier) */
+#define SSLBM_ERR_NONFINITE (-5)   /* a diagnostic found NaN or Inf in the state */
+#define SSLBM_ERR_WORKSPACE (-6)   /* workspace missing, too small or misaligned */
+#define SSLBM_ERR_UNSUPPORTED (-7) /* valid request this build does not provide */
+#define SSLBM_ERR_STATE (-8)       /* call out of order (e.g. stepping an unwritten scheme) */
+
+/* ---- enumerations ------------------------------------------------------- */
+enum { SSLBM_BC_PERIODIC = 0, SSLBM_BC_NOFLUX = 1 };
+/* Storage and arithmetic precision of a solver's fields.
+ *   FP64       : double fields, double arithmetic.
+ *   FP32       : float fields, float arithmetic.
+ *   FP32_DEV   : float fields; S is stored as its deviation sigma = s_ref - S from a
+ *                uniform reference value, so that increments of order 1e-7 next to
+ *                S ~ 1 are not rounded away.  Diffusion of sigma is that of S with the
+ *                sign flipped (the stencil annihilates the constant s_ref exactly).
+ *   FP32_KAHAN : float fields plus one float compensation plane per compartment;
+ *                every step's increment is added with compensated (Kahan) summation. */
+enum { SSLBM_FP64 = 0, SSLBM_FP32 = 1, SSLBM_FP32_DEV = 2, SSLBM_FP32_KAHAN = 3 };
+enum { SSLBM_SCHEME_SSLBM = 0, SSLBM_SCHEME_BGK = 1 };
+enum { SSLBM_S = 0, SSLBM_E = 1, SSLBM_I = 2, SSLBM_R = 3, SSLBM_D = 4, SSLBM_NCOMP = 5 };
+enum { SSLBM_ALL = -1 }; /* comp argument: all five planes, consecutive */
+enum { SSLBM_DT_F64 = 0, SSLBM_DT_F32 = 1 };
+/* schemes bitmask of sslbm_grid */
+enum { SSLBM_WANT_SSLBM = 1, SSLBM_WANT_BGK = 2 };
+
+/* ---- problem description (Sec. II.A problem statement, Sec. III test case) -- */
+typedef struct sslbm_grid {
+  int64_t nx, ny;      /* lattice cells along x and y, each >= 1 */
+  double dx, dt;       /* lattice spacing and time step (> 0); lattice units: 1, 1 */
+  int32_t bc;          /* SSLBM_BC_PERIODIC or SSLBM_BC_NOFLUX (homogeneous Neumann,
+                          cell-centred mirror; BGK: halfway bounce-back) */
+  int32_t precision;   /* SSLBM_FP64 .. SSLBM_FP32_KAHAN (BGK supports FP64 and FP32) */
+  int32_t schemes;     /* SSLBM_WANT_SSLBM | SSLBM_WANT_BGK: which state to hold */
+  int32_t reserved;    /* must be 0 */
+} sslbm_grid;
+
+/* Epidemiological parameters in the notation of Table I:
+ * beta contact rate, alpha incubation rate (inverse mean incubation period),
+ * gamma removal rate (I -> R or D), phi infection fatality ratio (0 <= phi <= 1).
+ * Rates are per unit of dt.  Diffusion: either physical coefficients d[C]
+ * (units dx^2 / dt, d[SSLBM_D] must be 0) converted with Eq. (diffusivity),
+ * tau = 3 d dt / dx^2 + 1/2, or relaxation times tau[C] directly (use_tau != 0).
+ * Stability (von Neumann analysis of Sec. II.C with the amplification
+ * G = 1 - (2 tau - 1)(1 - Lambda)): 1/2 <= tau <= 5/4 for each mobile compartment,
+ * otherwise sslbm_create returns SSLBM_ERR_UNSTABLE.  With strict != 0 the
+ * nonnegativity condition 4 d_lattice + (outflow rate) dt <= 1 (outflow beta for S,
+ * alpha for E, gamma for I) is enforced as well. */
+typedef struct sslbm_params {
+  double beta, alpha, gamma, phi;
+  double d[5];        /* S, E, I, R, D */
+  double tau[4];      /* S, E, I, R (read when use_tau != 0) */
+  double s_ref;       /* FP32_DEV: reference value of S (typically the total density) */
+  int32_t use_tau;
+  int32_t strict;
+} sslbm_params;
+
+typedef struct sslbm_handle sslbm_handle;
+
+/* ---- lifecycle -------------------------------------------------------------- */
+
+/* Name of a status code (static string, never NULL). */
+const char* sslbm_strerror(int status);
+
+/* Detail of the last failure on the calling thread (static thread-local buffer). */
+const char* sslbm_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int sslbm_version(void);
+
+/* Bytes of device workspace a solver for grid g needs (both ping-pong state
+ * buffers of each requested scheme, the diagnostics scratch and padding).
+ * Writes *bytes; returns SSLBM_ERR_BAD_ARG for an invalid grid. */
+int sslbm_workspace_bytes(const sslbm_grid* g, size_t* bytes);
+
+/* Create a solver.  g, p: problem (copied).  dev_ws: caller-owned device memory of
+ * at least sslbm_workspace_bytes(g) bytes, 256-byte aligned, which must outlive the
+ * handle.  stream: a cudaStream_t (NULL = legacy default stream).  On success
+ * *out receives the handle and the state of each scheme is zero until written.
+ * Validates the parameters (see sslbm_params) and converts d -> tau with
+ * Eq. (diffusivity). */
+int sslbm_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_t ws_bytes,
+                 void* stream, sslbm_handle** out);
+
+/* Change the stream subsequent work is ordered on. */
+int sslbm_set_stream(sslbm_handle* h, void* stream);
+
+/* Destroy the handle (host object only; the caller frees the workspace afterwards,
+ * once work on the stream has finished).  NULL is accepted. */
+void sslbm_destroy(sslbm_handle* h);
+
+/* ---- state transfer ------------------------------------------------------------ */
+
+/* Set compartment comp (SSLBM_S..SSLBM_D, or SSLBM_ALL for five consecutive planes)
+ * of scheme `scheme` from src: ny*nx values of type src_dtype (SSLBM_DT_F64 or
+ * SSLBM_DT_F32) per plane, row-major, on the host (src_on_device = 0, pageable or
+ * pinned) or the device (src_on_device = 1).  Values are rounded to the solver's
+ * precision.  For BGK the populations of the written compartments are set to the
+ * equilibrium f_i = w_i rho (Sec. II.B; the initial populations are not stated in
+ * the paper).  Resets that scheme's Kahan compensation and, when comp is
+ * SSLBM_ALL, its step counter.  Host sources are consumed before the call returns. */
+int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_dtype,
+                int src_on_device);
+
+/* Copy compartment comp (or SSLBM_ALL) of scheme `scheme` to dst in dst_dtype; for
+ * BGK the density rho = sum_i f_i.  FP32_DEV returns S = s_ref - sigma and
+ * FP32_KAHAN the compensated value, both evaluated in double precision.
+ * A host destination synchronises the stream; a device destination is stream-ordered. */
+int sslbm_read(sslbm_handle* h, int scheme, int comp, void* dst, int dst_dtype, int dst_on_device);
+
+/* ---- time stepping ------------------------------------------------------------------ */
+
+/* Advance the SSLBM state by n >= 0 time steps: Eq. (sslbm_final_clean) for S, E, I,
+ * R with rho_f, rho_b, rho_c of Eqs. (rhof, rhob, rhoc) on the D2Q5 lattice and the
+ * sources of Eq. (sources) at (x, t), and D(t+dt) = D + phi gamma I dt (Eq. rhoD).
+ * On D2Q5 rho_f = rho_b, so the kernels evaluate the algebraically identical
+ * rho_c + d_lattice (sum of the four neighbours - 4 rho_c) + Psi dt.
+ * Several steps are fused per pass over memory (temporal blocking, depth set by
+ * sslbm_set_blocking or sslbm_autotune); results do not depend on the depth beyond
+ * the order of floating-point operations, which is the same for every depth.
+ * Enqueues on the handle's stream and returns. */
+int sslbm_step(sslbm_handle* h, int64_t n);
+
+/* Advance the BGK state by n >= 0 steps of Eq. (pdf) (collide, then stream along
+ * the D2Q5 links; no-flux walls by halfway bounce-back) with D by Eq. (rhoD). */
+int bgk_step(sslbm_handle* h, int64_t n);
+
+/* Steps taken by a scheme since its last full write. */
+int64_t sslbm_steps_done(const sslbm_handle* h, int scheme);
+
+/* ---- diagnostics (Sec. II.C 'Mass conservation') ------------------------------------ */
+
+/* Per-compartment totals sum_x rho^C(x) accumulated in double precision, and the
+ * peak infected density max_x I(x), of a scheme's current state.  totals: 5 doubles
+ * (may be NULL), peak_I (may be NULL).  Synchronises the stream.  Returns
+ * SSLBM_ERR_NONFINITE if any total is NaN or Inf (results still written). */
+int sslbm_diagnostics(sslbm_handle* h, int scheme, double* totals, double* peak_I);
+
+/* ---- tuning --------------------------------------------------------------------------- */
+
+/* Temporal-blocking depth k (steps fused per pass, 1..SSLBM_MAX_DEPTH) and the
+ * kernel's row-segment length seg_rows (0 = automatic).  k = 0 restores the default. */
+#define SSLBM_MAX_DEPTH 4
+int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows);
+
+/* Current blocking depth and segment length. */
+int sslbm_get_blocking(const sslbm_handle* h, int* k, int* seg_rows);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSLBM_H */

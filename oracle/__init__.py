@@ -153,6 +153,17 @@ def sslbm_run(state, tau, rates, dt: float = 1.0, bc: int = 0, nsteps: int = 1) 
     return a
 
 
+def sslbm_run_inplace(state: np.ndarray, scratch: np.ndarray, tau, rates, dt: float = 1.0,
+                      bc: int = 0, nsteps: int = 1) -> None:
+    """sslbm_run on caller-owned float64 (5, ny, nx) buffers, without copies (used to
+    time the oracle itself)."""
+    lib = _load()
+    _, ny, nx = state.shape
+    assert scratch.shape == state.shape
+    lib.oracle_sslbm_run(nx, ny, int(bc), _ptr(_vec(tau, 4)), _ptr(_vec(rates, 4)), float(dt),
+                         int(nsteps), _ptr(state), _ptr(scratch))
+
+
 def bgk_init(state):
     """Equilibrium initialisation f_i = w_i rho; returns (f (4,5,ny,nx), D (ny,nx))."""
     lib = _load()

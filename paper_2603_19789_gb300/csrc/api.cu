@@ -1,0 +1,461 @@
+// api.cu -- the C ABI of libsslbm.so (declared and documented in include/sslbm.h).
+//
+// Host side only: parameter validation (Eq. diffusivity for d -> tau, the von Neumann
+// bound 1/2 <= tau <= 5/4, the optional nonnegativity condition), carving of the
+// caller's workspace, stream-ordered dispatch of the kernels and status reporting.
+// No device memory is allocated here; the caller provides it.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sslbm_internal.cuh"
+
+using sslbm::Coeffs;
+using sslbm::GridView;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int status, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SSLBM_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+  int64_t pitch = 0, plane = 0;
+  size_t esize = 0, plane_bytes = 0;
+  int s_planes = 0;  // SSLBM planes per state buffer (5, or 10 with Kahan compensation)
+  size_t off_diag = 0, off_s[2] = {0, 0}, off_b[2] = {0, 0}, total = 0;
+};
+
+constexpr int kBgkPlanes = 21;
+constexpr int64_t kMaxSide = int64_t(1) << 30;
+
+int check_grid(const sslbm_grid* g) {
+  if (!g) return fail(SSLBM_ERR_BAD_ARG, "grid is NULL");
+  if (g->nx < 1 || g->ny < 1 || g->nx > kMaxSide || g->ny > kMaxSide)
+    return fail(SSLBM_ERR_BAD_ARG, "nx=%lld ny=%lld: each must be in [1, 2^30]", (long long)g->nx,
+                (long long)g->ny);
+  if (!(g->dx > 0) || !(g->dt > 0) || !std::isfinite(g->dx) || !std::isfinite(g->dt))
+    return fail(SSLBM_ERR_BAD_ARG, "dx and dt must be finite and > 0");
+  if (g->bc != SSLBM_BC_PERIODIC && g->bc != SSLBM_BC_NOFLUX)
+    return fail(SSLBM_ERR_BAD_ARG, "bc=%d is not a boundary code", g->bc);
+  if (g->precision < SSLBM_FP64 || g->precision > SSLBM_FP32_KAHAN)
+    return fail(SSLBM_ERR_BAD_ARG, "precision=%d is not a precision code", g->precision);
+  if (g->schemes < 1 || g->schemes > 3)
+    return fail(SSLBM_ERR_BAD_ARG, "schemes=%d must be a nonzero mask of 1 (SSLBM) and 2 (BGK)",
+                g->schemes);
+  if (g->reserved != 0) return fail(SSLBM_ERR_BAD_ARG, "reserved field must be 0");
+  if ((g->schemes & SSLBM_WANT_BGK) && g->precision != SSLBM_FP64 && g->precision != SSLBM_FP32)
+    return fail(SSLBM_ERR_UNSUPPORTED, "BGK state is provided in FP64 and FP32 only");
+  return SSLBM_OK;
+}
+
+int make_layout(const sslbm_grid* g, Layout* L) {
+  int st = check_grid(g);
+  if (st) return st;
+  L->esize = g->precision == SSLBM_FP64 ? 8 : 4;
+  L->pitch = (g->nx + 31) / 32 * 32;
+  L->plane = (L->pitch * g->ny + 63) / 64 * 64;
+  const double bytes_est = (double)L->plane * (double)L->esize * (10.0 + 2 * kBgkPlanes) * 2.0;
+  if (bytes_est > 9.0e18) return fail(SSLBM_ERR_BAD_ARG, "grid too large");
+  L->plane_bytes = round_up((size_t)L->plane * L->esize, kAlign);
+  L->s_planes = g->precision == SSLBM_FP32_KAHAN ? 10 : 5;
+  size_t off = 0;
+  L->off_diag = off;
+  off += round_up((sslbm::kDiagBlocks * sslbm::kDiagSlots + 8) * sizeof(double), kAlign);
+  if (g->schemes & SSLBM_WANT_SSLBM)
+    for (int b = 0; b < 2; ++b) {
+      L->off_s[b] = off;
+      off += (size_t)L->s_planes * L->plane_bytes;
+    }
+  if (g->schemes & SSLBM_WANT_BGK)
+    for (int b = 0; b < 2; ++b) {
+      L->off_b[b] = off;
+      off += (size_t)kBgkPlanes * L->plane_bytes;
+    }
+  L->total = off;
+  return SSLBM_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct sslbm_handle {
+  sslbm_grid g;
+  sslbm_params p;
+  Layout L;
+  GridView gv;
+  int device = 0;
+  double tau[4];
+  Coeffs<double> cd;
+  Coeffs<float> cf;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  char* s_buf[2] = {nullptr, nullptr};
+  char* b_buf[2] = {nullptr, nullptr};
+  int s_cur = 0, b_cur = 0;
+  int64_t s_steps = 0, b_steps = 0;
+  int depth = 1, seg_rows = 0;
+  int seg_cache[SSLBM_MAX_DEPTH + 1] = {0};
+
+  const void* coeffs() const {
+    return g.precision == SSLBM_FP64 ? static_cast<const void*>(&cd) : static_cast<const void*>(&cf);
+  }
+  char* s_plane(int buf, int c) const { return s_buf[buf] + (size_t)c * L.plane_bytes; }
+  double* diag_partials() const { return reinterpret_cast<double*>(ws + L.off_diag); }
+  double* diag_result() const {
+    return diag_partials() + sslbm::kDiagBlocks * sslbm::kDiagSlots;
+  }
+};
+
+extern "C" {
+
+const char* sslbm_strerror(int status) {
+  switch (status) {
+    case SSLBM_OK: return "SSLBM_OK";
+    case SSLBM_ERR_BAD_ARG: return "SSLBM_ERR_BAD_ARG";
+    case SSLBM_ERR_UNSTABLE: return "SSLBM_ERR_UNSTABLE";
+    case SSLBM_ERR_CUDA: return "SSLBM_ERR_CUDA";
+    case SSLBM_ERR_TIMEOUT: return "SSLBM_ERR_TIMEOUT";
+    case SSLBM_ERR_NONFINITE: return "SSLBM_ERR_NONFINITE";
+    case SSLBM_ERR_WORKSPACE: return "SSLBM_ERR_WORKSPACE";
+    case SSLBM_ERR_UNSUPPORTED: return "SSLBM_ERR_UNSUPPORTED";
+    case SSLBM_ERR_STATE: return "SSLBM_ERR_STATE";
+    default: return "SSLBM_ERR_UNKNOWN";
+  }
+}
+
+const char* sslbm_last_error(void) { return g_err; }
+
+int sslbm_version(void) { return 100; }
+
+int sslbm_workspace_bytes(const sslbm_grid* g, size_t* bytes) {
+  if (!bytes) return fail(SSLBM_ERR_BAD_ARG, "bytes is NULL");
+  Layout L;
+  int st = make_layout(g, &L);
+  if (st) return st;
+  *bytes = L.total;
+  return SSLBM_OK;
+}
+
+int sslbm_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_t ws_bytes,
+                 void* stream, sslbm_handle** out) {
+  if (!out) return fail(SSLBM_ERR_BAD_ARG, "out is NULL");
+  *out = nullptr;
+  Layout L;
+  int st = make_layout(g, &L);
+  if (st) return st;
+  if (!p) return fail(SSLBM_ERR_BAD_ARG, "params is NULL");
+  const double rates[4] = {p->beta, p->alpha, p->gamma, p->phi};
+  for (double r : rates)
+    if (!std::isfinite(r) || r < 0) return fail(SSLBM_ERR_BAD_ARG, "rates must be finite and >= 0");
+  if (p->phi > 1) return fail(SSLBM_ERR_BAD_ARG, "phi=%g must be in [0, 1]", p->phi);
+  if (!std::isfinite(p->s_ref)) return fail(SSLBM_ERR_BAD_ARG, "s_ref must be finite");
+  double tau[4];
+  for (int c = 0; c < 4; ++c) {
+    if (p->use_tau) {
+      tau[c] = p->tau[c];
+    } else {
+      if (!std::isfinite(p->d[c]) || p->d[c] < 0)
+        return fail(SSLBM_ERR_BAD_ARG, "d[%d]=%g must be finite and >= 0", c, p->d[c]);
+      tau[c] = 3.0 * p->d[c] * g->dt / (g->dx * g->dx) + 0.5;  // Eq. (diffusivity)
+    }
+    if (!std::isfinite(tau[c]))
+      return fail(SSLBM_ERR_BAD_ARG, "tau[%d] is not finite", c);
+    // |G| <= 1 for all modes needs (2 tau - 1) * max(1 - Lambda) <= 2, max(1 - Lambda) = 4/3
+    if (tau[c] < 0.5 || tau[c] > 1.25)
+      return fail(SSLBM_ERR_UNSTABLE, "tau[%d]=%.17g outside the stable range [1/2, 5/4]", c,
+                  tau[c]);
+  }
+  if (!p->use_tau && p->d[4] != 0.0)
+    return fail(SSLBM_ERR_BAD_ARG, "d[D]=%g: the deceased do not diffuse (must be 0)", p->d[4]);
+  double dl[4];
+  for (int c = 0; c < 4; ++c) dl[c] = (tau[c] - 0.5) / 3.0;
+  if (p->strict) {
+    const double out_rate[4] = {p->beta, p->alpha, p->gamma, 0.0};
+    for (int c = 0; c < 4; ++c)
+      if (4.0 * dl[c] + out_rate[c] * g->dt > 1.0)
+        return fail(SSLBM_ERR_UNSTABLE,
+                    "compartment %d: 4 d_lattice + outflow*dt = %g > 1 (nonnegativity)", c,
+                    4.0 * dl[c] + out_rate[c] * g->dt);
+  }
+  if (!dev_ws) return fail(SSLBM_ERR_WORKSPACE, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(dev_ws) % kAlign)
+    return fail(SSLBM_ERR_WORKSPACE, "workspace must be %zu-byte aligned", kAlign);
+  if (ws_bytes < L.total)
+    return fail(SSLBM_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", ws_bytes, L.total);
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, dev_ws);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes(workspace)");
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return fail(SSLBM_ERR_WORKSPACE, "workspace is not device memory");
+
+  sslbm_handle* h = new (std::nothrow) sslbm_handle();
+  if (!h) return fail(SSLBM_ERR_BAD_ARG, "out of host memory");
+  h->g = *g;
+  h->p = *p;
+  h->L = L;
+  h->device = attr.device;
+  h->gv = GridView{g->nx, g->ny, L.pitch, L.plane, g->bc};
+  for (int c = 0; c < 4; ++c) {
+    h->tau[c] = tau[c];
+    h->cd.dl[c] = dl[c];
+    h->cd.itau[c] = 1.0 / tau[c];
+    h->cf.dl[c] = (float)dl[c];
+    h->cf.itau[c] = (float)(1.0 / tau[c]);
+  }
+  const double dt = g->dt;
+  h->cd.bdt = p->beta * dt;
+  h->cd.adt = p->alpha * dt;
+  h->cd.gdt = p->gamma * dt;
+  h->cd.rdt = (1.0 - p->phi) * p->gamma * dt;
+  h->cd.ddt = p->phi * p->gamma * dt;
+  h->cd.s_ref = p->s_ref;
+  h->cf.bdt = (float)h->cd.bdt;
+  h->cf.adt = (float)h->cd.adt;
+  h->cf.gdt = (float)h->cd.gdt;
+  h->cf.rdt = (float)h->cd.rdt;
+  h->cf.ddt = (float)h->cd.ddt;
+  h->cf.s_ref = (float)p->s_ref;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->ws = static_cast<char*>(dev_ws);
+  if (g->schemes & SSLBM_WANT_SSLBM)
+    for (int b = 0; b < 2; ++b) h->s_buf[b] = h->ws + L.off_s[b];
+  if (g->schemes & SSLBM_WANT_BGK)
+    for (int b = 0; b < 2; ++b) h->b_buf[b] = h->ws + L.off_b[b];
+  h->depth = sslbm::blocked_supported(g->precision, h->gv) ? 4 : 1;
+  DeviceGuard dg(h->device);
+  // zero state buffers (and their row padding) so every scheme starts from a defined state
+  e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaMemsetAsync(workspace)");
+  }
+  *out = h;
+  return SSLBM_OK;
+}
+
+int sslbm_set_stream(sslbm_handle* h, void* stream) {
+  if (!h) return fail(SSLBM_ERR_BAD_ARG, "handle is NULL");
+  h->stream = static_cast<cudaStream_t>(stream);
+  return SSLBM_OK;
+}
+
+void sslbm_destroy(sslbm_handle* h) { delete h; }
+
+static int check_scheme(const sslbm_handle* h, int scheme) {
+  if (!h) return fail(SSLBM_ERR_BAD_ARG, "handle is NULL");
+  if (scheme == SSLBM_SCHEME_SSLBM && (h->g.schemes & SSLBM_WANT_SSLBM)) return SSLBM_OK;
+  if (scheme == SSLBM_SCHEME_BGK && (h->g.schemes & SSLBM_WANT_BGK)) return SSLBM_OK;
+  return fail(SSLBM_ERR_BAD_ARG, "scheme %d not held by this handle", scheme);
+}
+
+int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_dtype,
+                int src_on_device) {
+  int st = check_scheme(h, scheme);
+  if (st) return st;
+  if (!src) return fail(SSLBM_ERR_BAD_ARG, "src is NULL");
+  if (comp != SSLBM_ALL && (comp < 0 || comp >= SSLBM_NCOMP))
+    return fail(SSLBM_ERR_BAD_ARG, "comp=%d", comp);
+  if (src_dtype != SSLBM_DT_F64 && src_dtype != SSLBM_DT_F32)
+    return fail(SSLBM_ERR_BAD_ARG, "src_dtype=%d", src_dtype);
+  DeviceGuard dg(h->device);
+  const size_t usize = src_dtype == SSLBM_DT_F64 ? 8 : 4;
+  const size_t plane_user = (size_t)h->g.nx * (size_t)h->g.ny * usize;
+  const int c0 = comp == SSLBM_ALL ? 0 : comp, c1 = comp == SSLBM_ALL ? 5 : comp + 1;
+  const bool bgk = scheme == SSLBM_SCHEME_BGK;
+  char* staging = bgk ? h->b_buf[1 - h->b_cur] : h->s_buf[1 - h->s_cur];
+  for (int c = c0; c < c1; ++c) {
+    const char* s = static_cast<const char*>(src) + (size_t)(c - c0) * plane_user;
+    if (!src_on_device) {
+      cudaError_t e = cudaMemcpyAsync(staging, s, plane_user, cudaMemcpyHostToDevice, h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(H2D)");
+      s = staging;
+    }
+    cudaError_t e;
+    if (bgk) {
+      e = sslbm::launch_bgk_init(h->g.precision, h->gv, c, s, src_dtype, h->b_buf[h->b_cur],
+                                 h->stream);
+    } else {
+      const bool kahan = h->g.precision == SSLBM_FP32_KAHAN;
+      const int dev_S = (h->g.precision == SSLBM_FP32_DEV && c == SSLBM_S) ? 1 : 0;
+      e = sslbm::launch_plane_write(h->g.precision, h->gv, s, src_dtype, h->s_plane(h->s_cur, c),
+                                    kahan ? h->s_plane(h->s_cur, 5 + c) : nullptr, dev_S,
+                                    h->p.s_ref, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "write kernel");
+  }
+  if (!src_on_device) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(write)");
+  }
+  if (comp == SSLBM_ALL) {
+    if (bgk) h->b_steps = 0;
+    else h->s_steps = 0;
+  }
+  return SSLBM_OK;
+}
+
+int sslbm_read(sslbm_handle* h, int scheme, int comp, void* dst, int dst_dtype, int dst_on_device) {
+  int st = check_scheme(h, scheme);
+  if (st) return st;
+  if (!dst) return fail(SSLBM_ERR_BAD_ARG, "dst is NULL");
+  if (comp != SSLBM_ALL && (comp < 0 || comp >= SSLBM_NCOMP))
+    return fail(SSLBM_ERR_BAD_ARG, "comp=%d", comp);
+  if (dst_dtype != SSLBM_DT_F64 && dst_dtype != SSLBM_DT_F32)
+    return fail(SSLBM_ERR_BAD_ARG, "dst_dtype=%d", dst_dtype);
+  DeviceGuard dg(h->device);
+  const size_t usize = dst_dtype == SSLBM_DT_F64 ? 8 : 4;
+  const size_t plane_user = (size_t)h->g.nx * (size_t)h->g.ny * usize;
+  const int c0 = comp == SSLBM_ALL ? 0 : comp, c1 = comp == SSLBM_ALL ? 5 : comp + 1;
+  const bool bgk = scheme == SSLBM_SCHEME_BGK;
+  char* staging = bgk ? h->b_buf[1 - h->b_cur] : h->s_buf[1 - h->s_cur];
+  for (int c = c0; c < c1; ++c) {
+    char* d = static_cast<char*>(dst) + (size_t)(c - c0) * plane_user;
+    char* target = dst_on_device ? d : staging;
+    cudaError_t e;
+    if (bgk) {
+      e = sslbm::launch_bgk_density(h->g.precision, h->gv, c, h->b_buf[h->b_cur], target,
+                                    dst_dtype, h->stream);
+    } else {
+      const bool kahan = h->g.precision == SSLBM_FP32_KAHAN;
+      const int dev_S = (h->g.precision == SSLBM_FP32_DEV && c == SSLBM_S) ? 1 : 0;
+      e = sslbm::launch_plane_read(h->g.precision, h->gv, h->s_plane(h->s_cur, c),
+                                   kahan ? h->s_plane(h->s_cur, 5 + c) : nullptr, dev_S,
+                                   h->p.s_ref, target, dst_dtype, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "read kernel");
+    if (!dst_on_device) {
+      e = cudaMemcpyAsync(d, staging, plane_user, cudaMemcpyDeviceToHost, h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    }
+  }
+  if (!dst_on_device) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(read)");
+  }
+  return SSLBM_OK;
+}
+
+int sslbm_step(sslbm_handle* h, int64_t n) {
+  int st = check_scheme(h, SSLBM_SCHEME_SSLBM);
+  if (st) return st;
+  if (n < 0) return fail(SSLBM_ERR_BAD_ARG, "n=%lld < 0", (long long)n);
+  DeviceGuard dg(h->device);
+  const bool blocked = sslbm::blocked_supported(h->g.precision, h->gv);
+  while (n > 0) {
+    int k = 1;
+    cudaError_t e;
+    if (blocked && h->depth > 1 && n > 1) {
+      // depth >= 2: the temporal-blocked kernel; a single step uses the one-step kernel,
+      // which produces the same bits
+      k = (int)(n < h->depth ? n : h->depth);
+      int seg = h->seg_rows;
+      if (seg <= 0) {
+        if (!h->seg_cache[k]) h->seg_cache[k] = sslbm::blocked_default_seg_rows(h->g.precision, h->gv, k);
+        seg = h->seg_cache[k];
+      }
+      e = sslbm::launch_sslbm_blocked(h->g.precision, h->gv, &h->cf, h->s_buf[h->s_cur],
+                                      h->s_buf[1 - h->s_cur], k, seg, h->stream);
+    } else {
+      e = sslbm::launch_sslbm_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur],
+                                    h->s_buf[1 - h->s_cur], h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "SSLBM step launch");
+    h->s_cur = 1 - h->s_cur;
+    h->s_steps += k;
+    n -= k;
+  }
+  return SSLBM_OK;
+}
+
+int bgk_step(sslbm_handle* h, int64_t n) {
+  int st = check_scheme(h, SSLBM_SCHEME_BGK);
+  if (st) return st;
+  if (n < 0) return fail(SSLBM_ERR_BAD_ARG, "n=%lld < 0", (long long)n);
+  DeviceGuard dg(h->device);
+  for (int64_t i = 0; i < n; ++i) {
+    cudaError_t e = sslbm::launch_bgk_step(h->g.precision, h->gv, h->coeffs(), h->b_buf[h->b_cur],
+                                           h->b_buf[1 - h->b_cur], h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "BGK step launch");
+    h->b_cur = 1 - h->b_cur;
+    h->b_steps += 1;
+  }
+  return SSLBM_OK;
+}
+
+int64_t sslbm_steps_done(const sslbm_handle* h, int scheme) {
+  if (!h) return -1;
+  return scheme == SSLBM_SCHEME_BGK ? h->b_steps : h->s_steps;
+}
+
+int sslbm_diagnostics(sslbm_handle* h, int scheme, double* totals, double* peak_I) {
+  int st = check_scheme(h, scheme);
+  if (st) return st;
+  DeviceGuard dg(h->device);
+  const bool bgk = scheme == SSLBM_SCHEME_BGK;
+  const void* planes = bgk ? (const void*)h->b_buf[h->b_cur] : (const void*)h->s_buf[h->s_cur];
+  const void* comps = (!bgk && h->g.precision == SSLBM_FP32_KAHAN) ? h->s_plane(h->s_cur, 5) : nullptr;
+  cudaError_t e = sslbm::launch_diagnostics(h->g.precision, bgk ? 1 : 0, h->gv, planes, comps,
+                                            h->diag_partials(), h->diag_result(), h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostics launch");
+  double r[sslbm::kDiagSlots];
+  e = cudaMemcpyAsync(r, h->diag_result(), sizeof(r), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(diagnostics)");
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(diagnostics)");
+  if (!bgk && h->g.precision == SSLBM_FP32_DEV)
+    r[0] = h->p.s_ref * (double)h->g.nx * (double)h->g.ny - r[0];
+  if (totals)
+    for (int c = 0; c < 5; ++c) totals[c] = r[c];
+  if (peak_I) *peak_I = r[5];
+  for (int c = 0; c < 5; ++c)
+    if (!std::isfinite(r[c])) return fail(SSLBM_ERR_NONFINITE, "total of compartment %d is %g", c, r[c]);
+  return SSLBM_OK;
+}
+
+int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows) {
+  if (!h) return fail(SSLBM_ERR_BAD_ARG, "handle is NULL");
+  if (k < 0 || k > SSLBM_MAX_DEPTH) return fail(SSLBM_ERR_BAD_ARG, "k=%d", k);
+  if (seg_rows < 0) return fail(SSLBM_ERR_BAD_ARG, "seg_rows=%d", seg_rows);
+  const bool blocked = sslbm::blocked_supported(h->g.precision, h->gv);
+  if (!blocked && k > 1)
+    return fail(SSLBM_ERR_UNSUPPORTED, "temporal blocking is provided for FP32 and FP32_DEV");
+  h->depth = k == 0 ? (blocked ? 4 : 1) : k;
+  if (seg_rows > 0 && seg_rows < 4 * h->depth) seg_rows = 4 * h->depth;
+  h->seg_rows = seg_rows;
+  return SSLBM_OK;
+}
+
+int sslbm_get_blocking(const sslbm_handle* h, int* k, int* seg_rows) {
+  if (!h) return fail(SSLBM_ERR_BAD_ARG, "handle is NULL");
+  if (k) *k = h->depth;
+  if (seg_rows) *seg_rows = h->seg_rows;
+  return SSLBM_OK;
+}
+
+}  // extern "C"

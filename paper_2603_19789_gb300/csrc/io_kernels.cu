@@ -1,0 +1,210 @@
+// io_kernels.cu -- conversion between the caller's contiguous ny x nx planes and the
+// solver's pitched storage, and the diagnostics reduction of Sec. II.C 'Mass conservation'
+// (per-compartment totals in double precision, peak infected density).
+#include <float.h>
+
+#include "sslbm_internal.cuh"
+
+namespace sslbm {
+
+namespace {
+
+dim3 row_grid(const GridView& g, int threads) {
+  int64_t gy = g.ny < 65535 ? g.ny : 65535;
+  return dim3((unsigned)((g.nx + threads - 1) / threads), (unsigned)gy);
+}
+
+// plane <- src (contiguous).  dev_S: store s_ref - value.  comp (Kahan) is reset to 0.
+template <typename T, typename U>
+__global__ void plane_write_kernel(const GridView g, const U* __restrict__ src,
+                                   T* __restrict__ plane, T* __restrict__ comp, int dev_S,
+                                   double s_ref) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.nx) return;
+  for (int64_t y = blockIdx.y; y < g.ny; y += gridDim.y) {
+    double v = (double)src[y * g.nx + x];
+    if (dev_S) v = s_ref - v;
+    plane[y * g.pitch + x] = (T)v;
+    if (comp) comp[y * g.pitch + x] = T(0);
+  }
+}
+
+// dst (contiguous) <- plane, evaluated in double: value - compensation, s_ref - sigma.
+template <typename T, typename U>
+__global__ void plane_read_kernel(const GridView g, const T* __restrict__ plane,
+                                  const T* __restrict__ comp, int dev_S, double s_ref,
+                                  U* __restrict__ dst) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.nx) return;
+  for (int64_t y = blockIdx.y; y < g.ny; y += gridDim.y) {
+    double v = (double)plane[y * g.pitch + x];
+    if (comp) v -= (double)comp[y * g.pitch + x];
+    if (dev_S) v = s_ref - v;
+    dst[y * g.nx + x] = (U)v;
+  }
+}
+
+// Block-wide reduction of kDiagSlots values (sums of slots 0..4, max of slot 5) in a fixed
+// order, result valid in thread 0.
+__device__ void block_reduce6(double (&v)[kDiagSlots]) {
+  __shared__ double sh[32][kDiagSlots];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], off);
+    v[5] = fmax(v[5], __shfl_down_sync(0xffffffffu, v[5], off));
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < kDiagSlots; ++j) sh[warp][j] = v[j];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) v[j] = lane < nw ? sh[lane][j] : 0.0;
+    v[5] = lane < nw ? sh[lane][5] : -DBL_MAX;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int j = 0; j < 5; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], off);
+      v[5] = fmax(v[5], __shfl_down_sync(0xffffffffu, v[5], off));
+    }
+  }
+}
+
+// Per-block partial totals of the five compartments and the maximum of I.
+// LAYOUT 0: SSLBM planes (value minus Kahan compensation when comp != nullptr);
+// LAYOUT 1: BGK populations, rho^C = sum_i f_i^C, and D in plane 20.
+template <typename T, int LAYOUT>
+__global__ void __launch_bounds__(256) diag_partial_kernel(const GridView g,
+                                                           const T* __restrict__ st,
+                                                           const T* __restrict__ comp,
+                                                           double* __restrict__ partials) {
+  double v[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0, -DBL_MAX};
+  for (int64_t y = blockIdx.x; y < g.ny; y += gridDim.x) {
+    for (int64_t x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      const int64_t idx = y * g.pitch + x;
+      double r[5];
+      if (LAYOUT == 0) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          r[c] = (double)st[c * g.plane + idx];
+          if (comp) r[c] -= (double)comp[c * g.plane + idx];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          T a = st[(c * 5) * g.plane + idx];
+#pragma unroll
+          for (int i = 1; i < 5; ++i) a = add_rn(a, st[(c * 5 + i) * g.plane + idx]);
+          r[c] = (double)a;
+        }
+        r[4] = (double)st[20 * g.plane + idx];
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) v[c] += r[c];
+      v[5] = fmax(v[5], r[2]);
+    }
+  }
+  block_reduce6(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < kDiagSlots; ++j) partials[blockIdx.x * kDiagSlots + j] = v[j];
+  }
+}
+
+// Sum of the per-block partials in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) diag_final_kernel(const double* __restrict__ partials,
+                                                         int nblocks, double* __restrict__ result) {
+  double v[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0, -DBL_MAX};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) v[j] += partials[b * kDiagSlots + j];
+    v[5] = fmax(v[5], partials[b * kDiagSlots + 5]);
+  }
+  block_reduce6(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < kDiagSlots; ++j) result[j] = v[j];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_plane_write(int precision, const GridView& g, const void* src, int src_dtype,
+                               void* plane, void* comp_plane, int dev_S, double s_ref,
+                               cudaStream_t s) {
+  const dim3 grid = row_grid(g, 128);
+  if (precision == SSLBM_FP64) {
+    if (src_dtype == SSLBM_DT_F64)
+      plane_write_kernel<double, double><<<grid, 128, 0, s>>>(g, (const double*)src, (double*)plane,
+                                                              (double*)comp_plane, dev_S, s_ref);
+    else
+      plane_write_kernel<double, float><<<grid, 128, 0, s>>>(g, (const float*)src, (double*)plane,
+                                                             (double*)comp_plane, dev_S, s_ref);
+  } else {
+    if (src_dtype == SSLBM_DT_F64)
+      plane_write_kernel<float, double><<<grid, 128, 0, s>>>(g, (const double*)src, (float*)plane,
+                                                             (float*)comp_plane, dev_S, s_ref);
+    else
+      plane_write_kernel<float, float><<<grid, 128, 0, s>>>(g, (const float*)src, (float*)plane,
+                                                            (float*)comp_plane, dev_S, s_ref);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plane_read(int precision, const GridView& g, const void* plane,
+                              const void* comp_plane, int dev_S, double s_ref, void* dst,
+                              int dst_dtype, cudaStream_t s) {
+  const dim3 grid = row_grid(g, 128);
+  if (precision == SSLBM_FP64) {
+    if (dst_dtype == SSLBM_DT_F64)
+      plane_read_kernel<double, double><<<grid, 128, 0, s>>>(g, (const double*)plane,
+                                                             (const double*)comp_plane, dev_S,
+                                                             s_ref, (double*)dst);
+    else
+      plane_read_kernel<double, float><<<grid, 128, 0, s>>>(g, (const double*)plane,
+                                                            (const double*)comp_plane, dev_S,
+                                                            s_ref, (float*)dst);
+  } else {
+    if (dst_dtype == SSLBM_DT_F64)
+      plane_read_kernel<float, double><<<grid, 128, 0, s>>>(g, (const float*)plane,
+                                                            (const float*)comp_plane, dev_S, s_ref,
+                                                            (double*)dst);
+    else
+      plane_read_kernel<float, float><<<grid, 128, 0, s>>>(g, (const float*)plane,
+                                                           (const float*)comp_plane, dev_S, s_ref,
+                                                           (float*)dst);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(int precision, int layout, const GridView& g, const void* planes,
+                               const void* comp_planes, double* partials, double* result,
+                               cudaStream_t s) {
+  int64_t blocks = g.ny < kDiagBlocks ? g.ny : kDiagBlocks;
+  if (blocks < 1) blocks = 1;
+  if (precision == SSLBM_FP64) {
+    if (layout == 0)
+      diag_partial_kernel<double, 0><<<(unsigned)blocks, 256, 0, s>>>(
+          g, (const double*)planes, (const double*)comp_planes, partials);
+    else
+      diag_partial_kernel<double, 1><<<(unsigned)blocks, 256, 0, s>>>(g, (const double*)planes,
+                                                                      nullptr, partials);
+  } else {
+    if (layout == 0)
+      diag_partial_kernel<float, 0><<<(unsigned)blocks, 256, 0, s>>>(
+          g, (const float*)planes, (const float*)comp_planes, partials);
+    else
+      diag_partial_kernel<float, 1><<<(unsigned)blocks, 256, 0, s>>>(g, (const float*)planes,
+                                                                     nullptr, partials);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, 256, 0, s>>>(partials, (int)blocks, result);
+  return cudaGetLastError();
+}
+
+}  // namespace sslbm

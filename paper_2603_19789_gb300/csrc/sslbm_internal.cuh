@@ -1,0 +1,181 @@
+// sslbm_internal.cuh -- internal definitions shared by the libsslbm translation units.
+//
+// Field layout in device memory: each plane (one compartment, or one BGK population
+// of one compartment) holds ny rows of `pitch` elements, x fastest; pitch is nx
+// rounded up to 32 elements so every row starts on a 128-byte boundary (FP32) and
+// vector loads never straddle rows.  Cells with x >= nx are padding, kept at zero
+// and never read as neighbours.  Planes are `plane` elements apart (pitch*ny rounded
+// up to 64 elements, i.e. 256-byte aligned for both precisions).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sslbm.h"
+
+namespace sslbm {
+
+enum Mode { MODE_PLAIN = 0, MODE_DEV = 1, MODE_KAHAN = 2 };
+
+struct GridView {
+  int64_t nx, ny, pitch, plane;
+  int bc;  // 0 periodic, 1 no-flux
+};
+
+// Per-step constants of the SSLBM / BGK updates in lattice form.
+//   dl[c]  lattice diffusivity d dt/dx^2 = (tau - 1/2)/3 (Eq. diffusivity)
+//   bdt    beta dt,  adt alpha dt,  gdt gamma dt,
+//   rdt    (1 - phi) gamma dt (inflow of R),  ddt phi gamma dt (inflow of D)
+//   s_ref  reference value of S for the deviation storage
+//   itau   1/tau (BGK collision)
+template <typename T>
+struct Coeffs {
+  T dl[4];
+  T itau[4];
+  T bdt, adt, gdt, rdt, ddt;
+  T s_ref;
+};
+
+// Map a row/column index that left [0, n) by at most one link (periodic wrap or the
+// cell-centred mirror, whose ghost equals the boundary cell).
+__device__ __forceinline__ int64_t link_index(int64_t i, int64_t n, int bc) {
+  if (i < 0) return bc == 0 ? i + n : 0;
+  if (i >= n) return bc == 0 ? i - n : n - 1;
+  return i;
+}
+
+// Map any index onto [0, n) for ghost layers of arbitrary width: periodic wrap, or the
+// even extension about the faces (period 2n), which is what repeated cell-centred
+// mirroring produces.  Evolving such a ghost layer with the same stencil keeps it the
+// mirror image of the interior, so interior results equal those of per-step mirroring.
+__device__ __forceinline__ int64_t ghost_index(int64_t i, int64_t n, int bc) {
+  if (i >= 0 && i < n) return i;
+  if (bc == 0) {
+    int64_t r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  int64_t p = 2 * n;
+  int64_t r = i % p;
+  if (r < 0) r += p;
+  return r < n ? r : p - 1 - r;
+}
+
+// Explicitly rounded operations: the per-cell arithmetic is spelled out with fma and
+// _rn intrinsics so the compiler has no freedom to contract or reorder it, and every
+// kernel that uses these helpers produces the same bits for the same cell.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+// FP32 uses the fast hardware-approximate quotient (max 2 ulp); FP64 the IEEE quotient.
+__device__ __forceinline__ float div_any(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_any(double a, double b) { return __ddiv_rn(a, b); }
+
+// Force of infection times dt, beta S I / N_c dt (Eq. sources), taken as 0 when the
+// contact-eligible population N_c = S + E + I + R is zero.
+template <typename T>
+__device__ __forceinline__ T force_dt(const Coeffs<T>& k, T S, T E, T I, T R) {
+  const T Nc = add_rn(add_rn(S, E), add_rn(I, R));
+  const T num = mul_rn(mul_rn(k.bdt, S), I);
+  return Nc != T(0) ? div_any(num, Nc) : T(0);
+}
+
+// Neighbour sum minus four times the centre.  On D2Q5 rho_f = rho_b = rho_c/3 + (sum of
+// the four neighbours)/6, so Eq. (sslbm_final_clean) equals
+//   rho_c + (2 tau - 1)/6 * (l + r + u + d - 4 rho_c) + Psi dt = rho_c + d_lattice * lap.
+template <typename T>
+__device__ __forceinline__ T lap5(T c, T l, T r, T u, T d) {
+  return fma_rn(T(-4), c, add_rn(add_rn(l, r), add_rn(u, d)));
+}
+
+// Increments of S, E, I, R, D of one cell over one step (Eq. sslbm_final_clean in
+// reduced form with Eq. sources; Eq. rhoD): d_lattice * lap + Psi dt.
+template <typename T>
+__device__ __forceinline__ void seird_cell(const Coeffs<T>& k, T S, T E, T I, T R, T D, T lS, T lE,
+                                           T lI, T lR, T& nS, T& nE, T& nI, T& nR, T& nD) {
+  const T F = force_dt(k, S, E, I, R);
+  nS = sub_rn(fma_rn(k.dl[0], lS, S), F);
+  nE = add_rn(fma_rn(k.dl[1], lE, E), fma_rn(-k.adt, E, F));
+  nI = add_rn(fma_rn(k.dl[2], lI, I), fma_rn(k.adt, E, -mul_rn(k.gdt, I)));
+  nR = fma_rn(k.rdt, I, fma_rn(k.dl[3], lR, R));
+  nD = fma_rn(k.ddt, I, D);
+}
+
+// Deviation storage: plane 0 holds sigma = s_ref - S.  The laplacian of sigma is minus
+// that of S (the constant s_ref is annihilated exactly), so
+// sigma' = sigma + d lap(sigma) + F dt.
+template <typename T>
+__device__ __forceinline__ void seird_cell_dev(const Coeffs<T>& k, T sig, T E, T I, T R, T D,
+                                               T lsig, T lE, T lI, T lR, T& nsig, T& nE, T& nI,
+                                               T& nR, T& nD) {
+  const T S = sub_rn(k.s_ref, sig);
+  const T F = force_dt(k, S, E, I, R);
+  nsig = add_rn(fma_rn(k.dl[0], lsig, sig), F);
+  nE = add_rn(fma_rn(k.dl[1], lE, E), fma_rn(-k.adt, E, F));
+  nI = add_rn(fma_rn(k.dl[2], lI, I), fma_rn(k.adt, E, -mul_rn(k.gdt, I)));
+  nR = fma_rn(k.rdt, I, fma_rn(k.dl[3], lR, R));
+  nD = fma_rn(k.ddt, I, D);
+}
+
+// Compensated (Kahan) accumulation of an increment: value v, running compensation c
+// (the part of earlier increments lost to rounding, with the sign Kahan's algorithm
+// gives it: the represented value is v - c).
+__device__ __forceinline__ void kahan_add(float& v, float& c, float inc) {
+  const float y = __fsub_rn(inc, c);
+  const float t = __fadd_rn(v, y);
+  c = __fsub_rn(__fsub_rn(t, v), y);
+  v = t;
+}
+
+// Increments of S, E, I, R, D for the Kahan variant (same expressions as seird_cell).
+__device__ __forceinline__ void seird_increments(const Coeffs<float>& k, float S, float E, float I,
+                                                 float R, float lS, float lE, float lI, float lR,
+                                                 float inc[5]) {
+  const float F = force_dt(k, S, E, I, R);
+  inc[0] = fma_rn(k.dl[0], lS, -F);
+  inc[1] = add_rn(mul_rn(k.dl[1], lE), fma_rn(-k.adt, E, F));
+  inc[2] = add_rn(mul_rn(k.dl[2], lI), fma_rn(k.adt, E, -mul_rn(k.gdt, I)));
+  inc[3] = fma_rn(k.rdt, I, mul_rn(k.dl[3], lR));
+  inc[4] = mul_rn(k.ddt, I);
+}
+
+// ---- launchers (defined in the kernel translation units) --------------------------
+// SSLBM: one step per launch (every precision) and K fused steps per launch (FP32 and
+// FP32 deviation-S).  seg_rows > 0 is the blocked kernel's row-segment length.
+cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coeffs, const void* in,
+                               void* out, cudaStream_t s);
+cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* coeffs,
+                                 const void* in, void* out, int depth, int seg_rows,
+                                 cudaStream_t s);
+bool blocked_supported(int precision, const GridView& g);
+// Segment length that makes one blocked launch a single wave of resident warps.
+int blocked_default_seg_rows(int precision, const GridView& g, int depth);
+// BGK: one collide-and-stream step; equilibrium initialisation and density of one
+// compartment from / to a contiguous ny x nx plane of type rho_dtype.
+cudaError_t launch_bgk_step(int precision, const GridView& g, const void* coeffs, const void* f_in,
+                            void* f_out, cudaStream_t s);
+cudaError_t launch_bgk_init(int precision, const GridView& g, int comp, const void* rho,
+                            int rho_dtype, void* f, cudaStream_t s);
+cudaError_t launch_bgk_density(int precision, const GridView& g, int comp, const void* f, void* rho,
+                               int rho_dtype, cudaStream_t s);
+// plane <-> contiguous user layout (dev_S: deviation storage of S; comp_plane: Kahan
+// compensation, reset on write and subtracted on read)
+cudaError_t launch_plane_write(int precision, const GridView& g, const void* src, int src_dtype,
+                               void* plane, void* comp_plane, int dev_S, double s_ref,
+                               cudaStream_t s);
+cudaError_t launch_plane_read(int precision, const GridView& g, const void* plane,
+                              const void* comp_plane, int dev_S, double s_ref, void* dst,
+                              int dst_dtype, cudaStream_t s);
+// diagnostics: per-block partial sums of the 5 compartments and max of I into `partials`
+// (kDiagBlocks x kDiagSlots doubles), then their fixed-order total into result[6].
+// layout 0: SSLBM planes; layout 1: BGK populations.
+constexpr int kDiagBlocks = 1024;
+constexpr int kDiagSlots = 6;
+cudaError_t launch_diagnostics(int precision, int layout, const GridView& g, const void* planes,
+                               const void* comp_planes, double* partials, double* result,
+                               cudaStream_t s);
+
+}  // namespace sslbm

@@ -1,0 +1,341 @@
+// sslbm_kernels.cu -- SSLBM time-step kernels (Sec. II.C, Eq. sslbm_final_clean with the
+// sources of Eq. sources and the deceased update of Eq. rhoD).
+//
+// Two kernels advance the same update:
+//   step1_kernel    one step per launch, every precision (FP64, FP32, FP32 deviation-S,
+//                   FP32 Kahan).  Each thread updates V consecutive cells of a row with
+//                   16-byte vector loads (float4 / double2) of the centre, upper and lower
+//                   rows and two scalar edge loads; neighbouring rows come from L1/L2.
+//   blocked_kernel  K steps per launch (temporal blocking) for the FP32 variants.  One
+//                   warp owns a 128-column strip (4 columns per lane, float4 loads) and
+//                   streams down a segment of rows.  For every level s = 1..K it keeps the
+//                   two previous rows of level s-1 in registers; when row q of level 0
+//                   arrives, level s computes row q - s.  x neighbours come from warp
+//                   shuffles; each strip carries a K-column halo on both sides (one or two
+//                   lanes), so warps never synchronise with each other.  Rows and columns
+//                   outside the domain are loaded as ghost images (periodic wrap or the
+//                   even mirror extension), which the uniform stencil keeps consistent, so
+//                   no boundary logic is needed inside the level loop.  DRAM traffic is one
+//                   read and one write of the five planes per K steps.
+// Both use the same per-cell expressions (sslbm_internal.cuh), so a blocked launch gives
+// the same bits as K one-step launches.
+#include "sslbm_internal.cuh"
+
+namespace sslbm {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T, int V>
+struct Vec;
+template <>
+struct Vec<float, 4> {
+  static __device__ __forceinline__ void load(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  static __device__ __forceinline__ void store(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct Vec<double, 2> {
+  static __device__ __forceinline__ void load(const double* p, double (&v)[2]) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+  static __device__ __forceinline__ void store(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
+template <typename T, int V, int MODE>
+__global__ void __launch_bounds__(256) step1_kernel(const GridView g, const Coeffs<T> k,
+                                                    const T* __restrict__ in, T* __restrict__ out) {
+  const int64_t nvec = (g.nx + V - 1) / V;
+  const int64_t vx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vx >= nvec) return;
+  const int64_t x0 = vx * V;
+  const int nvalid = (int)((g.nx - x0) < V ? (g.nx - x0) : V);
+  const int64_t xl = link_index(x0 - 1, g.nx, g.bc);
+  const int64_t xr = link_index(x0 + nvalid, g.nx, g.bc);
+  for (int64_t y = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; y < g.ny;
+       y += (int64_t)gridDim.y * blockDim.y) {
+    const int64_t rc = y * g.pitch;
+    const int64_t ru = link_index(y - 1, g.ny, g.bc) * g.pitch;
+    const int64_t rd = link_index(y + 1, g.ny, g.bc) * g.pitch;
+    T c[4][V], lap[4][V];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const T* P = in + f * g.plane;
+      T u[V], d[V];
+      Vec<T, V>::load(P + rc + x0, c[f]);
+      Vec<T, V>::load(P + ru + x0, u);
+      Vec<T, V>::load(P + rd + x0, d);
+      const T L = P[rc + xl];
+      const T R = P[rc + xr];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const T l = (j == 0) ? L : c[f][j > 0 ? j - 1 : 0];
+        T r = R;
+        if (j + 1 < V) {
+          if (j + 1 < nvalid) r = c[f][j + 1 < V ? j + 1 : j];
+        }
+        lap[f][j] = lap5(c[f][j], l, r, u[j], d[j]);
+      }
+    }
+    T D[V];
+    Vec<T, V>::load(in + 4 * g.plane + rc + x0, D);
+    T n[5][V];
+    if constexpr (MODE == MODE_KAHAN) {
+      T cmp[5][V];
+#pragma unroll
+      for (int f = 0; f < 5; ++f) Vec<T, V>::load(in + (5 + f) * g.plane + rc + x0, cmp[f]);
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        float inc[5];
+        seird_increments(k, c[0][j], c[1][j], c[2][j], c[3][j], lap[0][j], lap[1][j], lap[2][j],
+                         lap[3][j], inc);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          n[f][j] = c[f][j];
+          kahan_add(n[f][j], cmp[f][j], inc[f]);
+        }
+        n[4][j] = D[j];
+        kahan_add(n[4][j], cmp[4][j], inc[4]);
+      }
+      if (nvalid == V) {
+#pragma unroll
+        for (int f = 0; f < 5; ++f) Vec<T, V>::store(out + (5 + f) * g.plane + rc + x0, cmp[f]);
+      } else {
+#pragma unroll
+        for (int f = 0; f < 5; ++f)
+#pragma unroll
+          for (int j = 0; j < V; ++j)
+            if (j < nvalid) out[(5 + f) * g.plane + rc + x0 + j] = cmp[f][j];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        if constexpr (MODE == MODE_DEV) {
+          seird_cell_dev(k, c[0][j], c[1][j], c[2][j], c[3][j], D[j], lap[0][j], lap[1][j],
+                         lap[2][j], lap[3][j], n[0][j], n[1][j], n[2][j], n[3][j], n[4][j]);
+        } else {
+          seird_cell(k, c[0][j], c[1][j], c[2][j], c[3][j], D[j], lap[0][j], lap[1][j], lap[2][j],
+                     lap[3][j], n[0][j], n[1][j], n[2][j], n[3][j], n[4][j]);
+        }
+      }
+    }
+    if (nvalid == V) {
+#pragma unroll
+      for (int f = 0; f < 5; ++f) Vec<T, V>::store(out + f * g.plane + rc + x0, n[f]);
+    } else {
+#pragma unroll
+      for (int f = 0; f < 5; ++f)
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+          if (j < nvalid) out[f * g.plane + rc + x0 + j] = n[f][j];
+    }
+  }
+}
+
+template <int MODE, int K>
+__global__ void __launch_bounds__(128) blocked_kernel(const GridView g, const Coeffs<float> k,
+                                                      const float* __restrict__ in,
+                                                      float* __restrict__ out, const int seg_rows,
+                                                      const int nstrips, const int64_t nwarps) {
+  constexpr int HL = (K + 3) / 4;     // halo lanes on each side of the strip
+  constexpr int WV = 128 - 8 * HL;    // columns written per strip
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (wid >= nwarps) return;  // whole warp leaves together
+  const int strip = (int)(wid % nstrips);
+  const int64_t y0 = (wid / nstrips) * (int64_t)seg_rows;
+  const int64_t y1 = (y0 + seg_rows < g.ny) ? y0 + seg_rows : g.ny;
+  const int64_t xs = (int64_t)strip * WV - 4 * HL + 4 * lane;
+  const bool vec_ok = xs >= 0 && xs + 3 < g.nx;
+  int64_t xm[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) xm[j] = ghost_index(xs + j, g.nx, g.bc);
+  const bool writer = lane >= HL && lane < 32 - HL && xs < g.nx;
+
+  float P[K][4][4], C[K][4][4], CD[K][4];
+#pragma unroll
+  for (int s = 0; s < K; ++s)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      CD[s][j] = 0.f;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) P[s][f][j] = C[s][f][j] = 0.f;
+    }
+
+  for (int64_t q = y0 - K; q < y1 + K; ++q) {
+    const int64_t row = ghost_index(q, g.ny, g.bc) * g.pitch;
+    float N[5][4];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      const float* p = in + f * g.plane + row;
+      if (vec_ok) {
+        Vec<float, 4>::load(p + xs, N[f]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) N[f][j] = p[xm[j]];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      // level s holds rows q-s-2 (P), q-s-1 (C); N is its row q-s.  Compute level s+1 at
+      // row q-s-1.
+      float lp[4][4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const float L = __shfl_up_sync(kFull, C[s][f][3], 1);
+        const float R = __shfl_down_sync(kFull, C[s][f][0], 1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float l = (j == 0) ? L : C[s][f][j > 0 ? j - 1 : 0];
+          const float r = (j == 3) ? R : C[s][f][j < 3 ? j + 1 : 3];
+          lp[f][j] = lap5(C[s][f][j], l, r, P[s][f][j], N[f][j]);
+        }
+      }
+      float M[5][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if constexpr (MODE == MODE_DEV) {
+          seird_cell_dev(k, C[s][0][j], C[s][1][j], C[s][2][j], C[s][3][j], CD[s][j], lp[0][j],
+                         lp[1][j], lp[2][j], lp[3][j], M[0][j], M[1][j], M[2][j], M[3][j], M[4][j]);
+        } else {
+          seird_cell(k, C[s][0][j], C[s][1][j], C[s][2][j], C[s][3][j], CD[s][j], lp[0][j],
+                     lp[1][j], lp[2][j], lp[3][j], M[0][j], M[1][j], M[2][j], M[3][j], M[4][j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          P[s][f][j] = C[s][f][j];
+          C[s][f][j] = N[f][j];
+        }
+        CD[s][j] = N[4][j];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) N[f][j] = M[f][j];
+      }
+    }
+    const int64_t r = q - K;
+    if (writer && r >= y0) {
+      float* o = out + r * g.pitch + xs;
+      if (xs + 3 < g.nx) {
+#pragma unroll
+        for (int f = 0; f < 5; ++f) Vec<float, 4>::store(o + f * g.plane, N[f]);
+      } else {
+#pragma unroll
+        for (int f = 0; f < 5; ++f)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (xs + j < g.nx) o[f * g.plane + j] = N[f][j];
+      }
+    }
+  }
+}
+
+template <typename T, int V, int MODE>
+cudaError_t launch_step1_t(const GridView& g, const void* coeffs, const void* in, void* out,
+                           cudaStream_t s) {
+  const int64_t nvec = (g.nx + V - 1) / V;
+  dim3 block(32, 8);
+  int64_t gy = (g.ny + 7) / 8;
+  if (gy > 65535) gy = 65535;
+  dim3 grid((unsigned)((nvec + 31) / 32), (unsigned)gy);
+  step1_kernel<T, V, MODE><<<grid, block, 0, s>>>(g, *static_cast<const Coeffs<T>*>(coeffs),
+                                                  static_cast<const T*>(in), static_cast<T*>(out));
+  return cudaGetLastError();
+}
+
+template <int MODE, int K>
+cudaError_t launch_blocked_t(const GridView& g, const void* coeffs, const void* in, void* out,
+                             int seg_rows, cudaStream_t s) {
+  constexpr int HL = (K + 3) / 4;
+  constexpr int WV = 128 - 8 * HL;
+  if (seg_rows <= 0) return cudaErrorInvalidValue;
+  const int64_t nstrips = (g.nx + WV - 1) / WV;
+  const int64_t nseg = (g.ny + seg_rows - 1) / seg_rows;
+  const int64_t nwarps = nstrips * nseg;
+  const int64_t blocks = (nwarps + 3) / 4;
+  if (blocks > 0x7fffffffLL || nstrips > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  blocked_kernel<MODE, K><<<(unsigned)blocks, 128, 0, s>>>(
+      g, *static_cast<const Coeffs<float>*>(coeffs), static_cast<const float*>(in),
+      static_cast<float*>(out), seg_rows, (int)nstrips, nwarps);
+  return cudaGetLastError();
+}
+
+template <int MODE, int K>
+int default_seg_rows_t(const GridView& g) {
+  constexpr int HL = (K + 3) / 4;
+  constexpr int WV = 128 - 8 * HL;
+  const int64_t nstrips = (g.nx + WV - 1) / WV;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blocked_kernel<MODE, K>, 128, 0);
+  const int64_t resident = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) * 4;
+  int64_t nseg = resident / nstrips;
+  if (nseg < 1) nseg = 1;
+  int64_t rows = (g.ny + nseg - 1) / nseg;
+  if (rows < 4 * K) rows = 4 * K;
+  if (rows > (1 << 30)) rows = 1 << 30;
+  return (int)rows;
+}
+
+template <int MODE>
+cudaError_t launch_blocked_mode(const GridView& g, const void* coeffs, const void* in, void* out,
+                                int depth, int seg_rows, cudaStream_t s) {
+  switch (depth) {
+    case 1: return launch_blocked_t<MODE, 1>(g, coeffs, in, out, seg_rows, s);
+    case 2: return launch_blocked_t<MODE, 2>(g, coeffs, in, out, seg_rows, s);
+    case 3: return launch_blocked_t<MODE, 3>(g, coeffs, in, out, seg_rows, s);
+    case 4: return launch_blocked_t<MODE, 4>(g, coeffs, in, out, seg_rows, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+int blocked_default_seg_rows(int precision, const GridView& g, int depth) {
+  if (precision != SSLBM_FP32 && precision != SSLBM_FP32_DEV) return 0;
+  const bool dev = precision == SSLBM_FP32_DEV;
+  switch (depth) {
+    case 1: return dev ? default_seg_rows_t<MODE_DEV, 1>(g) : default_seg_rows_t<MODE_PLAIN, 1>(g);
+    case 2: return dev ? default_seg_rows_t<MODE_DEV, 2>(g) : default_seg_rows_t<MODE_PLAIN, 2>(g);
+    case 3: return dev ? default_seg_rows_t<MODE_DEV, 3>(g) : default_seg_rows_t<MODE_PLAIN, 3>(g);
+    case 4: return dev ? default_seg_rows_t<MODE_DEV, 4>(g) : default_seg_rows_t<MODE_PLAIN, 4>(g);
+    default: return 0;
+  }
+}
+
+bool blocked_supported(int precision, const GridView&) {
+  return precision == SSLBM_FP32 || precision == SSLBM_FP32_DEV;
+}
+
+cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coeffs, const void* in,
+                               void* out, cudaStream_t s) {
+  switch (precision) {
+    case SSLBM_FP64: return launch_step1_t<double, 2, MODE_PLAIN>(g, coeffs, in, out, s);
+    case SSLBM_FP32: return launch_step1_t<float, 4, MODE_PLAIN>(g, coeffs, in, out, s);
+    case SSLBM_FP32_DEV: return launch_step1_t<float, 4, MODE_DEV>(g, coeffs, in, out, s);
+    case SSLBM_FP32_KAHAN: return launch_step1_t<float, 4, MODE_KAHAN>(g, coeffs, in, out, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* coeffs,
+                                 const void* in, void* out, int depth, int seg_rows,
+                                 cudaStream_t s) {
+  if (precision == SSLBM_FP32)
+    return launch_blocked_mode<MODE_PLAIN>(g, coeffs, in, out, depth, seg_rows, s);
+  if (precision == SSLBM_FP32_DEV)
+    return launch_blocked_mode<MODE_DEV>(g, coeffs, in, out, depth, seg_rows, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace sslbm

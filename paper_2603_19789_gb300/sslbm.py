@@ -1,0 +1,279 @@
+"""ctypes binding of libsslbm.so (include/sslbm.h), with the C entry points' names.
+
+Argument marshalling only: every computation runs in the library's CUDA kernels.
+PyTorch supplies device memory (the workspace) and streams.  If the library has not
+been built, the first call raises; there is no CPU fallback.
+
+Functions mirror the C ABI one to one (``sslbm_create``, ``sslbm_step``,
+``bgk_step``, ``sslbm_read`` ...) and raise ``SslbmError`` on a negative status.
+``Solver`` bundles a handle with its torch-allocated workspace for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsslbm.so")
+
+# constants of include/sslbm.h
+SSLBM_OK = 0
+BC_PERIODIC, BC_NOFLUX = 0, 1
+FP64, FP32, FP32_DEV, FP32_KAHAN = 0, 1, 2, 3
+SCHEME_SSLBM, SCHEME_BGK = 0, 1
+S, E, I, R, D, NCOMP = 0, 1, 2, 3, 4, 5
+ALL = -1
+DT_F64, DT_F32 = 0, 1
+WANT_SSLBM, WANT_BGK = 1, 2
+MAX_DEPTH = 4
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP32_KAHAN}
+
+# every symbol include/sslbm.h declares
+EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspace_bytes",
+           "sslbm_create", "sslbm_set_stream", "sslbm_destroy", "sslbm_write", "sslbm_read",
+           "sslbm_step", "bgk_step", "sslbm_steps_done", "sslbm_diagnostics",
+           "sslbm_set_blocking", "sslbm_get_blocking")
+
+
+class SslbmError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {sslbm_strerror(status)} ({status}): {detail}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("dx", ctypes.c_double),
+                ("dt", ctypes.c_double), ("bc", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("schemes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("alpha", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("phi", ctypes.c_double), ("d", ctypes.c_double * 5), ("tau", ctypes.c_double * 4),
+                ("s_ref", ctypes.c_double), ("use_tau", ctypes.c_int32), ("strict", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+
+
+def load(path: str = LIB_PATH):
+    """Load libsslbm.so (raises if it is missing: build it with paper_2603_19789_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -m paper_2603_19789_gb300.build` (no CPU fallback exists)")
+        lib = ctypes.CDLL(path)
+        i32, i64 = ctypes.c_int, ctypes.c_int64
+        sig = {
+            "sslbm_strerror": (ctypes.c_char_p, [i32]),
+            "sslbm_last_error": (ctypes.c_char_p, []),
+            "sslbm_version": (i32, []),
+            "sslbm_workspace_bytes": (i32, [ctypes.POINTER(Grid), ctypes.POINTER(ctypes.c_size_t)]),
+            "sslbm_create": (i32, [ctypes.POINTER(Grid), ctypes.POINTER(Params), _vp, ctypes.c_size_t,
+                                   _vp, ctypes.POINTER(_vp)]),
+            "sslbm_set_stream": (i32, [_vp, _vp]),
+            "sslbm_destroy": (None, [_vp]),
+            "sslbm_write": (i32, [_vp, i32, i32, _vp, i32, i32]),
+            "sslbm_read": (i32, [_vp, i32, i32, _vp, i32, i32]),
+            "sslbm_step": (i32, [_vp, i64]),
+            "bgk_step": (i32, [_vp, i64]),
+            "sslbm_steps_done": (i64, [_vp, i32]),
+            "sslbm_diagnostics": (i32, [_vp, i32, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+            "sslbm_set_blocking": (i32, [_vp, i32, i32]),
+            "sslbm_get_blocking": (i32, [_vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != SSLBM_OK:
+        raise SslbmError(status, where, sslbm_last_error())
+
+
+def sslbm_strerror(status: int) -> str:
+    return load().sslbm_strerror(int(status)).decode()
+
+
+def sslbm_last_error() -> str:
+    return load().sslbm_last_error().decode()
+
+
+def sslbm_version() -> int:
+    return int(load().sslbm_version())
+
+
+def make_grid(nx, ny, dx=1.0, dt=1.0, bc=BC_PERIODIC, precision=FP64, schemes=WANT_SSLBM) -> Grid:
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    return Grid(int(nx), int(ny), float(dx), float(dt), int(bc), int(precision), int(schemes), 0)
+
+
+def make_params(beta, alpha, gamma, phi, d=None, tau=None, s_ref=1.0, strict=False) -> Params:
+    p = Params()
+    p.beta, p.alpha, p.gamma, p.phi = float(beta), float(alpha), float(gamma), float(phi)
+    if tau is not None:
+        p.use_tau = 1
+        for c in range(4):
+            p.tau[c] = float(tau[c])
+    else:
+        dd = list(d) + [0.0] * (5 - len(d))
+        for c in range(5):
+            p.d[c] = float(dd[c])
+    p.s_ref = float(s_ref)
+    p.strict = 1 if strict else 0
+    return p
+
+
+def sslbm_workspace_bytes(grid: Grid) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().sslbm_workspace_bytes(ctypes.byref(grid), ctypes.byref(n)), "sslbm_workspace_bytes")
+    return int(n.value)
+
+
+def sslbm_create(grid: Grid, params: Params, ws_ptr: int, ws_bytes: int, stream: int = 0):
+    h = _vp()
+    _check(load().sslbm_create(ctypes.byref(grid), ctypes.byref(params), _vp(ws_ptr), int(ws_bytes),
+                               _vp(stream), ctypes.byref(h)), "sslbm_create")
+    return h
+
+
+def sslbm_set_stream(h, stream: int):
+    _check(load().sslbm_set_stream(h, _vp(stream)), "sslbm_set_stream")
+
+
+def sslbm_destroy(h):
+    if h:
+        load().sslbm_destroy(h)
+
+
+def _buffer(a):
+    """(pointer, on_device, dtype code, nbytes) of a numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        code = {np.dtype(np.float64): DT_F64, np.dtype(np.float32): DT_F32}.get(a.dtype)
+        if code is None:
+            raise TypeError(f"unsupported dtype {a.dtype}")
+        return a.ctypes.data, 0, code, a.nbytes
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise TypeError(type(a))
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    code = {torch.float64: DT_F64, torch.float32: DT_F32}.get(a.dtype)
+    if code is None:
+        raise TypeError(f"unsupported dtype {a.dtype}")
+    return a.data_ptr(), 1 if a.is_cuda else 0, code, a.numel() * a.element_size()
+
+
+def sslbm_write(h, scheme: int, comp: int, src):
+    ptr, dev, code, _ = _buffer(src)
+    _check(load().sslbm_write(h, int(scheme), int(comp), _vp(ptr), code, dev), "sslbm_write")
+
+
+def sslbm_read(h, scheme: int, comp: int, dst):
+    ptr, dev, code, _ = _buffer(dst)
+    _check(load().sslbm_read(h, int(scheme), int(comp), _vp(ptr), code, dev), "sslbm_read")
+    return dst
+
+
+def sslbm_step(h, n: int):
+    _check(load().sslbm_step(h, int(n)), "sslbm_step")
+
+
+def bgk_step(h, n: int):
+    _check(load().bgk_step(h, int(n)), "bgk_step")
+
+
+def sslbm_steps_done(h, scheme: int = SCHEME_SSLBM) -> int:
+    return int(load().sslbm_steps_done(h, int(scheme)))
+
+
+def sslbm_diagnostics(h, scheme: int = SCHEME_SSLBM):
+    tot = (ctypes.c_double * 5)()
+    pk = ctypes.c_double(0.0)
+    _check(load().sslbm_diagnostics(h, int(scheme), tot, ctypes.byref(pk)), "sslbm_diagnostics")
+    return np.array(tot[:]), float(pk.value)
+
+
+def sslbm_set_blocking(h, k: int, seg_rows: int = 0):
+    _check(load().sslbm_set_blocking(h, int(k), int(seg_rows)), "sslbm_set_blocking")
+
+
+def sslbm_get_blocking(h):
+    k, s = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().sslbm_get_blocking(h, ctypes.byref(k), ctypes.byref(s)), "sslbm_get_blocking")
+    return int(k.value), int(s.value)
+
+
+class Solver:
+    """A handle plus its torch-allocated device workspace.
+
+    rates: (beta, alpha, gamma, phi) in the paper's notation; d: diffusivities of
+    S, E, I, R (and D = 0) or tau: relaxation times of S, E, I, R.
+    """
+
+    def __init__(self, nx, ny, rates, d=None, tau=None, dx=1.0, dt=1.0, bc=BC_PERIODIC,
+                 precision=FP64, schemes=WANT_SSLBM, s_ref=1.0, strict=False, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device if device is not None else "cuda")
+        self.grid = make_grid(nx, ny, dx, dt, bc, precision, schemes)
+        self.params = make_params(*rates, d=d, tau=tau, s_ref=s_ref, strict=strict)
+        self.nx, self.ny = int(nx), int(ny)
+        nbytes = sslbm_workspace_bytes(self.grid)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.h = sslbm_create(self.grid, self.params, self.ws.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.stream.synchronize()
+            sslbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def write(self, state, scheme=SCHEME_SSLBM, comp=ALL):
+        sslbm_write(self.h, scheme, comp, state)
+
+    def read(self, scheme=SCHEME_SSLBM, comp=ALL, dtype=np.float64):
+        shape = (5, self.ny, self.nx) if comp == ALL else (self.ny, self.nx)
+        out = np.empty(shape, dtype=dtype)
+        return sslbm_read(self.h, scheme, comp, out)
+
+    def step(self, n):
+        sslbm_step(self.h, n)
+
+    def bgk_step(self, n):
+        bgk_step(self.h, n)
+
+    def diagnostics(self, scheme=SCHEME_SSLBM):
+        return sslbm_diagnostics(self.h, scheme)
+
+    def set_blocking(self, k, seg_rows=0):
+        sslbm_set_blocking(self.h, k, seg_rows)
+
+    def get_blocking(self):
+        return sslbm_get_blocking(self.h)
+
+    def steps_done(self, scheme=SCHEME_SSLBM):
+        return sslbm_steps_done(self.h, scheme)
