@@ -4,10 +4,11 @@ Tolerances, stated here and derived in the design doc:
   FP64   relative max-norm per compartment <= 1e-12 (the kernels use the reduced form of
          Eq. sslbm_final_clean, which differs from the oracle's literal form only in the
          rounding of each step, ~1e-16 relative).
-  FP32   relative L2 and relative max-norm per compartment against the FP64 oracle
-         <= 2e-4 over the 2000-step centre-bump run (n u with n = 2000 steps and
-         u = 6e-8 the unit roundoff bounds the accumulated rounding of a contractive
-         update), <= 1e-5 for runs of <= 20 steps.
+  FP32   L2 (root mean square) and max-norm error per compartment against the FP64
+         oracle, divided by the compartment's peak value over the run, <= 2e-4 over the
+         2000-step centre-bump run (n u with n = 2000 steps and u = 6e-8 the unit
+         roundoff bounds the accumulated rounding of a contractive update); relative
+         max-norm <= 1e-5 for runs of <= 20 steps.
 Blocked launches (K fused steps) must give the same bits as K one-step launches.
 """
 import numpy as np
@@ -116,15 +117,28 @@ def test_zero_steps_is_identity_and_roundtrip_exact():
 
 @pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_KAHAN])
 def test_centre_bump_fp32_variants_within_tolerance(precision):
+    """Errors are normalised by each compartment's peak over the run: after the epidemic
+    wave E and I decay below FP32's smallest subnormal (1.4e-45) while FP64 keeps
+    decaying, so a ratio to the final field's own maximum would be meaningless."""
     wl = inputs.centre_bump_workload()
     s = solver_for(wl, precision)
     s.write(wl["state"])
-    s.step(wl["steps"])
-    got = s.read()
-    want = oracle.sslbm_run(wl["state"], taus(wl["d"]), wl["rates"].as_tuple(), 1.0, wl["bc"], wl["steps"])
-    e2, einf = rel_l2(got, want), rel_max(got, want)
-    print(f"precision {precision}: rel L2 {e2}, rel Linf {einf}")
-    assert (e2 <= FP32_LONG_TOL).all() and (einf <= FP32_LONG_TOL).all(), (e2, einf)
+    ref = wl["state"]
+    tau, rates = taus(wl["d"]), wl["rates"].as_tuple()
+    done = 0
+    got, want = {}, {}
+    for t in (100, 300, wl["steps"]):
+        s.step(t - done)
+        ref = oracle.sslbm_run(ref, tau, rates, 1.0, wl["bc"], t - done)
+        done = t
+        got[t], want[t] = s.read(), ref
+    peak = np.max([np.abs(w).reshape(5, -1).max(axis=1) for w in want.values()], axis=0)
+    for t in got:
+        diff = (got[t] - want[t]).reshape(5, -1)
+        einf = np.abs(diff).max(axis=1) / peak
+        e2 = np.sqrt((diff ** 2).mean(axis=1)) / peak
+        print(f"precision {precision} t={t}: rel-to-peak L2 {e2}, Linf {einf}")
+        assert (e2 <= FP32_LONG_TOL).all() and (einf <= FP32_LONG_TOL).all(), (t, e2, einf)
 
 
 @pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV])
@@ -186,10 +200,19 @@ def test_bgk_fp32_centre_bump_within_tolerance():
     wl = inputs.centre_bump_workload()
     s = solver_for(wl, L.FP32, schemes=L.WANT_BGK | L.WANT_SSLBM)
     s.write(wl["state"], scheme=L.SCHEME_BGK)
-    s.bgk_step(500)
-    got = s.read(scheme=L.SCHEME_BGK)
-    want = oracle.bgk_run_state(wl["state"], taus(wl["d"]), wl["rates"].as_tuple(), 1.0, wl["bc"], 500)
-    assert (rel_max(got, want) <= FP32_LONG_TOL).all(), rel_max(got, want)
+    tau, rates = taus(wl["d"]), wl["rates"].as_tuple()
+    got, want = {}, {}
+    f, D = oracle.bgk_init(wl["state"])
+    done = 0
+    for t in (100, 500):
+        s.bgk_step(t - done)
+        f, D = oracle.bgk_run(f, D, tau, rates, 1.0, wl["bc"], t - done)
+        done = t
+        got[t], want[t] = s.read(scheme=L.SCHEME_BGK), oracle.bgk_density(f, D)
+    peak = np.max([np.abs(w).reshape(5, -1).max(axis=1) for w in want.values()], axis=0)
+    for t in got:
+        einf = np.abs((got[t] - want[t]).reshape(5, -1)).max(axis=1) / peak
+        assert (einf <= FP32_LONG_TOL).all(), (t, einf)
 
 
 # ---------------------------------------------------------------------------
