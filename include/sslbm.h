@@ -182,6 +182,26 @@ int64_t sslbm_steps_done(const sslbm_handle* h, int scheme);
  * SSLBM_ERR_NONFINITE if any total is NaN or Inf (results still written). */
 int sslbm_diagnostics(sslbm_handle* h, int scheme, double* totals, double* peak_I);
 
+/* Totals and peak infected of caller-provided fields, allocating no device memory.
+ * The paper has no counterpart: this serves callers that hold device buffers but
+ * cannot allocate -- e.g. a monitoring hook inside another framework's time loop whose
+ * memory pool owns the free device memory (a cudaMalloc could fail, fragment the pool
+ * or synchronise the device), or a plain C caller with no allocator for this device --
+ * and so cannot give sslbm_create() the workspace sslbm_diagnostics() uses.
+ * fields: device pointer to five planes S, E, I, R, D of ny x nx values each, laid out
+ * [5][ny][nx] (the layout sslbm_read() returns), of type dtype (SSLBM_DT_F64 or
+ * SSLBM_DT_F32).  totals (5 doubles) and peak_I are host outputs (either may be NULL).
+ * stream: a cudaStream_t (NULL = legacy default stream); the call synchronises it.
+ * Limit: ny <= 16384 rows (the scratch is a built-in 768 KiB device array, one slot
+ * per row); larger ny returns SSLBM_ERR_BAD_ARG.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.  The first call on each device looks up the
+ * array's device address (with that device current) and should come before any stream
+ * capture.  All calls on a device share the array and it keeps the last call's
+ * partial sums; calls that overlap on the GPU race on it, so order them on one stream.
+ * Returns SSLBM_ERR_NONFINITE if a total is NaN or Inf (results still written). */
+int sslbm_diagnostics_noalloc(const void* fields, int dtype, int64_t nx, int64_t ny,
+                              double* totals, double* peak_I, void* stream);
+
 /* ---- tuning --------------------------------------------------------------------------- */
 
 /* Temporal-blocking depth k (steps fused per pass, 1..SSLBM_MAX_DEPTH) and the

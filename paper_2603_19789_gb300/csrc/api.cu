@@ -104,6 +104,11 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace sslbm {
+// Record a failure for sslbm_last_error() from another translation unit.
+int record_error(int status, const char* msg) { return fail(status, "%s", msg); }
+}  // namespace sslbm
+
 struct sslbm_handle {
   sslbm_grid g;
   sslbm_params p;

@@ -35,7 +35,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP
 EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspace_bytes",
            "sslbm_create", "sslbm_set_stream", "sslbm_destroy", "sslbm_write", "sslbm_read",
            "sslbm_step", "bgk_step", "sslbm_steps_done", "sslbm_diagnostics",
-           "sslbm_set_blocking", "sslbm_get_blocking")
+           "sslbm_set_blocking", "sslbm_get_blocking", "sslbm_diagnostics_noalloc")
 
 
 class SslbmError(RuntimeError):
@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH):
                                         ctypes.POINTER(ctypes.c_double)]),
             "sslbm_set_blocking": (i32, [_vp, i32, i32]),
             "sslbm_get_blocking": (i32, [_vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "sslbm_diagnostics_noalloc": (i32, [_vp, i32, i64, i64, ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_double), _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -207,6 +209,22 @@ def sslbm_diagnostics(h, scheme: int = SCHEME_SSLBM):
     tot = (ctypes.c_double * 5)()
     pk = ctypes.c_double(0.0)
     _check(load().sslbm_diagnostics(h, int(scheme), tot, ctypes.byref(pk)), "sslbm_diagnostics")
+    return np.array(tot[:]), float(pk.value)
+
+
+def sslbm_diagnostics_noalloc(fields, stream: int = 0):
+    """Totals and peak infected of a device tensor of shape (5, ny, nx) (float64 or
+    float32) through the allocation-free entry point; returns (totals, peak_I)."""
+    ptr, dev, code, _ = _buffer(fields)
+    if not dev:
+        raise ValueError("fields must be a device tensor")
+    if fields.dim() != 3 or fields.shape[0] != 5:
+        raise ValueError("fields must have shape (5, ny, nx)")
+    tot = (ctypes.c_double * 5)()
+    pk = ctypes.c_double(0.0)
+    _check(load().sslbm_diagnostics_noalloc(_vp(ptr), code, int(fields.shape[2]), int(fields.shape[1]),
+                                            tot, ctypes.byref(pk), _vp(stream)),
+           "sslbm_diagnostics_noalloc")
     return np.array(tot[:]), float(pk.value)
 
 
