@@ -211,6 +211,7 @@ def timed_steps(solver, n_lat, steps, stream, diag=True):
 
 
 def main():
+    global NX, NY
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=103)
@@ -220,6 +221,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary variant timings")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nx", type=int, default=NX, help="grid width (profiling cases; default 8192)")
+    ap.add_argument("--ny", type=int, default=NY, help="grid height (profiling cases; default 8192)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -232,6 +235,7 @@ def main():
     from paper_2603_19789_gb300 import inputs
     from paper_2603_19789_gb300 import sslbm as L
 
+    NX, NY = args.nx, args.ny
     rank, world, local = dist_setup(args.gpus)
     libbuild.build()
     L.load()
@@ -292,7 +296,8 @@ def main():
             "config": {"workload": wl["name"], "nx": NX, "ny": NY, "bc": "no-flux",
                        "precision": "fp32", "lattice_steps_per_step": LATTICE_STEPS_PER_STEP,
                        "temporal_block_depth": depth, "seg_rows": seg or "auto",
-                       "l2": "state 1.34 GB > 129 MB L2 (no flush needed)",
+                       "l2": f"state {20 * cells / 1e9:.2f} GB vs 129 MB L2"
+                             + (" (no flush needed)" if 20 * cells > 129e6 else " (fits in L2)"),
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
@@ -366,7 +371,7 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
         torch.cuda.empty_cache()
         return cells * n_lat * reps / (ms * 1e-3) / 1e9, ms / (n_lat * reps)
 
-    for k in (1, 2, 3, 4):
+    for k in (1, 2, 3, 4, 6, 8):
         g, ms = glups_of(L.FP32, 48, 4, depth=k)
         out[f"fp32_depth{k}_glups"] = g
         if k == 1:

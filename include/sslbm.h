@@ -206,7 +206,7 @@ int sslbm_diagnostics_noalloc(const void* fields, int dtype, int64_t nx, int64_t
 
 /* Temporal-blocking depth k (steps fused per pass, 1..SSLBM_MAX_DEPTH) and the
  * kernel's row-segment length seg_rows (0 = automatic).  k = 0 restores the default. */
-#define SSLBM_MAX_DEPTH 4
+#define SSLBM_MAX_DEPTH 8
 int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows);
 
 /* Current blocking depth and segment length. */

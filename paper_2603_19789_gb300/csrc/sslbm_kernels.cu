@@ -6,16 +6,20 @@
 //                   FP32 Kahan).  Each thread updates V consecutive cells of a row with
 //                   16-byte vector loads (float4 / double2) of the centre, upper and lower
 //                   rows and two scalar edge loads; neighbouring rows come from L1/L2.
-//   blocked_kernel  K steps per launch (temporal blocking) for the FP32 variants.  One
-//                   warp owns a 128-column strip (4 columns per lane, float4 loads) and
-//                   streams down a segment of rows.  For every level s = 1..K it keeps the
-//                   two previous rows of level s-1 in registers; when row q of level 0
-//                   arrives, level s computes row q - s.  x neighbours come from warp
-//                   shuffles; each strip carries a K-column halo on both sides (one or two
-//                   lanes), so warps never synchronise with each other.  Rows and columns
+//   pipe_kernel     K steps per launch (temporal blocking, K = 2..8) for the FP32
+//                   variants, as a pipeline of K warps per CTA: warp s computes level s+1
+//                   of the time-step wavefront.  A CTA owns a 128-column strip (4 columns
+//                   per lane, 16-byte accesses) with a K-column halo on each side and
+//                   streams down a segment of rows.  Warp 0 brings level-0 rows in with
+//                   cp.async into a shared-memory ring several rows ahead; every level's
+//                   output row goes through a double-buffered shared-memory slot to the
+//                   next warp, one CTA barrier per row; the last warp writes level K to
+//                   global memory.  Each warp keeps only its own level's two previous rows
+//                   in registers (about 110 registers per thread), so several CTAs share
+//                   an SM.  x neighbours come from warp shuffles.  Rows and columns
 //                   outside the domain are loaded as ghost images (periodic wrap or the
 //                   even mirror extension), which the uniform stencil keeps consistent, so
-//                   no boundary logic is needed inside the level loop.  DRAM traffic is one
+//                   no boundary logic is needed inside the pipeline.  DRAM traffic is one
 //                   read and one write of the five planes per K steps.
 // Both use the same per-cell expressions (sslbm_internal.cuh), so a blocked launch gives
 // the same bits as K one-step launches.
@@ -26,6 +30,23 @@ namespace sslbm {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRing0 = 4;  // level-0 rows in flight per CTA
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+// Asynchronous global -> shared copies (cp.async): 16 bytes bypassing L1, or 4 bytes.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 template <typename T, int V>
 struct Vec;
@@ -141,102 +162,143 @@ __global__ void __launch_bounds__(256) step1_kernel(const GridView g, const Coef
 }
 
 template <int MODE, int K>
-__global__ void __launch_bounds__(128) blocked_kernel(const GridView g, const Coeffs<float> k,
-                                                      const float* __restrict__ in,
-                                                      float* __restrict__ out, const int seg_rows,
-                                                      const int nstrips, const int64_t nwarps) {
-  constexpr int HL = (K + 3) / 4;     // halo lanes on each side of the strip
-  constexpr int WV = 128 - 8 * HL;    // columns written per strip
+__global__ void __launch_bounds__(32 * K) pipe_kernel(const GridView g, const Coeffs<float> k,
+                                                     const float* __restrict__ in,
+                                                     float* __restrict__ out, const int seg_rows,
+                                                     const int nstrips) {
+  constexpr int HL = (K + 3) / 4;   // halo lanes on each side of the strip
+  constexpr int WV = 128 - 8 * HL;  // columns written per strip
+  // r0: level-0 rows (warp 0's lanes read back exactly what they copied);
+  // rl[s-1]: level-s rows from warp s-1 to warp s, double-buffered by iteration parity.
+  __shared__ __align__(16) float r0[kRing0][5][128];
+  __shared__ __align__(16) float rl[K - 1][2][5][128];
   const int lane = threadIdx.x & 31;
-  const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (wid >= nwarps) return;  // whole warp leaves together
-  const int strip = (int)(wid % nstrips);
-  const int64_t y0 = (wid / nstrips) * (int64_t)seg_rows;
+  const int s = threadIdx.x >> 5;  // this warp computes level s + 1
+  const int strip = (int)(blockIdx.x % (unsigned)nstrips);
+  const int64_t y0 = (int64_t)(blockIdx.x / (unsigned)nstrips) * seg_rows;
   const int64_t y1 = (y0 + seg_rows < g.ny) ? y0 + seg_rows : g.ny;
   const int64_t xs = (int64_t)strip * WV - 4 * HL + 4 * lane;
   const bool vec_ok = xs >= 0 && xs + 3 < g.nx;
-  int64_t xm[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) xm[j] = ghost_index(xs + j, g.nx, g.bc);
   const bool writer = lane >= HL && lane < 32 - HL && xs < g.nx;
+  // A column more than K cells outside the domain cannot influence a written cell within
+  // K steps, so lanes made only of such columns (the tail of the last strip) load nothing.
+  const bool loads = xs < g.nx + K && xs + 3 >= -K;
+  int xm[4];  // ghost images of this lane's columns, for lanes on a domain edge
+#pragma unroll
+  for (int j = 0; j < 4; ++j) xm[j] = (int)ghost_index(xs + j, g.nx, g.bc);
+  // Warp s computes, at iteration q, level s+1 of row q - 2s - 1 from level-s rows
+  // q-2s-2 (P), q-2s-1 (C) and q-2s (N).  Level-0 rows span [y0-K, y1+K); the last warp
+  // finishes row y1-1 at iteration y1 + 2K - 2.
+  const int64_t qa = y0 - K, qb = y1 + 2 * K - 1, load_end = y1 + K;
 
-  float P[K][4][4], C[K][4][4], CD[K][4];
-#pragma unroll
-  for (int s = 0; s < K; ++s)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      CD[s][j] = 0.f;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) P[s][f][j] = C[s][f][j] = 0.f;
-    }
+  for (int i = threadIdx.x; i < kRing0 * 5 * 128; i += 32 * K) (&r0[0][0][0])[i] = 0.f;
+  for (int i = threadIdx.x; i < (K - 1) * 2 * 5 * 128; i += 32 * K) (&rl[0][0][0][0])[i] = 0.f;
+  __syncthreads();
 
-  for (int64_t q = y0 - K; q < y1 + K; ++q) {
+  auto issue = [&](int64_t q) {  // warp 0: copy level-0 row q into its ring slot
+    if (!loads) return;
+    const int slot = (int)((q - qa) % kRing0);
     const int64_t row = ghost_index(q, g.ny, g.bc) * g.pitch;
-    float N[5][4];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
-      const float* p = in + f * g.plane + row;
+      const float* src = in + f * g.plane + row;
+      float* dst = &r0[slot][f][4 * lane];
       if (vec_ok) {
-        Vec<float, 4>::load(p + xs, N[f]);
+        cp_async16(dst, src + xs);
       } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) N[f][j] = p[xm[j]];
+        for (int j = 0; j < 4; ++j) cp_async4(dst + j, src + xm[j]);
       }
     }
+  };
+  if (s == 0) {
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-      // level s holds rows q-s-2 (P), q-s-1 (C); N is its row q-s.  Compute level s+1 at
-      // row q-s-1.
-      float lp[4][4];
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const float L = __shfl_up_sync(kFull, C[s][f][3], 1);
-        const float R = __shfl_down_sync(kFull, C[s][f][0], 1);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float l = (j == 0) ? L : C[s][f][j > 0 ? j - 1 : 0];
-          const float r = (j == 3) ? R : C[s][f][j < 3 ? j + 1 : 3];
-          lp[f][j] = lap5(C[s][f][j], l, r, P[s][f][j], N[f][j]);
-        }
-      }
-      float M[5][4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if constexpr (MODE == MODE_DEV) {
-          seird_cell_dev(k, C[s][0][j], C[s][1][j], C[s][2][j], C[s][3][j], CD[s][j], lp[0][j],
-                         lp[1][j], lp[2][j], lp[3][j], M[0][j], M[1][j], M[2][j], M[3][j], M[4][j]);
-        } else {
-          seird_cell(k, C[s][0][j], C[s][1][j], C[s][2][j], C[s][3][j], CD[s][j], lp[0][j],
-                     lp[1][j], lp[2][j], lp[3][j], M[0][j], M[1][j], M[2][j], M[3][j], M[4][j]);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          P[s][f][j] = C[s][f][j];
-          C[s][f][j] = N[f][j];
-        }
-        CD[s][j] = N[4][j];
-#pragma unroll
-        for (int f = 0; f < 5; ++f) N[f][j] = M[f][j];
-      }
-    }
-    const int64_t r = q - K;
-    if (writer && r >= y0) {
-      float* o = out + r * g.pitch + xs;
-      if (xs + 3 < g.nx) {
-#pragma unroll
-        for (int f = 0; f < 5; ++f) Vec<float, 4>::store(o + f * g.plane, N[f]);
-      } else {
-#pragma unroll
-        for (int f = 0; f < 5; ++f)
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (xs + j < g.nx) o[f * g.plane + j] = N[f][j];
-      }
+    for (int p = 0; p < kRing0 - 1; ++p) {
+      if (qa + p < load_end) issue(qa + p);
+      cp_async_commit();
     }
   }
+
+  float P[4][4], C[4][4], CD[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    CD[j] = 0.f;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) P[f][j] = C[f][j] = 0.f;
+  }
+
+  for (int64_t q = qa; q < qb; ++q) {
+    float N[5][4];
+    const float* src;
+    if (s == 0) {
+      if (q + kRing0 - 1 < load_end) issue(q + kRing0 - 1);
+      cp_async_commit();
+      cp_async_wait<kRing0 - 1>();
+      src = &r0[(int)((q - qa) % kRing0)][0][4 * lane];
+    } else {
+      src = &rl[s - 1][(int)((q - 1) & 1)][0][4 * lane];
+    }
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      const float4 t = *reinterpret_cast<const float4*>(src + 128 * f);
+      N[f][0] = t.x; N[f][1] = t.y; N[f][2] = t.z; N[f][3] = t.w;
+    }
+    float lp[4][4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const float L = __shfl_up_sync(kFull, C[f][3], 1);
+      const float R = __shfl_down_sync(kFull, C[f][0], 1);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float l = (j == 0) ? L : C[f][j > 0 ? j - 1 : 0];
+        const float r = (j == 3) ? R : C[f][j < 3 ? j + 1 : 3];
+        lp[f][j] = lap5(C[f][j], l, r, P[f][j], N[f][j]);
+      }
+    }
+    float M[5][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if constexpr (MODE == MODE_DEV) {
+        seird_cell_dev(k, C[0][j], C[1][j], C[2][j], C[3][j], CD[j], lp[0][j], lp[1][j], lp[2][j],
+                       lp[3][j], M[0][j], M[1][j], M[2][j], M[3][j], M[4][j]);
+      } else {
+        seird_cell(k, C[0][j], C[1][j], C[2][j], C[3][j], CD[j], lp[0][j], lp[1][j], lp[2][j],
+                   lp[3][j], M[0][j], M[1][j], M[2][j], M[3][j], M[4][j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        P[f][j] = C[f][j];
+        C[f][j] = N[f][j];
+      }
+      CD[j] = N[4][j];
+    }
+    if (s < K - 1) {
+      float* dst = &rl[s < K - 1 ? s : 0][(int)(q & 1)][0][4 * lane];
+#pragma unroll
+      for (int f = 0; f < 5; ++f)
+        *reinterpret_cast<float4*>(dst + 128 * f) = make_float4(M[f][0], M[f][1], M[f][2], M[f][3]);
+    } else {
+      const int64_t r = q - 2 * K + 1;
+      if (writer && r >= y0 && r < y1) {
+        float* o = out + r * g.pitch + xs;
+        if (xs + 3 < g.nx) {
+#pragma unroll
+          for (int f = 0; f < 5; ++f) Vec<float, 4>::store(o + f * g.plane, M[f]);
+        } else {
+#pragma unroll
+          for (int f = 0; f < 5; ++f)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (xs + j < g.nx) o[f * g.plane + j] = M[f][j];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (s == 0) cp_async_wait<0>();
 }
 
 template <typename T, int V, int MODE>
@@ -253,19 +315,29 @@ cudaError_t launch_step1_t(const GridView& g, const void* coeffs, const void* in
 }
 
 template <int MODE, int K>
+void prefer_shared(bool& done) {
+  if (!done) {
+    cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    done = true;
+  }
+}
+
+template <int MODE, int K>
 cudaError_t launch_blocked_t(const GridView& g, const void* coeffs, const void* in, void* out,
                              int seg_rows, cudaStream_t s) {
   constexpr int HL = (K + 3) / 4;
   constexpr int WV = 128 - 8 * HL;
+  static bool carveout_set = false;
+  prefer_shared<MODE, K>(carveout_set);
   if (seg_rows <= 0) return cudaErrorInvalidValue;
   const int64_t nstrips = (g.nx + WV - 1) / WV;
   const int64_t nseg = (g.ny + seg_rows - 1) / seg_rows;
-  const int64_t nwarps = nstrips * nseg;
-  const int64_t blocks = (nwarps + 3) / 4;
-  if (blocks > 0x7fffffffLL || nstrips > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  blocked_kernel<MODE, K><<<(unsigned)blocks, 128, 0, s>>>(
+  const int64_t blocks = nstrips * nseg;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  pipe_kernel<MODE, K><<<(unsigned)blocks, 32 * K, 0, s>>>(
       g, *static_cast<const Coeffs<float>*>(coeffs), static_cast<const float*>(in),
-      static_cast<float*>(out), seg_rows, (int)nstrips, nwarps);
+      static_cast<float*>(out), seg_rows, (int)nstrips);
   return cudaGetLastError();
 }
 
@@ -273,12 +345,15 @@ template <int MODE, int K>
 int default_seg_rows_t(const GridView& g) {
   constexpr int HL = (K + 3) / 4;
   constexpr int WV = 128 - 8 * HL;
+  static bool carveout_set = false;
+  prefer_shared<MODE, K>(carveout_set);
   const int64_t nstrips = (g.nx + WV - 1) / WV;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blocked_kernel<MODE, K>, 128, 0);
-  const int64_t resident = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) * 4;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_kernel<MODE, K>, 32 * K, 0);
+  // one wave: as many CTAs as fit on the device at once, split into row segments
+  const int64_t resident = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
   int64_t nseg = resident / nstrips;
   if (nseg < 1) nseg = 1;
   int64_t rows = (g.ny + nseg - 1) / nseg;
@@ -291,26 +366,37 @@ template <int MODE>
 cudaError_t launch_blocked_mode(const GridView& g, const void* coeffs, const void* in, void* out,
                                 int depth, int seg_rows, cudaStream_t s) {
   switch (depth) {
-    case 1: return launch_blocked_t<MODE, 1>(g, coeffs, in, out, seg_rows, s);
     case 2: return launch_blocked_t<MODE, 2>(g, coeffs, in, out, seg_rows, s);
     case 3: return launch_blocked_t<MODE, 3>(g, coeffs, in, out, seg_rows, s);
     case 4: return launch_blocked_t<MODE, 4>(g, coeffs, in, out, seg_rows, s);
+    case 5: return launch_blocked_t<MODE, 5>(g, coeffs, in, out, seg_rows, s);
+    case 6: return launch_blocked_t<MODE, 6>(g, coeffs, in, out, seg_rows, s);
+    case 7: return launch_blocked_t<MODE, 7>(g, coeffs, in, out, seg_rows, s);
+    case 8: return launch_blocked_t<MODE, 8>(g, coeffs, in, out, seg_rows, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int MODE>
+int default_seg_rows_mode(const GridView& g, int depth) {
+  switch (depth) {
+    case 2: return default_seg_rows_t<MODE, 2>(g);
+    case 3: return default_seg_rows_t<MODE, 3>(g);
+    case 4: return default_seg_rows_t<MODE, 4>(g);
+    case 5: return default_seg_rows_t<MODE, 5>(g);
+    case 6: return default_seg_rows_t<MODE, 6>(g);
+    case 7: return default_seg_rows_t<MODE, 7>(g);
+    case 8: return default_seg_rows_t<MODE, 8>(g);
+    default: return 0;
   }
 }
 
 }  // namespace
 
 int blocked_default_seg_rows(int precision, const GridView& g, int depth) {
-  if (precision != SSLBM_FP32 && precision != SSLBM_FP32_DEV) return 0;
-  const bool dev = precision == SSLBM_FP32_DEV;
-  switch (depth) {
-    case 1: return dev ? default_seg_rows_t<MODE_DEV, 1>(g) : default_seg_rows_t<MODE_PLAIN, 1>(g);
-    case 2: return dev ? default_seg_rows_t<MODE_DEV, 2>(g) : default_seg_rows_t<MODE_PLAIN, 2>(g);
-    case 3: return dev ? default_seg_rows_t<MODE_DEV, 3>(g) : default_seg_rows_t<MODE_PLAIN, 3>(g);
-    case 4: return dev ? default_seg_rows_t<MODE_DEV, 4>(g) : default_seg_rows_t<MODE_PLAIN, 4>(g);
-    default: return 0;
-  }
+  if (precision == SSLBM_FP32) return default_seg_rows_mode<MODE_PLAIN>(g, depth);
+  if (precision == SSLBM_FP32_DEV) return default_seg_rows_mode<MODE_DEV>(g, depth);
+  return 0;
 }
 
 bool blocked_supported(int precision, const GridView&) {

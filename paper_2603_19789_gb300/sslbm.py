@@ -28,7 +28,7 @@ S, E, I, R, D, NCOMP = 0, 1, 2, 3, 4, 5
 ALL = -1
 DT_F64, DT_F32 = 0, 1
 WANT_SSLBM, WANT_BGK = 1, 2
-MAX_DEPTH = 4
+MAX_DEPTH = 8
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP32_KAHAN}
 
 # every symbol include/sslbm.h declares

@@ -151,7 +151,7 @@ def test_blocked_depths_give_identical_bits(precision, bc, nx, ny):
     ref.set_blocking(1)
     ref.step(11)
     base = ref.read(dtype=np.float32)
-    for k in (2, 3, 4):
+    for k in (2, 3, 4, 5, 8):
         s = solver_for(wl, precision)
         s.write(wl["state"])
         s.set_blocking(k)
@@ -163,8 +163,8 @@ def test_blocked_depths_give_identical_bits(precision, bc, nx, ny):
     assert (rel_max(base.astype(np.float64), want) <= FP32_SHORT_TOL).all()
 
 
-@pytest.mark.parametrize("seg_rows", [12, 16, 50, 333])
-def test_blocked_segment_lengths_give_identical_bits(seg_rows):
+@pytest.mark.parametrize("depth,seg_rows", [(3, 12), (3, 16), (3, 50), (3, 333), (8, 32), (8, 41), (6, 100)])
+def test_blocked_segment_lengths_give_identical_bits(depth, seg_rows):
     wl = small_workload(300, 333, 1, seed=5)
     ref = solver_for(wl, L.FP32)
     ref.write(wl["state"])
@@ -173,7 +173,7 @@ def test_blocked_segment_lengths_give_identical_bits(seg_rows):
     base = ref.read(dtype=np.float32)
     s = solver_for(wl, L.FP32)
     s.write(wl["state"])
-    s.set_blocking(3, seg_rows)
+    s.set_blocking(depth, seg_rows)
     s.step(9)
     assert np.array_equal(s.read(dtype=np.float32).view(np.uint32), base.view(np.uint32))
 
