@@ -246,10 +246,13 @@ def main():
     rates = wl["rates"].as_tuple()
 
     s = L.Solver(NX, NY, rates, d=wl["d"], bc=wl["bc"], precision=L.FP32)
+    s.write(state32)
+    tuned = None
     if args.depth:
         s.set_blocking(args.depth)
+    else:
+        tuned = s.autotune(300.0)  # (depth, seg_rows, ms per lattice step) from the library's autotuner
     depth, seg = s.get_blocking()
-    s.write(state32)
     for _ in range(args.warmup):
         s.step(LATTICE_STEPS_PER_STEP)
         s.diagnostics()
@@ -265,7 +268,7 @@ def main():
     total_ms = max_over_ranks(total_ms, world)
     cells = NX * NY
     value = world * cells * LATTICE_STEPS_PER_STEP * args.steps / (total_ms * 1e-3) / 1e9
-    launches_per_step = math.ceil(LATTICE_STEPS_PER_STEP / depth) + 2  # blocked launches + 2 diagnostics kernels
+    launches_per_step = math.ceil(LATTICE_STEPS_PER_STEP / depth) + 2  # step launches + 2 diagnostics kernels
     launch_ms = kern_ms / (args.steps * math.ceil(LATTICE_STEPS_PER_STEP / depth))
     hbm, peak_kind = load_peaks()
     achieved = BYTES_PER_CELL_FP32 * cells / (launch_ms * 1e-3) / 1e9
@@ -296,12 +299,13 @@ def main():
             "config": {"workload": wl["name"], "nx": NX, "ny": NY, "bc": "no-flux",
                        "precision": "fp32", "lattice_steps_per_step": LATTICE_STEPS_PER_STEP,
                        "temporal_block_depth": depth, "seg_rows": seg or "auto",
+                       "blocking_chosen_by": "autotuner" if tuned else "--depth",
                        "l2": f"state {20 * cells / 1e9:.2f} GB vs 129 MB L2"
                              + (" (no flush needed)" if 20 * cells > 129e6 else " (fits in L2)"),
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": f"blocked_kernel<fp32, K={depth}>",
+                         "kernel": f"pipe_kernel<fp32, K={depth}>" if depth > 1 else "step1_kernel<fp32>",
                          "bytes_per_launch": BYTES_PER_CELL_FP32 * cells,
                          "launch_ms": launch_ms,
                          "cell_updates_per_launch": cells * depth},

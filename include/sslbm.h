@@ -209,6 +209,16 @@ int sslbm_diagnostics_noalloc(const void* fields, int dtype, int64_t nx, int64_t
 #define SSLBM_MAX_DEPTH 8
 int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows);
 
+/* Autotuner: choose the blocking depth (1..SSLBM_MAX_DEPTH) and segment length for this
+ * handle's grid and precision by timing candidate launches on the handle's stream.  The
+ * candidates read the current state and write the spare buffer, so the state is left
+ * unchanged.  budget_ms bounds the search (0 = 300 ms).  The choice is cached per
+ * (device, nx, ny, precision, boundary) for the life of the process, applied to the
+ * handle, and returned through depth, seg_rows and ms_per_step (each may be NULL).
+ * Synchronises the stream.  Not part of the paper (which gives no implementation). */
+int sslbm_autotune(sslbm_handle* h, double budget_ms, int* depth, int* seg_rows,
+                   double* ms_per_step);
+
 /* Current blocking depth and segment length. */
 int sslbm_get_blocking(const sslbm_handle* h, int* k, int* seg_rows);
 

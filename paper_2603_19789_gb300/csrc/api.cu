@@ -8,7 +8,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
+#include <vector>
 
 #include "sslbm_internal.cuh"
 
@@ -453,6 +457,112 @@ int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows) {
   h->depth = k == 0 ? (blocked ? 4 : 1) : k;
   if (seg_rows > 0 && seg_rows < 4 * h->depth) seg_rows = 4 * h->depth;
   h->seg_rows = seg_rows;
+  return SSLBM_OK;
+}
+
+namespace {
+struct TuneKey {
+  int device, precision, bc;
+  int64_t nx, ny;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(device, precision, bc, nx, ny) < std::tie(o.device, o.precision, o.bc, o.nx, o.ny);
+  }
+};
+struct TuneResult {
+  int depth, seg_rows;
+  double ms_per_step;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneResult> g_tune_cache;
+
+// Launch one pass of (depth, seg) from the current buffer into the spare one.
+cudaError_t tune_launch(sslbm_handle* h, int depth, int seg) {
+  if (depth == 1)
+    return sslbm::launch_sslbm_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur],
+                                     h->s_buf[1 - h->s_cur], h->stream);
+  return sslbm::launch_sslbm_blocked(h->g.precision, h->gv, &h->cf, h->s_buf[h->s_cur],
+                                     h->s_buf[1 - h->s_cur], depth, seg, h->stream);
+}
+}  // namespace
+
+int sslbm_autotune(sslbm_handle* h, double budget_ms, int* depth_out, int* seg_out,
+                   double* ms_per_step_out) {
+  int st = check_scheme(h, SSLBM_SCHEME_SSLBM);
+  if (st) return st;
+  if (!(budget_ms >= 0)) return fail(SSLBM_ERR_BAD_ARG, "budget_ms must be >= 0");
+  if (budget_ms == 0) budget_ms = 300.0;
+  DeviceGuard dg(h->device);
+  const TuneKey key{h->device, h->g.precision, h->g.bc, h->g.nx, h->g.ny};
+  TuneResult best{1, 0, 0.0};
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      best = it->second;
+      cached = true;
+    }
+  }
+  if (!cached) {
+    std::vector<std::pair<int, int>> cand;
+    cand.push_back({1, 0});
+    if (sslbm::blocked_supported(h->g.precision, h->gv)) {
+      for (int d = 2; d <= SSLBM_MAX_DEPTH; ++d) {
+        const int base = sslbm::blocked_default_seg_rows(h->g.precision, h->gv, d);
+        int segs[3] = {base, base / 2, base * 2};
+        for (int sg : segs) {
+          if (sg < 4 * d) sg = 4 * d;
+          bool dup = false;
+          for (auto& c : cand) dup |= (c.first == d && c.second == sg);
+          if (!dup) cand.push_back({d, sg});
+        }
+      }
+    }
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      return cuda_fail(e, "cudaEventCreate");
+    }
+    const double per_cand = budget_ms / (double)cand.size();
+    best.ms_per_step = 1e300;
+    for (auto& c : cand) {
+      // one untimed launch (also sizes the repetition count), then the timed repetitions
+      e = cudaEventRecord(e0, h->stream);
+      if (e == cudaSuccess) e = tune_launch(h, c.first, c.second);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms1 = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms1, e0, e1);
+      int reps = ms1 > 0 ? (int)(per_cand / (double)ms1) : 3;
+      if (reps < 2) reps = 2;
+      if (reps > 50) reps = 50;
+      if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = tune_launch(h, c.first, c.second);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(e, "autotune timing");
+      }
+      const double per_step = (double)ms / (double)(reps * c.first);
+      if (per_step < best.ms_per_step) best = TuneResult{c.first, c.second, per_step};
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  h->depth = best.depth;
+  h->seg_rows = best.depth > 1 ? best.seg_rows : 0;
+  if (depth_out) *depth_out = best.depth;
+  if (seg_out) *seg_out = h->seg_rows;
+  if (ms_per_step_out) *ms_per_step_out = best.ms_per_step;
   return SSLBM_OK;
 }
 

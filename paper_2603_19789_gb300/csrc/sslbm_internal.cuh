@@ -70,17 +70,28 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
-// FP32 uses the fast hardware-approximate quotient (max 2 ulp); FP64 the IEEE quotient.
-__device__ __forceinline__ float div_any(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double div_any(double a, double b) { return __ddiv_rn(a, b); }
+// Force of infection times dt, beta S I / N_c dt (Eq. sources).  The quotient is taken
+// against max(N_c, smallest normal): for nonnegative states N_c = 0 forces S = I = 0, so
+// the force is 0 there -- the reading used for the case the paper leaves open -- without
+// a branch.  FP32 multiplies by the hardware reciprocal (rcp.approx, <= 1 ulp); FP64
+// divides with the IEEE quotient.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float force_quot(float num, float Nc) {
+  return __fmul_rn(num, rcp_approx(fmaxf(Nc, 1.17549435e-38f)));
+}
+__device__ __forceinline__ double force_quot(double num, double Nc) {
+  return __ddiv_rn(num, fmax(Nc, 2.2250738585072014e-308));
+}
 
-// Force of infection times dt, beta S I / N_c dt (Eq. sources), taken as 0 when the
-// contact-eligible population N_c = S + E + I + R is zero.
 template <typename T>
 __device__ __forceinline__ T force_dt(const Coeffs<T>& k, T S, T E, T I, T R) {
   const T Nc = add_rn(add_rn(S, E), add_rn(I, R));
   const T num = mul_rn(mul_rn(k.bdt, S), I);
-  return Nc != T(0) ? div_any(num, Nc) : T(0);
+  return force_quot(num, Nc);
 }
 
 // Neighbour sum minus four times the centre.  On D2Q5 rho_f = rho_b = rho_c/3 + (sum of
@@ -140,6 +151,45 @@ __device__ __forceinline__ void seird_increments(const Coeffs<float>& k, float S
   inc[2] = add_rn(mul_rn(k.dl[2], lI), fma_rn(k.adt, E, -mul_rn(k.gdt, I)));
   inc[3] = fma_rn(k.rdt, I, mul_rn(k.dl[3], lR));
   inc[4] = mul_rn(k.ddt, I);
+}
+
+// ---- packed FP32 (two cells per instruction) ---------------------------------------
+// __fadd2_rn / __fmul2_rn / __ffma2_rn round each component exactly like the scalar
+// __fadd_rn / __fmul_rn / __fmaf_rn, and a - b is a + (-b) exactly, so the packed cell
+// update below gives the same bits as seird_cell / seird_cell_dev on each component.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
+
+// lap5 on two cells: lr = l + r (formed by the caller), u, d the rows above and below.
+__device__ __forceinline__ float2 lap5x2(float2 c, float2 lr, float2 u, float2 d) {
+  return fma2(splat2(-4.f), c, add2(lr, add2(u, d)));
+}
+
+__device__ __forceinline__ float2 force_dt2(const Coeffs<float>& k, float2 S, float2 E, float2 I,
+                                            float2 R) {
+  const float2 Nc = add2(add2(S, E), add2(I, R));
+  const float2 num = mul2(mul2(splat2(k.bdt), S), I);
+  const float2 r = make_float2(rcp_approx(fmaxf(Nc.x, 1.17549435e-38f)),
+                               rcp_approx(fmaxf(Nc.y, 1.17549435e-38f)));
+  return mul2(num, r);
+}
+
+// MODE 0: plain storage (x0 = S); MODE 1: deviation storage (x0 = sigma = s_ref - S).
+template <int DEV>
+__device__ __forceinline__ void seird_cell2(const Coeffs<float>& k, float2 x0, float2 E, float2 I,
+                                            float2 R, float2 D, float2 l0, float2 lE, float2 lI,
+                                            float2 lR, float2& n0, float2& nE, float2& nI,
+                                            float2& nR, float2& nD) {
+  const float2 S = DEV ? add2(splat2(k.s_ref), neg2(x0)) : x0;
+  const float2 F = force_dt2(k, S, E, I, R);
+  n0 = DEV ? add2(fma2(splat2(k.dl[0]), l0, x0), F) : add2(fma2(splat2(k.dl[0]), l0, x0), neg2(F));
+  nE = add2(fma2(splat2(k.dl[1]), lE, E), fma2(splat2(-k.adt), E, F));
+  nI = add2(fma2(splat2(k.dl[2]), lI, I), fma2(splat2(k.adt), E, neg2(mul2(splat2(k.gdt), I))));
+  nR = fma2(splat2(k.rdt), I, fma2(splat2(k.dl[3]), lR, R));
+  nD = fma2(splat2(k.ddt), I, D);
 }
 
 // ---- launchers (defined in the kernel translation units) --------------------------

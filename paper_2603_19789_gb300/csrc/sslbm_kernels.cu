@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) step1_kernel(const GridView g, const Coef
 }
 
 template <int MODE, int K>
-__global__ void __launch_bounds__(32 * K) pipe_kernel(const GridView g, const Coeffs<float> k,
+__global__ void __launch_bounds__(32 * K, 24 / K) pipe_kernel(const GridView g, const Coeffs<float> k,
                                                      const float* __restrict__ in,
                                                      float* __restrict__ out, const int seg_rows,
                                                      const int nstrips) {
@@ -219,16 +219,17 @@ __global__ void __launch_bounds__(32 * K) pipe_kernel(const GridView g, const Co
     }
   }
 
-  float P[4][4], C[4][4], CD[4];
+  // this warp's level: rows q-2s-2 (P) and q-2s-1 (C) as column pairs (0,1) and (2,3)
+  float2 P[4][2], C[4][2], CD[2];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    CD[j] = 0.f;
+  for (int h = 0; h < 2; ++h) {
+    CD[h] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) P[f][j] = C[f][j] = 0.f;
+    for (int f = 0; f < 4; ++f) P[f][h] = C[f][h] = make_float2(0.f, 0.f);
   }
 
   for (int64_t q = qa; q < qb; ++q) {
-    float N[5][4];
+    float2 N[5][2];
     const float* src;
     if (s == 0) {
       if (q + kRing0 - 1 < load_end) issue(q + kRing0 - 1);
@@ -241,58 +242,57 @@ __global__ void __launch_bounds__(32 * K) pipe_kernel(const GridView g, const Co
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
       const float4 t = *reinterpret_cast<const float4*>(src + 128 * f);
-      N[f][0] = t.x; N[f][1] = t.y; N[f][2] = t.z; N[f][3] = t.w;
+      N[f][0] = make_float2(t.x, t.y);
+      N[f][1] = make_float2(t.z, t.w);
     }
-    float lp[4][4];
+    float2 lp[4][2];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      const float L = __shfl_up_sync(kFull, C[f][3], 1);
-      const float R = __shfl_down_sync(kFull, C[f][0], 1);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float l = (j == 0) ? L : C[f][j > 0 ? j - 1 : 0];
-        const float r = (j == 3) ? R : C[f][j < 3 ? j + 1 : 3];
-        lp[f][j] = lap5(C[f][j], l, r, P[f][j], N[f][j]);
-      }
+      const float L = __shfl_up_sync(kFull, C[f][1].y, 1);
+      const float R = __shfl_down_sync(kFull, C[f][0].x, 1);
+      // left + right neighbour of columns 0..3, then the packed rest of lap5
+      const float2 lr0 = make_float2(__fadd_rn(L, C[f][0].y), __fadd_rn(C[f][0].x, C[f][1].x));
+      const float2 lr1 = make_float2(__fadd_rn(C[f][0].y, C[f][1].y), __fadd_rn(C[f][1].x, R));
+      lp[f][0] = lap5x2(C[f][0], lr0, P[f][0], N[f][0]);
+      lp[f][1] = lap5x2(C[f][1], lr1, P[f][1], N[f][1]);
     }
-    float M[5][4];
+    float2 M[5][2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if constexpr (MODE == MODE_DEV) {
-        seird_cell_dev(k, C[0][j], C[1][j], C[2][j], C[3][j], CD[j], lp[0][j], lp[1][j], lp[2][j],
-                       lp[3][j], M[0][j], M[1][j], M[2][j], M[3][j], M[4][j]);
-      } else {
-        seird_cell(k, C[0][j], C[1][j], C[2][j], C[3][j], CD[j], lp[0][j], lp[1][j], lp[2][j],
-                   lp[3][j], M[0][j], M[1][j], M[2][j], M[3][j], M[4][j]);
-      }
-    }
+    for (int h = 0; h < 2; ++h)
+      seird_cell2<MODE == MODE_DEV>(k, C[0][h], C[1][h], C[2][h], C[3][h], CD[h], lp[0][h], lp[1][h],
+                                    lp[2][h], lp[3][h], M[0][h], M[1][h], M[2][h], M[3][h], M[4][h]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int h = 0; h < 2; ++h) {
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        P[f][j] = C[f][j];
-        C[f][j] = N[f][j];
+        P[f][h] = C[f][h];
+        C[f][h] = N[f][h];
       }
-      CD[j] = N[4][j];
+      CD[h] = N[4][h];
     }
     if (s < K - 1) {
       float* dst = &rl[s < K - 1 ? s : 0][(int)(q & 1)][0][4 * lane];
 #pragma unroll
       for (int f = 0; f < 5; ++f)
-        *reinterpret_cast<float4*>(dst + 128 * f) = make_float4(M[f][0], M[f][1], M[f][2], M[f][3]);
+        *reinterpret_cast<float4*>(dst + 128 * f) =
+            make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
     } else {
       const int64_t r = q - 2 * K + 1;
       if (writer && r >= y0 && r < y1) {
         float* o = out + r * g.pitch + xs;
         if (xs + 3 < g.nx) {
 #pragma unroll
-          for (int f = 0; f < 5; ++f) Vec<float, 4>::store(o + f * g.plane, M[f]);
+          for (int f = 0; f < 5; ++f)
+            *reinterpret_cast<float4*>(o + f * g.plane) =
+                make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
         } else {
 #pragma unroll
-          for (int f = 0; f < 5; ++f)
+          for (int f = 0; f < 5; ++f) {
+            const float v[4] = {M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y};
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-              if (xs + j < g.nx) o[f * g.plane + j] = M[f][j];
+              if (xs + j < g.nx) o[f * g.plane + j] = v[j];
+          }
         }
       }
     }

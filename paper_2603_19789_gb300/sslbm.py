@@ -35,7 +35,8 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP
 EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspace_bytes",
            "sslbm_create", "sslbm_set_stream", "sslbm_destroy", "sslbm_write", "sslbm_read",
            "sslbm_step", "bgk_step", "sslbm_steps_done", "sslbm_diagnostics",
-           "sslbm_set_blocking", "sslbm_get_blocking", "sslbm_diagnostics_noalloc")
+           "sslbm_set_blocking", "sslbm_get_blocking", "sslbm_diagnostics_noalloc",
+           "sslbm_autotune")
 
 
 class SslbmError(RuntimeError):
@@ -90,6 +91,8 @@ def load(path: str = LIB_PATH):
                                         ctypes.POINTER(ctypes.c_double)]),
             "sslbm_set_blocking": (i32, [_vp, i32, i32]),
             "sslbm_get_blocking": (i32, [_vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "sslbm_autotune": (i32, [_vp, ctypes.c_double, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(ctypes.c_double)]),
             "sslbm_diagnostics_noalloc": (i32, [_vp, i32, i64, i64, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_double), _vp]),
         }
@@ -232,6 +235,15 @@ def sslbm_set_blocking(h, k: int, seg_rows: int = 0):
     _check(load().sslbm_set_blocking(h, int(k), int(seg_rows)), "sslbm_set_blocking")
 
 
+def sslbm_autotune(h, budget_ms: float = 0.0):
+    """Time candidate (depth, segment) launches and apply the fastest; returns
+    (depth, seg_rows, ms_per_lattice_step)."""
+    k, sg, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(load().sslbm_autotune(h, float(budget_ms), ctypes.byref(k), ctypes.byref(sg), ctypes.byref(ms)),
+           "sslbm_autotune")
+    return int(k.value), int(sg.value), float(ms.value)
+
+
 def sslbm_get_blocking(h):
     k, s = ctypes.c_int(0), ctypes.c_int(0)
     _check(load().sslbm_get_blocking(h, ctypes.byref(k), ctypes.byref(s)), "sslbm_get_blocking")
@@ -292,6 +304,9 @@ class Solver:
 
     def get_blocking(self):
         return sslbm_get_blocking(self.h)
+
+    def autotune(self, budget_ms=0.0):
+        return sslbm_autotune(self.h, budget_ms)
 
     def steps_done(self, scheme=SCHEME_SSLBM):
         return sslbm_steps_done(self.h, scheme)

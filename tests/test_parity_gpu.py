@@ -274,3 +274,24 @@ def test_error_statuses_on_gpu():
     with pytest.raises(L.SslbmError) as ei:
         s.bgk_step(1)  # this handle holds no BGK state
     assert ei.value.status == -1
+
+
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP64])
+def test_autotune_leaves_state_and_picks_a_valid_configuration(precision):
+    wl = small_workload(600, 333, 1, seed=12)
+    s = solver_for(wl, precision)
+    s.write(wl["state"])
+    before = s.read()
+    depth, seg, ms = s.autotune(40.0)
+    assert np.array_equal(s.read(), before)  # candidates write only the spare buffer
+    assert 1 <= depth <= L.MAX_DEPTH and ms > 0
+    if precision == L.FP64:
+        assert depth == 1
+    assert s.get_blocking() == (depth, seg)
+    assert s.autotune(40.0)[:2] == (depth, seg)  # cached per grid and precision
+    s.step(13)
+    ref = solver_for(wl, precision)
+    ref.write(wl["state"])
+    ref.set_blocking(1)
+    ref.step(13)
+    assert np.array_equal(s.read(), ref.read())
