@@ -222,6 +222,67 @@ int sslbm_autotune(sslbm_handle* h, double budget_ms, int* depth, int* seg_rows,
 /* Current blocking depth and segment length. */
 int sslbm_get_blocking(const sslbm_handle* h, int* k, int* seg_rows);
 
+/* ---- ensembles: many scenarios in one persistent launch ---------------------------------
+ * Not in the paper (which runs one scenario at a time): a batch of independent SEIRD
+ * scenarios, each on its own periodic grid (nx a multiple of 4) with its own rates and
+ * diffusivities, all advanced by the SSLBM update of sslbm_step with one persistent,
+ * CUDA-graph-captured launch per run.  The caller owns the device workspace. */
+typedef struct sslbm_scenario {
+  int64_t nx, ny;                  /* periodic grid of this scenario */
+  double dx, dt;                   /* lattice spacing and time step (> 0) */
+  double beta, alpha, gamma, phi;  /* Table I notation */
+  double d[5];                     /* diffusivities S, E, I, R, D (d[D] = 0), Eq. (diffusivity) */
+  double s_ref;                    /* FP32_DEV reference value of S */
+} sslbm_scenario;
+
+typedef struct sslbm_ensemble sslbm_ensemble;
+
+/* Workspace bytes for n scenarios in the given precision (SSLBM_FP32 or SSLBM_FP32_DEV). */
+int sslbm_ensemble_workspace_bytes(int n, const sslbm_scenario* sc, int precision, size_t* bytes);
+
+/* Create an ensemble (scenarios copied; states zero until written).  dev_ws: caller-owned,
+ * 256-byte aligned device memory of at least sslbm_ensemble_workspace_bytes bytes.
+ * Returns SSLBM_ERR_UNSTABLE when a relaxation time exceeds 5/4. */
+int sslbm_ensemble_create(int n, const sslbm_scenario* sc, int precision, void* dev_ws,
+                          size_t ws_bytes, void* stream, sslbm_ensemble** out);
+
+void sslbm_ensemble_destroy(sslbm_ensemble* e);
+
+/* Tile shape of the persistent launch: steps fused per pass (depth in {2..6, 8}) and the
+ * row-segment length of a tile (>= 4 * depth); the tile width is one 128-column strip. */
+int sslbm_ensemble_set_tiling(sslbm_ensemble* e, int depth, int seg_rows);
+int sslbm_ensemble_get_tiling(const sslbm_ensemble* e, int* depth, int* seg_rows);
+
+/* Bound on each dependency wait of the persistent launch (polls, default 2^24), and a
+ * fault-injection hook for tests: the work item numbered stall_item (-1 = none) never
+ * reports completion, so the waits that depend on it run out and sslbm_ensemble_run
+ * returns SSLBM_ERR_TIMEOUT instead of hanging.  After a timeout the states are undefined. */
+int sslbm_ensemble_set_wait_limit(sslbm_ensemble* e, long long spin_limit, long long stall_item);
+
+/* Set / get all five planes ([5][ny][nx]) of scenario idx, as in sslbm_write / sslbm_read
+ * (FP64 or FP32 values; host or device memory).  Both synchronise the stream. */
+int sslbm_ensemble_write(sslbm_ensemble* e, int idx, const void* src, int src_dtype, int on_device);
+int sslbm_ensemble_read(sslbm_ensemble* e, int idx, void* dst, int dst_dtype, int on_device);
+
+/* Advance every scenario by nsteps SSLBM steps: nsteps / depth fused step-blocks in one
+ * persistent launch (replayed from a cached CUDA graph), the remainder by one-step
+ * launches.  Synchronises the stream to check the wait status (SSLBM_ERR_TIMEOUT). */
+int sslbm_ensemble_run(sslbm_ensemble* e, int64_t nsteps);
+
+/* Per-scenario totals (n x 5 doubles, row = scenario) and peaks of I (n doubles), as in
+ * sslbm_diagnostics.  Either pointer may be NULL. */
+int sslbm_ensemble_diagnostics(sslbm_ensemble* e, double* totals, double* peak_I);
+
+/* Autotuner for the ensemble launch: times trial_blocks step-blocks (0 = 3) for each
+ * depth in {2, 3, 4, 6, 8} and segment length in {32, 64, 128, 256}, keeps the fastest
+ * per lattice step, and returns it (pointers may be NULL).  The trials run on the current
+ * contents and the states are cleared to zero afterwards, so call it before writing the
+ * initial states.  Synchronises the stream. */
+int sslbm_ensemble_autotune(sslbm_ensemble* e, int trial_blocks, int* depth, int* seg_rows,
+                            double* ms_per_step);
+
+int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,30 +24,13 @@
 // Both use the same per-cell expressions (sslbm_internal.cuh), so a blocked launch gives
 // the same bits as K one-step launches.
 #include "sslbm_internal.cuh"
+#include "sslbm_pipe.cuh"
 
 namespace sslbm {
 
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kRing0 = 4;  // level-0 rows in flight per CTA
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-// Asynchronous global -> shared copies (cp.async): 16 bytes bypassing L1, or 4 bytes.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 template <typename T, int V>
 struct Vec;
 template <>
@@ -163,142 +146,14 @@ __global__ void __launch_bounds__(256) step1_kernel(const GridView g, const Coef
 
 template <int MODE, int K>
 __global__ void __launch_bounds__(32 * K, 24 / K) pipe_kernel(const GridView g, const Coeffs<float> k,
-                                                     const float* __restrict__ in,
-                                                     float* __restrict__ out, const int seg_rows,
-                                                     const int nstrips) {
-  constexpr int HL = (K + 3) / 4;   // halo lanes on each side of the strip
-  constexpr int WV = 128 - 8 * HL;  // columns written per strip
-  // r0: level-0 rows (warp 0's lanes read back exactly what they copied);
-  // rl[s-1]: level-s rows from warp s-1 to warp s, double-buffered by iteration parity.
-  __shared__ __align__(16) float r0[kRing0][5][128];
-  __shared__ __align__(16) float rl[K - 1][2][5][128];
-  const int lane = threadIdx.x & 31;
-  const int s = threadIdx.x >> 5;  // this warp computes level s + 1
+                                                             const float* __restrict__ in,
+                                                             float* __restrict__ out,
+                                                             const int seg_rows, const int nstrips) {
+  __shared__ PipeSmem<K> sm;
   const int strip = (int)(blockIdx.x % (unsigned)nstrips);
   const int64_t y0 = (int64_t)(blockIdx.x / (unsigned)nstrips) * seg_rows;
   const int64_t y1 = (y0 + seg_rows < g.ny) ? y0 + seg_rows : g.ny;
-  const int64_t xs = (int64_t)strip * WV - 4 * HL + 4 * lane;
-  const bool vec_ok = xs >= 0 && xs + 3 < g.nx;
-  const bool writer = lane >= HL && lane < 32 - HL && xs < g.nx;
-  // A column more than K cells outside the domain cannot influence a written cell within
-  // K steps, so lanes made only of such columns (the tail of the last strip) load nothing.
-  const bool loads = xs < g.nx + K && xs + 3 >= -K;
-  int xm[4];  // ghost images of this lane's columns, for lanes on a domain edge
-#pragma unroll
-  for (int j = 0; j < 4; ++j) xm[j] = (int)ghost_index(xs + j, g.nx, g.bc);
-  // Warp s computes, at iteration q, level s+1 of row q - 2s - 1 from level-s rows
-  // q-2s-2 (P), q-2s-1 (C) and q-2s (N).  Level-0 rows span [y0-K, y1+K); the last warp
-  // finishes row y1-1 at iteration y1 + 2K - 2.
-  const int64_t qa = y0 - K, qb = y1 + 2 * K - 1, load_end = y1 + K;
-
-  for (int i = threadIdx.x; i < kRing0 * 5 * 128; i += 32 * K) (&r0[0][0][0])[i] = 0.f;
-  for (int i = threadIdx.x; i < (K - 1) * 2 * 5 * 128; i += 32 * K) (&rl[0][0][0][0])[i] = 0.f;
-  __syncthreads();
-
-  auto issue = [&](int64_t q) {  // warp 0: copy level-0 row q into its ring slot
-    if (!loads) return;
-    const int slot = (int)((q - qa) % kRing0);
-    const int64_t row = ghost_index(q, g.ny, g.bc) * g.pitch;
-#pragma unroll
-    for (int f = 0; f < 5; ++f) {
-      const float* src = in + f * g.plane + row;
-      float* dst = &r0[slot][f][4 * lane];
-      if (vec_ok) {
-        cp_async16(dst, src + xs);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cp_async4(dst + j, src + xm[j]);
-      }
-    }
-  };
-  if (s == 0) {
-#pragma unroll
-    for (int p = 0; p < kRing0 - 1; ++p) {
-      if (qa + p < load_end) issue(qa + p);
-      cp_async_commit();
-    }
-  }
-
-  // this warp's level: rows q-2s-2 (P) and q-2s-1 (C) as column pairs (0,1) and (2,3)
-  float2 P[4][2], C[4][2], CD[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    CD[h] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int f = 0; f < 4; ++f) P[f][h] = C[f][h] = make_float2(0.f, 0.f);
-  }
-
-  for (int64_t q = qa; q < qb; ++q) {
-    float2 N[5][2];
-    const float* src;
-    if (s == 0) {
-      if (q + kRing0 - 1 < load_end) issue(q + kRing0 - 1);
-      cp_async_commit();
-      cp_async_wait<kRing0 - 1>();
-      src = &r0[(int)((q - qa) % kRing0)][0][4 * lane];
-    } else {
-      src = &rl[s - 1][(int)((q - 1) & 1)][0][4 * lane];
-    }
-#pragma unroll
-    for (int f = 0; f < 5; ++f) {
-      const float4 t = *reinterpret_cast<const float4*>(src + 128 * f);
-      N[f][0] = make_float2(t.x, t.y);
-      N[f][1] = make_float2(t.z, t.w);
-    }
-    float2 lp[4][2];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const float L = __shfl_up_sync(kFull, C[f][1].y, 1);
-      const float R = __shfl_down_sync(kFull, C[f][0].x, 1);
-      // left + right neighbour of columns 0..3, then the packed rest of lap5
-      const float2 lr0 = make_float2(__fadd_rn(L, C[f][0].y), __fadd_rn(C[f][0].x, C[f][1].x));
-      const float2 lr1 = make_float2(__fadd_rn(C[f][0].y, C[f][1].y), __fadd_rn(C[f][1].x, R));
-      lp[f][0] = lap5x2(C[f][0], lr0, P[f][0], N[f][0]);
-      lp[f][1] = lap5x2(C[f][1], lr1, P[f][1], N[f][1]);
-    }
-    float2 M[5][2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-      seird_cell2<MODE == MODE_DEV>(k, C[0][h], C[1][h], C[2][h], C[3][h], CD[h], lp[0][h], lp[1][h],
-                                    lp[2][h], lp[3][h], M[0][h], M[1][h], M[2][h], M[3][h], M[4][h]);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        P[f][h] = C[f][h];
-        C[f][h] = N[f][h];
-      }
-      CD[h] = N[4][h];
-    }
-    if (s < K - 1) {
-      float* dst = &rl[s < K - 1 ? s : 0][(int)(q & 1)][0][4 * lane];
-#pragma unroll
-      for (int f = 0; f < 5; ++f)
-        *reinterpret_cast<float4*>(dst + 128 * f) =
-            make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
-    } else {
-      const int64_t r = q - 2 * K + 1;
-      if (writer && r >= y0 && r < y1) {
-        float* o = out + r * g.pitch + xs;
-        if (xs + 3 < g.nx) {
-#pragma unroll
-          for (int f = 0; f < 5; ++f)
-            *reinterpret_cast<float4*>(o + f * g.plane) =
-                make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
-        } else {
-#pragma unroll
-          for (int f = 0; f < 5; ++f) {
-            const float v[4] = {M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y};
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (xs + j < g.nx) o[f * g.plane + j] = v[j];
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (s == 0) cp_async_wait<0>();
+  pipe_tile<MODE, K>(sm, g, k, in, out, strip, y0, y1);
 }
 
 template <typename T, int V, int MODE>

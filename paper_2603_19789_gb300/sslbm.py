@@ -36,7 +36,11 @@ EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspa
            "sslbm_create", "sslbm_set_stream", "sslbm_destroy", "sslbm_write", "sslbm_read",
            "sslbm_step", "bgk_step", "sslbm_steps_done", "sslbm_diagnostics",
            "sslbm_set_blocking", "sslbm_get_blocking", "sslbm_diagnostics_noalloc",
-           "sslbm_autotune")
+           "sslbm_autotune", "sslbm_ensemble_workspace_bytes", "sslbm_ensemble_create",
+           "sslbm_ensemble_destroy", "sslbm_ensemble_set_tiling", "sslbm_ensemble_get_tiling",
+           "sslbm_ensemble_set_wait_limit", "sslbm_ensemble_write", "sslbm_ensemble_read",
+           "sslbm_ensemble_run", "sslbm_ensemble_diagnostics", "sslbm_ensemble_autotune",
+           "sslbm_ensemble_steps_done")
 
 
 class SslbmError(RuntimeError):
@@ -49,6 +53,13 @@ class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("dx", ctypes.c_double),
                 ("dt", ctypes.c_double), ("bc", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("schemes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Scenario(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("dx", ctypes.c_double),
+                ("dt", ctypes.c_double), ("beta", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("phi", ctypes.c_double), ("d", ctypes.c_double * 5),
+                ("s_ref", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -93,6 +104,20 @@ def load(path: str = LIB_PATH):
             "sslbm_get_blocking": (i32, [_vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "sslbm_autotune": (i32, [_vp, ctypes.c_double, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(ctypes.c_double)]),
+            "sslbm_ensemble_workspace_bytes": (i32, [i32, _vp, i32, ctypes.POINTER(ctypes.c_size_t)]),
+            "sslbm_ensemble_create": (i32, [i32, _vp, i32, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
+            "sslbm_ensemble_destroy": (None, [_vp]),
+            "sslbm_ensemble_set_tiling": (i32, [_vp, i32, i32]),
+            "sslbm_ensemble_get_tiling": (i32, [_vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "sslbm_ensemble_set_wait_limit": (i32, [_vp, ctypes.c_longlong, ctypes.c_longlong]),
+            "sslbm_ensemble_write": (i32, [_vp, i32, _vp, i32, i32]),
+            "sslbm_ensemble_read": (i32, [_vp, i32, _vp, i32, i32]),
+            "sslbm_ensemble_run": (i32, [_vp, i64]),
+            "sslbm_ensemble_diagnostics": (i32, [_vp, ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_double)]),
+            "sslbm_ensemble_autotune": (i32, [_vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                              ctypes.POINTER(ctypes.c_double)]),
+            "sslbm_ensemble_steps_done": (i64, [_vp]),
             "sslbm_diagnostics_noalloc": (i32, [_vp, i32, i64, i64, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_double), _vp]),
         }
@@ -240,7 +265,11 @@ def sslbm_autotune(h, budget_ms: float = 0.0):
     (depth, seg_rows, ms_per_lattice_step)."""
     k, sg, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
     _check(load().sslbm_autotune(h, float(budget_ms), ctypes.byref(k), ctypes.byref(sg), ctypes.byref(ms)),
-           "sslbm_autotune")
+           "sslbm_autotune", "sslbm_ensemble_workspace_bytes", "sslbm_ensemble_create",
+           "sslbm_ensemble_destroy", "sslbm_ensemble_set_tiling", "sslbm_ensemble_get_tiling",
+           "sslbm_ensemble_set_wait_limit", "sslbm_ensemble_write", "sslbm_ensemble_read",
+           "sslbm_ensemble_run", "sslbm_ensemble_diagnostics", "sslbm_ensemble_autotune",
+           "sslbm_ensemble_steps_done")
     return int(k.value), int(sg.value), float(ms.value)
 
 
@@ -310,3 +339,145 @@ class Solver:
 
     def steps_done(self, scheme=SCHEME_SSLBM):
         return sslbm_steps_done(self.h, scheme)
+
+
+# ---------------------------------------------------------------------------
+# ensembles
+# ---------------------------------------------------------------------------
+
+def make_scenarios(specs):
+    """specs: iterable of dicts with nx, ny, rates (beta, alpha, gamma, phi), d (4 or 5
+    values), optional dx, dt, s_ref."""
+    specs = list(specs)
+    arr = (Scenario * len(specs))()
+    for i, sp in enumerate(specs):
+        sc = arr[i]
+        sc.nx, sc.ny = int(sp["nx"]), int(sp["ny"])
+        sc.dx, sc.dt = float(sp.get("dx", 1.0)), float(sp.get("dt", 1.0))
+        sc.beta, sc.alpha, sc.gamma, sc.phi = (float(v) for v in sp["rates"])
+        d = list(sp["d"]) + [0.0] * (5 - len(sp["d"]))
+        for c in range(5):
+            sc.d[c] = float(d[c])
+        sc.s_ref = float(sp.get("s_ref", 1.0))
+    return arr
+
+
+def sslbm_ensemble_workspace_bytes(scenarios, precision=FP32) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().sslbm_ensemble_workspace_bytes(len(scenarios), ctypes.cast(scenarios, _vp), int(precision),
+                                                 ctypes.byref(n)), "sslbm_ensemble_workspace_bytes")
+    return int(n.value)
+
+
+def sslbm_ensemble_create(scenarios, precision, ws_ptr, ws_bytes, stream=0):
+    e = _vp()
+    _check(load().sslbm_ensemble_create(len(scenarios), ctypes.cast(scenarios, _vp), int(precision), _vp(ws_ptr),
+                                        int(ws_bytes), _vp(stream), ctypes.byref(e)), "sslbm_ensemble_create")
+    return e
+
+
+def sslbm_ensemble_destroy(e):
+    if e:
+        load().sslbm_ensemble_destroy(e)
+
+
+def sslbm_ensemble_set_tiling(e, depth, seg_rows):
+    _check(load().sslbm_ensemble_set_tiling(e, int(depth), int(seg_rows)), "sslbm_ensemble_set_tiling")
+
+
+def sslbm_ensemble_get_tiling(e):
+    d, s = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().sslbm_ensemble_get_tiling(e, ctypes.byref(d), ctypes.byref(s)), "sslbm_ensemble_get_tiling")
+    return int(d.value), int(s.value)
+
+
+def sslbm_ensemble_set_wait_limit(e, spin_limit, stall_item=-1):
+    _check(load().sslbm_ensemble_set_wait_limit(e, int(spin_limit), int(stall_item)),
+           "sslbm_ensemble_set_wait_limit")
+
+
+def sslbm_ensemble_write(e, idx, src):
+    ptr, dev, code, _ = _buffer(src)
+    _check(load().sslbm_ensemble_write(e, int(idx), _vp(ptr), code, dev), "sslbm_ensemble_write")
+
+
+def sslbm_ensemble_read(e, idx, dst):
+    ptr, dev, code, _ = _buffer(dst)
+    _check(load().sslbm_ensemble_read(e, int(idx), _vp(ptr), code, dev), "sslbm_ensemble_read")
+    return dst
+
+
+def sslbm_ensemble_run(e, nsteps):
+    _check(load().sslbm_ensemble_run(e, int(nsteps)), "sslbm_ensemble_run")
+
+
+def sslbm_ensemble_diagnostics(e, n):
+    tot = (ctypes.c_double * (5 * n))()
+    pk = (ctypes.c_double * n)()
+    _check(load().sslbm_ensemble_diagnostics(e, tot, pk), "sslbm_ensemble_diagnostics")
+    return np.array(tot[:]).reshape(n, 5), np.array(pk[:])
+
+
+def sslbm_ensemble_autotune(e, trial_blocks=0):
+    d, s, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(load().sslbm_ensemble_autotune(e, int(trial_blocks), ctypes.byref(d), ctypes.byref(s),
+                                          ctypes.byref(ms)), "sslbm_ensemble_autotune")
+    return int(d.value), int(s.value), float(ms.value)
+
+
+def sslbm_ensemble_steps_done(e):
+    return int(load().sslbm_ensemble_steps_done(e))
+
+
+class Ensemble:
+    """A batch of periodic scenarios with a torch-allocated device workspace."""
+
+    def __init__(self, specs, precision=FP32, device=None, stream=None):
+        import torch
+        self.specs = list(specs)
+        self.n = len(self.specs)
+        self.precision = precision
+        self.scen = make_scenarios(self.specs)
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = sslbm_ensemble_workspace_bytes(self.scen, precision)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.e = sslbm_ensemble_create(self.scen, precision, self.ws.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "e", None):
+            self.stream.synchronize()
+            sslbm_ensemble_destroy(self.e)
+            self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def write(self, idx, state):
+        sslbm_ensemble_write(self.e, idx, state)
+
+    def read(self, idx, dtype=np.float64):
+        sp = self.specs[idx]
+        out = np.empty((5, int(sp["ny"]), int(sp["nx"])), dtype=dtype)
+        return sslbm_ensemble_read(self.e, idx, out)
+
+    def run(self, nsteps):
+        sslbm_ensemble_run(self.e, nsteps)
+
+    def diagnostics(self):
+        return sslbm_ensemble_diagnostics(self.e, self.n)
+
+    def set_tiling(self, depth, seg_rows):
+        sslbm_ensemble_set_tiling(self.e, depth, seg_rows)
+
+    def get_tiling(self):
+        return sslbm_ensemble_get_tiling(self.e)
+
+    def set_wait_limit(self, spin_limit, stall_item=-1):
+        sslbm_ensemble_set_wait_limit(self.e, spin_limit, stall_item)
+
+    def autotune(self, trial_blocks=0):
+        return sslbm_ensemble_autotune(self.e, trial_blocks)
