@@ -221,6 +221,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary variant timings")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the ensemble measurement")
     ap.add_argument("--nx", type=int, default=NX, help="grid width (profiling cases; default 8192)")
     ap.add_argument("--ny", type=int, default=NY, help="grid height (profiling cases; default 8192)")
     args = ap.parse_args()
@@ -278,6 +279,10 @@ def main():
     if not args.no_extras:
         extras = secondary_timings(L, wl, state64, state32, stream, hbm)
 
+    ens = None
+    if not args.no_ensemble and rank == 0:
+        ens = ensemble_timing(L, torch, stream)
+
     e2e = None
     if not args.no_e2e:
         e2e = e2e_timing(L, torch, s, state32, stream, world)
@@ -315,6 +320,7 @@ def main():
             "cpu_baseline": cpu,
             "diagnostics": {"total_population": float(tot.sum()), "peak_I": peak_I},
             "extras": extras,
+            "ensemble": ens,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -391,6 +397,72 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
     out["bgk_fp32_glups"] = g
     out["bgk_fp32_hbm_frac"] = BGK_BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm
     return out
+
+
+def ensemble_timing(L, torch, stream, n_scen=512, steps=5000, err_scen=6, fp64_steps=40):
+    """The 512-scenario ensemble (grids 256..1024 squared, periodic, FP32) for 5000 steps in
+    one persistent graph-captured launch, against the plain FP64 SSLBM run scenario by
+    scenario on the same GPU.  The FP64 time is measured on one scenario of each grid size
+    for fp64_steps steps and weighted by the ensemble's size mix; the FP32 error is the
+    root-mean-square difference from FP64 per compartment (density units, total ~1) on the
+    first err_scen scenarios after all steps."""
+    from paper_2603_19789_gb300 import inputs
+    scen = inputs.ensemble_scenarios(n_scen)
+    specs = [dict(nx=s["nx"], ny=s["ny"], rates=s["rates"].as_tuple(), d=s["d"]) for s in scen]
+    ens = L.Ensemble(specs, precision=L.FP32)
+    depth, seg, tune_ms = ens.autotune(trial_blocks=2)
+    for i, s in enumerate(scen):
+        ens.write(i, inputs.ensemble_state(s).astype(np.float32))
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ens.run(steps)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    cells = sum(s["nx"] * s["ny"] for s in scen)
+    # plain FP64 SSLBM, one scenario per grid size
+    per_size = {}
+    for s in scen:
+        if s["nx"] in per_size:
+            continue
+        f = L.Solver(s["nx"], s["ny"], s["rates"].as_tuple(), d=s["d"], bc=L.BC_PERIODIC, precision=L.FP64)
+        f.write(inputs.ensemble_state(s))
+        f.step(4)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f.step(fp64_steps)
+        e1.record(stream)
+        e1.synchronize()
+        per_size[s["nx"]] = e0.elapsed_time(e1) / fp64_steps
+        f.close()
+    fp64_ms = sum(per_size[s["nx"]] * steps for s in scen)
+    # error of the FP32 ensemble against FP64 on a few scenarios
+    rms = np.zeros(5)
+    for i in range(err_scen):
+        s = scen[i]
+        f = L.Solver(s["nx"], s["ny"], s["rates"].as_tuple(), d=s["d"], bc=L.BC_PERIODIC, precision=L.FP64)
+        f.write(inputs.ensemble_state(s))
+        f.step(steps)
+        ref = f.read()
+        f.close()
+        got = ens.read(i)
+        rms = np.maximum(rms, np.sqrt(((got - ref) ** 2).reshape(5, -1).mean(axis=1)))
+    ens.close()
+    del ens
+    torch.cuda.empty_cache()
+    return {"scenarios": n_scen, "steps": steps, "cells": cells, "precision": "fp32",
+            "tiling": {"depth": depth, "seg_rows": seg, "chosen_by": "autotuner"},
+            "launch": "one persistent kernel per run, replayed from a CUDA graph",
+            "ms": ms, "scenario_steps_per_s": n_scen * steps / (ms * 1e-3),
+            "glups": cells * steps / (ms * 1e-3) / 1e9,
+            "fp64_plain_scenario_steps_per_s": n_scen * steps / (fp64_ms * 1e-3),
+            "fp64_plain_note": f"plain FP64 SSLBM per scenario, {fp64_steps} steps timed on one "
+                               "scenario per grid size, weighted by the size mix",
+            "speedup_vs_fp64": fp64_ms / ms,
+            "rms_error_vs_fp64": {"S": rms[0], "E": rms[1], "I": rms[2], "R": rms[3], "D": rms[4],
+                                  "scenarios": err_scen, "units": "density (total ~1)"}}
 
 
 if __name__ == "__main__":

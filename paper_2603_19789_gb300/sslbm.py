@@ -34,10 +34,10 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP
 # every symbol include/sslbm.h declares
 EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspace_bytes",
            "sslbm_create", "sslbm_set_stream", "sslbm_destroy", "sslbm_write", "sslbm_read",
-           "sslbm_step", "bgk_step", "sslbm_steps_done", "sslbm_diagnostics",
-           "sslbm_set_blocking", "sslbm_get_blocking", "sslbm_diagnostics_noalloc",
-           "sslbm_autotune", "sslbm_ensemble_workspace_bytes", "sslbm_ensemble_create",
-           "sslbm_ensemble_destroy", "sslbm_ensemble_set_tiling", "sslbm_ensemble_get_tiling",
+           "sslbm_step", "bgk_step", "sslbm_steps_done", "sslbm_diagnostics", "sslbm_set_blocking",
+           "sslbm_get_blocking", "sslbm_diagnostics_noalloc", "sslbm_autotune",
+           "sslbm_ensemble_workspace_bytes", "sslbm_ensemble_create", "sslbm_ensemble_destroy",
+           "sslbm_ensemble_set_tiling", "sslbm_ensemble_get_tiling",
            "sslbm_ensemble_set_wait_limit", "sslbm_ensemble_write", "sslbm_ensemble_read",
            "sslbm_ensemble_run", "sslbm_ensemble_diagnostics", "sslbm_ensemble_autotune",
            "sslbm_ensemble_steps_done")
@@ -265,11 +265,7 @@ def sslbm_autotune(h, budget_ms: float = 0.0):
     (depth, seg_rows, ms_per_lattice_step)."""
     k, sg, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
     _check(load().sslbm_autotune(h, float(budget_ms), ctypes.byref(k), ctypes.byref(sg), ctypes.byref(ms)),
-           "sslbm_autotune", "sslbm_ensemble_workspace_bytes", "sslbm_ensemble_create",
-           "sslbm_ensemble_destroy", "sslbm_ensemble_set_tiling", "sslbm_ensemble_get_tiling",
-           "sslbm_ensemble_set_wait_limit", "sslbm_ensemble_write", "sslbm_ensemble_read",
-           "sslbm_ensemble_run", "sslbm_ensemble_diagnostics", "sslbm_ensemble_autotune",
-           "sslbm_ensemble_steps_done")
+           "sslbm_autotune")
     return int(k.value), int(sg.value), float(ms.value)
 
 

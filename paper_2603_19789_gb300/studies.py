@@ -1,0 +1,107 @@
+"""Measurement studies built on the library (run on a GPU).
+
+precision  -- the small-increment precision study: the multi-seed no-flux workload at
+              4096 x 4096 with every infected seed at amplitude 1e-6, 50,000 steps, in four
+              storage/arithmetic variants: FP64, FP32, FP32 with S stored as its deviation
+              from the total density, FP32 with compensated (Kahan) accumulation.  Reports,
+              at log-spaced checkpoints, each FP32 variant's per-compartment root-mean-square
+              and max-norm error against the FP64 run, divided by the compartment's peak so
+              far (E and I decay to ~0 after the wave), the relative L2 error of the infected
+              fraction 1 - S, and every variant's drift of the total population (FP64
+              reductions).  The FP64 run is the reference: it matches the CPU oracle to
+              1e-12 relative on the parity workloads, and the oracle itself would need tens of
+              minutes of host time for 50,000 steps of this grid.
+
+Usage:  python -m paper_2603_19789_gb300.studies precision [--n 4096] [--steps 50000]
+        [--checkpoints 5] [--out FILE]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import inputs
+from . import sslbm as L
+
+VARIANTS = (("fp64", L.FP64), ("fp32", L.FP32), ("fp32_dev", L.FP32_DEV), ("fp32_kahan", L.FP32_KAHAN))
+
+
+def precision_study(n: int = 4096, steps: int = 50000, checkpoints: int = 6, seed: int = inputs.DEFAULT_SEED):
+    import torch
+    wl = inputs.precision_workload(n, n, seed)
+    st = wl["state"]
+    total0 = float(st.sum())
+    # log-spaced checkpoints: the take-off (smallest increments) comes first
+    marks = sorted({int(round(steps ** ((i + 1) / checkpoints))) for i in range(checkpoints)} | {steps})
+    solvers = {}
+    for name, prec in VARIANTS:
+        s = L.Solver(n, n, wl["rates"].as_tuple(), d=wl["d"], bc=wl["bc"], precision=prec,
+                     s_ref=1.0)
+        s.write(st)
+        if prec in (L.FP32, L.FP32_DEV):
+            s.autotune(200.0)
+        solvers[name] = s
+    out = {"workload": wl["name"], "n": n, "steps": steps, "seed_amplitude": 1e-6,
+           "reference": "fp64 (GPU)", "checkpoints": []}
+    done = 0
+    peaks = {}
+    timing = {name: 0.0 for name, _ in VARIANTS}
+    for t in marks:
+        rec = {"step": t, "drift": {}, "l2_over_peak": {}, "linf_over_peak": {},
+               "rel_l2_one_minus_S": {}}
+        states = {}
+        for name, _ in VARIANTS:
+            s = solvers[name]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.step(t - done)
+            torch.cuda.synchronize()
+            timing[name] += time.perf_counter() - t0
+            tot, _ = s.diagnostics()
+            rec["drift"][name] = (float(tot.sum()) - total0) / total0
+            states[name] = s.read()
+        ref = states["fp64"]
+        for name, _ in VARIANTS:
+            peaks[name] = np.maximum(peaks.get(name, 0.0), np.abs(ref).reshape(5, -1).max(axis=1))
+        for name, _ in VARIANTS[1:]:
+            diff = (states[name] - ref).reshape(5, -1)
+            # each compartment's error over its peak value so far (E and I decay to ~0)
+            pk = peaks["fp64"]
+            rec["l2_over_peak"][name] = dict(zip("SEIRD", (np.sqrt((diff ** 2).mean(axis=1)) / pk).tolist()))
+            rec["linf_over_peak"][name] = dict(zip("SEIRD", (np.abs(diff).max(axis=1) / pk).tolist()))
+            dref = 1.0 - ref[0]
+            da = 1.0 - states[name][0]
+            rec["rel_l2_one_minus_S"][name] = float(np.linalg.norm(da - dref) / np.linalg.norm(dref))
+        out["checkpoints"].append(rec)
+        done = t
+        del states
+    out["glups"] = {name: n * n * steps / timing[name] / 1e9 for name, _ in VARIANTS}
+    for s in solvers.values():
+        s.close()
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("study", choices=["precision"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--steps", type=int, default=50000)
+    ap.add_argument("--checkpoints", type=int, default=6)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args(argv)
+    from . import build
+    build.build()
+    res = precision_study(args.n, args.steps, args.checkpoints)
+    text = json.dumps(res, indent=1)
+    if args.out:
+        with open(args.out, "w") as fh:
+            fh.write(text + "\n")
+    print(text)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
