@@ -143,8 +143,9 @@ void sslbm_destroy(sslbm_handle* h);
  * pinned) or the device (src_on_device = 1).  Values are rounded to the solver's
  * precision.  For BGK the populations of the written compartments are set to the
  * equilibrium f_i = w_i rho (Sec. II.B; the initial populations are not stated in
- * the paper).  Resets that scheme's Kahan compensation and, when comp is
- * SSLBM_ALL, its step counter.  Host sources are consumed before the call returns. */
+ * the paper).  FP32_KAHAN keeps the rounding residue of each written value in its
+ * compensation plane, so FP64 input is represented to ~1e-15.  When comp is SSLBM_ALL
+ * the scheme's step counter is reset.  Host sources are consumed before the call returns. */
 int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_dtype,
                 int src_on_device);
 

@@ -14,7 +14,8 @@ dim3 row_grid(const GridView& g, int threads) {
   return dim3((unsigned)((g.nx + threads - 1) / threads), (unsigned)gy);
 }
 
-// plane <- src (contiguous).  dev_S: store s_ref - value.  comp (Kahan) is reset to 0.
+// plane <- src (contiguous).  dev_S: store s_ref - value.  comp (Kahan): the rounding residue
+// of the stored value, so that value - compensation reproduces the input.
 template <typename T, typename U>
 __global__ void plane_write_kernel(const GridView g, const U* __restrict__ src,
                                    T* __restrict__ plane, T* __restrict__ comp, int dev_S,
@@ -24,8 +25,9 @@ __global__ void plane_write_kernel(const GridView g, const U* __restrict__ src,
   for (int64_t y = blockIdx.y; y < g.ny; y += gridDim.y) {
     double v = (double)src[y * g.nx + x];
     if (dev_S) v = s_ref - v;
-    plane[y * g.pitch + x] = (T)v;
-    if (comp) comp[y * g.pitch + x] = T(0);
+    const T hi = (T)v;
+    plane[y * g.pitch + x] = hi;
+    if (comp) comp[y * g.pitch + x] = (T)((double)hi - v);
   }
 }
 

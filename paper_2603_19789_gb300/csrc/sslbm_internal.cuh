@@ -102,6 +102,15 @@ __device__ __forceinline__ T lap5(T c, T l, T r, T u, T d) {
   return fma_rn(T(-4), c, add_rn(add_rn(l, r), add_rn(u, d)));
 }
 
+// The same neighbour sum formed from differences to the centre: for a nearly constant
+// field (S ~ 1) each difference is exact (Sterbenz), so the laplacian keeps full relative
+// accuracy where (l + r) + (u + d) - 4c would lose ~1e-7 absolute.  Used by the
+// compensated (Kahan) variant, whose memory-bound kernel has ALU to spare.
+__device__ __forceinline__ float lap5_diff(float c, float l, float r, float u, float d) {
+  return __fadd_rn(__fadd_rn(__fsub_rn(l, c), __fsub_rn(r, c)),
+                   __fadd_rn(__fsub_rn(u, c), __fsub_rn(d, c)));
+}
+
 // Increments of S, E, I, R, D of one cell over one step (Eq. sslbm_final_clean in
 // reduced form with Eq. sources; Eq. rhoD): d_lattice * lap + Psi dt.
 template <typename T>

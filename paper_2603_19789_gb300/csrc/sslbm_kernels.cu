@@ -44,6 +44,16 @@ struct Vec<float, 4> {
   }
 };
 template <>
+struct Vec<float, 2> {
+  static __device__ __forceinline__ void load(const float* p, float (&v)[2]) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+  static __device__ __forceinline__ void store(float* p, const float (&v)[2]) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  }
+};
+template <>
 struct Vec<double, 2> {
   static __device__ __forceinline__ void load(const double* p, double (&v)[2]) {
     const double2 t = *reinterpret_cast<const double2*>(p);
@@ -86,7 +96,29 @@ __global__ void __launch_bounds__(256) step1_kernel(const GridView g, const Coef
         if (j + 1 < V) {
           if (j + 1 < nvalid) r = c[f][j + 1 < V ? j + 1 : j];
         }
-        lap[f][j] = lap5(c[f][j], l, r, u[j], d[j]);
+        if constexpr (MODE == MODE_KAHAN)
+          lap[f][j] = lap5_diff(c[f][j], l, r, u[j], d[j]);
+        else
+          lap[f][j] = lap5(c[f][j], l, r, u[j], d[j]);
+      }
+      if constexpr (MODE == MODE_KAHAN) {
+        // the represented value is value - compensation: subtract the compensation's laplacian
+        const T* Q = in + (5 + f) * g.plane;
+        T qc[V], qu[V], qd[V];
+        Vec<T, V>::load(Q + rc + x0, qc);
+        Vec<T, V>::load(Q + ru + x0, qu);
+        Vec<T, V>::load(Q + rd + x0, qd);
+        const T QL = Q[rc + xl];
+        const T QR = Q[rc + xr];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          const T l = (j == 0) ? QL : qc[j > 0 ? j - 1 : 0];
+          T r = QR;
+          if (j + 1 < V) {
+            if (j + 1 < nvalid) r = qc[j + 1 < V ? j + 1 : j];
+          }
+          lap[f][j] = sub_rn(lap[f][j], lap5_diff(qc[j], l, r, qu[j], qd[j]));
+        }
       }
     }
     T D[V];
@@ -264,7 +296,8 @@ cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coe
     case SSLBM_FP64: return launch_step1_t<double, 2, MODE_PLAIN>(g, coeffs, in, out, s);
     case SSLBM_FP32: return launch_step1_t<float, 4, MODE_PLAIN>(g, coeffs, in, out, s);
     case SSLBM_FP32_DEV: return launch_step1_t<float, 4, MODE_DEV>(g, coeffs, in, out, s);
-    case SSLBM_FP32_KAHAN: return launch_step1_t<float, 4, MODE_KAHAN>(g, coeffs, in, out, s);
+    // two cells per thread: the compensated update carries twice the state per cell
+    case SSLBM_FP32_KAHAN: return launch_step1_t<float, 2, MODE_KAHAN>(g, coeffs, in, out, s);
     default: return cudaErrorInvalidValue;
   }
 }
