@@ -45,6 +45,31 @@ BYTES_PER_CELL_FP64 = 80
 BGK_BYTES_PER_CELL_FP32 = 168  # 20 populations + D, read and write
 
 
+PIPE_SOURCES = ("paper_2603_19789_gb300/csrc/sslbm_pipe.cuh", "paper_2603_19789_gb300/csrc/sslbm_internal.cuh",
+                "paper_2603_19789_gb300/csrc/sslbm_kernels.cu")
+
+
+def captured_traffic(depth: int, cells: int):
+    """DRAM bytes per launch of the fused kernel at this depth, from the ncu capture summarised
+    in profiles/ (bytes per cell x cells), or None when no capture matches the current sources."""
+    import glob
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for p in PIPE_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    pat = re.compile(r"^TRAFFIC kernel=pipe_kernel K=(\d+) bytes_per_cell_per_launch=([0-9.]+) sources=(\w+)")
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(path) as fh:
+            for line in fh:
+                m = pat.match(line.strip())
+                if m and int(m.group(1)) == depth and m.group(3) == digest:
+                    return float(m.group(2)) * cells
+    return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -222,6 +247,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the ensemble measurement")
+    ap.add_argument("--ens-scenarios", type=int, default=512, help="ensemble size (profiling cases)")
+    ap.add_argument("--ens-steps", type=int, default=5000, help="ensemble steps (profiling cases)")
+    ap.add_argument("--ens-tiling", default="", help="depth,seg_rows instead of the autotuner")
     ap.add_argument("--nx", type=int, default=NX, help="grid width (profiling cases; default 8192)")
     ap.add_argument("--ny", type=int, default=NY, help="grid height (profiling cases; default 8192)")
     args = ap.parse_args()
@@ -281,7 +309,9 @@ def main():
 
     ens = None
     if not args.no_ensemble and rank == 0:
-        ens = ensemble_timing(L, torch, stream)
+        tiling = tuple(int(v) for v in args.ens_tiling.split(",")) if args.ens_tiling else None
+        ens = ensemble_timing(L, torch, stream, n_scen=args.ens_scenarios, steps=args.ens_steps,
+                              tiling=tiling)
 
     e2e = None
     if not args.no_e2e:
@@ -309,7 +339,10 @@ def main():
                              + (" (no flush needed)" if 20 * cells > 129e6 else " (fits in L2)"),
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / hbm, "traffic": captured_traffic(depth, cells),
+                         "traffic_source": "ncu capture in profiles/ scaled by cells (null if the "
+                                           "kernel sources changed since)",
+                         "peak_kind": peak_kind,
                          "kernel": f"pipe_kernel<fp32, K={depth}>" if depth > 1 else "step1_kernel<fp32>",
                          "bytes_per_launch": BYTES_PER_CELL_FP32 * cells,
                          "launch_ms": launch_ms,
@@ -399,7 +432,7 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
     return out
 
 
-def ensemble_timing(L, torch, stream, n_scen=512, steps=5000, err_scen=6, fp64_steps=40):
+def ensemble_timing(L, torch, stream, n_scen=512, steps=5000, err_scen=6, fp64_steps=40, tiling=None):
     """The 512-scenario ensemble (grids 256..1024 squared, periodic, FP32) for 5000 steps in
     one persistent graph-captured launch, against the plain FP64 SSLBM run scenario by
     scenario on the same GPU.  The FP64 time is measured on one scenario of each grid size
@@ -410,7 +443,11 @@ def ensemble_timing(L, torch, stream, n_scen=512, steps=5000, err_scen=6, fp64_s
     scen = inputs.ensemble_scenarios(n_scen)
     specs = [dict(nx=s["nx"], ny=s["ny"], rates=s["rates"].as_tuple(), d=s["d"]) for s in scen]
     ens = L.Ensemble(specs, precision=L.FP32)
-    depth, seg, tune_ms = ens.autotune(trial_blocks=2)
+    if tiling:
+        ens.set_tiling(*tiling)
+        depth, seg = tiling
+    else:
+        depth, seg, _ = ens.autotune(trial_blocks=2)
     for i, s in enumerate(scen):
         ens.write(i, inputs.ensemble_state(s).astype(np.float32))
     torch.cuda.synchronize()
@@ -440,7 +477,7 @@ def ensemble_timing(L, torch, stream, n_scen=512, steps=5000, err_scen=6, fp64_s
     fp64_ms = sum(per_size[s["nx"]] * steps for s in scen)
     # error of the FP32 ensemble against FP64 on a few scenarios
     rms = np.zeros(5)
-    for i in range(err_scen):
+    for i in range(min(err_scen, n_scen)):
         s = scen[i]
         f = L.Solver(s["nx"], s["ny"], s["rates"].as_tuple(), d=s["d"], bc=L.BC_PERIODIC, precision=L.FP64)
         f.write(inputs.ensemble_state(s))
@@ -453,7 +490,7 @@ def ensemble_timing(L, torch, stream, n_scen=512, steps=5000, err_scen=6, fp64_s
     del ens
     torch.cuda.empty_cache()
     return {"scenarios": n_scen, "steps": steps, "cells": cells, "precision": "fp32",
-            "tiling": {"depth": depth, "seg_rows": seg, "chosen_by": "autotuner"},
+            "tiling": {"depth": depth, "seg_rows": seg, "chosen_by": "--ens-tiling" if tiling else "autotuner"},
             "launch": "one persistent kernel per run, replayed from a CUDA graph",
             "ms": ms, "scenario_steps_per_s": n_scen * steps / (ms * 1e-3),
             "glups": cells * steps / (ms * 1e-3) / 1e9,
