@@ -284,6 +284,61 @@ int sslbm_ensemble_autotune(sslbm_ensemble* e, int trial_blocks, int* depth, int
 
 int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e);
 
+/* ---- learned surrogate -------------------------------------------------------------------
+ * Not in the paper.  A Fourier-neural-operator-style network that maps the five SEIRD
+ * fields of a periodic n x n grid (plus two constant channels, (R0 - 2.6)/1.4 and
+ * log10(d) + 2) to the fields 20 SSLBM steps later:
+ *   h0 = A0 x + a0; z_l = K_l(h_{l-1}) + B_l h_{l-1} + b_l, h_l = gelu(z_l) (l < L), h_L = z_L;
+ *   y = x[:5] + Q2 gelu(Q1 h_L + q1) + q2,
+ * K_l a spectral convolution on the kx in {0..m-1, n-m..n-1}, ky in {0..m-1} Fourier modes
+ * with complex weights R_l[i][o][kx][ky].  Parameters are one flat FP32 vector in the order
+ * A0[W][7], a0[W], {R_l[W][W][2m][m][2], B_l[W][W], b_l[W]}_{l=1..L}, Q1[H][W], q1[H],
+ * Q2[5][H], q2[5].  Dense contractions run on BF16 tensor cores with FP32 accumulation;
+ * activations are BF16, parameters, gradients and Adam moments FP32.  All tensors passed
+ * in are device pointers, FP32, laid out [batch][channel][n][n]. */
+typedef struct sslbm_fno_config {
+  int32_t n;          /* grid side (periodic), 2 * modes <= n */
+  int32_t width;      /* W: channels of the hidden layers */
+  int32_t modes;      /* m: retained modes per direction (2m x m kept) */
+  int32_t layers;     /* L: spectral layers (<= 16) */
+  int32_t hidden;     /* H: width of the projection */
+  int32_t max_batch;  /* largest batch a call may use (sizes the activations) */
+} sslbm_fno_config;
+
+typedef struct sslbm_fno sslbm_fno;
+
+int sslbm_fno_workspace_bytes(const sslbm_fno_config* c, size_t* bytes);
+int sslbm_fno_create(const sslbm_fno_config* c, void* dev_ws, size_t ws_bytes, void* stream,
+                     sslbm_fno** out);
+void sslbm_fno_destroy(sslbm_fno* f);
+/* Number of parameters (-1 for a NULL handle). */
+int64_t sslbm_fno_num_params(const sslbm_fno* f);
+/* Set (also resets the Adam moments) / get the flat FP32 parameters, host or device memory. */
+int sslbm_fno_set_params(sslbm_fno* f, const float* theta, int on_device);
+int sslbm_fno_get_params(sslbm_fno* f, float* theta, int on_device);
+/* Gradients of the last backward pass (flat, parameter order). */
+int sslbm_fno_get_grads(sslbm_fno* f, float* grad, int on_device);
+/* x[b] (7 channels) from states u[b][5][n][n] and per-scenario R0[b], log10(d)[b]. */
+int sslbm_fno_make_input(sslbm_fno* f, int batch, const float* u, const float* r0,
+                         const float* log10d, float* x);
+/* y[b][5][n][n] = network(x[b]); keeps the activations for a following backward pass. */
+int sslbm_fno_forward(sslbm_fno* f, int batch, const float* x, float* y);
+/* Parameter gradients of a scalar loss with dL/dy = dy, after sslbm_fno_forward on x. */
+int sslbm_fno_backward(sslbm_fno* f, int batch, const float* x, const float* dy);
+/* Adam hyper-parameters (defaults 0.9, 0.999, 1e-8, no weight decay). */
+int sslbm_fno_set_adam(sslbm_fno* f, float beta1, float beta2, float eps, float weight_decay);
+/* One training step on the mean squared error to target: forward, loss, backward, Adam with
+ * learning rate lr.  y_scratch and dy_scratch are [batch][5][n][n] device buffers.  loss
+ * (host, may be NULL) receives the loss before the update; a non-NULL loss synchronises. */
+int sslbm_fno_train_step(sslbm_fno* f, int batch, const float* x, const float* target,
+                         float* y_scratch, float* dy_scratch, float lr, double* loss);
+/* Residual checks of a prediction y against the input state u (both [batch][5][n][n]):
+ * residuals[2b] = |sum y - sum u| / sum u (conservation of the total population),
+ * residuals[2b+1] = sum max(-y, 0) / sum u (mass below zero).  Then y is projected in
+ * place: clamped at zero and rescaled to the input's total.  Synchronises the stream. */
+int sslbm_fno_check_project(sslbm_fno* f, int batch, float* y, const float* u,
+                            double* residuals);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,870 @@
+// fno.cu -- the learned surrogate: a Fourier-neural-operator-style network that advances
+// the five SEIRD fields of a periodic n x n grid by 20 SSLBM steps, with hand-written
+// forward and backward passes, MSE loss and Adam, behind the C ABI of include/sslbm.h.
+// The paper has no learned component; the network is defined by this project:
+//
+//   x  = [S, E, I, R, D, (R0 - 2.6)/1.4, log10(d) + 2]     (7 channels)
+//   h0 = A0 x + a0
+//   z_l = K_l(h_{l-1}) + B_l h_{l-1} + b_l, h_l = gelu(z_l) for l < L, h_L = z_L
+//   p  = gelu(Q1 h_L + q1),  y = x[:5] + Q2 p + q2
+//
+// K_l is the spectral convolution on the 2m x m retained Fourier modes, evaluated as real
+// DFT products: H1 = h Fx (along x), T = Fy H1 (along y), combine to complex, mix with the
+// complex weights R_l, expand, G1 = Fyi U, K(h) = G1 Fxi / n^2.  The DFT products and the
+// channel maps run on BF16 tensor cores with FP32 accumulation (fno_gemm.cu); activations
+// are stored in BF16, parameters, gradients and optimizer moments in FP32, the spectral
+// mixing in FP32 SIMT (it is small).  Parameters are one flat FP32 vector in the order
+// A0, a0, {R_l, B_l, b_l}_{l=1..L}, Q1, q1, Q2, q2.
+#include <cuda_bf16.h>
+#include <float.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+#include <vector>
+
+#include "fno_gemm.cuh"
+#include "sslbm_internal.cuh"
+
+namespace sslbm {
+int record_error(int status, const char* msg);
+}
+
+using sslbm::GemmArgs;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+int err(int status, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  return sslbm::record_error(status, buf);
+}
+
+int cuda_err(cudaError_t e, const char* what) {
+  return err(SSLBM_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(call, what)                            \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_err(e_, what); \
+  } while (0)
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+constexpr int kThreads = 256;
+unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads > 1048576 ? 1048576 : (n + kThreads - 1) / kThreads); }
+
+// ---- elementwise / small kernels ---------------------------------------------------------
+
+// h0[b, o, p] = sum_c A0[o, c] x[b, c, p] + a0[o]
+__global__ void lift_kernel(const float* __restrict__ x, const float* __restrict__ A0,
+                            const float* __restrict__ a0, bf16* __restrict__ h, int B, int W,
+                            int64_t P) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / P, p = t - b * P;
+    float xin[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) xin[c] = x[(b * 7 + c) * P + p];
+    for (int o = 0; o < W; ++o) {
+      float acc = a0[o];
+#pragma unroll
+      for (int c = 0; c < 7; ++c) acc = fmaf(A0[o * 7 + c], xin[c], acc);
+      h[(b * W + o) * P + p] = __float2bfloat16_rn(acc);
+    }
+  }
+}
+
+// z = acc + bias[ch]; optionally store z (bf16) and h = gelu(z) (or h = z) (bf16)
+__global__ void bias_act_kernel(const float* __restrict__ acc, const float* __restrict__ bias,
+                                bf16* __restrict__ zout, bf16* __restrict__ hout, int C, int64_t P,
+                                int64_t total, int act) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int ch = (int)((t / P) % C);
+    const float z = acc[t] + bias[ch];
+    if (zout) zout[t] = __float2bfloat16_rn(z);
+    hout[t] = __float2bfloat16_rn(act ? gelu_f(z) : z);
+  }
+}
+
+// d *= gelu'(z)
+__global__ void gelu_bwd_kernel(float* __restrict__ d, const bf16* __restrict__ z, int64_t total) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x)
+    d[t] *= gelu_grad_f(__bfloat162float(z[t]));
+}
+
+// out[ch] += sum over (b, p) of src[b, ch, p]   (bias gradients)
+__global__ void channel_sum_kernel(const float* __restrict__ src, float* __restrict__ out, int B,
+                                   int C, int64_t P) {
+  const int ch = blockIdx.y;
+  float acc = 0.f;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / P, p = t - b * P;
+    acc += src[(b * C + ch) * P + p];
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  __shared__ float sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.f;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (threadIdx.x == 0) atomicAdd(out + ch, acc);
+  }
+}
+
+// y[b, c, p] += q2[c] + x[b, c, p] (c < 5): residual output
+__global__ void output_kernel(float* __restrict__ y, const float* __restrict__ q2,
+                              const float* __restrict__ x, int B, int64_t P) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * 5 * P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / (5 * P), r = t - b * 5 * P;
+    const int c = (int)(r / P);
+    y[t] += q2[c] + x[b * 7 * P + r];
+  }
+}
+
+// T[(b,i), 2m, 4m] -> hat[(b,i), 2m(kx), m(ky), 2]
+__global__ void combine_kernel(const float* __restrict__ T, float* __restrict__ hat, int BW, int m) {
+  const int64_t total = (int64_t)BW * 2 * m * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t % m), j = (int)((t / m) % (2 * m));
+    const int64_t bi = t / (2 * m * m);
+    const float* Tb = T + bi * (2 * m) * (4 * m);
+    const float re = Tb[(2 * q) * 4 * m + 2 * j] - Tb[(2 * q + 1) * 4 * m + 2 * j + 1];
+    const float im = Tb[(2 * q) * 4 * m + 2 * j + 1] + Tb[(2 * q + 1) * 4 * m + 2 * j];
+    hat[t * 2] = re;
+    hat[t * 2 + 1] = im;
+  }
+}
+
+// hat_g[b, o, j, q] = sum_i hat[b, i, j, q] R[i, o, j, q] (complex), written expanded into
+// U[(b,o), 2m, 4m] with the c_ky weights (c_0 = 1, c_ky = 2)
+__global__ void mix_expand_kernel(const float* __restrict__ hat, const float* __restrict__ R,
+                                  float* __restrict__ U, int B, int W, int m) {
+  const int modes = 2 * m * m;
+  const int64_t total = (int64_t)B * W * modes;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t % modes);
+    const int o = (int)((t / modes) % W);
+    const int64_t b = t / ((int64_t)modes * W);
+    float re = 0.f, im = 0.f;
+    for (int i = 0; i < W; ++i) {
+      const float hr = hat[((b * W + i) * modes + k) * 2], hi = hat[((b * W + i) * modes + k) * 2 + 1];
+      const float rr = R[(((int64_t)i * W + o) * modes + k) * 2], ri = R[(((int64_t)i * W + o) * modes + k) * 2 + 1];
+      re = fmaf(hr, rr, fmaf(-hi, ri, re));
+      im = fmaf(hr, ri, fmaf(hi, rr, im));
+    }
+    const int q = k % m, j = k / m;
+    const float c = q == 0 ? 1.f : 2.f;
+    float* Ub = U + (b * W + o) * (2 * m) * (4 * m);
+    Ub[(2 * q) * 4 * m + 2 * j] = c * re;
+    Ub[(2 * q + 1) * 4 * m + 2 * j] = -c * im;
+    Ub[(2 * q) * 4 * m + 2 * j + 1] = c * im;
+    Ub[(2 * q + 1) * 4 * m + 2 * j + 1] = c * re;
+  }
+}
+
+// adjoint of expand: dU[(b,o), 2m, 4m] -> dG[b, o, j, q, 2]
+__global__ void expand_adj_kernel(const float* __restrict__ dU, float* __restrict__ dG, int BW, int m) {
+  const int modes = 2 * m * m;
+  const int64_t total = (int64_t)BW * modes;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t % modes);
+    const int64_t bo = t / modes;
+    const int q = k % m, j = k / m;
+    const float c = q == 0 ? 1.f : 2.f;
+    const float* D = dU + bo * (2 * m) * (4 * m);
+    const float dre = D[(2 * q) * 4 * m + 2 * j] + D[(2 * q + 1) * 4 * m + 2 * j + 1];
+    const float dim = -D[(2 * q + 1) * 4 * m + 2 * j] + D[(2 * q) * 4 * m + 2 * j + 1];
+    dG[t * 2] = c * dre;
+    dG[t * 2 + 1] = c * dim;
+  }
+}
+
+// dR[i, o, k] += sum_b conj(hat[b, i, k]) dG[b, o, k]
+__global__ void dR_kernel(const float* __restrict__ hat, const float* __restrict__ dG,
+                          float* __restrict__ dR, int B, int W, int m) {
+  const int modes = 2 * m * m;
+  const int64_t total = (int64_t)W * W * modes;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t % modes);
+    const int o = (int)((t / modes) % W);
+    const int i = (int)(t / ((int64_t)modes * W));
+    float re = 0.f, im = 0.f;
+    for (int b = 0; b < B; ++b) {
+      const float hr = hat[(((int64_t)b * W + i) * modes + k) * 2], hi = hat[(((int64_t)b * W + i) * modes + k) * 2 + 1];
+      const float gr = dG[(((int64_t)b * W + o) * modes + k) * 2], gi = dG[(((int64_t)b * W + o) * modes + k) * 2 + 1];
+      re = fmaf(hr, gr, fmaf(hi, gi, re));
+      im = fmaf(hr, gi, fmaf(-hi, gr, im));
+    }
+    dR[t * 2] += re;
+    dR[t * 2 + 1] += im;
+  }
+}
+
+// dhat[b, i, k] = sum_o dG[b, o, k] conj(R[i, o, k]), written as dT (adjoint of combine)
+__global__ void dhat_combine_adj_kernel(const float* __restrict__ dG, const float* __restrict__ R,
+                                        float* __restrict__ dT, int B, int W, int m) {
+  const int modes = 2 * m * m;
+  const int64_t total = (int64_t)B * W * modes;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t % modes);
+    const int i = (int)((t / modes) % W);
+    const int64_t b = t / ((int64_t)modes * W);
+    float re = 0.f, im = 0.f;
+    for (int o = 0; o < W; ++o) {
+      const float gr = dG[((b * W + o) * modes + k) * 2], gi = dG[((b * W + o) * modes + k) * 2 + 1];
+      const float rr = R[(((int64_t)i * W + o) * modes + k) * 2], ri = R[(((int64_t)i * W + o) * modes + k) * 2 + 1];
+      re = fmaf(gr, rr, fmaf(gi, ri, re));
+      im = fmaf(gi, rr, fmaf(-gr, ri, im));
+    }
+    const int q = k % m, j = k / m;
+    float* D = dT + (b * W + i) * (2 * m) * (4 * m);
+    D[(2 * q) * 4 * m + 2 * j] = re;
+    D[(2 * q + 1) * 4 * m + 2 * j + 1] = -re;
+    D[(2 * q) * 4 * m + 2 * j + 1] = im;
+    D[(2 * q + 1) * 4 * m + 2 * j] = im;
+  }
+}
+
+// MSE: dy = 2 (y - t) / N, loss += sum (y - t)^2 / N
+__global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ tgt,
+                           float* __restrict__ dy, double* __restrict__ loss, int64_t N) {
+  double acc = 0.0;
+  const float inv = 1.f / (float)N;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const float d = y[t] - tgt[t];
+    dy[t] = 2.f * d * inv;
+    acc += (double)d * d;
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (double)N);
+}
+
+// Adam (decoupled weight decay), then refresh the BF16 copy used as GEMM operand
+__global__ void adam_kernel(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ mo,
+                            float* __restrict__ ve, bf16* __restrict__ th16, int64_t P, float lr,
+                            float b1, float b2, float eps, float wd, float c1, float c2) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const float gr = g[t];
+    const float m_ = b1 * mo[t] + (1.f - b1) * gr;
+    const float v_ = b2 * ve[t] + (1.f - b2) * gr * gr;
+    mo[t] = m_;
+    ve[t] = v_;
+    const float upd = (m_ / c1) / (sqrtf(v_ / c2) + eps);
+    const float nt = th[t] - lr * (upd + wd * th[t]);
+    th[t] = nt;
+    th16[t] = __float2bfloat16_rn(nt);
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ a, bf16* __restrict__ b, int64_t n) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    b[t] = __float2bfloat16_rn(a[t]);
+}
+
+// real DFT factors (see fno.py's dft_mats): Fx [n][4m], Fy [2m][n], Fyi [n][2m], Fxi [4m][n]
+__global__ void dft_init_kernel(bf16* Fx, bf16* Fy, bf16* Fyi, bf16* Fxi, int n, int m) {
+  const int64_t total = (int64_t)n * 4 * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t / (4 * m)), c = (int)(t % (4 * m));
+    const int j = c >> 1;
+    const int kx = j < m ? j : n - 2 * m + j;
+    double s, co;
+    sincospi(2.0 * (double)((int64_t)kx * x % n) / n, &s, &co);
+    Fx[(int64_t)x * 4 * m + c] = __float2bfloat16_rn((float)((c & 1) ? -s : co));
+    Fxi[(int64_t)c * n + x] = __float2bfloat16_rn((float)((c & 1) ? -s : co));
+    if (c < 2 * m) {
+      const int q = c >> 1;
+      double s2, c2;
+      sincospi(2.0 * (double)((int64_t)q * x % n) / n, &s2, &c2);
+      Fy[(int64_t)c * n + x] = __float2bfloat16_rn((float)((c & 1) ? -s2 : c2));
+      Fyi[(int64_t)x * 2 * m + c] = __float2bfloat16_rn((float)((c & 1) ? s2 : c2));
+    }
+  }
+}
+
+// x[b] = [u (5 planes), (R0 - 2.6)/1.4, log10(d) + 2] from u[b, 5, P] and per-scenario params
+__global__ void make_input_kernel(const float* __restrict__ u, const float* __restrict__ r0,
+                                  const float* __restrict__ logd, float* __restrict__ x, int B,
+                                  int64_t P) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * 7 * P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / (7 * P), r = t - b * 7 * P;
+    const int c = (int)(r / P);
+    x[t] = c < 5 ? u[b * 5 * P + r] : (c == 5 ? (r0[b] - 2.6f) / 1.4f : logd[b] + 2.f);
+  }
+}
+
+// per scenario: totals of the raw prediction and of the input state, and the mass clipped
+// below zero -> res[b] = {sum y, sum u, sum max(-y, 0)} in double
+__global__ void residual_kernel(const float* __restrict__ y, const float* __restrict__ u,
+                                double* __restrict__ res, int64_t P5) {
+  const int64_t b = blockIdx.y;
+  double sy = 0.0, su = 0.0, sn = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P5;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const float yv = y[b * P5 + t];
+    sy += yv;
+    su += u[b * P5 + t];
+    sn += yv < 0.f ? -yv : 0.f;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    sy += __shfl_down_sync(0xffffffffu, sy, off);
+    su += __shfl_down_sync(0xffffffffu, su, off);
+    sn += __shfl_down_sync(0xffffffffu, sn, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(res + 3 * b, sy);
+    atomicAdd(res + 3 * b + 1, su);
+    atomicAdd(res + 3 * b + 2, sn);
+  }
+}
+
+// accepted predictions: clamp at zero and rescale to the input's total
+__global__ void project_kernel(float* __restrict__ y, const double* __restrict__ res, int64_t P5) {
+  const int64_t b = blockIdx.y;
+  const double pos = res[3 * b] + res[3 * b + 2];  // sum of max(y, 0)
+  const float scale = pos > 0 ? (float)(res[3 * b + 1] / pos) : 1.f;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P5;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const float v = y[b * P5 + t];
+    y[b * P5 + t] = v > 0.f ? v * scale : 0.f;
+  }
+}
+
+// ---- parameter layout ------------------------------------------------------------------
+
+struct Layout {
+  int n, W, m, L, H, maxB;
+  int64_t P;  // cells per plane
+  int64_t nparams;
+  int64_t off_A0, off_a0, off_R[16], off_B[16], off_b[16], off_Q1, off_q1, off_Q2, off_q2;
+};
+
+int make_param_layout(const sslbm_fno_config* c, Layout* L) {
+  if (!c) return err(SSLBM_ERR_BAD_ARG, "config is NULL");
+  if (c->n < 8 || c->width < 1 || c->modes < 1 || c->layers < 1 || c->layers > 16 || c->hidden < 1 ||
+      c->max_batch < 1 || 2 * c->modes > c->n || c->n > 4096 || c->width > 256 || c->hidden > 512)
+    return err(SSLBM_ERR_BAD_ARG, "invalid surrogate configuration (n=%d width=%d modes=%d layers=%d "
+               "hidden=%d max_batch=%d; need 2*modes <= n)", c->n, c->width, c->modes, c->layers,
+               c->hidden, c->max_batch);
+  L->n = c->n; L->W = c->width; L->m = c->modes; L->L = c->layers; L->H = c->hidden; L->maxB = c->max_batch;
+  L->P = (int64_t)c->n * c->n;
+  int64_t o = 0;
+  const int W = L->W, m = L->m;
+  L->off_A0 = o; o += (int64_t)W * 7;
+  L->off_a0 = o; o += W;
+  for (int l = 0; l < L->L; ++l) {
+    L->off_R[l] = o; o += (int64_t)W * W * 2 * m * m * 2;
+    L->off_B[l] = o; o += (int64_t)W * W;
+    L->off_b[l] = o; o += W;
+  }
+  L->off_Q1 = o; o += (int64_t)L->H * W;
+  L->off_q1 = o; o += L->H;
+  L->off_Q2 = o; o += (int64_t)5 * L->H;
+  L->off_q2 = o; o += 5;
+  L->nparams = o;
+  return SSLBM_OK;
+}
+
+struct Buffers {
+  size_t total;
+  size_t theta, theta16, grad, mom, vel, dft, hcat, zcat, zp, p, f32a, f32b, f32p, h1, tt, hat, dg, loss, res;
+};
+
+size_t rup(size_t v) { return (v + 255) / 256 * 256; }
+
+void make_buffers(const Layout& L, Buffers* b) {
+  const size_t P = (size_t)L.P, B = (size_t)L.maxB, W = (size_t)L.W, m = (size_t)L.m, n = (size_t)L.n;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o += rup(bytes); return r; };
+  b->theta = take(L.nparams * 4);
+  b->theta16 = take(L.nparams * 2);
+  b->grad = take(L.nparams * 4);
+  b->mom = take(L.nparams * 4);
+  b->vel = take(L.nparams * 4);
+  b->dft = take((4 * m * n * 2 + 2 * m * n * 2) * 2);
+  b->hcat = take((size_t)(L.L + 1) * B * W * P * 2);       // h_0 .. h_L (bf16)
+  b->zcat = take((size_t)(L.L > 1 ? L.L - 1 : 1) * B * W * P * 2);  // z_1 .. z_{L-1} (bf16)
+  b->zp = take(B * L.H * P * 2);
+  b->p = take(B * L.H * P * 2);
+  b->f32a = take(B * W * P * 4);
+  b->f32b = take(B * W * P * 4);
+  b->f32p = take(B * L.H * P * 4);
+  b->h1 = take(B * W * n * 4 * m * 4);
+  b->tt = take(B * W * 2 * m * 4 * m * 4);
+  b->hat = take((size_t)L.L * B * W * 2 * m * m * 2 * 4);
+  b->dg = take(B * W * 2 * m * m * 2 * 4);
+  b->loss = take(8);
+  b->res = take(B * 3 * 8);
+  b->total = o;
+}
+
+}  // namespace
+
+struct sslbm_fno {
+  Layout L;
+  Buffers bu;
+  char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t adam_t = 0;
+  float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f, wd = 0.f;
+  template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+  float* theta() const { return at<float>(bu.theta); }
+  bf16* theta16() const { return at<bf16>(bu.theta16); }
+  float* grad() const { return at<float>(bu.grad); }
+  bf16* Fx() const { return at<bf16>(bu.dft); }
+  bf16* Fxi() const { return Fx() + (size_t)L.n * 4 * L.m; }
+  bf16* Fy() const { return Fxi() + (size_t)L.n * 4 * L.m; }
+  bf16* Fyi() const { return Fy() + (size_t)L.n * 2 * L.m; }
+  bf16* h(int l, int B) const { return at<bf16>(bu.hcat) + (size_t)l * B * L.W * L.P; }
+  bf16* z(int l, int B) const { return at<bf16>(bu.zcat) + (size_t)(l - 1) * B * L.W * L.P; }
+  float* hat(int l, int B) const { return at<float>(bu.hat) + (size_t)(l - 1) * B * L.W * 2 * L.m * L.m * 2; }
+};
+
+namespace {
+
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DevGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+GemmArgs gemm0() {
+  GemmArgs g{};
+  g.K0 = 0;
+  g.batch = 1;
+  g.splits = 1;
+  g.alpha = 1.f;
+  g.beta = 0.f;
+  return g;
+}
+
+int run(const GemmArgs& g0, cudaStream_t s, const char* what) {
+  GemmArgs g = g0;
+  if (g.K0 == 0) g.K0 = g.K;
+  cudaError_t e = sslbm::gemm_bf16(g, s);
+  if (e != cudaSuccess) return cuda_err(e, what);
+  return SSLBM_OK;
+}
+
+// C[b] (rows x P) = Wt (rows x cin) * src[b] (cin x P) (+ beta C): the per-cell channel map
+int channel_map(const sslbm_fno* f, const bf16* Wt, int rows, int cin, const void* src, int src_bf16,
+                void* C, int c_bf16, float beta, int B, const char* what) {
+  GemmArgs g = gemm0();
+  g.M = rows; g.N = (int)f->L.P; g.K = cin; g.batch = B;
+  g.A = Wt; g.a_bf16 = 1; g.sAb = 0; g.sAm = cin; g.sAk0 = 1;
+  g.B = src; g.b_bf16 = src_bf16; g.sBb = (int64_t)cin * f->L.P; g.sBk0 = f->L.P; g.sBn = 1;
+  g.C = C; g.c_bf16 = c_bf16; g.sCb = (int64_t)rows * f->L.P; g.sCm = f->L.P; g.sCn = 1;
+  g.beta = beta;
+  return run(g, f->stream, what);
+}
+
+// C[b] (rows x P) = Wt^T (rows x cin, Wt stored cin x rows) * src[b] (cin x P) (+ beta C)
+int channel_map_t(const sslbm_fno* f, const bf16* Wt, int rows, int cin, const float* src, float* C,
+                  float beta, int B, const char* what) {
+  GemmArgs g = gemm0();
+  g.M = rows; g.N = (int)f->L.P; g.K = cin; g.batch = B;
+  g.A = Wt; g.a_bf16 = 1; g.sAb = 0; g.sAm = 1; g.sAk0 = rows;
+  g.B = src; g.b_bf16 = 0; g.sBb = (int64_t)cin * f->L.P; g.sBk0 = f->L.P; g.sBn = 1;
+  g.C = C; g.c_bf16 = 0; g.sCb = (int64_t)rows * f->L.P; g.sCm = f->L.P; g.sCn = 1;
+  g.beta = beta;
+  return run(g, f->stream, what);
+}
+
+// dW (rows x cols) += sum_b sum_p d[b](rows x P) * act[b](cols x P)^T  (split-K, atomics)
+int weight_grad(const sslbm_fno* f, const float* d, int rows, const void* act, int act_bf16, int cols,
+                float* dW, int B, const char* what) {
+  GemmArgs g = gemm0();
+  g.M = rows; g.N = cols; g.K = (int)(B * f->L.P); g.K0 = (int)f->L.P; g.batch = 1;
+  g.splits = (int)std::min<int64_t>(2048, std::max<int64_t>(1, g.K / 4096));
+  g.A = d; g.a_bf16 = 0; g.sAm = f->L.P; g.sAk0 = 1; g.sAk1 = (int64_t)rows * f->L.P;
+  g.B = act; g.b_bf16 = act_bf16; g.sBk0 = 1; g.sBk1 = (int64_t)cols * f->L.P; g.sBn = f->L.P;
+  g.C = dW; g.c_bf16 = 0; g.sCm = cols; g.sCn = 1; g.atomic = 1;
+  return run(g, f->stream, what);
+}
+
+int channel_sum(const sslbm_fno* f, const float* src, float* out, int B, int C) {
+  dim3 grid(std::min<int64_t>(256, (B * f->L.P + kThreads - 1) / kThreads), C);
+  channel_sum_kernel<<<grid, kThreads, 0, f->stream>>>(src, out, B, C, f->L.P);
+  CK(cudaGetLastError(), "channel_sum");
+  return SSLBM_OK;
+}
+
+// the spectral convolution of layer l (1-based): out (FP32 [B, W, P]) = K_l(h_{l-1})
+int spectral_fwd(sslbm_fno* f, int l, int B, const bf16* hin, float* out) {
+  const Layout& L = f->L;
+  const int n = L.n, m = L.m, W = L.W, BW = B * W;
+  float* H1 = f->at<float>(f->bu.h1);
+  float* T = f->at<float>(f->bu.tt);
+  const float* R = f->theta() + L.off_R[l - 1];
+  int st;
+  {  // H1[(b,c,y), 4m] = h[(b,c,y), x] Fx[x, 4m]
+    GemmArgs g = gemm0();
+    g.M = BW * n; g.N = 4 * m; g.K = n;
+    g.A = hin; g.a_bf16 = 1; g.sAm = n; g.sAk0 = 1;
+    g.B = f->Fx(); g.b_bf16 = 1; g.sBk0 = 4 * m; g.sBn = 1;
+    g.C = H1; g.sCm = 4 * m; g.sCn = 1;
+    if ((st = run(g, f->stream, "dft x"))) return st;
+  }
+  {  // T[(b,c)] (2m x 4m) = Fy (2m x n) H1[(b,c)] (n x 4m)
+    GemmArgs g = gemm0();
+    g.M = 2 * m; g.N = 4 * m; g.K = n; g.batch = BW;
+    g.A = f->Fy(); g.a_bf16 = 1; g.sAb = 0; g.sAm = n; g.sAk0 = 1;
+    g.B = H1; g.sBb = (int64_t)n * 4 * m; g.sBk0 = 4 * m; g.sBn = 1;
+    g.C = T; g.sCb = 2 * m * 4 * m; g.sCm = 4 * m; g.sCn = 1;
+    if ((st = run(g, f->stream, "dft y"))) return st;
+  }
+  float* hat = f->hat(l, B);
+  combine_kernel<<<blocks_for((int64_t)BW * 2 * m * m), kThreads, 0, f->stream>>>(T, hat, BW, m);
+  CK(cudaGetLastError(), "combine");
+  mix_expand_kernel<<<blocks_for((int64_t)BW * 2 * m * m), kThreads, 0, f->stream>>>(hat, R, T, B, W, m);
+  CK(cudaGetLastError(), "mix");
+  {  // G1[(b,o)] (n x 4m) = Fyi (n x 2m) U[(b,o)] (2m x 4m)   (G1 reuses H1)
+    GemmArgs g = gemm0();
+    g.M = n; g.N = 4 * m; g.K = 2 * m; g.batch = BW;
+    g.A = f->Fyi(); g.a_bf16 = 1; g.sAb = 0; g.sAm = 2 * m; g.sAk0 = 1;
+    g.B = T; g.sBb = 2 * m * 4 * m; g.sBk0 = 4 * m; g.sBn = 1;
+    g.C = H1; g.sCb = (int64_t)n * 4 * m; g.sCm = 4 * m; g.sCn = 1;
+    if ((st = run(g, f->stream, "idft y"))) return st;
+  }
+  {  // out[(b,o,y), x] = G1[(b,o,y), 4m] Fxi[4m, x] / n^2
+    GemmArgs g = gemm0();
+    g.M = BW * n; g.N = n; g.K = 4 * m;
+    g.A = H1; g.sAm = 4 * m; g.sAk0 = 1;
+    g.B = f->Fxi(); g.b_bf16 = 1; g.sBk0 = n; g.sBn = 1;
+    g.C = out; g.sCm = n; g.sCn = 1;
+    g.alpha = 1.f / ((float)n * (float)n);
+    if ((st = run(g, f->stream, "idft x"))) return st;
+  }
+  return SSLBM_OK;
+}
+
+// adjoint of spectral_fwd: dh (FP32 [B, W, P], overwritten) and dR (accumulated)
+int spectral_bwd(sslbm_fno* f, int l, int B, const float* dz, float* dh) {
+  const Layout& L = f->L;
+  const int n = L.n, m = L.m, W = L.W, BW = B * W;
+  float* H1 = f->at<float>(f->bu.h1);
+  float* T = f->at<float>(f->bu.tt);
+  float* dG = f->at<float>(f->bu.dg);
+  const float* R = f->theta() + L.off_R[l - 1];
+  float* dR = f->grad() + L.off_R[l - 1];
+  int st;
+  {  // dG1[(b,o,y), 4m] = dz[(b,o,y), x] Fxi^T[x, 4m] / n^2
+    GemmArgs g = gemm0();
+    g.M = BW * n; g.N = 4 * m; g.K = n;
+    g.A = dz; g.sAm = n; g.sAk0 = 1;
+    g.B = f->Fxi(); g.b_bf16 = 1; g.sBk0 = 1; g.sBn = n;
+    g.C = H1; g.sCm = 4 * m; g.sCn = 1;
+    g.alpha = 1.f / ((float)n * (float)n);
+    if ((st = run(g, f->stream, "idft x adjoint"))) return st;
+  }
+  {  // dU[(b,o)] (2m x 4m) = Fyi^T (2m x n) dG1[(b,o)] (n x 4m)
+    GemmArgs g = gemm0();
+    g.M = 2 * m; g.N = 4 * m; g.K = n; g.batch = BW;
+    g.A = f->Fyi(); g.a_bf16 = 1; g.sAb = 0; g.sAm = 1; g.sAk0 = 2 * m;
+    g.B = H1; g.sBb = (int64_t)n * 4 * m; g.sBk0 = 4 * m; g.sBn = 1;
+    g.C = T; g.sCb = 2 * m * 4 * m; g.sCm = 4 * m; g.sCn = 1;
+    if ((st = run(g, f->stream, "idft y adjoint"))) return st;
+  }
+  expand_adj_kernel<<<blocks_for((int64_t)BW * 2 * m * m), kThreads, 0, f->stream>>>(T, dG, BW, m);
+  CK(cudaGetLastError(), "expand adjoint");
+  dR_kernel<<<blocks_for((int64_t)W * W * 2 * m * m), kThreads, 0, f->stream>>>(f->hat(l, B), dG, dR, B, W, m);
+  CK(cudaGetLastError(), "dR");
+  dhat_combine_adj_kernel<<<blocks_for((int64_t)BW * 2 * m * m), kThreads, 0, f->stream>>>(dG, R, T, B, W, m);
+  CK(cudaGetLastError(), "dhat");
+  {  // dH1[(b,c)] (n x 4m) = Fy^T (n x 2m) dT[(b,c)] (2m x 4m)
+    GemmArgs g = gemm0();
+    g.M = n; g.N = 4 * m; g.K = 2 * m; g.batch = BW;
+    g.A = f->Fy(); g.a_bf16 = 1; g.sAb = 0; g.sAm = 1; g.sAk0 = n;
+    g.B = T; g.sBb = 2 * m * 4 * m; g.sBk0 = 4 * m; g.sBn = 1;
+    g.C = H1; g.sCb = (int64_t)n * 4 * m; g.sCm = 4 * m; g.sCn = 1;
+    if ((st = run(g, f->stream, "dft y adjoint"))) return st;
+  }
+  {  // dh[(b,c,y), x] = dH1[(b,c,y), 4m] Fx^T[4m, x]
+    GemmArgs g = gemm0();
+    g.M = BW * n; g.N = n; g.K = 4 * m;
+    g.A = H1; g.sAm = 4 * m; g.sAk0 = 1;
+    g.B = f->Fx(); g.b_bf16 = 1; g.sBk0 = 1; g.sBn = 4 * m;
+    g.C = dh; g.sCm = n; g.sCn = 1;
+    if ((st = run(g, f->stream, "dft x adjoint"))) return st;
+  }
+  return SSLBM_OK;
+}
+
+int forward_impl(sslbm_fno* f, int B, const float* x, float* y) {
+  const Layout& L = f->L;
+  const int W = L.W;
+  const int64_t P = L.P;
+  float* acc = f->at<float>(f->bu.f32a);
+  int st;
+  lift_kernel<<<blocks_for(B * P), kThreads, 0, f->stream>>>(x, f->theta() + L.off_A0, f->theta() + L.off_a0,
+                                                            f->h(0, B), B, W, P);
+  CK(cudaGetLastError(), "lift");
+  for (int l = 1; l <= L.L; ++l) {
+    if ((st = spectral_fwd(f, l, B, f->h(l - 1, B), acc))) return st;
+    if ((st = channel_map(f, f->theta16() + L.off_B[l - 1], W, W, f->h(l - 1, B), 1, acc, 0, 1.f, B,
+                          "pointwise"))) return st;
+    bias_act_kernel<<<blocks_for(B * W * P), kThreads, 0, f->stream>>>(
+        acc, f->theta() + L.off_b[l - 1], l < L.L ? f->z(l, B) : nullptr, f->h(l, B), W, P,
+        (int64_t)B * W * P, l < L.L ? 1 : 0);
+    CK(cudaGetLastError(), "bias/gelu");
+  }
+  float* accp = f->at<float>(f->bu.f32p);
+  if ((st = channel_map(f, f->theta16() + L.off_Q1, L.H, W, f->h(L.L, B), 1, accp, 0, 0.f, B, "projection 1")))
+    return st;
+  bias_act_kernel<<<blocks_for(B * L.H * P), kThreads, 0, f->stream>>>(
+      accp, f->theta() + L.off_q1, f->at<bf16>(f->bu.zp), f->at<bf16>(f->bu.p), L.H, P, (int64_t)B * L.H * P, 1);
+  CK(cudaGetLastError(), "projection gelu");
+  if ((st = channel_map(f, f->theta16() + L.off_Q2, 5, L.H, f->at<bf16>(f->bu.p), 1, y, 0, 0.f, B,
+                        "projection 2"))) return st;
+  output_kernel<<<blocks_for(B * 5 * P), kThreads, 0, f->stream>>>(y, f->theta() + L.off_q2, x, B, P);
+  CK(cudaGetLastError(), "output");
+  return SSLBM_OK;
+}
+
+int backward_impl(sslbm_fno* f, int B, const float* x, const float* dy) {
+  const Layout& L = f->L;
+  const int W = L.W;
+  const int64_t P = L.P;
+  float* g = f->grad();
+  int st;
+  CK(cudaMemsetAsync(g, 0, L.nparams * sizeof(float), f->stream), "zero gradients");
+  if ((st = channel_sum(f, dy, g + L.off_q2, B, 5))) return st;
+  if ((st = weight_grad(f, dy, 5, f->at<bf16>(f->bu.p), 1, L.H, g + L.off_Q2, B, "dQ2"))) return st;
+  float* dp = f->at<float>(f->bu.f32p);
+  if ((st = channel_map_t(f, f->theta16() + L.off_Q2, L.H, 5, dy, dp, 0.f, B, "dp"))) return st;
+  gelu_bwd_kernel<<<blocks_for(B * L.H * P), kThreads, 0, f->stream>>>(dp, f->at<bf16>(f->bu.zp), (int64_t)B * L.H * P);
+  CK(cudaGetLastError(), "gelu' projection");
+  if ((st = channel_sum(f, dp, g + L.off_q1, B, L.H))) return st;
+  if ((st = weight_grad(f, dp, L.H, f->h(L.L, B), 1, W, g + L.off_Q1, B, "dQ1"))) return st;
+  float* dz = f->at<float>(f->bu.f32a);
+  float* dh = f->at<float>(f->bu.f32b);
+  if ((st = channel_map_t(f, f->theta16() + L.off_Q1, W, L.H, dp, dz, 0.f, B, "dh_L"))) return st;
+  for (int l = L.L; l >= 1; --l) {
+    if ((st = channel_sum(f, dz, g + L.off_b[l - 1], B, W))) return st;
+    if ((st = weight_grad(f, dz, W, f->h(l - 1, B), 1, W, g + L.off_B[l - 1], B, "dB"))) return st;
+    if ((st = spectral_bwd(f, l, B, dz, dh))) return st;
+    if ((st = channel_map_t(f, f->theta16() + L.off_B[l - 1], W, W, dz, dh, 1.f, B, "dh pointwise"))) return st;
+    if (l > 1) {
+      gelu_bwd_kernel<<<blocks_for(B * W * P), kThreads, 0, f->stream>>>(dh, f->z(l - 1, B), (int64_t)B * W * P);
+      CK(cudaGetLastError(), "gelu'");
+    }
+    float* t = dz;
+    dz = dh;
+    dh = t;
+  }
+  // lift: dA0 = sum dh0 x^T, da0 = sum dh0
+  if ((st = channel_sum(f, dz, g + L.off_a0, B, W))) return st;
+  if ((st = weight_grad(f, dz, W, x, 0, 7, g + L.off_A0, B, "dA0"))) return st;
+  return SSLBM_OK;
+}
+
+int check_batch(const sslbm_fno* f, int B) {
+  if (!f) return err(SSLBM_ERR_BAD_ARG, "surrogate is NULL");
+  if (B < 1 || B > f->L.maxB) return err(SSLBM_ERR_BAD_ARG, "batch %d not in [1, %d]", B, f->L.maxB);
+  return SSLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sslbm_fno_workspace_bytes(const sslbm_fno_config* c, size_t* bytes) {
+  if (!bytes) return err(SSLBM_ERR_BAD_ARG, "bytes is NULL");
+  Layout L;
+  int st = make_param_layout(c, &L);
+  if (st) return st;
+  Buffers b;
+  make_buffers(L, &b);
+  *bytes = b.total;
+  return SSLBM_OK;
+}
+
+int sslbm_fno_create(const sslbm_fno_config* c, void* dev_ws, size_t ws_bytes, void* stream,
+                     sslbm_fno** out) {
+  if (!out) return err(SSLBM_ERR_BAD_ARG, "out is NULL");
+  *out = nullptr;
+  Layout L;
+  int st = make_param_layout(c, &L);
+  if (st) return st;
+  Buffers bu;
+  make_buffers(L, &bu);
+  if (!dev_ws || reinterpret_cast<uintptr_t>(dev_ws) % 256)
+    return err(SSLBM_ERR_WORKSPACE, "workspace missing or not 256-byte aligned");
+  if (ws_bytes < bu.total) return err(SSLBM_ERR_WORKSPACE, "workspace of %zu bytes < %zu", ws_bytes, bu.total);
+  cudaPointerAttributes attr;
+  CK(cudaPointerGetAttributes(&attr, dev_ws), "cudaPointerGetAttributes");
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return err(SSLBM_ERR_WORKSPACE, "workspace is not device memory");
+  sslbm_fno* f = new (std::nothrow) sslbm_fno();
+  if (!f) return err(SSLBM_ERR_BAD_ARG, "out of host memory");
+  f->L = L;
+  f->bu = bu;
+  f->ws = static_cast<char*>(dev_ws);
+  f->stream = static_cast<cudaStream_t>(stream);
+  f->device = attr.device;
+  DevGuard dg(f->device);
+  cudaError_t e = cudaMemsetAsync(f->ws, 0, bu.total, f->stream);
+  if (e == cudaSuccess) {
+    dft_init_kernel<<<blocks_for((int64_t)L.n * 4 * L.m), kThreads, 0, f->stream>>>(f->Fx(), f->Fy(), f->Fyi(),
+                                                                                   f->Fxi(), L.n, L.m);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    delete f;
+    return cuda_err(e, "surrogate init");
+  }
+  *out = f;
+  return SSLBM_OK;
+}
+
+void sslbm_fno_destroy(sslbm_fno* f) { delete f; }
+
+int64_t sslbm_fno_num_params(const sslbm_fno* f) { return f ? f->L.nparams : -1; }
+
+int sslbm_fno_set_params(sslbm_fno* f, const float* theta, int on_device) {
+  if (!f || !theta) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  DevGuard dg(f->device);
+  CK(cudaMemcpyAsync(f->theta(), theta, f->L.nparams * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     f->stream), "set params");
+  to_bf16_kernel<<<blocks_for(f->L.nparams), kThreads, 0, f->stream>>>(f->theta(), f->theta16(), f->L.nparams);
+  CK(cudaGetLastError(), "params to bf16");
+  CK(cudaMemsetAsync(f->at<float>(f->bu.mom), 0, f->L.nparams * 4, f->stream), "reset moments");
+  CK(cudaMemsetAsync(f->at<float>(f->bu.vel), 0, f->L.nparams * 4, f->stream), "reset moments");
+  f->adam_t = 0;
+  if (!on_device) CK(cudaStreamSynchronize(f->stream), "sync");
+  return SSLBM_OK;
+}
+
+int sslbm_fno_get_params(sslbm_fno* f, float* theta, int on_device) {
+  if (!f || !theta) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  DevGuard dg(f->device);
+  CK(cudaMemcpyAsync(theta, f->theta(), f->L.nparams * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     f->stream), "get params");
+  if (!on_device) CK(cudaStreamSynchronize(f->stream), "sync");
+  return SSLBM_OK;
+}
+
+int sslbm_fno_get_grads(sslbm_fno* f, float* grad, int on_device) {
+  if (!f || !grad) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  DevGuard dg(f->device);
+  CK(cudaMemcpyAsync(grad, f->grad(), f->L.nparams * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     f->stream), "get grads");
+  if (!on_device) CK(cudaStreamSynchronize(f->stream), "sync");
+  return SSLBM_OK;
+}
+
+int sslbm_fno_make_input(sslbm_fno* f, int batch, const float* u, const float* r0, const float* logd, float* x) {
+  int st = check_batch(f, batch);
+  if (st) return st;
+  if (!u || !r0 || !logd || !x) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  DevGuard dg(f->device);
+  make_input_kernel<<<blocks_for(batch * 7 * f->L.P), kThreads, 0, f->stream>>>(u, r0, logd, x, batch, f->L.P);
+  CK(cudaGetLastError(), "make input");
+  return SSLBM_OK;
+}
+
+int sslbm_fno_forward(sslbm_fno* f, int batch, const float* x, float* y) {
+  int st = check_batch(f, batch);
+  if (st) return st;
+  if (!x || !y) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  DevGuard dg(f->device);
+  return forward_impl(f, batch, x, y);
+}
+
+int sslbm_fno_backward(sslbm_fno* f, int batch, const float* x, const float* dy) {
+  int st = check_batch(f, batch);
+  if (st) return st;
+  if (!x || !dy) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  DevGuard dg(f->device);
+  return backward_impl(f, batch, x, dy);
+}
+
+int sslbm_fno_set_adam(sslbm_fno* f, float beta1, float beta2, float eps, float weight_decay) {
+  if (!f) return err(SSLBM_ERR_BAD_ARG, "surrogate is NULL");
+  f->b1 = beta1; f->b2 = beta2; f->eps = eps; f->wd = weight_decay;
+  return SSLBM_OK;
+}
+
+int sslbm_fno_train_step(sslbm_fno* f, int batch, const float* x, const float* target, float* y_scratch,
+                         float* dy_scratch, float lr, double* loss) {
+  int st = check_batch(f, batch);
+  if (st) return st;
+  if (!x || !target || !y_scratch || !dy_scratch) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  DevGuard dg(f->device);
+  if ((st = forward_impl(f, batch, x, y_scratch))) return st;
+  double* dl = f->at<double>(f->bu.loss);
+  CK(cudaMemsetAsync(dl, 0, 8, f->stream), "zero loss");
+  const int64_t N = (int64_t)batch * 5 * f->L.P;
+  mse_kernel<<<blocks_for(N), kThreads, 0, f->stream>>>(y_scratch, target, dy_scratch, dl, N);
+  CK(cudaGetLastError(), "mse");
+  if ((st = backward_impl(f, batch, x, dy_scratch))) return st;
+  f->adam_t += 1;
+  const float c1 = 1.f - powf(f->b1, (float)f->adam_t), c2 = 1.f - powf(f->b2, (float)f->adam_t);
+  adam_kernel<<<blocks_for(f->L.nparams), kThreads, 0, f->stream>>>(
+      f->theta(), f->grad(), f->at<float>(f->bu.mom), f->at<float>(f->bu.vel), f->theta16(), f->L.nparams, lr,
+      f->b1, f->b2, f->eps, f->wd, c1, c2);
+  CK(cudaGetLastError(), "adam");
+  if (loss) {
+    CK(cudaMemcpyAsync(loss, dl, 8, cudaMemcpyDeviceToHost, f->stream), "loss");
+    CK(cudaStreamSynchronize(f->stream), "sync");
+  }
+  return SSLBM_OK;
+}
+
+int sslbm_fno_check_project(sslbm_fno* f, int batch, float* y, const float* u, double* residuals) {
+  int st = check_batch(f, batch);
+  if (st) return st;
+  if (!y || !u || !residuals) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  DevGuard dg(f->device);
+  double* res = f->at<double>(f->bu.res);
+  CK(cudaMemsetAsync(res, 0, (size_t)batch * 3 * 8, f->stream), "zero residuals");
+  const int64_t P5 = 5 * f->L.P;
+  dim3 grid((unsigned)std::min<int64_t>(64, (P5 + kThreads - 1) / kThreads), batch);
+  residual_kernel<<<grid, kThreads, 0, f->stream>>>(y, u, res, P5);
+  CK(cudaGetLastError(), "residual");
+  project_kernel<<<grid, kThreads, 0, f->stream>>>(y, res, P5);
+  CK(cudaGetLastError(), "project");
+  std::vector<double> r((size_t)batch * 3);
+  CK(cudaMemcpyAsync(r.data(), res, r.size() * 8, cudaMemcpyDeviceToHost, f->stream), "residual copy");
+  CK(cudaStreamSynchronize(f->stream), "sync");
+  for (int b = 0; b < batch; ++b) {
+    const double su = r[3 * b + 1];
+    residuals[2 * b] = su != 0 ? std::fabs(r[3 * b] - su) / std::fabs(su) : std::fabs(r[3 * b]);
+    residuals[2 * b + 1] = su != 0 ? r[3 * b + 2] / std::fabs(su) : r[3 * b + 2];
+  }
+  return SSLBM_OK;
+}
+
+}  // extern "C"

@@ -40,7 +40,11 @@ EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspa
            "sslbm_ensemble_set_tiling", "sslbm_ensemble_get_tiling",
            "sslbm_ensemble_set_wait_limit", "sslbm_ensemble_write", "sslbm_ensemble_read",
            "sslbm_ensemble_run", "sslbm_ensemble_diagnostics", "sslbm_ensemble_autotune",
-           "sslbm_ensemble_steps_done")
+           "sslbm_ensemble_steps_done", "sslbm_fno_workspace_bytes", "sslbm_fno_create",
+           "sslbm_fno_destroy", "sslbm_fno_num_params", "sslbm_fno_set_params",
+           "sslbm_fno_get_params", "sslbm_fno_get_grads", "sslbm_fno_make_input",
+           "sslbm_fno_forward", "sslbm_fno_backward", "sslbm_fno_set_adam",
+           "sslbm_fno_train_step", "sslbm_fno_check_project")
 
 
 class SslbmError(RuntimeError):
@@ -60,6 +64,11 @@ class Scenario(ctypes.Structure):
                 ("dt", ctypes.c_double), ("beta", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("phi", ctypes.c_double), ("d", ctypes.c_double * 5),
                 ("s_ref", ctypes.c_double)]
+
+
+class FnoConfig(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("width", ctypes.c_int32), ("modes", ctypes.c_int32),
+                ("layers", ctypes.c_int32), ("hidden", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -118,6 +127,20 @@ def load(path: str = LIB_PATH):
             "sslbm_ensemble_autotune": (i32, [_vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                               ctypes.POINTER(ctypes.c_double)]),
             "sslbm_ensemble_steps_done": (i64, [_vp]),
+            "sslbm_fno_workspace_bytes": (i32, [ctypes.POINTER(FnoConfig), ctypes.POINTER(ctypes.c_size_t)]),
+            "sslbm_fno_create": (i32, [ctypes.POINTER(FnoConfig), _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
+            "sslbm_fno_destroy": (None, [_vp]),
+            "sslbm_fno_num_params": (i64, [_vp]),
+            "sslbm_fno_set_params": (i32, [_vp, _vp, i32]),
+            "sslbm_fno_get_params": (i32, [_vp, _vp, i32]),
+            "sslbm_fno_get_grads": (i32, [_vp, _vp, i32]),
+            "sslbm_fno_make_input": (i32, [_vp, i32, _vp, _vp, _vp, _vp]),
+            "sslbm_fno_forward": (i32, [_vp, i32, _vp, _vp]),
+            "sslbm_fno_backward": (i32, [_vp, i32, _vp, _vp]),
+            "sslbm_fno_set_adam": (i32, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+            "sslbm_fno_train_step": (i32, [_vp, i32, _vp, _vp, _vp, _vp, ctypes.c_float,
+                                           ctypes.POINTER(ctypes.c_double)]),
+            "sslbm_fno_check_project": (i32, [_vp, i32, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
             "sslbm_diagnostics_noalloc": (i32, [_vp, i32, i64, i64, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_double), _vp]),
         }
@@ -477,3 +500,152 @@ class Ensemble:
 
     def autotune(self, trial_blocks=0):
         return sslbm_ensemble_autotune(self.e, trial_blocks)
+
+
+# ---------------------------------------------------------------------------
+# learned surrogate
+# ---------------------------------------------------------------------------
+
+def _dptr(t):
+    """Device pointer of a contiguous float32 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    return _vp(t.data_ptr())
+
+
+def sslbm_fno_workspace_bytes(cfg: FnoConfig) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().sslbm_fno_workspace_bytes(ctypes.byref(cfg), ctypes.byref(n)), "sslbm_fno_workspace_bytes")
+    return int(n.value)
+
+
+def sslbm_fno_create(cfg, ws_ptr, ws_bytes, stream=0):
+    f = _vp()
+    _check(load().sslbm_fno_create(ctypes.byref(cfg), _vp(ws_ptr), int(ws_bytes), _vp(stream), ctypes.byref(f)),
+           "sslbm_fno_create")
+    return f
+
+
+def sslbm_fno_destroy(f):
+    if f:
+        load().sslbm_fno_destroy(f)
+
+
+def sslbm_fno_num_params(f) -> int:
+    return int(load().sslbm_fno_num_params(f))
+
+
+def sslbm_fno_set_params(f, theta):
+    ptr, dev, code, _ = _buffer(theta)
+    if code != DT_F32:
+        raise TypeError("parameters are float32")
+    _check(load().sslbm_fno_set_params(f, _vp(ptr), dev), "sslbm_fno_set_params")
+
+
+def sslbm_fno_get_params(f, out):
+    ptr, dev, code, _ = _buffer(out)
+    _check(load().sslbm_fno_get_params(f, _vp(ptr), dev), "sslbm_fno_get_params")
+    return out
+
+
+def sslbm_fno_get_grads(f, out):
+    ptr, dev, code, _ = _buffer(out)
+    _check(load().sslbm_fno_get_grads(f, _vp(ptr), dev), "sslbm_fno_get_grads")
+    return out
+
+
+def sslbm_fno_make_input(f, batch, u, r0, logd, x):
+    _check(load().sslbm_fno_make_input(f, int(batch), _dptr(u), _dptr(r0), _dptr(logd), _dptr(x)),
+           "sslbm_fno_make_input")
+
+
+def sslbm_fno_forward(f, batch, x, y):
+    _check(load().sslbm_fno_forward(f, int(batch), _dptr(x), _dptr(y)), "sslbm_fno_forward")
+
+
+def sslbm_fno_backward(f, batch, x, dy):
+    _check(load().sslbm_fno_backward(f, int(batch), _dptr(x), _dptr(dy)), "sslbm_fno_backward")
+
+
+def sslbm_fno_set_adam(f, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+    _check(load().sslbm_fno_set_adam(f, beta1, beta2, eps, weight_decay), "sslbm_fno_set_adam")
+
+
+def sslbm_fno_train_step(f, batch, x, target, y_scratch, dy_scratch, lr, want_loss=True):
+    loss = ctypes.c_double(0.0)
+    _check(load().sslbm_fno_train_step(f, int(batch), _dptr(x), _dptr(target), _dptr(y_scratch), _dptr(dy_scratch),
+                                       float(lr), ctypes.byref(loss) if want_loss else None),
+           "sslbm_fno_train_step")
+    return float(loss.value) if want_loss else None
+
+
+def sslbm_fno_check_project(f, batch, y, u):
+    res = (ctypes.c_double * (2 * batch))()
+    _check(load().sslbm_fno_check_project(f, int(batch), _dptr(y), _dptr(u), res), "sslbm_fno_check_project")
+    return np.array(res[:]).reshape(batch, 2)
+
+
+class Surrogate:
+    """The learned surrogate with a torch-allocated workspace (see include/sslbm.h)."""
+
+    def __init__(self, n=256, width=32, modes=12, layers=4, hidden=64, max_batch=16, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.cfg = FnoConfig(int(n), int(width), int(modes), int(layers), int(hidden), int(max_batch))
+        self.n, self.max_batch = int(n), int(max_batch)
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = sslbm_fno_workspace_bytes(self.cfg)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.f = sslbm_fno_create(self.cfg, self.ws.data_ptr(), nbytes, self.stream.cuda_stream)
+        self.nparams = sslbm_fno_num_params(self.f)
+        shape = (self.max_batch, 5, self.n, self.n)
+        self._y = torch.empty(shape, dtype=torch.float32, device=self.device)
+        self._dy = torch.empty(shape, dtype=torch.float32, device=self.device)
+
+    def close(self):
+        if getattr(self, "f", None):
+            self.stream.synchronize()
+            sslbm_fno_destroy(self.f)
+            self.f = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        sslbm_fno_set_params(self.f, theta)
+
+    def get_params(self):
+        out = np.empty(self.nparams, dtype=np.float32)
+        return sslbm_fno_get_params(self.f, out)
+
+    def get_grads(self):
+        out = np.empty(self.nparams, dtype=np.float32)
+        return sslbm_fno_get_grads(self.f, out)
+
+    def make_input(self, u, r0, logd):
+        B = u.shape[0]
+        x = self.torch.empty((B, 7, self.n, self.n), dtype=self.torch.float32, device=self.device)
+        sslbm_fno_make_input(self.f, B, u, r0, logd, x)
+        return x
+
+    def forward(self, x, y=None):
+        B = x.shape[0]
+        if y is None:
+            y = self.torch.empty((B, 5, self.n, self.n), dtype=self.torch.float32, device=self.device)
+        sslbm_fno_forward(self.f, B, x, y)
+        return y
+
+    def backward(self, x, dy):
+        sslbm_fno_backward(self.f, x.shape[0], x, dy)
+
+    def train_step(self, x, target, lr, want_loss=True):
+        B = x.shape[0]
+        return sslbm_fno_train_step(self.f, B, x, target, self._y[:B], self._dy[:B], lr, want_loss)
+
+    def check_project(self, y, u):
+        return sslbm_fno_check_project(self.f, y.shape[0], y, u)
