@@ -12,8 +12,16 @@ precision  -- the small-increment precision study: the multi-seed no-flux worklo
               1e-12 relative on the parity workloads, and the oracle itself would need tens of
               minutes of host time for 50,000 steps of this grid.
 
+surrogate  -- the learned surrogate end to end on n x n periodic grids (default 256): 2000
+              ensemble trajectories x 10 snapshot pairs (t, t + 20), Adam training with the
+              library's forward/backward kernels, then a 64-scenario x 100-step rollout with
+              residual checks and SSLBM fallback, judged against the SSLBM run in lock step,
+              and its scenario-steps/s against the plain FP64 SSLBM on the same grid.
+
 Usage:  python -m paper_2603_19789_gb300.studies precision [--n 4096] [--steps 50000]
         [--checkpoints 5] [--out FILE]
+        python -m paper_2603_19789_gb300.studies surrogate [--n 256] [--trajectories 2000]
+        [--train-steps 3000] [--out FILE]
 """
 from __future__ import annotations
 
@@ -85,17 +93,53 @@ def precision_study(n: int = 4096, steps: int = 50000, checkpoints: int = 6, see
     return out
 
 
+def surrogate_study(n=256, trajectories=2000, snapshots=10, spacing=200, train_steps=3000, batch=16,
+                    lr=1e-3, width=32, modes=12, layers=4, hidden=64, scenarios=64, rollout_steps=100):
+    """Generate trajectories with the ensemble kernel, train the surrogate on the GPU, and
+    roll it out with residual checks and SSLBM fallback, judged against the SSLBM."""
+    import torch
+
+    from . import surrogate as S
+    t0 = time.perf_counter()
+    X, Y, r0, logd = S.generate_pairs(n, trajectories, snapshots, spacing)
+    t_data = time.perf_counter() - t0
+    sur = L.Surrogate(n=n, width=width, modes=modes, layers=layers, hidden=hidden,
+                      max_batch=max(batch, scenarios))
+    sur.set_params(S.initial_params(width, modes, layers, hidden))
+    hist = S.train(sur, X, Y, r0, logd, steps=train_steps, batch=batch, lr=lr)
+    del X, Y
+    torch.cuda.empty_cache()
+    roll = S.rollout(sur, n=n, scenarios=scenarios, steps=rollout_steps)
+    roll.pop("state")
+    roll.pop("reference_state")
+    fp64 = S.fp64_scenario_steps_per_s(n)
+    return {"n": n, "trajectories": trajectories, "pairs": trajectories * snapshots,
+            "params": sur.nparams, "data_seconds": t_data, "train": hist, "rollout": roll,
+            "fp64_plain_scenario_steps_per_s": fp64,
+            "speedup_vs_fp64": roll["scenario_steps_per_s"] / fp64}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["precision"])
-    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("study", choices=["precision", "surrogate"])
+    ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--steps", type=int, default=50000)
     ap.add_argument("--checkpoints", type=int, default=6)
+    ap.add_argument("--trajectories", type=int, default=2000)
+    ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     from . import build
     build.build()
-    res = precision_study(args.n, args.steps, args.checkpoints)
+    if args.study == "surrogate":
+        res = surrogate_study(n=args.n or 256, trajectories=args.trajectories, train_steps=args.train_steps)
+        text = json.dumps(res, indent=1)
+        if args.out:
+            with open(args.out, "w") as fh:
+                fh.write(text + "\n")
+        print(text)
+        return
+    res = precision_study(args.n or 4096, args.steps, args.checkpoints)
     text = json.dumps(res, indent=1)
     if args.out:
         with open(args.out, "w") as fh:

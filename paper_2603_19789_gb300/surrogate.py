@@ -1,0 +1,211 @@
+"""Training data, training and rollout of the learned surrogate (host orchestration only:
+every computation runs in libsslbm's kernels; torch provides device buffers and batch
+gathering).
+
+Data: trajectories of the periodic ensemble workload's parameter ranges (R0 ~ U[1.2, 4],
+d ~ logU[1e-3, 1e-1], 1..8 Gaussian seeds) on n x n grids, produced by the persistent
+ensemble launch; from each trajectory, snapshots at t_j = j * spacing (j = 0..snapshots-1)
+paired with the state 20 steps later.
+
+Rollout: each surrogate step advances a batch of scenarios by 20 SSLBM steps.  The raw
+prediction y is checked against the input state u: the conservation residual
+|sum y - sum u| / sum u and the nonnegativity residual sum max(-y, 0) / sum u.  A scenario
+whose conservation residual exceeds the threshold (1e-4), or whose negative mass exceeds
+neg_threshold (by default the same 1e-4: negatives that the projection below removes
+while moving the state by no more than the conservation tolerance), takes the SSLBM's 20
+steps instead (the fallback, run by the ensemble kernel); accepted predictions are
+projected onto the admissible set (clamped at zero, rescaled to the input's total).  With
+neg_threshold=0 any negative value triggers the fallback.  The rollout also counts the
+scenario-steps with any negative value at all.  The SSLBM also judges the rollout: a
+reference ensemble advanced in lock step gives the error every ten surrogate steps.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import inputs
+from . import sslbm as L
+
+K_STEPS = 20
+
+
+def initial_params(width=32, modes=12, layers=4, hidden=64, seed=0):
+    """Seeded starting point for training, in the flat FP32 parameter order of
+    sslbm_fno_set_params: dense maps uniform in +-1/sqrt(fan_in), spectral weights uniform
+    in +-1/width^2, biases zero."""
+    g = np.random.default_rng(seed)
+    W, m, H = width, modes, hidden
+
+    def dense(rows, cols):
+        b = 1.0 / math.sqrt(cols)
+        return g.uniform(-b, b, rows * cols)
+
+    parts = [dense(W, 7), np.zeros(W)]
+    for _ in range(layers):
+        parts += [g.uniform(-1.0, 1.0, W * W * 2 * m * m * 2) / (W * W), dense(W, W), np.zeros(W)]
+    parts += [dense(H, W), np.zeros(H), dense(5, H), np.zeros(5)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def scenario_specs(count, n, seed):
+    sc = inputs.ensemble_scenarios(count, seed=seed, sizes=(n,))
+    specs = [dict(nx=s["nx"], ny=s["ny"], rates=s["rates"].as_tuple(), d=s["d"]) for s in sc]
+    r0 = np.array([s["R0"] for s in sc], dtype=np.float32)
+    logd = np.array([math.log10(s["d"][0]) for s in sc], dtype=np.float32)
+    return sc, specs, r0, logd
+
+
+def generate_pairs(n=256, trajectories=2000, snapshots=10, spacing=200, seed=7, chunk=500):
+    """Returns device tensors X, Y [pairs, 5, n, n] (float32) and per-pair r0, logd."""
+    import torch
+    sc, specs, r0, logd = scenario_specs(trajectories, n, seed)
+    pairs = trajectories * snapshots
+    X = torch.empty((pairs, 5, n, n), dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(X)
+    pr0 = torch.empty(pairs, dtype=torch.float32, device="cuda")
+    plogd = torch.empty_like(pr0)
+    for c0 in range(0, trajectories, chunk):
+        c1 = min(trajectories, c0 + chunk)
+        ens = L.Ensemble(specs[c0:c1])
+        ens.set_tiling(4, 64)
+        for i in range(c0, c1):
+            ens.write(i - c0, inputs.ensemble_state(sc[i]).astype(np.float32))
+        t = 0
+        for j in range(snapshots):
+            ens.run(j * spacing - t)
+            t = j * spacing
+            for i in range(c0, c1):
+                L.sslbm_ensemble_read(ens.e, i - c0, X[i * snapshots + j])
+            ens.run(K_STEPS)
+            t += K_STEPS
+            for i in range(c0, c1):
+                L.sslbm_ensemble_read(ens.e, i - c0, Y[i * snapshots + j])
+        ens.close()
+        idx = torch.arange(c0 * snapshots, c1 * snapshots, device="cuda")
+        pr0[idx] = torch.from_numpy(np.repeat(r0[c0:c1], snapshots)).cuda()
+        plogd[idx] = torch.from_numpy(np.repeat(logd[c0:c1], snapshots)).cuda()
+    torch.cuda.synchronize()
+    return X, Y, pr0, plogd
+
+
+def train(sur, X, Y, r0, logd, steps=3000, batch=16, lr=1e-3, lr_min=1e-5, seed=0, val_frac=0.05,
+          log_every=500):
+    """Adam on random batches with a cosine learning-rate schedule; returns a history."""
+    import torch
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    pairs = X.shape[0]
+    nval = max(batch, int(pairs * val_frac))
+    perm = torch.randperm(pairs, generator=g)
+    val_idx, tr_idx = perm[:nval], perm[nval:]
+    hist = {"loss": [], "val": []}
+    t0 = time.perf_counter()
+    for it in range(steps):
+        sel = tr_idx[torch.randint(0, tr_idx.numel(), (batch,), generator=g)].cuda()
+        x = sur.make_input(X[sel].contiguous(), r0[sel].contiguous(), logd[sel].contiguous())
+        cur_lr = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * it / max(1, steps)))
+        want = (it % log_every == 0) or it == steps - 1
+        loss = sur.train_step(x, Y[sel].contiguous(), cur_lr, want_loss=want)
+        if want:
+            hist["loss"].append((it, loss))
+    torch.cuda.synchronize()
+    hist["train_seconds"] = time.perf_counter() - t0
+    hist["val_mse"] = evaluate(sur, X, Y, r0, logd, val_idx, batch)
+    # the do-nothing baseline (prediction = input) on the same validation pairs
+    hist["val_mse_persistence"] = float(sum(((X[val_idx[i:i + batch]] - Y[val_idx[i:i + batch]]) ** 2).mean().item()
+                                            * min(batch, nval - i) for i in range(0, nval, batch)) / nval)
+    return hist
+
+
+def evaluate(sur, X, Y, r0, logd, idx, batch):
+    tot, cnt = 0.0, 0
+    for i in range(0, idx.numel(), batch):
+        sel = idx[i:i + batch].cuda()
+        x = sur.make_input(X[sel].contiguous(), r0[sel].contiguous(), logd[sel].contiguous())
+        y = sur.forward(x)
+        tot += float(((y - Y[sel]) ** 2).mean().item()) * sel.numel()
+        cnt += sel.numel()
+    return tot / cnt
+
+
+def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_threshold=1e-4,
+            reference=True, err_every=10):
+    """Surrogate rollout with residual checks and SSLBM fallback.  Returns timings, the
+    fallback count and (with reference=True) the error against an SSLBM run in lock step."""
+    import torch
+    sc, specs, r0, logd = scenario_specs(scenarios, n, seed)
+    u = torch.empty((scenarios, 5, n, n), dtype=torch.float32, device="cuda")
+    for i, s in enumerate(sc):
+        u[i].copy_(torch.from_numpy(inputs.ensemble_state(s).astype(np.float32)))
+    tr0, tlogd = torch.from_numpy(r0).cuda(), torch.from_numpy(logd).cuda()
+    fb = L.Ensemble(specs)          # runs the fallback steps
+    fb.set_tiling(4, 64)
+    ref = L.Ensemble(specs) if reference else None
+    if ref is not None:
+        ref.set_tiling(4, 64)
+        for i in range(scenarios):
+            L.sslbm_ensemble_write(ref.e, i, u[i])
+    total0 = u.double().sum(dim=(1, 2, 3))
+    fallbacks = 0
+    any_negative = 0
+    t_sur = 0.0
+    err_hist = []
+    last_ref = None
+    for step in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = sur.make_input(u, tr0, tlogd)
+        y = sur.forward(x)
+        res = sur.check_project(y, u)
+        any_negative += int((res[:, 1] > 0).sum())
+        bad = np.nonzero((res[:, 0] > threshold) | (res[:, 1] > neg_threshold))[0]
+        if bad.size:
+            fallbacks += int(bad.size)
+            for i in bad:
+                L.sslbm_ensemble_write(fb.e, int(i), u[int(i)])
+            fb.run(K_STEPS)
+            for i in bad:
+                L.sslbm_ensemble_read(fb.e, int(i), y[int(i)])
+        u = y
+        torch.cuda.synchronize()
+        t_sur += time.perf_counter() - t0
+        if ref is not None:
+            ref.run(K_STEPS)
+            if (step + 1) % err_every == 0 or step == steps - 1:
+                r = torch.empty_like(u)
+                for i in range(scenarios):
+                    L.sslbm_ensemble_read(ref.e, i, r[i])
+                d2 = ((u.double() - r.double()) ** 2).sum(dim=(0, 2, 3))
+                rms = (d2 / (scenarios * n * n)).sqrt().cpu().numpy()
+                rel = (d2 / (r.double() ** 2).sum(dim=(0, 2, 3))).sqrt().cpu().numpy()
+                err_hist.append({"step": step + 1, "rms": rms.tolist(), "rel_l2": rel.tolist()})
+                last_ref = r
+    drift = float(((u.double().sum(dim=(1, 2, 3)) - total0).abs() / total0).max())
+    fb.close()
+    if ref is not None:
+        ref.close()
+    return {"scenarios": scenarios, "surrogate_steps": steps, "sslbm_steps_equivalent": steps * K_STEPS,
+            "seconds": t_sur, "scenario_steps_per_s": scenarios * steps * K_STEPS / t_sur,
+            "fallbacks": fallbacks, "fallback_rate": fallbacks / (scenarios * steps),
+            "scenario_steps_with_any_negative": any_negative,
+            "rms_error_vs_sslbm": err_hist, "max_population_drift": drift,
+            "min_value": float(u.min()), "state": u, "reference_state": last_ref}
+
+
+def fp64_scenario_steps_per_s(n=256, steps=40, seed=11):
+    """Plain FP64 SSLBM on one n x n scenario (the baseline the surrogate is compared with)."""
+    import torch
+    sc, specs, _, _ = scenario_specs(1, n, seed)
+    s = L.Solver(n, n, specs[0]["rates"], d=specs[0]["d"], bc=L.BC_PERIODIC, precision=L.FP64)
+    s.write(inputs.ensemble_state(sc[0]))
+    s.step(4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.step(steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    return steps / dt

@@ -3,6 +3,8 @@ host-side validation answers with the documented status codes.  No GPU calls."""
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_2603_19789_gb300 import build as sbuild
@@ -144,3 +146,22 @@ def test_small_workspace(lib):
     p = L.make_params(0.3, 0.2, 0.11, 1 / 11, d=(0.05,) * 4)
     st, _ = _create_status(g, p, ws=0x10000, nbytes=100)
     assert st == -6
+
+
+@pytest.mark.parametrize("cfg", [(32, 12, 4, 64), (16, 8, 2, 32), (8, 4, 2, 12)])
+def test_surrogate_initial_params_follow_the_flat_layout(cfg):
+    """The seeded starting point has one value per parameter, biases zero, spectral
+    weights at the 1/width^2 scale (layout of sslbm_fno_set_params)."""
+    from oracle import fno
+    from paper_2603_19789_gb300 import surrogate as S
+    W, m, Lr, H = cfg
+    th = S.initial_params(W, m, Lr, H, seed=1)
+    assert th.dtype == np.float32 and th.size == fno.n_params(W, m, Lr, H)
+    p = fno.unflatten(th.astype(np.float64), W, m, Lr, H)
+    for name, v in p.items():
+        if name[0] in "abq":
+            assert not v.any(), name
+        elif name[0] == "R":
+            assert 0 < np.abs(v).max() <= 1.0 / (W * W)
+        else:
+            assert 0 < np.abs(v).max() <= 1.0 / np.sqrt(v.shape[1])

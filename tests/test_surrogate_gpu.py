@@ -1,0 +1,95 @@
+"""The learned surrogate end to end on small grids: trajectories generated by the ensemble
+kernel, training by the library's own forward/backward/Adam kernels, and the rollout with
+residual checks and SSLBM fallback, judged by the SSLBM.
+
+What the trained network gains over the method without it: the plain SSLBM needs 20
+lattice steps where the network takes one forward pass.  These tests check the accuracy
+side of that trade on a 64 x 64 configuration (the throughput side is measured at 256 x 256
+by the surrogate study): the trained network predicts the 20-step map far better than the
+do-nothing (persistence) predictor, and its rollout stays nonnegative, conserves the
+population and tracks the SSLBM.  With every check forced to fail the rollout is the SSLBM
+itself, bit for bit.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_19789_gb300 import sslbm as L
+
+pytestmark = pytest.mark.gpu
+
+N = 64
+CFG = dict(width=16, modes=8, layers=2, hidden=32)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_2603_19789_gb300 import build
+    from paper_2603_19789_gb300 import surrogate as S
+    build.build()
+    L.load()
+    X, Y, r0, logd = S.generate_pairs(n=N, trajectories=64, snapshots=6, spacing=120, seed=3, chunk=64)
+    sur = L.Surrogate(n=N, max_batch=16, **CFG)
+    sur.set_params(S.initial_params(CFG["width"], CFG["modes"], CFG["layers"], CFG["hidden"], seed=0))
+    hist0 = S.evaluate(sur, X, Y, r0, logd, _val_idx(X.shape[0]), 8)
+    hist = S.train(sur, X, Y, r0, logd, steps=600, batch=8, lr=2e-3, seed=0)
+    return S, sur, X, Y, r0, logd, hist0, hist
+
+
+def _val_idx(pairs, batch=8, val_frac=0.05, seed=0):
+    import torch
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    nval = max(batch, int(pairs * val_frac))
+    return torch.randperm(pairs, generator=g)[:nval]
+
+
+def test_training_data_are_sslbm_trajectories():
+    """Each pair (X, Y) is 20 steps of the single-scenario SSLBM solver apart."""
+    import torch
+    from paper_2603_19789_gb300 import build, inputs
+    from paper_2603_19789_gb300 import surrogate as S
+    build.build()
+    X, Y, r0, logd = S.generate_pairs(n=N, trajectories=3, snapshots=2, spacing=40, seed=5, chunk=3)
+    sc, specs, _, _ = S.scenario_specs(3, N, 5)
+    for i in range(3):
+        s = L.Solver(N, N, specs[i]["rates"], d=specs[i]["d"], bc=L.BC_PERIODIC, precision=L.FP32)
+        s.write(inputs.ensemble_state(sc[i]).astype(np.float32))
+        s.step(40)
+        np.testing.assert_array_equal(s.read(dtype=np.float32), X[2 * i + 1].cpu().numpy())
+        s.step(20)
+        np.testing.assert_array_equal(s.read(dtype=np.float32), Y[2 * i + 1].cpu().numpy())
+        s.close()
+    assert torch.allclose(r0[::2], torch.from_numpy(np.array([q["R0"] for q in sc], np.float32)).cuda())
+
+
+def test_trained_network_beats_persistence(trained):
+    S, sur, X, Y, r0, logd, mse0, hist = trained
+    # the loss went down during training, and the network learned the 20-step map:
+    # its validation error is well below that of predicting "no change"
+    assert hist["loss"][-1][1] < 0.2 * hist["loss"][0][1], hist["loss"]
+    assert hist["val_mse"] < 0.25 * hist["val_mse_persistence"], hist
+    assert hist["val_mse"] < mse0
+
+
+def test_rollout_conserves_and_tracks_sslbm(trained):
+    S, sur, *_ = trained
+    out = S.rollout(sur, n=N, scenarios=8, steps=10, seed=11, err_every=5)
+    u, ref = out["state"], out["reference_state"]
+    assert out["min_value"] >= 0.0
+    assert out["max_population_drift"] < 1e-4
+    assert np.isfinite(out["rms_error_vs_sslbm"][-1]["rms"]).all()
+    # the rollout tracks the SSLBM better than the initial state does (the do-nothing rollout)
+    sc, _, _, _ = S.scenario_specs(8, N, 11)
+    u0 = np.stack([S.inputs.ensemble_state(s) for s in sc]).astype(np.float32)
+    r = ref.cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(u.cpu().numpy() - r)
+    err_still = np.linalg.norm(u0 - r)
+    assert err < 0.5 * err_still, (err, err_still, out["fallbacks"])
+
+
+def test_forced_fallback_is_the_sslbm(trained):
+    """With the checks forced to fail every step, the rollout is the SSLBM bit for bit."""
+    S, sur, *_ = trained
+    out = S.rollout(sur, n=N, scenarios=4, steps=3, seed=13, threshold=-1.0, err_every=1)
+    assert out["fallbacks"] == 4 * 3
+    np.testing.assert_array_equal(out["state"].cpu().numpy(), out["reference_state"].cpu().numpy())
