@@ -286,16 +286,24 @@ int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e);
 
 /* ---- learned surrogate -------------------------------------------------------------------
  * Not in the paper.  A Fourier-neural-operator-style network that maps the five SEIRD
- * fields of a periodic n x n grid (plus two constant channels, (R0 - 2.6)/1.4 and
- * log10(d) + 2) to the fields 20 SSLBM steps later:
+ * fields of a periodic n x n grid to the fields 20 SSLBM steps later.  With the infection
+ * scale s = max over the grid of (E, I) (at least 1e-12), e = (log10 s + 4)/4 and
+ * s' = 10^(4e - 4), the input has 8 channels
+ *   x = [S, E/s', I/s', R, D, (R0 - 2.6)/1.4, log10(d) + 2, e]
+ * and the network is
  *   h0 = A0 x + a0; z_l = K_l(h_{l-1}) + B_l h_{l-1} + b_l, h_l = gelu(z_l) (l < L), h_L = z_L;
- *   y = x[:5] + Q2 gelu(Q1 h_L + q1) + q2,
+ *   delta = Q2 gelu(Q1 h_L + q1) + q2;  y_c = sigma_c (x_c + delta_c), sigma = (1, s', s', 1, 1),
  * K_l a spectral convolution on the kx in {0..m-1, n-m..n-1}, ky in {0..m-1} Fourier modes
- * with complex weights R_l[i][o][kx][ky].  Parameters are one flat FP32 vector in the order
- * A0[W][7], a0[W], {R_l[W][W][2m][m][2], B_l[W][W], b_l[W]}_{l=1..L}, Q1[H][W], q1[H],
- * Q2[5][H], q2[5].  Dense contractions run on BF16 tensor cores with FP32 accumulation;
- * activations are BF16, parameters, gradients and Adam moments FP32.  All tensors passed
- * in are device pointers, FP32, laid out [batch][channel][n][n]. */
+ * with complex weights R_l[i][o][kx][ky].  E and I enter and leave in units of the
+ * infection scale, so the early exponential phase is the same problem at every amplitude.
+ * Parameters are one flat FP32 vector in the order A0[W][8], a0[W],
+ * {R_l[W][W][2m][m][2], B_l[W][W], b_l[W]}_{l=1..L}, Q1[H][W], q1[H], Q2[5][H], q2[5].
+ * Dense contractions run on BF16 tensor cores with FP32 accumulation; activations are
+ * BF16, parameters, gradients and Adam moments FP32.  For (W, m, H) = (32, 12, 64) or
+ * (16, 8, 32) and n in {64, 128, 256} the forward pass runs as fused per-row kernels
+ * (sslbm_fno_fused() says which); other shapes use one product per contraction.  All
+ * tensors passed in are device pointers, FP32, laid out [batch][channel][n][n], 16-byte
+ * aligned. */
 typedef struct sslbm_fno_config {
   int32_t n;          /* grid side (periodic), 2 * modes <= n */
   int32_t width;      /* W: channels of the hidden layers */
@@ -318,18 +326,32 @@ int sslbm_fno_set_params(sslbm_fno* f, const float* theta, int on_device);
 int sslbm_fno_get_params(sslbm_fno* f, float* theta, int on_device);
 /* Gradients of the last backward pass (flat, parameter order). */
 int sslbm_fno_get_grads(sslbm_fno* f, float* grad, int on_device);
-/* x[b] (7 channels) from states u[b][5][n][n] and per-scenario R0[b], log10(d)[b]. */
+/* x[b] (8 channels, above) from states u[b][5][n][n] and per-scenario R0[b], log10(d)[b]. */
 int sslbm_fno_make_input(sslbm_fno* f, int batch, const float* u, const float* r0,
                          const float* log10d, float* x);
 /* y[b][5][n][n] = network(x[b]); keeps the activations for a following backward pass. */
 int sslbm_fno_forward(sslbm_fno* f, int batch, const float* x, float* y);
-/* Parameter gradients of a scalar loss with dL/dy = dy, after sslbm_fno_forward on x. */
+/* The same y without keeping the activations (the rollout's call; a following backward
+ * pass returns SSLBM_ERR_STATE). */
+int sslbm_fno_infer(sslbm_fno* f, int batch, const float* x, float* y);
+/* 1 when this configuration runs the fused forward kernels, 0 otherwise, < 0 on error. */
+int sslbm_fno_fused(const sslbm_fno* f);
+/* Parameter gradients of a scalar loss with dL/dy = dy, after sslbm_fno_forward on x with
+ * the same batch (SSLBM_ERR_STATE otherwise). */
 int sslbm_fno_backward(sslbm_fno* f, int batch, const float* x, const float* dy);
 /* Adam hyper-parameters (defaults 0.9, 0.999, 1e-8, no weight decay). */
 int sslbm_fno_set_adam(sslbm_fno* f, float beta1, float beta2, float eps, float weight_decay);
-/* One training step on the mean squared error to target: forward, loss, backward, Adam with
- * learning rate lr.  y_scratch and dy_scratch are [batch][5][n][n] device buffers.  loss
- * (host, may be NULL) receives the loss before the update; a non-NULL loss synchronises. */
+/* Weights (>= 0, default 0) of the two residual terms of the training loss:
+ *   loss = mse_w + mass_weight mean_b r_b^2 + neg_weight mean_b n_b^2,
+ *   mse_w = mean of ((y - t) / sigma_c)^2,  r_b = (sum y_b - sum t_b) / sum t_b,
+ *   n_b = sum max(-y_b, 0) / sum t_b,
+ * which teach the network to pass the conservation and nonnegativity checks of
+ * sslbm_fno_check_project. */
+int sslbm_fno_set_loss_weights(sslbm_fno* f, float mass_weight, float neg_weight);
+/* One training step on the loss of sslbm_fno_set_loss_weights: forward, loss, backward,
+ * Adam with learning rate lr.  y_scratch and dy_scratch are [batch][5][n][n] device
+ * buffers.  loss (host, may be NULL) receives mse_w before the update; a non-NULL loss
+ * synchronises. */
 int sslbm_fno_train_step(sslbm_fno* f, int batch, const float* x, const float* target,
                          float* y_scratch, float* dy_scratch, float lr, double* loss);
 /* Residual checks of a prediction y against the input state u (both [batch][5][n][n]):

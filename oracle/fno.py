@@ -8,11 +8,17 @@ to central finite differences (every parameter gradient).  The CUDA kernels are 
 against it.
 
 Network (all per grid cell unless spectral):
-    x  = [S, E, I, R, D, (R0 - 2.6)/1.4, log10(d) + 2]            7 input channels
+    s  = max over the grid of (E, I), at least 1e-12                the infection scale
+    e  = (log10(s) + 4) / 4,  s' = 10^(4 e - 4)                     (s' = s up to rounding)
+    x  = [S, E/s', I/s', R, D, (R0 - 2.6)/1.4, log10(d) + 2, e]    8 input channels
     h0 = A0 x + a0                                                  lift, width W
     z_l = K_l(h_{l-1}) + B_l h_{l-1} + b_l,  h_l = gelu(z_l) (l < L), h_L = z_L
     p  = gelu(Q1 h_L + q1)                                          width H
-    y  = x[:5] + Q2 p + q2                                          state 20 steps ahead
+    delta = Q2 p + q2
+    y_c = sigma_c (x_c + delta_c), sigma = (1, s', s', 1, 1)        state 20 steps ahead
+E and I enter and leave in units of the infection scale, so the early exponential phase
+(E, I of order 1e-4 on S ~ 1) is learned as the scale-free problem it is; the loss weighs
+E and I in the same units (weights 1 / sigma_c^2).
 Spectral convolution K on an n x n periodic grid, kept modes kx in {0..m-1} U {n-m..n-1},
 ky in {0..m-1} (2m x m modes), complex weights R[i, o, kx, ky]:
     hat_h[k] = sum_{x,y} h[y, x] exp(-2 pi i (kx x + ky y) / n)
@@ -36,7 +42,8 @@ try:
 except Exception:  # pragma: no cover - scipy is present on every machine this runs on
     _erf = np.vectorize(math.erf)
 
-C_IN, C_OUT = 7, 5
+C_IN, C_OUT = 8, 5
+SCALE_FLOOR = 1e-12
 
 
 def param_shapes(W=32, m=12, L=4, H=64):
@@ -211,13 +218,29 @@ def pointwise(Wt, h, b=None):
 
 
 def make_input(u, R0, logd):
-    """x = [u (5 channels), (R0 - 2.6)/1.4, log10(d) + 2] for u[B, 5, n, n], R0[B], logd[B]."""
+    """x[B, 8, n, n] from u[B, 5, n, n], R0[B], logd[B] (see the module docstring)."""
     B, _, n, _ = u.shape
+    s = np.maximum(np.maximum(u[:, 1].reshape(B, -1).max(axis=1), u[:, 2].reshape(B, -1).max(axis=1)),
+                   SCALE_FLOOR)
+    e = (np.log10(s) + 4.0) / 4.0
+    sp = 10.0 ** (4.0 * e - 4.0)
     x = np.empty((B, C_IN, n, n))
     x[:, :5] = u
+    x[:, 1] /= sp[:, None, None]
+    x[:, 2] /= sp[:, None, None]
     x[:, 5] = ((np.asarray(R0) - 2.6) / 1.4)[:, None, None]
     x[:, 6] = (np.asarray(logd) + 2.0)[:, None, None]
+    x[:, 7] = e[:, None, None]
     return x
+
+
+def out_scale(x):
+    """sigma[B, 5] = (1, s', s', 1, 1) from the scale channel of x."""
+    sp = 10.0 ** (4.0 * x[:, 7, 0, 0] - 4.0)
+    sig = np.ones((x.shape[0], C_OUT))
+    sig[:, 1] = sp
+    sig[:, 2] = sp
+    return sig
 
 
 def forward(params, x, W=32, m=12, L=4, H=64):
@@ -236,7 +259,8 @@ def forward(params, x, W=32, m=12, L=4, H=64):
     zp = pointwise(params["Q1"], h, params["q1"])
     p = gelu(zp)
     cache["zp"], cache["p"] = zp, p
-    y = x[:, :5] + pointwise(params["Q2"], p, params["q2"])
+    sig = out_scale(x)[:, :, None, None]
+    y = sig * (x[:, :5] + pointwise(params["Q2"], p, params["q2"]))
     return y, cache
 
 
@@ -245,6 +269,7 @@ def backward(params, cache, dy, W=32, m=12, L=4, H=64):
     n = dy.shape[-1]
     g = {}
     p = cache["p"]
+    dy = dy * out_scale(cache["x"])[:, :, None, None]      # d/d delta
     g["Q2"] = np.einsum("boyx,biyx->oi", dy, p)
     g["q2"] = dy.sum(axis=(0, 2, 3))
     dp = pointwise(params["Q2"].T, dy)
@@ -269,3 +294,25 @@ def backward(params, cache, dy, W=32, m=12, L=4, H=64):
 def mse(y, target):
     d = y - target
     return float(np.mean(d * d)), 2.0 * d / d.size
+
+
+def loss(y, target, x, mass_weight=0.0, neg_weight=0.0):
+    """The training loss and dL/dy:
+        mse_w = mean over (b, c, cell) of ((y - t) / sigma_c)^2
+        r_b   = (sum y_b - sum t_b) / sum t_b          relative mass residual
+        n_b   = sum max(-y_b, 0) / sum t_b             relative mass below zero
+        L     = mse_w + mass_weight mean_b r_b^2 + neg_weight mean_b n_b^2
+    Returns (mse_w, L, dL/dy)."""
+    B = y.shape[0]
+    sig = out_scale(x)[:, :, None, None]
+    d = y - target
+    mse_w = float(np.mean((d / sig) ** 2))
+    st = target.reshape(B, -1).sum(axis=1)
+    r = d.reshape(B, -1).sum(axis=1) / st
+    neg = np.maximum(-y, 0.0)
+    nb = neg.reshape(B, -1).sum(axis=1) / st
+    total = mse_w + mass_weight * float(np.mean(r ** 2)) + neg_weight * float(np.mean(nb ** 2))
+    dy = 2.0 * d / (sig ** 2 * d.size)
+    dy = dy + (2.0 * mass_weight / B * r / st)[:, None, None, None]
+    dy = dy - (y < 0) * (2.0 * neg_weight / B * nb / st)[:, None, None, None]
+    return mse_w, total, dy

@@ -3,10 +3,12 @@
 // forward and backward passes, MSE loss and Adam, behind the C ABI of include/sslbm.h.
 // The paper has no learned component; the network is defined by this project:
 //
-//   x  = [S, E, I, R, D, (R0 - 2.6)/1.4, log10(d) + 2]     (7 channels)
+//   s  = max(max E, max I, 1e-12) per scenario (the infection scale), e = (log10 s + 4)/4,
+//   s' = 10^(4e - 4);  x = [S, E/s', I/s', R, D, (R0 - 2.6)/1.4, log10(d) + 2, e]   (8 channels)
 //   h0 = A0 x + a0
 //   z_l = K_l(h_{l-1}) + B_l h_{l-1} + b_l, h_l = gelu(z_l) for l < L, h_L = z_L
-//   p  = gelu(Q1 h_L + q1),  y = x[:5] + Q2 p + q2
+//   p  = gelu(Q1 h_L + q1),  delta = Q2 p + q2,  y_c = sigma_c (x_c + delta_c)
+//   with sigma = (1, s', s', 1, 1): E and I enter and leave in units of the infection scale.
 //
 // K_l is the spectral convolution on the 2m x m retained Fourier modes, evaluated as real
 // DFT products: H1 = h Fx (along x), T = Fy H1 (along y), combine to complex, mix with the
@@ -25,6 +27,7 @@
 #include <new>
 #include <vector>
 
+#include "fno_fused.cuh"
 #include "fno_gemm.cuh"
 #include "sslbm_internal.cuh"
 
@@ -62,6 +65,11 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 }
 
 constexpr int kThreads = 256;
+constexpr int kCin = 8;                 // input channels
+constexpr float kScaleFloor = 1e-12f;   // infection scale of a scenario without E and I
+
+// sigma of E and I from the scale channel e of the input: s' = 10^(4e - 4)
+__device__ __forceinline__ float scale_from_e(float e) { return exp10f(4.f * e - 4.f); }
 unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads > 1048576 ? 1048576 : (n + kThreads - 1) / kThreads); }
 
 // ---- elementwise / small kernels ---------------------------------------------------------
@@ -73,13 +81,13 @@ __global__ void lift_kernel(const float* __restrict__ x, const float* __restrict
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * P;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / P, p = t - b * P;
-    float xin[7];
+    float xin[kCin];
 #pragma unroll
-    for (int c = 0; c < 7; ++c) xin[c] = x[(b * 7 + c) * P + p];
+    for (int c = 0; c < kCin; ++c) xin[c] = x[(b * kCin + c) * P + p];
     for (int o = 0; o < W; ++o) {
       float acc = a0[o];
 #pragma unroll
-      for (int c = 0; c < 7; ++c) acc = fmaf(A0[o * 7 + c], xin[c], acc);
+      for (int c = 0; c < kCin; ++c) acc = fmaf(A0[o * kCin + c], xin[c], acc);
       h[(b * W + o) * P + p] = __float2bfloat16_rn(acc);
     }
   }
@@ -126,14 +134,26 @@ __global__ void channel_sum_kernel(const float* __restrict__ src, float* __restr
   }
 }
 
-// y[b, c, p] += q2[c] + x[b, c, p] (c < 5): residual output
+// y[b, c, p] = sigma_c (x[b, c, p] + (y[b, c, p] + q2[c])) with y holding Q2 p on entry
 __global__ void output_kernel(float* __restrict__ y, const float* __restrict__ q2,
                               const float* __restrict__ x, int B, int64_t P) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * 5 * P;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / (5 * P), r = t - b * 5 * P;
     const int c = (int)(r / P);
-    y[t] += q2[c] + x[b * 7 * P + r];
+    const float v = x[b * kCin * P + r] + (y[t] + q2[c]);
+    y[t] = (c == 1 || c == 2) ? scale_from_e(x[(b * kCin + 7) * P]) * v : v;
+  }
+}
+
+// dd = sigma dy: the derivative with respect to delta = Q2 p + q2
+__global__ void scale_dy_kernel(const float* __restrict__ dy, const float* __restrict__ x,
+                                float* __restrict__ dd, int B, int64_t P) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * 5 * P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / (5 * P);
+    const int c = (int)((t - b * 5 * P) / P);
+    dd[t] = (c == 1 || c == 2) ? scale_from_e(x[(b * kCin + 7) * P]) * dy[t] : dy[t];
   }
 }
 
@@ -246,16 +266,56 @@ __global__ void dhat_combine_adj_kernel(const float* __restrict__ dG, const floa
   }
 }
 
-// MSE: dy = 2 (y - t) / N, loss += sum (y - t)^2 / N
-__global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ tgt,
-                           float* __restrict__ dy, double* __restrict__ loss, int64_t N) {
+// per sample: sums[3b] += sum (y - t), sums[3b+1] += sum t, sums[3b+2] += sum max(-y, 0)
+__global__ void loss_sums_kernel(const float* __restrict__ y, const float* __restrict__ tgt,
+                                 double* __restrict__ sums, int64_t P5) {
+  const int64_t b = blockIdx.y;
+  double se = 0.0, st = 0.0, sn = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P5;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const float tv = tgt[b * P5 + t], yv = y[b * P5 + t];
+    se += (double)(yv - tv);
+    st += tv;
+    sn += yv < 0.f ? -(double)yv : 0.0;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    se += __shfl_down_sync(0xffffffffu, se, off);
+    st += __shfl_down_sync(0xffffffffu, st, off);
+    sn += __shfl_down_sync(0xffffffffu, sn, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(sums + 3 * b, se);
+    atomicAdd(sums + 3 * b + 1, st);
+    atomicAdd(sums + 3 * b + 2, sn);
+  }
+}
+
+// The training loss (N = B * 5 * P):
+//   mse_w = (1/N) sum ((y - t) / sigma_c)^2,  r_b = sum(y_b - t_b) / sum t_b,
+//   n_b = sum max(-y_b, 0) / sum t_b,  L = mse_w + lm mean_b r_b^2 + ln mean_b n_b^2;
+// dy = dL/dy; loss receives mse_w.  sums may be NULL when lm = ln = 0.
+__global__ void loss_kernel(const float* __restrict__ y, const float* __restrict__ tgt,
+                            const float* __restrict__ x, float* __restrict__ dy, double* __restrict__ loss,
+                            int64_t N, int64_t P, const double* __restrict__ sums, float lm, float ln, int B) {
   double acc = 0.0;
   const float inv = 1.f / (float)N;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / (5 * P);
+    const int c = (int)((t - b * 5 * P) / P);
     const float d = y[t] - tgt[t];
-    dy[t] = 2.f * d * inv;
-    acc += (double)d * d;
+    const float rs = (c == 1 || c == 2) ? 1.f / scale_from_e(x[(b * kCin + 7) * P]) : 1.f;
+    const float dn = d * rs;
+    float g = 2.f * dn * rs * inv;
+    if (sums) {
+      const double st = sums[3 * b + 1];
+      if (st != 0.0) {
+        g += (float)(2.0 * lm / B * (sums[3 * b] / st) / st);
+        if (y[t] < 0.f) g -= (float)(2.0 * ln / B * (sums[3 * b + 2] / st) / st);
+      }
+    }
+    dy[t] = g;
+    acc += (double)dn * dn;
   }
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
   if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (double)N);
@@ -307,15 +367,34 @@ __global__ void dft_init_kernel(bf16* Fx, bf16* Fy, bf16* Fyi, bf16* Fxi, int n,
   }
 }
 
-// x[b] = [u (5 planes), (R0 - 2.6)/1.4, log10(d) + 2] from u[b, 5, P] and per-scenario params
+// smax[b] = max over the grid of (E, I, 0) as float bits (non-negative floats order as ints)
+__global__ void infection_scale_kernel(const float* __restrict__ u, int* __restrict__ smax, int64_t P) {
+  const int64_t b = blockIdx.y;
+  float mx = 0.f;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * P;
+       t += (int64_t)gridDim.x * blockDim.x)
+    mx = fmaxf(mx, u[(b * 5 + 1) * P + t]);
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(smax + b, __float_as_int(mx));
+}
+
+// x[b] = [S, E/s', I/s', R, D, (R0 - 2.6)/1.4, log10(d) + 2, e]
 __global__ void make_input_kernel(const float* __restrict__ u, const float* __restrict__ r0,
-                                  const float* __restrict__ logd, float* __restrict__ x, int B,
-                                  int64_t P) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * 7 * P;
+                                  const float* __restrict__ logd, const int* __restrict__ smax,
+                                  float* __restrict__ x, int B, int64_t P) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * kCin * P;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = t / (7 * P), r = t - b * 7 * P;
+    const int64_t b = t / (kCin * P), r = t - b * kCin * P;
     const int c = (int)(r / P);
-    x[t] = c < 5 ? u[b * 5 * P + r] : (c == 5 ? (r0[b] - 2.6f) / 1.4f : logd[b] + 2.f);
+    const float e = (log10f(fmaxf(__int_as_float(smax[b]), kScaleFloor)) + 4.f) * 0.25f;
+    float v;
+    if (c < 5) {
+      v = u[b * 5 * P + r];
+      if (c == 1 || c == 2) v = v / scale_from_e(e);
+    } else {
+      v = c == 5 ? (r0[b] - 2.6f) / 1.4f : (c == 6 ? logd[b] + 2.f : e);
+    }
+    x[t] = v;
   }
 }
 
@@ -376,7 +455,7 @@ int make_param_layout(const sslbm_fno_config* c, Layout* L) {
   L->P = (int64_t)c->n * c->n;
   int64_t o = 0;
   const int W = L->W, m = L->m;
-  L->off_A0 = o; o += (int64_t)W * 7;
+  L->off_A0 = o; o += (int64_t)W * kCin;
   L->off_a0 = o; o += W;
   for (int l = 0; l < L->L; ++l) {
     L->off_R[l] = o; o += (int64_t)W * W * 2 * m * m * 2;
@@ -393,7 +472,8 @@ int make_param_layout(const sslbm_fno_config* c, Layout* L) {
 
 struct Buffers {
   size_t total;
-  size_t theta, theta16, grad, mom, vel, dft, hcat, zcat, zp, p, f32a, f32b, f32p, h1, tt, hat, dg, loss, res;
+  size_t theta, theta16, grad, mom, vel, dft, hcat, zcat, zp, p, f32a, f32b, f32p, h1, tt, hat, dg, dd, smax, loss,
+      res;
 };
 
 size_t rup(size_t v) { return (v + 255) / 256 * 256; }
@@ -419,6 +499,8 @@ void make_buffers(const Layout& L, Buffers* b) {
   b->tt = take(B * W * 2 * m * 4 * m * 4);
   b->hat = take((size_t)L.L * B * W * 2 * m * m * 2 * 4);
   b->dg = take(B * W * 2 * m * m * 2 * 4);
+  b->dd = take(B * 5 * P * 4);
+  b->smax = take(B * 4);
   b->loss = take(8);
   b->res = take(B * 3 * 8);
   b->total = o;
@@ -434,6 +516,8 @@ struct sslbm_fno {
   int device = 0;
   int64_t adam_t = 0;
   float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f, wd = 0.f;
+  float mass_weight = 0.f, neg_weight = 0.f;
+  int cached_batch = 0;  // batch whose intermediates the backward pass can use (0: none)
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   float* theta() const { return at<float>(bu.theta); }
   bf16* theta16() const { return at<bf16>(bu.theta16); }
@@ -622,7 +706,8 @@ int spectral_bwd(sslbm_fno* f, int l, int B, const float* dz, float* dh) {
   return SSLBM_OK;
 }
 
-int forward_impl(sslbm_fno* f, int B, const float* x, float* y) {
+// the generic forward pass: one strided tensor-core product per contraction (any shape)
+int forward_generic(sslbm_fno* f, int B, const float* x, float* y) {
   const Layout& L = f->L;
   const int W = L.W;
   const int64_t P = L.P;
@@ -653,13 +738,82 @@ int forward_impl(sslbm_fno* f, int B, const float* x, float* y) {
   return SSLBM_OK;
 }
 
-int backward_impl(sslbm_fno* f, int B, const float* x, const float* dy) {
+// the fused forward pass (fno_fused.cu): 1 + 3L launches; store = write what backward reads
+int forward_fused(sslbm_fno* f, int B, const float* x, float* y, int store) {
+  namespace F = sslbm::fno_fused;
+  const Layout& L = f->L;
+  const int W = L.W, m = L.m, n = L.n, KF = 4 * L.m;
+  if (reinterpret_cast<uintptr_t>(x) % 16 || reinterpret_cast<uintptr_t>(y) % 16)
+    return err(SSLBM_ERR_BAD_ARG, "x and y must be 16-byte aligned");
+  bf16* H1 = f->at<bf16>(f->bu.h1);
+  bf16* G1 = H1 + (size_t)B * n * W * KF;
+  F::RowArgs a{};
+  a.B = B;
+  a.n = n;
+  a.x = x;
+  a.F = f->Fx();
+  a.store = store;
+  a.A0 = f->theta() + L.off_A0;
+  a.a0 = f->theta() + L.off_a0;
+  a.hout = f->h(0, B);
+  a.H1out = H1;
+  CK(F::launch_row(F::ROW_LIFT, W, m, L.H, a, f->stream), "fused lift");
+  for (int l = 1; l <= L.L; ++l) {
+    float* hat = f->hat(l, B);
+    CK(F::launch_dft_y(W, m, B, n, H1, f->Fy(), hat, f->stream), "fused transform along y");
+    CK(F::launch_mix_idft_y(W, m, B, n, hat, f->theta() + L.off_R[l - 1], f->Fyi(), G1, 1.f / ((float)n * (float)n),
+                            f->stream),
+       "fused spectral mix");
+    F::RowArgs r{};
+    r.B = B;
+    r.n = n;
+    r.x = x;
+    r.F = f->Fx();
+    r.store = store;
+    r.hin = f->h(l - 1, B);
+    r.g1 = G1;
+    r.Bl = f->theta16() + L.off_B[l - 1];
+    r.bl = f->theta() + L.off_b[l - 1];
+    r.hout = f->h(l, B);
+    if (l < L.L) {
+      r.zout = f->z(l, B);
+      r.H1out = H1;
+      CK(F::launch_row(F::ROW_MID, W, m, L.H, r, f->stream), "fused layer");
+    } else {
+      r.Q1 = f->theta16() + L.off_Q1;
+      r.q1 = f->theta() + L.off_q1;
+      r.Q2 = f->theta16() + L.off_Q2;
+      r.q2 = f->theta() + L.off_q2;
+      r.zp = f->at<bf16>(f->bu.zp);
+      r.p = f->at<bf16>(f->bu.p);
+      r.y = y;
+      CK(F::launch_row(F::ROW_LAST, W, m, L.H, r, f->stream), "fused last layer");
+    }
+  }
+  return SSLBM_OK;
+}
+
+int forward_impl(sslbm_fno* f, int B, const float* x, float* y, int store) {
+  int st;
+  if (sslbm::fno_fused::supported(f->L.W, f->L.m, f->L.H, f->L.n))
+    st = forward_fused(f, B, x, y, store);
+  else
+    st = forward_generic(f, B, x, y);  // always stores
+  f->cached_batch = st == SSLBM_OK && (store || !sslbm::fno_fused::supported(f->L.W, f->L.m, f->L.H, f->L.n)) ? B : 0;
+  return st;
+}
+
+int backward_impl(sslbm_fno* f, int B, const float* x, const float* dy_out) {
   const Layout& L = f->L;
   const int W = L.W;
   const int64_t P = L.P;
   float* g = f->grad();
   int st;
   CK(cudaMemsetAsync(g, 0, L.nparams * sizeof(float), f->stream), "zero gradients");
+  // seed: the derivative with respect to delta = Q2 p + q2 (y_c = sigma_c (x_c + delta_c))
+  float* dy = f->at<float>(f->bu.dd);
+  scale_dy_kernel<<<blocks_for((int64_t)B * 5 * P), kThreads, 0, f->stream>>>(dy_out, x, dy, B, P);
+  CK(cudaGetLastError(), "output scale");
   if ((st = channel_sum(f, dy, g + L.off_q2, B, 5))) return st;
   if ((st = weight_grad(f, dy, 5, f->at<bf16>(f->bu.p), 1, L.H, g + L.off_Q2, B, "dQ2"))) return st;
   float* dp = f->at<float>(f->bu.f32p);
@@ -686,7 +840,7 @@ int backward_impl(sslbm_fno* f, int B, const float* x, const float* dy) {
   }
   // lift: dA0 = sum dh0 x^T, da0 = sum dh0
   if ((st = channel_sum(f, dz, g + L.off_a0, B, W))) return st;
-  if ((st = weight_grad(f, dz, W, x, 0, 7, g + L.off_A0, B, "dA0"))) return st;
+  if ((st = weight_grad(f, dz, W, x, 0, kCin, g + L.off_A0, B, "dA0"))) return st;
   return SSLBM_OK;
 }
 
@@ -790,7 +944,13 @@ int sslbm_fno_make_input(sslbm_fno* f, int batch, const float* u, const float* r
   if (st) return st;
   if (!u || !r0 || !logd || !x) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
   DevGuard dg(f->device);
-  make_input_kernel<<<blocks_for(batch * 7 * f->L.P), kThreads, 0, f->stream>>>(u, r0, logd, x, batch, f->L.P);
+  int* smax = f->at<int>(f->bu.smax);
+  CK(cudaMemsetAsync(smax, 0, (size_t)batch * 4, f->stream), "zero scale");
+  dim3 grid((unsigned)std::min<int64_t>(64, (2 * f->L.P + kThreads - 1) / kThreads), batch);
+  infection_scale_kernel<<<grid, kThreads, 0, f->stream>>>(u, smax, f->L.P);
+  CK(cudaGetLastError(), "infection scale");
+  make_input_kernel<<<blocks_for((int64_t)batch * kCin * f->L.P), kThreads, 0, f->stream>>>(u, r0, logd, smax, x, batch,
+                                                                                          f->L.P);
   CK(cudaGetLastError(), "make input");
   return SSLBM_OK;
 }
@@ -800,13 +960,28 @@ int sslbm_fno_forward(sslbm_fno* f, int batch, const float* x, float* y) {
   if (st) return st;
   if (!x || !y) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
   DevGuard dg(f->device);
-  return forward_impl(f, batch, x, y);
+  return forward_impl(f, batch, x, y, 1);
+}
+
+int sslbm_fno_infer(sslbm_fno* f, int batch, const float* x, float* y) {
+  int st = check_batch(f, batch);
+  if (st) return st;
+  if (!x || !y) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  DevGuard dg(f->device);
+  return forward_impl(f, batch, x, y, 0);
+}
+
+int sslbm_fno_fused(const sslbm_fno* f) {
+  if (!f) return err(SSLBM_ERR_BAD_ARG, "surrogate is NULL");
+  return sslbm::fno_fused::supported(f->L.W, f->L.m, f->L.H, f->L.n) ? 1 : 0;
 }
 
 int sslbm_fno_backward(sslbm_fno* f, int batch, const float* x, const float* dy) {
   int st = check_batch(f, batch);
   if (st) return st;
   if (!x || !dy) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  if (f->cached_batch != batch)
+    return err(SSLBM_ERR_STATE, "backward needs a preceding sslbm_fno_forward on the same batch");
   DevGuard dg(f->device);
   return backward_impl(f, batch, x, dy);
 }
@@ -817,18 +992,36 @@ int sslbm_fno_set_adam(sslbm_fno* f, float beta1, float beta2, float eps, float 
   return SSLBM_OK;
 }
 
+int sslbm_fno_set_loss_weights(sslbm_fno* f, float mass_weight, float neg_weight) {
+  if (!f) return err(SSLBM_ERR_BAD_ARG, "surrogate is NULL");
+  if (!(mass_weight >= 0.f) || !std::isfinite(mass_weight) || !(neg_weight >= 0.f) || !std::isfinite(neg_weight))
+    return err(SSLBM_ERR_BAD_ARG, "loss weights must be finite and >= 0");
+  f->mass_weight = mass_weight;
+  f->neg_weight = neg_weight;
+  return SSLBM_OK;
+}
+
 int sslbm_fno_train_step(sslbm_fno* f, int batch, const float* x, const float* target, float* y_scratch,
                          float* dy_scratch, float lr, double* loss) {
   int st = check_batch(f, batch);
   if (st) return st;
   if (!x || !target || !y_scratch || !dy_scratch) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
   DevGuard dg(f->device);
-  if ((st = forward_impl(f, batch, x, y_scratch))) return st;
+  if ((st = forward_impl(f, batch, x, y_scratch, 1))) return st;
   double* dl = f->at<double>(f->bu.loss);
   CK(cudaMemsetAsync(dl, 0, 8, f->stream), "zero loss");
-  const int64_t N = (int64_t)batch * 5 * f->L.P;
-  mse_kernel<<<blocks_for(N), kThreads, 0, f->stream>>>(y_scratch, target, dy_scratch, dl, N);
-  CK(cudaGetLastError(), "mse");
+  const int64_t P5 = 5 * f->L.P, N = (int64_t)batch * P5;
+  double* sums = nullptr;
+  if (f->mass_weight != 0.f || f->neg_weight != 0.f) {
+    sums = f->at<double>(f->bu.res);
+    CK(cudaMemsetAsync(sums, 0, (size_t)batch * 3 * 8, f->stream), "zero loss sums");
+    dim3 grid((unsigned)std::min<int64_t>(64, (P5 + kThreads - 1) / kThreads), batch);
+    loss_sums_kernel<<<grid, kThreads, 0, f->stream>>>(y_scratch, target, sums, P5);
+    CK(cudaGetLastError(), "loss sums");
+  }
+  loss_kernel<<<blocks_for(N), kThreads, 0, f->stream>>>(y_scratch, target, x, dy_scratch, dl, N, f->L.P, sums,
+                                                         f->mass_weight, f->neg_weight, batch);
+  CK(cudaGetLastError(), "loss");
   if ((st = backward_impl(f, batch, x, dy_scratch))) return st;
   f->adam_t += 1;
   const float c1 = 1.f - powf(f->b1, (float)f->adam_t), c2 = 1.f - powf(f->b2, (float)f->adam_t);

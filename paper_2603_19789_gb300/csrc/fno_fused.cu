@@ -1,0 +1,671 @@
+// fno_fused.cu -- fused forward kernels of the learned surrogate (see fno_fused.cuh).
+#include <cuda_bf16.h>
+
+#include "fno_fused.cuh"
+
+namespace sslbm {
+namespace fno_fused {
+namespace {
+
+typedef __nv_bfloat162 bf162;
+
+constexpr int kRowThreads = 256;  // 8 warps; warp w owns grid columns [w n/8, (w+1) n/8)
+constexpr int kCin = 8;           // input channels
+
+__device__ __forceinline__ unsigned saddr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void wait_groups() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ldmatrix: four (or two) 8x8 b16 tiles; lane l supplies the address of row l % 8 of tile l / 8
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(saddr(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const bf16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(saddr(p)));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t (&r)[2], const bf16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(saddr(p)));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t (&r)[2], const bf16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(saddr(p)));
+}
+
+__device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The A fragment of a 16 x 16 tile of a row-major [m][k] array with row stride ld (elements)
+__device__ __forceinline__ void load_a(uint32_t (&a)[4], const bf16* base, int ld, int m0, int k0, int lane) {
+  ldsm_x4(a, base + (m0 + (lane & 15)) * ld + k0 + (lane >> 4) * 8);
+}
+// B fragments (k16 x n8) of n tiles n0 and n0 + 8 from a [k][n] array (n contiguous)
+__device__ __forceinline__ void load_b_kn2(uint32_t (&b)[4], const bf16* base, int ld, int k0, int n0, int lane) {
+  ldsm_x4_t(b, base + (k0 + (lane & 15)) * ld + n0 + (lane >> 4) * 8);
+}
+__device__ __forceinline__ void load_b_kn1(uint32_t (&b)[2], const bf16* base, int ld, int k0, int n0, int lane) {
+  ldsm_x2_t(b, base + (k0 + (lane & 15)) * ld + n0);
+}
+// B fragments from an [n][k] array (k contiguous)
+__device__ __forceinline__ void load_b_nk2(uint32_t (&b)[4], const bf16* base, int ld, int k0, int n0, int lane) {
+  ldsm_x4(b, base + (n0 + (lane & 7) + (lane >> 4) * 8) * ld + k0 + ((lane >> 3) & 1) * 8);
+}
+__device__ __forceinline__ void load_b_nk1(uint32_t (&b)[2], const bf16* base, int ld, int k0, int n0, int lane) {
+  ldsm_x2(b, base + (n0 + (lane & 7)) * ld + k0 + ((lane >> 3) & 1) * 8);
+}
+
+// the same GELU as the unfused path
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+
+__device__ __forceinline__ void st_bf2(bf16* p, float a, float b) {
+  *reinterpret_cast<bf162*>(p) = __floats2bfloat162_rn(a, b);
+}
+
+// ---- row kernel -------------------------------------------------------------------------
+
+template <int W, int KF, int H, int NT, int MODE>
+struct RowSmem {
+  static constexpr int n = 64 * NT, SH = n + 8, SF = KF + 8, SB = W + 8, SQ = H + 8;
+  static constexpr bool lift = MODE == ROW_LIFT, last = MODE == ROW_LAST;
+  static constexpr size_t oF = 0;                                             // bf16 [n][SF]
+  static constexpr size_t oBl = oF + (size_t)n * SF * 2;                       // bf16 [W][SB]
+  static constexpr size_t oOut = oBl + (lift ? 0 : (size_t)W * SB * 2);        // bf16 [W][SH]
+  static constexpr size_t oRed = oOut + (size_t)W * SH * 2;                    // f32 [2][W][KF]
+  static constexpr size_t oQ1 = oRed + (last ? 0 : (size_t)2 * W * KF * 4);    // bf16 [H][SB]
+  static constexpr size_t oQ2 = oQ1 + (last ? (size_t)H * SB * 2 : 0);         // bf16 [16][SQ]
+  static constexpr size_t oP = oQ2 + (last ? (size_t)16 * SQ * 2 : 0);         // bf16 [H][SH]
+  static constexpr size_t oA0 = oP + (last ? (size_t)H * SH * 2 : 0);          // f32 [W][12]
+  static constexpr size_t oStage = oA0 + (lift ? (size_t)W * 12 * 4 : 0);
+  // one input row: x (8 planes, FP32) or {h_{l-1} [W][SH], G1 [W][SF]} (BF16)
+  static constexpr size_t stage = lift ? (size_t)kCin * n * 4 : (size_t)W * SH * 2 + (size_t)W * SF * 2;
+  static constexpr size_t bytes = oStage + 2 * stage;
+};
+
+template <int W, int KF, int H, int NT, int MODE>
+__global__ void __launch_bounds__(kRowThreads, MODE == ROW_LAST ? 1 : 2) row_kernel(const RowArgs a) {
+  using S = RowSmem<W, KF, H, NT, MODE>;
+  constexpr int n = S::n, SH = S::SH, SF = S::SF, SB = S::SB, SQ = S::SQ;
+  constexpr int CW = 8 * NT;  // columns per warp
+  constexpr int MT = W / 16;  // 16-row tiles of the channel dimension
+  static_assert(W % 16 == 0 && KF % 16 == 0 && H % 16 == 0, "tile multiples");
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16* sF = reinterpret_cast<bf16*>(smem + S::oF);
+  bf16* sBl = reinterpret_cast<bf16*>(smem + S::oBl);
+  bf16* sOut = reinterpret_cast<bf16*>(smem + S::oOut);
+  float* sRed = reinterpret_cast<float*>(smem + S::oRed);
+  bf16* sQ1 = reinterpret_cast<bf16*>(smem + S::oQ1);
+  bf16* sQ2 = reinterpret_cast<bf16*>(smem + S::oQ2);
+  bf16* sP = reinterpret_cast<bf16*>(smem + S::oP);
+  float* sA0 = reinterpret_cast<float*>(smem + S::oA0);
+  unsigned char* stage0 = smem + S::oStage;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gr = lane >> 2, tg = lane & 3;
+  const int rows = a.B * n;
+
+  // constants, published by the first barrier of the row loop
+  for (int i = tid; i < n * (KF / 8); i += kRowThreads) {
+    const int r = i / (KF / 8), c = i - r * (KF / 8);
+    *reinterpret_cast<uint4*>(sF + r * SF + 8 * c) = *reinterpret_cast<const uint4*>(a.F + (size_t)r * KF + 8 * c);
+  }
+  if (MODE == ROW_LIFT) {
+    // sA0[o][0..7] = A0[o][:], sA0[o][8] = a0[o]
+    for (int i = tid; i < W * 9; i += kRowThreads) {
+      const int o = i / 9, c = i - o * 9;
+      sA0[o * 12 + c] = c < kCin ? a.A0[o * kCin + c] : a.a0[o];
+    }
+  } else {
+    for (int i = tid; i < W * W; i += kRowThreads) sBl[(i / W) * SB + i % W] = a.Bl[i];
+  }
+  if (MODE == ROW_LAST) {
+    for (int i = tid; i < H * W; i += kRowThreads) sQ1[(i / W) * SB + i % W] = a.Q1[i];
+    for (int i = tid; i < 16 * H; i += kRowThreads) {
+      const int r = i / H, c = i - r * H;
+      sQ2[r * SQ + c] = r < 5 ? a.Q2[r * H + c] : __float2bfloat16_rn(0.f);
+    }
+  }
+  float bias[MT][2];
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt) {
+    bias[mt][0] = MODE == ROW_LIFT ? 0.f : a.bl[mt * 16 + gr];
+    bias[mt][1] = MODE == ROW_LIFT ? 0.f : a.bl[mt * 16 + gr + 8];
+  }
+
+  auto issue = [&](int row, int s) {
+    if (row < rows) {
+      const int b = row / n, y = row - b * n;
+      unsigned char* st = stage0 + s * S::stage;
+      if (MODE == ROW_LIFT) {
+        float* dx = reinterpret_cast<float*>(st);
+        for (int i = tid; i < kCin * (n / 4); i += kRowThreads) {
+          const int c = i / (n / 4), j = i - c * (n / 4);
+          cp16(dx + c * n + 4 * j, a.x + (((size_t)b * kCin + c) * n + y) * n + 4 * j);
+        }
+      } else {
+        bf16* dh = reinterpret_cast<bf16*>(st);
+        bf16* dg = dh + W * SH;
+        for (int i = tid; i < W * (n / 8); i += kRowThreads) {
+          const int c = i / (n / 8), j = i - c * (n / 8);
+          cp16(dh + c * SH + 8 * j, a.hin + (((size_t)b * W + c) * n + y) * n + 8 * j);
+        }
+        for (int i = tid; i < W * (KF / 8); i += kRowThreads) {
+          const int c = i / (KF / 8), j = i - c * (KF / 8);
+          cp16(dg + c * SF + 8 * j, a.g1 + (((size_t)b * n + y) * W + c) * KF + 8 * j);
+        }
+      }
+    }
+    commit();  // possibly empty: every thread keeps the same group count
+  };
+
+  int s = 0;
+  issue(blockIdx.x, 0);
+  for (int row = blockIdx.x; row < rows; row += gridDim.x, s ^= 1) {
+    issue(row + gridDim.x, s ^ 1);
+    wait_groups<1>();
+    __syncthreads();
+    const int b = row / n, y = row - b * n;
+    const int x0 = warp * CW;
+    unsigned char* st = stage0 + s * S::stage;
+
+    if (MODE == ROW_LIFT) {
+      // h0 = A0 x + a0 in FP32, one grid column per thread
+      const float* xs = reinterpret_cast<const float*>(st);
+      for (int xx = tid; xx < n; xx += kRowThreads) {
+        float xin[kCin];
+#pragma unroll
+        for (int c = 0; c < kCin; ++c) xin[c] = xs[c * n + xx];
+        for (int o = 0; o < W; ++o) {
+          float acc = sA0[o * 12 + kCin];
+#pragma unroll
+          for (int c = 0; c < kCin; ++c) acc = fmaf(sA0[o * 12 + c], xin[c], acc);
+          sOut[o * SH + xx] = __float2bfloat16_rn(acc);
+        }
+      }
+    } else {
+      // z[o, x] = sum_i B[o, i] h[i, x] + sum_k G1[o, k] Fxi[k, x] + b[o]  (K = W + 4m)
+      const bf16* sh = reinterpret_cast<const bf16*>(st);
+      const bf16* sg = sh + W * SH;
+      float acc[MT][NT][4];
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0.f;
+#pragma unroll
+      for (int k0 = 0; k0 < W; k0 += 16) {
+        uint32_t af[MT][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) load_a(af[mt], sBl, SB, mt * 16, k0, lane);
+#pragma unroll
+        for (int nt = 0; nt < NT; nt += 2) {
+          if (nt + 1 < NT) {
+            uint32_t bf[4];
+            load_b_kn2(bf, sh, SH, k0, x0 + nt * 8, lane);
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+              mma(acc[mt][nt], af[mt], bf[0], bf[1]);
+              mma(acc[mt][nt + 1], af[mt], bf[2], bf[3]);
+            }
+          } else {
+            uint32_t bf[2];
+            load_b_kn1(bf, sh, SH, k0, x0 + nt * 8, lane);
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) mma(acc[mt][nt], af[mt], bf[0], bf[1]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k0 = 0; k0 < KF; k0 += 16) {
+        uint32_t af[MT][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) load_a(af[mt], sg, SF, mt * 16, k0, lane);
+#pragma unroll
+        for (int nt = 0; nt < NT; nt += 2) {
+          if (nt + 1 < NT) {
+            uint32_t bf[4];
+            load_b_nk2(bf, sF, SF, k0, x0 + nt * 8, lane);  // Fxi[k][x] = Fx[x][k]
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+              mma(acc[mt][nt], af[mt], bf[0], bf[1]);
+              mma(acc[mt][nt + 1], af[mt], bf[2], bf[3]);
+            }
+          } else {
+            uint32_t bf[2];
+            load_b_nk1(bf, sF, SF, k0, x0 + nt * 8, lane);
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) mma(acc[mt][nt], af[mt], bf[0], bf[1]);
+          }
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int o = mt * 16 + gr + 8 * h2, xx = x0 + nt * 8 + 2 * tg;
+            float z0 = acc[mt][nt][2 * h2] + bias[mt][h2], z1 = acc[mt][nt][2 * h2 + 1] + bias[mt][h2];
+            if (MODE == ROW_MID) {
+              if (a.store) st_bf2(a.zout + (((size_t)b * W + o) * n + y) * n + xx, z0, z1);
+              z0 = gelu(z0);
+              z1 = gelu(z1);
+            }
+            st_bf2(sOut + o * SH + xx, z0, z1);
+          }
+    }
+    __syncthreads();
+
+    if (MODE != ROW_LAST || a.store) {
+      for (int i = tid; i < W * (n / 8); i += kRowThreads) {
+        const int c = i / (n / 8), j = i - c * (n / 8);
+        *reinterpret_cast<uint4*>(a.hout + (((size_t)b * W + c) * n + y) * n + 8 * j) =
+            *reinterpret_cast<const uint4*>(sOut + c * SH + 8 * j);
+      }
+    }
+
+    if (MODE != ROW_LAST) {
+      // next layer's transform along x: H1[o, k] = sum_x h[o, x] Fx[x, k]; warp = (tile group,
+      // half of x); the two halves meet in shared memory
+      constexpr int T2 = MT * (KF / 8), TPG = T2 / 4;
+      static_assert(T2 % 4 == 0, "tile groups");
+      const int g = warp & 3, kh = warp >> 2;
+      float acc2[TPG][4];
+#pragma unroll
+      for (int u = 0; u < TPG; ++u)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc2[u][r] = 0.f;
+      for (int k0 = kh * (n / 2); k0 < (kh + 1) * (n / 2); k0 += 16) {
+#pragma unroll
+        for (int u = 0; u < TPG; ++u) {
+          const int t = g * TPG + u, mt = t / (KF / 8), nt = t - mt * (KF / 8);
+          uint32_t af[4], bf[2];
+          load_a(af, sOut, SH, mt * 16, k0, lane);
+          load_b_kn1(bf, sF, SF, k0, nt * 8, lane);
+          mma(acc2[u], af, bf[0], bf[1]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < TPG; ++u) {
+        const int t = g * TPG + u, mt = t / (KF / 8), nt = t - mt * (KF / 8);
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int o = mt * 16 + gr + 8 * h2, c = nt * 8 + 2 * tg;
+          sRed[(kh * W + o) * KF + c] = acc2[u][2 * h2];
+          sRed[(kh * W + o) * KF + c + 1] = acc2[u][2 * h2 + 1];
+        }
+      }
+      __syncthreads();
+      bf16* dst = a.H1out + ((size_t)b * n + y) * W * KF;
+      for (int i = tid; i < W * KF / 2; i += kRowThreads)
+        st_bf2(dst + 2 * i, sRed[2 * i] + sRed[W * KF + 2 * i], sRed[2 * i + 1] + sRed[W * KF + 2 * i + 1]);
+    } else {
+      // projection on the warp's own columns: p = gelu(Q1 h_L + q1), y = Q2 p + q2 + x[:5]
+      constexpr int MH = H / 16;
+      float acc3[MH][NT][4];
+#pragma unroll
+      for (int mh = 0; mh < MH; ++mh)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc3[mh][nt][r] = 0.f;
+#pragma unroll
+      for (int k0 = 0; k0 < W; k0 += 16) {
+        uint32_t af[MH][4];
+#pragma unroll
+        for (int mh = 0; mh < MH; ++mh) load_a(af[mh], sQ1, SB, mh * 16, k0, lane);
+#pragma unroll
+        for (int nt = 0; nt < NT; nt += 2) {
+          if (nt + 1 < NT) {
+            uint32_t bf[4];
+            load_b_kn2(bf, sOut, SH, k0, x0 + nt * 8, lane);
+#pragma unroll
+            for (int mh = 0; mh < MH; ++mh) {
+              mma(acc3[mh][nt], af[mh], bf[0], bf[1]);
+              mma(acc3[mh][nt + 1], af[mh], bf[2], bf[3]);
+            }
+          } else {
+            uint32_t bf[2];
+            load_b_kn1(bf, sOut, SH, k0, x0 + nt * 8, lane);
+#pragma unroll
+            for (int mh = 0; mh < MH; ++mh) mma(acc3[mh][nt], af[mh], bf[0], bf[1]);
+          }
+        }
+      }
+#pragma unroll
+      for (int mh = 0; mh < MH; ++mh)
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int hh = mh * 16 + gr + 8 * h2;
+          const float qv = a.q1[hh];
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            const int xx = x0 + nt * 8 + 2 * tg;
+            const float z0 = acc3[mh][nt][2 * h2] + qv, z1 = acc3[mh][nt][2 * h2 + 1] + qv;
+            const size_t off = (((size_t)b * H + hh) * n + y) * n + xx;
+            if (a.store) st_bf2(a.zp + off, z0, z1);
+            const bf162 pv = __floats2bfloat162_rn(gelu(z0), gelu(z1));
+            *reinterpret_cast<bf162*>(sP + hh * SH + xx) = pv;
+            if (a.store) *reinterpret_cast<bf162*>(a.p + off) = pv;
+          }
+        }
+      __syncwarp();
+      float acc4[NT][4];
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc4[nt][r] = 0.f;
+#pragma unroll
+      for (int k0 = 0; k0 < H; k0 += 16) {
+        uint32_t af[4];
+        load_a(af, sQ2, SQ, 0, k0, lane);
+#pragma unroll
+        for (int nt = 0; nt < NT; nt += 2) {
+          if (nt + 1 < NT) {
+            uint32_t bf[4];
+            load_b_kn2(bf, sP, SH, k0, x0 + nt * 8, lane);
+            mma(acc4[nt], af, bf[0], bf[1]);
+            mma(acc4[nt + 1], af, bf[2], bf[3]);
+          } else {
+            uint32_t bf[2];
+            load_b_kn1(bf, sP, SH, k0, x0 + nt * 8, lane);
+            mma(acc4[nt], af, bf[0], bf[1]);
+          }
+        }
+      }
+      if (gr < 5) {
+        // y_c = sigma_c (x_c + delta_c), sigma_E = sigma_I = 10^(4e - 4) from the scale channel
+        const int c = gr;
+        const float qc = a.q2[c];
+        const float sig = (c == 1 || c == 2) ? exp10f(4.f * a.x[((size_t)b * kCin + 7) * n * n] - 4.f) : 1.f;
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const int xx = x0 + nt * 8 + 2 * tg;
+          const float2 xv = *reinterpret_cast<const float2*>(a.x + (((size_t)b * kCin + c) * n + y) * n + xx);
+          float2 out;
+          out.x = xv.x + (acc4[nt][0] + qc);
+          out.y = xv.y + (acc4[nt][1] + qc);
+          if (c == 1 || c == 2) {
+            out.x *= sig;
+            out.y *= sig;
+          }
+          *reinterpret_cast<float2*>(a.y + (((size_t)b * 5 + c) * n + y) * n + xx) = out;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  wait_groups<0>();
+}
+
+// ---- transform along y and combine ---------------------------------------------------------
+
+// CTA = (sample b, CG channels): T[c] = Fy (2m x n) H1[b, :, c, :] (n x 4m), combined into
+// hat[b, c, j, q] = (T[2q, 2j] - T[2q+1, 2j+1], T[2q, 2j+1] + T[2q+1, 2j])
+template <int KF, int CG>
+__global__ void __launch_bounds__(128) dft_y_kernel(const bf16* __restrict__ H1, const bf16* __restrict__ Fy,
+                                                    float* __restrict__ hat, int W, int n) {
+  constexpr int M2 = KF / 2, m = KF / 4, NC = CG * KF, SC = NC + 8, modes = 2 * m * m;
+  constexpr int NTT = NC / 8, TPW = NTT / 4;
+  static_assert(NTT % 4 == 0 && M2 <= 32, "tiling");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int SY = n + 8;
+  bf16* sFy = reinterpret_cast<bf16*>(smem);          // [32][SY], rows >= 2m zero
+  bf16* sT = sFy + 32 * SY;                            // [n][SC]
+  float* sO = reinterpret_cast<float*>(sT + (size_t)n * SC);  // [2m][NC]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gr = lane >> 2, tg = lane & 3;
+  const int b = blockIdx.y, c0 = blockIdx.x * CG;
+  for (int i = tid; i < 32 * (n / 8); i += 128) {
+    const int r = i / (n / 8), j = i - r * (n / 8);
+    if (r < M2)
+      cp16(sFy + r * SY + 8 * j, Fy + (size_t)r * n + 8 * j);
+    else
+      *reinterpret_cast<uint4*>(sFy + r * SY + 8 * j) = make_uint4(0, 0, 0, 0);
+  }
+  for (int i = tid; i < n * (NC / 8); i += 128) {
+    const int yy = i / (NC / 8), j = i - yy * (NC / 8);
+    cp16(sT + yy * SC + 8 * j, H1 + (((size_t)b * n + yy) * W + c0) * KF + 8 * j);
+  }
+  commit();
+  wait_groups<0>();
+  __syncthreads();
+  float acc[2][TPW][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int u = 0; u < TPW; ++u)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[mt][u][r] = 0.f;
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    uint32_t af[2][4];
+    load_a(af[0], sFy, SY, 0, k0, lane);
+    load_a(af[1], sFy, SY, 16, k0, lane);
+#pragma unroll
+    for (int u = 0; u < TPW; ++u) {
+      uint32_t bf[2];
+      load_b_kn1(bf, sT, SC, k0, (warp * TPW + u) * 8, lane);
+      mma(acc[0][u], af[0], bf[0], bf[1]);
+      mma(acc[1][u], af[1], bf[0], bf[1]);
+    }
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int u = 0; u < TPW; ++u)
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int r = mt * 16 + gr + 8 * h2, col = (warp * TPW + u) * 8 + 2 * tg;
+        if (r < M2) {
+          sO[r * NC + col] = acc[mt][u][2 * h2];
+          sO[r * NC + col + 1] = acc[mt][u][2 * h2 + 1];
+        }
+      }
+  __syncthreads();
+  for (int i = tid; i < CG * modes; i += 128) {
+    const int cc = i / modes, k = i - cc * modes, j = k / m, q = k - j * m;
+    const float* T = sO + cc * KF;
+    const float re = T[(2 * q) * NC + 2 * j] - T[(2 * q + 1) * NC + 2 * j + 1];
+    const float im = T[(2 * q) * NC + 2 * j + 1] + T[(2 * q + 1) * NC + 2 * j];
+    float* h = hat + (((size_t)b * W + c0 + cc) * modes + k) * 2;
+    h[0] = re;
+    h[1] = im;
+  }
+}
+
+// ---- spectral mix and inverse transform along y ---------------------------------------------
+
+// CTA = (sample b, OG output channels): U[o] = expand(sum_i hat[b, i] R[i, o]) (2m x 4m, the
+// c_ky weights of the real inverse), then G1[b, y, o, :] = bf16(scale * Fyi[y, :] U[o])
+template <int KF, int OG>
+__global__ void __launch_bounds__(256) mix_idft_y_kernel(const float* __restrict__ hat, const float* __restrict__ R,
+                                                         const bf16* __restrict__ Fyi, bf16* __restrict__ G1,
+                                                         int W, int n, float scale) {
+  constexpr int M2 = KF / 2, m = KF / 4, modes = 2 * m * m, NC = OG * KF, SU = NC + 8, SY = 40;
+  constexpr int NTT = NC / 8;
+  static_assert(NTT % 2 == 0 && M2 <= 32, "tiling");
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16* sFyi = reinterpret_cast<bf16*>(smem);  // [n][SY], columns >= 2m zero
+  bf16* sU = sFyi + (size_t)n * SY;             // [32][SU], rows >= 2m zero
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gr = lane >> 2, tg = lane & 3;
+  const int b = blockIdx.y, o0 = blockIdx.x * OG;
+  const bf16 zero = __float2bfloat16_rn(0.f);
+  for (int i = tid; i < n * 32; i += 256) {
+    const int yy = i >> 5, r = i & 31;
+    sFyi[yy * SY + r] = r < M2 ? Fyi[(size_t)yy * M2 + r] : zero;
+  }
+  for (int i = tid; i < (32 - M2) * NC; i += 256) sU[(M2 + i / NC) * SU + i % NC] = zero;
+  for (int i = tid; i < OG * modes; i += 256) {
+    const int oo = i / modes, k = i - oo * modes, o = o0 + oo;
+    float re = 0.f, im = 0.f;
+    for (int ii = 0; ii < W; ++ii) {
+      const float2 hv = *reinterpret_cast<const float2*>(hat + (((size_t)b * W + ii) * modes + k) * 2);
+      const float2 rv = *reinterpret_cast<const float2*>(R + (((size_t)ii * W + o) * modes + k) * 2);
+      re = fmaf(hv.x, rv.x, fmaf(-hv.y, rv.y, re));
+      im = fmaf(hv.x, rv.y, fmaf(hv.y, rv.x, im));
+    }
+    const int j = k / m, q = k - j * m;
+    const float cw = q == 0 ? 1.f : 2.f;
+    bf16* U = sU + oo * KF;
+    U[(2 * q) * SU + 2 * j] = __float2bfloat16_rn(cw * re);
+    U[(2 * q + 1) * SU + 2 * j] = __float2bfloat16_rn(-cw * im);
+    U[(2 * q) * SU + 2 * j + 1] = __float2bfloat16_rn(cw * im);
+    U[(2 * q + 1) * SU + 2 * j + 1] = __float2bfloat16_rn(cw * re);
+  }
+  __syncthreads();
+  for (int mt = warp; mt < n / 16; mt += 8) {
+    float acc[NTT][4];
+#pragma unroll
+    for (int t = 0; t < NTT; ++t)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[t][r] = 0.f;
+#pragma unroll
+    for (int k0 = 0; k0 < 32; k0 += 16) {
+      uint32_t af[4];
+      load_a(af, sFyi, SY, mt * 16, k0, lane);
+#pragma unroll
+      for (int t = 0; t < NTT; t += 2) {
+        uint32_t bf[4];
+        load_b_kn2(bf, sU, SU, k0, t * 8, lane);
+        mma(acc[t], af, bf[0], bf[1]);
+        mma(acc[t + 1], af, bf[2], bf[3]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NTT; ++t)
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int yy = mt * 16 + gr + 8 * h2, col = t * 8 + 2 * tg;
+        st_bf2(G1 + (((size_t)b * n + yy) * W + o0) * KF + col, acc[t][2 * h2] * scale, acc[t][2 * h2 + 1] * scale);
+      }
+  }
+}
+
+// ---- launchers -------------------------------------------------------------------------------
+
+constexpr int kMaxDev = 64;
+
+int sm_count() {
+  static int cache[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 0;
+  if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
+  return cache[dev];
+}
+
+template <int W, int KF, int H, int NT, int MODE>
+cudaError_t launch_row_t(const RowArgs& a, cudaStream_t s) {
+  using S = RowSmem<W, KF, H, NT, MODE>;
+  static int per_sm[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  auto kern = row_kernel<W, KF, H, NT, MODE>;
+  if (!per_sm[dev]) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes)) != cudaSuccess)
+      return e;
+    int per = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kRowThreads, S::bytes)) != cudaSuccess)
+      return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    per_sm[dev] = per;
+  }
+  const int rows = a.B * S::n;
+  const int grid = rows < per_sm[dev] * sm_count() ? rows : per_sm[dev] * sm_count();
+  kern<<<grid, kRowThreads, S::bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int W, int KF, int H, int MODE>
+cudaError_t row_by_n(const RowArgs& a, cudaStream_t s) {
+  switch (a.n) {
+    case 64: return launch_row_t<W, KF, H, 1, MODE>(a, s);
+    case 128: return launch_row_t<W, KF, H, 2, MODE>(a, s);
+    case 256: return launch_row_t<W, KF, H, 4, MODE>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int W, int KF, int H>
+cudaError_t row_by_mode(int mode, const RowArgs& a, cudaStream_t s) {
+  switch (mode) {
+    case ROW_LIFT: return row_by_n<W, KF, H, ROW_LIFT>(a, s);
+    case ROW_MID: return row_by_n<W, KF, H, ROW_MID>(a, s);
+    case ROW_LAST: return row_by_n<W, KF, H, ROW_LAST>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int KF, int CG>
+cudaError_t launch_dft_y_t(int W, int B, int n, const bf16* H1, const bf16* Fy, float* hat, cudaStream_t s) {
+  constexpr int NC = CG * KF;
+  const size_t bytes = (size_t)32 * (n + 8) * 2 + (size_t)n * (NC + 8) * 2 + (size_t)(KF / 2) * NC * 4;
+  cudaError_t e = cudaFuncSetAttribute(dft_y_kernel<KF, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  dft_y_kernel<KF, CG><<<dim3(W / CG, B), 128, bytes, s>>>(H1, Fy, hat, W, n);
+  return cudaGetLastError();
+}
+
+template <int KF, int OG>
+cudaError_t launch_mix_t(int W, int B, int n, const float* hat, const float* R, const bf16* Fyi, bf16* G1,
+                         float scale, cudaStream_t s) {
+  const size_t bytes = (size_t)n * 40 * 2 + (size_t)32 * (OG * KF + 8) * 2;
+  cudaError_t e =
+      cudaFuncSetAttribute(mix_idft_y_kernel<KF, OG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  mix_idft_y_kernel<KF, OG><<<dim3(W / OG, B), 256, bytes, s>>>(hat, R, Fyi, G1, W, n, scale);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool supported(int W, int m, int H, int n) {
+  const bool shape = (W == 32 && m == 12 && H == 64) || (W == 16 && m == 8 && H == 32);
+  return shape && (n == 64 || n == 128 || n == 256);
+}
+
+static bool spectral_supported(int W, int m, int n) {
+  return ((W == 32 && m == 12) || (W == 16 && m == 8)) && (n == 64 || n == 128 || n == 256);
+}
+
+cudaError_t launch_row(int mode, int W, int m, int H, const RowArgs& a, cudaStream_t s) {
+  if (!supported(W, m, H, a.n) || a.B < 1) return cudaErrorInvalidValue;
+  if (W == 32) return row_by_mode<32, 48, 64>(mode, a, s);
+  return row_by_mode<16, 32, 32>(mode, a, s);
+}
+
+cudaError_t launch_dft_y(int W, int m, int B, int n, const bf16* H1, const bf16* Fy, float* hat, cudaStream_t s) {
+  if (!spectral_supported(W, m, n) || B < 1) return cudaErrorInvalidValue;
+  if (m == 12) return launch_dft_y_t<48, 2>(W, B, n, H1, Fy, hat, s);
+  return launch_dft_y_t<32, 2>(W, B, n, H1, Fy, hat, s);
+}
+
+cudaError_t launch_mix_idft_y(int W, int m, int B, int n, const float* hat, const float* R, const bf16* Fyi,
+                              bf16* G1, float scale, cudaStream_t s) {
+  if (!spectral_supported(W, m, n) || B < 1) return cudaErrorInvalidValue;
+  if (m == 12) return launch_mix_t<48, 2>(W, B, n, hat, R, Fyi, G1, scale, s);
+  return launch_mix_t<32, 2>(W, B, n, hat, R, Fyi, G1, scale, s);
+}
+
+}  // namespace fno_fused
+}  // namespace sslbm

@@ -43,7 +43,8 @@ EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspa
            "sslbm_ensemble_steps_done", "sslbm_fno_workspace_bytes", "sslbm_fno_create",
            "sslbm_fno_destroy", "sslbm_fno_num_params", "sslbm_fno_set_params",
            "sslbm_fno_get_params", "sslbm_fno_get_grads", "sslbm_fno_make_input",
-           "sslbm_fno_forward", "sslbm_fno_backward", "sslbm_fno_set_adam",
+           "sslbm_fno_forward", "sslbm_fno_backward", "sslbm_fno_set_adam", "sslbm_fno_set_loss_weights",
+           "sslbm_fno_infer", "sslbm_fno_fused",
            "sslbm_fno_train_step", "sslbm_fno_check_project")
 
 
@@ -138,6 +139,9 @@ def load(path: str = LIB_PATH):
             "sslbm_fno_forward": (i32, [_vp, i32, _vp, _vp]),
             "sslbm_fno_backward": (i32, [_vp, i32, _vp, _vp]),
             "sslbm_fno_set_adam": (i32, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+            "sslbm_fno_set_loss_weights": (i32, [_vp, ctypes.c_float, ctypes.c_float]),
+            "sslbm_fno_infer": (i32, [_vp, i32, _vp, _vp]),
+            "sslbm_fno_fused": (i32, [_vp]),
             "sslbm_fno_train_step": (i32, [_vp, i32, _vp, _vp, _vp, _vp, ctypes.c_float,
                                            ctypes.POINTER(ctypes.c_double)]),
             "sslbm_fno_check_project": (i32, [_vp, i32, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
@@ -572,6 +576,20 @@ def sslbm_fno_set_adam(f, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
     _check(load().sslbm_fno_set_adam(f, beta1, beta2, eps, weight_decay), "sslbm_fno_set_adam")
 
 
+def sslbm_fno_set_loss_weights(f, mass_weight=0.0, neg_weight=0.0):
+    _check(load().sslbm_fno_set_loss_weights(f, float(mass_weight), float(neg_weight)), "sslbm_fno_set_loss_weights")
+
+
+def sslbm_fno_infer(f, batch, x, y):
+    _check(load().sslbm_fno_infer(f, int(batch), _dptr(x), _dptr(y)), "sslbm_fno_infer")
+
+
+def sslbm_fno_fused(f) -> bool:
+    r = int(load().sslbm_fno_fused(f))
+    _check(min(r, 0), "sslbm_fno_fused")
+    return r == 1
+
+
 def sslbm_fno_train_step(f, batch, x, target, y_scratch, dy_scratch, lr, want_loss=True):
     loss = ctypes.c_double(0.0)
     _check(load().sslbm_fno_train_step(f, int(batch), _dptr(x), _dptr(target), _dptr(y_scratch), _dptr(dy_scratch),
@@ -629,7 +647,7 @@ class Surrogate:
 
     def make_input(self, u, r0, logd):
         B = u.shape[0]
-        x = self.torch.empty((B, 7, self.n, self.n), dtype=self.torch.float32, device=self.device)
+        x = self.torch.empty((B, 8, self.n, self.n), dtype=self.torch.float32, device=self.device)
         sslbm_fno_make_input(self.f, B, u, r0, logd, x)
         return x
 
@@ -642,6 +660,20 @@ class Surrogate:
 
     def backward(self, x, dy):
         sslbm_fno_backward(self.f, x.shape[0], x, dy)
+
+    def set_loss_weights(self, mass_weight=0.0, neg_weight=0.0):
+        sslbm_fno_set_loss_weights(self.f, mass_weight, neg_weight)
+
+    @property
+    def fused(self):
+        return sslbm_fno_fused(self.f)
+
+    def infer(self, x, y=None):
+        B = x.shape[0]
+        if y is None:
+            y = self.torch.empty((B, 5, self.n, self.n), dtype=self.torch.float32, device=self.device)
+        sslbm_fno_infer(self.f, B, x, y)
+        return y
 
     def train_step(self, x, target, lr, want_loss=True):
         B = x.shape[0]

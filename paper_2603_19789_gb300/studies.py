@@ -93,7 +93,7 @@ def precision_study(n: int = 4096, steps: int = 50000, checkpoints: int = 6, see
     return out
 
 
-def surrogate_study(n=256, trajectories=2000, snapshots=10, spacing=200, train_steps=3000, batch=16,
+def surrogate_study(n=256, trajectories=2000, snapshots=10, horizon=2000, train_steps=3000, batch=16,
                     lr=1e-3, width=32, modes=12, layers=4, hidden=64, scenarios=64, rollout_steps=100):
     """Generate trajectories with the ensemble kernel, train the surrogate on the GPU, and
     roll it out with residual checks and SSLBM fallback, judged against the SSLBM."""
@@ -101,7 +101,7 @@ def surrogate_study(n=256, trajectories=2000, snapshots=10, spacing=200, train_s
 
     from . import surrogate as S
     t0 = time.perf_counter()
-    X, Y, r0, logd = S.generate_pairs(n, trajectories, snapshots, spacing)
+    X, Y, r0, logd = S.generate_pairs(n, trajectories, snapshots, horizon)
     t_data = time.perf_counter() - t0
     sur = L.Surrogate(n=n, width=width, modes=modes, layers=layers, hidden=hidden,
                       max_batch=max(batch, scenarios))
@@ -110,11 +110,14 @@ def surrogate_study(n=256, trajectories=2000, snapshots=10, spacing=200, train_s
     del X, Y
     torch.cuda.empty_cache()
     roll = S.rollout(sur, n=n, scenarios=scenarios, steps=rollout_steps)
+    strict = S.rollout(sur, n=n, scenarios=scenarios, steps=rollout_steps, neg_threshold=0.0, reference=False)
     roll.pop("state")
     roll.pop("reference_state")
     fp64 = S.fp64_scenario_steps_per_s(n)
     return {"n": n, "trajectories": trajectories, "pairs": trajectories * snapshots,
             "params": sur.nparams, "data_seconds": t_data, "train": hist, "rollout": roll,
+            "rollout_strict_negativity": {k: strict[k] for k in ("fallbacks", "fallback_rate", "seconds",
+                                                                 "scenario_steps_per_s")},
             "fp64_plain_scenario_steps_per_s": fp64,
             "speedup_vs_fp64": roll["scenario_steps_per_s"] / fp64}
 

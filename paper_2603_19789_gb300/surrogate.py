@@ -4,8 +4,8 @@ gathering).
 
 Data: trajectories of the periodic ensemble workload's parameter ranges (R0 ~ U[1.2, 4],
 d ~ logU[1e-3, 1e-1], 1..8 Gaussian seeds) on n x n grids, produced by the persistent
-ensemble launch; from each trajectory, snapshots at t_j = j * spacing (j = 0..snapshots-1)
-paired with the state 20 steps later.
+ensemble launch; from each trajectory, snapshots at stratified random multiples of 20 steps
+over the rollout horizon (one per stratum), each paired with the state 20 steps later.
 
 Rollout: each surrogate step advances a batch of scenarios by 20 SSLBM steps.  The raw
 prediction y is checked against the input state u: the conservation residual
@@ -43,7 +43,7 @@ def initial_params(width=32, modes=12, layers=4, hidden=64, seed=0):
         b = 1.0 / math.sqrt(cols)
         return g.uniform(-b, b, rows * cols)
 
-    parts = [dense(W, 7), np.zeros(W)]
+    parts = [dense(W, 8), np.zeros(W)]
     for _ in range(layers):
         parts += [g.uniform(-1.0, 1.0, W * W * 2 * m * m * 2) / (W * W), dense(W, W), np.zeros(W)]
     parts += [dense(H, W), np.zeros(H), dense(5, H), np.zeros(5)]
@@ -58,31 +58,43 @@ def scenario_specs(count, n, seed):
     return sc, specs, r0, logd
 
 
-def generate_pairs(n=256, trajectories=2000, snapshots=10, spacing=200, seed=7, chunk=500):
-    """Returns device tensors X, Y [pairs, 5, n, n] (float32) and per-pair r0, logd."""
+def snapshot_slots(trajectories, snapshots=10, horizon=2000, seed=7):
+    """Stratified random snapshot times, in units of K_STEPS: the horizon is cut into
+    `snapshots` equal strata of slots and each trajectory draws one slot from each, so
+    the pairs cover the whole rollout window (the early exponential growth included)."""
+    slots = horizon // K_STEPS
+    per = slots // snapshots
+    if per < 1:
+        raise ValueError("horizon too short for this many snapshots")
+    rng = inputs._rng(seed + 1)
+    return np.arange(snapshots)[None, :] * per + rng.integers(0, per, (trajectories, snapshots))
+
+
+def generate_pairs(n=256, trajectories=2000, snapshots=10, horizon=2000, seed=7, chunk=500):
+    """Returns device tensors X, Y [pairs, 5, n, n] (float32) and per-pair r0, logd.  Pair
+    (i, j) is trajectory i's state at step 20 * slot[i, j] and 20 steps later."""
     import torch
     sc, specs, r0, logd = scenario_specs(trajectories, n, seed)
+    slot = snapshot_slots(trajectories, snapshots, horizon, seed)
     pairs = trajectories * snapshots
     X = torch.empty((pairs, 5, n, n), dtype=torch.float32, device="cuda")
     Y = torch.empty_like(X)
     pr0 = torch.empty(pairs, dtype=torch.float32, device="cuda")
     plogd = torch.empty_like(pr0)
+    last = int(slot.max()) + 1
     for c0 in range(0, trajectories, chunk):
         c1 = min(trajectories, c0 + chunk)
         ens = L.Ensemble(specs[c0:c1])
         ens.set_tiling(4, 64)
         for i in range(c0, c1):
             ens.write(i - c0, inputs.ensemble_state(sc[i]).astype(np.float32))
-        t = 0
-        for j in range(snapshots):
-            ens.run(j * spacing - t)
-            t = j * spacing
-            for i in range(c0, c1):
-                L.sslbm_ensemble_read(ens.e, i - c0, X[i * snapshots + j])
-            ens.run(K_STEPS)
-            t += K_STEPS
-            for i in range(c0, c1):
-                L.sslbm_ensemble_read(ens.e, i - c0, Y[i * snapshots + j])
+        for t in range(last + 1):
+            if t:
+                ens.run(K_STEPS)
+            for i, j in zip(*np.nonzero(slot[c0:c1] == t)):
+                L.sslbm_ensemble_read(ens.e, int(i), X[(c0 + i) * snapshots + j])
+            for i, j in zip(*np.nonzero(slot[c0:c1] == t - 1)):
+                L.sslbm_ensemble_read(ens.e, int(i), Y[(c0 + i) * snapshots + j])
         ens.close()
         idx = torch.arange(c0 * snapshots, c1 * snapshots, device="cuda")
         pr0[idx] = torch.from_numpy(np.repeat(r0[c0:c1], snapshots)).cuda()
@@ -92,9 +104,12 @@ def generate_pairs(n=256, trajectories=2000, snapshots=10, spacing=200, seed=7, 
 
 
 def train(sur, X, Y, r0, logd, steps=3000, batch=16, lr=1e-3, lr_min=1e-5, seed=0, val_frac=0.05,
-          log_every=500):
-    """Adam on random batches with a cosine learning-rate schedule; returns a history."""
+          log_every=500, mass_weight=30.0, neg_weight=30.0):
+    """Adam on random batches with a cosine learning-rate schedule; the loss is the scaled
+    MSE plus the mass-residual and negative-mass terms (sslbm_fno_set_loss_weights);
+    returns a history."""
     import torch
+    sur.set_loss_weights(mass_weight, neg_weight)
     g = torch.Generator(device="cpu")
     g.manual_seed(seed)
     pairs = X.shape[0]
@@ -125,7 +140,7 @@ def evaluate(sur, X, Y, r0, logd, idx, batch):
     for i in range(0, idx.numel(), batch):
         sel = idx[i:i + batch].cuda()
         x = sur.make_input(X[sel].contiguous(), r0[sel].contiguous(), logd[sel].contiguous())
-        y = sur.forward(x)
+        y = sur.infer(x)
         tot += float(((y - Y[sel]) ** 2).mean().item()) * sel.numel()
         cnt += sel.numel()
     return tot / cnt
@@ -158,7 +173,7 @@ def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_th
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         x = sur.make_input(u, tr0, tlogd)
-        y = sur.forward(x)
+        y = sur.infer(x)
         res = sur.check_project(y, u)
         any_negative += int((res[:, 1] > 0).sum())
         bad = np.nonzero((res[:, 0] > threshold) | (res[:, 1] > neg_threshold))[0]

@@ -69,3 +69,64 @@ def test_backward_matches_finite_differences(seed):
         tm[i] -= eps
         fd = (loss_of(tp) - loss_of(tm)) / (2 * eps)
         assert abs(fd - grads[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (i, fd, grads[i])
+
+
+def test_input_scaling_recovers_the_state_and_is_scale_free():
+    g = np.random.default_rng(7)
+    u = g.uniform(0, 1, (3, 5, 8, 8))
+    u[1, 1:3] *= 1e-5                        # an early-growth sample: E, I tiny
+    u[2, 1:3] = 0.0                          # no infection at all: the scale floor
+    x = fno.make_input(u, np.full(3, 2.0), np.full(3, -2.0))
+    sig = fno.out_scale(x)
+    np.testing.assert_allclose(x[:, :5] * sig[:, :, None, None], u, rtol=1e-13, atol=0)
+    peak = np.maximum(u[:, 1].reshape(3, -1).max(1), u[:, 2].reshape(3, -1).max(1))
+    np.testing.assert_allclose(sig[:2, 1], peak[:2], rtol=1e-13)
+    assert sig[2, 1] == pytest.approx(fno.SCALE_FLOOR, rel=1e-12)
+    assert np.abs(x[:2, 1:3]).max() <= 1.0 + 1e-12 and np.isclose(x[:2, 1:3].max(), 1.0)
+    # multiplying E and I by alpha leaves their input channels unchanged and shifts the
+    # scale channel by log10(alpha) / 4
+    v = u[:2].copy()
+    v[:, 1:3] *= 1e-3
+    xv = fno.make_input(v, np.full(2, 2.0), np.full(2, -2.0))
+    np.testing.assert_allclose(xv[:, 1:3], x[:2, 1:3], rtol=1e-12)
+    np.testing.assert_allclose(xv[:, 7], x[:2, 7] - 0.75, atol=1e-12)
+
+
+def test_zero_increment_network_is_persistence():
+    W, m, L, H, n = 4, 2, 2, 6, 8
+    g = np.random.default_rng(3)
+    params = fno.init_params(1, W, m, L, H)
+    params["Q2"][:] = 0.0
+    params["q2"][:] = 0.0
+    u = g.uniform(0, 1, (2, 5, n, n))
+    u[0, 1:3] *= 1e-4
+    x = fno.make_input(u, np.array([1.5, 3.0]), np.array([-1.5, -2.5]))
+    y, _ = fno.forward(params, x, W, m, L, H)
+    np.testing.assert_allclose(y, u, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("mass_weight,neg_weight", [(0.0, 0.0), (10.0, 0.0), (3.0, 50.0)])
+def test_loss_gradient_matches_finite_differences(mass_weight, neg_weight):
+    g = np.random.default_rng(11)
+    B, n = 2, 6
+    u = g.uniform(0, 1, (B, 5, n, n))
+    u[1, 1:3] *= 1e-3
+    x = fno.make_input(u, np.array([2.0, 3.0]), np.array([-2.0, -1.0]))
+    t = g.uniform(0, 1, (B, 5, n, n))
+    t[1, 1:3] *= 1e-3
+    y = t + g.normal(0, 0.2, t.shape)        # some entries negative
+    y[1, 1:3] = t[1, 1:3] + g.normal(0, 1e-4, (2, n, n))
+    _, total, dy = fno.loss(y, t, x, mass_weight, neg_weight)
+    idx = [(0, 0, 1, 2), (0, 2, 3, 3), (1, 1, 0, 0), (1, 4, 5, 1), (1, 2, 2, 4)]
+    idx += [tuple(int(v) for v in np.argwhere(y < 0)[0])]
+    for i in idx:
+        h = 1e-7 * max(1e-3, abs(y[i]))
+        yp, ym = y.copy(), y.copy()
+        yp[i] += h
+        ym[i] -= h
+        fd = (fno.loss(yp, t, x, mass_weight, neg_weight)[1] - fno.loss(ym, t, x, mass_weight, neg_weight)[1]) / (2 * h)
+        assert fd == pytest.approx(dy[i], rel=1e-5, abs=1e-12), (i, fd, dy[i])
+    # the weighted error of E and I is measured in units of the infection scale
+    sig = fno.out_scale(x)
+    ref = np.mean(((y - t) / sig[:, :, None, None]) ** 2)
+    assert fno.loss(y, t, x)[0] == pytest.approx(ref, rel=1e-13)

@@ -27,7 +27,7 @@ def trained():
     from paper_2603_19789_gb300 import surrogate as S
     build.build()
     L.load()
-    X, Y, r0, logd = S.generate_pairs(n=N, trajectories=64, snapshots=6, spacing=120, seed=3, chunk=64)
+    X, Y, r0, logd = S.generate_pairs(n=N, trajectories=64, snapshots=6, horizon=240, seed=3, chunk=64)
     sur = L.Surrogate(n=N, max_batch=16, **CFG)
     sur.set_params(S.initial_params(CFG["width"], CFG["modes"], CFG["layers"], CFG["hidden"], seed=0))
     hist0 = S.evaluate(sur, X, Y, r0, logd, _val_idx(X.shape[0]), 8)
@@ -44,20 +44,26 @@ def _val_idx(pairs, batch=8, val_frac=0.05, seed=0):
 
 
 def test_training_data_are_sslbm_trajectories():
-    """Each pair (X, Y) is 20 steps of the single-scenario SSLBM solver apart."""
+    """Each pair (X, Y) is the single-scenario SSLBM solver's state at its snapshot time and
+    20 steps later; snapshot times cover each stratum of the horizon once."""
     import torch
     from paper_2603_19789_gb300 import build, inputs
     from paper_2603_19789_gb300 import surrogate as S
     build.build()
-    X, Y, r0, logd = S.generate_pairs(n=N, trajectories=3, snapshots=2, spacing=40, seed=5, chunk=3)
+    X, Y, r0, logd = S.generate_pairs(n=N, trajectories=3, snapshots=2, horizon=120, seed=5, chunk=3)
+    slot = S.snapshot_slots(3, 2, 120, 5)
+    assert ((slot[:, 0] >= 0) & (slot[:, 0] < 3) & (slot[:, 1] >= 3) & (slot[:, 1] < 6)).all()
     sc, specs, _, _ = S.scenario_specs(3, N, 5)
     for i in range(3):
         s = L.Solver(N, N, specs[i]["rates"], d=specs[i]["d"], bc=L.BC_PERIODIC, precision=L.FP32)
         s.write(inputs.ensemble_state(sc[i]).astype(np.float32))
-        s.step(40)
-        np.testing.assert_array_equal(s.read(dtype=np.float32), X[2 * i + 1].cpu().numpy())
-        s.step(20)
-        np.testing.assert_array_equal(s.read(dtype=np.float32), Y[2 * i + 1].cpu().numpy())
+        t = 0
+        for j in range(2):
+            s.step(20 * int(slot[i, j]) - t)
+            np.testing.assert_array_equal(s.read(dtype=np.float32), X[2 * i + j].cpu().numpy())
+            s.step(20)
+            t = 20 * int(slot[i, j]) + 20
+            np.testing.assert_array_equal(s.read(dtype=np.float32), Y[2 * i + j].cpu().numpy())
         s.close()
     assert torch.allclose(r0[::2], torch.from_numpy(np.array([q["R0"] for q in sc], np.float32)).cuda())
 
