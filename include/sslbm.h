@@ -306,10 +306,10 @@ int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e);
  * aligned. */
 typedef struct sslbm_fno_config {
   int32_t n;          /* grid side (periodic), 2 * modes <= n */
-  int32_t width;      /* W: channels of the hidden layers */
+  int32_t width;      /* W: channels of the hidden layers (<= 64) */
   int32_t modes;      /* m: retained modes per direction (2m x m kept) */
   int32_t layers;     /* L: spectral layers (<= 16) */
-  int32_t hidden;     /* H: width of the projection */
+  int32_t hidden;     /* H: width of the projection (<= 64) */
   int32_t max_batch;  /* largest batch a call may use (sizes the activations) */
 } sslbm_fno_config;
 

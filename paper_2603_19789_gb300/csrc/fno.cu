@@ -447,9 +447,9 @@ struct Layout {
 int make_param_layout(const sslbm_fno_config* c, Layout* L) {
   if (!c) return err(SSLBM_ERR_BAD_ARG, "config is NULL");
   if (c->n < 8 || c->width < 1 || c->modes < 1 || c->layers < 1 || c->layers > 16 || c->hidden < 1 ||
-      c->max_batch < 1 || 2 * c->modes > c->n || c->n > 4096 || c->width > 256 || c->hidden > 512)
+      c->max_batch < 1 || 2 * c->modes > c->n || c->n > 4096 || c->width > 64 || c->hidden > 64)
     return err(SSLBM_ERR_BAD_ARG, "invalid surrogate configuration (n=%d width=%d modes=%d layers=%d "
-               "hidden=%d max_batch=%d; need 2*modes <= n)", c->n, c->width, c->modes, c->layers,
+               "hidden=%d max_batch=%d; need 2*modes <= n, width and hidden <= 64)", c->n, c->width, c->modes, c->layers,
                c->hidden, c->max_batch);
   L->n = c->n; L->W = c->width; L->m = c->modes; L->L = c->layers; L->H = c->hidden; L->maxB = c->max_batch;
   L->P = (int64_t)c->n * c->n;
@@ -565,37 +565,23 @@ int run(const GemmArgs& g0, cudaStream_t s, const char* what) {
 // C[b] (rows x P) = Wt (rows x cin) * src[b] (cin x P) (+ beta C): the per-cell channel map
 int channel_map(const sslbm_fno* f, const bf16* Wt, int rows, int cin, const void* src, int src_bf16,
                 void* C, int c_bf16, float beta, int B, const char* what) {
-  GemmArgs g = gemm0();
-  g.M = rows; g.N = (int)f->L.P; g.K = cin; g.batch = B;
-  g.A = Wt; g.a_bf16 = 1; g.sAb = 0; g.sAm = cin; g.sAk0 = 1;
-  g.B = src; g.b_bf16 = src_bf16; g.sBb = (int64_t)cin * f->L.P; g.sBk0 = f->L.P; g.sBn = 1;
-  g.C = C; g.c_bf16 = c_bf16; g.sCb = (int64_t)rows * f->L.P; g.sCm = f->L.P; g.sCn = 1;
-  g.beta = beta;
-  return run(g, f->stream, what);
+  CK(sslbm::fno_fused::cell_map(B, rows, cin, f->L.P, Wt, cin, 1, src, src_bf16, C, c_bf16, 1.f, beta, f->stream),
+     what);
+  return SSLBM_OK;
 }
 
 // C[b] (rows x P) = Wt^T (rows x cin, Wt stored cin x rows) * src[b] (cin x P) (+ beta C)
 int channel_map_t(const sslbm_fno* f, const bf16* Wt, int rows, int cin, const float* src, float* C,
                   float beta, int B, const char* what) {
-  GemmArgs g = gemm0();
-  g.M = rows; g.N = (int)f->L.P; g.K = cin; g.batch = B;
-  g.A = Wt; g.a_bf16 = 1; g.sAb = 0; g.sAm = 1; g.sAk0 = rows;
-  g.B = src; g.b_bf16 = 0; g.sBb = (int64_t)cin * f->L.P; g.sBk0 = f->L.P; g.sBn = 1;
-  g.C = C; g.c_bf16 = 0; g.sCb = (int64_t)rows * f->L.P; g.sCm = f->L.P; g.sCn = 1;
-  g.beta = beta;
-  return run(g, f->stream, what);
+  CK(sslbm::fno_fused::cell_map(B, rows, cin, f->L.P, Wt, 1, rows, src, 0, C, 0, 1.f, beta, f->stream), what);
+  return SSLBM_OK;
 }
 
-// dW (rows x cols) += sum_b sum_p d[b](rows x P) * act[b](cols x P)^T  (split-K, atomics)
+// dW (rows x cols) += sum_b sum_p d[b](rows x P) * act[b](cols x P)^T
 int weight_grad(const sslbm_fno* f, const float* d, int rows, const void* act, int act_bf16, int cols,
                 float* dW, int B, const char* what) {
-  GemmArgs g = gemm0();
-  g.M = rows; g.N = cols; g.K = (int)(B * f->L.P); g.K0 = (int)f->L.P; g.batch = 1;
-  g.splits = (int)std::min<int64_t>(2048, std::max<int64_t>(1, g.K / 4096));
-  g.A = d; g.a_bf16 = 0; g.sAm = f->L.P; g.sAk0 = 1; g.sAk1 = (int64_t)rows * f->L.P;
-  g.B = act; g.b_bf16 = act_bf16; g.sBk0 = 1; g.sBk1 = (int64_t)cols * f->L.P; g.sBn = f->L.P;
-  g.C = dW; g.c_bf16 = 0; g.sCm = cols; g.sCn = 1; g.atomic = 1;
-  return run(g, f->stream, what);
+  CK(sslbm::fno_fused::cell_wgrad(B, rows, cols, f->L.P, d, act, act_bf16, dW, f->stream), what);
+  return SSLBM_OK;
 }
 
 int channel_sum(const sslbm_fno* f, const float* src, float* out, int B, int C) {
@@ -738,7 +724,7 @@ int forward_generic(sslbm_fno* f, int B, const float* x, float* y) {
   return SSLBM_OK;
 }
 
-// the fused forward pass (fno_fused.cu): 1 + 3L launches; store = write what backward reads
+// the fused forward pass (fno_fused.cu): 1 + 4L launches; store = write what backward reads
 int forward_fused(sslbm_fno* f, int B, const float* x, float* y, int store) {
   namespace F = sslbm::fno_fused;
   const Layout& L = f->L;
@@ -761,8 +747,8 @@ int forward_fused(sslbm_fno* f, int B, const float* x, float* y, int store) {
   for (int l = 1; l <= L.L; ++l) {
     float* hat = f->hat(l, B);
     CK(F::launch_dft_y(W, m, B, n, H1, f->Fy(), hat, f->stream), "fused transform along y");
-    CK(F::launch_mix_idft_y(W, m, B, n, hat, f->theta() + L.off_R[l - 1], f->Fyi(), G1, 1.f / ((float)n * (float)n),
-                            f->stream),
+    CK(F::launch_mix_idft_y(W, m, B, n, hat, f->theta() + L.off_R[l - 1], f->Fyi(), G1, f->at<float>(f->bu.dg),
+                            1.f / ((float)n * (float)n), f->stream),
        "fused spectral mix");
     F::RowArgs r{};
     r.B = B;

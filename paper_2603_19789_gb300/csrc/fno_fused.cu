@@ -89,19 +89,25 @@ struct RowSmem {
   static constexpr size_t oF = 0;                                             // bf16 [n][SF]
   static constexpr size_t oBl = oF + (size_t)n * SF * 2;                       // bf16 [W][SB]
   static constexpr size_t oOut = oBl + (lift ? 0 : (size_t)W * SB * 2);        // bf16 [W][SH]
-  static constexpr size_t oRed = oOut + (size_t)W * SH * 2;                    // f32 [2][W][KF]
-  static constexpr size_t oQ1 = oRed + (last ? 0 : (size_t)2 * W * KF * 4);    // bf16 [H][SB]
-  static constexpr size_t oQ2 = oQ1 + (last ? (size_t)H * SB * 2 : 0);         // bf16 [16][SQ]
-  static constexpr size_t oP = oQ2 + (last ? (size_t)16 * SQ * 2 : 0);         // bf16 [H][SH]
-  static constexpr size_t oA0 = oP + (last ? (size_t)H * SH * 2 : 0);          // f32 [W][12]
-  static constexpr size_t oStage = oA0 + (lift ? (size_t)W * 12 * 4 : 0);
   // one input row: x (8 planes, FP32) or {h_{l-1} [W][SH], G1 [W][SF]} (BF16)
   static constexpr size_t stage = lift ? (size_t)kCin * n * 4 : (size_t)W * SH * 2 + (size_t)W * SF * 2;
-  static constexpr size_t bytes = oStage + 2 * stage;
+  // f32 [2][W][KF] partial sums of the next layer's transform along x: in the current input
+  // stage (dead after the first product) when they fit, else a region of their own
+  static constexpr size_t red_bytes = (size_t)2 * W * KF * 4;
+  static constexpr bool red_in_stage = MODE == ROW_MID && red_bytes <= stage;
+  static constexpr size_t oRed = oOut + (size_t)W * SH * 2;
+  static constexpr size_t oQ1 = oRed + (last || red_in_stage ? 0 : red_bytes);  // bf16 [H][SB]
+  static constexpr size_t oQ2 = oQ1 + (last ? (size_t)H * SB * 2 : 0);         // bf16 [16][SQ]
+  static constexpr size_t oA0 = oQ2 + (last ? (size_t)16 * SQ * 2 : 0);        // f32 [W][12]
+  static constexpr size_t oStage = oA0 + (lift ? (size_t)W * 12 * 4 : 0);
+  // input rows in flight: two ahead, except the last layer (two CTAs per SM need the room)
+  static constexpr int NST = last ? 2 : 3;
+  static constexpr size_t bytes = oStage + NST * stage;
+  static_assert(!last || (H / 2 <= W && H % 32 == 0), "half of the projection fits in a stage");
 };
 
 template <int W, int KF, int H, int NT, int MODE>
-__global__ void __launch_bounds__(kRowThreads, MODE == ROW_LAST ? 1 : 2) row_kernel(const RowArgs a) {
+__global__ void __launch_bounds__(kRowThreads, 2) row_kernel(const RowArgs a) {
   using S = RowSmem<W, KF, H, NT, MODE>;
   constexpr int n = S::n, SH = S::SH, SF = S::SF, SB = S::SB, SQ = S::SQ;
   constexpr int CW = 8 * NT;  // columns per warp
@@ -111,10 +117,8 @@ __global__ void __launch_bounds__(kRowThreads, MODE == ROW_LAST ? 1 : 2) row_ker
   bf16* sF = reinterpret_cast<bf16*>(smem + S::oF);
   bf16* sBl = reinterpret_cast<bf16*>(smem + S::oBl);
   bf16* sOut = reinterpret_cast<bf16*>(smem + S::oOut);
-  float* sRed = reinterpret_cast<float*>(smem + S::oRed);
   bf16* sQ1 = reinterpret_cast<bf16*>(smem + S::oQ1);
   bf16* sQ2 = reinterpret_cast<bf16*>(smem + S::oQ2);
-  bf16* sP = reinterpret_cast<bf16*>(smem + S::oP);
   float* sA0 = reinterpret_cast<float*>(smem + S::oA0);
   unsigned char* stage0 = smem + S::oStage;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -175,15 +179,20 @@ __global__ void __launch_bounds__(kRowThreads, MODE == ROW_LAST ? 1 : 2) row_ker
     commit();  // possibly empty: every thread keeps the same group count
   };
 
+  constexpr int NST = S::NST;
+#pragma unroll
+  for (int k = 0; k < NST - 1; ++k) issue(blockIdx.x + k * gridDim.x, k);
   int s = 0;
-  issue(blockIdx.x, 0);
-  for (int row = blockIdx.x; row < rows; row += gridDim.x, s ^= 1) {
-    issue(row + gridDim.x, s ^ 1);
-    wait_groups<1>();
+  for (int row = blockIdx.x; row < rows; row += gridDim.x, s = s + 1 == NST ? 0 : s + 1) {
+    issue(row + (NST - 1) * gridDim.x, s == 0 ? NST - 1 : s - 1);
+    wait_groups<NST - 1>();
     __syncthreads();
     const int b = row / n, y = row - b * n;
     const int x0 = warp * CW;
     unsigned char* st = stage0 + s * S::stage;
+    // scratch that reuses the current input stage once the first product has read it
+    float* sRed = S::red_in_stage ? reinterpret_cast<float*>(st) : reinterpret_cast<float*>(smem + S::oRed);
+    bf16* sP = reinterpret_cast<bf16*>(st);  // [H/2][SH] (last layer)
 
     if (MODE == ROW_LIFT) {
       // h0 = A0 x + a0 in FP32, one grid column per thread
@@ -318,76 +327,82 @@ __global__ void __launch_bounds__(kRowThreads, MODE == ROW_LAST ? 1 : 2) row_ker
       for (int i = tid; i < W * KF / 2; i += kRowThreads)
         st_bf2(dst + 2 * i, sRed[2 * i] + sRed[W * KF + 2 * i], sRed[2 * i + 1] + sRed[W * KF + 2 * i + 1]);
     } else {
-      // projection on the warp's own columns: p = gelu(Q1 h_L + q1), y = Q2 p + q2 + x[:5]
-      constexpr int MH = H / 16;
-      float acc3[MH][NT][4];
-#pragma unroll
-      for (int mh = 0; mh < MH; ++mh)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) acc3[mh][nt][r] = 0.f;
-#pragma unroll
-      for (int k0 = 0; k0 < W; k0 += 16) {
-        uint32_t af[MH][4];
-#pragma unroll
-        for (int mh = 0; mh < MH; ++mh) load_a(af[mh], sQ1, SB, mh * 16, k0, lane);
-#pragma unroll
-        for (int nt = 0; nt < NT; nt += 2) {
-          if (nt + 1 < NT) {
-            uint32_t bf[4];
-            load_b_kn2(bf, sOut, SH, k0, x0 + nt * 8, lane);
-#pragma unroll
-            for (int mh = 0; mh < MH; ++mh) {
-              mma(acc3[mh][nt], af[mh], bf[0], bf[1]);
-              mma(acc3[mh][nt + 1], af[mh], bf[2], bf[3]);
-            }
-          } else {
-            uint32_t bf[2];
-            load_b_kn1(bf, sOut, SH, k0, x0 + nt * 8, lane);
-#pragma unroll
-            for (int mh = 0; mh < MH; ++mh) mma(acc3[mh][nt], af[mh], bf[0], bf[1]);
-          }
-        }
-      }
-#pragma unroll
-      for (int mh = 0; mh < MH; ++mh)
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-          const int hh = mh * 16 + gr + 8 * h2;
-          const float qv = a.q1[hh];
-#pragma unroll
-          for (int nt = 0; nt < NT; ++nt) {
-            const int xx = x0 + nt * 8 + 2 * tg;
-            const float z0 = acc3[mh][nt][2 * h2] + qv, z1 = acc3[mh][nt][2 * h2 + 1] + qv;
-            const size_t off = (((size_t)b * H + hh) * n + y) * n + xx;
-            if (a.store) st_bf2(a.zp + off, z0, z1);
-            const bf162 pv = __floats2bfloat162_rn(gelu(z0), gelu(z1));
-            *reinterpret_cast<bf162*>(sP + hh * SH + xx) = pv;
-            if (a.store) *reinterpret_cast<bf162*>(a.p + off) = pv;
-          }
-        }
-      __syncwarp();
+      // projection on the warp's own columns: p = gelu(Q1 h_L + q1), delta = Q2 p + q2, in two
+      // halves of the H rows of p (each half staged in the warp's columns of sP)
+      constexpr int MH = H / 32;  // 16-row tiles per half
       float acc4[NT][4];
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
         for (int r = 0; r < 4; ++r) acc4[nt][r] = 0.f;
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+        const int h0 = half * (H / 2);
+        float acc3[MH][NT][4];
 #pragma unroll
-      for (int k0 = 0; k0 < H; k0 += 16) {
-        uint32_t af[4];
-        load_a(af, sQ2, SQ, 0, k0, lane);
+        for (int mh = 0; mh < MH; ++mh)
 #pragma unroll
-        for (int nt = 0; nt < NT; nt += 2) {
-          if (nt + 1 < NT) {
-            uint32_t bf[4];
-            load_b_kn2(bf, sP, SH, k0, x0 + nt * 8, lane);
-            mma(acc4[nt], af, bf[0], bf[1]);
-            mma(acc4[nt + 1], af, bf[2], bf[3]);
-          } else {
-            uint32_t bf[2];
-            load_b_kn1(bf, sP, SH, k0, x0 + nt * 8, lane);
-            mma(acc4[nt], af, bf[0], bf[1]);
+          for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc3[mh][nt][r] = 0.f;
+#pragma unroll
+        for (int k0 = 0; k0 < W; k0 += 16) {
+          uint32_t af[MH][4];
+#pragma unroll
+          for (int mh = 0; mh < MH; ++mh) load_a(af[mh], sQ1, SB, h0 + mh * 16, k0, lane);
+#pragma unroll
+          for (int nt = 0; nt < NT; nt += 2) {
+            if (nt + 1 < NT) {
+              uint32_t bf[4];
+              load_b_kn2(bf, sOut, SH, k0, x0 + nt * 8, lane);
+#pragma unroll
+              for (int mh = 0; mh < MH; ++mh) {
+                mma(acc3[mh][nt], af[mh], bf[0], bf[1]);
+                mma(acc3[mh][nt + 1], af[mh], bf[2], bf[3]);
+              }
+            } else {
+              uint32_t bf[2];
+              load_b_kn1(bf, sOut, SH, k0, x0 + nt * 8, lane);
+#pragma unroll
+              for (int mh = 0; mh < MH; ++mh) mma(acc3[mh][nt], af[mh], bf[0], bf[1]);
+            }
+          }
+        }
+        __syncwarp();  // the previous half's reads of this warp's sP columns are done
+#pragma unroll
+        for (int mh = 0; mh < MH; ++mh)
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int hl = mh * 16 + gr + 8 * h2, hh = h0 + hl;
+            const float qv = a.q1[hh];
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+              const int xx = x0 + nt * 8 + 2 * tg;
+              const float z0 = acc3[mh][nt][2 * h2] + qv, z1 = acc3[mh][nt][2 * h2 + 1] + qv;
+              const size_t off = (((size_t)b * H + hh) * n + y) * n + xx;
+              if (a.store) st_bf2(a.zp + off, z0, z1);
+              const bf162 pv = __floats2bfloat162_rn(gelu(z0), gelu(z1));
+              *reinterpret_cast<bf162*>(sP + hl * SH + xx) = pv;
+              if (a.store) *reinterpret_cast<bf162*>(a.p + off) = pv;
+            }
+          }
+        __syncwarp();
+#pragma unroll
+        for (int k0 = 0; k0 < H / 2; k0 += 16) {
+          uint32_t af[4];
+          load_a(af, sQ2, SQ, 0, h0 + k0, lane);
+#pragma unroll
+          for (int nt = 0; nt < NT; nt += 2) {
+            if (nt + 1 < NT) {
+              uint32_t bf[4];
+              load_b_kn2(bf, sP, SH, k0, x0 + nt * 8, lane);
+              mma(acc4[nt], af, bf[0], bf[1]);
+              mma(acc4[nt + 1], af, bf[2], bf[3]);
+            } else {
+              uint32_t bf[2];
+              load_b_kn1(bf, sP, SH, k0, x0 + nt * 8, lane);
+              mma(acc4[nt], af, bf[0], bf[1]);
+            }
           }
         }
       }
@@ -491,14 +506,59 @@ __global__ void __launch_bounds__(128) dft_y_kernel(const bf16* __restrict__ H1,
   }
 }
 
-// ---- spectral mix and inverse transform along y ---------------------------------------------
+// ---- spectral mix ------------------------------------------------------------------------
 
-// CTA = (sample b, OG output channels): U[o] = expand(sum_i hat[b, i] R[i, o]) (2m x 4m, the
-// c_ky weights of the real inverse), then G1[b, y, o, :] = bf16(scale * Fyi[y, :] U[o])
+// CTA = MC modes: hatg[b, o, k] = sum_i hat[b, i, k] R[i, o, k] (complex), all b and o.  Each
+// mode's weights R[:, :, k] are read once and applied to the whole batch.
+template <int MC, int BC>
+__global__ void __launch_bounds__(256) mix_kernel(const float2* __restrict__ hat, const float2* __restrict__ R,
+                                                  float2* __restrict__ hatg, int B, int W, int modes) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* sR = reinterpret_cast<float2*>(smem);  // [W][W][MC]
+  float2* sHt = sR + (size_t)W * W * MC;         // [BC][W][MC]
+  const int tid = threadIdx.x;
+  const int k0 = blockIdx.x * MC;
+  const int mc = min(MC, modes - k0);
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int i = tid; i < W * W * MC; i += 256) {
+    const int io = i / MC, kk = i - io * MC;
+    sR[i] = kk < mc ? R[(size_t)io * modes + k0 + kk] : zero;
+  }
+  for (int b0 = 0; b0 < B; b0 += BC) {
+    const int nb = min(BC, B - b0);
+    __syncthreads();
+    for (int i = tid; i < nb * W * MC; i += 256) {
+      const int bi = i / MC, kk = i - bi * MC;
+      sHt[i] = kk < mc ? hat[((size_t)b0 * W + bi) * modes + k0 + kk] : zero;
+    }
+    __syncthreads();
+    for (int t = tid; t < nb * W; t += 256) {
+      const int bl = t / W, o = t - bl * W;
+      float re[MC], im[MC];
+#pragma unroll
+      for (int kk = 0; kk < MC; ++kk) re[kk] = im[kk] = 0.f;
+      for (int i = 0; i < W; ++i) {
+#pragma unroll
+        for (int kk = 0; kk < MC; ++kk) {
+          const float2 h = sHt[(bl * W + i) * MC + kk], r = sR[(i * W + o) * MC + kk];
+          re[kk] = fmaf(h.x, r.x, fmaf(-h.y, r.y, re[kk]));
+          im[kk] = fmaf(h.x, r.y, fmaf(h.y, r.x, im[kk]));
+        }
+      }
+#pragma unroll
+      for (int kk = 0; kk < MC; ++kk)
+        if (kk < mc) hatg[((size_t)(b0 + bl) * W + o) * modes + k0 + kk] = make_float2(re[kk], im[kk]);
+    }
+  }
+}
+
+// ---- inverse transform along y -------------------------------------------------------------
+
+// CTA = (sample b, OG output channels): U[o] = expand(hatg[b, o]) (2m x 4m, the c_ky weights
+// of the real inverse), then G1[b, y, o, :] = bf16(scale * Fyi[y, :] U[o])
 template <int KF, int OG>
-__global__ void __launch_bounds__(256) mix_idft_y_kernel(const float* __restrict__ hat, const float* __restrict__ R,
-                                                         const bf16* __restrict__ Fyi, bf16* __restrict__ G1,
-                                                         int W, int n, float scale) {
+__global__ void __launch_bounds__(256) idft_y_kernel(const float2* __restrict__ hatg, const bf16* __restrict__ Fyi,
+                                                     bf16* __restrict__ G1, int W, int n, float scale) {
   constexpr int M2 = KF / 2, m = KF / 4, modes = 2 * m * m, NC = OG * KF, SU = NC + 8, SY = 40;
   constexpr int NTT = NC / 8;
   static_assert(NTT % 2 == 0 && M2 <= 32, "tiling");
@@ -515,21 +575,15 @@ __global__ void __launch_bounds__(256) mix_idft_y_kernel(const float* __restrict
   }
   for (int i = tid; i < (32 - M2) * NC; i += 256) sU[(M2 + i / NC) * SU + i % NC] = zero;
   for (int i = tid; i < OG * modes; i += 256) {
-    const int oo = i / modes, k = i - oo * modes, o = o0 + oo;
-    float re = 0.f, im = 0.f;
-    for (int ii = 0; ii < W; ++ii) {
-      const float2 hv = *reinterpret_cast<const float2*>(hat + (((size_t)b * W + ii) * modes + k) * 2);
-      const float2 rv = *reinterpret_cast<const float2*>(R + (((size_t)ii * W + o) * modes + k) * 2);
-      re = fmaf(hv.x, rv.x, fmaf(-hv.y, rv.y, re));
-      im = fmaf(hv.x, rv.y, fmaf(hv.y, rv.x, im));
-    }
+    const int oo = i / modes, k = i - oo * modes;
+    const float2 g = hatg[((size_t)b * W + o0 + oo) * modes + k];
     const int j = k / m, q = k - j * m;
     const float cw = q == 0 ? 1.f : 2.f;
     bf16* U = sU + oo * KF;
-    U[(2 * q) * SU + 2 * j] = __float2bfloat16_rn(cw * re);
-    U[(2 * q + 1) * SU + 2 * j] = __float2bfloat16_rn(-cw * im);
-    U[(2 * q) * SU + 2 * j + 1] = __float2bfloat16_rn(cw * im);
-    U[(2 * q + 1) * SU + 2 * j + 1] = __float2bfloat16_rn(cw * re);
+    U[(2 * q) * SU + 2 * j] = __float2bfloat16_rn(cw * g.x);
+    U[(2 * q + 1) * SU + 2 * j] = __float2bfloat16_rn(-cw * g.y);
+    U[(2 * q) * SU + 2 * j + 1] = __float2bfloat16_rn(cw * g.y);
+    U[(2 * q + 1) * SU + 2 * j + 1] = __float2bfloat16_rn(cw * g.x);
   }
   __syncthreads();
   for (int mt = warp; mt < n / 16; mt += 8) {
@@ -557,6 +611,171 @@ __global__ void __launch_bounds__(256) mix_idft_y_kernel(const float* __restrict
         const int yy = mt * 16 + gr + 8 * h2, col = t * 8 + 2 * tg;
         st_bf2(G1 + (((size_t)b * n + yy) * W + o0) * KF + col, acc[t][2 * h2] * scale, acc[t][2 * h2 + 1] * scale);
       }
+  }
+}
+
+// ---- per-cell channel products (the backward pass's contractions over channels) ---------------
+
+constexpr int kCellChunk = 128;  // grid cells per work item
+
+// S chunk [K][128] (FP32 or BF16 in memory) -> BF16 shared tile [64][136], zero outside
+__device__ __forceinline__ void load_cell_tile(bf16* dst, const void* src, int src_bf16, int K, int64_t P,
+                                               int64_t p0, int tid, int nthreads) {
+  const bf16 zero = __float2bfloat16_rn(0.f);
+  if ((P & 3) == 0) {
+    for (int i = tid; i < 64 * (kCellChunk / 4); i += nthreads) {
+      const int k = i / (kCellChunk / 4), j = 4 * (i - k * (kCellChunk / 4));
+      bf16* d = dst + k * (kCellChunk + 8) + j;
+      const int64_t p = p0 + j;
+      if (k < K && p < P) {
+        if (src_bf16) {
+          const uint2 v = *reinterpret_cast<const uint2*>(static_cast<const bf16*>(src) + (size_t)k * P + p);
+          *reinterpret_cast<uint2*>(d) = v;
+        } else {
+          const float4 v = *reinterpret_cast<const float4*>(static_cast<const float*>(src) + (size_t)k * P + p);
+          *reinterpret_cast<bf162*>(d) = __floats2bfloat162_rn(v.x, v.y);
+          *reinterpret_cast<bf162*>(d + 2) = __floats2bfloat162_rn(v.z, v.w);
+        }
+      } else {
+        d[0] = d[1] = d[2] = d[3] = zero;
+      }
+    }
+  } else {
+    for (int i = tid; i < 64 * kCellChunk; i += nthreads) {
+      const int k = i / kCellChunk, j = i - k * kCellChunk;
+      const int64_t p = p0 + j;
+      float v = 0.f;
+      if (k < K && p < P)
+        v = src_bf16 ? __bfloat162float(static_cast<const bf16*>(src)[(size_t)k * P + p])
+                     : static_cast<const float*>(src)[(size_t)k * P + p];
+      dst[k * (kCellChunk + 8) + j] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// C[b](rows x P) = alpha Wm (rows x K) S[b] (K x P) + beta C[b];  rows, K <= 64.  CTA work item:
+// (b, 128 cells); warp w owns cells [16w, 16w + 16) of the item, all rows.
+__global__ void __launch_bounds__(256) cell_map_kernel(int B, int rows, int K, int64_t P, const bf16* __restrict__ Wm,
+                                                       int64_t sWr, int64_t sWk, const void* __restrict__ S,
+                                                       int s_bf16, void* __restrict__ C, int c_bf16, float alpha,
+                                                       float beta) {
+  constexpr int SW = 72, SS = kCellChunk + 8;
+  __shared__ __align__(16) bf16 sW[64 * SW];
+  __shared__ __align__(16) bf16 sS[64 * SS];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gr = lane >> 2, tg = lane & 3;
+  for (int i = tid; i < 64 * 64; i += 256) {
+    const int r = i >> 6, k = i & 63;
+    sW[r * SW + k] = (r < rows && k < K) ? Wm[r * sWr + k * sWk] : __float2bfloat16_rn(0.f);
+  }
+  const int MT = (rows + 15) / 16, KS = (K + 15) / 16;
+  const int64_t chunks = (P + kCellChunk - 1) / kCellChunk, items = (int64_t)B * chunks;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int b = (int)(it / chunks);
+    const int64_t p0 = (it - (int64_t)b * chunks) * kCellChunk;
+    __syncthreads();
+    load_cell_tile(sS, s_bf16 ? (const void*)(static_cast<const bf16*>(S) + (size_t)b * K * P)
+                              : (const void*)(static_cast<const float*>(S) + (size_t)b * K * P),
+                   s_bf16, K, P, p0, tid, 256);
+    __syncthreads();
+    float acc[4][2][4];
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0.f;
+    for (int ks = 0; ks < KS; ++ks) {
+      uint32_t bf[4];
+      load_b_kn2(bf, sS, SS, ks * 16, warp * 16, lane);
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt) {
+        if (mt < MT) {
+          uint32_t af[4];
+          load_a(af, sW, SW, mt * 16, ks * 16, lane);
+          mma(acc[mt][0], af, bf[0], bf[1]);
+          mma(acc[mt][1], af, bf[2], bf[3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+      if (mt >= MT) continue;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int r = mt * 16 + gr + 8 * h2;
+          const int64_t p = p0 + warp * 16 + nt * 8 + 2 * tg;
+          if (r >= rows) continue;
+          const size_t off = ((size_t)b * rows + r) * P + p;
+          for (int e = 0; e < 2; ++e) {
+            if (p + e >= P) continue;
+            const float v = alpha * acc[mt][nt][2 * h2 + e];
+            if (c_bf16) {
+              bf16* c = static_cast<bf16*>(C) + off + e;
+              *c = __float2bfloat16_rn(beta != 0.f ? v + beta * __bfloat162float(*c) : v);
+            } else {
+              float* c = static_cast<float*>(C) + off + e;
+              *c = beta != 0.f ? v + beta * *c : v;
+            }
+          }
+        }
+    }
+  }
+}
+
+// dW (rows x cols) += sum_b sum_p D[b](rows x P) A[b](cols x P)^T;  rows, cols <= 64.  Each CTA
+// accumulates its work items in registers and adds them to dW once.
+__global__ void __launch_bounds__(256) cell_wgrad_kernel(int B, int rows, int cols, int64_t P,
+                                                         const float* __restrict__ D, const void* __restrict__ A,
+                                                         int a_bf16, float* __restrict__ dW) {
+  constexpr int SS = kCellChunk + 8;
+  __shared__ __align__(16) bf16 sD[64 * SS];
+  __shared__ __align__(16) bf16 sA[64 * SS];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gr = lane >> 2, tg = lane & 3;
+  const int MT = (rows + 15) / 16, NT = (cols + 7) / 8, T = MT * NT;
+  const int64_t chunks = (P + kCellChunk - 1) / kCellChunk, items = (int64_t)B * chunks;
+  float acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc[u][r] = 0.f;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int b = (int)(it / chunks);
+    const int64_t p0 = (it - (int64_t)b * chunks) * kCellChunk;
+    __syncthreads();
+    load_cell_tile(sD, D + (size_t)b * rows * P, 0, rows, P, p0, tid, 256);
+    load_cell_tile(sA, a_bf16 ? (const void*)(static_cast<const bf16*>(A) + (size_t)b * cols * P)
+                              : (const void*)(static_cast<const float*>(A) + (size_t)b * cols * P),
+                   a_bf16, cols, P, p0, tid, 256);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = warp + 8 * u;
+      if (t >= T) continue;
+      const int mt = t / NT, nt = t - mt * NT;
+#pragma unroll
+      for (int k0 = 0; k0 < kCellChunk; k0 += 16) {
+        uint32_t af[4], bf[2];
+        load_a(af, sD, SS, mt * 16, k0, lane);
+        load_b_nk1(bf, sA, SS, k0, nt * 8, lane);
+        mma(acc[u], af, bf[0], bf[1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int t = warp + 8 * u;
+    if (t >= T) continue;
+    const int mt = t / NT, nt = t - mt * NT;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int r = mt * 16 + gr + 8 * h2, c = nt * 8 + 2 * tg;
+      if (r < rows && c < cols) atomicAdd(dW + r * cols + c, acc[u][2 * h2]);
+      if (r < rows && c + 1 < cols) atomicAdd(dW + r * cols + c + 1, acc[u][2 * h2 + 1]);
+    }
   }
 }
 
@@ -628,16 +847,42 @@ cudaError_t launch_dft_y_t(int W, int B, int n, const bf16* H1, const bf16* Fy, 
 
 template <int KF, int OG>
 cudaError_t launch_mix_t(int W, int B, int n, const float* hat, const float* R, const bf16* Fyi, bf16* G1,
-                         float scale, cudaStream_t s) {
-  const size_t bytes = (size_t)n * 40 * 2 + (size_t)32 * (OG * KF + 8) * 2;
-  cudaError_t e =
-      cudaFuncSetAttribute(mix_idft_y_kernel<KF, OG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+                         float* hatg, float scale, cudaStream_t s) {
+  constexpr int MC = 2, BC = 64, m = KF / 4, modes = 2 * m * m;
+  const size_t mbytes = ((size_t)W * W * MC + (size_t)BC * W * MC) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(mix_kernel<MC, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mbytes);
   if (e != cudaSuccess) return e;
-  mix_idft_y_kernel<KF, OG><<<dim3(W / OG, B), 256, bytes, s>>>(hat, R, Fyi, G1, W, n, scale);
+  mix_kernel<MC, BC><<<(modes + MC - 1) / MC, 256, mbytes, s>>>(reinterpret_cast<const float2*>(hat),
+                                                              reinterpret_cast<const float2*>(R),
+                                                              reinterpret_cast<float2*>(hatg), B, W, modes);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t bytes = (size_t)n * 40 * 2 + (size_t)32 * (OG * KF + 8) * 2;
+  e = cudaFuncSetAttribute(idft_y_kernel<KF, OG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  idft_y_kernel<KF, OG><<<dim3(W / OG, B), 256, bytes, s>>>(reinterpret_cast<const float2*>(hatg), Fyi, G1, W, n,
+                                                           scale);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t cell_map(int B, int rows, int K, int64_t P, const bf16* Wm, int64_t sWr, int64_t sWk, const void* S,
+                     int s_bf16, void* C, int c_bf16, float alpha, float beta, cudaStream_t s) {
+  if (B < 1 || rows < 1 || rows > 64 || K < 1 || K > 64 || P < 1) return cudaErrorInvalidValue;
+  const int64_t items = (int64_t)B * ((P + kCellChunk - 1) / kCellChunk);
+  const int grid = (int)(items < 8 * sm_count() ? items : 8 * sm_count());
+  cell_map_kernel<<<grid, 256, 0, s>>>(B, rows, K, P, Wm, sWr, sWk, S, s_bf16, C, c_bf16, alpha, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t cell_wgrad(int B, int rows, int cols, int64_t P, const float* D, const void* A, int a_bf16, float* dW,
+                       cudaStream_t s) {
+  if (B < 1 || rows < 1 || rows > 64 || cols < 1 || cols > 64 || P < 1) return cudaErrorInvalidValue;
+  const int64_t items = (int64_t)B * ((P + kCellChunk - 1) / kCellChunk);
+  const int grid = (int)(items < 4 * sm_count() ? items : 4 * sm_count());
+  cell_wgrad_kernel<<<grid, 256, 0, s>>>(B, rows, cols, P, D, A, a_bf16, dW);
+  return cudaGetLastError();
+}
 
 bool supported(int W, int m, int H, int n) {
   const bool shape = (W == 32 && m == 12 && H == 64) || (W == 16 && m == 8 && H == 32);
@@ -661,10 +906,10 @@ cudaError_t launch_dft_y(int W, int m, int B, int n, const bf16* H1, const bf16*
 }
 
 cudaError_t launch_mix_idft_y(int W, int m, int B, int n, const float* hat, const float* R, const bf16* Fyi,
-                              bf16* G1, float scale, cudaStream_t s) {
+                              bf16* G1, float* hatg, float scale, cudaStream_t s) {
   if (!spectral_supported(W, m, n) || B < 1) return cudaErrorInvalidValue;
-  if (m == 12) return launch_mix_t<48, 2>(W, B, n, hat, R, Fyi, G1, scale, s);
-  return launch_mix_t<32, 2>(W, B, n, hat, R, Fyi, G1, scale, s);
+  if (m == 12) return launch_mix_t<48, 2>(W, B, n, hat, R, Fyi, G1, hatg, scale, s);
+  return launch_mix_t<32, 2>(W, B, n, hat, R, Fyi, G1, hatg, scale, s);
 }
 
 }  // namespace fno_fused

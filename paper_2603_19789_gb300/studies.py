@@ -93,7 +93,7 @@ def precision_study(n: int = 4096, steps: int = 50000, checkpoints: int = 6, see
     return out
 
 
-def surrogate_study(n=256, trajectories=2000, snapshots=10, horizon=2000, train_steps=3000, batch=16,
+def surrogate_study(n=256, trajectories=2000, snapshots=10, horizon=2000, train_steps=20000, batch=16,
                     lr=1e-3, width=32, modes=12, layers=4, hidden=64, scenarios=64, rollout_steps=100):
     """Generate trajectories with the ensemble kernel, train the surrogate on the GPU, and
     roll it out with residual checks and SSLBM fallback, judged against the SSLBM."""
@@ -107,6 +107,7 @@ def surrogate_study(n=256, trajectories=2000, snapshots=10, horizon=2000, train_
                       max_batch=max(batch, scenarios))
     sur.set_params(S.initial_params(width, modes, layers, hidden))
     hist = S.train(sur, X, Y, r0, logd, steps=train_steps, batch=batch, lr=lr)
+    theta = sur.get_params()
     del X, Y
     torch.cuda.empty_cache()
     roll = S.rollout(sur, n=n, scenarios=scenarios, steps=rollout_steps)
@@ -114,12 +115,13 @@ def surrogate_study(n=256, trajectories=2000, snapshots=10, horizon=2000, train_
     roll.pop("state")
     roll.pop("reference_state")
     fp64 = S.fp64_scenario_steps_per_s(n)
-    return {"n": n, "trajectories": trajectories, "pairs": trajectories * snapshots,
+    out = {"n": n, "trajectories": trajectories, "pairs": trajectories * snapshots,
             "params": sur.nparams, "data_seconds": t_data, "train": hist, "rollout": roll,
             "rollout_strict_negativity": {k: strict[k] for k in ("fallbacks", "fallback_rate", "seconds",
                                                                  "scenario_steps_per_s")},
             "fp64_plain_scenario_steps_per_s": fp64,
             "speedup_vs_fp64": roll["scenario_steps_per_s"] / fp64}
+    return out, theta
 
 
 def main(argv=None):
@@ -129,17 +131,18 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=50000)
     ap.add_argument("--checkpoints", type=int, default=6)
     ap.add_argument("--trajectories", type=int, default=2000)
-    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--train-steps", type=int, default=20000)
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     from . import build
     build.build()
     if args.study == "surrogate":
-        res = surrogate_study(n=args.n or 256, trajectories=args.trajectories, train_steps=args.train_steps)
+        res, theta = surrogate_study(n=args.n or 256, trajectories=args.trajectories, train_steps=args.train_steps)
         text = json.dumps(res, indent=1)
         if args.out:
             with open(args.out, "w") as fh:
                 fh.write(text + "\n")
+            np.save(args.out.rsplit(".", 1)[0] + "_params.npy", theta)
         print(text)
         return
     res = precision_study(args.n or 4096, args.steps, args.checkpoints)

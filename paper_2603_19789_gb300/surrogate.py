@@ -104,12 +104,13 @@ def generate_pairs(n=256, trajectories=2000, snapshots=10, horizon=2000, seed=7,
 
 
 def train(sur, X, Y, r0, logd, steps=3000, batch=16, lr=1e-3, lr_min=1e-5, seed=0, val_frac=0.05,
-          log_every=500, mass_weight=30.0, neg_weight=30.0):
+          log_every=500, mass_weight=3000.0, neg_weight=3000.0, ramp=0.5):
     """Adam on random batches with a cosine learning-rate schedule; the loss is the scaled
-    MSE plus the mass-residual and negative-mass terms (sslbm_fno_set_loss_weights);
-    returns a history."""
+    MSE plus the mass-residual and negative-mass terms (sslbm_fno_set_loss_weights), whose
+    weights rise linearly from zero over the first `ramp` fraction of the steps, so the
+    network learns the dynamics before it is held to the residual checks; returns a
+    history."""
     import torch
-    sur.set_loss_weights(mass_weight, neg_weight)
     g = torch.Generator(device="cpu")
     g.manual_seed(seed)
     pairs = X.shape[0]
@@ -122,6 +123,8 @@ def train(sur, X, Y, r0, logd, steps=3000, batch=16, lr=1e-3, lr_min=1e-5, seed=
         sel = tr_idx[torch.randint(0, tr_idx.numel(), (batch,), generator=g)].cuda()
         x = sur.make_input(X[sel].contiguous(), r0[sel].contiguous(), logd[sel].contiguous())
         cur_lr = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * it / max(1, steps)))
+        w = min(1.0, it / max(1.0, ramp * steps)) if ramp > 0 else 1.0
+        sur.set_loss_weights(w * mass_weight, w * neg_weight)
         want = (it % log_every == 0) or it == steps - 1
         loss = sur.train_step(x, Y[sel].contiguous(), cur_lr, want_loss=want)
         if want:
@@ -165,6 +168,7 @@ def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_th
             L.sslbm_ensemble_write(ref.e, i, u[i])
     total0 = u.double().sum(dim=(1, 2, 3))
     fallbacks = 0
+    fail_mass = fail_neg = 0
     any_negative = 0
     t_sur = 0.0
     err_hist = []
@@ -176,6 +180,8 @@ def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_th
         y = sur.infer(x)
         res = sur.check_project(y, u)
         any_negative += int((res[:, 1] > 0).sum())
+        fail_mass += int((res[:, 0] > threshold).sum())
+        fail_neg += int((res[:, 1] > neg_threshold).sum())
         bad = np.nonzero((res[:, 0] > threshold) | (res[:, 1] > neg_threshold))[0]
         if bad.size:
             fallbacks += int(bad.size)
@@ -205,6 +211,7 @@ def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_th
     return {"scenarios": scenarios, "surrogate_steps": steps, "sslbm_steps_equivalent": steps * K_STEPS,
             "seconds": t_sur, "scenario_steps_per_s": scenarios * steps * K_STEPS / t_sur,
             "fallbacks": fallbacks, "fallback_rate": fallbacks / (scenarios * steps),
+            "failed_conservation": fail_mass, "failed_nonnegativity": fail_neg,
             "scenario_steps_with_any_negative": any_negative,
             "rms_error_vs_sslbm": err_hist, "max_population_drift": drift,
             "min_value": float(u.min()), "state": u, "reference_state": last_ref}
