@@ -292,10 +292,12 @@ int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e);
  *   x = [S, E/s', I/s', R, D, (R0 - 2.6)/1.4, log10(d) + 2, e]
  * and the network is
  *   h0 = A0 x + a0; z_l = K_l(h_{l-1}) + B_l h_{l-1} + b_l, h_l = gelu(z_l) (l < L), h_L = z_L;
- *   delta = Q2 gelu(Q1 h_L + q1) + q2;  y_c = sigma_c (x_c + delta_c), sigma = (1, s', s', 1, 1),
+ *   delta = Q2 gelu(Q1 h_L + q1) + q2;  v_c = sigma_c (x_c + delta_c), sigma = (1, s', s', 1, 1);
+ *   y = v - u kappa, u_c = sigma_c x_c, kappa = (sum v - sum u) / sum u (sums over a sample),
  * K_l a spectral convolution on the kx in {0..m-1, n-m..n-1}, ky in {0..m-1} Fourier modes
  * with complex weights R_l[i][o][kx][ky].  E and I enter and leave in units of the
- * infection scale, so the early exponential phase is the same problem at every amplitude.
+ * infection scale, so the early exponential phase is the same problem at every amplitude;
+ * the last step makes y conserve the total population of its input (zero fields stay zero). 
  * Parameters are one flat FP32 vector in the order A0[W][8], a0[W],
  * {R_l[W][W][2m][m][2], B_l[W][W], b_l[W]}_{l=1..L}, Q1[H][W], q1[H], Q2[5][H], q2[5].
  * Dense contractions run on BF16 tensor cores with FP32 accumulation; activations are

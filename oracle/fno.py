@@ -15,10 +15,15 @@ Network (all per grid cell unless spectral):
     z_l = K_l(h_{l-1}) + B_l h_{l-1} + b_l,  h_l = gelu(z_l) (l < L), h_L = z_L
     p  = gelu(Q1 h_L + q1)                                          width H
     delta = Q2 p + q2
-    y_c = sigma_c (x_c + delta_c), sigma = (1, s', s', 1, 1)        state 20 steps ahead
+    v_c = sigma_c (x_c + delta_c), sigma = (1, s', s', 1, 1)        raw prediction
+    u_c = sigma_c x_c                                                the input state
+    y = v - u kappa,  kappa = (sum v - sum u) / sum u               state 20 steps ahead
 E and I enter and leave in units of the infection scale, so the early exponential phase
 (E, I of order 1e-4 on S ~ 1) is learned as the scale-free problem it is; the loss weighs
-E and I in the same units (weights 1 / sigma_c^2).
+E and I in the same units (weights 1 / sigma_c^2).  The last step removes the raw
+prediction's change of the total population in proportion to the input state (sums over
+all channels and cells of a sample), so y conserves the population exactly and zero
+fields stay zero.
 Spectral convolution K on an n x n periodic grid, kept modes kx in {0..m-1} U {n-m..n-1},
 ky in {0..m-1} (2m x m modes), complex weights R[i, o, kx, ky]:
     hat_h[k] = sum_{x,y} h[y, x] exp(-2 pi i (kx x + ky y) / n)
@@ -260,7 +265,11 @@ def forward(params, x, W=32, m=12, L=4, H=64):
     p = gelu(zp)
     cache["zp"], cache["p"] = zp, p
     sig = out_scale(x)[:, :, None, None]
-    y = sig * (x[:, :5] + pointwise(params["Q2"], p, params["q2"]))
+    v = sig * (x[:, :5] + pointwise(params["Q2"], p, params["q2"]))
+    u = sig * x[:, :5]
+    su = u.reshape(u.shape[0], -1).sum(axis=1)
+    kappa = (v.reshape(v.shape[0], -1).sum(axis=1) - su) / su
+    y = v - u * kappa[:, None, None, None]
     return y, cache
 
 
@@ -269,7 +278,11 @@ def backward(params, cache, dy, W=32, m=12, L=4, H=64):
     n = dy.shape[-1]
     g = {}
     p = cache["p"]
-    dy = dy * out_scale(cache["x"])[:, :, None, None]      # d/d delta
+    sig = out_scale(cache["x"])[:, :, None, None]
+    u = sig * cache["x"][:, :5]
+    B = u.shape[0]
+    lam = (dy * u).reshape(B, -1).sum(axis=1) / u.reshape(B, -1).sum(axis=1)
+    dy = (dy - lam[:, None, None, None]) * sig               # d/d delta through y = v - u kappa
     g["Q2"] = np.einsum("boyx,biyx->oi", dy, p)
     g["q2"] = dy.sum(axis=(0, 2, 3))
     dp = pointwise(params["Q2"].T, dy)

@@ -7,8 +7,10 @@
 //   s' = 10^(4e - 4);  x = [S, E/s', I/s', R, D, (R0 - 2.6)/1.4, log10(d) + 2, e]   (8 channels)
 //   h0 = A0 x + a0
 //   z_l = K_l(h_{l-1}) + B_l h_{l-1} + b_l, h_l = gelu(z_l) for l < L, h_L = z_L
-//   p  = gelu(Q1 h_L + q1),  delta = Q2 p + q2,  y_c = sigma_c (x_c + delta_c)
-//   with sigma = (1, s', s', 1, 1): E and I enter and leave in units of the infection scale.
+//   p  = gelu(Q1 h_L + q1),  delta = Q2 p + q2,  v_c = sigma_c (x_c + delta_c)
+//   with sigma = (1, s', s', 1, 1): E and I enter and leave in units of the infection scale;
+//   y = v - u kappa with u_c = sigma_c x_c the input state and kappa = (sum v - sum u) / sum u
+//   per sample, so the prediction conserves the total population.
 //
 // K_l is the spectral convolution on the 2m x m retained Fourier modes, evaluated as real
 // DFT products: H1 = h Fx (along x), T = Fy H1 (along y), combine to complex, mix with the
@@ -146,14 +148,59 @@ __global__ void output_kernel(float* __restrict__ y, const float* __restrict__ q
   }
 }
 
-// dd = sigma dy: the derivative with respect to delta = Q2 p + q2
+// per sample: sums[2b] += sum_{c,p} a[b, c, p] w[b, c, p], sums[2b+1] += sum u[b, c, p], with
+// u_c = sigma_c x_c the input state and w = u (the population of the raw prediction a) or
+// w = 1 (a = dy: the backward pass's sum of dy u uses a = dy, w = u)
+__global__ void state_sums_kernel(const float* __restrict__ a, const float* __restrict__ x,
+                                  double* __restrict__ sums, int64_t P, int weight_by_u) {
+  const int64_t b = blockIdx.y;
+  const float sg = scale_from_e(x[(b * kCin + 7) * P]);
+  double sa = 0.0, su = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 5 * P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / P);
+    const float u = (c == 1 || c == 2) ? sg * x[b * kCin * P + t] : x[b * kCin * P + t];
+    const float av = a[b * 5 * P + t];
+    sa += weight_by_u ? (double)av * u : (double)av;
+    su += u;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    sa += __shfl_down_sync(0xffffffffu, sa, off);
+    su += __shfl_down_sync(0xffffffffu, su, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(sums + 2 * b, sa);
+    atomicAdd(sums + 2 * b + 1, su);
+  }
+}
+
+// y = v - u kappa, kappa = (sum v - sum u) / sum u: the prediction conserves the population
+__global__ void conserve_kernel(float* __restrict__ y, const float* __restrict__ x, const double* __restrict__ sums,
+                                int B, int64_t P) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * 5 * P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / (5 * P), r = t - b * 5 * P;
+    const int c = (int)(r / P);
+    const double su = sums[2 * b + 1];
+    const float kappa = su != 0.0 ? (float)((sums[2 * b] - su) / su) : 0.f;
+    const float xv = x[b * kCin * P + r];
+    const float u = (c == 1 || c == 2) ? scale_from_e(x[(b * kCin + 7) * P]) * xv : xv;
+    y[t] = fmaf(-u, kappa, y[t]);
+  }
+}
+
+// dd = sigma (dy - lambda_b), lambda_b = sum(dy u) / sum u: the derivative with respect to
+// delta = Q2 p + q2 through y = v - u kappa and v_c = sigma_c (x_c + delta_c)
 __global__ void scale_dy_kernel(const float* __restrict__ dy, const float* __restrict__ x,
-                                float* __restrict__ dd, int B, int64_t P) {
+                                const double* __restrict__ sums, float* __restrict__ dd, int B, int64_t P) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * 5 * P;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / (5 * P);
     const int c = (int)((t - b * 5 * P) / P);
-    dd[t] = (c == 1 || c == 2) ? scale_from_e(x[(b * kCin + 7) * P]) * dy[t] : dy[t];
+    const double su = sums[2 * b + 1];
+    const float lam = su != 0.0 ? (float)(sums[2 * b] / su) : 0.f;
+    const float g = dy[t] - lam;
+    dd[t] = (c == 1 || c == 2) ? scale_from_e(x[(b * kCin + 7) * P]) * g : g;
   }
 }
 
@@ -472,8 +519,8 @@ int make_param_layout(const sslbm_fno_config* c, Layout* L) {
 
 struct Buffers {
   size_t total;
-  size_t theta, theta16, grad, mom, vel, dft, hcat, zcat, zp, p, f32a, f32b, f32p, h1, tt, hat, dg, dd, smax, loss,
-      res;
+  size_t theta, theta16, grad, mom, vel, dft, hcat, zcat, zp, p, f32a, f32b, f32p, h1, tt, hat, dg, dd, smax, csum,
+      loss, res;
 };
 
 size_t rup(size_t v) { return (v + 255) / 256 * 256; }
@@ -501,6 +548,7 @@ void make_buffers(const Layout& L, Buffers* b) {
   b->dg = take(B * W * 2 * m * m * 2 * 4);
   b->dd = take(B * 5 * P * 4);
   b->smax = take(B * 4);
+  b->csum = take(B * 2 * 8);
   b->loss = take(8);
   b->res = take(B * 3 * 8);
   b->total = o;
@@ -779,12 +827,26 @@ int forward_fused(sslbm_fno* f, int B, const float* x, float* y, int store) {
   return SSLBM_OK;
 }
 
+// the per-sample conservation step of the output: y = v - u kappa
+int conserve(sslbm_fno* f, int B, const float* x, float* y) {
+  double* sums = f->at<double>(f->bu.csum);
+  CK(cudaMemsetAsync(sums, 0, (size_t)B * 2 * 8, f->stream), "zero population sums");
+  const int64_t P = f->L.P;
+  dim3 grid((unsigned)std::min<int64_t>(64, (5 * P + kThreads - 1) / kThreads), B);
+  state_sums_kernel<<<grid, kThreads, 0, f->stream>>>(y, x, sums, P, 0);
+  CK(cudaGetLastError(), "population sums");
+  conserve_kernel<<<blocks_for((int64_t)B * 5 * P), kThreads, 0, f->stream>>>(y, x, sums, B, P);
+  CK(cudaGetLastError(), "conservation");
+  return SSLBM_OK;
+}
+
 int forward_impl(sslbm_fno* f, int B, const float* x, float* y, int store) {
   int st;
   if (sslbm::fno_fused::supported(f->L.W, f->L.m, f->L.H, f->L.n))
     st = forward_fused(f, B, x, y, store);
   else
     st = forward_generic(f, B, x, y);  // always stores
+  if (st == SSLBM_OK) st = conserve(f, B, x, y);
   f->cached_batch = st == SSLBM_OK && (store || !sslbm::fno_fused::supported(f->L.W, f->L.m, f->L.H, f->L.n)) ? B : 0;
   return st;
 }
@@ -798,7 +860,12 @@ int backward_impl(sslbm_fno* f, int B, const float* x, const float* dy_out) {
   CK(cudaMemsetAsync(g, 0, L.nparams * sizeof(float), f->stream), "zero gradients");
   // seed: the derivative with respect to delta = Q2 p + q2 (y_c = sigma_c (x_c + delta_c))
   float* dy = f->at<float>(f->bu.dd);
-  scale_dy_kernel<<<blocks_for((int64_t)B * 5 * P), kThreads, 0, f->stream>>>(dy_out, x, dy, B, P);
+  double* sums = f->at<double>(f->bu.csum);
+  CK(cudaMemsetAsync(sums, 0, (size_t)B * 2 * 8, f->stream), "zero population sums");
+  dim3 sgrid((unsigned)std::min<int64_t>(64, (5 * P + kThreads - 1) / kThreads), B);
+  state_sums_kernel<<<sgrid, kThreads, 0, f->stream>>>(dy_out, x, sums, P, 1);
+  CK(cudaGetLastError(), "population sums");
+  scale_dy_kernel<<<blocks_for((int64_t)B * 5 * P), kThreads, 0, f->stream>>>(dy_out, x, sums, dy, B, P);
   CK(cudaGetLastError(), "output scale");
   if ((st = channel_sum(f, dy, g + L.off_q2, B, 5))) return st;
   if ((st = weight_grad(f, dy, 5, f->at<bf16>(f->bu.p), 1, L.H, g + L.off_Q2, B, "dQ2"))) return st;

@@ -104,11 +104,12 @@ def generate_pairs(n=256, trajectories=2000, snapshots=10, horizon=2000, seed=7,
 
 
 def train(sur, X, Y, r0, logd, steps=3000, batch=16, lr=1e-3, lr_min=1e-5, seed=0, val_frac=0.05,
-          log_every=500, mass_weight=3000.0, neg_weight=3000.0, ramp=0.5):
+          log_every=500, mass_weight=0.0, neg_weight=30.0, ramp=0.5):
     """Adam on random batches with a cosine learning-rate schedule; the loss is the scaled
-    MSE plus the mass-residual and negative-mass terms (sslbm_fno_set_loss_weights), whose
+    MSE plus the negative-mass term (and optionally the mass-residual term, which the
+    network's conservation step makes redundant) of sslbm_fno_set_loss_weights, whose
     weights rise linearly from zero over the first `ramp` fraction of the steps, so the
-    network learns the dynamics before it is held to the residual checks; returns a
+    network learns the dynamics before it is held to the nonnegativity check; returns a
     history."""
     import torch
     g = torch.Generator(device="cpu")

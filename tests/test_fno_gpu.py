@@ -100,12 +100,13 @@ def test_forward_matches_oracle(shape, seed):
     # network works in: divided by sigma
     sig = fno.out_scale(xo)[:, :, None, None]
     assert rel((y - u) / sig, (yo - u) / sig) < 3e-2
-    # the inference call computes the same values without keeping activations
+    # the inference call computes the same values without keeping activations (up to the
+    # order of the FP64 atomic sums of the conservation step)
     yi = s.infer(x).cpu().numpy()
-    if s.fused:
-        np.testing.assert_array_equal(yi, y.astype(np.float32))
-    else:
-        assert rel(yi.astype(np.float64) - u, y - u) < 1e-6
+    assert rel(yi.astype(np.float64) - u, y - u) < 1e-5
+    # the prediction conserves each sample's population to FP32 rounding
+    np.testing.assert_allclose(y.reshape(B, -1).sum(axis=1), u.astype(np.float64).reshape(B, -1).sum(axis=1),
+                               rtol=2e-6)
 
 
 @pytest.mark.parametrize("shape", list(SHAPES))

@@ -130,3 +130,27 @@ def test_loss_gradient_matches_finite_differences(mass_weight, neg_weight):
     sig = fno.out_scale(x)
     ref = np.mean(((y - t) / sig[:, :, None, None]) ** 2)
     assert fno.loss(y, t, x)[0] == pytest.approx(ref, rel=1e-13)
+
+
+def test_prediction_conserves_the_population_exactly():
+    W, m, L, H, n = 4, 2, 2, 6, 8
+    g = np.random.default_rng(8)
+    params = fno.init_params(2, W, m, L, H)
+    for k in params:
+        params[k] = params[k] + 0.3 * g.standard_normal(params[k].shape)
+    u = g.uniform(0, 1, (3, 5, n, n))
+    u[2, 1:3] *= 1e-5
+    x = fno.make_input(u, np.array([1.5, 3.0, 2.0]), np.array([-1.5, -2.5, -2.0]))
+    y, _ = fno.forward(params, x, W, m, L, H)
+    np.testing.assert_allclose(y.reshape(3, -1).sum(axis=1), u.reshape(3, -1).sum(axis=1), rtol=1e-13)
+    # the raw prediction does not conserve: the correction is doing the work
+    sig = fno.out_scale(x)[:, :, None, None]
+    v = sig * (x[:, :5] + fno.pointwise(params["Q2"], fno.gelu(fno.pointwise(params["Q1"],
+                                                                           _last_hidden(params, x, W, m, L, H),
+                                                                           params["q1"])), params["q2"]))
+    assert np.abs(v.reshape(3, -1).sum(axis=1) - u.reshape(3, -1).sum(axis=1)).max() > 1e-3
+
+
+def _last_hidden(params, x, W, m, L, H):
+    _, cache = fno.forward(params, x, W, m, L, H)
+    return cache[f"h{L}"]

@@ -31,7 +31,7 @@ def trained():
     sur = L.Surrogate(n=N, max_batch=16, **CFG)
     sur.set_params(S.initial_params(CFG["width"], CFG["modes"], CFG["layers"], CFG["hidden"], seed=0))
     hist0 = S.evaluate(sur, X, Y, r0, logd, _val_idx(X.shape[0]), 8)
-    hist = S.train(sur, X, Y, r0, logd, steps=2000, batch=8, lr=1e-3, seed=0, mass_weight=30.0, neg_weight=30.0)
+    hist = S.train(sur, X, Y, r0, logd, steps=2000, batch=8, lr=1e-3, seed=0, neg_weight=30.0)
     return S, sur, X, Y, r0, logd, hist0, hist
 
 
