@@ -359,8 +359,15 @@ int sslbm_fno_train_step(sslbm_fno* f, int batch, const float* x, const float* t
 /* Residual checks of a prediction y against the input state u (both [batch][5][n][n]):
  * residuals[2b] = |sum y - sum u| / sum u (conservation of the total population),
  * residuals[2b+1] = sum max(-y, 0) / sum u (mass below zero).  Then y is projected in
- * place: clamped at zero and rescaled to the input's total.  Synchronises the stream. */
-int sslbm_fno_check_project(sslbm_fno* f, int batch, float* y, const float* u,
+ * place onto the admissible states:
+ *   - with reach > 0, E, I, R and D are set to zero outside the domain of dependence of
+ *     the input's infection: the cells farther than reach (periodic, per axis) from every
+ *     cell where E + I or R + D exceeds 1e-6 of its maximum over the grid (reach = 20 for
+ *     20 steps of the 5-point stencil, which moves information one cell per step);
+ *   - every value is clamped at zero;
+ *   - the state is rescaled to the input's total.
+ * Synchronises the stream. */
+int sslbm_fno_check_project(sslbm_fno* f, int batch, float* y, const float* u, int reach,
                             double* residuals);
 
 #ifdef __cplusplus

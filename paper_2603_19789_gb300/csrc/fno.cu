@@ -471,15 +471,83 @@ __global__ void residual_kernel(const float* __restrict__ y, const float* __rest
 }
 
 // accepted predictions: clamp at zero and rescale to the input's total
-__global__ void project_kernel(float* __restrict__ y, const double* __restrict__ res, int64_t P5) {
+// per scenario, as float bits: scales[2b] = max(E + I), scales[2b+1] = max(R + D) over the grid
+__global__ void support_scales_kernel(const float* __restrict__ u, int* __restrict__ scales, int64_t P) {
   const int64_t b = blockIdx.y;
-  const double pos = res[3 * b] + res[3 * b + 2];  // sum of max(y, 0)
-  const float scale = pos > 0 ? (float)(res[3 * b + 1] / pos) : 1.f;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P5;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const float v = y[b * P5 + t];
-    y[b * P5 + t] = v > 0.f ? v * scale : 0.f;
+  float ei = 0.f, rd = 0.f;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P; t += (int64_t)gridDim.x * blockDim.x) {
+    const float* ub = u + b * 5 * P + t;
+    ei = fmaxf(ei, ub[P] + ub[2 * P]);
+    rd = fmaxf(rd, ub[3 * P] + ub[4 * P]);
   }
+  for (int off = 16; off > 0; off >>= 1) {
+    ei = fmaxf(ei, __shfl_down_sync(0xffffffffu, ei, off));
+    rd = fmaxf(rd, __shfl_down_sync(0xffffffffu, rd, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(scales + 2 * b, __float_as_int(ei));
+    atomicMax(scales + 2 * b + 1, __float_as_int(rd));
+  }
+}
+
+// ind = 1 where the input holds infected (E + I) or removed (R + D) population above a
+// fraction thr of the scenario's maximum, else 0
+__global__ void support_kernel(const float* __restrict__ u, const int* __restrict__ scales,
+                               unsigned char* __restrict__ ind, int B, int64_t P, float thr) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / P, p = t - b * P;
+    const float* ub = u + b * 5 * P + p;
+    const float sei = __int_as_float(scales[2 * b]), srd = __int_as_float(scales[2 * b + 1]);
+    ind[t] = (ub[P] + ub[2 * P] > thr * sei && sei > 0.f) || (ub[3 * P] + ub[4 * P] > thr * srd && srd > 0.f);
+  }
+}
+
+// out = max of in over the periodic window [-r, r] along x (dir 0) or y (dir 1)
+__global__ void dilate_kernel(const unsigned char* __restrict__ in, unsigned char* __restrict__ out, int B, int n,
+                              int r, int dir) {
+  const int64_t P = (int64_t)n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / P;
+    const int p = (int)(t - b * P), y = p / n, x = p - y * n;
+    const unsigned char* ib = in + b * P;
+    unsigned char v = 0;
+    for (int d = -r; d <= r && !v; ++d) {
+      const int q = ((dir ? y : x) + d) % n;
+      const int qq = q < 0 ? q + n : q;
+      v = dir ? ib[(int64_t)qq * n + x] : ib[(int64_t)y * n + qq];
+    }
+    out[t] = v;
+  }
+}
+
+// projection: E, I, R, D set to zero outside the mask (when given), every value clamped at
+// zero; sums[b] += the projected total (the rescaling's denominator)
+__global__ void mask_clamp_kernel(float* __restrict__ y, const unsigned char* __restrict__ mask,
+                                  double* __restrict__ sums, int64_t P) {
+  const int64_t b = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 5 * P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / P, p = t - c * P;
+    float v = y[b * 5 * P + t];
+    if (mask && c > 0 && !mask[b * P + p]) v = 0.f;
+    v = v > 0.f ? v : 0.f;
+    y[b * 5 * P + t] = v;
+    acc += v;
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(sums + b, acc);
+}
+
+// y *= sum u / sum y (res[3b+1] = sum u)
+__global__ void rescale_kernel(float* __restrict__ y, const double* __restrict__ res, const double* __restrict__ sums,
+                               int64_t P5) {
+  const int64_t b = blockIdx.y;
+  const float scale = sums[b] > 0.0 ? (float)(res[3 * b + 1] / sums[b]) : 1.f;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P5; t += (int64_t)gridDim.x * blockDim.x)
+    y[b * P5 + t] *= scale;
 }
 
 // ---- parameter layout ------------------------------------------------------------------
@@ -520,7 +588,7 @@ int make_param_layout(const sslbm_fno_config* c, Layout* L) {
 struct Buffers {
   size_t total;
   size_t theta, theta16, grad, mom, vel, dft, hcat, zcat, zp, p, f32a, f32b, f32p, h1, tt, hat, dg, dd, smax, csum,
-      loss, res;
+      mask, mscale, loss, res;
 };
 
 size_t rup(size_t v) { return (v + 255) / 256 * 256; }
@@ -549,6 +617,8 @@ void make_buffers(const Layout& L, Buffers* b) {
   b->dd = take(B * 5 * P * 4);
   b->smax = take(B * 4);
   b->csum = take(B * 2 * 8);
+  b->mask = take(B * P * 2);
+  b->mscale = take(B * 2 * 4);
   b->loss = take(8);
   b->res = take(B * 3 * 8);
   b->total = o;
@@ -1089,19 +1159,39 @@ int sslbm_fno_train_step(sslbm_fno* f, int batch, const float* x, const float* t
   return SSLBM_OK;
 }
 
-int sslbm_fno_check_project(sslbm_fno* f, int batch, float* y, const float* u, double* residuals) {
+int sslbm_fno_check_project(sslbm_fno* f, int batch, float* y, const float* u, int reach, double* residuals) {
   int st = check_batch(f, batch);
   if (st) return st;
   if (!y || !u || !residuals) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  if (reach < 0) return err(SSLBM_ERR_BAD_ARG, "reach %d < 0", reach);
   DevGuard dg(f->device);
   double* res = f->at<double>(f->bu.res);
+  double* sums = f->at<double>(f->bu.csum);
   CK(cudaMemsetAsync(res, 0, (size_t)batch * 3 * 8, f->stream), "zero residuals");
-  const int64_t P5 = 5 * f->L.P;
+  CK(cudaMemsetAsync(sums, 0, (size_t)batch * 8, f->stream), "zero sums");
+  const int64_t P = f->L.P, P5 = 5 * P;
   dim3 grid((unsigned)std::min<int64_t>(64, (P5 + kThreads - 1) / kThreads), batch);
   residual_kernel<<<grid, kThreads, 0, f->stream>>>(y, u, res, P5);
   CK(cudaGetLastError(), "residual");
-  project_kernel<<<grid, kThreads, 0, f->stream>>>(y, res, P5);
-  CK(cudaGetLastError(), "project");
+  unsigned char* mask = nullptr;
+  if (reach > 0) {
+    const int r = std::min(reach, f->L.n / 2);
+    unsigned char* ind = f->at<unsigned char>(f->bu.mask);
+    mask = ind + (size_t)batch * P;
+    int* scales = f->at<int>(f->bu.mscale);
+    CK(cudaMemsetAsync(scales, 0, (size_t)batch * 2 * 4, f->stream), "zero scales");
+    dim3 g1((unsigned)std::min<int64_t>(64, (P + kThreads - 1) / kThreads), batch);
+    support_scales_kernel<<<g1, kThreads, 0, f->stream>>>(u, scales, P);
+    support_kernel<<<blocks_for((int64_t)batch * P), kThreads, 0, f->stream>>>(u, scales, ind, batch, P, 1e-6f);
+    dilate_kernel<<<blocks_for((int64_t)batch * P), kThreads, 0, f->stream>>>(ind, mask, batch, f->L.n, r, 0);
+    dilate_kernel<<<blocks_for((int64_t)batch * P), kThreads, 0, f->stream>>>(mask, ind, batch, f->L.n, r, 1);
+    mask = ind;
+    CK(cudaGetLastError(), "support mask");
+  }
+  mask_clamp_kernel<<<grid, kThreads, 0, f->stream>>>(y, mask, sums, P);
+  CK(cudaGetLastError(), "clamp");
+  rescale_kernel<<<grid, kThreads, 0, f->stream>>>(y, res, sums, P5);
+  CK(cudaGetLastError(), "rescale");
   std::vector<double> r((size_t)batch * 3);
   CK(cudaMemcpyAsync(r.data(), res, r.size() * 8, cudaMemcpyDeviceToHost, f->stream), "residual copy");
   CK(cudaStreamSynchronize(f->stream), "sync");

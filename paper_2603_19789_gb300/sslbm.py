@@ -144,7 +144,7 @@ def load(path: str = LIB_PATH):
             "sslbm_fno_fused": (i32, [_vp]),
             "sslbm_fno_train_step": (i32, [_vp, i32, _vp, _vp, _vp, _vp, ctypes.c_float,
                                            ctypes.POINTER(ctypes.c_double)]),
-            "sslbm_fno_check_project": (i32, [_vp, i32, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
+            "sslbm_fno_check_project": (i32, [_vp, i32, _vp, _vp, i32, ctypes.POINTER(ctypes.c_double)]),
             "sslbm_diagnostics_noalloc": (i32, [_vp, i32, i64, i64, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_double), _vp]),
         }
@@ -598,9 +598,10 @@ def sslbm_fno_train_step(f, batch, x, target, y_scratch, dy_scratch, lr, want_lo
     return float(loss.value) if want_loss else None
 
 
-def sslbm_fno_check_project(f, batch, y, u):
+def sslbm_fno_check_project(f, batch, y, u, reach=0):
     res = (ctypes.c_double * (2 * batch))()
-    _check(load().sslbm_fno_check_project(f, int(batch), _dptr(y), _dptr(u), res), "sslbm_fno_check_project")
+    _check(load().sslbm_fno_check_project(f, int(batch), _dptr(y), _dptr(u), int(reach), res),
+           "sslbm_fno_check_project")
     return np.array(res[:]).reshape(batch, 2)
 
 
@@ -679,5 +680,5 @@ class Surrogate:
         B = x.shape[0]
         return sslbm_fno_train_step(self.f, B, x, target, self._y[:B], self._dy[:B], lr, want_loss)
 
-    def check_project(self, y, u):
-        return sslbm_fno_check_project(self.f, y.shape[0], y, u)
+    def check_project(self, y, u, reach=0):
+        return sslbm_fno_check_project(self.f, y.shape[0], y, u, reach)

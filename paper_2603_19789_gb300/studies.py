@@ -94,22 +94,28 @@ def precision_study(n: int = 4096, steps: int = 50000, checkpoints: int = 6, see
 
 
 def surrogate_study(n=256, trajectories=2000, snapshots=10, horizon=2000, train_steps=20000, batch=16,
-                    lr=1e-3, width=32, modes=12, layers=4, hidden=64, scenarios=64, rollout_steps=100):
+                    lr=1e-3, width=32, modes=12, layers=4, hidden=64, scenarios=64, rollout_steps=100,
+                    params=None):
     """Generate trajectories with the ensemble kernel, train the surrogate on the GPU, and
-    roll it out with residual checks and SSLBM fallback, judged against the SSLBM."""
+    roll it out with residual checks and SSLBM fallback, judged against the SSLBM.  With
+    params (a flat FP32 parameter vector) the training is skipped."""
     import torch
 
     from . import surrogate as S
-    t0 = time.perf_counter()
-    X, Y, r0, logd = S.generate_pairs(n, trajectories, snapshots, horizon)
-    t_data = time.perf_counter() - t0
     sur = L.Surrogate(n=n, width=width, modes=modes, layers=layers, hidden=hidden,
                       max_batch=max(batch, scenarios))
-    sur.set_params(S.initial_params(width, modes, layers, hidden))
-    hist = S.train(sur, X, Y, r0, logd, steps=train_steps, batch=batch, lr=lr)
+    t_data, hist = 0.0, None
+    if params is None:
+        t0 = time.perf_counter()
+        X, Y, r0, logd = S.generate_pairs(n, trajectories, snapshots, horizon)
+        t_data = time.perf_counter() - t0
+        sur.set_params(S.initial_params(width, modes, layers, hidden))
+        hist = S.train(sur, X, Y, r0, logd, steps=train_steps, batch=batch, lr=lr)
+        del X, Y
+        torch.cuda.empty_cache()
+    else:
+        sur.set_params(np.asarray(params, dtype=np.float32))
     theta = sur.get_params()
-    del X, Y
-    torch.cuda.empty_cache()
     roll = S.rollout(sur, n=n, scenarios=scenarios, steps=rollout_steps)
     strict = S.rollout(sur, n=n, scenarios=scenarios, steps=rollout_steps, neg_threshold=0.0, reference=False)
     roll.pop("state")
@@ -132,12 +138,14 @@ def main(argv=None):
     ap.add_argument("--checkpoints", type=int, default=6)
     ap.add_argument("--trajectories", type=int, default=2000)
     ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--params", default=None, help="trained parameters (.npy): skip the training")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     from . import build
     build.build()
     if args.study == "surrogate":
-        res, theta = surrogate_study(n=args.n or 256, trajectories=args.trajectories, train_steps=args.train_steps)
+        res, theta = surrogate_study(n=args.n or 256, trajectories=args.trajectories, train_steps=args.train_steps,
+                                     params=np.load(args.params) if args.params else None)
         text = json.dumps(res, indent=1)
         if args.out:
             with open(args.out, "w") as fh:

@@ -13,11 +13,13 @@ prediction y is checked against the input state u: the conservation residual
 whose conservation residual exceeds the threshold (1e-4), or whose negative mass exceeds
 neg_threshold (by default the same 1e-4: negatives that the projection below removes
 while moving the state by no more than the conservation tolerance), takes the SSLBM's 20
-steps instead (the fallback, run by the ensemble kernel); accepted predictions are
-projected onto the admissible set (clamped at zero, rescaled to the input's total).  With
-neg_threshold=0 any negative value triggers the fallback.  The rollout also counts the
-scenario-steps with any negative value at all.  The SSLBM also judges the rollout: a
-reference ensemble advanced in lock step gives the error every ten surrogate steps.
+steps instead (the fallback, run by the ensemble kernel).  Accepted predictions are
+projected onto the admissible set: E, I, R and D zeroed outside the domain of dependence
+of the input's infection (20 steps of the 5-point stencil move information at most 20
+cells), clamped at zero, rescaled to the input's total.  With neg_threshold=0 any negative
+value triggers the fallback.  The rollout also counts the scenario-steps with any
+negative value at all.  The SSLBM also judges the rollout: a reference ensemble advanced
+in lock step gives the error every ten surrogate steps.
 """
 from __future__ import annotations
 
@@ -151,7 +153,7 @@ def evaluate(sur, X, Y, r0, logd, idx, batch):
 
 
 def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_threshold=1e-4,
-            reference=True, err_every=10):
+            reference=True, err_every=10, reach=K_STEPS):
     """Surrogate rollout with residual checks and SSLBM fallback.  Returns timings, the
     fallback count and (with reference=True) the error against an SSLBM run in lock step."""
     import torch
@@ -179,7 +181,7 @@ def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_th
         t0 = time.perf_counter()
         x = sur.make_input(u, tr0, tlogd)
         y = sur.infer(x)
-        res = sur.check_project(y, u)
+        res = sur.check_project(y, u, reach)
         any_negative += int((res[:, 1] > 0).sum())
         fail_mass += int((res[:, 0] > threshold).sum())
         fail_neg += int((res[:, 1] > neg_threshold).sum())
@@ -203,7 +205,15 @@ def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_th
                 d2 = ((u.double() - r.double()) ** 2).sum(dim=(0, 2, 3))
                 rms = (d2 / (scenarios * n * n)).sqrt().cpu().numpy()
                 rel = (d2 / (r.double() ** 2).sum(dim=(0, 2, 3))).sqrt().cpu().numpy()
-                err_hist.append({"step": step + 1, "rms": rms.tolist(), "rel_l2": rel.tolist()})
+                # the epidemic curves: each compartment's share of the population, per scenario
+                fu = u.double().mean(dim=(2, 3)) / u.double().mean(dim=(2, 3)).sum(dim=1, keepdim=True)
+                fr = r.double().mean(dim=(2, 3)) / r.double().mean(dim=(2, 3)).sum(dim=1, keepdim=True)
+                frac = (fu - fr).abs()
+                peak = (u[:, 2].amax(dim=(1, 2)).double() / r[:, 2].amax(dim=(1, 2)).double().clamp_min(1e-30) - 1).abs()
+                err_hist.append({"step": step + 1, "rms": rms.tolist(), "rel_l2": rel.tolist(),
+                                 "share_abs_err_mean": frac.mean(dim=0).cpu().numpy().tolist(),
+                                 "share_abs_err_max": frac.amax(dim=0).cpu().numpy().tolist(),
+                                 "peak_I_rel_err_median": float(peak.median())})
                 last_ref = r
     drift = float(((u.double().sum(dim=(1, 2, 3)) - total0).abs() / total0).max())
     fb.close()

@@ -187,3 +187,33 @@ def test_check_project_residuals_and_projection():
     assert out.min() >= 0
     np.testing.assert_allclose(out.astype(np.float64).reshape(B, -1).sum(axis=1),
                                u.astype(np.float64).reshape(B, -1).sum(axis=1), rtol=1e-5)
+
+
+def test_projection_zeroes_outside_the_domain_of_dependence():
+    """With reach r, E, I, R, D of the prediction vanish farther than r cells (per axis,
+    periodic) from the input's infected or removed cells; inside they are only rescaled."""
+    import torch
+    cfg, n = _cfg("generic")
+    s = L.Surrogate(n=n, width=cfg["W"], modes=cfg["m"], layers=cfg["L"], hidden=cfg["H"], max_batch=B)
+    g = np.random.default_rng(9)
+    u = np.zeros((B, 5, n, n), np.float32)
+    u[:, 0] = 1.0
+    u[0, 2, 3:5, 30:32] = 1e-3          # sample 0: infection near the periodic edge
+    u[1, 3, 20, 10] = 0.2               # sample 1: removed population only
+    y = u + np.abs(g.normal(0, 1e-4, u.shape)).astype(np.float32)
+    ty = torch.from_numpy(y).cuda()
+    r = 4
+    s.check_project(ty, torch.from_numpy(u).cuda(), reach=r)
+    out = ty.cpu().numpy().astype(np.float64)
+    for b, (ys, xs) in enumerate([(range(3, 5), range(30, 32)), ([20], [10])]):
+        inside = np.zeros((n, n), bool)
+        for yy in ys:
+            for xx in xs:
+                for dy in range(-r, r + 1):
+                    inside[(yy + dy) % n, [(xx + dx) % n for dx in range(-r, r + 1)]] = True
+        assert np.all(out[b, 1:, ~inside] == 0.0)
+        assert np.all(out[b, 1:, inside] > 0.0)
+        np.testing.assert_allclose(out[b].sum(), u[b].astype(np.float64).sum(), rtol=1e-5)
+        # S is untouched by the mask (only rescaled)
+        ratio = out[b, 0] / y[b, 0]
+        np.testing.assert_allclose(ratio, ratio.mean(), rtol=1e-6)
