@@ -153,13 +153,8 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2603_19789_gb300.decomp import max_over_ranks as _max
+    return _max(x, world, device="cuda")
 
 
 def cpu_oracle_glups(state64, wl, budget_s: float = 12.0, rows: int | None = None):

@@ -72,6 +72,8 @@ constexpr float kScaleFloor = 1e-12f;   // infection scale of a scenario without
 
 // sigma of E and I from the scale channel e of the input: s' = 10^(4e - 4)
 __device__ __forceinline__ float scale_from_e(float e) { return exp10f(4.f * e - 4.f); }
+// blocks per sample of the per-sample kernels (grid.y = sample)
+unsigned rows_grid(int64_t P) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(32, (P + kThreads - 1) / kThreads)); }
 unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads > 1048576 ? 1048576 : (n + kThreads - 1) / kThreads); }
 
 // ---- elementwise / small kernels ---------------------------------------------------------
@@ -148,59 +150,127 @@ __global__ void output_kernel(float* __restrict__ y, const float* __restrict__ q
   }
 }
 
-// per sample: sums[2b] += sum_{c,p} a[b, c, p] w[b, c, p], sums[2b+1] += sum u[b, c, p], with
-// u_c = sigma_c x_c the input state and w = u (the population of the raw prediction a) or
-// w = 1 (a = dy: the backward pass's sum of dy u uses a = dy, w = u)
-__global__ void state_sums_kernel(const float* __restrict__ a, const float* __restrict__ x,
-                                  double* __restrict__ sums, int64_t P, int weight_by_u) {
-  const int64_t b = blockIdx.y;
-  const float sg = scale_from_e(x[(b * kCin + 7) * P]);
-  double sa = 0.0, su = 0.0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 5 * P;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(t / P);
-    const float u = (c == 1 || c == 2) ? sg * x[b * kCin * P + t] : x[b * kCin * P + t];
-    const float av = a[b * 5 * P + t];
-    sa += weight_by_u ? (double)av * u : (double)av;
-    su += u;
-  }
+// Block-wide sums of FP64 values (blockDim.x a multiple of 32, <= 1024); thread 0 adds them
+// to out[] (shared memory scratch of 64 doubles)
+__device__ __forceinline__ void block_add2(double a, double b, double* out, double* sh) {
   for (int off = 16; off > 0; off >>= 1) {
-    sa += __shfl_down_sync(0xffffffffu, sa, off);
-    su += __shfl_down_sync(0xffffffffu, su, off);
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
   }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(sums + 2 * b, sa);
-    atomicAdd(sums + 2 * b + 1, su);
+    sh[w] = a;
+    sh[32 + w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    a = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    b = threadIdx.x < nw ? sh[32 + threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, off);
+      b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    if (threadIdx.x == 0) {
+      atomicAdd(out, a);
+      atomicAdd(out + 1, b);
+    }
   }
 }
 
+__device__ __forceinline__ void block_add1(double a, double* out, double* sh) {
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) sh[w] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    a = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (threadIdx.x == 0) atomicAdd(out, a);
+  }
+}
+
+// this block's share (strided over gridDim.x) of the sum of a plane of P values: FP32
+// partials per thread, float4 loads when aligned
+__device__ __forceinline__ float plane_sum(const float* __restrict__ a, int64_t P) {
+  float acc = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((P & 3) == 0 && (reinterpret_cast<uintptr_t>(a) & 15) == 0) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    for (int64_t i = i0; i < P / 4; i += stride) {
+      const float4 v = a4[i];
+      acc += (v.x + v.y) + (v.z + v.w);
+    }
+  } else {
+    for (int64_t i = i0; i < P; i += stride) acc += a[i];
+  }
+  return acc;
+}
+
+// per sample b = blockIdx.y: sums[2b] += sum_{c,p} a[b, c, p] w[b, c, p], sums[2b+1] += sum u[b, c, p]
+// with u_c = sigma_c x_c the input state and w = 1 (a = the raw prediction v) or w = u
+// (a = dy: the backward pass's sum of dy u)
+__global__ void state_sums_kernel(const float* __restrict__ a, const float* __restrict__ x,
+                                  double* __restrict__ sums, int64_t P, int weight_by_u) {
+  __shared__ double sh[64];
+  const int64_t b = blockIdx.y;
+  const float sg = scale_from_e(x[(b * kCin + 7) * P]);
+  double sa = 0.0, su = 0.0;
+  for (int c = 0; c < 5; ++c) {
+    const float f = (c == 1 || c == 2) ? sg : 1.f;
+    const float* ab = a + (b * 5 + c) * P;
+    const float* xb = x + (b * kCin + c) * P;
+    if (weight_by_u) {
+      float acc = 0.f;
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fmaf(ab[i], xb[i], acc);
+      sa += (double)f * acc;
+    } else {
+      sa += plane_sum(ab, P);
+    }
+    su += (double)f * plane_sum(xb, P);
+  }
+  block_add2(sa, su, sums + 2 * b, sh);
+}
+
 // y = v - u kappa, kappa = (sum v - sum u) / sum u: the prediction conserves the population
+// (b = blockIdx.y)
 __global__ void conserve_kernel(float* __restrict__ y, const float* __restrict__ x, const double* __restrict__ sums,
-                                int B, int64_t P) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * 5 * P;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = t / (5 * P), r = t - b * 5 * P;
-    const int c = (int)(r / P);
+                                int64_t P) {
+  __shared__ float kap;
+  const int64_t b = blockIdx.y;
+  if (threadIdx.x == 0) {
     const double su = sums[2 * b + 1];
-    const float kappa = su != 0.0 ? (float)((sums[2 * b] - su) / su) : 0.f;
-    const float xv = x[b * kCin * P + r];
-    const float u = (c == 1 || c == 2) ? scale_from_e(x[(b * kCin + 7) * P]) * xv : xv;
-    y[t] = fmaf(-u, kappa, y[t]);
+    kap = su != 0.0 ? (float)((sums[2 * b] - su) / su) : 0.f;
+  }
+  __syncthreads();
+  const float kappa = kap, sg = scale_from_e(x[(b * kCin + 7) * P]);
+  for (int c = 0; c < 5; ++c) {
+    const float k = (c == 1 || c == 2) ? sg * kappa : kappa;
+    float* yb = y + (b * 5 + c) * P;
+    const float* xb = x + (b * kCin + c) * P;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
+      yb[i] = fmaf(-xb[i], k, yb[i]);
   }
 }
 
 // dd = sigma (dy - lambda_b), lambda_b = sum(dy u) / sum u: the derivative with respect to
-// delta = Q2 p + q2 through y = v - u kappa and v_c = sigma_c (x_c + delta_c)
+// delta = Q2 p + q2 through y = v - u kappa and v_c = sigma_c (x_c + delta_c)  (b = blockIdx.y)
 __global__ void scale_dy_kernel(const float* __restrict__ dy, const float* __restrict__ x,
-                                const double* __restrict__ sums, float* __restrict__ dd, int B, int64_t P) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * 5 * P;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = t / (5 * P);
-    const int c = (int)((t - b * 5 * P) / P);
+                                const double* __restrict__ sums, float* __restrict__ dd, int64_t P) {
+  __shared__ float lm;
+  const int64_t b = blockIdx.y;
+  if (threadIdx.x == 0) {
     const double su = sums[2 * b + 1];
-    const float lam = su != 0.0 ? (float)(sums[2 * b] / su) : 0.f;
-    const float g = dy[t] - lam;
-    dd[t] = (c == 1 || c == 2) ? scale_from_e(x[(b * kCin + 7) * P]) * g : g;
+    lm = su != 0.0 ? (float)(sums[2 * b] / su) : 0.f;
+  }
+  __syncthreads();
+  const float lam = lm, sg = scale_from_e(x[(b * kCin + 7) * P]);
+  for (int c = 0; c < 5; ++c) {
+    const float f = (c == 1 || c == 2) ? sg : 1.f;
+    const float* g = dy + (b * 5 + c) * P;
+    float* d = dd + (b * 5 + c) * P;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
+      d[i] = f * (g[i] - lam);
   }
 }
 
@@ -425,52 +495,41 @@ __global__ void infection_scale_kernel(const float* __restrict__ u, int* __restr
   if ((threadIdx.x & 31) == 0) atomicMax(smax + b, __float_as_int(mx));
 }
 
-// x[b] = [S, E/s', I/s', R, D, (R0 - 2.6)/1.4, log10(d) + 2, e]
+// x[b] = [S, E/s', I/s', R, D, (R0 - 2.6)/1.4, log10(d) + 2, e]   (b = blockIdx.y)
 __global__ void make_input_kernel(const float* __restrict__ u, const float* __restrict__ r0,
                                   const float* __restrict__ logd, const int* __restrict__ smax,
-                                  float* __restrict__ x, int B, int64_t P) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * kCin * P;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = t / (kCin * P), r = t - b * kCin * P;
-    const int c = (int)(r / P);
-    const float e = (log10f(fmaxf(__int_as_float(smax[b]), kScaleFloor)) + 4.f) * 0.25f;
-    float v;
-    if (c < 5) {
-      v = u[b * 5 * P + r];
-      if (c == 1 || c == 2) v = v / scale_from_e(e);
-    } else {
-      v = c == 5 ? (r0[b] - 2.6f) / 1.4f : (c == 6 ? logd[b] + 2.f : e);
-    }
-    x[t] = v;
+                                  float* __restrict__ x, int64_t P) {
+  const int64_t b = blockIdx.y;
+  const float e = (log10f(fmaxf(__int_as_float(smax[b]), kScaleFloor)) + 4.f) * 0.25f;
+  const float sp = scale_from_e(e);
+  const float c5 = (r0[b] - 2.6f) / 1.4f, c6 = logd[b] + 2.f;
+  for (int c = 0; c < kCin; ++c) {
+    float* xb = x + (b * kCin + c) * P;
+    const float* ub = u + (b * 5 + (c < 5 ? c : 0)) * P;
+    const float cv = c == 5 ? c5 : (c == 6 ? c6 : e);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
+      xb[i] = c < 5 ? ((c == 1 || c == 2) ? ub[i] / sp : ub[i]) : cv;
   }
 }
 
 // per scenario: totals of the raw prediction and of the input state, and the mass clipped
-// below zero -> res[b] = {sum y, sum u, sum max(-y, 0)} in double
+// below zero -> res[3b..3b+2] = {sum y, sum u, sum max(-y, 0)} in double (b = blockIdx.y)
 __global__ void residual_kernel(const float* __restrict__ y, const float* __restrict__ u,
                                 double* __restrict__ res, int64_t P5) {
+  __shared__ double sh[64];
   const int64_t b = blockIdx.y;
-  double sy = 0.0, su = 0.0, sn = 0.0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P5;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  float sy = 0.f, su = 0.f, sn = 0.f;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P5; t += (int64_t)gridDim.x * blockDim.x) {
     const float yv = y[b * P5 + t];
     sy += yv;
     su += u[b * P5 + t];
     sn += yv < 0.f ? -yv : 0.f;
   }
-  for (int off = 16; off > 0; off >>= 1) {
-    sy += __shfl_down_sync(0xffffffffu, sy, off);
-    su += __shfl_down_sync(0xffffffffu, su, off);
-    sn += __shfl_down_sync(0xffffffffu, sn, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(res + 3 * b, sy);
-    atomicAdd(res + 3 * b + 1, su);
-    atomicAdd(res + 3 * b + 2, sn);
-  }
+  block_add2(sy, su, res + 3 * b, sh);
+  __syncthreads();
+  block_add1(sn, res + 3 * b + 2, sh);
 }
 
-// accepted predictions: clamp at zero and rescale to the input's total
 // per scenario, as float bits: scales[2b] = max(E + I), scales[2b+1] = max(R + D) over the grid
 __global__ void support_scales_kernel(const float* __restrict__ u, int* __restrict__ scales, int64_t P) {
   const int64_t b = blockIdx.y;
@@ -526,26 +585,31 @@ __global__ void dilate_kernel(const unsigned char* __restrict__ in, unsigned cha
 // zero; sums[b] += the projected total (the rescaling's denominator)
 __global__ void mask_clamp_kernel(float* __restrict__ y, const unsigned char* __restrict__ mask,
                                   double* __restrict__ sums, int64_t P) {
+  __shared__ double sh[64];
   const int64_t b = blockIdx.y;
-  double acc = 0.0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 5 * P;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = t / P, p = t - c * P;
-    float v = y[b * 5 * P + t];
-    if (mask && c > 0 && !mask[b * P + p]) v = 0.f;
-    v = v > 0.f ? v : 0.f;
-    y[b * 5 * P + t] = v;
-    acc += v;
+  float acc = 0.f;
+  for (int c = 0; c < 5; ++c) {
+    float* yb = y + (b * 5 + c) * P;
+    const unsigned char* mb = mask && c > 0 ? mask + b * P : nullptr;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+      float v = yb[p];
+      if (mb && !mb[p]) v = 0.f;
+      v = v > 0.f ? v : 0.f;
+      yb[p] = v;
+      acc += v;
+    }
   }
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) atomicAdd(sums + b, acc);
+  block_add1(acc, sums + b, sh);
 }
 
 // y *= sum u / sum y (res[3b+1] = sum u)
 __global__ void rescale_kernel(float* __restrict__ y, const double* __restrict__ res, const double* __restrict__ sums,
                                int64_t P5) {
+  __shared__ float scl;
   const int64_t b = blockIdx.y;
-  const float scale = sums[b] > 0.0 ? (float)(res[3 * b + 1] / sums[b]) : 1.f;
+  if (threadIdx.x == 0) scl = sums[b] > 0.0 ? (float)(res[3 * b + 1] / sums[b]) : 1.f;
+  __syncthreads();
+  const float scale = scl;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P5; t += (int64_t)gridDim.x * blockDim.x)
     y[b * P5 + t] *= scale;
 }
@@ -905,7 +969,7 @@ int conserve(sslbm_fno* f, int B, const float* x, float* y) {
   dim3 grid((unsigned)std::min<int64_t>(64, (5 * P + kThreads - 1) / kThreads), B);
   state_sums_kernel<<<grid, kThreads, 0, f->stream>>>(y, x, sums, P, 0);
   CK(cudaGetLastError(), "population sums");
-  conserve_kernel<<<blocks_for((int64_t)B * 5 * P), kThreads, 0, f->stream>>>(y, x, sums, B, P);
+  conserve_kernel<<<dim3(rows_grid(P), B), kThreads, 0, f->stream>>>(y, x, sums, P);
   CK(cudaGetLastError(), "conservation");
   return SSLBM_OK;
 }
@@ -935,7 +999,7 @@ int backward_impl(sslbm_fno* f, int B, const float* x, const float* dy_out) {
   dim3 sgrid((unsigned)std::min<int64_t>(64, (5 * P + kThreads - 1) / kThreads), B);
   state_sums_kernel<<<sgrid, kThreads, 0, f->stream>>>(dy_out, x, sums, P, 1);
   CK(cudaGetLastError(), "population sums");
-  scale_dy_kernel<<<blocks_for((int64_t)B * 5 * P), kThreads, 0, f->stream>>>(dy_out, x, sums, dy, B, P);
+  scale_dy_kernel<<<dim3(rows_grid(P), B), kThreads, 0, f->stream>>>(dy_out, x, sums, dy, P);
   CK(cudaGetLastError(), "output scale");
   if ((st = channel_sum(f, dy, g + L.off_q2, B, 5))) return st;
   if ((st = weight_grad(f, dy, 5, f->at<bf16>(f->bu.p), 1, L.H, g + L.off_Q2, B, "dQ2"))) return st;
@@ -1072,8 +1136,7 @@ int sslbm_fno_make_input(sslbm_fno* f, int batch, const float* u, const float* r
   dim3 grid((unsigned)std::min<int64_t>(64, (2 * f->L.P + kThreads - 1) / kThreads), batch);
   infection_scale_kernel<<<grid, kThreads, 0, f->stream>>>(u, smax, f->L.P);
   CK(cudaGetLastError(), "infection scale");
-  make_input_kernel<<<blocks_for((int64_t)batch * kCin * f->L.P), kThreads, 0, f->stream>>>(u, r0, logd, smax, x, batch,
-                                                                                          f->L.P);
+  make_input_kernel<<<dim3(rows_grid(f->L.P), batch), kThreads, 0, f->stream>>>(u, r0, logd, smax, x, f->L.P);
   CK(cudaGetLastError(), "make input");
   return SSLBM_OK;
 }
