@@ -242,6 +242,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the ensemble measurement")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate kernel timing")
     ap.add_argument("--ens-scenarios", type=int, default=512, help="ensemble size (profiling cases)")
     ap.add_argument("--ens-steps", type=int, default=5000, help="ensemble steps (profiling cases)")
     ap.add_argument("--ens-tiling", default="", help="depth,seg_rows instead of the autotuner")
@@ -308,6 +309,10 @@ def main():
         ens = ensemble_timing(L, torch, stream, n_scen=args.ens_scenarios, steps=args.ens_steps,
                               tiling=tiling)
 
+    sur = None
+    if not args.no_surrogate and rank == 0:
+        sur = surrogate_timing(L, torch, stream, hbm)
+
     e2e = None
     if not args.no_e2e:
         e2e = e2e_timing(L, torch, s, state32, stream, world)
@@ -349,6 +354,7 @@ def main():
             "diagnostics": {"total_population": float(tot.sum()), "peak_I": peak_I},
             "extras": extras,
             "ensemble": ens,
+            "surrogate": sur,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -425,6 +431,47 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
     out["bgk_fp32_glups"] = g
     out["bgk_fp32_hbm_frac"] = BGK_BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm
     return out
+
+
+def surrogate_timing(L, torch, stream, hbm, batch=64, n=256, reps=10):
+    """The learned surrogate's kernels at the rollout's batch (64 scenarios, 256 x 256): one
+    surrogate step = make_input + inference + residual check/projection, with seeded initial
+    parameters (the time does not depend on their values).  Without fallbacks a step
+    advances every scenario by 20 lattice steps."""
+    from paper_2603_19789_gb300 import surrogate as S
+    sur = L.Surrogate(n=n, max_batch=batch)
+    sur.set_params(S.initial_params())
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    u = torch.rand((batch, 5, n, n), device="cuda", generator=g)
+    r0 = torch.full((batch,), 2.6, device="cuda")
+    ld = torch.full((batch,), -2.0, device="cuda")
+    x = sur.make_input(u, r0, ld)
+    y = sur.infer(x)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    infer_ms = timed(lambda: sur.infer(x, y))
+    step_ms = timed(lambda: (sur.make_input(u, r0, ld), sur.infer(x, y), sur.check_project(y, u)))
+    flops = batch * S.forward_flops(n)
+    nbytes = batch * S.forward_bytes(n)
+    sur.close()
+    return {"batch": batch, "n": n, "params": S.initial_params().size, "fused": True,
+            "infer_ms": infer_ms, "gflop_per_inference": flops / 1e9, "tflops": flops / (infer_ms * 1e-3) / 1e12,
+            "hbm_bytes_per_inference": nbytes, "hbm_frac": nbytes / (infer_ms * 1e-3) / 1e9 / hbm,
+            "surrogate_step_ms": step_ms,
+            "scenario_steps_per_s_without_fallback": batch * 20 / (step_ms * 1e-3),
+            "note": "trained rollout with checks, fallbacks and the SSLBM judge: studies.py surrogate"}
 
 
 def ensemble_timing(L, torch, stream, n_scen=512, steps=5000, err_scen=6, fp64_steps=40, tiling=None):

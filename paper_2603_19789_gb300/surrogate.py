@@ -34,6 +34,34 @@ from . import sslbm as L
 K_STEPS = 20
 
 
+def forward_flops(n=256, width=32, modes=12, layers=4, hidden=64, cin=8):
+    """Floating-point operations of one forward pass of one sample, from the layer sizes
+    (multiply-adds count 2): lift, per layer the transforms along x and y and their
+    inverses plus the channel map, the complex mode mixing, and the projection MLP."""
+    P, W, m, H = n * n, width, modes, hidden
+    lift = 2 * cin * W * P
+    per_layer = (2 * W * P * 4 * m            # along x: h Fx
+                 + 2 * W * 2 * m * n * 4 * m  # along y: Fy H1
+                 + 8 * W * W * 2 * m * m      # complex mixing of the 2m x m modes
+                 + 2 * W * n * 2 * m * 4 * m  # inverse along y: Fyi U
+                 + 2 * W * (W + 4 * m) * P)   # channel map + inverse along x: [B | G1] [h ; Fxi]
+    proj = 2 * H * W * P + 2 * 5 * H * P
+    return lift + layers * per_layer + proj
+
+
+def forward_bytes(n=256, width=32, modes=12, layers=4, cin=8):
+    """HBM bytes one sample's fused inference must move: the input, each layer's BF16
+    activations in and out, the transforms' BF16 rows (H1, G1) and the FP32 output; the
+    spectral weights and modes (a few MB for the whole batch) stay in L2."""
+    P, W, m = n * n, width, modes
+    act = 2 * W * P                 # one BF16 activation field
+    rows = 2 * W * n * 4 * m        # one BF16 H1 or G1 array
+    lift = 4 * cin * P + act + rows
+    mid = 2 * rows + act + act + rows       # along y reads H1, inverse writes G1; row kernel: h, G1 in; h, H1 out
+    last = 2 * rows + act + 4 * 5 * P + 4 * 5 * P   # G1 written/read, h in, x[:5] in, y out
+    return lift + (layers - 1) * mid + last
+
+
 def initial_params(width=32, modes=12, layers=4, hidden=64, seed=0):
     """Seeded starting point for training, in the flat FP32 parameter order of
     sslbm_fno_set_params: dense maps uniform in +-1/sqrt(fan_in), spectral weights uniform
