@@ -43,6 +43,7 @@ LATTICE_STEPS_PER_STEP = 100
 BYTES_PER_CELL_FP32 = 40  # read + write of five FP32 planes per launch
 BYTES_PER_CELL_FP64 = 80
 BGK_BYTES_PER_CELL_FP32 = 168  # 20 populations + D, read and write
+FD4_PLANES_PER_CELL = 85  # RK4 stage kernels: 15 + 25 + 25 + 20 plane reads and writes per step
 
 
 PIPE_SOURCES = ("paper_2603_19789_gb300/csrc/sslbm_pipe.cuh", "paper_2603_19789_gb300/csrc/sslbm_internal.cuh",
@@ -430,6 +431,24 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
     g, ms = glups_of(L.FP32, 20, 2, schemes=L.WANT_BGK, bgk=True)
     out["bgk_fp32_glups"] = g
     out["bgk_fp32_hbm_frac"] = BGK_BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm
+    # the fourth-order finite-difference reference (RK4): four stage kernels per step that
+    # move 85 planes per cell (stage states, slope sum and u, read and written)
+    for prec, name, esz, reps in ((L.FP64, "fp64", 8, 3), (L.FP32, "fp32", 4, 6)):
+        f = L.Fd4(NX, NY, rates, wl["d"][:4], bc=wl["bc"], precision=prec)
+        f.write(state64 if prec == L.FP64 else state32)
+        f.step(1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f.step(reps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[f"fd4_{name}_glups"] = cells / (ms * 1e-3) / 1e9
+        out[f"fd4_{name}_hbm_frac"] = FD4_PLANES_PER_CELL * esz * cells / (ms * 1e-3) / 1e9 / hbm
+        f.close()
+        del f
+        torch.cuda.empty_cache()
     return out
 
 

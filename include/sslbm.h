@@ -284,6 +284,29 @@ int sslbm_ensemble_autotune(sslbm_ensemble* e, int trial_blocks, int* depth, int
 
 int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e);
 
+/* ---- fourth-order finite-difference reference (Sec. III) ----------------------------------
+ * The paper's accuracy reference: classical RK4 in time with the fourth-order centred
+ * Laplacian L4 u = sum over axes (-u[-2] + 16 u[-1] - 30 u[0] + 16 u[+1] - u[+2]) / (12 dx^2),
+ *   d/dt C = Psi^C + d^C L4 C (C = S, E, I, R),   d/dt D = phi gamma I,
+ * Psi from Eq. (sources) at every stage.  Boundaries: periodic wrap, or no-flux as the even
+ * reflection about the boundary face (u[-1] = u[0], u[-2] = u[1]).  g: nx, ny, dx, dt, bc,
+ * precision SSLBM_FP64 or SSLBM_FP32 (schemes and reserved are ignored).  p: beta, alpha,
+ * gamma, phi and the physical diffusivities d[] (use_tau must be 0, d[D] = 0); RK4
+ * stability needs d dt / dx^2 <= 0.26 for every compartment (else SSLBM_ERR_UNSTABLE).
+ * State: five contiguous planes [5][ny][nx] in the workspace (4 states: u, two stage
+ * states, the slope sum), caller-owned like the solver's. */
+typedef struct sslbm_fd4 sslbm_fd4;
+int sslbm_fd4_workspace_bytes(const sslbm_grid* g, size_t* bytes);
+int sslbm_fd4_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_t ws_bytes,
+                     void* stream, sslbm_fd4** out);
+void sslbm_fd4_destroy(sslbm_fd4* f);
+/* The whole state, [5][ny][nx] FP64 or FP32, host or device; host transfers synchronise. */
+int sslbm_fd4_write(sslbm_fd4* f, const void* src, int src_dtype, int src_on_device);
+int sslbm_fd4_read(sslbm_fd4* f, void* dst, int dst_dtype, int dst_on_device);
+/* n RK4 steps of dt (four stage launches each), stream-ordered. */
+int sslbm_fd4_step(sslbm_fd4* f, int64_t n);
+int64_t sslbm_fd4_steps_done(const sslbm_fd4* f);
+
 /* ---- learned surrogate -------------------------------------------------------------------
  * Not in the paper.  A Fourier-neural-operator-style network that maps the five SEIRD
  * fields of a periodic n x n grid to the fields 20 SSLBM steps later.  With the infection

@@ -1,0 +1,348 @@
+// fd4.cu -- the fourth-order finite-difference reference of Sec. III on the GPU: classical
+// RK4 in time and the fourth-order centred Laplacian in space,
+//   L4 u = sum over axes of (-u[-2] + 16 u[-1] - 30 u[0] + 16 u[+1] - u[+2]) / (12 dx^2),
+//   d/dt C = Psi^C + d^C L4 C (C = S, E, I, R),  d/dt D = phi gamma I   (Eqs. EqSEIRD_S..D),
+// with the reactions of Eq. (sources) evaluated at every stage.  Ghost cells: periodic wrap,
+// or (no-flux) the even reflection about the boundary face, u[-1] = u[0], u[-2] = u[1].
+//
+// One step is four stage launches.  Stage s reads the previous stage's state with the
+// stencil and writes the next stage's state and the running sum of the slopes:
+//   s = 1: acc = k1,         t = u + (dt/2) k1
+//   s = 2: acc = acc + 2 k2, t = u + (dt/2) k2
+//   s = 3: acc = acc + 2 k3, t = u + dt k3
+//   s = 4: u = u + (dt/6) (acc + k4)
+// Every operation is rounded on its own (no contraction) in the order of the formulas
+// above, so the FP64 path reproduces a plain evaluation of them operation by operation.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+
+#include "sslbm.h"
+
+namespace sslbm {
+int record_error(int status, const char* msg);
+}
+
+namespace {
+
+int err(int status, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  return sslbm::record_error(status, buf);
+}
+
+int cuda_err(cudaError_t e, const char* what) {
+  return err(SSLBM_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_err(e_, what);   \
+  } while (0)
+
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float dvd(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double dvd(double a, double b) { return __ddiv_rn(a, b); }
+
+template <typename T>
+struct Fd4Coeffs {
+  T beta, alpha, gamma, rg, dg;  // rg = (1 - phi) gamma, dg = phi gamma
+  T d[4];                        // diffusivities of S, E, I, R
+  T inv;                         // 1 / (12 dx^2)
+  T half_dt, dt, dt6;            // dt/2, dt, dt/6
+};
+
+// index of a (possibly ghost) cell along an axis of n cells
+__device__ __forceinline__ int64_t ghost2(int64_t i, int64_t n, int bc) {
+  if (i >= 0 && i < n) return i;
+  if (bc == SSLBM_BC_PERIODIC) {
+    int64_t r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  if (i < 0) i = -1 - i;
+  if (i >= n) i = 2 * n - 1 - i;
+  if (i < 0) i = 0;  // grids narrower than the stencil
+  if (i >= n) i = n - 1;
+  return i;
+}
+
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(256) fd4_stage_kernel(int64_t nx, int64_t ny, int bc, const Fd4Coeffs<T> k,
+                                                        const T* __restrict__ src, const T* u, T* acc,
+                                                        T* dst) {
+  const int64_t M = nx * ny;
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  const int64_t xm2 = ghost2(x - 2, nx, bc), xm1 = ghost2(x - 1, nx, bc);
+  const int64_t xp1 = ghost2(x + 1, nx, bc), xp2 = ghost2(x + 2, nx, bc);
+  for (int64_t y = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; y < ny; y += (int64_t)gridDim.y * blockDim.y) {
+    const int64_t c0 = y * nx + x;
+    const int64_t ym2 = ghost2(y - 2, ny, bc) * nx, ym1 = ghost2(y - 1, ny, bc) * nx;
+    const int64_t yp1 = ghost2(y + 1, ny, bc) * nx, yp2 = ghost2(y + 2, ny, bc) * nx;
+    const T S = src[c0], E = src[M + c0], I = src[2 * M + c0], R = src[3 * M + c0];
+    // reactions, Eq. (sources)
+    const T Nc = add(add(add(S, E), I), R);
+    const T F = Nc != T(0) ? dvd(mul(mul(k.beta, S), I), Nc) : T(0);
+    const T aE = mul(k.alpha, E);
+    T rhs[5];
+    rhs[0] = -F;
+    rhs[1] = sub(F, aE);
+    rhs[2] = sub(aE, mul(k.gamma, I));
+    rhs[3] = mul(k.rg, I);
+    rhs[4] = mul(k.dg, I);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const T* p = src + c * M;
+      const T u0 = p[c0];
+      const T lx = sub(add(sub(add(-p[y * nx + xm2], mul(T(16), p[y * nx + xm1])), mul(T(30), u0)),
+                           mul(T(16), p[y * nx + xp1])),
+                       p[y * nx + xp2]);
+      const T ly = sub(add(sub(add(-p[ym2 + x], mul(T(16), p[ym1 + x])), mul(T(30), u0)), mul(T(16), p[yp1 + x])),
+                       p[yp2 + x]);
+      rhs[c] = add(rhs[c], mul(mul(k.d[c], add(lx, ly)), k.inv));
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const int64_t i = c * M + c0;
+      const T r = rhs[c];
+      if (STAGE == 1) {
+        acc[i] = r;
+        dst[i] = add(u[i], mul(k.half_dt, r));
+      } else if (STAGE == 2) {
+        acc[i] = add(acc[i], mul(T(2), r));
+        dst[i] = add(u[i], mul(k.half_dt, r));
+      } else if (STAGE == 3) {
+        acc[i] = add(acc[i], mul(T(2), r));
+        dst[i] = add(u[i], mul(k.dt, r));
+      } else {
+        dst[i] = add(u[i], mul(k.dt6, add(acc[i], r)));
+      }
+    }
+  }
+}
+
+template <typename A, typename B>
+__global__ void convert_kernel(const A* __restrict__ a, B* __restrict__ b, int64_t n) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    b[t] = (B)a[t];
+}
+
+size_t rup(size_t v) { return (v + 255) / 256 * 256; }
+
+int check_grid(const sslbm_grid* g) {
+  if (!g) return err(SSLBM_ERR_BAD_ARG, "grid is NULL");
+  if (g->nx < 1 || g->ny < 1 || g->nx > (1 << 20) || g->ny > (1 << 20))
+    return err(SSLBM_ERR_BAD_ARG, "grid %lld x %lld out of range", (long long)g->nx, (long long)g->ny);
+  if (!(g->dx > 0) || !(g->dt > 0) || !std::isfinite(g->dx) || !std::isfinite(g->dt))
+    return err(SSLBM_ERR_BAD_ARG, "dx and dt must be finite and > 0");
+  if (g->bc != SSLBM_BC_PERIODIC && g->bc != SSLBM_BC_NOFLUX) return err(SSLBM_ERR_BAD_ARG, "bc %d", g->bc);
+  if (g->precision != SSLBM_FP64 && g->precision != SSLBM_FP32)
+    return err(SSLBM_ERR_UNSUPPORTED, "the FD4 reference runs in FP64 or FP32");
+  return SSLBM_OK;
+}
+
+size_t state_bytes(const sslbm_grid* g) {
+  return rup((size_t)5 * g->nx * g->ny * (g->precision == SSLBM_FP64 ? 8 : 4));
+}
+
+unsigned blocks1(int64_t n) { return (unsigned)std::min<int64_t>(65536, (n + 255) / 256); }
+
+}  // namespace
+
+struct sslbm_fd4 {
+  sslbm_grid g;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  char* ws = nullptr;
+  size_t sb = 0;  // bytes of one 5-plane state
+  Fd4Coeffs<double> k64;
+  Fd4Coeffs<float> k32;
+  int64_t steps = 0;
+  void* buf(int i) const { return ws + (size_t)i * sb; }  // 0 u, 1 t1, 2 t2, 3 acc
+};
+
+namespace {
+
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DevGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+cudaError_t run_step(const sslbm_fd4* f, const Fd4Coeffs<T>& k) {
+  const int64_t nx = f->g.nx, ny = f->g.ny;
+  dim3 block(32, 8);
+  dim3 grid((unsigned)((nx + 31) / 32), (unsigned)std::min<int64_t>(65535, (ny + 7) / 8));
+  T* u = static_cast<T*>(f->buf(0));
+  T* t1 = static_cast<T*>(f->buf(1));
+  T* t2 = static_cast<T*>(f->buf(2));
+  T* acc = static_cast<T*>(f->buf(3));
+  const int bc = f->g.bc;
+  fd4_stage_kernel<T, 1><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, u, u, acc, t1);
+  fd4_stage_kernel<T, 2><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, t1, u, acc, t2);
+  fd4_stage_kernel<T, 3><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, t2, u, acc, t1);
+  fd4_stage_kernel<T, 4><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, t1, u, acc, u);
+  return cudaGetLastError();
+}
+
+template <typename T>
+Fd4Coeffs<T> make_coeffs(const sslbm_grid* g, const sslbm_params* p) {
+  Fd4Coeffs<T> k;
+  k.beta = (T)p->beta;
+  k.alpha = (T)p->alpha;
+  k.gamma = (T)p->gamma;
+  k.rg = (T)((1.0 - p->phi) * p->gamma);
+  k.dg = (T)(p->phi * p->gamma);
+  for (int c = 0; c < 4; ++c) k.d[c] = (T)p->d[c];
+  k.inv = (T)(1.0 / (12.0 * g->dx * g->dx));
+  k.half_dt = (T)(0.5 * g->dt);
+  k.dt = (T)g->dt;
+  k.dt6 = (T)(g->dt / 6.0);
+  return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sslbm_fd4_workspace_bytes(const sslbm_grid* g, size_t* bytes) {
+  if (!bytes) return err(SSLBM_ERR_BAD_ARG, "bytes is NULL");
+  int st = check_grid(g);
+  if (st) return st;
+  *bytes = 4 * state_bytes(g);
+  return SSLBM_OK;
+}
+
+int sslbm_fd4_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_t ws_bytes, void* stream,
+                     sslbm_fd4** out) {
+  if (!out) return err(SSLBM_ERR_BAD_ARG, "out is NULL");
+  *out = nullptr;
+  int st = check_grid(g);
+  if (st) return st;
+  if (!p) return err(SSLBM_ERR_BAD_ARG, "params is NULL");
+  if (p->use_tau) return err(SSLBM_ERR_BAD_ARG, "the FD4 reference takes diffusivities d, not tau");
+  const double rates[4] = {p->beta, p->alpha, p->gamma, p->phi};
+  for (double r : rates)
+    if (!std::isfinite(r) || r < 0) return err(SSLBM_ERR_BAD_ARG, "rates must be finite and >= 0");
+  if (p->phi > 1) return err(SSLBM_ERR_BAD_ARG, "phi %g > 1", p->phi);
+  for (int c = 0; c < 4; ++c)
+    if (!std::isfinite(p->d[c]) || p->d[c] < 0) return err(SSLBM_ERR_BAD_ARG, "d[%d] must be finite and >= 0", c);
+  if (p->d[4] != 0) return err(SSLBM_ERR_BAD_ARG, "d[D] must be 0 (D does not move)");
+  // RK4 is stable on the negative real axis up to |z| = 2.78; the fourth-order Laplacian's
+  // most negative eigenvalue is -(64/12) per axis / dx^2, so d dt / dx^2 <= 0.26 in 2D
+  for (int c = 0; c < 4; ++c)
+    if (p->d[c] * g->dt / (g->dx * g->dx) > 0.26)
+      return err(SSLBM_ERR_UNSTABLE, "d[%d] dt / dx^2 = %g > 0.26 (RK4 with the fourth-order Laplacian)", c,
+                 p->d[c] * g->dt / (g->dx * g->dx));
+  const size_t need = 4 * state_bytes(g);
+  if (!dev_ws || reinterpret_cast<uintptr_t>(dev_ws) % 256)
+    return err(SSLBM_ERR_WORKSPACE, "workspace missing or not 256-byte aligned");
+  if (ws_bytes < need) return err(SSLBM_ERR_WORKSPACE, "workspace of %zu bytes < %zu", ws_bytes, need);
+  cudaPointerAttributes attr;
+  CK(cudaPointerGetAttributes(&attr, dev_ws), "cudaPointerGetAttributes");
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return err(SSLBM_ERR_WORKSPACE, "workspace is not device memory");
+  sslbm_fd4* f = new (std::nothrow) sslbm_fd4();
+  if (!f) return err(SSLBM_ERR_BAD_ARG, "out of host memory");
+  f->g = *g;
+  f->ws = static_cast<char*>(dev_ws);
+  f->sb = state_bytes(g);
+  f->stream = static_cast<cudaStream_t>(stream);
+  f->device = attr.device;
+  f->k64 = make_coeffs<double>(g, p);
+  f->k32 = make_coeffs<float>(g, p);
+  DevGuard dg(f->device);
+  cudaError_t e = cudaMemsetAsync(f->ws, 0, need, f->stream);
+  if (e != cudaSuccess) {
+    delete f;
+    return cuda_err(e, "zero workspace");
+  }
+  *out = f;
+  return SSLBM_OK;
+}
+
+void sslbm_fd4_destroy(sslbm_fd4* f) { delete f; }
+
+int sslbm_fd4_write(sslbm_fd4* f, const void* src, int src_dtype, int src_on_device) {
+  if (!f || !src) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  if (src_dtype != SSLBM_DT_F64 && src_dtype != SSLBM_DT_F32) return err(SSLBM_ERR_BAD_ARG, "dtype %d", src_dtype);
+  DevGuard dg(f->device);
+  const int64_t n = 5 * f->g.nx * f->g.ny;
+  const size_t esz = src_dtype == SSLBM_DT_F64 ? 8 : 4;
+  const void* s = src;
+  if (!src_on_device) {  // stage through the second stage buffer (two buffers when FP32 holds FP64)
+    CK(cudaMemcpyAsync(f->buf(1), src, (size_t)n * esz, cudaMemcpyHostToDevice, f->stream), "host -> device");
+    s = f->buf(1);
+  }
+  const bool f64 = f->g.precision == SSLBM_FP64;
+  if (src_dtype == SSLBM_DT_F64 && f64)
+    CK(cudaMemcpyAsync(f->buf(0), s, (size_t)n * 8, cudaMemcpyDeviceToDevice, f->stream), "copy");
+  else if (src_dtype == SSLBM_DT_F32 && !f64)
+    CK(cudaMemcpyAsync(f->buf(0), s, (size_t)n * 4, cudaMemcpyDeviceToDevice, f->stream), "copy");
+  else if (src_dtype == SSLBM_DT_F64)
+    convert_kernel<double, float><<<blocks1(n), 256, 0, f->stream>>>(static_cast<const double*>(s),
+                                                                     static_cast<float*>(f->buf(0)), n);
+  else
+    convert_kernel<float, double><<<blocks1(n), 256, 0, f->stream>>>(static_cast<const float*>(s),
+                                                                     static_cast<double*>(f->buf(0)), n);
+  CK(cudaGetLastError(), "convert");
+  if (!src_on_device) CK(cudaStreamSynchronize(f->stream), "sync");
+  f->steps = 0;
+  return SSLBM_OK;
+}
+
+int sslbm_fd4_read(sslbm_fd4* f, void* dst, int dst_dtype, int dst_on_device) {
+  if (!f || !dst) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  if (dst_dtype != SSLBM_DT_F64 && dst_dtype != SSLBM_DT_F32) return err(SSLBM_ERR_BAD_ARG, "dtype %d", dst_dtype);
+  DevGuard dg(f->device);
+  const int64_t n = 5 * f->g.nx * f->g.ny;
+  const size_t esz = dst_dtype == SSLBM_DT_F64 ? 8 : 4;
+  void* d = dst_on_device ? dst : f->buf(1);
+  const bool f64 = f->g.precision == SSLBM_FP64;
+  if ((dst_dtype == SSLBM_DT_F64) == f64)
+    CK(cudaMemcpyAsync(d, f->buf(0), (size_t)n * esz, cudaMemcpyDeviceToDevice, f->stream), "copy");
+  else if (f64)
+    convert_kernel<double, float><<<blocks1(n), 256, 0, f->stream>>>(static_cast<const double*>(f->buf(0)),
+                                                                     static_cast<float*>(d), n);
+  else
+    convert_kernel<float, double><<<blocks1(n), 256, 0, f->stream>>>(static_cast<const float*>(f->buf(0)),
+                                                                     static_cast<double*>(d), n);
+  CK(cudaGetLastError(), "convert");
+  if (!dst_on_device) CK(cudaMemcpyAsync(dst, d, (size_t)n * esz, cudaMemcpyDeviceToHost, f->stream), "device -> host");
+  CK(cudaStreamSynchronize(f->stream), "sync");
+  return SSLBM_OK;
+}
+
+int sslbm_fd4_step(sslbm_fd4* f, int64_t n) {
+  if (!f) return err(SSLBM_ERR_BAD_ARG, "NULL handle");
+  if (n < 0) return err(SSLBM_ERR_BAD_ARG, "n < 0");
+  DevGuard dg(f->device);
+  for (int64_t i = 0; i < n; ++i) {
+    cudaError_t e = f->g.precision == SSLBM_FP64 ? run_step<double>(f, f->k64) : run_step<float>(f, f->k32);
+    if (e != cudaSuccess) return cuda_err(e, "FD4 stage launch");
+    ++f->steps;
+  }
+  return SSLBM_OK;
+}
+
+int64_t sslbm_fd4_steps_done(const sslbm_fd4* f) { return f ? f->steps : -1; }
+
+}  // extern "C"

@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(_PKG, "libsslbm.so")
 
 # constants of include/sslbm.h
 SSLBM_OK = 0
+(SSLBM_ERR_BAD_ARG, SSLBM_ERR_UNSTABLE, SSLBM_ERR_CUDA, SSLBM_ERR_TIMEOUT, SSLBM_ERR_NONFINITE,
+ SSLBM_ERR_WORKSPACE, SSLBM_ERR_UNSUPPORTED, SSLBM_ERR_STATE) = (-1, -2, -3, -4, -5, -6, -7, -8)
 BC_PERIODIC, BC_NOFLUX = 0, 1
 FP64, FP32, FP32_DEV, FP32_KAHAN = 0, 1, 2, 3
 SCHEME_SSLBM, SCHEME_BGK = 0, 1
@@ -45,7 +47,9 @@ EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspa
            "sslbm_fno_get_params", "sslbm_fno_get_grads", "sslbm_fno_make_input",
            "sslbm_fno_forward", "sslbm_fno_backward", "sslbm_fno_set_adam", "sslbm_fno_set_loss_weights",
            "sslbm_fno_infer", "sslbm_fno_fused",
-           "sslbm_fno_train_step", "sslbm_fno_check_project")
+           "sslbm_fno_train_step", "sslbm_fno_check_project",
+           "sslbm_fd4_workspace_bytes", "sslbm_fd4_create", "sslbm_fd4_destroy", "sslbm_fd4_write",
+           "sslbm_fd4_read", "sslbm_fd4_step", "sslbm_fd4_steps_done")
 
 
 class SslbmError(RuntimeError):
@@ -115,6 +119,14 @@ def load(path: str = LIB_PATH):
             "sslbm_autotune": (i32, [_vp, ctypes.c_double, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(ctypes.c_double)]),
             "sslbm_ensemble_workspace_bytes": (i32, [i32, _vp, i32, ctypes.POINTER(ctypes.c_size_t)]),
+            "sslbm_fd4_workspace_bytes": (i32, [ctypes.POINTER(Grid), ctypes.POINTER(ctypes.c_size_t)]),
+            "sslbm_fd4_create": (i32, [ctypes.POINTER(Grid), ctypes.POINTER(Params), _vp, ctypes.c_size_t, _vp,
+                                       ctypes.POINTER(_vp)]),
+            "sslbm_fd4_destroy": (None, [_vp]),
+            "sslbm_fd4_write": (i32, [_vp, _vp, i32, i32]),
+            "sslbm_fd4_read": (i32, [_vp, _vp, i32, i32]),
+            "sslbm_fd4_step": (i32, [_vp, ctypes.c_int64]),
+            "sslbm_fd4_steps_done": (ctypes.c_int64, [_vp]),
             "sslbm_ensemble_create": (i32, [i32, _vp, i32, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
             "sslbm_ensemble_destroy": (None, [_vp]),
             "sslbm_ensemble_set_tiling": (i32, [_vp, i32, i32]),
@@ -450,6 +462,89 @@ def sslbm_ensemble_autotune(e, trial_blocks=0):
 
 def sslbm_ensemble_steps_done(e):
     return int(load().sslbm_ensemble_steps_done(e))
+
+
+# ---------------------------------------------------------------------------
+# fourth-order finite-difference reference
+# ---------------------------------------------------------------------------
+
+def sslbm_fd4_workspace_bytes(g: Grid) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().sslbm_fd4_workspace_bytes(ctypes.byref(g), ctypes.byref(n)), "sslbm_fd4_workspace_bytes")
+    return int(n.value)
+
+
+def sslbm_fd4_create(g: Grid, p: Params, ws_ptr, ws_bytes, stream=0):
+    f = _vp()
+    _check(load().sslbm_fd4_create(ctypes.byref(g), ctypes.byref(p), _vp(ws_ptr), int(ws_bytes), _vp(stream),
+                                   ctypes.byref(f)), "sslbm_fd4_create")
+    return f
+
+
+def sslbm_fd4_destroy(f):
+    if f:
+        load().sslbm_fd4_destroy(f)
+
+
+def sslbm_fd4_write(f, src):
+    ptr, dev, code, _ = _buffer(src)
+    _check(load().sslbm_fd4_write(f, _vp(ptr), code, dev), "sslbm_fd4_write")
+
+
+def sslbm_fd4_read(f, dst):
+    ptr, dev, code, _ = _buffer(dst)
+    _check(load().sslbm_fd4_read(f, _vp(ptr), code, dev), "sslbm_fd4_read")
+    return dst
+
+
+def sslbm_fd4_step(f, n):
+    _check(load().sslbm_fd4_step(f, int(n)), "sslbm_fd4_step")
+
+
+def sslbm_fd4_steps_done(f) -> int:
+    return int(load().sslbm_fd4_steps_done(f))
+
+
+class Fd4:
+    """The fourth-order finite-difference reference (RK4 + fourth-order Laplacian) with a
+    torch-allocated workspace; rates (beta, alpha, gamma, phi), d the physical
+    diffusivities of S, E, I, R (and D = 0)."""
+
+    def __init__(self, nx, ny, rates, d, dx=1.0, dt=1.0, bc=BC_PERIODIC, precision=FP64, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device if device is not None else "cuda")
+        self.grid = make_grid(nx, ny, dx, dt, bc, precision)
+        self.params = make_params(*rates, d=d)
+        self.nx, self.ny = int(nx), int(ny)
+        nbytes = sslbm_fd4_workspace_bytes(self.grid)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.f = sslbm_fd4_create(self.grid, self.params, self.ws.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "f", None):
+            self.stream.synchronize()
+            sslbm_fd4_destroy(self.f)
+            self.f = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def write(self, state):
+        sslbm_fd4_write(self.f, state)
+
+    def read(self, dtype=np.float64):
+        return sslbm_fd4_read(self.f, np.empty((5, self.ny, self.nx), dtype=dtype))
+
+    def step(self, n):
+        sslbm_fd4_step(self.f, n)
+
+    def steps_done(self):
+        return sslbm_fd4_steps_done(self.f)
 
 
 class Ensemble:
