@@ -78,20 +78,35 @@ __device__ __forceinline__ int64_t ghost2(int64_t i, int64_t n, int bc) {
   return i;
 }
 
+constexpr int kTX = 32, kTY = 8, kH = 2;  // tile of cells per CTA and the stencil's halo
+
+// One RK4 stage on a kTX x kTY tile of cells: the four mobile planes of the stage input are
+// staged in shared memory with a halo of two cells (ghost cells resolved once, at load),
+// then every cell evaluates its right-hand side from the tile.
 template <typename T, int STAGE>
-__global__ void __launch_bounds__(256) fd4_stage_kernel(int64_t nx, int64_t ny, int bc, const Fd4Coeffs<T> k,
-                                                        const T* __restrict__ src, const T* u, T* acc,
-                                                        T* dst) {
+__global__ void __launch_bounds__(kTX * kTY) fd4_stage_kernel(int64_t nx, int64_t ny, int bc, const Fd4Coeffs<T> k,
+                                                              const T* __restrict__ src, const T* u, T* acc,
+                                                              T* dst) {
+  constexpr int SX = kTX + 2 * kH, SY = kTY + 2 * kH;
+  __shared__ T tile[4][SY][SX];
   const int64_t M = nx * ny;
-  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= nx) return;
-  const int64_t xm2 = ghost2(x - 2, nx, bc), xm1 = ghost2(x - 1, nx, bc);
-  const int64_t xp1 = ghost2(x + 1, nx, bc), xp2 = ghost2(x + 2, nx, bc);
-  for (int64_t y = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; y < ny; y += (int64_t)gridDim.y * blockDim.y) {
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
+  const int64_t bx0 = (int64_t)blockIdx.x * kTX;
+  for (int64_t by0 = (int64_t)blockIdx.y * kTY; by0 < ny; by0 += (int64_t)gridDim.y * kTY) {
+    __syncthreads();  // the previous tile's readers are done
+    for (int i = tid; i < SX * SY; i += kTX * kTY) {
+      const int sy = i / SX, sx = i - sy * SX;
+      const int64_t gx = ghost2(bx0 + sx - kH, nx, bc), gy = ghost2(by0 + sy - kH, ny, bc);
+      const int64_t off = gy * nx + gx;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tile[c][sy][sx] = src[c * M + off];
+    }
+    __syncthreads();
+    const int64_t x = bx0 + tx, y = by0 + ty;
+    if (x >= nx || y >= ny) continue;
     const int64_t c0 = y * nx + x;
-    const int64_t ym2 = ghost2(y - 2, ny, bc) * nx, ym1 = ghost2(y - 1, ny, bc) * nx;
-    const int64_t yp1 = ghost2(y + 1, ny, bc) * nx, yp2 = ghost2(y + 2, ny, bc) * nx;
-    const T S = src[c0], E = src[M + c0], I = src[2 * M + c0], R = src[3 * M + c0];
+    const int cx = tx + kH, cy = ty + kH;
+    const T S = tile[0][cy][cx], E = tile[1][cy][cx], I = tile[2][cy][cx], R = tile[3][cy][cx];
     // reactions, Eq. (sources)
     const T Nc = add(add(add(S, E), I), R);
     const T F = Nc != T(0) ? dvd(mul(mul(k.beta, S), I), Nc) : T(0);
@@ -104,13 +119,13 @@ __global__ void __launch_bounds__(256) fd4_stage_kernel(int64_t nx, int64_t ny, 
     rhs[4] = mul(k.dg, I);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const T* p = src + c * M;
-      const T u0 = p[c0];
-      const T lx = sub(add(sub(add(-p[y * nx + xm2], mul(T(16), p[y * nx + xm1])), mul(T(30), u0)),
-                           mul(T(16), p[y * nx + xp1])),
-                       p[y * nx + xp2]);
-      const T ly = sub(add(sub(add(-p[ym2 + x], mul(T(16), p[ym1 + x])), mul(T(30), u0)), mul(T(16), p[yp1 + x])),
-                       p[yp2 + x]);
+      const T u0 = tile[c][cy][cx];
+      const T lx = sub(add(sub(add(-tile[c][cy][cx - 2], mul(T(16), tile[c][cy][cx - 1])), mul(T(30), u0)),
+                           mul(T(16), tile[c][cy][cx + 1])),
+                       tile[c][cy][cx + 2]);
+      const T ly = sub(add(sub(add(-tile[c][cy - 2][cx], mul(T(16), tile[c][cy - 1][cx])), mul(T(30), u0)),
+                           mul(T(16), tile[c][cy + 1][cx])),
+                       tile[c][cy + 2][cx]);
       rhs[c] = add(rhs[c], mul(mul(k.d[c], add(lx, ly)), k.inv));
     }
 #pragma unroll
@@ -189,8 +204,8 @@ struct DevGuard {
 template <typename T>
 cudaError_t run_step(const sslbm_fd4* f, const Fd4Coeffs<T>& k) {
   const int64_t nx = f->g.nx, ny = f->g.ny;
-  dim3 block(32, 8);
-  dim3 grid((unsigned)((nx + 31) / 32), (unsigned)std::min<int64_t>(65535, (ny + 7) / 8));
+  dim3 block(kTX, kTY);
+  dim3 grid((unsigned)((nx + kTX - 1) / kTX), (unsigned)std::min<int64_t>(65535, (ny + kTY - 1) / kTY));
   T* u = static_cast<T*>(f->buf(0));
   T* t1 = static_cast<T*>(f->buf(1));
   T* t2 = static_cast<T*>(f->buf(2));
