@@ -18,10 +18,15 @@ surrogate  -- the learned surrogate end to end on n x n periodic grids (default 
               residual checks and SSLBM fallback, judged against the SSLBM run in lock step,
               and its scenario-steps/s against the plain FP64 SSLBM on the same grid.
 
+accuracy   -- the accuracy comparison of Sec. III at scale: FP64 SSLBM and BGK against the
+              GPU fourth-order finite-difference RK4 reference under diffusive refinement
+              (grids 64..512, fixed tau), relative L2 / max-norm errors and observed order.
+
 Usage:  python -m paper_2603_19789_gb300.studies precision [--n 4096] [--steps 50000]
         [--checkpoints 5] [--out FILE]
         python -m paper_2603_19789_gb300.studies surrogate [--n 256] [--trajectories 2000]
         [--train-steps 3000] [--out FILE]
+        python -m paper_2603_19789_gb300.studies accuracy [--out FILE]
 """
 from __future__ import annotations
 
@@ -93,6 +98,63 @@ def precision_study(n: int = 4096, steps: int = 50000, checkpoints: int = 6, see
     return out
 
 
+def accuracy_study(sizes=(64, 128, 256, 512), d_phys=1e-4, d_lattice=0.05, t_end=None, sub=4):
+    """The accuracy comparison of Sec. III at scale: the SSLBM and the BGK LBM against the
+    fourth-order finite-difference RK4 reference, under diffusive refinement.
+
+    The centre-bump workload on the unit square (periodic), its bump width fixed
+    physically (sigma = 1/16), no perturbation; d = d_phys for S, E, I, R; rates per unit
+    time as in the workload.  Each grid n has dx = 1/n and dt = d_lattice dx^2 / d_phys,
+    so tau (= 3 d_lattice + 1/2) is the same on every grid and the time error (first order
+    in dt) scales like the space error (second order in dx).  The reference runs on the
+    same grid with dt / sub.  Reported per compartment at the final time: relative L2 and
+    max-norm errors of SSLBM and BGK against the reference, and the observed order of the
+    SSLBM between successive grids."""
+    out = {"d_phys": d_phys, "d_lattice": d_lattice, "tau": 3 * d_lattice + 0.5, "sub": sub, "grids": []}
+    dt0 = d_lattice * (1.0 / 128) ** 2 / d_phys
+    t_end = t_end if t_end is not None else 2000 * dt0
+    out["t_end"] = t_end
+    prev = None
+    for n in sizes:
+        wl = inputs.centre_bump_workload(n, n, sig=n / 16.0, noise=0.0)
+        st = wl["state"]
+        rates = wl["rates"].as_tuple()
+        dx = 1.0 / n
+        dt = d_lattice * dx * dx / d_phys
+        steps = int(round(t_end / dt))
+        d = (d_phys, d_phys, d_phys, d_phys, 0.0)
+        t0 = time.perf_counter()
+        s = L.Solver(n, n, rates, d=d, dx=dx, dt=dt, bc=L.BC_PERIODIC, precision=L.FP64,
+                     schemes=L.WANT_SSLBM | L.WANT_BGK)
+        s.write(st)
+        s.write(st, scheme=L.SCHEME_BGK)
+        s.step(steps)
+        s.bgk_step(steps)
+        a = s.read()
+        b = s.read(scheme=L.SCHEME_BGK)
+        s.close()
+        f = L.Fd4(n, n, rates, d[:4], dx=dx, dt=dt / sub, bc=L.BC_PERIODIC, precision=L.FP64)
+        f.write(st)
+        f.step(steps * sub)
+        ref = f.read()
+        f.close()
+        el = time.perf_counter() - t0
+
+        def errs(x):
+            l2 = [float(np.linalg.norm(x[c] - ref[c]) / np.linalg.norm(ref[c])) for c in range(5)]
+            li = [float(np.abs(x[c] - ref[c]).max() / np.abs(ref[c]).max()) for c in range(5)]
+            return {"rel_l2": dict(zip("SEIRD", l2)), "rel_linf": dict(zip("SEIRD", li))}
+
+        rec = {"n": n, "dx": dx, "dt": dt, "steps": steps, "seconds": el,
+               "sslbm": errs(a), "bgk": errs(b)}
+        if prev is not None:
+            rec["sslbm_order_l2"] = {c: float(np.log2(prev["sslbm"]["rel_l2"][c] / rec["sslbm"]["rel_l2"][c]))
+                                     for c in "SEIRD"}
+        out["grids"].append(rec)
+        prev = rec
+    return out
+
+
 def surrogate_study(n=256, trajectories=2000, snapshots=10, horizon=2000, train_steps=20000, batch=16,
                     lr=1e-3, width=32, modes=12, layers=4, hidden=64, scenarios=64, rollout_steps=100,
                     params=None):
@@ -132,7 +194,7 @@ def surrogate_study(n=256, trajectories=2000, snapshots=10, horizon=2000, train_
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["precision", "surrogate"])
+    ap.add_argument("study", choices=["precision", "surrogate", "accuracy"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--steps", type=int, default=50000)
     ap.add_argument("--checkpoints", type=int, default=6)
@@ -143,6 +205,14 @@ def main(argv=None):
     args = ap.parse_args(argv)
     from . import build
     build.build()
+    if args.study == "accuracy":
+        res = accuracy_study()
+        text = json.dumps(res, indent=1)
+        if args.out:
+            with open(args.out, "w") as fh:
+                fh.write(text + "\n")
+        print(text)
+        return
     if args.study == "surrogate":
         res, theta = surrogate_study(n=args.n or 256, trajectories=args.trajectories, train_steps=args.train_steps,
                                      params=np.load(args.params) if args.params else None)
