@@ -80,6 +80,8 @@ def _load():
         lib.oracle_bgk_run.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double, _i64, _dp, _dp]
         lib.oracle_fd4_rk4_run.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                            ctypes.c_double, _i64, _dp]
+        lib.oracle_fd2_rk4_run.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                           ctypes.c_double, _i64, _dp]
         lib.oracle_ode_rk4.argtypes = [_dp, ctypes.c_double, _i64, _dp]
         lib.oracle_sources.argtypes = [_dp, _dp, _dp]
         lib.oracle_diagnostics.argtypes = [_i64, _i64, _dp, _dp, _dp]
@@ -208,6 +210,16 @@ def fd4_rk4_run(state, d, rates, dx: float = 1.0, dt: float = 1.0, bc: int = 0, 
     a = _state(state)
     _, ny, nx = a.shape
     lib.oracle_fd4_rk4_run(nx, ny, int(bc), _ptr(_vec(d, 4)), _ptr(_vec(rates, 4)), float(dx),
+                           float(dt), int(nsteps), _ptr(a))
+    return a
+
+
+def fd2_rk4_run(state, d, rates, dx: float = 1.0, dt: float = 1.0, bc: int = 0, nsteps: int = 1):
+    """Second-order FD (5-point Laplacian) + RK4: the "FDM 2nd" of the cost comparison."""
+    lib = _load()
+    a = _state(state)
+    _, ny, nx = a.shape
+    lib.oracle_fd2_rk4_run(nx, ny, int(bc), _ptr(_vec(d, 4)), _ptr(_vec(rates, 4)), float(dx),
                            float(dt), int(nsteps), _ptr(a))
     return a
 

@@ -281,6 +281,55 @@ static void fd4_rhs(i64 nx, i64 ny, int bc, const double d[4], const double rate
     }
 }
 
+/*
+ * Second-order counterpart for the cost comparison of Sec. IV (Table tab:timing, "FDM
+ * 2nd"): the same classical RK4 with the second-order centred Laplacian
+ *   L2 u = sum over axes of (u[-1] - 2 u[0] + u[+1]) / dx^2,
+ * the same sources and the same ghost rule.
+ */
+static void fd2_rhs(i64 nx, i64 ny, int bc, const double d[4], const double rates[4], double dx,
+                    const double* u, double* rhs) {
+  const i64 M = nx * ny;
+  const double inv = 1.0 / (dx * dx);
+#pragma omp parallel for schedule(static)
+  for (i64 y = 0; y < ny; ++y)
+    for (i64 x = 0; x < nx; ++x) {
+      const i64 k = y * nx + x;
+      double psi[5];
+      seird_sources(rates, u[k], u[M + k], u[2 * M + k], u[3 * M + k], psi);
+      for (int c = 0; c < 4; ++c) {
+        const double* p = u + c * M;
+        const double u0 = p[k];
+        double lx = p[y * nx + ghost2(x - 1, nx, bc)] - 2.0 * u0 + p[y * nx + ghost2(x + 1, nx, bc)];
+        double ly = p[ghost2(y - 1, ny, bc) * nx + x] - 2.0 * u0 + p[ghost2(y + 1, ny, bc) * nx + x];
+        rhs[c * M + k] = psi[c] + d[c] * (lx + ly) * inv;
+      }
+      rhs[4 * M + k] = psi[4];
+    }
+}
+
+void oracle_fd2_rk4_run(i64 nx, i64 ny, int bc, const double d[4], const double rates[4],
+                        double dx, double dt, i64 nsteps, double* state) {
+  const i64 n = 5 * nx * ny;
+  double* k1 = (double*)malloc((size_t)n * sizeof(double));
+  double* k2 = (double*)malloc((size_t)n * sizeof(double));
+  double* k3 = (double*)malloc((size_t)n * sizeof(double));
+  double* k4 = (double*)malloc((size_t)n * sizeof(double));
+  double* tmp = (double*)malloc((size_t)n * sizeof(double));
+  for (i64 s = 0; s < nsteps; ++s) {
+    fd2_rhs(nx, ny, bc, d, rates, dx, state, k1);
+    for (i64 j = 0; j < n; ++j) tmp[j] = state[j] + 0.5 * dt * k1[j];
+    fd2_rhs(nx, ny, bc, d, rates, dx, tmp, k2);
+    for (i64 j = 0; j < n; ++j) tmp[j] = state[j] + 0.5 * dt * k2[j];
+    fd2_rhs(nx, ny, bc, d, rates, dx, tmp, k3);
+    for (i64 j = 0; j < n; ++j) tmp[j] = state[j] + dt * k3[j];
+    fd2_rhs(nx, ny, bc, d, rates, dx, tmp, k4);
+    for (i64 j = 0; j < n; ++j)
+      state[j] += dt / 6.0 * (k1[j] + 2.0 * k2[j] + 2.0 * k3[j] + k4[j]);
+  }
+  free(k1); free(k2); free(k3); free(k4); free(tmp);
+}
+
 void oracle_fd4_rk4_run(i64 nx, i64 ny, int bc, const double d[4], const double rates[4],
                         double dx, double dt, i64 nsteps, double* state) {
   const i64 n = 5 * nx * ny;

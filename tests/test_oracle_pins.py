@@ -351,6 +351,49 @@ def test_fd4_mode_evolution_exact(bc):
 
 
 @pytest.mark.parametrize("bc", [0, 1])
+def test_fd2_mode_evolution_exact(bc):
+    """RK4 on a mode of the second-order (5-point) Laplacian multiplies it by R(z) per step,
+    z = dt d (s_x + s_y)/dx^2 with the textbook symbol s(th) = 2 cos th - 2."""
+    nx, ny, nsteps = 26, 18, 30
+    d, dx, dt = 0.09, 1.0, 1.0
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    m, q = 3, 2
+    if bc == 0:
+        thx, thy = 2 * math.pi * m / nx, 2 * math.pi * q / ny
+        shape = np.cos(thx * x + thy * y)
+    else:
+        thx, thy = math.pi * m / nx, math.pi * q / ny
+        shape = np.cos(thx * (x + 0.5)) * np.cos(thy * (y + 0.5))
+    z = dt * d * ((2 * math.cos(thx) - 2) + (2 * math.cos(thy) - 2)) / dx ** 2
+    R = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+    st = np.zeros((5, ny, nx))
+    st[:4] = 1.0 + 0.3 * shape
+    out = oracle.fd2_rk4_run(st, [d] * 4, NO_REACTION, dx, dt, bc, nsteps)
+    np.testing.assert_allclose(out[0], 1.0 + 0.3 * R ** nsteps * shape, rtol=0, atol=1e-13)
+
+
+def test_fd2_second_order_convergence():
+    errs = [_diffusion_mode_l2_fd2(n, 0.1, 0.05) for n in (16, 32, 64)]
+    ours = [math.log2(a / b) for a, b in zip(errs, errs[1:])]
+    assert all(abs(p - 2.0) < 0.1 for p in ours), ours
+
+
+def _diffusion_mode_l2_fd2(n, D, c):
+    dx = 1.0 / n
+    dt = c * dx * dx / D
+    steps = int(round(0.05 / dt))
+    t_end = steps * dt
+    cc = (np.arange(n) + 0.5) / n
+    shape = np.sin(2 * math.pi * cc)[None, :] * np.sin(2 * math.pi * cc)[:, None]
+    st = np.zeros((5, n, n))
+    st[:4] = 1.0 + shape
+    out = oracle.fd2_rk4_run(st, [D] * 4, NO_REACTION, dx, dt, 0, steps)
+    exact = 1.0 + shape * math.exp(-2 * D * (2 * math.pi) ** 2 * t_end)
+    return math.sqrt(np.mean((out[0] - exact) ** 2))
+
+
+@pytest.mark.parametrize("bc", [0, 1])
 def test_fd4_conserves_population(bc):
     st = inputs.epidemic_state(20, 17, seed=2)
     out = oracle.fd4_rk4_run(st, [0.05, 0.05, 0.01, 0.05], (0.5, 0.2, 0.11, 1 / 11), 1.0, 0.5, bc, 50)
