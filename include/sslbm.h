@@ -306,6 +306,10 @@ int sslbm_fd4_read(sslbm_fd4* f, void* dst, int dst_dtype, int dst_on_device);
 /* n RK4 steps of dt (four stage launches each), stream-ordered. */
 int sslbm_fd4_step(sslbm_fd4* f, int64_t n);
 int64_t sslbm_fd4_steps_done(const sslbm_fd4* f);
+/* Order of the Laplacian: 4 (default, the reference) or 2, the second-order centred
+ * Laplacian sum over axes (u[-1] - 2 u[0] + u[+1]) / dx^2 with the same RK4, sources and
+ * ghost rule ("FDM 2nd" of the cost comparison, Table tab:timing). */
+int sslbm_fd4_set_order(sslbm_fd4* f, int order);
 
 /* ---- learned surrogate -------------------------------------------------------------------
  * Not in the paper.  A Fourier-neural-operator-style network that maps the five SEIRD

@@ -1,4 +1,5 @@
-// fd4.cu -- the fourth-order finite-difference reference of Sec. III on the GPU: classical
+// fd4.cu -- the fourth-order finite-difference reference of Sec. III on the GPU (and, for the
+// cost comparison of Sec. IV, its second-order counterpart, sslbm_fd4_set_order): classical
 // RK4 in time and the fourth-order centred Laplacian in space,
 //   L4 u = sum over axes of (-u[-2] + 16 u[-1] - 30 u[0] + 16 u[+1] - u[+2]) / (12 dx^2),
 //   d/dt C = Psi^C + d^C L4 C (C = S, E, I, R),  d/dt D = phi gamma I   (Eqs. EqSEIRD_S..D),
@@ -60,7 +61,7 @@ template <typename T>
 struct Fd4Coeffs {
   T beta, alpha, gamma, rg, dg;  // rg = (1 - phi) gamma, dg = phi gamma
   T d[4];                        // diffusivities of S, E, I, R
-  T inv;                         // 1 / (12 dx^2)
+  T inv, inv2;                   // 1 / (12 dx^2), 1 / dx^2
   T half_dt, dt, dt6;            // dt/2, dt, dt/6
 };
 
@@ -83,7 +84,7 @@ constexpr int kTX = 32, kTY = 8, kH = 2;  // tile of cells per CTA and the stenc
 // One RK4 stage on a kTX x kTY tile of cells: the four mobile planes of the stage input are
 // staged in shared memory with a halo of two cells (ghost cells resolved once, at load),
 // then every cell evaluates its right-hand side from the tile.
-template <typename T, int STAGE>
+template <typename T, int STAGE, int ORDER>
 __global__ void __launch_bounds__(kTX * kTY) fd4_stage_kernel(int64_t nx, int64_t ny, int bc, const Fd4Coeffs<T> k,
                                                               const T* __restrict__ src, const T* u, T* acc,
                                                               T* dst) {
@@ -120,13 +121,19 @@ __global__ void __launch_bounds__(kTX * kTY) fd4_stage_kernel(int64_t nx, int64_
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const T u0 = tile[c][cy][cx];
-      const T lx = sub(add(sub(add(-tile[c][cy][cx - 2], mul(T(16), tile[c][cy][cx - 1])), mul(T(30), u0)),
-                           mul(T(16), tile[c][cy][cx + 1])),
-                       tile[c][cy][cx + 2]);
-      const T ly = sub(add(sub(add(-tile[c][cy - 2][cx], mul(T(16), tile[c][cy - 1][cx])), mul(T(30), u0)),
-                           mul(T(16), tile[c][cy + 1][cx])),
-                       tile[c][cy + 2][cx]);
-      rhs[c] = add(rhs[c], mul(mul(k.d[c], add(lx, ly)), k.inv));
+      T lx, ly;
+      if (ORDER == 4) {
+        lx = sub(add(sub(add(-tile[c][cy][cx - 2], mul(T(16), tile[c][cy][cx - 1])), mul(T(30), u0)),
+                     mul(T(16), tile[c][cy][cx + 1])),
+                 tile[c][cy][cx + 2]);
+        ly = sub(add(sub(add(-tile[c][cy - 2][cx], mul(T(16), tile[c][cy - 1][cx])), mul(T(30), u0)),
+                     mul(T(16), tile[c][cy + 1][cx])),
+                 tile[c][cy + 2][cx]);
+      } else {  // second order: u[-1] - 2 u[0] + u[+1]
+        lx = add(sub(tile[c][cy][cx - 1], mul(T(2), u0)), tile[c][cy][cx + 1]);
+        ly = add(sub(tile[c][cy - 1][cx], mul(T(2), u0)), tile[c][cy + 1][cx]);
+      }
+      rhs[c] = add(rhs[c], mul(mul(k.d[c], add(lx, ly)), ORDER == 4 ? k.inv : k.inv2));
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
@@ -185,6 +192,7 @@ struct sslbm_fd4 {
   Fd4Coeffs<double> k64;
   Fd4Coeffs<float> k32;
   int64_t steps = 0;
+  int order = 4;  // order of the Laplacian: 4 (the reference) or 2
   void* buf(int i) const { return ws + (size_t)i * sb; }  // 0 u, 1 t1, 2 t2, 3 acc
 };
 
@@ -201,7 +209,7 @@ struct DevGuard {
   }
 };
 
-template <typename T>
+template <typename T, int ORDER>
 cudaError_t run_step(const sslbm_fd4* f, const Fd4Coeffs<T>& k) {
   const int64_t nx = f->g.nx, ny = f->g.ny;
   dim3 block(kTX, kTY);
@@ -211,10 +219,10 @@ cudaError_t run_step(const sslbm_fd4* f, const Fd4Coeffs<T>& k) {
   T* t2 = static_cast<T*>(f->buf(2));
   T* acc = static_cast<T*>(f->buf(3));
   const int bc = f->g.bc;
-  fd4_stage_kernel<T, 1><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, u, u, acc, t1);
-  fd4_stage_kernel<T, 2><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, t1, u, acc, t2);
-  fd4_stage_kernel<T, 3><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, t2, u, acc, t1);
-  fd4_stage_kernel<T, 4><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, t1, u, acc, u);
+  fd4_stage_kernel<T, 1, ORDER><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, u, u, acc, t1);
+  fd4_stage_kernel<T, 2, ORDER><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, t1, u, acc, t2);
+  fd4_stage_kernel<T, 3, ORDER><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, t2, u, acc, t1);
+  fd4_stage_kernel<T, 4, ORDER><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, t1, u, acc, u);
   return cudaGetLastError();
 }
 
@@ -228,6 +236,7 @@ Fd4Coeffs<T> make_coeffs(const sslbm_grid* g, const sslbm_params* p) {
   k.dg = (T)(p->phi * p->gamma);
   for (int c = 0; c < 4; ++c) k.d[c] = (T)p->d[c];
   k.inv = (T)(1.0 / (12.0 * g->dx * g->dx));
+  k.inv2 = (T)(1.0 / (g->dx * g->dx));
   k.half_dt = (T)(0.5 * g->dt);
   k.dt = (T)g->dt;
   k.dt6 = (T)(g->dt / 6.0);
@@ -351,7 +360,11 @@ int sslbm_fd4_step(sslbm_fd4* f, int64_t n) {
   if (n < 0) return err(SSLBM_ERR_BAD_ARG, "n < 0");
   DevGuard dg(f->device);
   for (int64_t i = 0; i < n; ++i) {
-    cudaError_t e = f->g.precision == SSLBM_FP64 ? run_step<double>(f, f->k64) : run_step<float>(f, f->k32);
+    cudaError_t e;
+    if (f->g.precision == SSLBM_FP64)
+      e = f->order == 4 ? run_step<double, 4>(f, f->k64) : run_step<double, 2>(f, f->k64);
+    else
+      e = f->order == 4 ? run_step<float, 4>(f, f->k32) : run_step<float, 2>(f, f->k32);
     if (e != cudaSuccess) return cuda_err(e, "FD4 stage launch");
     ++f->steps;
   }
@@ -359,5 +372,12 @@ int sslbm_fd4_step(sslbm_fd4* f, int64_t n) {
 }
 
 int64_t sslbm_fd4_steps_done(const sslbm_fd4* f) { return f ? f->steps : -1; }
+
+int sslbm_fd4_set_order(sslbm_fd4* f, int order) {
+  if (!f) return err(SSLBM_ERR_BAD_ARG, "NULL handle");
+  if (order != 2 && order != 4) return err(SSLBM_ERR_BAD_ARG, "order %d is not 2 or 4", order);
+  f->order = order;  // the create-time stability check (d dt / dx^2 <= 0.26) covers both orders
+  return SSLBM_OK;
+}
 
 }  // extern "C"

@@ -49,7 +49,7 @@ EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspa
            "sslbm_fno_infer", "sslbm_fno_fused",
            "sslbm_fno_train_step", "sslbm_fno_check_project",
            "sslbm_fd4_workspace_bytes", "sslbm_fd4_create", "sslbm_fd4_destroy", "sslbm_fd4_write",
-           "sslbm_fd4_read", "sslbm_fd4_step", "sslbm_fd4_steps_done")
+           "sslbm_fd4_read", "sslbm_fd4_step", "sslbm_fd4_steps_done", "sslbm_fd4_set_order")
 
 
 class SslbmError(RuntimeError):
@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH):
             "sslbm_fd4_read": (i32, [_vp, _vp, i32, i32]),
             "sslbm_fd4_step": (i32, [_vp, ctypes.c_int64]),
             "sslbm_fd4_steps_done": (ctypes.c_int64, [_vp]),
+            "sslbm_fd4_set_order": (i32, [_vp, i32]),
             "sslbm_ensemble_create": (i32, [i32, _vp, i32, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
             "sslbm_ensemble_destroy": (None, [_vp]),
             "sslbm_ensemble_set_tiling": (i32, [_vp, i32, i32]),
@@ -505,12 +506,17 @@ def sslbm_fd4_steps_done(f) -> int:
     return int(load().sslbm_fd4_steps_done(f))
 
 
+def sslbm_fd4_set_order(f, order):
+    _check(load().sslbm_fd4_set_order(f, int(order)), "sslbm_fd4_set_order")
+
+
 class Fd4:
     """The fourth-order finite-difference reference (RK4 + fourth-order Laplacian) with a
     torch-allocated workspace; rates (beta, alpha, gamma, phi), d the physical
     diffusivities of S, E, I, R (and D = 0)."""
 
-    def __init__(self, nx, ny, rates, d, dx=1.0, dt=1.0, bc=BC_PERIODIC, precision=FP64, device=None, stream=None):
+    def __init__(self, nx, ny, rates, d, dx=1.0, dt=1.0, bc=BC_PERIODIC, precision=FP64, order=4, device=None,
+                 stream=None):
         import torch
         self.torch = torch
         self.device = torch.device(device if device is not None else "cuda")
@@ -521,6 +527,7 @@ class Fd4:
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.f = sslbm_fd4_create(self.grid, self.params, self.ws.data_ptr(), nbytes, self.stream.cuda_stream)
+        sslbm_fd4_set_order(self.f, order)
 
     def close(self):
         if getattr(self, "f", None):

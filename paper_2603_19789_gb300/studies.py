@@ -22,11 +22,16 @@ accuracy   -- the accuracy comparison of Sec. III at scale: FP64 SSLBM and BGK a
               GPU fourth-order finite-difference RK4 reference under diffusive refinement
               (grids 64..512, fixed tau), relative L2 / max-norm errors and observed order.
 
+timing     -- the cost comparison of Sec. IV (Table tab:timing): time per step of SSLBM,
+              BGK, second- and fourth-order FDM (RK4) in FP64 and FP32 on grids 200..8192,
+              normalised by the FP64 SSLBM at 200 x 200.
+
 Usage:  python -m paper_2603_19789_gb300.studies precision [--n 4096] [--steps 50000]
         [--checkpoints 5] [--out FILE]
         python -m paper_2603_19789_gb300.studies surrogate [--n 256] [--trajectories 2000]
         [--train-steps 3000] [--out FILE]
         python -m paper_2603_19789_gb300.studies accuracy [--out FILE]
+        python -m paper_2603_19789_gb300.studies timing [--out FILE]
 """
 from __future__ import annotations
 
@@ -155,6 +160,64 @@ def accuracy_study(sizes=(64, 128, 256, 512), d_phys=1e-4, d_lattice=0.05, t_end
     return out
 
 
+def timing_study(sizes=(200, 400, 600, 800, 1000, 2048, 4096, 8192), budget_ms=150.0):
+    """The cost comparison of Sec. IV (Table tab:timing) on one GB300: time per step of the
+    SSLBM, the BGK LBM, the second-order FDM and the fourth-order FDM (both RK4 in time)
+    on n x n periodic grids, in FP64 and FP32, normalised by the FP64 SSLBM at 200 x 200
+    as the paper normalises by its SSLBM at 200 x 200.  The state is the centre-bump
+    workload (d = 0.05 lattice units for S, E, I, R; R0 = 3 with gamma + mu = 0.11).
+    Each case: 3 warm-up steps, a trial, then enough steps for about budget_ms, timed with
+    CUDA events on the solver's stream.  FP32 SSLBM uses the library's default blocking."""
+    import torch
+    rates = inputs.rates_from_sigma_mu(3 * 0.11, 0.2, 0.1, 0.01).as_tuple()
+    d = (0.05, 0.05, 0.05, 0.05, 0.0)
+    cases = [("SSLBM", L.FP64), ("BGK", L.FP64), ("FDM 2nd", L.FP64), ("FDM 4th", L.FP64),
+             ("SSLBM", L.FP32), ("BGK", L.FP32), ("FDM 2nd", L.FP32), ("FDM 4th", L.FP32)]
+    out = {"sizes": list(sizes), "unit": "ms per step", "cases": [], "rows": {}}
+    for n in sizes:
+        st = inputs.centre_bump_workload(n, n)["state"]
+        row = {}
+        for name, prec in cases:
+            if name == "SSLBM":
+                obj = L.Solver(n, n, rates, d=d, precision=prec)
+                obj.write(st if prec == L.FP64 else st.astype(np.float32))
+                run = obj.step
+            elif name == "BGK":
+                obj = L.Solver(n, n, rates, d=d, precision=prec, schemes=L.WANT_BGK)
+                obj.write(st, scheme=L.SCHEME_BGK)
+                run = obj.bgk_step
+            else:
+                obj = L.Fd4(n, n, rates, d[:4], precision=prec, order=2 if name == "FDM 2nd" else 4)
+                obj.write(st)
+                run = obj.step
+            stream = obj.stream
+            run(3)
+
+            def timed(k):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                run(k)
+                b.record(stream)
+                b.synchronize()
+                return a.elapsed_time(b) / k
+
+            trial = timed(5)
+            k = int(min(20000, max(5, budget_ms / max(trial, 1e-4))))
+            ms = timed(k)
+            obj.close()
+            del obj
+            torch.cuda.empty_cache()
+            key = f"{name} {'fp64' if prec == L.FP64 else 'fp32'}"
+            row[key] = {"ms_per_step": ms, "glups": n * n / (ms * 1e-3) / 1e9, "steps_timed": k}
+        out["rows"][str(n)] = row
+    base = out["rows"][str(sizes[0])]["SSLBM fp64"]["ms_per_step"]
+    for n in sizes:
+        for key, v in out["rows"][str(n)].items():
+            v["normalised"] = v["ms_per_step"] / base
+    return out
+
+
 def surrogate_study(n=256, trajectories=2000, snapshots=10, horizon=2000, train_steps=20000, batch=16,
                     lr=1e-3, width=32, modes=12, layers=4, hidden=64, scenarios=64, rollout_steps=100,
                     params=None):
@@ -194,7 +257,7 @@ def surrogate_study(n=256, trajectories=2000, snapshots=10, horizon=2000, train_
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["precision", "surrogate", "accuracy"])
+    ap.add_argument("study", choices=["precision", "surrogate", "accuracy", "timing"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--steps", type=int, default=50000)
     ap.add_argument("--checkpoints", type=int, default=6)
@@ -205,8 +268,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     from . import build
     build.build()
-    if args.study == "accuracy":
-        res = accuracy_study()
+    if args.study in ("accuracy", "timing"):
+        res = accuracy_study() if args.study == "accuracy" else timing_study()
         text = json.dumps(res, indent=1)
         if args.out:
             with open(args.out, "w") as fh:

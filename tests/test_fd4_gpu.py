@@ -1,5 +1,5 @@
 """The fourth-order finite-difference reference on the GPU (sslbm_fd4_*) against the FP64
-oracle's fd4_rk4_run.
+oracle's fd4_rk4_run, and its second-order variant against fd2_rk4_run.
 
 The kernels evaluate every operation in the oracle's order with one rounding each (no
 contraction) and IEEE division, so FP64 agrees to the last bit up to the order of nothing
@@ -52,6 +52,18 @@ def test_fp64_matches_oracle(bc, nx, ny):
 
 
 @pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
+@pytest.mark.parametrize("nx,ny", [(37, 29), (3, 5)])
+def test_second_order_fp64_matches_oracle(bc, nx, ny):
+    st = _state(nx, ny, 2 * nx + ny)
+    f = L.Fd4(nx, ny, RATES, D, dx=0.7, dt=0.9, bc=bc, precision=L.FP64, order=2)
+    f.write(st)
+    f.step(12)
+    ref = oracle.fd2_rk4_run(st, D, RATES, 0.7, 0.9, bc, 12)
+    assert relmax(f.read(), ref) <= 1e-15
+    f.close()
+
+
+@pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
 def test_fp32_matches_oracle(bc):
     st = _state(45, 33, 3)
     f = L.Fd4(45, 33, RATES, D, dx=0.5, dt=0.8, bc=bc, precision=L.FP32)
@@ -98,3 +110,5 @@ def test_rejects_what_it_does_not_run():
         L.Fd4(16, 16, RATES, D, precision=L.FP32_DEV)
     with pytest.raises(L.SslbmError):
         L.Fd4(16, 16, RATES, (0.05, 0.05, 0.05, 0.05, 0.01))  # D does not move
+    with pytest.raises(L.SslbmError):
+        L.Fd4(16, 16, RATES, D, order=3)
