@@ -121,6 +121,64 @@ void oracle_sslbm_step(i64 nx, i64 ny, int bc, const double tau[4], const double
   }
 }
 
+/*
+ * The SSLBM on the D2Q9 lattice (Sec. II.C, isotropy discussion): the same update,
+ * Eq. (sslbm_final_clean), with rho_f and rho_b summed over the nine velocities
+ * c_0 = (0,0), c_1..4 = (+-1,0),(0,+-1), c_5..8 = (+-1,+-1), weights 4/9, 1/9, 1/36, and
+ * tau = 3 d dt / dx^2 + 1/2 (c_s^2 = 1/3 as on D2Q5).  Boundaries: periodic wrap per
+ * coordinate; no-flux as halfway bounce-back, a link that leaves the domain sees the
+ * cell's own value (on axis links this is the D2Q5 mirror; on diagonal links it keeps the
+ * discrete population exactly conserved, which a per-coordinate mirror does not).
+ */
+static const int CX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double W9[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+static inline double val9(const double* plane, i64 nx, i64 ny, int bc, i64 x0, i64 y0, i64 x, i64 y) {
+  if (bc == 0) return plane[wrap_or_clamp(y, ny, 0) * nx + wrap_or_clamp(x, nx, 0)];
+  if (x < 0 || x >= nx || y < 0 || y >= ny) return plane[y0 * nx + x0];
+  return plane[y * nx + x];
+}
+
+void oracle_sslbm9_step(i64 nx, i64 ny, int bc, const double tau[4], const double rates[4],
+                        double dt, const double* in, double* out) {
+  const i64 M = nx * ny;
+#pragma omp parallel for schedule(static)
+  for (i64 y = 0; y < ny; ++y) {
+    for (i64 x = 0; x < nx; ++x) {
+      const i64 k = y * nx + x;
+      double psi[5];
+      seird_sources(rates, in[0 * M + k], in[1 * M + k], in[2 * M + k], in[3 * M + k], psi);
+      for (int c = 0; c < 4; ++c) {
+        const double* p = in + c * M;
+        double rho_f = 0.0, rho_b = 0.0;
+        for (int i = 0; i < 9; ++i) {
+          rho_f += W9[i] * val9(p, nx, ny, bc, x, y, x + CX9[i], y + CY9[i]);
+          rho_b += W9[i] * val9(p, nx, ny, bc, x, y, x - CX9[i], y - CY9[i]);
+        }
+        const double rho_c = p[k];
+        out[c * M + k] = rho_b + (tau[c] - 1.0) * (rho_f - 2.0 * rho_c + rho_b) + psi[c] * dt;
+      }
+      out[4 * M + k] = in[4 * M + k] + psi[4] * dt;
+    }
+  }
+}
+
+void oracle_sslbm9_run(i64 nx, i64 ny, int bc, const double tau[4], const double rates[4],
+                       double dt, i64 nsteps, double* state, double* scratch) {
+  const i64 n = 5 * nx * ny;
+  double* a = state;
+  double* b = scratch;
+  for (i64 s = 0; s < nsteps; ++s) {
+    oracle_sslbm9_step(nx, ny, bc, tau, rates, dt, a, b);
+    double* t = a;
+    a = b;
+    b = t;
+  }
+  if (a != state) memcpy(state, a, (size_t)n * sizeof(double));
+}
+
 /* nsteps SSLBM steps; `state` holds the input and receives the result,
  * `scratch` is a second state-sized buffer. */
 void oracle_sslbm_run(i64 nx, i64 ny, int bc, const double tau[4], const double rates[4],
