@@ -431,6 +431,24 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
     g, ms = glups_of(L.FP32, 20, 2, schemes=L.WANT_BGK, bgk=True)
     out["bgk_fp32_glups"] = g
     out["bgk_fp32_hbm_frac"] = BGK_BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm
+    # the D2Q9 lattice (one step per launch, shared-memory tiles): 40 / 80 B per cell-step
+    for prec, name, nbytes in ((L.FP32, "fp32", BYTES_PER_CELL_FP32), (L.FP64, "fp64", BYTES_PER_CELL_FP64)):
+        s9 = L.Solver(NX, NY, rates, d=wl["d"], bc=wl["bc"], precision=prec, lattice=L.LATTICE_D2Q9)
+        s9.write(state32 if prec == L.FP32 else state64)
+        s9.step(2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20 if prec == L.FP32 else 6
+        a.record(stream)
+        s9.step(reps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[f"d2q9_{name}_glups"] = cells / (ms * 1e-3) / 1e9
+        out[f"d2q9_{name}_hbm_frac"] = nbytes * cells / (ms * 1e-3) / 1e9 / hbm
+        s9.close()
+        del s9
+        torch.cuda.empty_cache()
     # the fourth-order finite-difference reference (RK4): four stage kernels per step that
     # move 85 planes per cell (stage states, slope sum and u, read and written)
     for prec, name, esz, reps in ((L.FP64, "fp64", 8, 3), (L.FP32, "fp32", 4, 6)):

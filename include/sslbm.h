@@ -69,6 +69,11 @@ enum { SSLBM_ALL = -1 }; /* comp argument: all five planes, consecutive */
 enum { SSLBM_DT_F64 = 0, SSLBM_DT_F32 = 1 };
 /* schemes bitmask of sslbm_grid */
 enum { SSLBM_WANT_SSLBM = 1, SSLBM_WANT_BGK = 2 };
+/* lattice of sslbm_grid.  D2Q9 (Sec. II.C, isotropy discussion): rho_f and rho_b summed over
+ * the nine velocities (weights 4/9, 1/9, 1/36), the isotropic 9-point Laplacian; stable for
+ * 1/2 <= tau <= 13/8 (max(1 - Lambda9) = 8/9); no-flux walls as halfway bounce-back (a link
+ * leaving the domain sees the cell's own value), which conserves the population exactly. */
+enum { SSLBM_LATTICE_D2Q5 = 0, SSLBM_LATTICE_D2Q9 = 1 };
 
 /* ---- problem description (Sec. II.A problem statement, Sec. III test case) -- */
 typedef struct sslbm_grid {
@@ -78,7 +83,8 @@ typedef struct sslbm_grid {
                           cell-centred mirror; BGK: halfway bounce-back) */
   int32_t precision;   /* SSLBM_FP64 .. SSLBM_FP32_KAHAN (BGK supports FP64 and FP32) */
   int32_t schemes;     /* SSLBM_WANT_SSLBM | SSLBM_WANT_BGK: which state to hold */
-  int32_t reserved;    /* must be 0 */
+  int32_t lattice;     /* SSLBM_LATTICE_D2Q5 (0) or SSLBM_LATTICE_D2Q9 (1, SSLBM scheme only,
+                          FP64 or FP32, one step per launch) */
 } sslbm_grid;
 
 /* Epidemiological parameters in the notation of Table I:
@@ -88,10 +94,10 @@ typedef struct sslbm_grid {
  * (units dx^2 / dt, d[SSLBM_D] must be 0) converted with Eq. (diffusivity),
  * tau = 3 d dt / dx^2 + 1/2, or relaxation times tau[C] directly (use_tau != 0).
  * Stability (von Neumann analysis of Sec. II.C with the amplification
- * G = 1 - (2 tau - 1)(1 - Lambda)): 1/2 <= tau <= 5/4 for each mobile compartment,
- * otherwise sslbm_create returns SSLBM_ERR_UNSTABLE.  With strict != 0 the
- * nonnegativity condition 4 d_lattice + (outflow rate) dt <= 1 (outflow beta for S,
- * alpha for E, gamma for I) is enforced as well. */
+ * G = 1 - (2 tau - 1)(1 - Lambda)): 1/2 <= tau <= 5/4 for each mobile compartment
+ * (13/8 on D2Q9), otherwise sslbm_create returns SSLBM_ERR_UNSTABLE.  With strict != 0
+ * the nonnegativity condition 4 d_lattice + (outflow rate) dt <= 1 (20/6 d_lattice on
+ * D2Q9; outflow beta for S, alpha for E, gamma for I) is enforced as well. */
 typedef struct sslbm_params {
   double beta, alpha, gamma, phi;
   double d[5];        /* S, E, I, R, D */
@@ -290,7 +296,7 @@ int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e);
  *   d/dt C = Psi^C + d^C L4 C (C = S, E, I, R),   d/dt D = phi gamma I,
  * Psi from Eq. (sources) at every stage.  Boundaries: periodic wrap, or no-flux as the even
  * reflection about the boundary face (u[-1] = u[0], u[-2] = u[1]).  g: nx, ny, dx, dt, bc,
- * precision SSLBM_FP64 or SSLBM_FP32 (schemes and reserved are ignored).  p: beta, alpha,
+ * precision SSLBM_FP64 or SSLBM_FP32 (schemes and lattice are ignored).  p: beta, alpha,
  * gamma, phi and the physical diffusivities d[] (use_tau must be 0, d[D] = 0); RK4
  * stability needs d dt / dx^2 <= 0.26 for every compartment (else SSLBM_ERR_UNSTABLE).
  * State: five contiguous planes [5][ny][nx] in the workspace (4 states: u, two stage

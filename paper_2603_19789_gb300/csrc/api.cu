@@ -62,7 +62,11 @@ int check_grid(const sslbm_grid* g) {
   if (g->schemes < 1 || g->schemes > 3)
     return fail(SSLBM_ERR_BAD_ARG, "schemes=%d must be a nonzero mask of 1 (SSLBM) and 2 (BGK)",
                 g->schemes);
-  if (g->reserved != 0) return fail(SSLBM_ERR_BAD_ARG, "reserved field must be 0");
+  if (g->lattice != SSLBM_LATTICE_D2Q5 && g->lattice != SSLBM_LATTICE_D2Q9)
+    return fail(SSLBM_ERR_BAD_ARG, "lattice=%d is not a lattice code", g->lattice);
+  if (g->lattice == SSLBM_LATTICE_D2Q9 &&
+      (g->schemes != SSLBM_WANT_SSLBM || (g->precision != SSLBM_FP64 && g->precision != SSLBM_FP32)))
+    return fail(SSLBM_ERR_UNSUPPORTED, "the D2Q9 SSLBM is provided for the SSLBM scheme in FP64 and FP32");
   if ((g->schemes & SSLBM_WANT_BGK) && g->precision != SSLBM_FP64 && g->precision != SSLBM_FP32)
     return fail(SSLBM_ERR_UNSUPPORTED, "BGK state is provided in FP64 and FP32 only");
   return SSLBM_OK;
@@ -195,10 +199,11 @@ int sslbm_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_
     }
     if (!std::isfinite(tau[c]))
       return fail(SSLBM_ERR_BAD_ARG, "tau[%d] is not finite", c);
-    // |G| <= 1 for all modes needs (2 tau - 1) * max(1 - Lambda) <= 2, max(1 - Lambda) = 4/3
-    if (tau[c] < 0.5 || tau[c] > 1.25)
-      return fail(SSLBM_ERR_UNSTABLE, "tau[%d]=%.17g outside the stable range [1/2, 5/4]", c,
-                  tau[c]);
+    // |G| <= 1 for all modes needs (2 tau - 1) * max(1 - Lambda) <= 2, with max(1 - Lambda)
+    // = 4/3 on D2Q5 (tau <= 5/4) and 8/9 on D2Q9 (tau <= 13/8)
+    const double tau_max = g->lattice == SSLBM_LATTICE_D2Q9 ? 1.625 : 1.25;
+    if (tau[c] < 0.5 || tau[c] > tau_max)
+      return fail(SSLBM_ERR_UNSTABLE, "tau[%d]=%.17g outside the stable range [1/2, %g]", c, tau[c], tau_max);
   }
   if (!p->use_tau && p->d[4] != 0.0)
     return fail(SSLBM_ERR_BAD_ARG, "d[D]=%g: the deceased do not diffuse (must be 0)", p->d[4]);
@@ -206,11 +211,13 @@ int sslbm_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_
   for (int c = 0; c < 4; ++c) dl[c] = (tau[c] - 0.5) / 3.0;
   if (p->strict) {
     const double out_rate[4] = {p->beta, p->alpha, p->gamma, 0.0};
+    // the centre's weight in the update must stay >= 0: 1 - 4 d (D2Q5) or 1 - 20 d / 6 (D2Q9)
+    const double cw = g->lattice == SSLBM_LATTICE_D2Q9 ? 20.0 / 6.0 : 4.0;
     for (int c = 0; c < 4; ++c)
-      if (4.0 * dl[c] + out_rate[c] * g->dt > 1.0)
+      if (cw * dl[c] + out_rate[c] * g->dt > 1.0)
         return fail(SSLBM_ERR_UNSTABLE,
-                    "compartment %d: 4 d_lattice + outflow*dt = %g > 1 (nonnegativity)", c,
-                    4.0 * dl[c] + out_rate[c] * g->dt);
+                    "compartment %d: %g d_lattice + outflow*dt = %g > 1 (nonnegativity)", c, cw,
+                    cw * dl[c] + out_rate[c] * g->dt);
   }
   if (!dev_ws) return fail(SSLBM_ERR_WORKSPACE, "workspace is NULL");
   if (reinterpret_cast<uintptr_t>(dev_ws) % kAlign)
@@ -375,6 +382,16 @@ int sslbm_step(sslbm_handle* h, int64_t n) {
   if (st) return st;
   if (n < 0) return fail(SSLBM_ERR_BAD_ARG, "n=%lld < 0", (long long)n);
   DeviceGuard dg(h->device);
+  if (h->g.lattice == SSLBM_LATTICE_D2Q9) {
+    for (; n > 0; --n) {
+      cudaError_t e = sslbm::launch_sslbm9_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur],
+                                                 h->s_buf[1 - h->s_cur], h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "D2Q9 step launch");
+      h->s_cur = 1 - h->s_cur;
+      h->s_steps += 1;
+    }
+    return SSLBM_OK;
+  }
   const bool blocked = sslbm::blocked_supported(h->g.precision, h->gv);
   while (n > 0) {
     int k = 1;
@@ -451,9 +468,9 @@ int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows) {
   if (!h) return fail(SSLBM_ERR_BAD_ARG, "handle is NULL");
   if (k < 0 || k > SSLBM_MAX_DEPTH) return fail(SSLBM_ERR_BAD_ARG, "k=%d", k);
   if (seg_rows < 0) return fail(SSLBM_ERR_BAD_ARG, "seg_rows=%d", seg_rows);
-  const bool blocked = sslbm::blocked_supported(h->g.precision, h->gv);
+  const bool blocked = sslbm::blocked_supported(h->g.precision, h->gv) && h->g.lattice == SSLBM_LATTICE_D2Q5;
   if (!blocked && k > 1)
-    return fail(SSLBM_ERR_UNSUPPORTED, "temporal blocking is provided for FP32 and FP32_DEV");
+    return fail(SSLBM_ERR_UNSUPPORTED, "temporal blocking is provided for FP32 and FP32_DEV on D2Q5");
   h->depth = k == 0 ? (blocked ? 4 : 1) : k;
   if (seg_rows > 0 && seg_rows < 4 * h->depth) seg_rows = 4 * h->depth;
   h->seg_rows = seg_rows;
@@ -491,6 +508,7 @@ int sslbm_autotune(sslbm_handle* h, double budget_ms, int* depth_out, int* seg_o
   if (st) return st;
   if (!(budget_ms >= 0)) return fail(SSLBM_ERR_BAD_ARG, "budget_ms must be >= 0");
   if (budget_ms == 0) budget_ms = 300.0;
+  if (h->g.lattice != SSLBM_LATTICE_D2Q5) return fail(SSLBM_ERR_UNSUPPORTED, "the autotuner tunes the D2Q5 kernels");
   DeviceGuard dg(h->device);
   const TuneKey key{h->device, h->g.precision, h->g.bc, h->g.nx, h->g.ny};
   TuneResult best{1, 0, 0.0};

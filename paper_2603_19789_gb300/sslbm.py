@@ -30,6 +30,7 @@ S, E, I, R, D, NCOMP = 0, 1, 2, 3, 4, 5
 ALL = -1
 DT_F64, DT_F32 = 0, 1
 WANT_SSLBM, WANT_BGK = 1, 2
+LATTICE_D2Q5, LATTICE_D2Q9 = 0, 1
 MAX_DEPTH = 8
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP32_KAHAN}
 
@@ -61,7 +62,7 @@ class SslbmError(RuntimeError):
 class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("dx", ctypes.c_double),
                 ("dt", ctypes.c_double), ("bc", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("schemes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("schemes", ctypes.c_int32), ("lattice", ctypes.c_int32)]
 
 
 class Scenario(ctypes.Structure):
@@ -186,10 +187,11 @@ def sslbm_version() -> int:
     return int(load().sslbm_version())
 
 
-def make_grid(nx, ny, dx=1.0, dt=1.0, bc=BC_PERIODIC, precision=FP64, schemes=WANT_SSLBM) -> Grid:
+def make_grid(nx, ny, dx=1.0, dt=1.0, bc=BC_PERIODIC, precision=FP64, schemes=WANT_SSLBM,
+              lattice=LATTICE_D2Q5) -> Grid:
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
-    return Grid(int(nx), int(ny), float(dx), float(dt), int(bc), int(precision), int(schemes), 0)
+    return Grid(int(nx), int(ny), float(dx), float(dt), int(bc), int(precision), int(schemes), int(lattice))
 
 
 def make_params(beta, alpha, gamma, phi, d=None, tau=None, s_ref=1.0, strict=False) -> Params:
@@ -323,11 +325,12 @@ class Solver:
     """
 
     def __init__(self, nx, ny, rates, d=None, tau=None, dx=1.0, dt=1.0, bc=BC_PERIODIC,
-                 precision=FP64, schemes=WANT_SSLBM, s_ref=1.0, strict=False, device=None, stream=None):
+                 precision=FP64, schemes=WANT_SSLBM, s_ref=1.0, strict=False, device=None, stream=None,
+                 lattice=LATTICE_D2Q5):
         import torch
         self.torch = torch
         self.device = torch.device(device if device is not None else "cuda")
-        self.grid = make_grid(nx, ny, dx, dt, bc, precision, schemes)
+        self.grid = make_grid(nx, ny, dx, dt, bc, precision, schemes, lattice)
         self.params = make_params(*rates, d=d, tau=tau, s_ref=s_ref, strict=strict)
         self.nx, self.ny = int(nx), int(ny)
         nbytes = sslbm_workspace_bytes(self.grid)
