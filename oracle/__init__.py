@@ -75,6 +75,7 @@ def _load():
         lib.oracle_sslbm_step.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp]
         lib.oracle_sslbm_run.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double, _i64, _dp, _dp]
         lib.oracle_sslbm9_run.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double, _i64, _dp, _dp]
+        lib.oracle_slbm_run.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double, _i64, _dp, _dp]
         lib.oracle_bgk_init.argtypes = [_i64, _i64, _dp, _dp]
         lib.oracle_bgk_density.argtypes = [_i64, _i64, _dp, _dp]
         lib.oracle_bgk_step.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp]
@@ -164,6 +165,17 @@ def sslbm9_run(state, tau, rates, dt: float = 1.0, bc: int = 0, nsteps: int = 1)
     _, ny, nx = a.shape
     lib.oracle_sslbm9_run(nx, ny, int(bc), _ptr(_vec(tau, 4)), _ptr(_vec(rates, 4)), float(dt),
                           int(nsteps), _ptr(a), _ptr(scratch))
+    return a
+
+
+def slbm_run(state, tau, rates, dt: float = 1.0, bc: int = 0, nsteps: int = 1) -> np.ndarray:
+    """nsteps of the two-pass SLBM (predictor-corrector); returns the new (5, ny, nx) state."""
+    lib = _load()
+    a = _state(state)
+    scratch = np.empty_like(a)
+    _, ny, nx = a.shape
+    lib.oracle_slbm_run(nx, ny, int(bc), _ptr(_vec(tau, 4)), _ptr(_vec(rates, 4)), float(dt),
+                        int(nsteps), _ptr(a), _ptr(scratch))
     return a
 
 

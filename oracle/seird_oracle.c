@@ -179,6 +179,59 @@ void oracle_sslbm9_run(i64 nx, i64 ny, int bc, const double tau[4], const double
   if (a != state) memcpy(state, a, (size_t)n * sizeof(double));
 }
 
+/*
+ * The two-pass simplified LBM (SLBM) of Sec. II.C, Eqs. (SLBM1, SLBM2), on D2Q5:
+ *   predictor  rho*(x)   = sum_i w_i rho(x - c_i, t)
+ *   corrector  rho(x, t+dt) = rho*(x) + (tau - 1)(sum_i w_i rho*(x + c_i) - rho(x, t))
+ *                             + Psi(x, t) dt
+ * for C in {S, E, I, R}; D takes the explicit update of Eq. (rhoD).  Neighbours follow the
+ * same rule as the SSLBM (periodic wrap or the cell-centred mirror).  `pred` is a scratch
+ * of 4 planes.
+ */
+void oracle_slbm_step(i64 nx, i64 ny, int bc, const double tau[4], const double rates[4], double dt,
+                      const double* in, double* pred, double* out) {
+  const i64 M = nx * ny;
+#pragma omp parallel for schedule(static)
+  for (i64 y = 0; y < ny; ++y)
+    for (i64 x = 0; x < nx; ++x)
+      for (int c = 0; c < 4; ++c) {
+        const double* p = in + c * M;
+        double r = 0.0;
+        for (int i = 0; i < 5; ++i) r += W[i] * val(p, nx, ny, bc, x - CX[i], y - CY[i]);
+        pred[c * M + y * nx + x] = r;
+      }
+#pragma omp parallel for schedule(static)
+  for (i64 y = 0; y < ny; ++y)
+    for (i64 x = 0; x < nx; ++x) {
+      const i64 k = y * nx + x;
+      double psi[5];
+      seird_sources(rates, in[0 * M + k], in[1 * M + k], in[2 * M + k], in[3 * M + k], psi);
+      for (int c = 0; c < 4; ++c) {
+        const double* q = pred + c * M;
+        double s = 0.0;
+        for (int i = 0; i < 5; ++i) s += W[i] * val(q, nx, ny, bc, x + CX[i], y + CY[i]);
+        out[c * M + k] = q[k] + (tau[c] - 1.0) * (s - in[c * M + k]) + psi[c] * dt;
+      }
+      out[4 * M + k] = in[4 * M + k] + psi[4] * dt;
+    }
+}
+
+void oracle_slbm_run(i64 nx, i64 ny, int bc, const double tau[4], const double rates[4], double dt,
+                     i64 nsteps, double* state, double* scratch) {
+  const i64 n = 5 * nx * ny;
+  double* pred = (double*)malloc((size_t)(4 * nx * ny) * sizeof(double));
+  double* a = state;
+  double* b = scratch;
+  for (i64 s = 0; s < nsteps; ++s) {
+    oracle_slbm_step(nx, ny, bc, tau, rates, dt, a, pred, b);
+    double* t = a;
+    a = b;
+    b = t;
+  }
+  if (a != state) memcpy(state, a, (size_t)n * sizeof(double));
+  free(pred);
+}
+
 /* nsteps SSLBM steps; `state` holds the input and receives the result,
  * `scratch` is a second state-sized buffer. */
 void oracle_sslbm_run(i64 nx, i64 ny, int bc, const double tau[4], const double rates[4],
