@@ -449,6 +449,25 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
         s9.close()
         del s9
         torch.cuda.empty_cache()
+    # the two-pass SLBM: predictor (4 planes in, 4 out) + corrector (4 predictor + 5 state
+    # planes in, 5 out) = 22 planes per cell-step
+    for prec, name, esz in ((L.FP32, "fp32", 4), (L.FP64, "fp64", 8)):
+        s2 = L.Solver(NX, NY, rates, d=wl["d"], bc=wl["bc"], precision=prec, lattice=L.LATTICE_D2Q5_SLBM)
+        s2.write(state32 if prec == L.FP32 else state64)
+        s2.step(2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20 if prec == L.FP32 else 6
+        a.record(stream)
+        s2.step(reps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[f"slbm_{name}_glups"] = cells / (ms * 1e-3) / 1e9
+        out[f"slbm_{name}_hbm_frac"] = 22 * esz * cells / (ms * 1e-3) / 1e9 / hbm
+        s2.close()
+        del s2
+        torch.cuda.empty_cache()
     # the fourth-order finite-difference reference (RK4): four stage kernels per step that
     # move 85 planes per cell (stage states, slope sum and u, read and written)
     for prec, name, esz, reps in ((L.FP64, "fp64", 8, 3), (L.FP32, "fp32", 4, 6)):

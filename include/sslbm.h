@@ -73,7 +73,12 @@ enum { SSLBM_WANT_SSLBM = 1, SSLBM_WANT_BGK = 2 };
  * the nine velocities (weights 4/9, 1/9, 1/36), the isotropic 9-point Laplacian; stable for
  * 1/2 <= tau <= 13/8 (max(1 - Lambda9) = 8/9); no-flux walls as halfway bounce-back (a link
  * leaving the domain sees the cell's own value), which conserves the population exactly. */
-enum { SSLBM_LATTICE_D2Q5 = 0, SSLBM_LATTICE_D2Q9 = 1 };
+enum { SSLBM_LATTICE_D2Q5 = 0, SSLBM_LATTICE_D2Q9 = 1, SSLBM_LATTICE_D2Q5_SLBM = 2 };
+/* SSLBM_LATTICE_D2Q5_SLBM: the two-pass simplified LBM of Eqs. (SLBM1, SLBM2) on D2Q5,
+ * predictor rho* = sum_i w_i rho(x - c_i) and corrector
+ * rho(t + dt) = rho* + (tau - 1)(sum_i w_i rho*(x + c_i) - rho) + Psi dt (two kernels per
+ * step, four extra planes of workspace); stable for 1/2 <= tau <= 7/4; kept for comparison
+ * with the single-step SSLBM, which needs one pass. */
 
 /* ---- problem description (Sec. II.A problem statement, Sec. III test case) -- */
 typedef struct sslbm_grid {
@@ -83,8 +88,9 @@ typedef struct sslbm_grid {
                           cell-centred mirror; BGK: halfway bounce-back) */
   int32_t precision;   /* SSLBM_FP64 .. SSLBM_FP32_KAHAN (BGK supports FP64 and FP32) */
   int32_t schemes;     /* SSLBM_WANT_SSLBM | SSLBM_WANT_BGK: which state to hold */
-  int32_t lattice;     /* SSLBM_LATTICE_D2Q5 (0) or SSLBM_LATTICE_D2Q9 (1, SSLBM scheme only,
-                          FP64 or FP32, one step per launch) */
+  int32_t lattice;     /* SSLBM_LATTICE_D2Q5 (0), SSLBM_LATTICE_D2Q9 (1) or
+                          SSLBM_LATTICE_D2Q5_SLBM (2); 1 and 2: SSLBM scheme only, FP64 or FP32,
+                          no temporal blocking */
 } sslbm_grid;
 
 /* Epidemiological parameters in the notation of Table I:
@@ -95,7 +101,7 @@ typedef struct sslbm_grid {
  * tau = 3 d dt / dx^2 + 1/2, or relaxation times tau[C] directly (use_tau != 0).
  * Stability (von Neumann analysis of Sec. II.C with the amplification
  * G = 1 - (2 tau - 1)(1 - Lambda)): 1/2 <= tau <= 5/4 for each mobile compartment
- * (13/8 on D2Q9), otherwise sslbm_create returns SSLBM_ERR_UNSTABLE.  With strict != 0
+ * (13/8 on D2Q9, 7/4 for the two-pass SLBM), otherwise sslbm_create returns SSLBM_ERR_UNSTABLE.  With strict != 0
  * the nonnegativity condition 4 d_lattice + (outflow rate) dt <= 1 (20/6 d_lattice on
  * D2Q9; outflow beta for S, alpha for E, gamma for I) is enforced as well. */
 typedef struct sslbm_params {

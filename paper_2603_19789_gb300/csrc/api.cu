@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "sslbm_internal.cuh"
+#include "variants.cuh"
 
 using sslbm::Coeffs;
 using sslbm::GridView;
@@ -42,7 +43,7 @@ struct Layout {
   int64_t pitch = 0, plane = 0;
   size_t esize = 0, plane_bytes = 0;
   int s_planes = 0;  // SSLBM planes per state buffer (5, or 10 with Kahan compensation)
-  size_t off_diag = 0, off_s[2] = {0, 0}, off_b[2] = {0, 0}, total = 0;
+  size_t off_diag = 0, off_s[2] = {0, 0}, off_b[2] = {0, 0}, off_pred = 0, total = 0;
 };
 
 constexpr int kBgkPlanes = 21;
@@ -62,11 +63,11 @@ int check_grid(const sslbm_grid* g) {
   if (g->schemes < 1 || g->schemes > 3)
     return fail(SSLBM_ERR_BAD_ARG, "schemes=%d must be a nonzero mask of 1 (SSLBM) and 2 (BGK)",
                 g->schemes);
-  if (g->lattice != SSLBM_LATTICE_D2Q5 && g->lattice != SSLBM_LATTICE_D2Q9)
+  if (g->lattice != SSLBM_LATTICE_D2Q5 && g->lattice != SSLBM_LATTICE_D2Q9 && g->lattice != SSLBM_LATTICE_D2Q5_SLBM)
     return fail(SSLBM_ERR_BAD_ARG, "lattice=%d is not a lattice code", g->lattice);
-  if (g->lattice == SSLBM_LATTICE_D2Q9 &&
+  if (g->lattice != SSLBM_LATTICE_D2Q5 &&
       (g->schemes != SSLBM_WANT_SSLBM || (g->precision != SSLBM_FP64 && g->precision != SSLBM_FP32)))
-    return fail(SSLBM_ERR_UNSUPPORTED, "the D2Q9 SSLBM is provided for the SSLBM scheme in FP64 and FP32");
+    return fail(SSLBM_ERR_UNSUPPORTED, "the D2Q9 and two-pass updates are provided for the SSLBM scheme in FP64 and FP32");
   if ((g->schemes & SSLBM_WANT_BGK) && g->precision != SSLBM_FP64 && g->precision != SSLBM_FP32)
     return fail(SSLBM_ERR_UNSUPPORTED, "BGK state is provided in FP64 and FP32 only");
   return SSLBM_OK;
@@ -95,6 +96,10 @@ int make_layout(const sslbm_grid* g, Layout* L) {
       L->off_b[b] = off;
       off += (size_t)kBgkPlanes * L->plane_bytes;
     }
+  if (g->lattice == SSLBM_LATTICE_D2Q5_SLBM) {  // the predictor's four planes
+    L->off_pred = off;
+    off += (size_t)4 * L->plane_bytes;
+  }
   L->total = off;
   return SSLBM_OK;
 }
@@ -130,6 +135,7 @@ struct sslbm_handle {
   char* ws = nullptr;
   char* s_buf[2] = {nullptr, nullptr};
   char* b_buf[2] = {nullptr, nullptr};
+  char* pred = nullptr;  // two-pass SLBM predictor planes
   int s_cur = 0, b_cur = 0;
   int64_t s_steps = 0, b_steps = 0;
   int depth = 1, seg_rows = 0;
@@ -201,7 +207,9 @@ int sslbm_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_
       return fail(SSLBM_ERR_BAD_ARG, "tau[%d] is not finite", c);
     // |G| <= 1 for all modes needs (2 tau - 1) * max(1 - Lambda) <= 2, with max(1 - Lambda)
     // = 4/3 on D2Q5 (tau <= 5/4) and 8/9 on D2Q9 (tau <= 13/8)
-    const double tau_max = g->lattice == SSLBM_LATTICE_D2Q9 ? 1.625 : 1.25;
+    // (two-pass SLBM: G = Lambda + (tau - 1)(Lambda^2 - 1), |G| <= 1 on Lambda in [-1/3, 1]
+    // for tau <= 7/4)
+    const double tau_max = g->lattice == SSLBM_LATTICE_D2Q9 ? 1.625 : (g->lattice == SSLBM_LATTICE_D2Q5_SLBM ? 1.75 : 1.25);
     if (tau[c] < 0.5 || tau[c] > tau_max)
       return fail(SSLBM_ERR_UNSTABLE, "tau[%d]=%.17g outside the stable range [1/2, %g]", c, tau[c], tau_max);
   }
@@ -263,6 +271,7 @@ int sslbm_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_
     for (int b = 0; b < 2; ++b) h->s_buf[b] = h->ws + L.off_s[b];
   if (g->schemes & SSLBM_WANT_BGK)
     for (int b = 0; b < 2; ++b) h->b_buf[b] = h->ws + L.off_b[b];
+  if (g->lattice == SSLBM_LATTICE_D2Q5_SLBM) h->pred = h->ws + L.off_pred;
   h->depth = sslbm::blocked_supported(g->precision, h->gv) ? 4 : 1;
   DeviceGuard dg(h->device);
   // zero state buffers (and their row padding) so every scheme starts from a defined state
@@ -382,6 +391,18 @@ int sslbm_step(sslbm_handle* h, int64_t n) {
   if (st) return st;
   if (n < 0) return fail(SSLBM_ERR_BAD_ARG, "n=%lld < 0", (long long)n);
   DeviceGuard dg(h->device);
+  if (h->g.lattice == SSLBM_LATTICE_D2Q5_SLBM) {
+    double tm1[4];
+    for (int c = 0; c < 4; ++c) tm1[c] = h->tau[c] - 1.0;
+    for (; n > 0; --n) {
+      cudaError_t e = sslbm::launch_slbm_step(h->g.precision, h->gv, h->coeffs(), tm1, h->s_buf[h->s_cur], h->pred,
+                                              h->s_buf[1 - h->s_cur], h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "SLBM step launch");
+      h->s_cur = 1 - h->s_cur;
+      h->s_steps += 1;
+    }
+    return SSLBM_OK;
+  }
   if (h->g.lattice == SSLBM_LATTICE_D2Q9) {
     for (; n > 0; --n) {
       cudaError_t e = sslbm::launch_sslbm9_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur],

@@ -13,7 +13,7 @@
 // the wrapped neighbours; no-flux: the clamped ones, corrected per link at the walls).
 #include <cuda_runtime.h>
 
-#include "sslbm_internal.cuh"
+#include "variants.cuh"
 
 namespace sslbm {
 namespace {

@@ -204,9 +204,6 @@ __device__ __forceinline__ void seird_cell2(const Coeffs<float>& k, float2 x0, f
 // ---- launchers (defined in the kernel translation units) --------------------------
 // SSLBM: one step per launch (every precision) and K fused steps per launch (FP32 and
 // FP32 deviation-S).  seg_rows > 0 is the blocked kernel's row-segment length.
-// one SSLBM step on the D2Q9 lattice (FP64 or FP32)
-cudaError_t launch_sslbm9_step1(int precision, const GridView& g, const void* coeffs, const void* in, void* out,
-                                cudaStream_t s);
 cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coeffs, const void* in,
                                void* out, cudaStream_t s);
 cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* coeffs,

@@ -30,7 +30,7 @@ S, E, I, R, D, NCOMP = 0, 1, 2, 3, 4, 5
 ALL = -1
 DT_F64, DT_F32 = 0, 1
 WANT_SSLBM, WANT_BGK = 1, 2
-LATTICE_D2Q5, LATTICE_D2Q9 = 0, 1
+LATTICE_D2Q5, LATTICE_D2Q9, LATTICE_D2Q5_SLBM = 0, 1, 2
 MAX_DEPTH = 8
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP32_KAHAN}
 
