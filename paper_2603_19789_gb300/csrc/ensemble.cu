@@ -70,7 +70,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 template <int MODE, int K>
-__global__ void __launch_bounds__(32 * K, 20 / K)
+__global__ void __launch_bounds__(32 * K, 16 / K)
     ensemble_kernel(const EnsScenario* __restrict__ tab, const int n, const int total_tiles,
                     const int nblocks, float* __restrict__ buf0, float* __restrict__ buf1,
                     EnsControl* ctl, unsigned* done, const long long spin_limit,

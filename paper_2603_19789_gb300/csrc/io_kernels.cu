@@ -2,6 +2,7 @@
 // solver's pitched storage, and the diagnostics reduction of Sec. II.C 'Mass conservation'
 // (per-compartment totals in double precision, peak infected density).
 #include <float.h>
+#include <stdint.h>
 
 #include "sslbm_internal.cuh"
 
@@ -117,6 +118,88 @@ __global__ void __launch_bounds__(256) diag_partial_kernel(const GridView g,
   }
 }
 
+// Knuth's TwoSum: hi + lo <- hi + x with the rounding error of the addition carried into lo,
+// so that FP32 arithmetic keeps the running sum to about twice FP32's precision.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+// The FP32 partials of diag_partial_kernel without per-cell FP64 arithmetic (few FP64 units
+// on this GPU): each thread reads 4 cells per plane at a time (16-byte loads; the pitch and
+// the plane stride are multiples of 4), keeps its share of the row as a TwoSum pair per
+// compartment and adds that pair to the FP64 partial once per row.  With at most a few dozen
+// cells per thread and row, the pair's own error stays near FP32's unit roundoff squared.
+// The peak of I is taken in FP32 (the same value as in FP64), or in FP64 as value minus
+// compensation when COMP.
+template <int LAYOUT, bool COMP>
+__global__ void __launch_bounds__(256) diag_partial_f32x4_kernel(const GridView g, const float* __restrict__ st,
+                                                                 const float* __restrict__ comp,
+                                                                 double* __restrict__ partials) {
+  double v[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0, -DBL_MAX};
+  for (int64_t y = blockIdx.x; y < g.ny; y += gridDim.x) {
+    float hi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float pk = -FLT_MAX;
+    for (int64_t x = 4 * (int64_t)threadIdx.x; x < g.nx; x += 4 * (int64_t)blockDim.x) {
+      const int64_t idx = y * g.pitch + x;
+      const int nv = g.nx - x < 4 ? (int)(g.nx - x) : 4;
+      float r[5][4];
+      if (LAYOUT == 0) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const float4 a = *reinterpret_cast<const float4*>(st + c * g.plane + idx);
+          r[c][0] = a.x, r[c][1] = a.y, r[c][2] = a.z, r[c][3] = a.w;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float4 a = *reinterpret_cast<const float4*>(st + (c * 5) * g.plane + idx);
+#pragma unroll
+          for (int i = 1; i < 5; ++i) {
+            const float4 b = *reinterpret_cast<const float4*>(st + (c * 5 + i) * g.plane + idx);
+            a.x = __fadd_rn(a.x, b.x), a.y = __fadd_rn(a.y, b.y), a.z = __fadd_rn(a.z, b.z), a.w = __fadd_rn(a.w, b.w);
+          }
+          r[c][0] = a.x, r[c][1] = a.y, r[c][2] = a.z, r[c][3] = a.w;
+        }
+        const float4 d = *reinterpret_cast<const float4*>(st + 20 * g.plane + idx);
+        r[4][0] = d.x, r[4][1] = d.y, r[4][2] = d.z, r[4][3] = d.w;
+      }
+      float q[5][4];
+      if (COMP) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const float4 b = *reinterpret_cast<const float4*>(comp + c * g.plane + idx);
+          q[c][0] = b.x, q[c][1] = b.y, q[c][2] = b.z, q[c][3] = b.w;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j >= nv) break;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          two_sum_add(hi[c], lo[c], r[c][j]);
+          if (COMP) two_sum_add(hi[c], lo[c], -q[c][j]);
+        }
+        if (COMP)
+          v[5] = fmax(v[5], (double)r[2][j] - (double)q[2][j]);
+        else
+          pk = fmaxf(pk, r[2][j]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) v[c] += (double)hi[c] + (double)lo[c];
+    if (!COMP) v[5] = fmax(v[5], (double)pk);
+  }
+  block_reduce6(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < kDiagSlots; ++j) partials[blockIdx.x * kDiagSlots + j] = v[j];
+  }
+}
+
 // Sum of the per-block partials in a fixed order (deterministic).
 __global__ void __launch_bounds__(256) diag_final_kernel(const double* __restrict__ partials,
                                                          int nblocks, double* __restrict__ result) {
@@ -195,6 +278,16 @@ cudaError_t launch_diagnostics(int precision, int layout, const GridView& g, con
     else
       diag_partial_kernel<double, 1><<<(unsigned)blocks, 256, 0, s>>>(g, (const double*)planes,
                                                                       nullptr, partials);
+  } else if (g.pitch % 4 == 0 && g.plane % 4 == 0 && reinterpret_cast<uintptr_t>(planes) % 16 == 0 &&
+             reinterpret_cast<uintptr_t>(comp_planes) % 16 == 0) {
+    const float* st = (const float*)planes;
+    const float* cp = (const float*)comp_planes;
+    if (layout == 1)
+      diag_partial_f32x4_kernel<1, false><<<(unsigned)blocks, 256, 0, s>>>(g, st, nullptr, partials);
+    else if (cp)
+      diag_partial_f32x4_kernel<0, true><<<(unsigned)blocks, 256, 0, s>>>(g, st, cp, partials);
+    else
+      diag_partial_f32x4_kernel<0, false><<<(unsigned)blocks, 256, 0, s>>>(g, st, nullptr, partials);
   } else {
     if (layout == 0)
       diag_partial_kernel<float, 0><<<(unsigned)blocks, 256, 0, s>>>(

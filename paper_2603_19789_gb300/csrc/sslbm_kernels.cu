@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) step1_kernel(const GridView g, const Coef
 }
 
 template <int MODE, int K>
-__global__ void __launch_bounds__(32 * K, 24 / K) pipe_kernel(const GridView g, const Coeffs<float> k,
+__global__ void __launch_bounds__(32 * K, 16 / K) pipe_kernel(const GridView g, const Coeffs<float> k,
                                                              const float* __restrict__ in,
                                                              float* __restrict__ out,
                                                              const int seg_rows, const int nstrips) {

@@ -45,6 +45,62 @@ struct PipeSmem {
   float rl[K - 1][2][5][128];
 };
 
+// One iteration of warp s: read its level's next row N from src, compute level s+1 of row C
+// from P, C, N (x neighbours by shuffles), and pass it to warp s+1 through the slot of parity
+// par, or (last warp) write it to row r of the output.  Ends with the CTA barrier.
+template <int MODE, int K>
+__device__ __forceinline__ void pipe_row(PipeSmem<K>& sm, const GridView& g, const Coeffs<float>& k,
+                                         const float* src, const float2 (&P)[5][2], const float2 (&C)[5][2],
+                                         float2 (&N)[5][2], float* __restrict__ out, const int s, const int lane,
+                                         const int par, const bool writer, const int64_t xs, const int64_t r,
+                                         const int64_t y0, const int64_t y1) {
+  constexpr unsigned kFull = 0xffffffffu;
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    const float4 t = *reinterpret_cast<const float4*>(src + 128 * f);
+    N[f][0] = make_float2(t.x, t.y);
+    N[f][1] = make_float2(t.z, t.w);
+  }
+  float2 lp[4][2];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const float L = __shfl_up_sync(kFull, C[f][1].y, 1);
+    const float R = __shfl_down_sync(kFull, C[f][0].x, 1);
+    // left + right neighbour of columns 0..3, then the packed rest of lap5
+    const float2 lr0 = make_float2(__fadd_rn(L, C[f][0].y), __fadd_rn(C[f][0].x, C[f][1].x));
+    const float2 lr1 = make_float2(__fadd_rn(C[f][0].y, C[f][1].y), __fadd_rn(C[f][1].x, R));
+    lp[f][0] = lap5x2(C[f][0], lr0, P[f][0], N[f][0]);
+    lp[f][1] = lap5x2(C[f][1], lr1, P[f][1], N[f][1]);
+  }
+  float2 M[5][2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    seird_cell2<MODE == MODE_DEV>(k, C[0][h], C[1][h], C[2][h], C[3][h], C[4][h], lp[0][h], lp[1][h], lp[2][h],
+                                  lp[3][h], M[0][h], M[1][h], M[2][h], M[3][h], M[4][h]);
+  if (s < K - 1) {
+    float* dst = &sm.rl[s < K - 1 ? s : 0][par][0][4 * lane];
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+      *reinterpret_cast<float4*>(dst + 128 * f) = make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
+  } else if (writer && r >= y0 && r < y1) {
+    float* o = out + r * g.pitch + xs;
+    if (xs + 3 < g.nx) {
+#pragma unroll
+      for (int f = 0; f < 5; ++f)
+        *reinterpret_cast<float4*>(o + f * g.plane) = make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
+    } else {
+#pragma unroll
+      for (int f = 0; f < 5; ++f) {
+        const float v[4] = {M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y};
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          if (xs + jj < g.nx) o[f * g.plane + jj] = v[jj];
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // WRAP16: periodic grid with nx a multiple of 4 -- every lane's four columns, ghosts
 // included, are one contiguous 16-byte group at the wrapped position, so all loads are
 // L2-only cp.async.cg (required when other CTAs of the same launch wrote the input, since
@@ -53,7 +109,6 @@ template <int MODE, int K, bool WRAP16 = false>
 __device__ __forceinline__ void pipe_tile(PipeSmem<K>& sm, const GridView& g, const Coeffs<float>& k,
                                           const float* __restrict__ in, float* __restrict__ out,
                                           const int strip, const int64_t y0, const int64_t y1) {
-  constexpr unsigned kFull = 0xffffffffu;
   constexpr int HL = (K + 3) / 4;   // halo lanes on each side of the strip
   constexpr int WV = 128 - 8 * HL;  // columns written per strip
   const int lane = threadIdx.x & 31;
@@ -103,85 +158,39 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K>& sm, const GridView& g, co
     }
   }
 
-  // this warp's level: rows q-2s-2 (P) and q-2s-1 (C) as column pairs (0,1) and (2,3)
-  float2 P[4][2], C[4][2], CD[2];
+  // Three row buffers rotate through the roles P (row q-2s-2), C (q-2s-1) and N (q-2s) of
+  // this warp's level, unrolled three ways so that no row is copied between registers.
+  float2 RA[5][2], RB[5][2], RC[5][2];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    CD[h] = make_float2(0.f, 0.f);
+  for (int f = 0; f < 5; ++f)
 #pragma unroll
-    for (int f = 0; f < 4; ++f) P[f][h] = C[f][h] = make_float2(0.f, 0.f);
-  }
+    for (int h = 0; h < 2; ++h) RA[f][h] = RB[f][h] = make_float2(0.f, 0.f);
 
-  for (int64_t q = qa; q < qb; ++q) {
-    float2 N[5][2];
-    const float* src;
+  const int nq = (int)(qb - qa), nload = (int)(load_end - qa), par0 = (int)((qa - 1) & 1);
+  const int64_t r0 = qa - 2 * K + 1;  // the level-K row the last warp finishes at iteration 0
+  // Row source of iteration j (q = qa + j): warp 0's ring slot, or the previous warp's slot.
+  auto fetch = [&](int j) -> const float* {
     if (s == 0) {
-      if (q + kRing0 - 1 < load_end) issue(q + kRing0 - 1);
+      if (j + kRing0 - 1 < nload) issue(qa + j + kRing0 - 1);
       cp_async_commit();
       cp_async_wait<kRing0 - 1>();
-      src = &sm.r0[(int)((q - qa) % kRing0)][0][4 * lane];
-    } else {
-      src = &sm.rl[s - 1][(int)((q - 1) & 1)][0][4 * lane];
+      return &sm.r0[j & (kRing0 - 1)][0][4 * lane];
     }
-#pragma unroll
-    for (int f = 0; f < 5; ++f) {
-      const float4 t = *reinterpret_cast<const float4*>(src + 128 * f);
-      N[f][0] = make_float2(t.x, t.y);
-      N[f][1] = make_float2(t.z, t.w);
-    }
-    float2 lp[4][2];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const float L = __shfl_up_sync(kFull, C[f][1].y, 1);
-      const float R = __shfl_down_sync(kFull, C[f][0].x, 1);
-      // left + right neighbour of columns 0..3, then the packed rest of lap5
-      const float2 lr0 = make_float2(__fadd_rn(L, C[f][0].y), __fadd_rn(C[f][0].x, C[f][1].x));
-      const float2 lr1 = make_float2(__fadd_rn(C[f][0].y, C[f][1].y), __fadd_rn(C[f][1].x, R));
-      lp[f][0] = lap5x2(C[f][0], lr0, P[f][0], N[f][0]);
-      lp[f][1] = lap5x2(C[f][1], lr1, P[f][1], N[f][1]);
-    }
-    float2 M[5][2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-      seird_cell2<MODE == MODE_DEV>(k, C[0][h], C[1][h], C[2][h], C[3][h], CD[h], lp[0][h], lp[1][h],
-                                    lp[2][h], lp[3][h], M[0][h], M[1][h], M[2][h], M[3][h], M[4][h]);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        P[f][h] = C[f][h];
-        C[f][h] = N[f][h];
-      }
-      CD[h] = N[4][h];
-    }
-    if (s < K - 1) {
-      float* dst = &sm.rl[s < K - 1 ? s : 0][(int)(q & 1)][0][4 * lane];
-#pragma unroll
-      for (int f = 0; f < 5; ++f)
-        *reinterpret_cast<float4*>(dst + 128 * f) =
-            make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
-    } else {
-      const int64_t r = q - 2 * K + 1;
-      if (writer && r >= y0 && r < y1) {
-        float* o = out + r * g.pitch + xs;
-        if (xs + 3 < g.nx) {
-#pragma unroll
-          for (int f = 0; f < 5; ++f)
-            *reinterpret_cast<float4*>(o + f * g.plane) =
-                make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
-        } else {
-#pragma unroll
-          for (int f = 0; f < 5; ++f) {
-            const float v[4] = {M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y};
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (xs + j < g.nx) o[f * g.plane + j] = v[j];
-          }
-        }
-      }
-    }
-    __syncthreads();
+    return &sm.rl[s - 1][(j + par0) & 1][0][4 * lane];
+  };
+  int j = 0;
+  for (; j + 3 <= nq; j += 3) {
+    pipe_row<MODE, K>(sm, g, k, fetch(j), RA, RB, RC, out, s, lane, (j + par0 + 1) & 1, writer, xs, r0 + j, y0, y1);
+    pipe_row<MODE, K>(sm, g, k, fetch(j + 1), RB, RC, RA, out, s, lane, (j + par0) & 1, writer, xs, r0 + j + 1, y0,
+                      y1);
+    pipe_row<MODE, K>(sm, g, k, fetch(j + 2), RC, RA, RB, out, s, lane, (j + par0 + 1) & 1, writer, xs, r0 + j + 2,
+                      y0, y1);
   }
+  if (j < nq)
+    pipe_row<MODE, K>(sm, g, k, fetch(j), RA, RB, RC, out, s, lane, (j + par0 + 1) & 1, writer, xs, r0 + j, y0, y1);
+  if (j + 1 < nq)
+    pipe_row<MODE, K>(sm, g, k, fetch(j + 1), RB, RC, RA, out, s, lane, (j + par0) & 1, writer, xs, r0 + j + 1, y0,
+                      y1);
   if (s == 0) cp_async_wait<0>();
 }
 

@@ -232,6 +232,23 @@ def test_diagnostics_match_oracle_on_read_back_state(precision):
     assert pk == pytest.approx(opk, rel=1e-7)
 
 
+@pytest.mark.parametrize("precision,scheme", [(L.FP32, L.SCHEME_SSLBM), (L.FP32_DEV, L.SCHEME_SSLBM),
+                                              (L.FP32_KAHAN, L.SCHEME_SSLBM), (L.FP32, L.SCHEME_BGK)])
+def test_diagnostics_on_wide_rows(precision, scheme):
+    """Rows of 4099 cells: a thread of the FP32 reduction adds several 4-cell groups of a row
+    in its TwoSum pair, and the row's last group holds three cells."""
+    wl = small_workload(4099, 13, 1, seed=21)
+    bgk = scheme == L.SCHEME_BGK
+    s = solver_for(wl, precision, schemes=L.WANT_BGK if bgk else L.WANT_SSLBM)
+    s.write(wl["state"], scheme=scheme)
+    (s.bgk_step if bgk else s.step)(7)
+    st = s.read(scheme=scheme)
+    tot, pk = s.diagnostics(scheme=scheme)
+    otot, opk = oracle.diagnostics(st)
+    np.testing.assert_allclose(tot, otot, rtol=1e-12)
+    assert pk == pytest.approx(opk, rel=1e-7)
+
+
 def test_nonfinite_state_is_reported_not_trapped():
     wl = small_workload(40, 30, 0)
     st = wl["state"].copy()
