@@ -61,6 +61,26 @@ def test_fp32_matches_oracle(bc):
     assert relmax(got, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
+@pytest.mark.parametrize("nx,ny", [(301, 19), (513, 10), (128, 9), (1, 7), (2, 3), (5, 1)])
+def test_fp32_rows_span_warps_and_ragged_tails(bc, nx, ny):
+    """A warp covers 32 groups of a row: these widths put the warp's last lane, a ragged last
+    group and single-group rows at every kind of edge (periodic wrap and walls)."""
+    st = inputs.epidemic_state(nx, ny, 5 * nx + ny)
+    got, _ = _run(nx, ny, bc, L.FP32, 25, st)
+    tau = [oracle.tau_from_d(d) for d in D[:4]]
+    ref = oracle.sslbm9_run(st.astype(np.float32).astype(np.float64), tau, RATES, 1.0, bc, 25)
+    assert relmax(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
+def test_fp64_wide_rows(bc):
+    st = inputs.epidemic_state(263, 17, 9)
+    got, _ = _run(263, 17, bc, L.FP64, 25, st)
+    tau = [oracle.tau_from_d(d) for d in D[:4]]
+    assert relmax(got, oracle.sslbm9_run(st, tau, RATES, 1.0, bc, 25)) <= 1e-12
+
+
 def test_stability_range_and_what_it_does_not_run():
     # tau = 1.5 (d = 1/3) is stable on D2Q9 (<= 13/8) and not on D2Q5 (<= 5/4)
     s = L.Solver(8, 8, RATES, d=(1 / 3, 0.05, 0.05, 0.05, 0.0), lattice=L.LATTICE_D2Q9)
