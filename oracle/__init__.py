@@ -23,6 +23,13 @@ Parity status of each routine (the pins live in tests/test_oracle_pins.py):
                    spatial convergence against the analytic diffusion mode.
   ode_rk4          pinned: fourth-order convergence against scipy's DOP853.
   diagnostics      pinned: exact sums of integer-valued fields, known maxima.
+  sslbm9_run       pinned (tests/test_oracle_d2q9.py): exact mode factor with the D2Q9
+                   symbol, fourth-order isotropy, conservation, brute force.
+  slbm_run         pinned (tests/test_oracle_slbm.py): exact predictor-corrector mode
+                   factor, conservation, brute force.
+  sslbm_vard_run   pinned (tests/test_oracle_vard.py): uniform fields give the SSLBM,
+                   conservation, symmetric operator, exact anisotropic mode factor,
+                   maximum principle, brute force.
 """
 from __future__ import annotations
 
@@ -76,6 +83,8 @@ def _load():
         lib.oracle_sslbm_run.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double, _i64, _dp, _dp]
         lib.oracle_sslbm9_run.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double, _i64, _dp, _dp]
         lib.oracle_slbm_run.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double, _i64, _dp, _dp]
+        lib.oracle_sslbm_vard_run.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp,
+                                              _i64, _dp, _dp]
         lib.oracle_bgk_init.argtypes = [_i64, _i64, _dp, _dp]
         lib.oracle_bgk_density.argtypes = [_i64, _i64, _dp, _dp]
         lib.oracle_bgk_step.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp]
@@ -176,6 +185,22 @@ def slbm_run(state, tau, rates, dt: float = 1.0, bc: int = 0, nsteps: int = 1) -
     _, ny, nx = a.shape
     lib.oracle_slbm_run(nx, ny, int(bc), _ptr(_vec(tau, 4)), _ptr(_vec(rates, 4)), float(dt),
                         int(nsteps), _ptr(a), _ptr(scratch))
+    return a
+
+
+def sslbm_vard_run(state, tau, rates, kx, ky, dt: float = 1.0, bc: int = 0, nsteps: int = 1) -> np.ndarray:
+    """nsteps of the SSLBM with per-cell diffusivity scale fields kx, ky ((ny, nx) each) in
+    the link form (the spatially varying, anisotropic extension of Sec. IV, as read here);
+    returns the new (5, ny, nx) state."""
+    lib = _load()
+    a = _state(state)
+    scratch = np.empty_like(a)
+    _, ny, nx = a.shape
+    fx = np.ascontiguousarray(kx, dtype=np.float64)
+    fy = np.ascontiguousarray(ky, dtype=np.float64)
+    assert fx.shape == (ny, nx) and fy.shape == (ny, nx), (fx.shape, fy.shape, (ny, nx))
+    lib.oracle_sslbm_vard_run(nx, ny, int(bc), _ptr(_vec(tau, 4)), _ptr(_vec(rates, 4)), float(dt), _ptr(fx),
+                              _ptr(fy), int(nsteps), _ptr(a), _ptr(scratch))
     return a
 
 

@@ -232,6 +232,61 @@ void oracle_slbm_run(i64 nx, i64 ny, int bc, const double tau[4], const double r
   free(pred);
 }
 
+/*
+ * The SSLBM with spatially varying, axis-anisotropic diffusion: the extension Sec. IV lists
+ * among the directions for future work.  The paper gives no discretisation for it; this is
+ * the reading the library uses.  The D2Q5 update in its link (flux) form,
+ *   rho(x, t+dt) = rho_c + sum_{i=1..4} D_i(x) (rho(x + c_i, t) - rho_c) + Psi(x, t) dt,
+ *   D_i(x) = d_lattice^C (k_a(x) + k_a(x + c_i)) / 2,
+ * with a = x on the links c_1, c_3 and a = y on c_2, c_4, d_lattice^C = (tau^C - 1/2) / 3,
+ * and per-cell scale fields kx, ky >= 0.  With kx = ky = 1 this is Eq. (sslbm_final_clean)
+ * on D2Q5, where rho_f = rho_b and rho_b + (tau - 1)(rho_f - 2 rho_c + rho_b)
+ * = rho_c + d_lattice sum_i (rho(x + c_i) - rho_c).  Both cells of a link use the same
+ * coefficient, so what one gains the other loses and the population total is conserved as
+ * in Sec. II.C.  Neighbours (of rho and of the scale fields) follow oracle_sslbm_step: the
+ * periodic wrap, or the boundary cell itself, whose difference is zero (no flux through a
+ * wall).  kx, ky: ny*nx values each, x fastest.  D takes the update of Eq. (rhoD).
+ */
+void oracle_sslbm_vard_step(i64 nx, i64 ny, int bc, const double tau[4], const double rates[4], double dt,
+                            const double* kx, const double* ky, const double* in, double* out) {
+  const i64 M = nx * ny;
+#pragma omp parallel for schedule(static)
+  for (i64 y = 0; y < ny; ++y) {
+    for (i64 x = 0; x < nx; ++x) {
+      const i64 k = y * nx + x;
+      double psi[5];
+      seird_sources(rates, in[0 * M + k], in[1 * M + k], in[2 * M + k], in[3 * M + k], psi);
+      for (int c = 0; c < 4; ++c) {
+        const double* p = in + c * M;
+        const double d_lattice = (tau[c] - 0.5) / 3.0;
+        const double rho_c = p[k];
+        double flux = 0.0;
+        for (int i = 1; i < 5; ++i) {
+          const double* kap = CX[i] != 0 ? kx : ky;
+          const double k_link = 0.5 * (kap[k] + val(kap, nx, ny, bc, x + CX[i], y + CY[i]));
+          flux += k_link * (val(p, nx, ny, bc, x + CX[i], y + CY[i]) - rho_c);
+        }
+        out[c * M + k] = rho_c + d_lattice * flux + psi[c] * dt;
+      }
+      out[4 * M + k] = in[4 * M + k] + psi[4] * dt;
+    }
+  }
+}
+
+void oracle_sslbm_vard_run(i64 nx, i64 ny, int bc, const double tau[4], const double rates[4], double dt,
+                           const double* kx, const double* ky, i64 nsteps, double* state, double* scratch) {
+  const i64 n = 5 * nx * ny;
+  double* a = state;
+  double* b = scratch;
+  for (i64 s = 0; s < nsteps; ++s) {
+    oracle_sslbm_vard_step(nx, ny, bc, tau, rates, dt, kx, ky, a, b);
+    double* t = a;
+    a = b;
+    b = t;
+  }
+  if (a != state) memcpy(state, a, (size_t)n * sizeof(double));
+}
+
 /* nsteps SSLBM steps; `state` holds the input and receives the result,
  * `scratch` is a second state-sized buffer. */
 void oracle_sslbm_run(i64 nx, i64 ny, int bc, const double tau[4], const double rates[4],

@@ -3,8 +3,8 @@
 Each case edits one expression of oracle/seird_oracle.c in a temporary copy
 (a dropped term, a wrong sign, a swapped rate, a transposed axis, a wrong weight
 or boundary rule), builds it, and runs tests/test_oracle_pins.py against that
-build in a subprocess.  The pins pass on the real oracle; every mutant must be
-caught by at least one of them.  CPU only.
+build in a subprocess (or the routine's own pin file, where the mutant names one).  The
+pins pass on the real oracle; every mutant must be caught by at least one of them.  CPU only.
 """
 import os
 import subprocess
@@ -31,13 +31,23 @@ MUTANTS = {
     "fd4_coefficient": ("16.0 * p[y * nx + ghost2(x + 1, nx, bc)]", "15.0 * p[y * nx + ghost2(x + 1, nx, bc)]"),
     "rk4_weight": ("y[j] += dt / 6.0 * (k1[j] + 2.0 * k2[j]", "y[j] += dt / 6.0 * (k1[j] + 1.0 * k2[j]"),
     "diagnostics_drop_compensation": ("totals[c] = s + comp;", "totals[c] = s;"),
+    # the spatially varying diffusion routine, against its own pins
+    "vard_percell_coefficient": ("const double k_link = 0.5 * (kap[k] + val(kap, nx, ny, bc, x + CX[i], y + CY[i]));",
+                                 "const double k_link = kap[k];", "test_oracle_vard.py"),
+    "vard_axes_swapped": ("const double* kap = CX[i] != 0 ? kx : ky;", "const double* kap = CX[i] != 0 ? ky : kx;",
+                          "test_oracle_vard.py"),
+    "vard_d_lattice": ("const double d_lattice = (tau[c] - 0.5) / 3.0;", "const double d_lattice = (tau[c] - 0.5) / 6.0;",
+                       "test_oracle_vard.py"),
+    "vard_link_mean_halved_twice": ("const double k_link = 0.5 * (kap[k]", "const double k_link = 0.25 * (kap[k]",
+                                    "test_oracle_vard.py"),
 }
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    old, new = MUTANTS[name]
+    old, new, *pins = MUTANTS[name]
+    pins_file = pins[0] if pins else "test_oracle_pins.py"
     src = open(SRC).read()
     assert src.count(old) >= 1, f"mutation anchor not found: {old}"
     mutated = tmp_path / "seird_oracle_mut.c"
@@ -47,6 +57,6 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                     "-o", str(lib), str(mutated), "-lm"], check=True)
     env = dict(os.environ, SEIRD_ORACLE_LIB=str(lib), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins_file)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
