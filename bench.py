@@ -387,8 +387,10 @@ def e2e_timing(L, torch, s, state32, stream, world, steps=3):
 
 
 def secondary_timings(L, wl, state64, state32, stream, hbm):
-    """Other variants on the same grid: FP64, deviation-S, Kahan, depth sweep, BGK."""
+    """Other variants on the same grid: FP64, deviation-S, Kahan, depth sweep, BGK, D2Q9,
+    two-pass SLBM, varying diffusivity, FD4."""
     import torch
+    from paper_2603_19789_gb300 import inputs
     out = {}
     rates = wl["rates"].as_tuple()
     cells = NX * NY
@@ -467,6 +469,27 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
         out[f"slbm_{name}_hbm_frac"] = 22 * esz * cells / (ms * 1e-3) / 1e9 / hbm
         s2.close()
         del s2
+        torch.cuda.empty_cache()
+    # spatially varying, anisotropic diffusion: 5 state planes and the 2 scale planes read,
+    # 5 planes written = 12 planes per cell-step; a mobility map of a few 'cities'
+    kx, ky = inputs.mobility_fields(NX, NY, 7)
+    for prec, name, esz in ((L.FP32, "fp32", 4), (L.FP64, "fp64", 8)):
+        sv = L.Solver(NX, NY, rates, d=wl["d"], bc=wl["bc"], precision=prec, lattice=L.LATTICE_D2Q5_VARD)
+        sv.set_diffusivity_scale(kx, ky)
+        sv.write(state32 if prec == L.FP32 else state64)
+        sv.step(2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20 if prec == L.FP32 else 6
+        a.record(stream)
+        sv.step(reps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[f"vard_{name}_glups"] = cells / (ms * 1e-3) / 1e9
+        out[f"vard_{name}_hbm_frac"] = 12 * esz * cells / (ms * 1e-3) / 1e9 / hbm
+        sv.close()
+        del sv
         torch.cuda.empty_cache()
     # the fourth-order finite-difference reference (RK4): four stage kernels per step that
     # move 85 planes per cell (stage states, slope sum and u, read and written)

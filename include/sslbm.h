@@ -73,12 +73,15 @@ enum { SSLBM_WANT_SSLBM = 1, SSLBM_WANT_BGK = 2 };
  * the nine velocities (weights 4/9, 1/9, 1/36), the isotropic 9-point Laplacian; stable for
  * 1/2 <= tau <= 13/8 (max(1 - Lambda9) = 8/9); no-flux walls as halfway bounce-back (a link
  * leaving the domain sees the cell's own value), which conserves the population exactly. */
-enum { SSLBM_LATTICE_D2Q5 = 0, SSLBM_LATTICE_D2Q9 = 1, SSLBM_LATTICE_D2Q5_SLBM = 2 };
+enum { SSLBM_LATTICE_D2Q5 = 0, SSLBM_LATTICE_D2Q9 = 1, SSLBM_LATTICE_D2Q5_SLBM = 2, SSLBM_LATTICE_D2Q5_VARD = 3 };
 /* SSLBM_LATTICE_D2Q5_SLBM: the two-pass simplified LBM of Eqs. (SLBM1, SLBM2) on D2Q5,
  * predictor rho* = sum_i w_i rho(x - c_i) and corrector
  * rho(t + dt) = rho* + (tau - 1)(sum_i w_i rho*(x + c_i) - rho) + Psi dt (two kernels per
  * step, four extra planes of workspace); stable for 1/2 <= tau <= 7/4; kept for comparison
  * with the single-step SSLBM, which needs one pass. */
+/* SSLBM_LATTICE_D2Q5_VARD: the D2Q5 SSLBM with spatially varying, axis-anisotropic
+ * diffusion, set per cell by sslbm_set_diffusivity_scale (Sec. IV lists this extension as
+ * future work; the discretisation is this library's reading, given there). */
 
 /* ---- problem description (Sec. II.A problem statement, Sec. III test case) -- */
 typedef struct sslbm_grid {
@@ -88,9 +91,9 @@ typedef struct sslbm_grid {
                           cell-centred mirror; BGK: halfway bounce-back) */
   int32_t precision;   /* SSLBM_FP64 .. SSLBM_FP32_KAHAN (BGK supports FP64 and FP32) */
   int32_t schemes;     /* SSLBM_WANT_SSLBM | SSLBM_WANT_BGK: which state to hold */
-  int32_t lattice;     /* SSLBM_LATTICE_D2Q5 (0), SSLBM_LATTICE_D2Q9 (1) or
-                          SSLBM_LATTICE_D2Q5_SLBM (2); 1 and 2: SSLBM scheme only, FP64 or FP32,
-                          no temporal blocking */
+  int32_t lattice;     /* SSLBM_LATTICE_D2Q5 (0), SSLBM_LATTICE_D2Q9 (1),
+                          SSLBM_LATTICE_D2Q5_SLBM (2) or SSLBM_LATTICE_D2Q5_VARD (3); 1 to 3:
+                          SSLBM scheme only, FP64 or FP32, no temporal blocking */
 } sslbm_grid;
 
 /* Epidemiological parameters in the notation of Table I:
@@ -166,6 +169,31 @@ int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_
  * FP32_KAHAN the compensated value, both evaluated in double precision.
  * A host destination synchronises the stream; a device destination is stream-ordered. */
 int sslbm_read(sslbm_handle* h, int scheme, int comp, void* dst, int dst_dtype, int dst_on_device);
+
+/* Per-cell diffusivity scale fields of a SSLBM_LATTICE_D2Q5_VARD solver: spatially varying
+ * and axis-anisotropic diffusion, which Sec. IV lists as future work without a
+ * discretisation.  The reading implemented here is the D2Q5 update in its link (flux) form:
+ *   rho_new = rho_c + sum_i D_i (rho(x + c_i) - rho_c) + Psi dt,
+ *   D_i = d_lattice^C (k_a(x) + k_a(x + c_i)) / 2,
+ * with a = x on the two x links and a = y on the two y links, and
+ * d_lattice^C = (tau^C - 1/2) / 3 from the params.  This is the conservative discretisation
+ * of div(d(x) grad rho): both cells of a link share its coefficient, so the population is
+ * conserved exactly (Sec. II.C).  Uniform fields of 1 give Eq. (sslbm_final_clean).  A link
+ * through a no-flux wall carries nothing, and the periodic wrap links opposite edges.
+ * kx, ky: ny*nx values each, row-major (x fastest), of type src_dtype (SSLBM_DT_F64 or
+ * SSLBM_DT_F32), on the host (src_on_device = 0) or the device (1); ky == NULL uses kx for
+ * both axes (isotropic).  Values are rounded to the solver's precision and copied into its
+ * workspace; host sources are consumed before the call returns.
+ * Validation, on the stored values: every value finite and >= 0, else SSLBM_ERR_BAD_ARG;
+ * max_x sum_i D_i(x) <= 1 for every mobile compartment (links through a no-flux wall left
+ * out), so that the centre weight of the update stays >= 0 and the diffusion part keeps a
+ * maximum principle (with strict, the outflow rate times dt is added as in sslbm_params),
+ * else SSLBM_ERR_UNSTABLE.  On any failure the solver has no fields until a call succeeds, and
+ * sslbm_step returns SSLBM_ERR_BAD_ARG.  At create time a VARD solver only requires
+ * tau >= 1/2; the fields decide stability.  Synchronises the stream.
+ * Other lattices: SSLBM_ERR_UNSUPPORTED. */
+int sslbm_set_diffusivity_scale(sslbm_handle* h, const void* kx, const void* ky, int src_dtype,
+                                int src_on_device);
 
 /* ---- time stepping ------------------------------------------------------------------ */
 

@@ -43,7 +43,7 @@ struct Layout {
   int64_t pitch = 0, plane = 0;
   size_t esize = 0, plane_bytes = 0;
   int s_planes = 0;  // SSLBM planes per state buffer (5, or 10 with Kahan compensation)
-  size_t off_diag = 0, off_s[2] = {0, 0}, off_b[2] = {0, 0}, off_pred = 0, total = 0;
+  size_t off_diag = 0, off_s[2] = {0, 0}, off_b[2] = {0, 0}, off_pred = 0, off_kappa = 0, total = 0;
 };
 
 constexpr int kBgkPlanes = 21;
@@ -63,11 +63,13 @@ int check_grid(const sslbm_grid* g) {
   if (g->schemes < 1 || g->schemes > 3)
     return fail(SSLBM_ERR_BAD_ARG, "schemes=%d must be a nonzero mask of 1 (SSLBM) and 2 (BGK)",
                 g->schemes);
-  if (g->lattice != SSLBM_LATTICE_D2Q5 && g->lattice != SSLBM_LATTICE_D2Q9 && g->lattice != SSLBM_LATTICE_D2Q5_SLBM)
+  if (g->lattice != SSLBM_LATTICE_D2Q5 && g->lattice != SSLBM_LATTICE_D2Q9 && g->lattice != SSLBM_LATTICE_D2Q5_SLBM &&
+      g->lattice != SSLBM_LATTICE_D2Q5_VARD)
     return fail(SSLBM_ERR_BAD_ARG, "lattice=%d is not a lattice code", g->lattice);
   if (g->lattice != SSLBM_LATTICE_D2Q5 &&
       (g->schemes != SSLBM_WANT_SSLBM || (g->precision != SSLBM_FP64 && g->precision != SSLBM_FP32)))
-    return fail(SSLBM_ERR_UNSUPPORTED, "the D2Q9 and two-pass updates are provided for the SSLBM scheme in FP64 and FP32");
+    return fail(SSLBM_ERR_UNSUPPORTED,
+                "the D2Q9, two-pass and varying-diffusivity updates are provided for the SSLBM scheme in FP64 and FP32");
   if ((g->schemes & SSLBM_WANT_BGK) && g->precision != SSLBM_FP64 && g->precision != SSLBM_FP32)
     return fail(SSLBM_ERR_UNSUPPORTED, "BGK state is provided in FP64 and FP32 only");
   return SSLBM_OK;
@@ -99,6 +101,10 @@ int make_layout(const sslbm_grid* g, Layout* L) {
   if (g->lattice == SSLBM_LATTICE_D2Q5_SLBM) {  // the predictor's four planes
     L->off_pred = off;
     off += (size_t)4 * L->plane_bytes;
+  }
+  if (g->lattice == SSLBM_LATTICE_D2Q5_VARD) {  // the diffusivity scale planes kx, ky
+    L->off_kappa = off;
+    off += (size_t)2 * L->plane_bytes;
   }
   L->total = off;
   return SSLBM_OK;
@@ -136,6 +142,8 @@ struct sslbm_handle {
   char* s_buf[2] = {nullptr, nullptr};
   char* b_buf[2] = {nullptr, nullptr};
   char* pred = nullptr;  // two-pass SLBM predictor planes
+  char* kappa = nullptr;  // varying diffusivity: scale planes kx, ky
+  bool kappa_ok = false;  // the scale planes hold validated fields
   int s_cur = 0, b_cur = 0;
   int64_t s_steps = 0, b_steps = 0;
   int depth = 1, seg_rows = 0;
@@ -209,7 +217,10 @@ int sslbm_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_
     // = 4/3 on D2Q5 (tau <= 5/4) and 8/9 on D2Q9 (tau <= 13/8)
     // (two-pass SLBM: G = Lambda + (tau - 1)(Lambda^2 - 1), |G| <= 1 on Lambda in [-1/3, 1]
     // for tau <= 7/4)
-    const double tau_max = g->lattice == SSLBM_LATTICE_D2Q9 ? 1.625 : (g->lattice == SSLBM_LATTICE_D2Q5_SLBM ? 1.75 : 1.25);
+    // (varying diffusivity: the scale fields decide, checked by sslbm_set_diffusivity_scale)
+    const double tau_max = g->lattice == SSLBM_LATTICE_D2Q9 ? 1.625
+                           : g->lattice == SSLBM_LATTICE_D2Q5_SLBM ? 1.75
+                           : g->lattice == SSLBM_LATTICE_D2Q5_VARD ? HUGE_VAL : 1.25;
     if (tau[c] < 0.5 || tau[c] > tau_max)
       return fail(SSLBM_ERR_UNSTABLE, "tau[%d]=%.17g outside the stable range [1/2, %g]", c, tau[c], tau_max);
   }
@@ -217,7 +228,7 @@ int sslbm_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_
     return fail(SSLBM_ERR_BAD_ARG, "d[D]=%g: the deceased do not diffuse (must be 0)", p->d[4]);
   double dl[4];
   for (int c = 0; c < 4; ++c) dl[c] = (tau[c] - 0.5) / 3.0;
-  if (p->strict) {
+  if (p->strict && g->lattice != SSLBM_LATTICE_D2Q5_VARD) {
     const double out_rate[4] = {p->beta, p->alpha, p->gamma, 0.0};
     // the centre's weight in the update must stay >= 0: 1 - 4 d (D2Q5) or 1 - 20 d / 6 (D2Q9)
     const double cw = g->lattice == SSLBM_LATTICE_D2Q9 ? 20.0 / 6.0 : 4.0;
@@ -272,6 +283,7 @@ int sslbm_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_
   if (g->schemes & SSLBM_WANT_BGK)
     for (int b = 0; b < 2; ++b) h->b_buf[b] = h->ws + L.off_b[b];
   if (g->lattice == SSLBM_LATTICE_D2Q5_SLBM) h->pred = h->ws + L.off_pred;
+  if (g->lattice == SSLBM_LATTICE_D2Q5_VARD) h->kappa = h->ws + L.off_kappa;
   h->depth = sslbm::blocked_supported(g->precision, h->gv) ? 4 : 1;
   DeviceGuard dg(h->device);
   // zero state buffers (and their row padding) so every scheme starts from a defined state
@@ -345,6 +357,55 @@ int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_
   return SSLBM_OK;
 }
 
+int sslbm_set_diffusivity_scale(sslbm_handle* h, const void* kx, const void* ky, int src_dtype,
+                                int src_on_device) {
+  int st = check_scheme(h, SSLBM_SCHEME_SSLBM);
+  if (st) return st;
+  if (h->g.lattice != SSLBM_LATTICE_D2Q5_VARD)
+    return fail(SSLBM_ERR_UNSUPPORTED, "diffusivity scale fields need the lattice SSLBM_LATTICE_D2Q5_VARD");
+  if (!kx) return fail(SSLBM_ERR_BAD_ARG, "kx is NULL");
+  if (!ky) ky = kx;
+  if (src_dtype != SSLBM_DT_F64 && src_dtype != SSLBM_DT_F32)
+    return fail(SSLBM_ERR_BAD_ARG, "src_dtype=%d", src_dtype);
+  DeviceGuard dg(h->device);
+  h->kappa_ok = false;
+  const size_t usize = src_dtype == SSLBM_DT_F64 ? 8 : 4;
+  const size_t plane_user = (size_t)h->g.nx * (size_t)h->g.ny * usize;
+  char* staging = h->s_buf[1 - h->s_cur];  // the step's output buffer, free between steps
+  const void* srcs[2] = {kx, ky};
+  for (int f = 0; f < 2; ++f) {
+    const void* s = srcs[f];
+    if (!src_on_device) {
+      cudaError_t e = cudaMemcpyAsync(staging, s, plane_user, cudaMemcpyHostToDevice, h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(H2D)");
+      s = staging;
+    }
+    cudaError_t e = sslbm::launch_plane_write(h->g.precision, h->gv, s, src_dtype,
+                                              h->kappa + (size_t)f * h->L.plane_bytes, nullptr, 0, 0.0, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "scale field write kernel");
+  }
+  cudaError_t e = sslbm::launch_vard_check(h->g.precision, h->gv, h->kappa, h->kappa + h->L.plane_bytes,
+                                           h->diag_partials(), h->diag_result(), h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "scale field check launch");
+  double r[2];
+  e = cudaMemcpyAsync(r, h->diag_result(), sizeof(r), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(scale field check)");
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(scale field check)");
+  if (r[1] > 0)
+    return fail(SSLBM_ERR_BAD_ARG, "%.0f scale values are negative or not finite", r[1]);
+  const double out_rate[4] = {h->p.beta, h->p.alpha, h->p.gamma, 0.0};
+  for (int c = 0; c < 4; ++c) {
+    const double w = h->cd.dl[c] * r[0] + (h->p.strict ? out_rate[c] * h->g.dt : 0.0);
+    if (w > 1.0 + 1e-12)
+      return fail(SSLBM_ERR_UNSTABLE,
+                  "compartment %d: d_lattice %.17g x max link sum %.17g%s = %.17g > 1 (centre weight < 0)", c,
+                  h->cd.dl[c], r[0], h->p.strict ? " + outflow*dt" : "", w);
+  }
+  h->kappa_ok = true;
+  return SSLBM_OK;
+}
+
 int sslbm_read(sslbm_handle* h, int scheme, int comp, void* dst, int dst_dtype, int dst_on_device) {
   int st = check_scheme(h, scheme);
   if (st) return st;
@@ -398,6 +459,19 @@ int sslbm_step(sslbm_handle* h, int64_t n) {
       cudaError_t e = sslbm::launch_slbm_step(h->g.precision, h->gv, h->coeffs(), tm1, h->s_buf[h->s_cur], h->pred,
                                               h->s_buf[1 - h->s_cur], h->stream);
       if (e != cudaSuccess) return cuda_fail(e, "SLBM step launch");
+      h->s_cur = 1 - h->s_cur;
+      h->s_steps += 1;
+    }
+    return SSLBM_OK;
+  }
+  if (h->g.lattice == SSLBM_LATTICE_D2Q5_VARD) {
+    if (!h->kappa_ok)
+      return fail(SSLBM_ERR_BAD_ARG, "the diffusivity scale fields are not set (sslbm_set_diffusivity_scale)");
+    for (; n > 0; --n) {
+      cudaError_t e = sslbm::launch_sslbm_vard_step(h->g.precision, h->gv, h->coeffs(), h->kappa,
+                                                    h->kappa + h->L.plane_bytes, h->s_buf[h->s_cur],
+                                                    h->s_buf[1 - h->s_cur], h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "varying-diffusivity step launch");
       h->s_cur = 1 - h->s_cur;
       h->s_steps += 1;
     }

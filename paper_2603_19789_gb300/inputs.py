@@ -197,3 +197,27 @@ def epidemic_state(nx: int, ny: int, seed: int) -> np.ndarray:
     st[3] = g.uniform(0.0, 0.2, (ny, nx))
     st[4] = g.uniform(0.0, 0.01, (ny, nx))
     return st
+
+
+def mobility_fields(nx: int, ny: int, seed: int, kind: str = "regions"):
+    """Per-cell diffusivity scale fields (kx, ky), float64 (ny, nx), for the spatially
+    varying, anisotropic diffusion variant.  kind="regions": a mobility map of a few
+    'cities' (discs of radius U[nx/16, nx/6] with scale U[1.2, 2.0]) on a background of
+    U[0.3, 0.7], piecewise constant, with ky = kx times U[0.5, 1.0] (transport faster along
+    x); kind="random": every cell and axis independent, U[0.2, 1.8] (the harshest case for
+    a discretisation: the coefficient jumps at every link)."""
+    rng = _rng(seed)
+    if kind == "random":
+        return rng.uniform(0.2, 1.8, (ny, nx)), rng.uniform(0.2, 1.8, (ny, nx))
+    kx = np.full((ny, nx), rng.uniform(0.3, 0.7))
+    for _ in range(int(rng.integers(3, 7))):
+        cx, cy = rng.uniform(0, nx), rng.uniform(0, ny)
+        r = rng.uniform(max(nx, ny) / 16, max(nx, ny) / 6)
+        y0, y1 = max(0, int(cy - r)), min(ny, int(cy + r) + 1)
+        x0, x1 = max(0, int(cx - r)), min(nx, int(cx + r) + 1)
+        y = np.arange(y0, y1)[:, None]
+        x = np.arange(x0, x1)[None, :]
+        box = kx[y0:y1, x0:x1]
+        box[(x - cx) ** 2 + (y - cy) ** 2 <= r * r] = rng.uniform(1.2, 2.0)
+    ky = kx * rng.uniform(0.5, 1.0)
+    return kx, ky

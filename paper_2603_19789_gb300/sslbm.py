@@ -30,14 +30,14 @@ S, E, I, R, D, NCOMP = 0, 1, 2, 3, 4, 5
 ALL = -1
 DT_F64, DT_F32 = 0, 1
 WANT_SSLBM, WANT_BGK = 1, 2
-LATTICE_D2Q5, LATTICE_D2Q9, LATTICE_D2Q5_SLBM = 0, 1, 2
+LATTICE_D2Q5, LATTICE_D2Q9, LATTICE_D2Q5_SLBM, LATTICE_D2Q5_VARD = 0, 1, 2, 3
 MAX_DEPTH = 8
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP32_KAHAN}
 
 # every symbol include/sslbm.h declares
 EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspace_bytes",
            "sslbm_create", "sslbm_set_stream", "sslbm_destroy", "sslbm_write", "sslbm_read",
-           "sslbm_step", "bgk_step", "sslbm_steps_done", "sslbm_diagnostics", "sslbm_set_blocking",
+           "sslbm_set_diffusivity_scale", "sslbm_step", "bgk_step", "sslbm_steps_done", "sslbm_diagnostics", "sslbm_set_blocking",
            "sslbm_get_blocking", "sslbm_diagnostics_noalloc", "sslbm_autotune",
            "sslbm_ensemble_workspace_bytes", "sslbm_ensemble_create", "sslbm_ensemble_destroy",
            "sslbm_ensemble_set_tiling", "sslbm_ensemble_get_tiling",
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
             "sslbm_destroy": (None, [_vp]),
             "sslbm_write": (i32, [_vp, i32, i32, _vp, i32, i32]),
             "sslbm_read": (i32, [_vp, i32, i32, _vp, i32, i32]),
+            "sslbm_set_diffusivity_scale": (i32, [_vp, _vp, _vp, i32, i32]),
             "sslbm_step": (i32, [_vp, i64]),
             "bgk_step": (i32, [_vp, i64]),
             "sslbm_steps_done": (i64, [_vp, i32]),
@@ -263,6 +264,19 @@ def sslbm_read(h, scheme: int, comp: int, dst):
     return dst
 
 
+def sslbm_set_diffusivity_scale(h, kx, ky=None):
+    """Per-cell diffusivity scale fields (ny, nx) of a LATTICE_D2Q5_VARD solver; ky=None uses
+    kx on both axes.  numpy arrays or torch tensors (host or device) of one dtype."""
+    px, dx, cx, nx_bytes = _buffer(kx)
+    py, cy_code = 0, cx
+    if ky is not None:
+        py, dy, cy_code, ny_bytes = _buffer(ky)
+        if dy != dx or cy_code != cx or ny_bytes != nx_bytes:
+            raise ValueError("kx and ky must share dtype, size and location")
+    _check(load().sslbm_set_diffusivity_scale(h, _vp(px), _vp(py) if ky is not None else None, cx, dx),
+           "sslbm_set_diffusivity_scale")
+
+
 def sslbm_step(h, n: int):
     _check(load().sslbm_step(h, int(n)), "sslbm_step")
 
@@ -357,6 +371,13 @@ class Solver:
         shape = (5, self.ny, self.nx) if comp == ALL else (self.ny, self.nx)
         out = np.empty(shape, dtype=dtype)
         return sslbm_read(self.h, scheme, comp, out)
+
+    def set_diffusivity_scale(self, kx, ky=None):
+        """Spatially varying (and, with ky, anisotropic) diffusion: d^C k(x) per cell."""
+        for f in (kx, ky):
+            if f is not None and tuple(f.shape) != (self.ny, self.nx):
+                raise ValueError(f"scale field of shape {tuple(f.shape)}, expected {(self.ny, self.nx)}")
+        sslbm_set_diffusivity_scale(self.h, kx, ky)
 
     def step(self, n):
         sslbm_step(self.h, n)
