@@ -326,8 +326,20 @@ int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_
   const int c0 = comp == SSLBM_ALL ? 0 : comp, c1 = comp == SSLBM_ALL ? 5 : comp + 1;
   const bool bgk = scheme == SSLBM_SCHEME_BGK;
   char* staging = bgk ? h->b_buf[1 - h->b_cur] : h->s_buf[1 - h->s_cur];
+  const int own_dtype = h->g.precision == SSLBM_FP64 ? SSLBM_DT_F64 : SSLBM_DT_F32;
   for (int c = c0; c < c1; ++c) {
     const char* s = static_cast<const char*>(src) + (size_t)(c - c0) * plane_user;
+    // values stored as given (same type, no deviation or compensation plane): one strided copy
+    // into the pitched plane, without staging or a conversion pass
+    if (!bgk && src_dtype == own_dtype && h->g.precision != SSLBM_FP32_KAHAN &&
+        !(h->g.precision == SSLBM_FP32_DEV && c == SSLBM_S)) {
+      cudaError_t e = cudaMemcpy2DAsync(h->s_plane(h->s_cur, c), (size_t)h->L.pitch * usize, s,
+                                        (size_t)h->g.nx * usize, (size_t)h->g.nx * usize, (size_t)h->g.ny,
+                                        src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                        h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync(write)");
+      continue;
+    }
     if (!src_on_device) {
       cudaError_t e = cudaMemcpyAsync(staging, s, plane_user, cudaMemcpyHostToDevice, h->stream);
       if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(H2D)");
@@ -420,8 +432,19 @@ int sslbm_read(sslbm_handle* h, int scheme, int comp, void* dst, int dst_dtype, 
   const int c0 = comp == SSLBM_ALL ? 0 : comp, c1 = comp == SSLBM_ALL ? 5 : comp + 1;
   const bool bgk = scheme == SSLBM_SCHEME_BGK;
   char* staging = bgk ? h->b_buf[1 - h->b_cur] : h->s_buf[1 - h->s_cur];
+  const int own_dtype = h->g.precision == SSLBM_FP64 ? SSLBM_DT_F64 : SSLBM_DT_F32;
   for (int c = c0; c < c1; ++c) {
     char* d = static_cast<char*>(dst) + (size_t)(c - c0) * plane_user;
+    // values stored as they are returned: one strided copy out of the pitched plane
+    if (!bgk && dst_dtype == own_dtype && h->g.precision != SSLBM_FP32_KAHAN &&
+        !(h->g.precision == SSLBM_FP32_DEV && c == SSLBM_S)) {
+      cudaError_t e = cudaMemcpy2DAsync(d, (size_t)h->g.nx * usize, h->s_plane(h->s_cur, c),
+                                        (size_t)h->L.pitch * usize, (size_t)h->g.nx * usize, (size_t)h->g.ny,
+                                        dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                        h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync(read)");
+      continue;
+    }
     char* target = dst_on_device ? d : staging;
     cudaError_t e;
     if (bgk) {
