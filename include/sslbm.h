@@ -420,7 +420,8 @@ int sslbm_fno_set_loss_weights(sslbm_fno* f, float mass_weight, float neg_weight
 /* One training step on the loss of sslbm_fno_set_loss_weights: forward, loss, backward,
  * Adam with learning rate lr.  y_scratch and dy_scratch are [batch][5][n][n] device
  * buffers.  loss (host, may be NULL) receives mse_w before the update; a non-NULL loss
- * synchronises. */
+ * synchronises, and then returns SSLBM_ERR_TIMEOUT if a tensor-core product of the step
+ * gave up waiting for its MMAs (bounded wait; the product's tile is then NaN). */
 int sslbm_fno_train_step(sslbm_fno* f, int batch, const float* x, const float* target,
                          float* y_scratch, float* dy_scratch, float lr, double* loss);
 /* Residual checks of a prediction y against the input state u (both [batch][5][n][n]):

@@ -1218,6 +1218,9 @@ int sslbm_fno_train_step(sslbm_fno* f, int batch, const float* x, const float* t
   if (loss) {
     CK(cudaMemcpyAsync(loss, dl, 8, cudaMemcpyDeviceToHost, f->stream), "loss");
     CK(cudaStreamSynchronize(f->stream), "sync");
+    unsigned int fault = 0;
+    CK(sslbm::gemm_fault_read_and_clear(&fault, f->stream), "tensor-core product status");
+    if (fault) return err(SSLBM_ERR_TIMEOUT, "a tensor-core product timed out waiting for its MMAs (results are NaN)");
   }
   return SSLBM_OK;
 }

@@ -8,8 +8,8 @@
 // cost nothing.  K may be two-level, k = k1 * K0 + k0, which lets a weight gradient sum
 // over (batch, cell) in one product.  Split-K (gridDim.z = batch * splits) adds partial
 // products into an FP32 C with atomics.  Operands may be FP32 or BF16 in memory; tiles
-// are converted to BF16 in shared memory and multiplied with mma.sync m16n8k16
-// (bf16 x bf16 -> f32).  CTA tile 64 x 64 x 32, four warps of 32 x 32.
+// are converted to BF16 in shared memory and multiplied by the tcgen05 tensor cores
+// (bf16 x bf16 -> f32, accumulator in tensor memory).  CTA tile 128 x 64 x 32.
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -33,5 +33,9 @@ struct GemmArgs {
 };
 
 cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s);
+
+// Whether a product timed out waiting for its tensor-core work since the last call (its
+// tile was then written as NaN); reads the device flag (synchronises s) and clears it.
+cudaError_t gemm_fault_read_and_clear(unsigned int* out, cudaStream_t s);
 
 }  // namespace sslbm
