@@ -417,6 +417,12 @@ int sslbm_fno_set_adam(sslbm_fno* f, float beta1, float beta2, float eps, float 
  * which teach the network to pass the conservation and nonnegativity checks of
  * sslbm_fno_check_project. */
 int sslbm_fno_set_loss_weights(sslbm_fno* f, float mass_weight, float neg_weight);
+/* Bound on each wait of the surrogate's tensor-core products for their MMAs (polls, default
+ * 2^24; 0 restores it), and a fault-injection hook for tests: with stall != 0 the products
+ * withhold their completion signal, so every wait runs out, the products write NaN and
+ * sslbm_fno_train_step returns SSLBM_ERR_TIMEOUT instead of hanging.  The paper has no
+ * counterpart.  After a timeout, parameters updated from NaN gradients are NaN. */
+int sslbm_fno_set_wait_limit(sslbm_fno* f, long long polls, int stall);
 /* One training step on the loss of sslbm_fno_set_loss_weights: forward, loss, backward,
  * Adam with learning rate lr.  y_scratch and dy_scratch are [batch][5][n][n] device
  * buffers.  loss (host, may be NULL) receives mse_w before the update; a non-NULL loss

@@ -696,6 +696,8 @@ struct sslbm_fno {
   char* ws = nullptr;
   cudaStream_t stream = nullptr;
   int device = 0;
+  long long gemm_wait_limit = 0;  // tensor-core waits: polls (0 = default) and the stall hook
+  int gemm_stall = 0;
   int64_t adam_t = 0;
   float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f, wd = 0.f;
   float mass_weight = 0.f, neg_weight = 0.f;
@@ -736,10 +738,12 @@ GemmArgs gemm0() {
   return g;
 }
 
-int run(const GemmArgs& g0, cudaStream_t s, const char* what) {
+int run(const sslbm_fno* f, const GemmArgs& g0, const char* what) {
   GemmArgs g = g0;
   if (g.K0 == 0) g.K0 = g.K;
-  cudaError_t e = sslbm::gemm_bf16(g, s);
+  g.wait_limit = f->gemm_wait_limit;
+  g.stall = f->gemm_stall;
+  cudaError_t e = sslbm::gemm_bf16(g, f->stream);
   if (e != cudaSuccess) return cuda_err(e, what);
   return SSLBM_OK;
 }
@@ -787,7 +791,7 @@ int spectral_fwd(sslbm_fno* f, int l, int B, const bf16* hin, float* out) {
     g.A = hin; g.a_bf16 = 1; g.sAm = n; g.sAk0 = 1;
     g.B = f->Fx(); g.b_bf16 = 1; g.sBk0 = 4 * m; g.sBn = 1;
     g.C = H1; g.sCm = 4 * m; g.sCn = 1;
-    if ((st = run(g, f->stream, "dft x"))) return st;
+    if ((st = run(f, g, "dft x"))) return st;
   }
   {  // T[(b,c)] (2m x 4m) = Fy (2m x n) H1[(b,c)] (n x 4m)
     GemmArgs g = gemm0();
@@ -795,7 +799,7 @@ int spectral_fwd(sslbm_fno* f, int l, int B, const bf16* hin, float* out) {
     g.A = f->Fy(); g.a_bf16 = 1; g.sAb = 0; g.sAm = n; g.sAk0 = 1;
     g.B = H1; g.sBb = (int64_t)n * 4 * m; g.sBk0 = 4 * m; g.sBn = 1;
     g.C = T; g.sCb = 2 * m * 4 * m; g.sCm = 4 * m; g.sCn = 1;
-    if ((st = run(g, f->stream, "dft y"))) return st;
+    if ((st = run(f, g, "dft y"))) return st;
   }
   float* hat = f->hat(l, B);
   combine_kernel<<<blocks_for((int64_t)BW * 2 * m * m), kThreads, 0, f->stream>>>(T, hat, BW, m);
@@ -808,7 +812,7 @@ int spectral_fwd(sslbm_fno* f, int l, int B, const bf16* hin, float* out) {
     g.A = f->Fyi(); g.a_bf16 = 1; g.sAb = 0; g.sAm = 2 * m; g.sAk0 = 1;
     g.B = T; g.sBb = 2 * m * 4 * m; g.sBk0 = 4 * m; g.sBn = 1;
     g.C = H1; g.sCb = (int64_t)n * 4 * m; g.sCm = 4 * m; g.sCn = 1;
-    if ((st = run(g, f->stream, "idft y"))) return st;
+    if ((st = run(f, g, "idft y"))) return st;
   }
   {  // out[(b,o,y), x] = G1[(b,o,y), 4m] Fxi[4m, x] / n^2
     GemmArgs g = gemm0();
@@ -817,7 +821,7 @@ int spectral_fwd(sslbm_fno* f, int l, int B, const bf16* hin, float* out) {
     g.B = f->Fxi(); g.b_bf16 = 1; g.sBk0 = n; g.sBn = 1;
     g.C = out; g.sCm = n; g.sCn = 1;
     g.alpha = 1.f / ((float)n * (float)n);
-    if ((st = run(g, f->stream, "idft x"))) return st;
+    if ((st = run(f, g, "idft x"))) return st;
   }
   return SSLBM_OK;
 }
@@ -839,7 +843,7 @@ int spectral_bwd(sslbm_fno* f, int l, int B, const float* dz, float* dh) {
     g.B = f->Fxi(); g.b_bf16 = 1; g.sBk0 = 1; g.sBn = n;
     g.C = H1; g.sCm = 4 * m; g.sCn = 1;
     g.alpha = 1.f / ((float)n * (float)n);
-    if ((st = run(g, f->stream, "idft x adjoint"))) return st;
+    if ((st = run(f, g, "idft x adjoint"))) return st;
   }
   {  // dU[(b,o)] (2m x 4m) = Fyi^T (2m x n) dG1[(b,o)] (n x 4m)
     GemmArgs g = gemm0();
@@ -847,7 +851,7 @@ int spectral_bwd(sslbm_fno* f, int l, int B, const float* dz, float* dh) {
     g.A = f->Fyi(); g.a_bf16 = 1; g.sAb = 0; g.sAm = 1; g.sAk0 = 2 * m;
     g.B = H1; g.sBb = (int64_t)n * 4 * m; g.sBk0 = 4 * m; g.sBn = 1;
     g.C = T; g.sCb = 2 * m * 4 * m; g.sCm = 4 * m; g.sCn = 1;
-    if ((st = run(g, f->stream, "idft y adjoint"))) return st;
+    if ((st = run(f, g, "idft y adjoint"))) return st;
   }
   expand_adj_kernel<<<blocks_for((int64_t)BW * 2 * m * m), kThreads, 0, f->stream>>>(T, dG, BW, m);
   CK(cudaGetLastError(), "expand adjoint");
@@ -861,7 +865,7 @@ int spectral_bwd(sslbm_fno* f, int l, int B, const float* dz, float* dh) {
     g.A = f->Fy(); g.a_bf16 = 1; g.sAb = 0; g.sAm = 1; g.sAk0 = n;
     g.B = T; g.sBb = 2 * m * 4 * m; g.sBk0 = 4 * m; g.sBn = 1;
     g.C = H1; g.sCb = (int64_t)n * 4 * m; g.sCm = 4 * m; g.sCn = 1;
-    if ((st = run(g, f->stream, "dft y adjoint"))) return st;
+    if ((st = run(f, g, "dft y adjoint"))) return st;
   }
   {  // dh[(b,c,y), x] = dH1[(b,c,y), 4m] Fx^T[4m, x]
     GemmArgs g = gemm0();
@@ -869,7 +873,7 @@ int spectral_bwd(sslbm_fno* f, int l, int B, const float* dz, float* dh) {
     g.A = H1; g.sAm = 4 * m; g.sAk0 = 1;
     g.B = f->Fx(); g.b_bf16 = 1; g.sBk0 = 1; g.sBn = 4 * m;
     g.C = dh; g.sCm = n; g.sCn = 1;
-    if ((st = run(g, f->stream, "dft x adjoint"))) return st;
+    if ((st = run(f, g, "dft x adjoint"))) return st;
   }
   return SSLBM_OK;
 }
@@ -1175,6 +1179,14 @@ int sslbm_fno_backward(sslbm_fno* f, int batch, const float* x, const float* dy)
 int sslbm_fno_set_adam(sslbm_fno* f, float beta1, float beta2, float eps, float weight_decay) {
   if (!f) return err(SSLBM_ERR_BAD_ARG, "surrogate is NULL");
   f->b1 = beta1; f->b2 = beta2; f->eps = eps; f->wd = weight_decay;
+  return SSLBM_OK;
+}
+
+int sslbm_fno_set_wait_limit(sslbm_fno* f, long long polls, int stall) {
+  if (!f) return err(SSLBM_ERR_BAD_ARG, "handle is NULL");
+  if (polls < 0) return err(SSLBM_ERR_BAD_ARG, "polls %lld < 0", polls);
+  f->gemm_wait_limit = polls;
+  f->gemm_stall = stall != 0;
   return SSLBM_OK;
 }
 

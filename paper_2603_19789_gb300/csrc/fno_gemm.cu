@@ -15,7 +15,8 @@
 // reads back its 32 rows (tcgen05.ld 32x32b) for the epilogue, alpha * acc + beta * C or an
 // atomic add.
 //
-// Waits are bounded: if an MMA has not completed after kWaitLimit polls, the kernel raises
+// Waits are bounded: if an MMA has not completed after kWaitLimit polls (or the caller's
+// bound; a test hook can also withhold the completion signal), the kernel raises
 // gemm_fault_flag, writes NaN into its tile (so the result cannot pass for a valid one),
 // frees its tensor memory and returns.  The 29 KB of shared memory per CTA keeps at most 7
 // CTAs on an SM, whose 7 x 64 columns fit in the 512 columns of tensor memory, so the
@@ -100,8 +101,8 @@ __device__ __forceinline__ void store_c(const GemmArgs& g, int64_t off, float ac
   }
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g) {
   const int kend = min(g.K, kbeg + kchunk);
   const bool a_kfast = g.sAk0 == 1, b_kfast = g.sBk0 == 1;
   const uint32_t bar_addr[2] = {smem_u32(bar), smem_u32(bar + 1)};
+  const long long limit = g.wait_limit > 0 ? g.wait_limit : kWaitLimit;
 
   if (tid == 0) {
     s_fault = 0;
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g) {
     unsigned char* sA = smem + st * kStageBytes;
     unsigned char* sB = sA + kABytes;
     if (t >= 2) {  // the stage's previous MMAs (tile t - 2) must have read it
-      if (!mbar_wait(bar_addr[st], (uint32_t)((t - 2) >> 1) & 1u)) s_fault = 1;
+      if (!mbar_wait(bar_addr[st], (uint32_t)((t - 2) >> 1) & 1u, limit)) s_fault = 1;
       __syncthreads();
       if (s_fault) break;
     }
@@ -190,15 +192,16 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g) {
             "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
             : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                       bar_addr[st])
-                   : "memory");
+      if (!g.stall)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         bar_addr[st])
+                     : "memory");
     }
     any = true;
   }
   if (any && !s_fault) {  // the last commit covers every MMA issued before it
     const int last = t - 1;
-    if (!mbar_wait(bar_addr[last & 1], (uint32_t)(last >> 1) & 1u)) s_fault = 1;
+    if (!mbar_wait(bar_addr[last & 1], (uint32_t)(last >> 1) & 1u, limit)) s_fault = 1;
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");

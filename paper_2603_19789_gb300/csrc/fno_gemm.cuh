@@ -30,6 +30,8 @@ struct GemmArgs {
   int64_t sCb, sCm, sCn;
   float alpha, beta;
   int atomic;  // add into FP32 C with atomics (split-K); beta is ignored
+  long long wait_limit;  // polls per tensor-core wait (0: the default bound, 2^24)
+  int stall;             // test hook: skip the completion signal, so the waits run out
 };
 
 cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s);

@@ -47,6 +47,7 @@ EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspa
            "sslbm_fno_destroy", "sslbm_fno_num_params", "sslbm_fno_set_params",
            "sslbm_fno_get_params", "sslbm_fno_get_grads", "sslbm_fno_make_input",
            "sslbm_fno_forward", "sslbm_fno_backward", "sslbm_fno_set_adam", "sslbm_fno_set_loss_weights",
+           "sslbm_fno_set_wait_limit",
            "sslbm_fno_infer", "sslbm_fno_fused",
            "sslbm_fno_train_step", "sslbm_fno_check_project",
            "sslbm_fd4_workspace_bytes", "sslbm_fd4_create", "sslbm_fd4_destroy", "sslbm_fd4_write",
@@ -155,6 +156,7 @@ def load(path: str = LIB_PATH):
             "sslbm_fno_backward": (i32, [_vp, i32, _vp, _vp]),
             "sslbm_fno_set_adam": (i32, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
             "sslbm_fno_set_loss_weights": (i32, [_vp, ctypes.c_float, ctypes.c_float]),
+            "sslbm_fno_set_wait_limit": (i32, [_vp, ctypes.c_longlong, i32]),
             "sslbm_fno_infer": (i32, [_vp, i32, _vp, _vp]),
             "sslbm_fno_fused": (i32, [_vp]),
             "sslbm_fno_train_step": (i32, [_vp, i32, _vp, _vp, _vp, _vp, ctypes.c_float,
@@ -702,6 +704,10 @@ def sslbm_fno_set_adam(f, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
     _check(load().sslbm_fno_set_adam(f, beta1, beta2, eps, weight_decay), "sslbm_fno_set_adam")
 
 
+def sslbm_fno_set_wait_limit(f, polls=0, stall=False):
+    _check(load().sslbm_fno_set_wait_limit(f, int(polls), 1 if stall else 0), "sslbm_fno_set_wait_limit")
+
+
 def sslbm_fno_set_loss_weights(f, mass_weight=0.0, neg_weight=0.0):
     _check(load().sslbm_fno_set_loss_weights(f, float(mass_weight), float(neg_weight)), "sslbm_fno_set_loss_weights")
 
@@ -790,6 +796,9 @@ class Surrogate:
 
     def set_loss_weights(self, mass_weight=0.0, neg_weight=0.0):
         sslbm_fno_set_loss_weights(self.f, mass_weight, neg_weight)
+
+    def set_wait_limit(self, polls=0, stall=False):
+        sslbm_fno_set_wait_limit(self.f, polls, stall)
 
     @property
     def fused(self):

@@ -168,6 +168,26 @@ def test_training_steps_reduce_the_loss():
         assert np.abs(v - fno.unflatten(fno.flatten(p32, **cfg), **cfg)[name]).max() > 0, name
 
 
+def test_lost_tensor_core_completion_times_out_instead_of_hanging():
+    """The tensor-core products wait for their MMAs with a bounded poll.  The test hook
+    withholds the completion signal (nothing then arrives on the barrier), so every wait runs
+    out: the step returns SSLBM_ERR_TIMEOUT, and the context stays usable afterwards."""
+    import torch
+    s, p32, x, xo, u, g, cfg = _setup(4, "generic")
+    theta = s.get_params()
+    target = torch.from_numpy(u).cuda().contiguous()
+    s.set_wait_limit(polls=2000, stall=True)
+    with pytest.raises(L.SslbmError) as e:
+        s.train_step(x, target, 1e-3)
+    assert e.value.status == L.SSLBM_ERR_TIMEOUT
+    s.set_wait_limit()  # defaults again
+    s.set_params(theta)  # the timed-out step updated the parameters from NaN gradients
+    y = s.forward(x)
+    assert torch.isfinite(y).all()
+    loss = s.train_step(x, target, 1e-3)  # the loss is taken before the (NaN-moment) update
+    assert np.isfinite(loss)
+
+
 def test_check_project_residuals_and_projection():
     import torch
     cfg, n = _cfg("generic")
