@@ -23,6 +23,7 @@
 // allocation never has to wait for another CTA.
 #include <cuda_bf16.h>
 #include <math.h>
+#include <stdint.h>
 
 #include "fno_gemm.cuh"
 
@@ -57,6 +58,22 @@ __device__ __forceinline__ uint32_t tile_offset(int row, int k) {
 // packed in k order (the lower k in the lower half of each 32-bit word); zeros outside.
 __device__ __forceinline__ uint4 gather8(const void* p, int bf16, bool in_range, int64_t base, int64_t sk0,
                                          int64_t sk1, int k, int kend, int K, int K0) {
+  // eight consecutive in-range elements at a 16-byte boundary: vector loads, same values
+  if (in_range && sk0 == 1 && K0 == K && k + 8 <= kend) {
+    if (bf16) {
+      const __nv_bfloat16* q = static_cast<const __nv_bfloat16*>(p) + base + k;
+      if ((reinterpret_cast<uintptr_t>(q) & 15) == 0) return *reinterpret_cast<const uint4*>(q);
+    } else {
+      const float* q = static_cast<const float*>(p) + base + k;
+      if ((reinterpret_cast<uintptr_t>(q) & 15) == 0) {
+        const float4 lo = reinterpret_cast<const float4*>(q)[0], hi = reinterpret_cast<const float4*>(q)[1];
+        const __nv_bfloat162 t0 = __floats2bfloat162_rn(lo.x, lo.y), t1 = __floats2bfloat162_rn(lo.z, lo.w);
+        const __nv_bfloat162 t2 = __floats2bfloat162_rn(hi.x, hi.y), t3 = __floats2bfloat162_rn(hi.z, hi.w);
+        return make_uint4(*reinterpret_cast<const uint32_t*>(&t0), *reinterpret_cast<const uint32_t*>(&t1),
+                          *reinterpret_cast<const uint32_t*>(&t2), *reinterpret_cast<const uint32_t*>(&t3));
+      }
+    }
+  }
   float v[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {

@@ -26,12 +26,15 @@ timing     -- the cost comparison of Sec. IV (Table tab:timing): time per step o
               BGK, second- and fourth-order FDM (RK4) in FP64 and FP32 on grids 200..8192,
               normalised by the FP64 SSLBM at 200 x 200.
 
+train-step -- time of one surrogate training step (B = 16, 256 x 256, default network).
+
 Usage:  python -m paper_2603_19789_gb300.studies precision [--n 4096] [--steps 50000]
         [--checkpoints 5] [--out FILE]
         python -m paper_2603_19789_gb300.studies surrogate [--n 256] [--trajectories 2000]
         [--train-steps 3000] [--out FILE]
         python -m paper_2603_19789_gb300.studies accuracy [--out FILE]
         python -m paper_2603_19789_gb300.studies timing [--out FILE]
+        python -m paper_2603_19789_gb300.studies train-step [--n 256] [--out FILE]
 """
 from __future__ import annotations
 
@@ -255,9 +258,36 @@ def surrogate_study(n=256, trajectories=2000, snapshots=10, horizon=2000, train_
     return out, theta
 
 
+def train_step_timing(n=256, batch=16, steps=50):
+    """Time of one training step (forward, loss, backward through the tensor-core products,
+    Adam) of the default network (W = 32, m = 12, L = 4, H = 64) on a synthetic batch, by
+    CUDA events over `steps` steps after five warm-up steps."""
+    import torch
+    from . import sslbm as L
+    from . import surrogate as S
+    L.load()
+    sur = L.Surrogate(n=n, max_batch=batch)
+    sur.set_params(S.initial_params(32, 12, 4, 64, seed=0))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    X = torch.rand((batch, 5, n, n), device="cuda", generator=g) * 0.2
+    Y = (X * 0.99).contiguous()
+    x = sur.make_input(X, torch.full((batch,), 2.0, device="cuda"), torch.full((batch,), -2.0, device="cuda"))
+    for _ in range(5):
+        sur.train_step(x, Y, 1e-4, want_loss=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(sur.stream)
+    for _ in range(steps):
+        sur.train_step(x, Y, 1e-4, want_loss=False)
+    b.record(sur.stream)
+    b.synchronize()
+    loss = sur.train_step(x, Y, 1e-4, want_loss=True)
+    return {"n": n, "batch": batch, "steps": steps, "ms_per_step": a.elapsed_time(b) / steps, "loss": loss}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["precision", "surrogate", "accuracy", "timing"])
+    ap.add_argument("study", choices=["precision", "surrogate", "accuracy", "timing", "train-step"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--steps", type=int, default=50000)
     ap.add_argument("--checkpoints", type=int, default=6)
@@ -268,8 +298,9 @@ def main(argv=None):
     args = ap.parse_args(argv)
     from . import build
     build.build()
-    if args.study in ("accuracy", "timing"):
-        res = accuracy_study() if args.study == "accuracy" else timing_study()
+    if args.study in ("accuracy", "timing", "train-step"):
+        res = (accuracy_study() if args.study == "accuracy" else
+               timing_study() if args.study == "timing" else train_step_timing(n=args.n or 256))
         text = json.dumps(res, indent=1)
         if args.out:
             with open(args.out, "w") as fh:
