@@ -210,6 +210,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def pass_split(n, depth):
+    """The passes sslbm_step makes for n steps at this depth (ceil(n / depth) passes whose
+    depths differ by at most one), as text, e.g. '10 x 7 + 5 x 6'."""
+    ks = []
+    while n > 0:
+        if depth > 1 and n > 1:
+            p = (n + depth - 1) // depth
+            k = (n + p - 1) // p
+        else:
+            k = 1
+        ks.append(k)
+        n -= k
+    return " + ".join(f"{ks.count(k)} x {k}" for k in sorted(set(ks), reverse=True))
+
+
 def timed_steps(solver, n_lat, steps, stream, diag=True):
     """Run `steps` benchmark steps; returns (total ms, kernel ms) from CUDA events."""
     import torch
@@ -317,7 +332,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_timing(L, torch, s, state32, stream, world, wl, jobs=4 * args.e2e_inflight,
+        e2e = e2e_timing(L, torch, s, state32, stream, world, wl, jobs=8 * args.e2e_inflight,
                          inflight=args.e2e_inflight)
 
     cpu = None
@@ -337,6 +352,7 @@ def main():
             "config": {"workload": wl["name"], "nx": NX, "ny": NY, "bc": "no-flux",
                        "precision": "fp32", "lattice_steps_per_step": LATTICE_STEPS_PER_STEP,
                        "temporal_block_depth": depth, "seg_rows": seg or "auto",
+                       "passes_per_step": pass_split(LATTICE_STEPS_PER_STEP, depth),
                        "blocking_chosen_by": "autotuner" if tuned else "--depth",
                        "l2": f"state {20 * cells / 1e9:.2f} GB vs 129 MB L2"
                              + (" (no flush needed)" if 20 * cells > 129e6 else " (fits in L2)"),

@@ -203,8 +203,9 @@ int sslbm_set_diffusivity_scale(sslbm_handle* h, const void* kx, const void* ky,
  * On D2Q5 rho_f = rho_b, so the kernels evaluate the algebraically identical
  * rho_c + d_lattice (sum of the four neighbours - 4 rho_c) + Psi dt.
  * Several steps are fused per pass over memory (temporal blocking, depth set by
- * sslbm_set_blocking or sslbm_autotune); results do not depend on the depth beyond
- * the order of floating-point operations, which is the same for every depth.
+ * sslbm_set_blocking or sslbm_autotune); n steps take ceil(n / depth) passes whose
+ * depths differ by at most one.  Results do not depend on the depth beyond the order of
+ * floating-point operations, which is the same for every depth.
  * Enqueues on the handle's stream and returns. */
 int sslbm_step(sslbm_handle* h, int64_t n);
 

@@ -516,8 +516,11 @@ int sslbm_step(sslbm_handle* h, int64_t n) {
     cudaError_t e;
     if (blocked && h->depth > 1 && n > 1) {
       // depth >= 2: the temporal-blocked kernel; a single step uses the one-step kernel,
-      // which produces the same bits
-      k = (int)(n < h->depth ? n : h->depth);
+      // which produces the same bits.  The n steps take ceil(n / depth) passes whose depths
+      // differ by at most one (100 steps at depth 7: 10 of 7 and 5 of 6), rather than full
+      // passes and a shallow remainder, which runs at a lower rate per step.
+      const int64_t passes = (n + h->depth - 1) / h->depth;
+      k = (int)((n + passes - 1) / passes);
       int seg = h->seg_rows;
       if (seg <= 0) {
         if (!h->seg_cache[k]) h->seg_cache[k] = sslbm::blocked_default_seg_rows(h->g.precision, h->gv, k);
