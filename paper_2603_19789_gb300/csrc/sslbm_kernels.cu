@@ -65,7 +65,7 @@ struct Vec<double, 2> {
 };
 
 template <typename T, int V, int MODE>
-__global__ void __launch_bounds__(256) step1_kernel(const GridView g, const Coeffs<T> k,
+__global__ void __launch_bounds__(256, MODE == MODE_KAHAN ? 2 : 1) step1_kernel(const GridView g, const Coeffs<T> k,
                                                     const T* __restrict__ in, T* __restrict__ out) {
   const int64_t nvec = (g.nx + V - 1) / V;
   const int64_t vx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
