@@ -41,7 +41,7 @@ def _run(nx, ny, bc, precision, steps, state):
 
 
 @pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
-@pytest.mark.parametrize("nx,ny", [(37, 29), (70, 41), (1, 5), (6, 1)])
+@pytest.mark.parametrize("nx,ny", [(37, 29), (70, 41), (1, 5), (6, 1), (263, 17)])
 def test_fp64_matches_oracle(bc, nx, ny):
     st = inputs.epidemic_state(nx, ny, 5 * nx + ny)
     got, tot = _run(nx, ny, bc, L.FP64, 25, st)
@@ -52,9 +52,11 @@ def test_fp64_matches_oracle(bc, nx, ny):
 
 
 @pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
-def test_fp32_matches_oracle(bc):
-    st = inputs.epidemic_state(45, 38, 17)
-    got, _ = _run(45, 38, bc, L.FP32, 25, st)
+@pytest.mark.parametrize("nx,ny", [(45, 38), (301, 19), (513, 10), (128, 9), (2, 3), (5, 1)])
+def test_fp32_matches_oracle(bc, nx, ny):
+    """Rows of several thread groups of 4 cells and ragged last groups, at every kind of edge."""
+    st = inputs.epidemic_state(nx, ny, 17 + nx)
+    got, _ = _run(nx, ny, bc, L.FP32, 25, st)
     tau = [oracle.tau_from_d(d) for d in D[:4]]
     ref = oracle.slbm_run(st.astype(np.float32).astype(np.float64), tau, RATES, 1.0, bc, 25)
     assert relmax(got, ref) <= 1e-5
