@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(32 * K, 16 / K)
                     const int nblocks, float* __restrict__ buf0, float* __restrict__ buf1,
                     EnsControl* ctl, unsigned* done, const long long spin_limit,
                     const long long stall_item) {
-  __shared__ sslbm::PipeSmem<K> sm;
+  extern __shared__ __align__(16) unsigned char ens_smem[];
+  sslbm::PipeSmem<K>& sm = *reinterpret_cast<sslbm::PipeSmem<K>*>(ens_smem);
   __shared__ long long item_sh;
   __shared__ int go_sh;
   const long long total = (long long)nblocks * total_tiles;
@@ -142,6 +143,20 @@ EnsKernel pick_kernel(int depth) {
     case 6: return ensemble_kernel<MODE, 6>;
     case 8: return ensemble_kernel<MODE, 8>;
     default: return nullptr;
+  }
+}
+
+// dynamic shared memory of the pipeline tile at this depth
+size_t pipe_smem_bytes(int depth) {
+  switch (depth) {
+    case 2: return sizeof(sslbm::PipeSmem<2>);
+    case 3: return sizeof(sslbm::PipeSmem<3>);
+    case 4: return sizeof(sslbm::PipeSmem<4>);
+    case 5: return sizeof(sslbm::PipeSmem<5>);
+    case 6: return sizeof(sslbm::PipeSmem<6>);
+    case 7: return sizeof(sslbm::PipeSmem<7>);
+    case 8: return sizeof(sslbm::PipeSmem<8>);
+    default: return 0;
   }
 }
 
@@ -290,7 +305,10 @@ int resident_ctas(EnsKernel kern, int depth, int* out) {
   if (ce == cudaSuccess)
     ce = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                               cudaSharedmemCarveoutMaxShared);
-  if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * depth, 0);
+  if (ce == cudaSuccess)
+    ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe_smem_bytes(depth));
+  if (ce == cudaSuccess)
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * depth, pipe_smem_bytes(depth));
   if (ce != cudaSuccess) return cuda_err(ce, "occupancy query");
   *out = sms * (per > 0 ? per : 1);
   return SSLBM_OK;
@@ -321,7 +339,7 @@ int launch_blocks(sslbm_ensemble* e, int nblocks) {
     if (ce == cudaSuccess) {
       float* b0 = e->buf(e->cur);
       float* b1 = e->buf(1 - e->cur);
-      kern<<<grid, 32 * e->depth, 0, cap>>>(e->dtab(), e->n, e->total_tiles, nblocks, b0, b1, e->ctl(),
+      kern<<<grid, 32 * e->depth, pipe_smem_bytes(e->depth), cap>>>(e->dtab(), e->n, e->total_tiles, nblocks, b0, b1, e->ctl(),
                                             e->done(), e->spin_limit, e->stall_item);
       ce = cudaGetLastError();
     }

@@ -181,7 +181,8 @@ __global__ void __launch_bounds__(32 * K, 16 / K) pipe_kernel(const GridView g, 
                                                              const float* __restrict__ in,
                                                              float* __restrict__ out,
                                                              const int seg_rows, const int nstrips) {
-  __shared__ PipeSmem<K> sm;
+  extern __shared__ __align__(16) unsigned char pipe_smem[];
+  PipeSmem<K>& sm = *reinterpret_cast<PipeSmem<K>*>(pipe_smem);
   const int strip = (int)(blockIdx.x % (unsigned)nstrips);
   const int64_t y0 = (int64_t)(blockIdx.x / (unsigned)nstrips) * seg_rows;
   const int64_t y1 = (y0 + seg_rows < g.ny) ? y0 + seg_rows : g.ny;
@@ -206,6 +207,8 @@ void prefer_shared(bool& done) {
   if (!done) {
     cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(PipeSmem<K>));
     done = true;
   }
 }
@@ -222,7 +225,7 @@ cudaError_t launch_blocked_t(const GridView& g, const void* coeffs, const void* 
   const int64_t nseg = (g.ny + seg_rows - 1) / seg_rows;
   const int64_t blocks = nstrips * nseg;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  pipe_kernel<MODE, K><<<(unsigned)blocks, 32 * K, 0, s>>>(
+  pipe_kernel<MODE, K><<<(unsigned)blocks, 32 * K, sizeof(PipeSmem<K>), s>>>(
       g, *static_cast<const Coeffs<float>*>(coeffs), static_cast<const float*>(in),
       static_cast<float*>(out), seg_rows, (int)nstrips);
   return cudaGetLastError();
@@ -238,7 +241,7 @@ int default_seg_rows_t(const GridView& g) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_kernel<MODE, K>, 32 * K, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_kernel<MODE, K>, 32 * K, sizeof(PipeSmem<K>));
   // one wave: as many CTAs as fit on the device at once, split into row segments
   const int64_t resident = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
   int64_t nseg = resident / nstrips;

@@ -19,7 +19,7 @@
 
 namespace sslbm {
 
-constexpr int kRing0 = 4;  // level-0 rows in flight per tile
+constexpr int kRing0 = 8;  // level-0 rows per tile in the ring: four pairs, three in flight
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -38,29 +38,20 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // r0: level-0 rows (warp 0's lanes read back exactly what they copied);
-// rl[s-1]: level-s rows from warp s-1 to warp s, double-buffered by iteration parity.
+// rl[s-1]: the pair of level-s rows from warp s-1 to warp s, double-buffered by iteration
+// parity.  Over 48 KB from K = 5 on: the kernels take it as dynamic shared memory.
 template <int K>
-struct PipeSmem {
+struct alignas(16) PipeSmem {
   float r0[kRing0][5][128];
-  float rl[K - 1][2][5][128];
+  float rl[K - 1][2][2][5][128];
 };
 
-// One iteration of warp s: read its level's next row N from src, compute level s+1 of row C
-// from P, C, N (x neighbours by shuffles), and pass it to warp s+1 through the slot of parity
-// par, or (last warp) write it to row r of the output.  Ends with the CTA barrier.
-template <int MODE, int K>
-__device__ __forceinline__ void pipe_row(PipeSmem<K>& sm, const GridView& g, const Coeffs<float>& k,
-                                         const float* src, const float2 (&P)[5][2], const float2 (&C)[5][2],
-                                         float2 (&N)[5][2], float* __restrict__ out, const int s, const int lane,
-                                         const int par, const bool writer, const int64_t xs, const int64_t r,
-                                         const int64_t y0, const int64_t y1) {
+// Level s+1 of row C (two float2 column pairs per field) from level-s rows P, C, N: x
+// neighbours by shuffles, the packed lap5 and the packed cell update.
+template <int MODE>
+__device__ __forceinline__ void cell_row(const Coeffs<float>& k, const float2 (&P)[5][2], const float2 (&C)[5][2],
+                                         const float2 (&N)[5][2], float2 (&M)[5][2]) {
   constexpr unsigned kFull = 0xffffffffu;
-#pragma unroll
-  for (int f = 0; f < 5; ++f) {
-    const float4 t = *reinterpret_cast<const float4*>(src + 128 * f);
-    N[f][0] = make_float2(t.x, t.y);
-    N[f][1] = make_float2(t.z, t.w);
-  }
   float2 lp[4][2];
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
@@ -72,13 +63,21 @@ __device__ __forceinline__ void pipe_row(PipeSmem<K>& sm, const GridView& g, con
     lp[f][0] = lap5x2(C[f][0], lr0, P[f][0], N[f][0]);
     lp[f][1] = lap5x2(C[f][1], lr1, P[f][1], N[f][1]);
   }
-  float2 M[5][2];
 #pragma unroll
   for (int h = 0; h < 2; ++h)
     seird_cell2<MODE == MODE_DEV>(k, C[0][h], C[1][h], C[2][h], C[3][h], C[4][h], lp[0][h], lp[1][h], lp[2][h],
                                   lp[3][h], M[0][h], M[1][h], M[2][h], M[3][h], M[4][h]);
+}
+
+// Hand level-(s+1) row M to the next warp (slot row `which` of parity par) or, for the last
+// warp, write it to row r of the output.
+template <int K>
+__device__ __forceinline__ void emit_row(PipeSmem<K>& sm, const GridView& g, const float2 (&M)[5][2],
+                                         float* __restrict__ out, const int s, const int lane, const int par,
+                                         const int which, const bool writer, const int64_t xs, const int64_t r,
+                                         const int64_t y0, const int64_t y1) {
   if (s < K - 1) {
-    float* dst = &sm.rl[s < K - 1 ? s : 0][par][0][4 * lane];
+    float* dst = &sm.rl[s < K - 1 ? s : 0][par][which][0][4 * lane];
 #pragma unroll
     for (int f = 0; f < 5; ++f)
       *reinterpret_cast<float4*>(dst + 128 * f) = make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
@@ -98,6 +97,31 @@ __device__ __forceinline__ void pipe_row(PipeSmem<K>& sm, const GridView& g, con
       }
     }
   }
+}
+
+// One iteration of warp s: read the pair of level-s rows b, b+1 (N0, N1) from src (row b+1
+// 640 floats further), compute level-(s+1) rows b-1 (from A = b-2, B = b-1, N0) and b (from
+// B, N0, N1), hand them on or write them as rows r, r+1.  Ends with the CTA barrier.
+template <int MODE, int K>
+__device__ __forceinline__ void pipe_pair(PipeSmem<K>& sm, const GridView& g, const Coeffs<float>& k,
+                                          const float* src, const float2 (&A)[5][2], const float2 (&B)[5][2],
+                                          float2 (&N0)[5][2], float2 (&N1)[5][2], float* __restrict__ out,
+                                          const int s, const int lane, const int par, const bool writer,
+                                          const int64_t xs, const int64_t r, const int64_t y0, const int64_t y1) {
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    const float4 t0 = *reinterpret_cast<const float4*>(src + 128 * f);
+    const float4 t1 = *reinterpret_cast<const float4*>(src + 640 + 128 * f);
+    N0[f][0] = make_float2(t0.x, t0.y);
+    N0[f][1] = make_float2(t0.z, t0.w);
+    N1[f][0] = make_float2(t1.x, t1.y);
+    N1[f][1] = make_float2(t1.z, t1.w);
+  }
+  float2 M[5][2];
+  cell_row<MODE>(k, A, B, N0, M);
+  emit_row<K>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
+  cell_row<MODE>(k, B, N0, N1, M);
+  emit_row<K>(sm, g, M, out, s, lane, par, 1, writer, xs, r + 1, y0, y1);
   __syncthreads();
 }
 
@@ -123,17 +147,20 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K>& sm, const GridView& g, co
   int xm[4];  // ghost images of this lane's columns, for lanes on a domain edge
 #pragma unroll
   for (int j = 0; j < 4; ++j) xm[j] = (int)ghost_index(xs + j, g.nx, g.bc);
-  // Warp s computes, at iteration q, level s+1 of row q - 2s - 1 from level-s rows
-  // q-2s-2 (P), q-2s-1 (C) and q-2s (N).  Level-0 rows span [y0-K, y1+K); the last warp
-  // finishes row y1-1 at iteration y1 + 2K - 2.
-  const int64_t qa = y0 - K, qb = y1 + 2 * K - 1, load_end = y1 + K;
+  // Rows go through the pipeline in pairs.  At iteration t warp s reads the level-s rows
+  // b, b+1 with b = qa + 2t - 3s (warp 0 from the ring, the others from the previous warp's
+  // output of iteration t-1) and computes level-(s+1) rows b-1 and b.  Level-0 rows span
+  // [y0-K, y1+K); the last warp finishes row y1-1 once b >= y1-1 for s = K-1.
+  const int64_t qa = y0 - K, load_end = y1 + K;
+  const int nt = (int)(((y1 - y0) + 4 * K - 4 + 1) / 2) + 1;
+  const int64_t rbase = qa - 3 * (K - 1) - 1;  // the first row the last warp emits (iteration 0)
 
   for (int i = threadIdx.x; i < kRing0 * 5 * 128; i += 32 * K) (&sm.r0[0][0][0])[i] = 0.f;
-  for (int i = threadIdx.x; i < (K - 1) * 2 * 5 * 128; i += 32 * K) (&sm.rl[0][0][0][0])[i] = 0.f;
+  for (int i = threadIdx.x; i < (K - 1) * 2 * 2 * 5 * 128; i += 32 * K) (&sm.rl[0][0][0][0][0])[i] = 0.f;
   __syncthreads();
 
   auto issue = [&](int64_t q) {  // warp 0: copy level-0 row q into its ring slot
-    if (!loads) return;
+    if (!loads || q >= load_end) return;
     const int slot = (int)((q - qa) % kRing0);
     const int64_t row = ghost_index(q, g.ny, g.bc) * g.pitch;
 #pragma unroll
@@ -150,47 +177,42 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K>& sm, const GridView& g, co
       }
     }
   };
+  constexpr int kPairsAhead = kRing0 / 2 - 1;
   if (s == 0) {
 #pragma unroll
-    for (int p = 0; p < kRing0 - 1; ++p) {
-      if (qa + p < load_end) issue(qa + p);
+    for (int p = 0; p < kPairsAhead; ++p) {
+      issue(qa + 2 * p);
+      issue(qa + 2 * p + 1);
       cp_async_commit();
     }
   }
 
-  // Three row buffers rotate through the roles P (row q-2s-2), C (q-2s-1) and N (q-2s) of
-  // this warp's level, unrolled three ways so that no row is copied between registers.
-  float2 RA[5][2], RB[5][2], RC[5][2];
+  // Four row buffers: A, B hold rows b-2, b-1; the pair b, b+1 arrives in the other two, and
+  // the roles swap every iteration (unrolled two ways, so no row is copied between registers).
+  float2 RA[5][2], RB[5][2], RC[5][2], RD[5][2];
 #pragma unroll
   for (int f = 0; f < 5; ++f)
 #pragma unroll
     for (int h = 0; h < 2; ++h) RA[f][h] = RB[f][h] = make_float2(0.f, 0.f);
-
-  const int nq = (int)(qb - qa), nload = (int)(load_end - qa), par0 = (int)((qa - 1) & 1);
-  const int64_t r0 = qa - 2 * K + 1;  // the level-K row the last warp finishes at iteration 0
-  // Row source of iteration j (q = qa + j): warp 0's ring slot, or the previous warp's slot.
-  auto fetch = [&](int j) -> const float* {
+  // source of the pair of iteration t: warp 0's ring slots, or the previous warp's slot
+  auto fetch = [&](int t) -> const float* {
     if (s == 0) {
-      if (j + kRing0 - 1 < nload) issue(qa + j + kRing0 - 1);
+      issue(qa + 2 * (t + kPairsAhead));
+      issue(qa + 2 * (t + kPairsAhead) + 1);
       cp_async_commit();
-      cp_async_wait<kRing0 - 1>();
-      return &sm.r0[j & (kRing0 - 1)][0][4 * lane];
+      cp_async_wait<kPairsAhead>();
+      return &sm.r0[(2 * t) & (kRing0 - 1)][0][4 * lane];
     }
-    return &sm.rl[s - 1][(j + par0) & 1][0][4 * lane];
+    return &sm.rl[s - 1][(t + 1) & 1][0][0][4 * lane];
   };
-  int j = 0;
-  for (; j + 3 <= nq; j += 3) {
-    pipe_row<MODE, K>(sm, g, k, fetch(j), RA, RB, RC, out, s, lane, (j + par0 + 1) & 1, writer, xs, r0 + j, y0, y1);
-    pipe_row<MODE, K>(sm, g, k, fetch(j + 1), RB, RC, RA, out, s, lane, (j + par0) & 1, writer, xs, r0 + j + 1, y0,
-                      y1);
-    pipe_row<MODE, K>(sm, g, k, fetch(j + 2), RC, RA, RB, out, s, lane, (j + par0 + 1) & 1, writer, xs, r0 + j + 2,
-                      y0, y1);
+  int t = 0;
+  for (; t + 2 <= nt; t += 2) {
+    pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0, y1);
+    pipe_pair<MODE, K>(sm, g, k, fetch(t + 1), RC, RD, RA, RB, out, s, lane, (t + 1) & 1, writer, xs,
+                       rbase + 2 * t + 2, y0, y1);
   }
-  if (j < nq)
-    pipe_row<MODE, K>(sm, g, k, fetch(j), RA, RB, RC, out, s, lane, (j + par0 + 1) & 1, writer, xs, r0 + j, y0, y1);
-  if (j + 1 < nq)
-    pipe_row<MODE, K>(sm, g, k, fetch(j + 1), RB, RC, RA, out, s, lane, (j + par0) & 1, writer, xs, r0 + j + 1, y0,
-                      y1);
+  if (t < nt)
+    pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0, y1);
   if (s == 0) cp_async_wait<0>();
 }
 
