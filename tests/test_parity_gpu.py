@@ -145,36 +145,50 @@ def test_centre_bump_fp32_variants_within_tolerance(precision):
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("nx,ny", [(5, 3), (130, 1), (1, 70), (37, 23), (1000, 333), (250, 260)])
 def test_blocked_depths_give_identical_bits(precision, bc, nx, ny):
+    """2k steps at depth k are two passes of exactly that depth (sslbm_step splits n steps
+    into passes of near-equal depth), so every depth's kernel is compared with the one-step
+    kernel bit for bit; then 11 steps, which mix depths."""
     wl = small_workload(nx, ny, bc, seed=nx + 3 * ny)
     ref = solver_for(wl, precision)
     ref.write(wl["state"])
     ref.set_blocking(1)
-    ref.step(11)
-    base = ref.read(dtype=np.float32)
-    for k in (2, 3, 4, 5, 8):
+    refs = {}
+    for n in range(1, 17):
+        ref.step(1)
+        refs[n] = ref.read(dtype=np.float32)
+    for k in range(2, 9):
+        s = solver_for(wl, precision)
+        s.write(wl["state"])
+        s.set_blocking(k)
+        s.step(2 * k)
+        got = s.read(dtype=np.float32)
+        assert np.array_equal(got.view(np.uint32), refs[2 * k].view(np.uint32)), (k, nx, ny, bc)
+    for k in (3, 8):
         s = solver_for(wl, precision)
         s.write(wl["state"])
         s.set_blocking(k)
         s.step(11)
-        got = s.read(dtype=np.float32)
-        assert np.array_equal(got.view(np.uint32), base.view(np.uint32)), (k, nx, ny, bc)
+        assert np.array_equal(s.read(dtype=np.float32).view(np.uint32), refs[11].view(np.uint32)), (k, 11)
+    base = refs[11]
     # and a short run agrees with the FP64 oracle to FP32 accuracy
     want = oracle.sslbm_run(wl["state"], taus(wl["d"]), wl["rates"].as_tuple(), 1.0, bc, 11)
     assert (rel_max(base.astype(np.float64), want) <= FP32_SHORT_TOL).all()
 
 
-@pytest.mark.parametrize("depth,seg_rows", [(3, 12), (3, 16), (3, 50), (3, 333), (8, 32), (8, 41), (6, 100)])
+@pytest.mark.parametrize("depth,seg_rows", [(3, 12), (3, 16), (3, 50), (3, 333), (8, 32), (8, 41), (6, 100),
+                                             (7, 28), (5, 21), (2, 8)])
 def test_blocked_segment_lengths_give_identical_bits(depth, seg_rows):
+    """2 x depth steps: two passes of exactly this depth with this row-segment length."""
     wl = small_workload(300, 333, 1, seed=5)
     ref = solver_for(wl, L.FP32)
     ref.write(wl["state"])
     ref.set_blocking(1)
-    ref.step(9)
+    ref.step(2 * depth)
     base = ref.read(dtype=np.float32)
     s = solver_for(wl, L.FP32)
     s.write(wl["state"])
     s.set_blocking(depth, seg_rows)
-    s.step(9)
+    s.step(2 * depth)
     assert np.array_equal(s.read(dtype=np.float32).view(np.uint32), base.view(np.uint32))
 
 
