@@ -365,7 +365,15 @@ def main():
                          "kernel": f"pipe_kernel<fp32, K={depth}>" if depth > 1 else "step1_kernel<fp32>",
                          "bytes_per_launch": BYTES_PER_CELL_FP32 * cells,
                          "launch_ms": launch_ms,
-                         "cell_updates_per_launch": cells * depth},
+                         "cell_updates_per_launch": cells * depth,
+                         # what one-step kernels would have to move for the same cell-steps: above
+                         # the HBM peak because the K steps of a launch share one pass over HBM
+                         "per_step_equivalent": {
+                             "achieved": BYTES_PER_CELL_FP32 * value * 1e9 / world / 1e9,
+                             "frac": BYTES_PER_CELL_FP32 * value / world / hbm,
+                             "unit": "GB/s",
+                             "note": "40 B per cell-step x cell-steps per second (whole step, diagnostics "
+                                     "included) / measured HBM peak"}},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "e2e": e2e,
