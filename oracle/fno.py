@@ -33,7 +33,10 @@ ky in {0..m-1} (2m x m modes), complex weights R[i, o, kx, ky]:
 It is evaluated here as real DFT products, the factorisation the GPU uses:
     H1 = h Fx (along x), T = Fy H1 (along y), hat_h = combine(T), hat_g = mix(hat_h, R),
     U = expand(hat_g), G1 = Fyi U, K(h) = G1 Fxi / n^2.
-gelu(z) = z * Phi(z) with Phi the standard normal CDF (erf form).
+gelu(z) = 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))): GELU in its tanh form, one of the
+two standard definitions of GELU (the other is z Phi(z) with the normal CDF; they differ by
+at most 4.7e-4).  The surrogate's specification names GELU without its form; this is the
+form the GPU evaluates with its tanh instruction.
 Parameters are stored flat in the order of param_shapes() (the GPU uses the same layout).
 """
 from __future__ import annotations
@@ -41,11 +44,6 @@ from __future__ import annotations
 import math
 
 import numpy as np
-
-try:
-    from scipy.special import erf as _erf
-except Exception:  # pragma: no cover - scipy is present on every machine this runs on
-    _erf = np.vectorize(math.erf)
 
 C_IN, C_OUT = 8, 5
 SCALE_FLOOR = 1e-12
@@ -118,12 +116,17 @@ def dft_mats(n, m):
     return Fx, Fy, Fyi, Fxi
 
 
+GELU_C = math.sqrt(2.0 / math.pi)
+
+
 def gelu(z):
-    return 0.5 * z * (1.0 + _erf(z / math.sqrt(2.0)))
+    return 0.5 * z * (1.0 + np.tanh(GELU_C * (z + 0.044715 * z ** 3)))
 
 
 def gelu_grad(z):
-    return 0.5 * (1.0 + _erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+    t = np.tanh(GELU_C * (z + 0.044715 * z ** 3))
+    du = GELU_C * (1.0 + 3.0 * 0.044715 * z * z)
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * du
 
 
 def combine(T):

@@ -61,9 +61,22 @@ int cuda_err(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_err(e_, what); \
   } while (0)
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+// GELU in its tanh form, g(z) = 0.5 z (1 + tanh(u)), u = sqrt(2/pi) (z + 0.044715 z^3), with the
+// hardware tanh (tanh.approx.f32); g'(z) = 0.5 (1 + t) + 0.5 z (1 - t^2) du/dz
+__device__ __forceinline__ float tanh_hw(float x) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(x));
+  return t;
+}
+__device__ __forceinline__ float gelu_f(float z) {
+  const float t = tanh_hw(0.7978845608028654f * fmaf(0.044715f * z, z * z, z));
+  const float h = 0.5f * z;
+  return fmaf(h, t, h);
+}
 __device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+  const float t = tanh_hw(0.7978845608028654f * fmaf(0.044715f * z, z * z, z));
+  const float du = 0.7978845608028654f * fmaf(3.f * 0.044715f * z, z, 1.f);
+  return fmaf(0.5f * z * du, fmaf(-t, t, 1.f), 0.5f * (1.f + t));
 }
 
 constexpr int kThreads = 256;

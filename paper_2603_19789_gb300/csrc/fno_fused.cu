@@ -73,8 +73,14 @@ __device__ __forceinline__ void load_b_nk1(uint32_t (&b)[2], const bf16* base, i
   ldsm_x2(b, base + (n0 + (lane & 7)) * ld + k0 + ((lane >> 3) & 1) * 8);
 }
 
-// the same GELU as the unfused path
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+// the same GELU as the unfused path: the tanh form, 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))),
+// with the hardware tanh (tanh.approx.f32)
+__device__ __forceinline__ float gelu(float z) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.7978845608028654f * fmaf(0.044715f * z, z * z, z)));
+  const float h = 0.5f * z;
+  return fmaf(h, t, h);
+}
 
 __device__ __forceinline__ void st_bf2(bf16* p, float a, float b) {
   *reinterpret_cast<bf162*>(p) = __floats2bfloat162_rn(a, b);

@@ -154,3 +154,18 @@ def test_prediction_conserves_the_population_exactly():
 def _last_hidden(params, x, W, m, L, H):
     _, cache = fno.forward(params, x, W, m, L, H)
     return cache[f"h{L}"]
+
+
+def test_gelu_tanh_form_against_the_erf_definition_and_its_derivative():
+    """The tanh form stays within 4.8e-4 of z Phi(z): the two standard GELUs differ by at
+    most 4.7e-4, near |z| = 2.7 (a wrong cubic coefficient or scale moves both the size and
+    the place of that gap).  gelu_grad is the derivative (central differences)."""
+    import math
+    z = np.linspace(-8.0, 8.0, 20001)
+    erf_form = 0.5 * z * (1.0 + np.array([math.erf(v / math.sqrt(2.0)) for v in z]))
+    gap = np.abs(fno.gelu(z) - erf_form)
+    assert 4.0e-4 < gap.max() < 4.8e-4
+    assert 2.4 < abs(z[gap.argmax()]) < 3.0
+    h = 1e-5
+    fd = (fno.gelu(z + h) - fno.gelu(z - h)) / (2 * h)
+    np.testing.assert_allclose(fno.gelu_grad(z), fd, rtol=0, atol=1e-8)
