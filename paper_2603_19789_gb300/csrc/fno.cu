@@ -245,6 +245,47 @@ __global__ void state_sums_kernel(const float* __restrict__ a, const float* __re
   block_add2(sa, su, sums + 2 * b, sh);
 }
 
+// The forward pass's sums in one sweep (b = blockIdx.y): sums[2b] += sum of the prediction v
+// over its five planes, sums[2b+1] += sum of u (u_c = sigma_c x_c, the input state).  All ten
+// planes are read in one loop body, four values per plane at a time, so that many loads are
+// in flight per thread.
+__global__ void pred_sums_kernel(const float* __restrict__ v, const float* __restrict__ x, double* __restrict__ sums,
+                                 int64_t P) {
+  __shared__ double sh[64];
+  const int64_t b = blockIdx.y;
+  const float sg = scale_from_e(x[(b * kCin + 7) * P]);
+  const float* vb = v + b * 5 * P;
+  const float* xb = x + b * kCin * P;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float sv = 0.f, su_plain = 0.f, su_scaled = 0.f;  // u of E and I carries the scale sigma
+  if ((P & 3) == 0 && (reinterpret_cast<uintptr_t>(vb) & 15) == 0 && (reinterpret_cast<uintptr_t>(xb) & 15) == 0) {
+    for (int64_t i = i0; i < P / 4; i += stride) {
+      float4 a[5], u[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        a[c] = reinterpret_cast<const float4*>(vb + c * P)[i];
+        u[c] = reinterpret_cast<const float4*>(xb + c * P)[i];
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        sv += (a[c].x + a[c].y) + (a[c].z + a[c].w);
+        const float q = (u[c].x + u[c].y) + (u[c].z + u[c].w);
+        if (c == 1 || c == 2) su_scaled += q;
+        else su_plain += q;
+      }
+    }
+  } else {
+    for (int64_t i = i0; i < P; i += stride)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        sv += vb[c * P + i];
+        if (c == 1 || c == 2) su_scaled += xb[c * P + i];
+        else su_plain += xb[c * P + i];
+      }
+  }
+  block_add2((double)sv, (double)su_plain + (double)sg * (double)su_scaled, sums + 2 * b, sh);
+}
+
 // y = v - u kappa, kappa = (sum v - sum u) / sum u: the prediction conserves the population
 // (b = blockIdx.y)
 __global__ void conserve_kernel(float* __restrict__ y, const float* __restrict__ x, const double* __restrict__ sums,
@@ -257,12 +298,25 @@ __global__ void conserve_kernel(float* __restrict__ y, const float* __restrict__
   }
   __syncthreads();
   const float kappa = kap, sg = scale_from_e(x[(b * kCin + 7) * P]);
-  for (int c = 0; c < 5; ++c) {
-    const float k = (c == 1 || c == 2) ? sg * kappa : kappa;
-    float* yb = y + (b * 5 + c) * P;
-    const float* xb = x + (b * kCin + c) * P;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
-      yb[i] = fmaf(-xb[i], k, yb[i]);
+  float* yb = y + b * 5 * P;
+  const float* xb = x + b * kCin * P;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((P & 3) == 0 && (reinterpret_cast<uintptr_t>(yb) & 15) == 0 && (reinterpret_cast<uintptr_t>(xb) & 15) == 0) {
+    for (int64_t i = i0; i < P / 4; i += stride) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const float k = (c == 1 || c == 2) ? sg * kappa : kappa;
+        float4 v = reinterpret_cast<float4*>(yb + c * P)[i];
+        const float4 u = reinterpret_cast<const float4*>(xb + c * P)[i];
+        v.x = fmaf(-u.x, k, v.x), v.y = fmaf(-u.y, k, v.y), v.z = fmaf(-u.z, k, v.z), v.w = fmaf(-u.w, k, v.w);
+        reinterpret_cast<float4*>(yb + c * P)[i] = v;
+      }
+    }
+  } else {
+    for (int c = 0; c < 5; ++c) {
+      const float k = (c == 1 || c == 2) ? sg * kappa : kappa;
+      for (int64_t i = i0; i < P; i += stride) yb[c * P + i] = fmaf(-xb[c * P + i], k, yb[c * P + i]);
+    }
   }
 }
 
@@ -983,8 +1037,7 @@ int conserve(sslbm_fno* f, int B, const float* x, float* y) {
   double* sums = f->at<double>(f->bu.csum);
   CK(cudaMemsetAsync(sums, 0, (size_t)B * 2 * 8, f->stream), "zero population sums");
   const int64_t P = f->L.P;
-  dim3 grid((unsigned)std::min<int64_t>(64, (5 * P + kThreads - 1) / kThreads), B);
-  state_sums_kernel<<<grid, kThreads, 0, f->stream>>>(y, x, sums, P, 0);
+  pred_sums_kernel<<<dim3(rows_grid(P), B), kThreads, 0, f->stream>>>(y, x, sums, P);
   CK(cudaGetLastError(), "population sums");
   conserve_kernel<<<dim3(rows_grid(P), B), kThreads, 0, f->stream>>>(y, x, sums, P);
   CK(cudaGetLastError(), "conservation");
