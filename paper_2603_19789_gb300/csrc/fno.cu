@@ -551,13 +551,25 @@ __global__ void dft_init_kernel(bf16* Fx, bf16* Fy, bf16* Fyi, bf16* Fxi, int n,
   }
 }
 
+// whether n floats at p can be read as float4 (P a multiple of 4 keeps every plane aligned)
+__device__ __forceinline__ bool vec4_ok(const void* p, int64_t n) {
+  return (n & 3) == 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
 // smax[b] = max over the grid of (E, I, 0) as float bits (non-negative floats order as ints)
 __global__ void infection_scale_kernel(const float* __restrict__ u, int* __restrict__ smax, int64_t P) {
   const int64_t b = blockIdx.y;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const float* ub = u + (b * 5 + 1) * P;
   float mx = 0.f;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * P;
-       t += (int64_t)gridDim.x * blockDim.x)
-    mx = fmaxf(mx, u[(b * 5 + 1) * P + t]);
+  if (vec4_ok(ub, 2 * P)) {
+    for (int64_t t = i0; t < 2 * P / 4; t += stride) {
+      const float4 v = reinterpret_cast<const float4*>(ub)[t];
+      mx = fmaxf(mx, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+    }
+  } else {
+    for (int64_t t = i0; t < 2 * P; t += stride) mx = fmaxf(mx, ub[t]);
+  }
   for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, off));
   if ((threadIdx.x & 31) == 0) atomicMax(smax + b, __float_as_int(mx));
 }
@@ -570,12 +582,26 @@ __global__ void make_input_kernel(const float* __restrict__ u, const float* __re
   const float e = (log10f(fmaxf(__int_as_float(smax[b]), kScaleFloor)) + 4.f) * 0.25f;
   const float sp = scale_from_e(e);
   const float c5 = (r0[b] - 2.6f) / 1.4f, c6 = logd[b] + 2.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool v4 = vec4_ok(x + b * kCin * P, P) && vec4_ok(u + b * 5 * P, P);
   for (int c = 0; c < kCin; ++c) {
     float* xb = x + (b * kCin + c) * P;
     const float* ub = u + (b * 5 + (c < 5 ? c : 0)) * P;
     const float cv = c == 5 ? c5 : (c == 6 ? c6 : e);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
-      xb[i] = c < 5 ? ((c == 1 || c == 2) ? ub[i] / sp : ub[i]) : cv;
+    if (v4) {
+      for (int64_t i = i0; i < P / 4; i += stride) {
+        float4 o;
+        if (c >= 5) {
+          o = make_float4(cv, cv, cv, cv);
+        } else {
+          o = reinterpret_cast<const float4*>(ub)[i];
+          if (c == 1 || c == 2) o.x = o.x / sp, o.y = o.y / sp, o.z = o.z / sp, o.w = o.w / sp;
+        }
+        reinterpret_cast<float4*>(xb)[i] = o;
+      }
+    } else {
+      for (int64_t i = i0; i < P; i += stride) xb[i] = c < 5 ? ((c == 1 || c == 2) ? ub[i] / sp : ub[i]) : cv;
+    }
   }
 }
 
@@ -586,6 +612,8 @@ __global__ void residual_kernel(const float* __restrict__ y, const float* __rest
   __shared__ double sh[64];
   const int64_t b = blockIdx.y;
   float sy = 0.f, su = 0.f, sn = 0.f;
+  // one value per thread and iteration: the residual |sum y - sum u| is a difference of
+  // nearly equal totals, so the partial sums stay short
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P5; t += (int64_t)gridDim.x * blockDim.x) {
     const float yv = y[b * P5 + t];
     sy += yv;
@@ -655,15 +683,33 @@ __global__ void mask_clamp_kernel(float* __restrict__ y, const unsigned char* __
   __shared__ double sh[64];
   const int64_t b = blockIdx.y;
   float acc = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool v4 = vec4_ok(y + b * 5 * P, P) && (!mask || (reinterpret_cast<uintptr_t>(mask + b * P) & 3) == 0);
   for (int c = 0; c < 5; ++c) {
     float* yb = y + (b * 5 + c) * P;
     const unsigned char* mb = mask && c > 0 ? mask + b * P : nullptr;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-      float v = yb[p];
-      if (mb && !mb[p]) v = 0.f;
-      v = v > 0.f ? v : 0.f;
-      yb[p] = v;
-      acc += v;
+    if (v4) {
+      for (int64_t p = i0; p < P / 4; p += stride) {
+        float4 v = reinterpret_cast<float4*>(yb)[p];
+        if (mb) {
+          const uchar4 m = reinterpret_cast<const uchar4*>(mb)[p];
+          if (!m.x) v.x = 0.f;
+          if (!m.y) v.y = 0.f;
+          if (!m.z) v.z = 0.f;
+          if (!m.w) v.w = 0.f;
+        }
+        v.x = v.x > 0.f ? v.x : 0.f, v.y = v.y > 0.f ? v.y : 0.f, v.z = v.z > 0.f ? v.z : 0.f, v.w = v.w > 0.f ? v.w : 0.f;
+        reinterpret_cast<float4*>(yb)[p] = v;
+        acc += (v.x + v.y) + (v.z + v.w);
+      }
+    } else {
+      for (int64_t p = i0; p < P; p += stride) {
+        float v = yb[p];
+        if (mb && !mb[p]) v = 0.f;
+        v = v > 0.f ? v : 0.f;
+        yb[p] = v;
+        acc += v;
+      }
     }
   }
   block_add1(acc, sums + b, sh);
@@ -677,8 +723,17 @@ __global__ void rescale_kernel(float* __restrict__ y, const double* __restrict__
   if (threadIdx.x == 0) scl = sums[b] > 0.0 ? (float)(res[3 * b + 1] / sums[b]) : 1.f;
   __syncthreads();
   const float scale = scl;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P5; t += (int64_t)gridDim.x * blockDim.x)
-    y[b * P5 + t] *= scale;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float* yb = y + b * P5;
+  if (vec4_ok(yb, P5)) {
+    for (int64_t t = i0; t < P5 / 4; t += stride) {
+      float4 v = reinterpret_cast<float4*>(yb)[t];
+      v.x *= scale, v.y *= scale, v.z *= scale, v.w *= scale;
+      reinterpret_cast<float4*>(yb)[t] = v;
+    }
+  } else {
+    for (int64_t t = i0; t < P5; t += stride) yb[t] *= scale;
+  }
 }
 
 // ---- parameter layout ------------------------------------------------------------------
