@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances, stated here and derived in the design doc:
+Tolerances, stated here and derived from the arithmetic of each variant:
   FP64   relative max-norm per compartment <= 1e-12 (the kernels use the reduced form of
          Eq. sslbm_final_clean, which differs from the oracle's literal form only in the
          rounding of each step, ~1e-16 relative).
