@@ -1,6 +1,8 @@
 // fno_fused.cu -- fused forward kernels of the learned surrogate (see fno_fused.cuh).
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "fno_fused.cuh"
 
 namespace sslbm {
@@ -789,34 +791,38 @@ __global__ void __launch_bounds__(256) cell_wgrad_kernel(int B, int rows, int co
 
 constexpr int kMaxDev = 64;
 
+// Per-device caches are atomics: concurrent callers on several host threads may fill the same
+// entry, with equal values.
 int sm_count() {
-  static int cache[kMaxDev] = {};
+  static std::atomic<int> cache[kMaxDev];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 0;
-  if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
-  return cache[dev];
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (!v && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+    cache[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 template <int W, int KF, int H, int NT, int MODE>
 cudaError_t launch_row_t(const RowArgs& a, cudaStream_t s) {
   using S = RowSmem<W, KF, H, NT, MODE>;
-  static int per_sm[kMaxDev] = {};
+  static std::atomic<int> per_sm[kMaxDev];  // set after the kernel's shared-memory attribute
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
   auto kern = row_kernel<W, KF, H, NT, MODE>;
-  if (!per_sm[dev]) {
+  int per = per_sm[dev].load(std::memory_order_acquire);
+  if (!per) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes)) != cudaSuccess)
       return e;
-    int per = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kRowThreads, S::bytes)) != cudaSuccess)
       return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
-    per_sm[dev] = per;
+    per_sm[dev].store(per, std::memory_order_release);
   }
   const int rows = a.B * S::n;
-  const int grid = rows < per_sm[dev] * sm_count() ? rows : per_sm[dev] * sm_count();
+  const int grid = rows < per * sm_count() ? rows : per * sm_count();
   kern<<<grid, kRowThreads, S::bytes, s>>>(a);
   return cudaGetLastError();
 }

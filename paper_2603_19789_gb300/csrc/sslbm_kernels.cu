@@ -10,19 +10,22 @@
 //                   variants, as a pipeline of K warps per CTA: warp s computes level s+1
 //                   of the time-step wavefront.  A CTA owns a 128-column strip (4 columns
 //                   per lane, 16-byte accesses) with a K-column halo on each side and
-//                   streams down a segment of rows.  Warp 0 brings level-0 rows in with
-//                   cp.async into a shared-memory ring several rows ahead; every level's
-//                   output row goes through a double-buffered shared-memory slot to the
-//                   next warp, one CTA barrier per row; the last warp writes level K to
-//                   global memory.  Each warp keeps only its own level's two previous rows
-//                   in registers (about 110 registers per thread), so several CTAs share
-//                   an SM.  x neighbours come from warp shuffles.  Rows and columns
+//                   streams down a segment of rows, two rows per step of the pipeline.
+//                   Warp 0 brings level-0 rows in with cp.async into a shared-memory ring
+//                   three row pairs ahead; every level's output pair goes through a
+//                   double-buffered shared-memory slot (dynamic shared memory) to the next
+//                   warp, one CTA barrier per pair; the last warp writes level K to global
+//                   memory.  Each warp keeps only its own level's rows in four register
+//                   buffers (about 110 registers per thread), so two or more CTAs share an
+//                   SM.  x neighbours come from warp shuffles.  Rows and columns
 //                   outside the domain are loaded as ghost images (periodic wrap or the
 //                   even mirror extension), which the uniform stencil keeps consistent, so
 //                   no boundary logic is needed inside the pipeline.  DRAM traffic is one
 //                   read and one write of the five planes per K steps.
 // Both use the same per-cell expressions (sslbm_internal.cuh), so a blocked launch gives
 // the same bits as K one-step launches.
+#include <atomic>
+
 #include "sslbm_internal.cuh"
 #include "sslbm_pipe.cuh"
 
@@ -30,7 +33,6 @@ namespace sslbm {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 template <typename T, int V>
 struct Vec;
 template <>
@@ -202,15 +204,19 @@ cudaError_t launch_step1_t(const GridView& g, const void* coeffs, const void* in
   return cudaGetLastError();
 }
 
+// The fused kernel's shared-memory attributes, set once per device (a bit per device in an
+// atomic mask: host threads may launch concurrently; setting them twice is harmless).
 template <int MODE, int K>
-void prefer_shared(bool& done) {
-  if (!done) {
-    cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(PipeSmem<K>));
-    done = true;
-  }
+void prefer_shared() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return;
+  cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<K>));
+  done.fetch_or(bit, std::memory_order_release);
 }
 
 template <int MODE, int K>
@@ -218,8 +224,7 @@ cudaError_t launch_blocked_t(const GridView& g, const void* coeffs, const void* 
                              int seg_rows, cudaStream_t s) {
   constexpr int HL = (K + 3) / 4;
   constexpr int WV = 128 - 8 * HL;
-  static bool carveout_set = false;
-  prefer_shared<MODE, K>(carveout_set);
+  prefer_shared<MODE, K>();
   if (seg_rows <= 0) return cudaErrorInvalidValue;
   const int64_t nstrips = (g.nx + WV - 1) / WV;
   const int64_t nseg = (g.ny + seg_rows - 1) / seg_rows;
@@ -235,8 +240,7 @@ template <int MODE, int K>
 int default_seg_rows_t(const GridView& g) {
   constexpr int HL = (K + 3) / 4;
   constexpr int WV = 128 - 8 * HL;
-  static bool carveout_set = false;
-  prefer_shared<MODE, K>(carveout_set);
+  prefer_shared<MODE, K>();
   const int64_t nstrips = (g.nx + WV - 1) / WV;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
