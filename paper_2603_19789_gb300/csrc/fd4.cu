@@ -155,6 +155,137 @@ __global__ void __launch_bounds__(kTX * kTY) fd4_stage_kernel(int64_t nx, int64_
   }
 }
 
+// The FP32 stage for grids whose width is a multiple of 4: a 128 x 8 tile, each thread
+// four consecutive cells of one row.  Rows are staged with 16-byte loads (row starts and
+// planes are then 16-byte aligned), the two halo columns on each side separately through
+// ghost2, and u, acc, dst move as float4.  Only the slopes of the four cells stay live
+// across planes (64 registers, four CTAs per SM).  Per cell the expressions and their
+// order are those of fd4_stage_kernel, so both give the same bits.
+constexpr int kVX = 128, kVY = 8, kVPad = 4;  // tile columns and rows; shared rows start 4 columns left
+constexpr int kVS = kVX + 2 * kVPad;            // floats per shared row
+
+template <int STAGE, int ORDER>
+__global__ void __launch_bounds__(32 * kVY, 4) fd4_stage_f32v_kernel(int64_t nx, int64_t ny, int bc,
+                                                                  const Fd4Coeffs<float> k,
+                                                                  const float* __restrict__ src, const float* u,
+                                                                  float* acc, float* dst) {
+  constexpr int RY = kVY + 2 * kH;  // staged rows
+  static_assert(4 * 4 * RY <= 32 * kVY, "one thread per halo cell of the staged rows");
+  __shared__ __align__(16) float tile[4][RY][kVS];
+  const int64_t M = nx * ny;
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int64_t bx0 = (int64_t)blockIdx.x * kVX;
+  const int64_t x = bx0 + 4 * lane;
+  for (int64_t by0 = (int64_t)blockIdx.y * kVY; by0 < ny; by0 += (int64_t)gridDim.y * kVY) {
+    __syncthreads();  // the previous tile's readers are done
+    for (int j = wy; j < 4 * RY; j += kVY) {  // staged row j % RY of plane j / RY, one warp per row
+      const int r = j % RY, c = j / RY;
+      const float* row = src + c * M + ghost2(by0 + r - kH, ny, bc) * nx;
+      float4 v;
+      if (x + 3 < nx) {
+        v = *reinterpret_cast<const float4*>(row + x);
+      } else {  // past the last column: ghost images
+        v.x = row[ghost2(x, nx, bc)];
+        v.y = row[ghost2(x + 1, nx, bc)];
+        v.z = row[ghost2(x + 2, nx, bc)];
+        v.w = row[ghost2(x + 3, nx, bc)];
+      }
+      *reinterpret_cast<float4*>(&tile[c][r][kVPad + 4 * lane]) = v;
+    }
+    if (threadIdx.x < 4 * 4 * RY) {  // halo columns -2, -1, kVX, kVX+1 of every staged row
+      const int h = threadIdx.x & 3, rc = threadIdx.x >> 2;
+      const int r = rc % RY, c = rc / RY;
+      const int col = h < 2 ? h - kH : kVX + h - 2;
+      tile[c][r][kVPad + col] = src[c * M + ghost2(by0 + r - kH, ny, bc) * nx + ghost2(bx0 + col, nx, bc)];
+    }
+    __syncthreads();
+    const int64_t y = by0 + wy;
+    if (x >= nx || y >= ny) continue;
+    const int cy = wy + kH;
+    float rhs[5][4];
+    {  // reactions at this thread's four cells, Eq. (sources)
+      const float4 S4 = *reinterpret_cast<const float4*>(&tile[0][cy][kVPad + 4 * lane]);
+      const float4 E4 = *reinterpret_cast<const float4*>(&tile[1][cy][kVPad + 4 * lane]);
+      const float4 I4 = *reinterpret_cast<const float4*>(&tile[2][cy][kVPad + 4 * lane]);
+      const float4 R4 = *reinterpret_cast<const float4*>(&tile[3][cy][kVPad + 4 * lane]);
+      const float Sv[4] = {S4.x, S4.y, S4.z, S4.w}, Ev[4] = {E4.x, E4.y, E4.z, E4.w};
+      const float Iv[4] = {I4.x, I4.y, I4.z, I4.w}, Rv[4] = {R4.x, R4.y, R4.z, R4.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float S = Sv[e], E = Ev[e], I = Iv[e], R = Rv[e];
+        const float Nc = add(add(add(S, E), I), R);
+        const float F = Nc != 0.f ? dvd(mul(mul(k.beta, S), I), Nc) : 0.f;
+        const float aE = mul(k.alpha, E);
+        rhs[0][e] = -F;
+        rhs[1][e] = sub(F, aE);
+        rhs[2][e] = sub(aE, mul(k.gamma, I));
+        rhs[3][e] = mul(k.rg, I);
+        rhs[4][e] = mul(k.dg, I);
+      }
+    }
+    // the Laplacian, one plane at a time: h[2 + e] is cell e of this thread in the centre row,
+    // h[0..1] and h[6..7] the two cells on each side; col[dy + 2][e] the rows above and below
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float* row = &tile[c][cy][0];
+      const float2 hl = *reinterpret_cast<const float2*>(row + 4 * lane + 2);
+      const float4 hc = *reinterpret_cast<const float4*>(row + kVPad + 4 * lane);
+      const float2 hr = *reinterpret_cast<const float2*>(row + 2 * kVPad + 4 * lane);
+      const float h[8] = {hl.x, hl.y, hc.x, hc.y, hc.z, hc.w, hr.x, hr.y};
+      float col[2 * kH + 1][4];
+#pragma unroll
+      for (int dy = -kH; dy <= kH; ++dy) {
+        if (dy != 0 && (ORDER == 4 || dy == -1 || dy == 1)) {
+          const float4 t = *reinterpret_cast<const float4*>(&tile[c][cy + dy][kVPad + 4 * lane]);
+          col[dy + kH][0] = t.x, col[dy + kH][1] = t.y, col[dy + kH][2] = t.z, col[dy + kH][3] = t.w;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float u0 = h[2 + e];
+        float lx, ly;
+        if (ORDER == 4) {
+          lx = sub(add(sub(add(-h[e], mul(16.f, h[1 + e])), mul(30.f, u0)), mul(16.f, h[3 + e])), h[4 + e]);
+          ly = sub(add(sub(add(-col[0][e], mul(16.f, col[1][e])), mul(30.f, u0)), mul(16.f, col[3][e])),
+                   col[4][e]);
+        } else {
+          lx = add(sub(h[1 + e], mul(2.f, u0)), h[3 + e]);
+          ly = add(sub(col[1][e], mul(2.f, u0)), col[3][e]);
+        }
+        rhs[c][e] = add(rhs[c][e], mul(mul(k.d[c], add(lx, ly)), ORDER == 4 ? k.inv : k.inv2));
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const int64_t i = c * M + y * nx + x;
+      const float4 uu = *reinterpret_cast<const float4*>(u + i);
+      const float uv[4] = {uu.x, uu.y, uu.z, uu.w};
+      float o[4], a[4];
+      if (STAGE == 1) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          a[e] = rhs[c][e];
+          o[e] = add(uv[e], mul(k.half_dt, rhs[c][e]));
+        }
+      } else {
+        const float4 aa = *reinterpret_cast<const float4*>(acc + i);
+        const float av[4] = {aa.x, aa.y, aa.z, aa.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (STAGE == 4) {
+            o[e] = add(uv[e], mul(k.dt6, add(av[e], rhs[c][e])));
+          } else {
+            a[e] = add(av[e], mul(2.f, rhs[c][e]));
+            o[e] = add(uv[e], mul(STAGE == 2 ? k.half_dt : k.dt, rhs[c][e]));
+          }
+        }
+      }
+      if (STAGE != 4) *reinterpret_cast<float4*>(acc + i) = make_float4(a[0], a[1], a[2], a[3]);
+      *reinterpret_cast<float4*>(dst + i) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+  }
+}
+
 template <typename A, typename B>
 __global__ void convert_kernel(const A* __restrict__ a, B* __restrict__ b, int64_t n) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
@@ -208,6 +339,22 @@ struct DevGuard {
     if (prev >= 0) cudaSetDevice(prev);
   }
 };
+
+template <int ORDER>
+cudaError_t run_step_f32v(const sslbm_fd4* f, const Fd4Coeffs<float>& k) {
+  const int64_t nx = f->g.nx, ny = f->g.ny;
+  dim3 grid((unsigned)((nx + kVX - 1) / kVX), (unsigned)std::min<int64_t>(65535, (ny + kVY - 1) / kVY));
+  float* u = static_cast<float*>(f->buf(0));
+  float* t1 = static_cast<float*>(f->buf(1));
+  float* t2 = static_cast<float*>(f->buf(2));
+  float* acc = static_cast<float*>(f->buf(3));
+  const int bc = f->g.bc;
+  fd4_stage_f32v_kernel<1, ORDER><<<grid, 32 * kVY, 0, f->stream>>>(nx, ny, bc, k, u, u, acc, t1);
+  fd4_stage_f32v_kernel<2, ORDER><<<grid, 32 * kVY, 0, f->stream>>>(nx, ny, bc, k, t1, u, acc, t2);
+  fd4_stage_f32v_kernel<3, ORDER><<<grid, 32 * kVY, 0, f->stream>>>(nx, ny, bc, k, t2, u, acc, t1);
+  fd4_stage_f32v_kernel<4, ORDER><<<grid, 32 * kVY, 0, f->stream>>>(nx, ny, bc, k, t1, u, acc, u);
+  return cudaGetLastError();
+}
 
 template <typename T, int ORDER>
 cudaError_t run_step(const sslbm_fd4* f, const Fd4Coeffs<T>& k) {
@@ -363,6 +510,8 @@ int sslbm_fd4_step(sslbm_fd4* f, int64_t n) {
     cudaError_t e;
     if (f->g.precision == SSLBM_FP64)
       e = f->order == 4 ? run_step<double, 4>(f, f->k64) : run_step<double, 2>(f, f->k64);
+    else if (f->g.nx % 4 == 0)
+      e = f->order == 4 ? run_step_f32v<4>(f, f->k32) : run_step_f32v<2>(f, f->k32);
     else
       e = f->order == 4 ? run_step<float, 4>(f, f->k32) : run_step<float, 2>(f, f->k32);
     if (e != cudaSuccess) return cuda_err(e, "FD4 stage launch");

@@ -5,7 +5,8 @@ The kernels evaluate every operation in the oracle's order with one rounding eac
 contraction) and IEEE division, so FP64 agrees to the last bit up to the order of nothing
 at all; the test allows 1e-15 relative.  FP32 keeps the same order in single precision:
 over 12 RK4 steps of a contractive stencil the error stays within a few hundred FP32
-roundings of the field's peak (2e-5 relative max-norm, per compartment).
+roundings of the field's peak (2e-5 relative max-norm, per compartment).  Both FP32
+kernels are also compared bit for bit with the same formulas evaluated in float32.
 """
 import numpy as np
 import pytest
@@ -73,6 +74,101 @@ def test_fp32_matches_oracle(bc):
     ref = oracle.fd4_rk4_run(st.astype(np.float32).astype(np.float64), D, RATES, 0.5, 0.8, bc, 12)
     assert relmax(got, ref) <= 2e-5
     f.close()
+
+
+def _ghost(i, n, periodic):
+    """Cell index along an axis of n cells for a possibly ghost index i: periodic wrap, or the
+    even reflection about the boundary face (u[-1] = u[0], u[-2] = u[1]), clamped to the grid
+    when it is narrower than the stencil."""
+    i = np.asarray(i)
+    if periodic:
+        return np.mod(i, n)
+    i = np.where(i < 0, -1 - i, i)
+    i = np.where(i >= n, 2 * n - 1 - i, i)
+    return np.clip(i, 0, n - 1)
+
+
+def _fd4_float32(st, d, rates, dx, dt, bc, steps, order):
+    """The RK4 stages evaluated in FP32 with one rounding per operation (numpy float32), in
+    the operation order the kernels document, for a bitwise comparison."""
+    f = np.float32
+    beta, alpha, gamma, phi = rates
+    kb, ka, kg = f(beta), f(alpha), f(gamma)
+    rg, dg = f((1.0 - phi) * gamma), f(phi * gamma)
+    kd = [f(x) for x in d[:4]]
+    scale = f(1.0 / (12.0 * dx * dx)) if order == 4 else f(1.0 / (dx * dx))
+    half_dt, fdt, dt6 = f(0.5 * dt), f(dt), f(dt / 6.0)
+    ny, nx = st.shape[1:]
+    periodic = bc == L.BC_PERIODIC
+    gx = {o: _ghost(np.arange(nx) + o, nx, periodic) for o in (-2, -1, 1, 2)}
+    gy = {o: _ghost(np.arange(ny) + o, ny, periodic) for o in (-2, -1, 1, 2)}
+    c2, c16, c30 = f(2), f(16), f(30)
+
+    def slope(v):
+        S, E, I, R = v[0], v[1], v[2], v[3]
+        Nc = ((S + E) + I) + R
+        with np.errstate(divide="ignore", invalid="ignore"):
+            F = np.where(Nc != 0, ((kb * S) * I) / Nc, f(0)).astype(f)
+        aE = ka * E
+        r = [-F, F - aE, aE - kg * I, rg * I, dg * I]
+        for c in range(4):
+            u0 = v[c]
+            xm2, xm1, xp1, xp2 = (u0[:, gx[o]] for o in (-2, -1, 1, 2))
+            ym2, ym1, yp1, yp2 = (u0[gy[o], :] for o in (-2, -1, 1, 2))
+            if order == 4:
+                lx = ((((-xm2) + c16 * xm1) - c30 * u0) + c16 * xp1) - xp2
+                ly = ((((-ym2) + c16 * ym1) - c30 * u0) + c16 * yp1) - yp2
+            else:
+                lx = (xm1 - c2 * u0) + xp1
+                ly = (ym1 - c2 * u0) + yp1
+            r[c] = r[c] + (kd[c] * (lx + ly)) * scale
+        return np.stack(r)
+
+    u = st.astype(f)
+    for _ in range(steps):
+        k1 = slope(u)
+        acc, t = k1, u + half_dt * k1
+        k2 = slope(t)
+        acc, t = acc + c2 * k2, u + half_dt * k2
+        k3 = slope(t)
+        acc, t = acc + c2 * k3, u + fdt * k3
+        k4 = slope(t)
+        u = u + dt6 * (acc + k4)
+    return u
+
+
+@pytest.mark.parametrize("order", [4, 2])
+@pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
+@pytest.mark.parametrize("nx,ny", [(45, 33), (3, 5), (128, 40), (260, 37), (4, 6), (8, 3), (516, 130)])
+def test_fp32_bitwise_against_float32_evaluation(bc, nx, ny, order):
+    """Both FP32 stage kernels (one cell per thread for any width; four cells per thread with
+    16-byte rows when the width is a multiple of 4) give the bits of the same formulas
+    evaluated in float32, one rounding per operation: several 128-column tiles, a ragged
+    last tile, grids narrower than the stencil, ragged row tiles."""
+    st = _state(nx, ny, 5 * nx + ny)
+    f = L.Fd4(nx, ny, RATES, D, dx=0.5, dt=0.8, bc=bc, precision=L.FP32, order=order)
+    f.write(st.astype(np.float32))
+    f.step(6)
+    got = f.read(dtype=np.float32)
+    f.close()
+    ref = _fd4_float32(st.astype(np.float32), D, RATES, 0.5, 0.8, bc, 6, order)
+    assert got.dtype == np.float32 and ref.dtype == np.float32
+    bad = np.argwhere(got.view(np.uint32) != ref.view(np.uint32))
+    assert bad.size == 0, (len(bad), bad[:3], got[tuple(bad[0])], ref[tuple(bad[0])])
+
+
+@pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
+def test_fp32_vector_tiles_match_oracle(bc):
+    """The four-cells-per-thread FP32 kernel (width a multiple of 4, several tiles both ways)
+    against the FP64 oracle, with the tolerance of the one-cell kernel's test."""
+    st = _state(260, 44, 11)
+    f = L.Fd4(260, 44, RATES, D, dx=0.5, dt=0.8, bc=bc, precision=L.FP32)
+    f.write(st.astype(np.float32))
+    f.step(12)
+    got = f.read().astype(np.float64)
+    f.close()
+    ref = oracle.fd4_rk4_run(st.astype(np.float32).astype(np.float64), D, RATES, 0.5, 0.8, bc, 12)
+    assert relmax(got, ref) <= 2e-5
 
 
 def test_uniform_state_follows_the_ode():
