@@ -324,6 +324,7 @@ struct sslbm_fd4 {
   Fd4Coeffs<float> k32;
   int64_t steps = 0;
   int order = 4;  // order of the Laplacian: 4 (the reference) or 2
+  int sms = 1;    // multiprocessors of the device
   void* buf(int i) const { return ws + (size_t)i * sb; }  // 0 u, 1 t1, 2 t2, 3 acc
 };
 
@@ -371,6 +372,14 @@ cudaError_t run_step(const sslbm_fd4* f, const Fd4Coeffs<T>& k) {
   fd4_stage_kernel<T, 3, ORDER><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, t2, u, acc, t1);
   fd4_stage_kernel<T, 4, ORDER><<<grid, block, 0, f->stream>>>(nx, ny, bc, k, t1, u, acc, u);
   return cudaGetLastError();
+}
+
+// The four-cells-per-thread FP32 stage needs a width that is a multiple of 4, and at
+// least 1.5 waves of its tiles (four resident per SM): on smaller grids the one-cell tiles
+// keep more of the GPU busy.
+bool use_f32v(const sslbm_fd4* f) {
+  const int64_t tiles = ((f->g.nx + kVX - 1) / kVX) * ((f->g.ny + kVY - 1) / kVY);
+  return f->g.nx % 4 == 0 && tiles >= 6 * (int64_t)f->sms;
 }
 
 template <typename T>
@@ -441,6 +450,8 @@ int sslbm_fd4_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, s
   f->k64 = make_coeffs<double>(g, p);
   f->k32 = make_coeffs<float>(g, p);
   DevGuard dg(f->device);
+  if (cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, f->device) != cudaSuccess || f->sms < 1)
+    f->sms = 1;
   cudaError_t e = cudaMemsetAsync(f->ws, 0, need, f->stream);
   if (e != cudaSuccess) {
     delete f;
@@ -510,7 +521,7 @@ int sslbm_fd4_step(sslbm_fd4* f, int64_t n) {
     cudaError_t e;
     if (f->g.precision == SSLBM_FP64)
       e = f->order == 4 ? run_step<double, 4>(f, f->k64) : run_step<double, 2>(f, f->k64);
-    else if (f->g.nx % 4 == 0)
+    else if (use_f32v(f))
       e = f->order == 4 ? run_step_f32v<4>(f, f->k32) : run_step_f32v<2>(f, f->k32);
     else
       e = f->order == 4 ? run_step<float, 4>(f, f->k32) : run_step<float, 2>(f, f->k32);

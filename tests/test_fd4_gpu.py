@@ -139,19 +139,21 @@ def _fd4_float32(st, d, rates, dx, dt, bc, steps, order):
 
 @pytest.mark.parametrize("order", [4, 2])
 @pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
-@pytest.mark.parametrize("nx,ny", [(45, 33), (3, 5), (128, 40), (260, 37), (4, 6), (8, 3), (516, 130)])
-def test_fp32_bitwise_against_float32_evaluation(bc, nx, ny, order):
-    """Both FP32 stage kernels (one cell per thread for any width; four cells per thread with
-    16-byte rows when the width is a multiple of 4) give the bits of the same formulas
-    evaluated in float32, one rounding per operation: several 128-column tiles, a ragged
-    last tile, grids narrower than the stencil, ragged row tiles."""
+@pytest.mark.parametrize("nx,ny,steps", [(45, 33, 6), (3, 5, 6), (128, 40, 6), (4, 6, 6), (8, 3, 6), (516, 130, 6),
+                                         (1028, 1001, 2)])
+def test_fp32_bitwise_against_float32_evaluation(bc, nx, ny, steps, order):
+    """Both FP32 stage kernels give the bits of the same formulas evaluated in float32, one
+    rounding per operation.  Grids of fewer than six 128 x 8 tiles per SM run the one-cell
+    kernel (several tiles, ragged edges, grids narrower than the stencil); 1028 x 1001
+    (1134 tiles, a last tile of 4 columns and a last row tile of 1 row) runs the
+    four-cells-per-thread kernel on a GB300's 152 SMs."""
     st = _state(nx, ny, 5 * nx + ny)
     f = L.Fd4(nx, ny, RATES, D, dx=0.5, dt=0.8, bc=bc, precision=L.FP32, order=order)
     f.write(st.astype(np.float32))
-    f.step(6)
+    f.step(steps)
     got = f.read(dtype=np.float32)
     f.close()
-    ref = _fd4_float32(st.astype(np.float32), D, RATES, 0.5, 0.8, bc, 6, order)
+    ref = _fd4_float32(st.astype(np.float32), D, RATES, 0.5, 0.8, bc, steps, order)
     assert got.dtype == np.float32 and ref.dtype == np.float32
     bad = np.argwhere(got.view(np.uint32) != ref.view(np.uint32))
     assert bad.size == 0, (len(bad), bad[:3], got[tuple(bad[0])], ref[tuple(bad[0])])
@@ -159,10 +161,10 @@ def test_fp32_bitwise_against_float32_evaluation(bc, nx, ny, order):
 
 @pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
 def test_fp32_vector_tiles_match_oracle(bc):
-    """The four-cells-per-thread FP32 kernel (width a multiple of 4, several tiles both ways)
-    against the FP64 oracle, with the tolerance of the one-cell kernel's test."""
-    st = _state(260, 44, 11)
-    f = L.Fd4(260, 44, RATES, D, dx=0.5, dt=0.8, bc=bc, precision=L.FP32)
+    """The four-cells-per-thread FP32 kernel (a grid of more than six tiles per SM, ragged in
+    both directions) against the FP64 oracle, with the tolerance of the one-cell kernel's test."""
+    st = _state(1028, 1001, 11)
+    f = L.Fd4(1028, 1001, RATES, D, dx=0.5, dt=0.8, bc=bc, precision=L.FP32)
     f.write(st.astype(np.float32))
     f.step(12)
     got = f.read().astype(np.float64)
