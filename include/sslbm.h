@@ -216,6 +216,35 @@ int bgk_step(sslbm_handle* h, int64_t n);
 /* Steps taken by a scheme since its last full write. */
 int64_t sslbm_steps_done(const sslbm_handle* h, int scheme);
 
+/* ---- checkpoint / resume ------------------------------------------------------------- */
+
+/* A checkpoint is the solver's state exactly as stored, so that a run resumed from it
+ * gives the bits of the uninterrupted run.  sslbm_read / sslbm_write cannot do that for
+ * every configuration: FP32_DEV returns S rebuilt from the stored deviation, FP32_KAHAN
+ * the compensated value, and a BGK write sets equilibrium populations.  Layout (a flat
+ * byte buffer, host or device, owned by the caller): a 128-byte header (magic "SSLC",
+ * version, nx, ny, precision, lattice, bc, schemes, the two step counters, the plane
+ * counts and the element size), then every stored plane in the solver's precision, each
+ * ny*nx values row-major: the SSLBM planes (5, or 10 with the Kahan compensations) when
+ * the handle holds that scheme, then the 21 BGK planes (20 populations, D) when it holds
+ * BGK.  Parameters, blocking and the diffusivity scale fields are the handle's own and
+ * are not part of a checkpoint. */
+
+/* Bytes of a checkpoint of this handle. */
+int sslbm_checkpoint_bytes(const sslbm_handle* h, size_t* bytes);
+
+/* Copy the state and the step counters into dst (bytes >= sslbm_checkpoint_bytes, else
+ * SSLBM_ERR_BAD_ARG), on the host (dst_on_device = 0) or the device (1).  Synchronises
+ * the stream. */
+int sslbm_checkpoint_save(sslbm_handle* h, void* dst, size_t bytes, int dst_on_device);
+
+/* Restore state and step counters from a checkpoint made by a handle of the same grid
+ * (nx, ny, precision, lattice, bc, schemes).  A buffer that is too short, has another
+ * magic or version, or was saved by a different configuration is rejected with
+ * SSLBM_ERR_BAD_ARG before anything is copied.  A host source is consumed before the call
+ * returns; a device source is read in stream order. */
+int sslbm_checkpoint_load(sslbm_handle* h, const void* src, size_t bytes, int src_on_device);
+
 /* ---- diagnostics (Sec. II.C 'Mass conservation') ------------------------------------ */
 
 /* Per-compartment totals sum_x rho^C(x) accumulated in double precision, and the

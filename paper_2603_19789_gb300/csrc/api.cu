@@ -5,6 +5,7 @@
 // caller's workspace, stream-ordered dispatch of the kernels and status reporting.
 // No device memory is allocated here; the caller provides it.
 #include <cmath>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -558,6 +559,131 @@ int bgk_step(sslbm_handle* h, int64_t n) {
 int64_t sslbm_steps_done(const sslbm_handle* h, int scheme) {
   if (!h) return -1;
   return scheme == SSLBM_SCHEME_BGK ? h->b_steps : h->s_steps;
+}
+
+}  // extern "C"
+
+namespace {
+constexpr uint32_t kCkptMagic = 0x434C5353u;  // the bytes "SSLC"
+constexpr uint32_t kCkptVersion = 1;
+constexpr size_t kCkptData = 128;  // the planes start here
+struct CkptHeader {
+  uint32_t magic, version;
+  int64_t nx, ny;
+  int32_t precision, lattice, bc, schemes;
+  int64_t s_steps, b_steps;
+  int32_t s_planes, b_planes, esize, reserved;
+};
+static_assert(sizeof(CkptHeader) <= kCkptData, "checkpoint header");
+
+CkptHeader ckpt_header(const sslbm_handle* h) {
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  hd.magic = kCkptMagic;
+  hd.version = kCkptVersion;
+  hd.nx = h->g.nx;
+  hd.ny = h->g.ny;
+  hd.precision = h->g.precision;
+  hd.lattice = h->g.lattice;
+  hd.bc = h->g.bc;
+  hd.schemes = h->g.schemes;
+  hd.s_steps = h->s_steps;
+  hd.b_steps = h->b_steps;
+  hd.s_planes = (h->g.schemes & SSLBM_WANT_SSLBM) ? h->L.s_planes : 0;
+  hd.b_planes = (h->g.schemes & SSLBM_WANT_BGK) ? kBgkPlanes : 0;
+  hd.esize = (int32_t)h->L.esize;
+  return hd;
+}
+
+size_t ckpt_bytes(const CkptHeader& hd) {
+  return kCkptData + (size_t)(hd.s_planes + hd.b_planes) * (size_t)hd.nx * (size_t)hd.ny * (size_t)hd.esize;
+}
+
+// The i-th stored plane: SSLBM planes first, then BGK.
+char* ckpt_plane(const sslbm_handle* h, const CkptHeader& hd, int i) {
+  if (i < hd.s_planes) return h->s_plane(h->s_cur, i);
+  return h->b_buf[h->b_cur] + (size_t)(i - hd.s_planes) * h->L.plane_bytes;
+}
+}  // namespace
+
+extern "C" {
+
+int sslbm_checkpoint_bytes(const sslbm_handle* h, size_t* bytes) {
+  if (!h || !bytes) return fail(SSLBM_ERR_BAD_ARG, "handle or bytes is NULL");
+  *bytes = ckpt_bytes(ckpt_header(h));
+  return SSLBM_OK;
+}
+
+int sslbm_checkpoint_save(sslbm_handle* h, void* dst, size_t bytes, int dst_on_device) {
+  if (!h || !dst) return fail(SSLBM_ERR_BAD_ARG, "handle or dst is NULL");
+  const CkptHeader hd = ckpt_header(h);
+  const size_t need = ckpt_bytes(hd);
+  if (bytes < need) return fail(SSLBM_ERR_BAD_ARG, "checkpoint buffer of %zu bytes < %zu", bytes, need);
+  DeviceGuard dg(h->device);
+  unsigned char head[kCkptData];
+  std::memset(head, 0, sizeof(head));
+  std::memcpy(head, &hd, sizeof(hd));
+  if (dst_on_device) {
+    cudaError_t e = cudaMemcpyAsync(dst, head, kCkptData, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(checkpoint header)");
+  } else {
+    std::memcpy(dst, head, kCkptData);
+  }
+  const size_t row = (size_t)hd.nx * hd.esize, plane_user = row * (size_t)hd.ny;
+  char* d = static_cast<char*>(dst) + kCkptData;
+  for (int i = 0; i < hd.s_planes + hd.b_planes; ++i, d += plane_user) {
+    cudaError_t e = cudaMemcpy2DAsync(d, row, ckpt_plane(h, hd, i), (size_t)h->L.pitch * h->L.esize, row,
+                                      (size_t)hd.ny, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                      h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync(checkpoint save)");
+  }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(checkpoint save)");
+  return SSLBM_OK;
+}
+
+int sslbm_checkpoint_load(sslbm_handle* h, const void* src, size_t bytes, int src_on_device) {
+  if (!h || !src) return fail(SSLBM_ERR_BAD_ARG, "handle or src is NULL");
+  if (bytes < kCkptData) return fail(SSLBM_ERR_BAD_ARG, "checkpoint of %zu bytes has no header", bytes);
+  DeviceGuard dg(h->device);
+  CkptHeader got;
+  if (src_on_device) {
+    cudaError_t e = cudaMemcpyAsync(&got, src, sizeof(got), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint header");
+  } else {
+    std::memcpy(&got, src, sizeof(got));
+  }
+  if (got.magic != kCkptMagic || got.version != kCkptVersion)
+    return fail(SSLBM_ERR_BAD_ARG, "not a checkpoint of this format (magic %08x, version %u)", got.magic,
+                got.version);
+  const CkptHeader own = ckpt_header(h);
+  if (got.nx != own.nx || got.ny != own.ny || got.precision != own.precision || got.lattice != own.lattice ||
+      got.bc != own.bc || got.schemes != own.schemes || got.s_planes != own.s_planes ||
+      got.b_planes != own.b_planes || got.esize != own.esize)
+    return fail(SSLBM_ERR_BAD_ARG,
+                "checkpoint of a %lld x %lld grid (precision %d, lattice %d, bc %d, schemes %d) does not match "
+                "this %lld x %lld solver (precision %d, lattice %d, bc %d, schemes %d)",
+                (long long)got.nx, (long long)got.ny, got.precision, got.lattice, got.bc, got.schemes,
+                (long long)own.nx, (long long)own.ny, own.precision, own.lattice, own.bc, own.schemes);
+  if (got.s_steps < 0 || got.b_steps < 0) return fail(SSLBM_ERR_BAD_ARG, "negative step counters");
+  const size_t need = ckpt_bytes(own);
+  if (bytes < need) return fail(SSLBM_ERR_BAD_ARG, "checkpoint of %zu bytes < %zu", bytes, need);
+  const size_t row = (size_t)own.nx * own.esize, plane_user = row * (size_t)own.ny;
+  const char* sp = static_cast<const char*>(src) + kCkptData;
+  for (int i = 0; i < own.s_planes + own.b_planes; ++i, sp += plane_user) {
+    cudaError_t e = cudaMemcpy2DAsync(ckpt_plane(h, own, i), (size_t)h->L.pitch * h->L.esize, sp, row, row,
+                                      (size_t)own.ny, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                      h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync(checkpoint load)");
+  }
+  if (!src_on_device) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(checkpoint load)");
+  }
+  h->s_steps = got.s_steps;
+  h->b_steps = got.b_steps;
+  return SSLBM_OK;
 }
 
 int sslbm_diagnostics(sslbm_handle* h, int scheme, double* totals, double* peak_I) {

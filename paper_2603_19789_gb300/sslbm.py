@@ -37,7 +37,9 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP
 # every symbol include/sslbm.h declares
 EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspace_bytes",
            "sslbm_create", "sslbm_set_stream", "sslbm_destroy", "sslbm_write", "sslbm_read",
-           "sslbm_set_diffusivity_scale", "sslbm_step", "bgk_step", "sslbm_steps_done", "sslbm_diagnostics", "sslbm_set_blocking",
+           "sslbm_set_diffusivity_scale", "sslbm_step", "bgk_step", "sslbm_steps_done",
+           "sslbm_checkpoint_bytes", "sslbm_checkpoint_save", "sslbm_checkpoint_load",
+           "sslbm_diagnostics", "sslbm_set_blocking",
            "sslbm_get_blocking", "sslbm_diagnostics_noalloc", "sslbm_autotune",
            "sslbm_ensemble_workspace_bytes", "sslbm_ensemble_create", "sslbm_ensemble_destroy",
            "sslbm_ensemble_set_tiling", "sslbm_ensemble_get_tiling",
@@ -115,6 +117,9 @@ def load(path: str = LIB_PATH):
             "sslbm_step": (i32, [_vp, i64]),
             "bgk_step": (i32, [_vp, i64]),
             "sslbm_steps_done": (i64, [_vp, i32]),
+            "sslbm_checkpoint_bytes": (i32, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+            "sslbm_checkpoint_save": (i32, [_vp, _vp, ctypes.c_size_t, i32]),
+            "sslbm_checkpoint_load": (i32, [_vp, _vp, ctypes.c_size_t, i32]),
             "sslbm_diagnostics": (i32, [_vp, i32, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]),
             "sslbm_set_blocking": (i32, [_vp, i32, i32]),
@@ -291,6 +296,38 @@ def sslbm_steps_done(h, scheme: int = SCHEME_SSLBM) -> int:
     return int(load().sslbm_steps_done(h, int(scheme)))
 
 
+def _raw(a):
+    """(pointer, on_device, nbytes) of a contiguous numpy array or torch tensor of any dtype."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0, a.nbytes
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise TypeError(type(a))
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr(), 1 if a.is_cuda else 0, a.numel() * a.element_size()
+
+
+def sslbm_checkpoint_bytes(h) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().sslbm_checkpoint_bytes(h, ctypes.byref(n)), "sslbm_checkpoint_bytes")
+    return int(n.value)
+
+
+def sslbm_checkpoint_save(h, dst):
+    """State and step counters into dst (a uint8 numpy array or torch tensor, host or device)."""
+    ptr, dev, nbytes = _raw(dst)
+    _check(load().sslbm_checkpoint_save(h, _vp(ptr), nbytes, dev), "sslbm_checkpoint_save")
+    return dst
+
+
+def sslbm_checkpoint_load(h, src):
+    ptr, dev, nbytes = _raw(src)
+    _check(load().sslbm_checkpoint_load(h, _vp(ptr), nbytes, dev), "sslbm_checkpoint_load")
+
+
 def sslbm_diagnostics(h, scheme: int = SCHEME_SSLBM):
     tot = (ctypes.c_double * 5)()
     pk = ctypes.c_double(0.0)
@@ -401,6 +438,21 @@ class Solver:
 
     def steps_done(self, scheme=SCHEME_SSLBM):
         return sslbm_steps_done(self.h, scheme)
+
+    def checkpoint(self, on_device=False):
+        """The state as stored, with the step counters: a host numpy uint8 array, or a
+        device uint8 tensor with on_device=True."""
+        n = sslbm_checkpoint_bytes(self.h)
+        if on_device:
+            buf = self.torch.empty(n, dtype=self.torch.uint8, device=self.device)
+        else:
+            buf = np.empty(n, dtype=np.uint8)
+        return sslbm_checkpoint_save(self.h, buf)
+
+    def restore(self, buf):
+        """Resume from a checkpoint of a solver with the same grid, precision, lattice,
+        boundary and schemes."""
+        sslbm_checkpoint_load(self.h, buf)
 
 
 # ---------------------------------------------------------------------------
