@@ -230,6 +230,23 @@ int64_t sslbm_steps_done(const sslbm_handle* h, int scheme);
  * BGK.  Parameters, blocking and the diffusivity scale fields are the handle's own and
  * are not part of a checkpoint. */
 
+/* ---- debug build -------------------------------------------------------------------- */
+
+/* Compiled with SSLBM_BOUNDS_CHECK (libsslbm_check.so, built by build.py --checked), the
+ * hot-path kernels -- the fused pipeline tile of sslbm_step and the ensemble, the one-step
+ * kernel, the BGK step and the diagnostics -- test the row and column indices of their
+ * global loads and stores against the grid before each access, skip an access whose index
+ * is out of range and record it.  sslbm_debug_bounds synchronises the current device,
+ * returns the number of such indices since the last call, the first one, the limit it
+ * missed and a site number (which check, offset by 100 per source file), then clears the
+ * records.  count = 0 means every checked index was in range; value, limit and site are
+ * then 0, 0 and -1.  Any pointer may be NULL.  sslbm_debug_bounds_probe checks value
+ * against [0, limit) once on the device (site 999 + 300), with no memory access behind the
+ * check: it exercises the recording path.  Release builds: both return
+ * SSLBM_ERR_UNSUPPORTED. */
+int sslbm_debug_bounds(long long* count, long long* value, long long* limit, int* site);
+int sslbm_debug_bounds_probe(long long value, long long limit);
+
 /* Bytes of a checkpoint of this handle. */
 int sslbm_checkpoint_bytes(const sslbm_handle* h, size_t* bytes);
 

@@ -3,7 +3,9 @@
 Each .cu translation unit under csrc/ compiles in parallel to an object file in
 _build/, then nvcc links them (with the static CUDA runtime) into
 paper_2603_19789_gb300/libsslbm.so.  Rebuilds only when a source or header is newer
-than the library.
+than the library.  `--checked` builds the debug library libsslbm_check.so instead, whose
+hot-path kernels check every row and column index before using it (SSLBM_BOUNDS_CHECK);
+the binding loads it when SSLBM_LIBRARY names it.
 """
 from __future__ import annotations
 
@@ -19,6 +21,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsslbm.so")
+# the debug build: every hot-path kernel checks its indices (SSLBM_BOUNDS_CHECK)
+LIB_CHECKED = os.path.join(PKG, "libsslbm_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC]
@@ -39,22 +43,27 @@ def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every translation unit for sm_103a and link libsslbm.so; with checked=True,
+    the debug library libsslbm_check.so with the kernels' index checks (SSLBM_BOUNDS_CHECK)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
+    bdir = os.path.join(BUILD, "check") if checked else BUILD
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
+    flags = [*NVCC_FLAGS, "-DSSLBM_BOUNDS_CHECK"] if checked else NVCC_FLAGS
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+        cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -67,15 +76,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         for _, err in results:
             print(err)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -15,6 +15,7 @@
 #include <tuple>
 #include <vector>
 
+#include "bounds.cuh"
 #include "sslbm_internal.cuh"
 #include "variants.cuh"
 
@@ -607,6 +608,48 @@ char* ckpt_plane(const sslbm_handle* h, const CkptHeader& hd, int i) {
 }  // namespace
 
 extern "C" {
+
+int sslbm_debug_bounds(long long* count, long long* value, long long* limit, int* site) {
+#ifndef SSLBM_BOUNDS_CHECK
+  (void)count, (void)value, (void)limit, (void)site;
+  return fail(SSLBM_ERR_UNSUPPORTED, "this library was built without SSLBM_BOUNDS_CHECK");
+#else
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize(bounds records)");
+  int (*const take[])(sslbm::OobRecord*) = {sslbm::oob_take_kernels, sslbm::oob_take_ensemble, sslbm::oob_take_bgk,
+                                            sslbm::oob_take_io};
+  const int tu_site[] = {0, 100, 200, 300};  // site numbers are offset by translation unit
+  unsigned long long total = 0;
+  sslbm::OobRecord first{};
+  int first_site = -1;
+  for (int i = 0; i < 4; ++i) {
+    sslbm::OobRecord r{};
+    if (take[i](&r) != 0) return fail(SSLBM_ERR_CUDA, "reading the bounds record of unit %d", i);
+    if (r.count && first_site < 0) {
+      first = r;
+      first_site = tu_site[i] + r.site;
+    }
+    total += r.count;
+  }
+  if (count) *count = (long long)total;
+  if (value) *value = first.value;
+  if (limit) *limit = first.limit;
+  if (site) *site = first_site;
+  return SSLBM_OK;
+#endif
+}
+
+int sslbm_debug_bounds_probe(long long value, long long limit) {
+#ifndef SSLBM_BOUNDS_CHECK
+  (void)value, (void)limit;
+  return fail(SSLBM_ERR_UNSUPPORTED, "this library was built without SSLBM_BOUNDS_CHECK");
+#else
+  cudaError_t e = sslbm::launch_oob_probe(value, limit, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "bounds probe");
+  return SSLBM_OK;
+#endif
+}
 
 int sslbm_checkpoint_bytes(const sslbm_handle* h, size_t* bytes) {
   if (!h || !bytes) return fail(SSLBM_ERR_BAD_ARG, "handle or bytes is NULL");

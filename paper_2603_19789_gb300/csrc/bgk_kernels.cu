@@ -14,7 +14,10 @@
 // neighbouring addresses).  A population that would leave through a no-flux wall is
 // written back into the opposite direction at the same cell (halfway bounce-back);
 // with periodic boundaries it wraps.
+#include "bounds.cuh"
 #include "sslbm_internal.cuh"
+
+SSLBM_OOB_ACCESSOR(bgk)
 
 namespace sslbm {
 
@@ -69,7 +72,10 @@ __global__ void __launch_bounds__(256) bgk_step_kernel(const GridView g, const C
       } else {
         tidx = idx;
         dir = kOpp[i];
+        tx = x;
+        ty = y;
       }
+      if (!(SSLBM_IN(tx, 1, g.nx, 20) && SSLBM_IN(ty, 1, g.ny, 21))) continue;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         // f + (w rho - f)/tau + w Psi dt

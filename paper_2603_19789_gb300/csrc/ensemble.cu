@@ -25,8 +25,11 @@
 #include <new>
 #include <vector>
 
+#include "bounds.cuh"
 #include "sslbm_internal.cuh"
 #include "sslbm_pipe.cuh"
+
+SSLBM_OOB_ACCESSOR(ensemble)
 
 namespace sslbm {
 int record_error(int status, const char* msg);

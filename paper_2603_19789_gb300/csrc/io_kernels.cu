@@ -4,7 +4,10 @@
 #include <float.h>
 #include <stdint.h>
 
+#include "bounds.cuh"
 #include "sslbm_internal.cuh"
+
+SSLBM_OOB_ACCESSOR(io)
 
 namespace sslbm {
 
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(256) diag_partial_kernel(const GridView g,
     }
   }
   block_reduce6(v);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && SSLBM_IN(blockIdx.x, 1, kDiagBlocks, 31)) {
 #pragma unroll
     for (int j = 0; j < kDiagSlots; ++j) partials[blockIdx.x * kDiagSlots + j] = v[j];
   }
@@ -144,6 +147,7 @@ __global__ void __launch_bounds__(256) diag_partial_f32x4_kernel(const GridView 
     float hi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     float pk = -FLT_MAX;
     for (int64_t x = 4 * (int64_t)threadIdx.x; x < g.nx; x += 4 * (int64_t)blockDim.x) {
+      if (!SSLBM_IN(x, 4, g.pitch, 30)) continue;
       const int64_t idx = y * g.pitch + x;
       const int nv = g.nx - x < 4 ? (int)(g.nx - x) : 4;
       float r[5][4];
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(256) diag_partial_f32x4_kernel(const GridView 
     if (!COMP) v[5] = fmax(v[5], (double)pk);
   }
   block_reduce6(v);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && SSLBM_IN(blockIdx.x, 1, kDiagBlocks, 31)) {
 #pragma unroll
     for (int j = 0; j < kDiagSlots; ++j) partials[blockIdx.x * kDiagSlots + j] = v[j];
   }
@@ -299,6 +303,16 @@ cudaError_t launch_diagnostics(int precision, int layout, const GridView& g, con
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   diag_final_kernel<<<1, 256, 0, s>>>(partials, (int)blocks, result);
+  return cudaGetLastError();
+}
+
+namespace {
+// One index check with no memory access behind it (site 999).
+__global__ void oob_probe_kernel(long long v, long long limit) { (void)SSLBM_IN(v, 1, limit, 999); }
+}  // namespace
+
+cudaError_t launch_oob_probe(long long v, long long limit, cudaStream_t s) {
+  oob_probe_kernel<<<1, 1, 0, s>>>(v, limit);
   return cudaGetLastError();
 }
 

@@ -26,8 +26,11 @@
 // the same bits as K one-step launches.
 #include <atomic>
 
+#include "bounds.cuh"
 #include "sslbm_internal.cuh"
 #include "sslbm_pipe.cuh"
+
+SSLBM_OOB_ACCESSOR(kernels)
 
 namespace sslbm {
 
@@ -78,9 +81,13 @@ __global__ void __launch_bounds__(256, MODE == MODE_KAHAN ? 2 : 1) step1_kernel(
   const int64_t xr = link_index(x0 + nvalid, g.nx, g.bc);
   for (int64_t y = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; y < g.ny;
        y += (int64_t)gridDim.y * blockDim.y) {
+    const int64_t yu = link_index(y - 1, g.ny, g.bc), yd = link_index(y + 1, g.ny, g.bc);
+    if (!(SSLBM_IN(yu, 1, g.ny, 10) && SSLBM_IN(yd, 1, g.ny, 11) && SSLBM_IN(x0, V, g.pitch, 12) &&
+          SSLBM_IN(xl, 1, g.nx, 13) && SSLBM_IN(xr, 1, g.nx, 14)))
+      continue;
     const int64_t rc = y * g.pitch;
-    const int64_t ru = link_index(y - 1, g.ny, g.bc) * g.pitch;
-    const int64_t rd = link_index(y + 1, g.ny, g.bc) * g.pitch;
+    const int64_t ru = yu * g.pitch;
+    const int64_t rd = yd * g.pitch;
     T c[4][V], lap[4][V];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {

@@ -15,6 +15,7 @@
 // The arithmetic is the packed form of seird_cell / seird_cell_dev, bit-identical to the
 // one-step kernel.
 #pragma once
+#include "bounds.cuh"
 #include "sslbm_internal.cuh"
 
 namespace sslbm {
@@ -81,19 +82,21 @@ __device__ __forceinline__ void emit_row(PipeSmem<K>& sm, const GridView& g, con
 #pragma unroll
     for (int f = 0; f < 5; ++f)
       *reinterpret_cast<float4*>(dst + 128 * f) = make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
-  } else if (writer && r >= y0 && r < y1) {
+  } else if (writer && r >= y0 && r < y1 && SSLBM_IN(r, 1, g.ny, 5)) {
     float* o = out + r * g.pitch + xs;
     if (xs + 3 < g.nx) {
+      if (SSLBM_IN(xs, 4, g.nx, 6)) {
 #pragma unroll
-      for (int f = 0; f < 5; ++f)
-        *reinterpret_cast<float4*>(o + f * g.plane) = make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
+        for (int f = 0; f < 5; ++f)
+          *reinterpret_cast<float4*>(o + f * g.plane) = make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
+      }
     } else {
 #pragma unroll
       for (int f = 0; f < 5; ++f) {
         const float v[4] = {M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y};
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj)
-          if (xs + jj < g.nx) o[f * g.plane + jj] = v[jj];
+          if (xs + jj < g.nx && SSLBM_IN(xs + jj, 1, g.nx, 7)) o[f * g.plane + jj] = v[jj];
       }
     }
   }
@@ -162,18 +165,21 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K>& sm, const GridView& g, co
   auto issue = [&](int64_t q) {  // warp 0: copy level-0 row q into its ring slot
     if (!loads || q >= load_end) return;
     const int slot = (int)((q - qa) % kRing0);
-    const int64_t row = ghost_index(q, g.ny, g.bc) * g.pitch;
+    const int64_t yq = ghost_index(q, g.ny, g.bc);
+    if (!SSLBM_IN(yq, 1, g.ny, 1)) return;
+    const int64_t row = yq * g.pitch;
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
       const float* src = in + f * g.plane + row;
       float* dst = &sm.r0[slot][f][4 * lane];
       if (WRAP16) {
-        cp_async16(dst, src + xw);
+        if (SSLBM_IN(xw, 4, g.nx, 2)) cp_async16(dst, src + xw);
       } else if (vec_ok) {
-        cp_async16(dst, src + xs);
+        if (SSLBM_IN(xs, 4, g.nx, 3)) cp_async16(dst, src + xs);
       } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cp_async4(dst + j, src + xm[j]);
+        for (int j = 0; j < 4; ++j)
+          if (SSLBM_IN(xm[j], 1, g.nx, 4)) cp_async4(dst + j, src + xm[j]);
       }
     }
   };

@@ -17,7 +17,8 @@ import threading
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libsslbm.so")
+# SSLBM_LIBRARY selects another build of the same library (the index-checked debug build)
+LIB_PATH = os.environ.get("SSLBM_LIBRARY") or os.path.join(_PKG, "libsslbm.so")
 
 # constants of include/sslbm.h
 SSLBM_OK = 0
@@ -39,6 +40,7 @@ EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspa
            "sslbm_create", "sslbm_set_stream", "sslbm_destroy", "sslbm_write", "sslbm_read",
            "sslbm_set_diffusivity_scale", "sslbm_step", "bgk_step", "sslbm_steps_done",
            "sslbm_checkpoint_bytes", "sslbm_checkpoint_save", "sslbm_checkpoint_load",
+           "sslbm_debug_bounds", "sslbm_debug_bounds_probe",
            "sslbm_diagnostics", "sslbm_set_blocking",
            "sslbm_get_blocking", "sslbm_diagnostics_noalloc", "sslbm_autotune",
            "sslbm_ensemble_workspace_bytes", "sslbm_ensemble_create", "sslbm_ensemble_destroy",
@@ -117,6 +119,9 @@ def load(path: str = LIB_PATH):
             "sslbm_step": (i32, [_vp, i64]),
             "bgk_step": (i32, [_vp, i64]),
             "sslbm_steps_done": (i64, [_vp, i32]),
+            "sslbm_debug_bounds": (i32, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i32)]),
+            "sslbm_debug_bounds_probe": (i32, [ctypes.c_longlong, ctypes.c_longlong]),
             "sslbm_checkpoint_bytes": (i32, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
             "sslbm_checkpoint_save": (i32, [_vp, _vp, ctypes.c_size_t, i32]),
             "sslbm_checkpoint_load": (i32, [_vp, _vp, ctypes.c_size_t, i32]),
@@ -308,6 +313,20 @@ def _raw(a):
     if not a.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return a.data_ptr(), 1 if a.is_cuda else 0, a.numel() * a.element_size()
+
+
+def sslbm_debug_bounds():
+    """Index checks of the debug build since the last call: {count, value, limit, site}
+    (SslbmError with SSLBM_ERR_UNSUPPORTED from a release build)."""
+    c, v, lim = ctypes.c_longlong(0), ctypes.c_longlong(0), ctypes.c_longlong(0)
+    site = ctypes.c_int(0)
+    _check(load().sslbm_debug_bounds(ctypes.byref(c), ctypes.byref(v), ctypes.byref(lim), ctypes.byref(site)),
+           "sslbm_debug_bounds")
+    return {"count": int(c.value), "value": int(v.value), "limit": int(lim.value), "site": int(site.value)}
+
+
+def sslbm_debug_bounds_probe(value: int, limit: int):
+    _check(load().sslbm_debug_bounds_probe(int(value), int(limit)), "sslbm_debug_bounds_probe")
 
 
 def sslbm_checkpoint_bytes(h) -> int:
