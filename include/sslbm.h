@@ -48,7 +48,7 @@ extern "C" {
 #define SSLBM_ERR_TIMEOUT (-4)     /* a bounded device wait ran out (ensemble barrier) */
 #define SSLBM_ERR_NONFINITE (-5)   /* a diagnostic found NaN or Inf in the state */
 #define SSLBM_ERR_WORKSPACE (-6)   /* workspace missing, too small or misaligned */
-#define SSLBM_ERR_UNSUPPORTED (-7) /* valid request this build does not provide */
+#define SSLBM_ERR_UNSUPPORTED (-7) /* valid request the library does not provide */
 #define SSLBM_ERR_STATE (-8)       /* call out of order (e.g. stepping an unwritten scheme) */
 
 /* ---- enumerations ------------------------------------------------------- */
