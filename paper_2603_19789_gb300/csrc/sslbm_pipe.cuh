@@ -5,11 +5,12 @@
 // A tile is a 128-column strip (4 columns per lane, 16-byte accesses; K columns of halo
 // on each side are recomputed) times a segment of rows [y0, y1), advanced K steps.  The
 // CTA's K warps form a pipeline over the time levels: warp s computes level s+1 of the
-// wavefront.  Warp 0 brings level-0 rows in with cp.async into a shared-memory ring
-// several rows ahead; each level's output row goes through a double-buffered
-// shared-memory slot to the next warp, one CTA barrier per row; the last warp writes
-// level K to global memory.  Each warp keeps only its own level's two previous rows in
-// registers.  x neighbours come from warp shuffles.  Rows and columns outside the domain
+// wavefront, two rows per iteration.  Warp 0 brings level-0 rows in with cp.async into a
+// shared-memory ring three row pairs ahead; each level's output pair goes through a
+// double-buffered shared-memory slot to the next warp, one CTA barrier per pair; the last
+// warp writes level K to global memory.  Each warp keeps its own level's rows in four
+// register buffers (the two previous rows and the arriving pair) whose roles rotate, so no
+// row is copied.  x neighbours come from warp shuffles.  Rows and columns outside the domain
 // are loaded as ghost images (periodic wrap or the even mirror extension), which the
 // uniform stencil keeps consistent, so no boundary logic is needed inside the pipeline.
 // The arithmetic is the packed form of seird_cell / seird_cell_dev, bit-identical to the
