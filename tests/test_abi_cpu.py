@@ -48,6 +48,25 @@ def test_binding_export_list_matches_header(lib):
     assert set(L.EXPORTS) <= set(_declared_functions())
 
 
+def test_release_library_refuses_the_debug_calls(lib):
+    """Index checks exist only in the debug build; the release library says so without
+    touching the device."""
+    assert lib.sslbm_debug_bounds(None, None, None, None) == L.SSLBM_ERR_UNSUPPORTED
+    assert lib.sslbm_debug_bounds_probe(5, 3) == L.SSLBM_ERR_UNSUPPORTED
+
+
+def test_checked_library_builds_and_exports_every_symbol():
+    """The index-checked debug build (SSLBM_BOUNDS_CHECK) compiles for sm_103a and exports the
+    same ABI; it is loaded on its own (RTLD_LOCAL), so its symbols do not mix with the
+    release library's."""
+    import ctypes
+    path = sbuild.build(checked=True)
+    assert path.endswith("libsslbm_check.so") and os.path.exists(path)
+    chk = ctypes.CDLL(path)
+    missing = [n for n in _declared_functions() if not hasattr(chk, n)]
+    assert not missing, missing
+
+
 def test_strerror_and_version(lib):
     assert L.sslbm_strerror(0) == "SSLBM_OK"
     assert L.sslbm_strerror(-2) == "SSLBM_ERR_UNSTABLE"
