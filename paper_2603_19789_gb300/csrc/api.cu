@@ -2,8 +2,9 @@
 //
 // Host side only: parameter validation (Eq. diffusivity for d -> tau, the von Neumann
 // bound 1/2 <= tau <= 5/4, the optional nonnegativity condition), carving of the
-// caller's workspace, stream-ordered dispatch of the kernels and status reporting.
-// No device memory is allocated here; the caller provides it.
+// caller's workspace, stream-ordered dispatch of the kernels and status reporting, the
+// checkpoint format (header plus the stored planes) and the collection of the debug
+// build's index-check records.  No device memory is allocated here; the caller provides it.
 #include <cmath>
 #include <cstdint>
 #include <cstdarg>
