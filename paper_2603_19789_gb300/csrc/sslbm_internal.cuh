@@ -73,8 +73,12 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 // Force of infection times dt, beta S I / N_c dt (Eq. sources).  The quotient is taken
 // against max(N_c, smallest normal): for nonnegative states N_c = 0 forces S = I = 0, so
 // the force is 0 there -- the reading used for the case the paper leaves open -- without
-// a branch.  FP32 multiplies by the hardware reciprocal (rcp.approx, <= 1 ulp); FP64
-// divides with the IEEE quotient.
+// a branch.  FP32 multiplies by the hardware reciprocal (rcp.approx, <= 1 ulp).  FP64, whose
+// arithmetic rate bounds every FP64 kernel here, refines a float reciprocal seed by two
+// Newton-Raphson steps (relative error ~1e-7, then ~1e-14, then below the double rounding)
+// and corrects the quotient with its exact FMA remainder (Markstein, IBM J. Res. Dev. 34,
+// 1990): within one ulp of the IEEE quotient, and equal to it except near ties.  Divisors
+// outside the float seed's range take the IEEE division.
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -84,7 +88,13 @@ __device__ __forceinline__ float force_quot(float num, float Nc) {
   return __fmul_rn(num, rcp_approx(fmaxf(Nc, 1.17549435e-38f)));
 }
 __device__ __forceinline__ double force_quot(double num, double Nc) {
-  return __ddiv_rn(num, fmax(Nc, 2.2250738585072014e-308));
+  const double d = fmax(Nc, 2.2250738585072014e-308);
+  if (!(d > 1e-30 && d < 1e30)) return __ddiv_rn(num, d);
+  double r = (double)rcp_approx(__double2float_rn(d));
+  r = __fma_rn(r, __fma_rn(-d, r, 1.0), r);
+  r = __fma_rn(r, __fma_rn(-d, r, 1.0), r);
+  const double q = __dmul_rn(num, r);
+  return __fma_rn(r, __fma_rn(-d, q, num), q);
 }
 
 template <typename T>
