@@ -371,6 +371,19 @@ int sslbm_ensemble_autotune(sslbm_ensemble* e, int trial_blocks, int* depth, int
 
 int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e);
 
+/* Checkpoint / resume of an ensemble, as sslbm_checkpoint_* for one grid: the stored FP32
+ * planes of every scenario (sigma = s_ref - S under FP32_DEV, as stored) and the step
+ * counter, so that a resumed run gives the bits of the uninterrupted one.  Layout: a 64-byte
+ * header (magic "SSLE", version, n, precision, steps), then (nx, ny) of every scenario as
+ * two int64, padded to a multiple of 128 bytes, then per scenario its five planes of ny*nx
+ * floats, row-major.  Scenario parameters and tiling are the handle's own and not saved.
+ * A load checks magic, version, the scenario count, the precision and every grid size before
+ * it copies anything (SSLBM_ERR_BAD_ARG otherwise).  Save synchronises the stream; a load
+ * from the host consumes its source before returning, one from the device is stream-ordered. */
+int sslbm_ensemble_checkpoint_bytes(const sslbm_ensemble* e, size_t* bytes);
+int sslbm_ensemble_checkpoint_save(sslbm_ensemble* e, void* dst, size_t bytes, int dst_on_device);
+int sslbm_ensemble_checkpoint_load(sslbm_ensemble* e, const void* src, size_t bytes, int src_on_device);
+
 /* ---- fourth-order finite-difference reference (Sec. III) ----------------------------------
  * The paper's accuracy reference: classical RK4 in time with the fourth-order centred
  * Laplacian L4 u = sum over axes (-u[-2] + 16 u[-1] - 30 u[0] + 16 u[+1] - u[+2]) / (12 dx^2),

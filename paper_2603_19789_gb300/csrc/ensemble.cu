@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -649,5 +650,131 @@ int sslbm_ensemble_autotune(sslbm_ensemble* e, int trial_blocks, int* depth_out,
 }
 
 int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e) { return e ? e->steps : -1; }
+
+}  // extern "C"
+
+namespace {
+constexpr uint32_t kEnsCkptMagic = 0x454C5353u;  // the bytes "SSLE"
+constexpr uint32_t kEnsCkptVersion = 1;
+struct EnsCkptHeader {
+  uint32_t magic, version;
+  int32_t n, precision;
+  int64_t steps;
+  int64_t reserved[5];
+};
+static_assert(sizeof(EnsCkptHeader) == 64, "ensemble checkpoint header");
+
+// header, then (nx, ny) of every scenario, then the planes from this offset
+size_t ens_ckpt_data_offset(int n) { return (sizeof(EnsCkptHeader) + (size_t)n * 16 + 127) / 128 * 128; }
+
+size_t ens_ckpt_bytes(const sslbm_ensemble* e) {
+  size_t b = ens_ckpt_data_offset(e->n);
+  for (int i = 0; i < e->n; ++i) b += (size_t)5 * e->sc[i].nx * e->sc[i].ny * sizeof(float);
+  return b;
+}
+}  // namespace
+
+extern "C" {
+
+int sslbm_ensemble_checkpoint_bytes(const sslbm_ensemble* e, size_t* bytes) {
+  if (!e || !bytes) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  *bytes = ens_ckpt_bytes(e);
+  return SSLBM_OK;
+}
+
+int sslbm_ensemble_checkpoint_save(sslbm_ensemble* e, void* dst, size_t bytes, int dst_on_device) {
+  if (!e || !dst) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  const size_t need = ens_ckpt_bytes(e);
+  if (bytes < need) return err(SSLBM_ERR_BAD_ARG, "checkpoint buffer of %zu bytes < %zu", bytes, need);
+  DevGuard dg(e->device);
+  const size_t data = ens_ckpt_data_offset(e->n);
+  std::vector<unsigned char> head(data, 0);
+  EnsCkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  hd.magic = kEnsCkptMagic;
+  hd.version = kEnsCkptVersion;
+  hd.n = e->n;
+  hd.precision = e->precision;
+  hd.steps = e->steps;
+  std::memcpy(head.data(), &hd, sizeof(hd));
+  for (int i = 0; i < e->n; ++i) {
+    const int64_t dims[2] = {e->sc[i].nx, e->sc[i].ny};
+    std::memcpy(head.data() + sizeof(hd) + (size_t)i * 16, dims, 16);
+  }
+  cudaError_t ce;
+  if (dst_on_device) {
+    ce = cudaMemcpyAsync(dst, head.data(), data, cudaMemcpyHostToDevice, e->stream);
+    if (ce != cudaSuccess) return cuda_err(ce, "cudaMemcpyAsync(checkpoint header)");
+  } else {
+    std::memcpy(dst, head.data(), data);
+  }
+  char* d = static_cast<char*>(dst) + data;
+  for (int i = 0; i < e->n; ++i) {
+    const GridView g = e->gv(i);
+    const size_t row = (size_t)g.nx * sizeof(float);
+    for (int c = 0; c < 5; ++c, d += row * (size_t)g.ny) {
+      ce = cudaMemcpy2DAsync(d, row, e->plane(e->cur, i, c), (size_t)g.pitch * sizeof(float), row, (size_t)g.ny,
+                             dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, e->stream);
+      if (ce != cudaSuccess) return cuda_err(ce, "cudaMemcpy2DAsync(checkpoint save)");
+    }
+  }
+  ce = cudaStreamSynchronize(e->stream);
+  if (ce != cudaSuccess) return cuda_err(ce, "cudaStreamSynchronize(checkpoint save)");
+  return SSLBM_OK;
+}
+
+int sslbm_ensemble_checkpoint_load(sslbm_ensemble* e, const void* src, size_t bytes, int src_on_device) {
+  if (!e || !src) return err(SSLBM_ERR_BAD_ARG, "NULL argument");
+  const size_t data = ens_ckpt_data_offset(e->n);
+  if (bytes < sizeof(EnsCkptHeader)) return err(SSLBM_ERR_BAD_ARG, "checkpoint of %zu bytes has no header", bytes);
+  DevGuard dg(e->device);
+  EnsCkptHeader hd;
+  cudaError_t ce;
+  if (src_on_device) {
+    ce = cudaMemcpyAsync(&hd, src, sizeof(hd), cudaMemcpyDeviceToHost, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    if (ce != cudaSuccess) return cuda_err(ce, "checkpoint header");
+  } else {
+    std::memcpy(&hd, src, sizeof(hd));
+  }
+  if (hd.magic != kEnsCkptMagic || hd.version != kEnsCkptVersion)
+    return err(SSLBM_ERR_BAD_ARG, "not an ensemble checkpoint of this format (magic %08x, version %u)", hd.magic,
+               hd.version);
+  if (hd.n != e->n || hd.precision != e->precision)
+    return err(SSLBM_ERR_BAD_ARG, "checkpoint of %d scenarios (precision %d) for an ensemble of %d (precision %d)", hd.n,
+               hd.precision, e->n, e->precision);
+  if (hd.steps < 0) return err(SSLBM_ERR_BAD_ARG, "negative step counter");
+  const size_t need = ens_ckpt_bytes(e);
+  if (bytes < need) return err(SSLBM_ERR_BAD_ARG, "checkpoint of %zu bytes < %zu", bytes, need);
+  std::vector<int64_t> dims((size_t)2 * e->n);
+  const char* tab = static_cast<const char*>(src) + sizeof(hd);
+  if (src_on_device) {
+    ce = cudaMemcpyAsync(dims.data(), tab, dims.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    if (ce != cudaSuccess) return cuda_err(ce, "checkpoint scenario table");
+  } else {
+    std::memcpy(dims.data(), tab, dims.size() * sizeof(int64_t));
+  }
+  for (int i = 0; i < e->n; ++i)
+    if (dims[2 * i] != e->sc[i].nx || dims[2 * i + 1] != e->sc[i].ny)
+      return err(SSLBM_ERR_BAD_ARG, "scenario %d: checkpoint grid %lld x %lld, ensemble grid %lld x %lld", i,
+                 (long long)dims[2 * i], (long long)dims[2 * i + 1], (long long)e->sc[i].nx, (long long)e->sc[i].ny);
+  const char* s = static_cast<const char*>(src) + data;
+  for (int i = 0; i < e->n; ++i) {
+    const GridView g = e->gv(i);
+    const size_t row = (size_t)g.nx * sizeof(float);
+    for (int c = 0; c < 5; ++c, s += row * (size_t)g.ny) {
+      ce = cudaMemcpy2DAsync(e->plane(e->cur, i, c), (size_t)g.pitch * sizeof(float), s, row, row, (size_t)g.ny,
+                             src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, e->stream);
+      if (ce != cudaSuccess) return cuda_err(ce, "cudaMemcpy2DAsync(checkpoint load)");
+    }
+  }
+  if (!src_on_device) {
+    ce = cudaStreamSynchronize(e->stream);
+    if (ce != cudaSuccess) return cuda_err(ce, "cudaStreamSynchronize(checkpoint load)");
+  }
+  e->steps = hd.steps;
+  return SSLBM_OK;
+}
 
 }  // extern "C"

@@ -47,7 +47,8 @@ EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspa
            "sslbm_ensemble_set_tiling", "sslbm_ensemble_get_tiling",
            "sslbm_ensemble_set_wait_limit", "sslbm_ensemble_write", "sslbm_ensemble_read",
            "sslbm_ensemble_run", "sslbm_ensemble_diagnostics", "sslbm_ensemble_autotune",
-           "sslbm_ensemble_steps_done", "sslbm_fno_workspace_bytes", "sslbm_fno_create",
+           "sslbm_ensemble_steps_done", "sslbm_ensemble_checkpoint_bytes", "sslbm_ensemble_checkpoint_save",
+           "sslbm_ensemble_checkpoint_load", "sslbm_fno_workspace_bytes", "sslbm_fno_create",
            "sslbm_fno_destroy", "sslbm_fno_num_params", "sslbm_fno_set_params",
            "sslbm_fno_get_params", "sslbm_fno_get_grads", "sslbm_fno_make_input",
            "sslbm_fno_forward", "sslbm_fno_backward", "sslbm_fno_set_adam", "sslbm_fno_set_loss_weights",
@@ -154,6 +155,9 @@ def load(path: str = LIB_PATH):
             "sslbm_ensemble_autotune": (i32, [_vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                               ctypes.POINTER(ctypes.c_double)]),
             "sslbm_ensemble_steps_done": (i64, [_vp]),
+            "sslbm_ensemble_checkpoint_bytes": (i32, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+            "sslbm_ensemble_checkpoint_save": (i32, [_vp, _vp, ctypes.c_size_t, i32]),
+            "sslbm_ensemble_checkpoint_load": (i32, [_vp, _vp, ctypes.c_size_t, i32]),
             "sslbm_fno_workspace_bytes": (i32, [ctypes.POINTER(FnoConfig), ctypes.POINTER(ctypes.c_size_t)]),
             "sslbm_fno_create": (i32, [ctypes.POINTER(FnoConfig), _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
             "sslbm_fno_destroy": (None, [_vp]),
@@ -562,6 +566,23 @@ def sslbm_ensemble_steps_done(e):
     return int(load().sslbm_ensemble_steps_done(e))
 
 
+def sslbm_ensemble_checkpoint_bytes(e) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().sslbm_ensemble_checkpoint_bytes(e, ctypes.byref(n)), "sslbm_ensemble_checkpoint_bytes")
+    return int(n.value)
+
+
+def sslbm_ensemble_checkpoint_save(e, dst):
+    ptr, dev, nbytes = _raw(dst)
+    _check(load().sslbm_ensemble_checkpoint_save(e, _vp(ptr), nbytes, dev), "sslbm_ensemble_checkpoint_save")
+    return dst
+
+
+def sslbm_ensemble_checkpoint_load(e, src):
+    ptr, dev, nbytes = _raw(src)
+    _check(load().sslbm_ensemble_checkpoint_load(e, _vp(ptr), nbytes, dev), "sslbm_ensemble_checkpoint_load")
+
+
 # ---------------------------------------------------------------------------
 # fourth-order finite-difference reference
 # ---------------------------------------------------------------------------
@@ -697,6 +718,20 @@ class Ensemble:
 
     def get_tiling(self):
         return sslbm_ensemble_get_tiling(self.e)
+
+    def checkpoint(self, on_device=False):
+        """Every scenario's stored state and the step counter (host uint8 array, or a device
+        tensor with on_device=True)."""
+        n = sslbm_ensemble_checkpoint_bytes(self.e)
+        if on_device:
+            import torch
+            buf = torch.empty(n, dtype=torch.uint8, device=self.device)
+        else:
+            buf = np.empty(n, dtype=np.uint8)
+        return sslbm_ensemble_checkpoint_save(self.e, buf)
+
+    def restore(self, buf):
+        sslbm_ensemble_checkpoint_load(self.e, buf)
 
     def set_wait_limit(self, spin_limit, stall_item=-1):
         sslbm_ensemble_set_wait_limit(self.e, spin_limit, stall_item)

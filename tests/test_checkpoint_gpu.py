@@ -1,12 +1,14 @@
-"""Checkpoint and resume (sslbm_checkpoint_bytes / _save / _load).
+"""Checkpoint and resume (sslbm_checkpoint_bytes / _save / _load, and the ensemble's
+sslbm_ensemble_checkpoint_*).
 
 A run resumed from a checkpoint gives the bits of the uninterrupted run, for every
 precision (the deviation storage of S and the Kahan compensations included), for BGK
 populations, for the other lattices, and through host and device buffers.  The
 read/write route cannot promise that (FP32_DEV reads S rebuilt from the deviation,
 FP32_KAHAN the compensated value, a BGK write sets equilibrium populations), which is
-what the checkpoint's stored planes are for.  Checkpoints of another configuration, short
-buffers and damaged headers are rejected before anything is copied.
+what the checkpoint's stored planes are for.  Ensembles resume bit for bit as well, in FP32
+and with deviation storage.  Checkpoints of another configuration, short buffers and damaged
+headers are rejected before anything is copied.
 """
 import numpy as np
 import pytest
@@ -147,5 +149,74 @@ def test_mismatched_or_damaged_checkpoints_are_rejected():
     b.restore(ck)
     assert b.steps_done() == 3
     assert _same_bits(b.read(), a.read())
+    a.close()
+    b.close()
+
+
+ENS_SIZES = [(64, 64), (132, 40), (12, 300), (4, 7)]
+
+
+def _ens_specs():
+    out = []
+    for i, (nx, ny) in enumerate(ENS_SIZES):
+        r = inputs.rates_from_sigma_mu(0.3 + 0.05 * i, 0.2, 0.1, 0.01)
+        out.append(dict(nx=nx, ny=ny, rates=r.as_tuple(), d=(0.03, 0.03, 0.02, 0.03, 0.0)))
+    return out
+
+
+def _ensemble(specs, precision=L.FP32):
+    e = L.Ensemble(specs, precision=precision)
+    e.set_tiling(4, 17)
+    return e
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV])
+def test_ensemble_resume_gives_the_bits_of_the_uninterrupted_run(precision, on_device):
+    specs = _ens_specs()
+    a = _ensemble(specs, precision)
+    for i, sp in enumerate(specs):
+        a.write(i, inputs.epidemic_state(sp["nx"], sp["ny"], 50 + i))
+    a.run(9)
+    ck = a.checkpoint(on_device=on_device)
+    assert len(ck) == L.sslbm_ensemble_checkpoint_bytes(a.e)
+    a.run(11)
+    refs = [a.read(i) for i in range(len(specs))]
+    a.close()
+    b = _ensemble(specs, precision)
+    b.restore(ck)
+    assert L.sslbm_ensemble_steps_done(b.e) == 9
+    b.run(11)
+    assert L.sslbm_ensemble_steps_done(b.e) == 20
+    for i in range(len(specs)):
+        assert _same_bits(b.read(i), refs[i]), i
+    b.close()
+
+
+def test_ensemble_checkpoint_mismatches_are_rejected():
+    specs = _ens_specs()
+    a = _ensemble(specs)
+    for i, sp in enumerate(specs):
+        a.write(i, inputs.epidemic_state(sp["nx"], sp["ny"], 60 + i))
+    a.run(3)
+    ck = a.checkpoint()
+    others = [_ensemble(specs[:-1]), _ensemble(specs, L.FP32_DEV), _ensemble(specs[:-1] + [dict(specs[-1], nx=8)])]
+    for o in others:
+        with pytest.raises(L.SslbmError) as ei:
+            o.restore(ck)
+        assert ei.value.status == L.SSLBM_ERR_BAD_ARG
+        assert L.sslbm_ensemble_steps_done(o.e) == 0
+        o.close()
+    b = _ensemble(specs)
+    bad = ck.copy()
+    bad[0] ^= 0xFF  # magic
+    for d in (ck[:-1], ck[:32], bad):
+        with pytest.raises(L.SslbmError) as ei:
+            b.restore(np.ascontiguousarray(d))
+        assert ei.value.status == L.SSLBM_ERR_BAD_ARG
+    b.restore(ck)
+    assert L.sslbm_ensemble_steps_done(b.e) == 3
+    for i in range(len(specs)):
+        assert _same_bits(b.read(i), a.read(i)), i
     a.close()
     b.close()
