@@ -218,7 +218,8 @@ int64_t sslbm_steps_done(const sslbm_handle* h, int scheme);
 
 /* ---- checkpoint / resume ------------------------------------------------------------- */
 
-/* A checkpoint is the solver's state exactly as stored, so that a run resumed from it
+/* Not part of the paper's method (it has no restart); a facility of this library.
+ * A checkpoint is the solver's state exactly as stored, so that a run resumed from it
  * gives the bits of the uninterrupted run.  sslbm_read / sslbm_write cannot do that for
  * every configuration: FP32_DEV returns S rebuilt from the stored deviation, FP32_KAHAN
  * the compensated value, and a BGK write sets equilibrium populations.  Layout (a flat
@@ -232,7 +233,8 @@ int64_t sslbm_steps_done(const sslbm_handle* h, int scheme);
 
 /* ---- debug build -------------------------------------------------------------------- */
 
-/* Compiled with SSLBM_BOUNDS_CHECK (libsslbm_check.so, built by build.py --checked), the
+/* Not part of the paper's method; a checking facility of this library.
+ * Compiled with SSLBM_BOUNDS_CHECK (libsslbm_check.so, built by build.py --checked), the
  * hot-path kernels -- the fused pipeline tile of sslbm_step and the ensemble, the one-step
  * kernel, the BGK step and the diagnostics -- test the row and column indices of their
  * global loads and stores against the grid before each access, skip an access whose index
@@ -371,7 +373,8 @@ int sslbm_ensemble_autotune(sslbm_ensemble* e, int trial_blocks, int* depth, int
 
 int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e);
 
-/* Checkpoint / resume of an ensemble, as sslbm_checkpoint_* for one grid: the stored FP32
+/* Checkpoint / resume of an ensemble (not part of the paper's method), as sslbm_checkpoint_*
+ * for one grid: the stored FP32
  * planes of every scenario (sigma = s_ref - S under FP32_DEV, as stored) and the step
  * counter, so that a resumed run gives the bits of the uninterrupted one.  Layout: a 64-byte
  * header (magic "SSLE", version, n, precision, steps), then (nx, ny) of every scenario as
