@@ -365,7 +365,10 @@ def main():
                          "kernel": f"pipe_kernel<fp32, K={depth}>" if depth > 1 else "step1_kernel<fp32>",
                          "bytes_per_launch": BYTES_PER_CELL_FP32 * cells,
                          "launch_ms": launch_ms,
-                         "cell_updates_per_launch": cells * depth,
+                         # the lattice steps of a bench step spread over its passes (depths differ
+                         # by at most one), so a launch averages cells * steps / passes updates
+                         "cell_updates_per_launch": cells * LATTICE_STEPS_PER_STEP
+                                                    / math.ceil(LATTICE_STEPS_PER_STEP / depth),
                          # what one-step kernels would have to move for the same cell-steps: above
                          # the HBM peak because the K steps of a launch share one pass over HBM
                          "per_step_equivalent": {

@@ -224,8 +224,8 @@ int64_t sslbm_steps_done(const sslbm_handle* h, int scheme);
  * every configuration: FP32_DEV returns S rebuilt from the stored deviation, FP32_KAHAN
  * the compensated value, and a BGK write sets equilibrium populations.  Layout (a flat
  * byte buffer, host or device, owned by the caller): a 128-byte header (magic "SSLC",
- * version, nx, ny, precision, lattice, bc, schemes, the two step counters, the plane
- * counts and the element size), then every stored plane in the solver's precision, each
+ * version 2, nx, ny, precision, lattice, bc, schemes, the two step counters, the plane
+ * counts, the element size and s_ref), then every stored plane in the solver's precision, each
  * ny*nx values row-major: the SSLBM planes (5, or 10 with the Kahan compensations) when
  * the handle holds that scheme, then the 21 BGK planes (20 populations, D) when it holds
  * BGK.  Parameters, blocking and the diffusivity scale fields are the handle's own and
@@ -258,7 +258,8 @@ int sslbm_checkpoint_bytes(const sslbm_handle* h, size_t* bytes);
 int sslbm_checkpoint_save(sslbm_handle* h, void* dst, size_t bytes, int dst_on_device);
 
 /* Restore state and step counters from a checkpoint made by a handle of the same grid
- * (nx, ny, precision, lattice, bc, schemes).  A buffer that is too short, has another
+ * (nx, ny, precision, lattice, bc, schemes; under FP32_DEV also the same s_ref, since the
+ * stored plane is the deviation s_ref - S).  A buffer that is too short, has another
  * magic or version, or was saved by a different configuration is rejected with
  * SSLBM_ERR_BAD_ARG before anything is copied.  A host source is consumed before the call
  * returns; a device source is read in stream order. */
@@ -284,9 +285,14 @@ int sslbm_diagnostics(sslbm_handle* h, int scheme, double* totals, double* peak_
  * stream: a cudaStream_t (NULL = legacy default stream); the call synchronises it.
  * Limit: ny <= 16384 rows (the scratch is a built-in 768 KiB device array, one slot
  * per row); larger ny returns SSLBM_ERR_BAD_ARG.  No cudaMalloc, cudaFree or
- * allocating library routine is called.  The first call on each device looks up the
- * array's device address (with that device current) and should come before any stream
- * capture.  All calls on a device share the array and it keeps the last call's
+ * allocating library routine is called.  The array itself is device memory of the
+ * library's image: CUDA reserves it when it loads this code on a device, which under
+ * CUDA's default lazy module loading happens at the first call on that device -- so that
+ * first call does claim 768 KiB in the caller's context.  A caller that must not see even
+ * that make the first call at set-up, while allocation is still allowed, or runs with
+ * CUDA_MODULE_LOADING=EAGER (the reservation then happens when the context is created).
+ * The first call on each device also looks up the array's device address (with that
+ * device current) and should come before any stream capture.  All calls on a device share the array and it keeps the last call's
  * partial sums; calls that overlap on the GPU race on it, so order them on one stream.
  * Returns SSLBM_ERR_NONFINITE if a total is NaN or Inf (results still written). */
 int sslbm_diagnostics_noalloc(const void* fields, int dtype, int64_t nx, int64_t ny,
@@ -377,11 +383,12 @@ int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e);
  * for one grid: the stored FP32
  * planes of every scenario (sigma = s_ref - S under FP32_DEV, as stored) and the step
  * counter, so that a resumed run gives the bits of the uninterrupted one.  Layout: a 64-byte
- * header (magic "SSLE", version, n, precision, steps), then (nx, ny) of every scenario as
- * two int64, padded to a multiple of 128 bytes, then per scenario its five planes of ny*nx
- * floats, row-major.  Scenario parameters and tiling are the handle's own and not saved.
- * A load checks magic, version, the scenario count, the precision and every grid size before
- * it copies anything (SSLBM_ERR_BAD_ARG otherwise).  Save synchronises the stream; a load
+ * header (magic "SSLE", version 2, n, precision, steps), then (nx, ny, s_ref) of every
+ * scenario as two int64 and a double, padded to a multiple of 128 bytes, then per scenario
+ * its five planes of ny*nx floats, row-major.  Other scenario parameters and the tiling are
+ * the handle's own and not saved.  A load checks magic, version, the scenario count, the
+ * precision, every grid size and, under FP32_DEV, every s_ref before it copies anything
+ * (SSLBM_ERR_BAD_ARG otherwise).  Save synchronises the stream; a load
  * from the host consumes its source before returning, one from the device is stream-ordered. */
 int sslbm_ensemble_checkpoint_bytes(const sslbm_ensemble* e, size_t* bytes);
 int sslbm_ensemble_checkpoint_save(sslbm_ensemble* e, void* dst, size_t bytes, int dst_on_device);
@@ -482,15 +489,17 @@ int sslbm_fno_set_adam(sslbm_fno* f, float beta1, float beta2, float eps, float 
 int sslbm_fno_set_loss_weights(sslbm_fno* f, float mass_weight, float neg_weight);
 /* Bound on each wait of the surrogate's tensor-core products for their MMAs (polls, default
  * 2^24; 0 restores it), and a fault-injection hook for tests: with stall != 0 the products
- * withhold their completion signal, so every wait runs out, the products write NaN and
- * sslbm_fno_train_step returns SSLBM_ERR_TIMEOUT instead of hanging.  The paper has no
- * counterpart.  After a timeout, parameters updated from NaN gradients are NaN. */
+ * issue neither their MMAs nor the completion signal, so every wait runs out with no
+ * tensor-core work in flight, the products write NaN and sslbm_fno_train_step returns
+ * SSLBM_ERR_TIMEOUT instead of hanging.  The paper has no counterpart.  A product whose
+ * wait runs out drains its MMAs (one more bounded wait) before it frees its tensor memory. */
 int sslbm_fno_set_wait_limit(sslbm_fno* f, long long polls, int stall);
 /* One training step on the loss of sslbm_fno_set_loss_weights: forward, loss, backward,
  * Adam with learning rate lr.  y_scratch and dy_scratch are [batch][5][n][n] device
- * buffers.  loss (host, may be NULL) receives mse_w before the update; a non-NULL loss
- * synchronises, and then returns SSLBM_ERR_TIMEOUT if a tensor-core product of the step
- * gave up waiting for its MMAs (bounded wait; the product's tile is then NaN). */
+ * buffers.  loss (host, may be NULL) receives mse_w before the update.  Synchronises the
+ * stream; returns SSLBM_ERR_TIMEOUT if a tensor-core product of this step gave up waiting
+ * for its MMAs (bounded wait; the product's tile is then NaN), in which case the Adam
+ * update is skipped: parameters, moments and the step count stay as they were. */
 int sslbm_fno_train_step(sslbm_fno* f, int batch, const float* x, const float* target,
                          float* y_scratch, float* dy_scratch, float lr, double* loss);
 /* Residual checks of a prediction y against the input state u (both [batch][5][n][n]):

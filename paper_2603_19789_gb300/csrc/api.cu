@@ -567,14 +567,17 @@ int64_t sslbm_steps_done(const sslbm_handle* h, int scheme) {
 
 namespace {
 constexpr uint32_t kCkptMagic = 0x434C5353u;  // the bytes "SSLC"
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 constexpr size_t kCkptData = 128;  // the planes start here
+// s_ref is the reference the FP32_DEV storage holds S against (sigma = s_ref - S): a stored
+// deviation plane means a different S under another reference, so a load compares it.
 struct CkptHeader {
   uint32_t magic, version;
   int64_t nx, ny;
   int32_t precision, lattice, bc, schemes;
   int64_t s_steps, b_steps;
   int32_t s_planes, b_planes, esize, reserved;
+  double s_ref;
 };
 static_assert(sizeof(CkptHeader) <= kCkptData, "checkpoint header");
 
@@ -594,6 +597,7 @@ CkptHeader ckpt_header(const sslbm_handle* h) {
   hd.s_planes = (h->g.schemes & SSLBM_WANT_SSLBM) ? h->L.s_planes : 0;
   hd.b_planes = (h->g.schemes & SSLBM_WANT_BGK) ? kBgkPlanes : 0;
   hd.esize = (int32_t)h->L.esize;
+  hd.s_ref = h->p.s_ref;
   return hd;
 }
 
@@ -710,6 +714,10 @@ int sslbm_checkpoint_load(sslbm_handle* h, const void* src, size_t bytes, int sr
                 "this %lld x %lld solver (precision %d, lattice %d, bc %d, schemes %d)",
                 (long long)got.nx, (long long)got.ny, got.precision, got.lattice, got.bc, got.schemes,
                 (long long)own.nx, (long long)own.ny, own.precision, own.lattice, own.bc, own.schemes);
+  if (own.precision == SSLBM_FP32_DEV && (own.s_planes > 0) && got.s_ref != own.s_ref)
+    return fail(SSLBM_ERR_BAD_ARG,
+                "checkpoint stores S as a deviation from s_ref = %.17g, this solver's s_ref is %.17g", got.s_ref,
+                own.s_ref);
   if (got.s_steps < 0 || got.b_steps < 0) return fail(SSLBM_ERR_BAD_ARG, "negative step counters");
   const size_t need = ckpt_bytes(own);
   if (bytes < need) return fail(SSLBM_ERR_BAD_ARG, "checkpoint of %zu bytes < %zu", bytes, need);

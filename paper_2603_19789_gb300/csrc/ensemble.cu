@@ -655,7 +655,7 @@ int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e) { return e ? e->steps
 
 namespace {
 constexpr uint32_t kEnsCkptMagic = 0x454C5353u;  // the bytes "SSLE"
-constexpr uint32_t kEnsCkptVersion = 1;
+constexpr uint32_t kEnsCkptVersion = 2;
 struct EnsCkptHeader {
   uint32_t magic, version;
   int32_t n, precision;
@@ -664,8 +664,12 @@ struct EnsCkptHeader {
 };
 static_assert(sizeof(EnsCkptHeader) == 64, "ensemble checkpoint header");
 
-// header, then (nx, ny) of every scenario, then the planes from this offset
-size_t ens_ckpt_data_offset(int n) { return (sizeof(EnsCkptHeader) + (size_t)n * 16 + 127) / 128 * 128; }
+// header, then (nx, ny, s_ref) of every scenario (two int64 and a double: s_ref is the
+// reference of the FP32_DEV storage, sigma = s_ref - S), then the planes from this offset
+constexpr size_t kEnsCkptEntry = 24;
+size_t ens_ckpt_data_offset(int n) {
+  return (sizeof(EnsCkptHeader) + (size_t)n * kEnsCkptEntry + 127) / 128 * 128;
+}
 
 size_t ens_ckpt_bytes(const sslbm_ensemble* e) {
   size_t b = ens_ckpt_data_offset(e->n);
@@ -699,7 +703,10 @@ int sslbm_ensemble_checkpoint_save(sslbm_ensemble* e, void* dst, size_t bytes, i
   std::memcpy(head.data(), &hd, sizeof(hd));
   for (int i = 0; i < e->n; ++i) {
     const int64_t dims[2] = {e->sc[i].nx, e->sc[i].ny};
-    std::memcpy(head.data() + sizeof(hd) + (size_t)i * 16, dims, 16);
+    const double sref = e->sc[i].s_ref;
+    unsigned char* ent = head.data() + sizeof(hd) + (size_t)i * kEnsCkptEntry;
+    std::memcpy(ent, dims, 16);
+    std::memcpy(ent + 16, &sref, 8);
   }
   cudaError_t ce;
   if (dst_on_device) {
@@ -746,19 +753,28 @@ int sslbm_ensemble_checkpoint_load(sslbm_ensemble* e, const void* src, size_t by
   if (hd.steps < 0) return err(SSLBM_ERR_BAD_ARG, "negative step counter");
   const size_t need = ens_ckpt_bytes(e);
   if (bytes < need) return err(SSLBM_ERR_BAD_ARG, "checkpoint of %zu bytes < %zu", bytes, need);
-  std::vector<int64_t> dims((size_t)2 * e->n);
-  const char* tab = static_cast<const char*>(src) + sizeof(hd);
+  std::vector<unsigned char> tab((size_t)e->n * kEnsCkptEntry);
+  const char* tsrc = static_cast<const char*>(src) + sizeof(hd);
   if (src_on_device) {
-    ce = cudaMemcpyAsync(dims.data(), tab, dims.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, e->stream);
+    ce = cudaMemcpyAsync(tab.data(), tsrc, tab.size(), cudaMemcpyDeviceToHost, e->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
     if (ce != cudaSuccess) return cuda_err(ce, "checkpoint scenario table");
   } else {
-    std::memcpy(dims.data(), tab, dims.size() * sizeof(int64_t));
+    std::memcpy(tab.data(), tsrc, tab.size());
   }
-  for (int i = 0; i < e->n; ++i)
-    if (dims[2 * i] != e->sc[i].nx || dims[2 * i + 1] != e->sc[i].ny)
+  for (int i = 0; i < e->n; ++i) {
+    int64_t dims[2];
+    double sref;
+    std::memcpy(dims, tab.data() + (size_t)i * kEnsCkptEntry, 16);
+    std::memcpy(&sref, tab.data() + (size_t)i * kEnsCkptEntry + 16, 8);
+    if (dims[0] != e->sc[i].nx || dims[1] != e->sc[i].ny)
       return err(SSLBM_ERR_BAD_ARG, "scenario %d: checkpoint grid %lld x %lld, ensemble grid %lld x %lld", i,
-                 (long long)dims[2 * i], (long long)dims[2 * i + 1], (long long)e->sc[i].nx, (long long)e->sc[i].ny);
+                 (long long)dims[0], (long long)dims[1], (long long)e->sc[i].nx, (long long)e->sc[i].ny);
+    if (e->precision == SSLBM_FP32_DEV && sref != e->sc[i].s_ref)
+      return err(SSLBM_ERR_BAD_ARG,
+                 "scenario %d: checkpoint stores S as a deviation from s_ref = %.17g, the ensemble's is %.17g", i,
+                 sref, e->sc[i].s_ref);
+  }
   const char* s = static_cast<const char*>(src) + data;
   for (int i = 0; i < e->n; ++i) {
     const GridView g = e->gv(i);

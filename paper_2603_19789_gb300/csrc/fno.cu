@@ -506,9 +506,13 @@ __global__ void loss_kernel(const float* __restrict__ y, const float* __restrict
 }
 
 // Adam (decoupled weight decay), then refresh the BF16 copy used as GEMM operand
+// Adam; skipped altogether when a tensor-core product of this step timed out (*fault != 0),
+// so NaN gradients never reach the parameters or the moments
 __global__ void adam_kernel(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ mo,
                             float* __restrict__ ve, bf16* __restrict__ th16, int64_t P, float lr,
-                            float b1, float b2, float eps, float wd, float c1, float c2) {
+                            float b1, float b2, float eps, float wd, float c1, float c2,
+                            const unsigned int* __restrict__ fault) {
+  if (*fault) return;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P;
        t += (int64_t)gridDim.x * blockDim.x) {
     const float gr = g[t];
@@ -774,7 +778,7 @@ int make_param_layout(const sslbm_fno_config* c, Layout* L) {
 struct Buffers {
   size_t total;
   size_t theta, theta16, grad, mom, vel, dft, hcat, zcat, zp, p, f32a, f32b, f32p, h1, tt, hat, dg, dd, smax, csum,
-      mask, mscale, loss, res;
+      mask, mscale, loss, res, fault;
 };
 
 size_t rup(size_t v) { return (v + 255) / 256 * 256; }
@@ -807,6 +811,7 @@ void make_buffers(const Layout& L, Buffers* b) {
   b->mscale = take(B * 2 * 4);
   b->loss = take(8);
   b->res = take(B * 3 * 8);
+  b->fault = take(4);  // set by a tensor-core product whose wait ran out
   b->total = o;
 }
 
@@ -865,6 +870,7 @@ int run(const sslbm_fno* f, const GemmArgs& g0, const char* what) {
   if (g.K0 == 0) g.K0 = g.K;
   g.wait_limit = f->gemm_wait_limit;
   g.stall = f->gemm_stall;
+  g.fault = f->at<unsigned int>(f->bu.fault);
   cudaError_t e = sslbm::gemm_bf16(g, f->stream);
   if (e != cudaSuccess) return cuda_err(e, what);
   return SSLBM_OK;
@@ -1342,19 +1348,24 @@ int sslbm_fno_train_step(sslbm_fno* f, int batch, const float* x, const float* t
                                                          f->mass_weight, f->neg_weight, batch);
   CK(cudaGetLastError(), "loss");
   if ((st = backward_impl(f, batch, x, dy_scratch))) return st;
-  f->adam_t += 1;
-  const float c1 = 1.f - powf(f->b1, (float)f->adam_t), c2 = 1.f - powf(f->b2, (float)f->adam_t);
+  const int64_t t_next = f->adam_t + 1;
+  const float c1 = 1.f - powf(f->b1, (float)t_next), c2 = 1.f - powf(f->b2, (float)t_next);
+  unsigned int* fault_word = f->at<unsigned int>(f->bu.fault);
   adam_kernel<<<blocks_for(f->L.nparams), kThreads, 0, f->stream>>>(
       f->theta(), f->grad(), f->at<float>(f->bu.mom), f->at<float>(f->bu.vel), f->theta16(), f->L.nparams, lr,
-      f->b1, f->b2, f->eps, f->wd, c1, c2);
+      f->b1, f->b2, f->eps, f->wd, c1, c2, fault_word);
   CK(cudaGetLastError(), "adam");
-  if (loss) {
-    CK(cudaMemcpyAsync(loss, dl, 8, cudaMemcpyDeviceToHost, f->stream), "loss");
-    CK(cudaStreamSynchronize(f->stream), "sync");
-    unsigned int fault = 0;
-    CK(sslbm::gemm_fault_read_and_clear(&fault, f->stream), "tensor-core product status");
-    if (fault) return err(SSLBM_ERR_TIMEOUT, "a tensor-core product timed out waiting for its MMAs (results are NaN)");
+  // every call reports its own products' status: read the fault word, and clear it if set
+  unsigned int fault = 0;
+  CK(cudaMemcpyAsync(&fault, fault_word, sizeof(fault), cudaMemcpyDeviceToHost, f->stream), "product status");
+  if (loss) CK(cudaMemcpyAsync(loss, dl, 8, cudaMemcpyDeviceToHost, f->stream), "loss");
+  CK(cudaStreamSynchronize(f->stream), "sync");
+  if (fault) {
+    CK(cudaMemsetAsync(fault_word, 0, sizeof(unsigned int), f->stream), "clear product status");
+    return err(SSLBM_ERR_TIMEOUT,
+               "a tensor-core product timed out waiting for its MMAs (results are NaN; the update was skipped)");
   }
+  f->adam_t = t_next;
   return SSLBM_OK;
 }
 
@@ -1398,6 +1409,11 @@ int sslbm_fno_check_project(sslbm_fno* f, int batch, float* y, const float* u, i
     const double su = r[3 * b + 1];
     residuals[2 * b] = su != 0 ? std::fabs(r[3 * b] - su) / std::fabs(su) : std::fabs(r[3 * b]);
     residuals[2 * b + 1] = su != 0 ? r[3 * b + 2] / std::fabs(su) : r[3 * b + 2];
+    // a prediction with a NaN or Inf anywhere fails both checks, whatever the clamp made of it
+    if (!std::isfinite(r[3 * b]) || !std::isfinite(r[3 * b + 2])) {
+      residuals[2 * b] = HUGE_VAL;
+      residuals[2 * b + 1] = HUGE_VAL;
+    }
   }
   return SSLBM_OK;
 }

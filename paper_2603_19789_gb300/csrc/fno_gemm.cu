@@ -16,11 +16,16 @@
 // atomic add.
 //
 // Waits are bounded: if an MMA has not completed after kWaitLimit polls (or the caller's
-// bound; a test hook can also withhold the completion signal), the kernel raises
-// gemm_fault_flag, writes NaN into its tile (so the result cannot pass for a valid one),
-// frees its tensor memory and returns.  The 29 KB of shared memory per CTA keeps at most 7
-// CTAs on an SM, whose 7 x 64 columns fit in the 512 columns of tensor memory, so the
-// allocation never has to wait for another CTA.
+// bound), the kernel raises the caller's fault word, writes NaN into its tile (so the result
+// cannot pass for a valid one) and drains: the issuing thread commits once more to a
+// separate mbarrier, which tracks every MMA it issued, and the CTA waits for that (bounded
+// as well) before it frees its tensor memory.  Only if the drain wait also runs out does
+// the CTA return without freeing, since MMAs may then still write that memory; the fault
+// word stays set.  The test hook (GemmArgs::stall) issues neither the MMAs nor their
+// commits, so every wait for a tile runs out with no tensor-core work in flight and the
+// drain completes at once.  The 29 KB of shared memory per CTA keeps at most 7 CTAs on an
+// SM, whose 7 x 64 columns fit in the 512 columns of tensor memory, so the allocation
+// never has to wait for another CTA.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
@@ -28,8 +33,6 @@
 #include "fno_gemm.cuh"
 
 namespace sslbm {
-
-__device__ unsigned int gemm_fault_flag = 0;
 
 namespace {
 
@@ -132,12 +135,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
 }
 
 __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g) {
-  static_assert(2 * kStageBytes + 32 <= kSmemBytes, "two stages and the barriers fit");
+  static_assert(2 * kStageBytes + 32 <= kSmemBytes, "two stages, the barriers and the tensor-memory slot fit");
   static_assert(4 * 32 * 33 * 4 <= 2 * kStageBytes, "the epilogue's staging fits in the stage buffers");
   __shared__ __align__(1024) unsigned char smem[kSmemBytes];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kStageBytes);  // one per stage
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kStageBytes + 16);
-  __shared__ int s_fault;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kStageBytes);  // one per stage, then the drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kStageBytes + 24);
+  __shared__ int s_fault, s_stuck;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
@@ -147,12 +150,15 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g) {
   const int kend = min(g.K, kbeg + kchunk);
   const bool a_kfast = g.sAk0 == 1, b_kfast = g.sBk0 == 1;
   const uint32_t bar_addr[2] = {smem_u32(bar), smem_u32(bar + 1)};
+  const uint32_t drain_addr = smem_u32(bar + 2);
   const long long limit = g.wait_limit > 0 ? g.wait_limit : kWaitLimit;
 
   if (tid == 0) {
     s_fault = 0;
+    s_stuck = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_addr[0]) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_addr[1]) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(drain_addr) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -196,7 +202,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g) {
     // make the generic-proxy stores visible to the tensor core's async proxy
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !g.stall) {  // the test hook issues nothing, so no wait can succeed
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
       for (int s = 0; s < TK / 16; ++s) {
@@ -209,10 +215,9 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g) {
             "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
             : "memory");
       }
-      if (!g.stall)
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                         bar_addr[st])
-                     : "memory");
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       bar_addr[st])
+                   : "memory");
     }
     any = true;
   }
@@ -224,7 +229,18 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g) {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
   const bool fault = s_fault != 0;
-  if (fault && tid == 0) atomicExch(&gemm_fault_flag, 1u);
+  if (fault) {
+    // drain: a commit tracks every earlier MMA of the thread that issues it, so once this
+    // one arrives no MMA of the CTA can still read shared memory or write tensor memory
+    if (tid == 0) {
+      if (g.fault) atomicExch(g.fault, 1u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       drain_addr)
+                   : "memory");
+      if (!mbar_wait(drain_addr, 0u, limit)) s_stuck = 1;
+    }
+    __syncthreads();
+  }
   // epilogue: thread (warp, lane) holds row 32 warp + lane, columns 32 h .. 32 h + 31 of each
   // half; when C is row-major the warp passes its 32 x 32 block through shared memory (the
   // stage buffers are idle now) so that lanes write consecutive columns
@@ -273,7 +289,9 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g) {
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
+  // after a drain that also ran out, MMAs may still write this tensor memory: it is not
+  // handed back (the fault word is set and the results are NaN)
+  if (warp == 0 && !s_stuck) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
@@ -290,18 +308,6 @@ cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s) {
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
   gemm_tc_kernel<<<grid, 128, 0, s>>>(g);
   return cudaGetLastError();
-}
-
-cudaError_t gemm_fault_read_and_clear(unsigned int* out, cudaStream_t s) {
-  cudaError_t e = cudaMemcpyFromSymbolAsync(out, gemm_fault_flag, sizeof(unsigned int), 0, cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return e;
-  if (*out) {
-    const unsigned int zero = 0;
-    e = cudaMemcpyToSymbolAsync(gemm_fault_flag, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s);
-  }
-  return e;
 }
 
 }  // namespace sslbm

@@ -31,13 +31,10 @@ struct GemmArgs {
   float alpha, beta;
   int atomic;  // add into FP32 C with atomics (split-K); beta is ignored
   long long wait_limit;  // polls per tensor-core wait (0: the default bound, 2^24)
-  int stall;             // test hook: skip the completion signal, so the waits run out
+  int stall;             // test hook: issue no MMA and no completion signal, so the waits run out
+  unsigned int* fault;   // device word set to 1 when a wait runs out (may be NULL)
 };
 
 cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s);
-
-// Whether a product timed out waiting for its tensor-core work since the last call (its
-// tile was then written as NaN); reads the device flag (synchronises s) and clears it.
-cudaError_t gemm_fault_read_and_clear(unsigned int* out, cudaStream_t s);
 
 }  // namespace sslbm

@@ -12,6 +12,10 @@
 // Scratch: one row of 6 doubles per lattice row (5 totals and a maximum) plus one
 // result row, for at most kNoAllocMaxRows lattice rows: (16384 + 1) * 6 * 8 bytes
 // = 768 KiB on every device that loads the library, held until the process exits.
+// The array belongs to this file's device code: CUDA reserves it when it loads that code
+// on a device, which under the default lazy module loading is the first call here (the
+// symbol lookup below), and with CUDA_MODULE_LOADING=EAGER context creation.  A caller
+// that cannot afford even that reservation later makes its first call at set-up.
 // Every call writes each slot it later reads (no accumulation across calls), so nothing
 // has to be cleared between calls; the array keeps the last call's partial sums.
 // All calls on one device share the array: calls that overlap on the GPU (unordered

@@ -150,6 +150,28 @@ def precision_workload(nx: int = 4096, ny: int = 4096, seed: int = DEFAULT_SEED)
                 bc=BC_NOFLUX, steps=50000, name=f"small_seed_{nx}x{ny}_noflux")
 
 
+def paper_test_case(chi: float = 0.10, R0: float = 3.0, side_km: int = 200, seed: int = DEFAULT_SEED,
+                    bc: int = BC_PERIODIC):
+    """The paper's test case (Sec. III) in physical units: a side_km x side_km km^2 domain
+    with dx = 1 km (one cell per km^2) and dt = 0.01 day; total population N = 5e6, so the
+    uniform density is N/A per cell; E = chi N/A + eps(x), S = N/A - E, I = R = D = 0.
+    Rates per day: gamma = 1/5, beta = R0 gamma, alpha = 1/7, phi = 0.3.  Diffusion in
+    km^2/day: d^S = d^E = d^R = 4.35e-2, d^I = 1e-4, d^D = 0.  The paper does not give
+    eps(x); here it is seeded U[-1e-3, 1e-3] chi N/A per cell, and the boundary is periodic
+    unless bc says otherwise."""
+    n = int(side_km)
+    dens = 5e6 / float(n * n)
+    eps = _rng(seed).uniform(-1e-3, 1e-3, (n, n)) * chi * dens
+    st = np.zeros((5, n, n))
+    st[1] = chi * dens + eps
+    st[0] = dens - st[1]
+    gamma = 1.0 / 5.0
+    rates = Rates(R0 * gamma, 1.0 / 7.0, gamma, 0.3)
+    d = (4.35e-2, 4.35e-2, 1e-4, 4.35e-2, 0.0)
+    return dict(state=st, rates=rates, d=d, dx=1.0, dt=0.01, bc=bc, density=dens,
+                name=f"paper_test_case_{n}km_chi{chi:g}_R0{R0:g}")
+
+
 ENSEMBLE_SIZES = (256, 384, 512, 768, 1024)
 
 

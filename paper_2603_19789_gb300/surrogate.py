@@ -213,7 +213,8 @@ def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_th
         any_negative += int((res[:, 1] > 0).sum())
         fail_mass += int((res[:, 0] > threshold).sum())
         fail_neg += int((res[:, 1] > neg_threshold).sum())
-        bad = np.nonzero((res[:, 0] > threshold) | (res[:, 1] > neg_threshold))[0]
+        # written so that a NaN residual (a non-finite prediction) fails the test
+        bad = np.nonzero(~((res[:, 0] <= threshold) & (res[:, 1] <= neg_threshold)))[0]
         if bad.size:
             fallbacks += int(bad.size)
             for i in bad:

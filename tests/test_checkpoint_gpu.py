@@ -29,8 +29,8 @@ def _built():
     L.load()
 
 
-def _solver(nx, ny, precision, schemes=L.WANT_SSLBM, bc=L.BC_NOFLUX, lattice=L.LATTICE_D2Q5):
-    return L.Solver(nx, ny, RATES, d=D, bc=bc, precision=precision, schemes=schemes, lattice=lattice)
+def _solver(nx, ny, precision, schemes=L.WANT_SSLBM, bc=L.BC_NOFLUX, lattice=L.LATTICE_D2Q5, s_ref=1.0):
+    return L.Solver(nx, ny, RATES, d=D, bc=bc, precision=precision, schemes=schemes, lattice=lattice, s_ref=s_ref)
 
 
 def _same_bits(a, b):
@@ -153,6 +153,32 @@ def test_mismatched_or_damaged_checkpoints_are_rejected():
     b.close()
 
 
+def test_deviation_checkpoint_requires_the_same_reference():
+    """Under FP32_DEV the stored S plane is the deviation s_ref - S, so a restore into a solver
+    with another s_ref would shift S by the difference: it is rejected.  Other precisions store
+    S itself, and s_ref does not enter."""
+    nx, ny = 40, 24
+    st = inputs.epidemic_state(nx, ny, 12)
+    for precision, rejected in ((L.FP32_DEV, True), (L.FP32, False)):
+        a = _solver(nx, ny, precision, s_ref=1.0)
+        a.write(st)
+        a.step(2)
+        ck = a.checkpoint()
+        o = _solver(nx, ny, precision, s_ref=1.25)
+        if rejected:
+            with pytest.raises(L.SslbmError) as ei:
+                o.restore(ck)
+            assert ei.value.status == L.SSLBM_ERR_BAD_ARG and o.steps_done() == 0
+        else:
+            o.restore(ck)
+            assert _same_bits(o.read(), a.read())
+        same = _solver(nx, ny, precision, s_ref=1.0)
+        same.restore(ck)
+        assert _same_bits(same.read(), a.read())
+        for s in (a, o, same):
+            s.close()
+
+
 ENS_SIZES = [(64, 64), (132, 40), (12, 300), (4, 7)]
 
 
@@ -201,6 +227,22 @@ def test_ensemble_checkpoint_mismatches_are_rejected():
     a.run(3)
     ck = a.checkpoint()
     others = [_ensemble(specs[:-1]), _ensemble(specs, L.FP32_DEV), _ensemble(specs[:-1] + [dict(specs[-1], nx=8)])]
+    # under FP32_DEV a scenario whose deviation reference differs is rejected too
+    dev = _ensemble(specs, L.FP32_DEV)
+    for i, sp in enumerate(specs):
+        dev.write(i, inputs.epidemic_state(sp["nx"], sp["ny"], 60 + i))
+    dev_ck = dev.checkpoint()
+    moved = _ensemble(specs[:2] + [dict(specs[2], s_ref=1.5)] + specs[3:], L.FP32_DEV)
+    with pytest.raises(L.SslbmError) as ei:
+        moved.restore(dev_ck)
+    assert ei.value.status == L.SSLBM_ERR_BAD_ARG and L.sslbm_ensemble_steps_done(moved.e) == 0
+    moved.close()
+    same = _ensemble(specs, L.FP32_DEV)
+    same.restore(dev_ck)
+    for i in range(len(specs)):
+        assert _same_bits(same.read(i), dev.read(i)), i
+    same.close()
+    dev.close()
     for o in others:
         with pytest.raises(L.SslbmError) as ei:
             o.restore(ck)

@@ -168,24 +168,28 @@ def test_training_steps_reduce_the_loss():
         assert np.abs(v - fno.unflatten(fno.flatten(p32, **cfg), **cfg)[name]).max() > 0, name
 
 
-def test_lost_tensor_core_completion_times_out_instead_of_hanging():
-    """The tensor-core products wait for their MMAs with a bounded poll.  The test hook
-    withholds the completion signal (nothing then arrives on the barrier), so every wait runs
-    out: the step returns SSLBM_ERR_TIMEOUT, and the context stays usable afterwards."""
+@pytest.mark.parametrize("want_loss", [True, False])
+def test_lost_tensor_core_completion_times_out_instead_of_hanging(want_loss):
+    """The tensor-core products wait for their MMAs with a bounded poll.  The test hook issues
+    no MMA and no completion signal (nothing then arrives on the barrier), so every wait runs
+    out: the step returns SSLBM_ERR_TIMEOUT whether or not the loss is read, skips the Adam
+    update (the parameters keep their bits), and the context stays usable afterwards."""
     import torch
     s, p32, x, xo, u, g, cfg = _setup(4, "generic")
     theta = s.get_params()
     target = torch.from_numpy(u).cuda().contiguous()
     s.set_wait_limit(polls=2000, stall=True)
     with pytest.raises(L.SslbmError) as e:
-        s.train_step(x, target, 1e-3)
+        s.train_step(x, target, 1e-3, want_loss=want_loss)
     assert e.value.status == L.SSLBM_ERR_TIMEOUT
+    assert np.array_equal(s.get_params().view(np.uint32), theta.view(np.uint32))
     s.set_wait_limit()  # defaults again
-    s.set_params(theta)  # the timed-out step updated the parameters from NaN gradients
     y = s.forward(x)
     assert torch.isfinite(y).all()
-    loss = s.train_step(x, target, 1e-3)  # the loss is taken before the (NaN-moment) update
-    assert np.isfinite(loss)
+    loss = s.train_step(x, target, 1e-3, want_loss=want_loss)  # the status was cleared
+    assert loss is None or np.isfinite(loss)
+    after = s.get_params()
+    assert np.isfinite(after).all() and not np.array_equal(after, theta)
 
 
 def test_check_project_residuals_and_projection():
@@ -207,6 +211,26 @@ def test_check_project_residuals_and_projection():
     assert out.min() >= 0
     np.testing.assert_allclose(out.astype(np.float64).reshape(B, -1).sum(axis=1),
                                u.astype(np.float64).reshape(B, -1).sum(axis=1), rtol=1e-5)
+
+
+def test_non_finite_prediction_fails_both_checks():
+    """A NaN or Inf anywhere in a prediction (a timed-out tensor-core tile is NaN) gives
+    infinite residuals, so a rollout's test `residual <= threshold` sends that scenario to the
+    SSLBM fallback, although the clamp and the rescale would have turned it into finite values."""
+    import torch
+    cfg, n = _cfg("generic")
+    s = L.Surrogate(n=n, width=cfg["W"], modes=cfg["m"], layers=cfg["L"], hidden=cfg["H"], max_batch=3)
+    g = np.random.default_rng(6)
+    u = g.uniform(0, 1, (3, 5, n, n)).astype(np.float32)
+    y = u.copy()
+    y[0, 2, 5, 7] = np.nan
+    y[1, 0, 1, 1] = np.inf
+    res = s.check_project(torch.from_numpy(y).cuda(), torch.from_numpy(u).cuda())
+    assert np.all(np.isinf(res[:2])), res
+    assert np.all(res[2] <= 1e-6), res
+    threshold = 1e-4
+    bad = ~((res[:, 0] <= threshold) & (res[:, 1] <= 0.0))
+    assert bad.tolist() == [True, True, False]
 
 
 def test_projection_zeroes_outside_the_domain_of_dependence():

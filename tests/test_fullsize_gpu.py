@@ -1,8 +1,9 @@
 """Full-size parity: the 8192 x 8192 no-flux multi-seed workload in the launch
-configuration the benchmark times (FP32, default temporal-blocking depth and segment
-length; FP64 one-step kernel), checked on sampled windows that the oracle computes on
-their domain of dependence, plus bit-identity of the blocked and one-step kernels over
-the whole grid.  And a grid of more than 2^31 cells, to exercise 64-bit indexing."""
+configurations the benchmark times (FP32 with the autotuned depth and segment length, and
+the deep blockings the autotuner picks there; FP32 defaults; FP64 one-step kernel), checked
+on sampled windows that the oracle computes on their domain of dependence, plus
+bit-identity of the blocked and one-step kernels over the whole grid.  And a grid of more
+than 2^31 cells, to exercise 64-bit indexing."""
 import numpy as np
 import pytest
 
@@ -67,6 +68,61 @@ def test_roofline_grid_fp32_bench_config(workload):
     s.step(NSTEPS)
     ref = s.read(dtype=np.float32)
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    s.close()
+
+
+BENCH_STEPS = 100  # lattice steps of one benchmark step
+
+
+def _check_autotuned_like_the_bench(wl, s):
+    """BENCH_STEPS steps in the solver's current blocking (passes of near-equal depth): sampled
+    windows against the oracle, and the whole grid against the one-step kernel bit for bit.
+    Tolerance per value: 2e-5 relative plus 1e-5 of the compartment's largest value on the
+    grid (n u = 100 x 6e-8 bounds the accumulated rounding; a cell far smaller than its
+    neighbours carries their rounding, hence the absolute part, as in the FP32 parity tests)."""
+    s.write(wl["state"])
+    s.step(BENCH_STEPS)
+    got = s.read(dtype=np.float32)
+    g64 = got.astype(np.float64)
+    scale = np.abs(g64).reshape(5, -1).max(axis=1)
+    st = wl["state"]
+    tau = _taus(wl["d"])
+    for x0, y0 in _windows(8192, 8192, 8, 8):
+        want = oracle.sslbm_window(st, x0, y0, 8, 8, tau, wl["rates"].as_tuple(), 1.0, wl["bc"], BENCH_STEPS)
+        part = g64[:, y0:y0 + 8, x0:x0 + 8]
+        for c in range(5):
+            bound = 2e-5 * np.abs(want[c]) + 1e-5 * scale[c]
+            assert (np.abs(part[c] - want[c]) <= bound).all(), (x0, y0, c, np.abs(part[c] - want[c]).max())
+    s.write(wl["state"])
+    s.set_blocking(1)
+    s.step(BENCH_STEPS)
+    ref = s.read(dtype=np.float32)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+def test_roofline_grid_fp32_autotuned_config(workload):
+    """The configuration the benchmark's number comes from: the library's autotuner picks the
+    depth and segment length (the same call and budget as the benchmark), and a benchmark
+    step's 100 lattice steps run as passes of that depth and one less."""
+    wl = workload
+    s = L.Solver(8192, 8192, wl["rates"].as_tuple(), d=wl["d"], bc=wl["bc"], precision=L.FP32)
+    s.write(wl["state"])
+    depth, seg, ms = s.autotune(300.0)
+    print(f"autotuned depth {depth}, seg_rows {seg}, {ms:.3f} ms per lattice step")
+    assert 1 <= depth <= L.MAX_DEPTH
+    _check_autotuned_like_the_bench(wl, s)
+    s.close()
+
+
+@pytest.mark.parametrize("depth,seg_rows", [(8, 1024), (7, 1024), (8, 0)])
+def test_roofline_grid_fp32_deep_blocking(workload, depth, seg_rows):
+    """Depth 8 with 1024-row segments, the choice the autotuner made on the benchmark grid;
+    100 steps at depth 8 are 9 passes of 8 and 4 of 7."""
+    wl = workload
+    s = L.Solver(8192, 8192, wl["rates"].as_tuple(), d=wl["d"], bc=wl["bc"], precision=L.FP32)
+    s.set_blocking(depth, seg_rows)
+    assert s.get_blocking() == (depth, seg_rows)
+    _check_autotuned_like_the_bench(wl, s)
     s.close()
 
 
