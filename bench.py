@@ -463,8 +463,8 @@ def e2e_timing(L, torch, s, state32, stream, world, wl, steps=3, jobs=8, infligh
 
 
 def secondary_timings(L, wl, state64, state32, stream, hbm):
-    """Other variants on the same grid: FP64, deviation-S, Kahan, depth sweep, BGK, D2Q9,
-    two-pass SLBM, varying diffusivity, FD4."""
+    """Other variants on the same grid: FP64, deviation-S, split-S, Kahan, depth sweep, BGK,
+    D2Q9, two-pass SLBM, varying diffusivity, FD4."""
     import torch
     from paper_2603_19789_gb300 import inputs
     out = {}
@@ -501,8 +501,14 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
             out["fp32_depth1_hbm_frac"] = BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm
     g, _ = glups_of(L.FP32_DEV, 48, 4)
     out["fp32_dev_glups"] = g
-    g, _ = glups_of(L.FP32_KAHAN, 20, 2)
+    g, _ = glups_of(L.FP32_SPLIT, 48, 4)
+    out["fp32_split_glups"] = g
+    g, ms = glups_of(L.FP32_SPLIT, 20, 2, depth=1)
+    out["fp32_split_depth1_glups"] = g
+    out["fp32_split_depth1_hbm_frac"] = 48 * cells / (ms * 1e-3) / 1e9 / hbm
+    g, ms = glups_of(L.FP32_KAHAN, 20, 2)
     out["fp32_kahan_glups"] = g
+    out["fp32_kahan_hbm_frac"] = 80 * cells / (ms * 1e-3) / 1e9 / hbm
     g, ms = glups_of(L.FP64, 20, 2)
     out["fp64_glups"] = g
     out["fp64_hbm_frac"] = BYTES_PER_CELL_FP64 * cells / (ms * 1e-3) / 1e9 / hbm

@@ -61,8 +61,14 @@ enum { SSLBM_BC_PERIODIC = 0, SSLBM_BC_NOFLUX = 1 };
  *                S ~ 1 are not rounded away.  Diffusion of sigma is that of S with the
  *                sign flipped (the stencil annihilates the constant s_ref exactly).
  *   FP32_KAHAN : float fields plus one float compensation plane per compartment;
- *                every step's increment is added with compensated (Kahan) summation. */
-enum { SSLBM_FP64 = 0, SSLBM_FP32 = 1, SSLBM_FP32_DEV = 2, SSLBM_FP32_KAHAN = 3 };
+ *                every step's increment is added with compensated (Kahan) summation.
+ *   FP32_SPLIT : float fields; S is stored as a hi/lo pair -- its value plane v and a
+ *                compensation plane c, S = v - c -- so that S keeps about twice FP32's
+ *                precision at every value of S (the deviation storage keeps it only while
+ *                S is near s_ref).  S's laplacian is taken in difference form on v minus
+ *                that of c, and S's increment is added with Kahan summation; E, I, R, D
+ *                are plain FP32.  Six planes: 48 bytes per cell-step. */
+enum { SSLBM_FP64 = 0, SSLBM_FP32 = 1, SSLBM_FP32_DEV = 2, SSLBM_FP32_KAHAN = 3, SSLBM_FP32_SPLIT = 4 };
 enum { SSLBM_SCHEME_SSLBM = 0, SSLBM_SCHEME_BGK = 1 };
 enum { SSLBM_S = 0, SSLBM_E = 1, SSLBM_I = 2, SSLBM_R = 3, SSLBM_D = 4, SSLBM_NCOMP = 5 };
 enum { SSLBM_ALL = -1 }; /* comp argument: all five planes, consecutive */
@@ -89,7 +95,7 @@ typedef struct sslbm_grid {
   double dx, dt;       /* lattice spacing and time step (> 0); lattice units: 1, 1 */
   int32_t bc;          /* SSLBM_BC_PERIODIC or SSLBM_BC_NOFLUX (homogeneous Neumann,
                           cell-centred mirror; BGK: halfway bounce-back) */
-  int32_t precision;   /* SSLBM_FP64 .. SSLBM_FP32_KAHAN (BGK supports FP64 and FP32) */
+  int32_t precision;   /* SSLBM_FP64 .. SSLBM_FP32_SPLIT (BGK supports FP64 and FP32) */
   int32_t schemes;     /* SSLBM_WANT_SSLBM | SSLBM_WANT_BGK: which state to hold */
   int32_t lattice;     /* SSLBM_LATTICE_D2Q5 (0), SSLBM_LATTICE_D2Q9 (1),
                           SSLBM_LATTICE_D2Q5_SLBM (2) or SSLBM_LATTICE_D2Q5_VARD (3); 1 to 3:
@@ -429,12 +435,13 @@ int sslbm_fd4_set_order(sslbm_fd4* f, int order);
  *   x = [S, E/s', I/s', R, D, (R0 - 2.6)/1.4, log10(d) + 2, e]
  * and the network is
  *   h0 = A0 x + a0; z_l = K_l(h_{l-1}) + B_l h_{l-1} + b_l, h_l = gelu(z_l) (l < L), h_L = z_L;
- *   delta = Q2 gelu(Q1 h_L + q1) + q2;  v_c = sigma_c (x_c + delta_c), sigma = (1, s', s', 1, 1);
- *   y = v - u kappa, u_c = sigma_c x_c, kappa = (sum v - sum u) / sum u (sums over a sample),
- * K_l a spectral convolution on the kx in {0..m-1, n-m..n-1}, ky in {0..m-1} Fourier modes
- * with complex weights R_l[i][o][kx][ky].  E and I enter and leave in units of the
- * infection scale, so the early exponential phase is the same problem at every amplitude;
- * the last step makes y conserve the total population of its input (zero fields stay zero). 
+ *   delta = Q2 gelu(Q1 h_L + q1) + q2;  v_c = sigma_c max(x_c + delta_c, 0),
+ *   sigma = (1, s', s', 1, 1);  y = v (sum u / sum v) (0 if sum v = 0), u_c = sigma_c x_c,
+ * sums over a sample, K_l a spectral convolution on the kx in {0..m-1, n-m..n-1},
+ * ky in {0..m-1} Fourier modes with complex weights R_l[i][o][kx][ky].  E and I enter and
+ * leave in units of the infection scale, so the early exponential phase is the same problem
+ * at every amplitude; the clamp makes every density of y nonnegative and the rescale makes y
+ * hold the total population of its input, by construction. 
  * Parameters are one flat FP32 vector in the order A0[W][8], a0[W],
  * {R_l[W][W][2m][m][2], B_l[W][W], b_l[W]}_{l=1..L}, Q1[H][W], q1[H], Q2[5][H], q2[5].
  * Dense contractions run on BF16 tensor cores with FP32 accumulation; activations are
@@ -515,6 +522,43 @@ int sslbm_fno_train_step(sslbm_fno* f, int batch, const float* x, const float* t
  * Synchronises the stream. */
 int sslbm_fno_check_project(sslbm_fno* f, int batch, float* y, const float* u, int reach,
                             double* residuals);
+
+/* ---- surrogate rollout with SSLBM fallback -------------------------------------------------
+ * Not in the paper; the learned surrogate's serving loop (the learned-surrogate workload:
+ * batched rollouts that fall back to the SSLBM when a conservation or nonnegativity residual
+ * check fails).  Advances `batch` scenarios by `steps` surrogate steps of k_steps lattice
+ * steps each (k_steps = the horizon the network was trained for, 20 for the surrogates this
+ * library trains).  Each step: x = sslbm_fno_make_input(u), y = sslbm_fno_infer(x), then
+ * the residuals of sslbm_fno_check_project (infinite for a non-finite prediction) and its
+ * projection with `reach`; a scenario with conservation residual > mass_threshold or
+ * negative mass > neg_threshold (either NaN also fails) takes the SSLBM instead: its state is
+ * written into scenario b of `fallback`, the ensemble kernel advances it k_steps lattice
+ * steps and the result replaces the prediction.  The rule of the learned-surrogate workload
+ * is mass_threshold = 1e-4, neg_threshold = 0 (any negative density falls back).
+ *   fallback: an ensemble whose scenarios 0..batch-1 are the rollout's scenarios (periodic
+ *             n x n grids, their rates and diffusivities), FP32 or FP32_DEV; the rollout
+ *             overwrites their states.  Its other scenarios are advanced too when it runs.
+ *   u:        device, FP32 [batch][5][n][n]: the initial states in, the final states out.
+ *   r0, log10d: device, FP32 [batch]: the network's per-scenario inputs.
+ *   x_scratch, y_scratch: device, FP32 [batch][8][n][n] and [batch][5][n][n], 16-byte aligned.
+ *   residuals: host [steps][batch][2] (conservation, negative mass) or NULL.
+ *   fell_back: host [steps][batch], 1 where the SSLBM took the step, or NULL.
+ *   stats:     host totals (or NULL).
+ * Synchronises the surrogate's stream once per step (the residuals decide on the host) and
+ * the ensemble's stream after each fallback; returns the first failing call's status. */
+typedef struct sslbm_rollout_stats {
+  int64_t surrogate_steps;       /* scenario-steps taken by the network */
+  int64_t fallbacks;             /* scenario-steps taken by the SSLBM instead */
+  int64_t failed_conservation;   /* scenario-steps whose conservation residual failed */
+  int64_t failed_nonnegativity;  /* scenario-steps whose negative mass failed */
+  double max_mass_residual;      /* largest finite conservation residual seen */
+  double max_neg_residual;       /* largest finite negative-mass residual seen */
+} sslbm_rollout_stats;
+
+int sslbm_surrogate_rollout(sslbm_fno* f, sslbm_ensemble* fallback, int batch, int steps, int k_steps,
+                            float* u, const float* r0, const float* log10d, float* x_scratch,
+                            float* y_scratch, double mass_threshold, double neg_threshold, int reach,
+                            double* residuals, unsigned char* fell_back, sslbm_rollout_stats* stats);
 
 #ifdef __cplusplus
 }

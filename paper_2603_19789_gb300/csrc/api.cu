@@ -45,7 +45,7 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct Layout {
   int64_t pitch = 0, plane = 0;
   size_t esize = 0, plane_bytes = 0;
-  int s_planes = 0;  // SSLBM planes per state buffer (5, or 10 with Kahan compensation)
+  int s_planes = 0;  // SSLBM planes per state buffer (5; 6 with the split S; 10 with Kahan)
   size_t off_diag = 0, off_s[2] = {0, 0}, off_b[2] = {0, 0}, off_pred = 0, off_kappa = 0, total = 0;
 };
 
@@ -61,7 +61,7 @@ int check_grid(const sslbm_grid* g) {
     return fail(SSLBM_ERR_BAD_ARG, "dx and dt must be finite and > 0");
   if (g->bc != SSLBM_BC_PERIODIC && g->bc != SSLBM_BC_NOFLUX)
     return fail(SSLBM_ERR_BAD_ARG, "bc=%d is not a boundary code", g->bc);
-  if (g->precision < SSLBM_FP64 || g->precision > SSLBM_FP32_KAHAN)
+  if (g->precision < SSLBM_FP64 || g->precision > SSLBM_FP32_SPLIT)
     return fail(SSLBM_ERR_BAD_ARG, "precision=%d is not a precision code", g->precision);
   if (g->schemes < 1 || g->schemes > 3)
     return fail(SSLBM_ERR_BAD_ARG, "schemes=%d must be a nonzero mask of 1 (SSLBM) and 2 (BGK)",
@@ -87,7 +87,7 @@ int make_layout(const sslbm_grid* g, Layout* L) {
   const double bytes_est = (double)L->plane * (double)L->esize * (10.0 + 2 * kBgkPlanes) * 2.0;
   if (bytes_est > 9.0e18) return fail(SSLBM_ERR_BAD_ARG, "grid too large");
   L->plane_bytes = round_up((size_t)L->plane * L->esize, kAlign);
-  L->s_planes = g->precision == SSLBM_FP32_KAHAN ? 10 : 5;
+  L->s_planes = g->precision == SSLBM_FP32_KAHAN ? 10 : g->precision == SSLBM_FP32_SPLIT ? 6 : 5;
   size_t off = 0;
   L->off_diag = off;
   off += round_up((sslbm::kDiagBlocks * sslbm::kDiagSlots + 8) * sizeof(double), kAlign);
@@ -335,7 +335,7 @@ int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_
     // values stored as given (same type, no deviation or compensation plane): one strided copy
     // into the pitched plane, without staging or a conversion pass
     if (!bgk && src_dtype == own_dtype && h->g.precision != SSLBM_FP32_KAHAN &&
-        !(h->g.precision == SSLBM_FP32_DEV && c == SSLBM_S)) {
+        !((h->g.precision == SSLBM_FP32_DEV || h->g.precision == SSLBM_FP32_SPLIT) && c == SSLBM_S)) {
       cudaError_t e = cudaMemcpy2DAsync(h->s_plane(h->s_cur, c), (size_t)h->L.pitch * usize, s,
                                         (size_t)h->g.nx * usize, (size_t)h->g.nx * usize, (size_t)h->g.ny,
                                         src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -354,9 +354,10 @@ int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_
                                  h->stream);
     } else {
       const bool kahan = h->g.precision == SSLBM_FP32_KAHAN;
+      const bool split = h->g.precision == SSLBM_FP32_SPLIT && c == SSLBM_S;
       const int dev_S = (h->g.precision == SSLBM_FP32_DEV && c == SSLBM_S) ? 1 : 0;
       e = sslbm::launch_plane_write(h->g.precision, h->gv, s, src_dtype, h->s_plane(h->s_cur, c),
-                                    kahan ? h->s_plane(h->s_cur, 5 + c) : nullptr, dev_S,
+                                    (kahan || split) ? h->s_plane(h->s_cur, 5 + c) : nullptr, dev_S,
                                     h->p.s_ref, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "write kernel");
@@ -440,7 +441,7 @@ int sslbm_read(sslbm_handle* h, int scheme, int comp, void* dst, int dst_dtype, 
     char* d = static_cast<char*>(dst) + (size_t)(c - c0) * plane_user;
     // values stored as they are returned: one strided copy out of the pitched plane
     if (!bgk && dst_dtype == own_dtype && h->g.precision != SSLBM_FP32_KAHAN &&
-        !(h->g.precision == SSLBM_FP32_DEV && c == SSLBM_S)) {
+        !((h->g.precision == SSLBM_FP32_DEV || h->g.precision == SSLBM_FP32_SPLIT) && c == SSLBM_S)) {
       cudaError_t e = cudaMemcpy2DAsync(d, (size_t)h->g.nx * usize, h->s_plane(h->s_cur, c),
                                         (size_t)h->L.pitch * usize, (size_t)h->g.nx * usize, (size_t)h->g.ny,
                                         dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -455,9 +456,10 @@ int sslbm_read(sslbm_handle* h, int scheme, int comp, void* dst, int dst_dtype, 
                                     dst_dtype, h->stream);
     } else {
       const bool kahan = h->g.precision == SSLBM_FP32_KAHAN;
+      const bool split = h->g.precision == SSLBM_FP32_SPLIT && c == SSLBM_S;
       const int dev_S = (h->g.precision == SSLBM_FP32_DEV && c == SSLBM_S) ? 1 : 0;
       e = sslbm::launch_plane_read(h->g.precision, h->gv, h->s_plane(h->s_cur, c),
-                                   kahan ? h->s_plane(h->s_cur, 5 + c) : nullptr, dev_S,
+                                   (kahan || split) ? h->s_plane(h->s_cur, 5 + c) : nullptr, dev_S,
                                    h->p.s_ref, target, dst_dtype, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "read kernel");
@@ -744,15 +746,21 @@ int sslbm_diagnostics(sslbm_handle* h, int scheme, double* totals, double* peak_
   DeviceGuard dg(h->device);
   const bool bgk = scheme == SSLBM_SCHEME_BGK;
   const void* planes = bgk ? (const void*)h->b_buf[h->b_cur] : (const void*)h->s_buf[h->s_cur];
-  const void* comps = (!bgk && h->g.precision == SSLBM_FP32_KAHAN) ? h->s_plane(h->s_cur, 5) : nullptr;
+  const bool comp = !bgk && (h->g.precision == SSLBM_FP32_KAHAN || h->g.precision == SSLBM_FP32_SPLIT);
+  const void* comps = comp ? h->s_plane(h->s_cur, 5) : nullptr;
   cudaError_t e = sslbm::launch_diagnostics(h->g.precision, bgk ? 1 : 0, h->gv, planes, comps,
-                                            h->diag_partials(), h->diag_result(), h->stream);
+                                            h->diag_partials(), h->diag_result(), h->stream,
+                                            h->g.precision == SSLBM_FP32_SPLIT ? 1 : 5);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics launch");
   double r[sslbm::kDiagSlots];
   e = cudaMemcpyAsync(r, h->diag_result(), sizeof(r), cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(diagnostics)");
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(diagnostics)");
+  unsigned pipe_fault = 0;
+  e = sslbm::pipe_fault_read_and_clear(&pipe_fault, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fused-kernel status");
+  if (pipe_fault) return fail(SSLBM_ERR_TIMEOUT, "a fused launch gave up waiting on its row handoff (state invalid)");
   if (!bgk && h->g.precision == SSLBM_FP32_DEV)
     r[0] = h->p.s_ref * (double)h->g.nx * (double)h->g.ny - r[0];
   if (totals)
@@ -769,7 +777,7 @@ int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows) {
   if (seg_rows < 0) return fail(SSLBM_ERR_BAD_ARG, "seg_rows=%d", seg_rows);
   const bool blocked = sslbm::blocked_supported(h->g.precision, h->gv) && h->g.lattice == SSLBM_LATTICE_D2Q5;
   if (!blocked && k > 1)
-    return fail(SSLBM_ERR_UNSUPPORTED, "temporal blocking is provided for FP32 and FP32_DEV on D2Q5");
+    return fail(SSLBM_ERR_UNSUPPORTED, "temporal blocking is provided for FP32, FP32_DEV and FP32_SPLIT on D2Q5");
   h->depth = k == 0 ? (blocked ? 4 : 1) : k;
   if (seg_rows > 0 && seg_rows < 4 * h->depth) seg_rows = 4 * h->depth;
   h->seg_rows = seg_rows;

@@ -29,6 +29,7 @@
 #include "bounds.cuh"
 #include "sslbm_internal.cuh"
 #include "sslbm_pipe.cuh"
+#include "handles_access.cuh"
 
 SSLBM_OOB_ACCESSOR(ensemble)
 
@@ -794,3 +795,16 @@ int sslbm_ensemble_checkpoint_load(sslbm_ensemble* e, const void* src, size_t by
 }
 
 }  // extern "C"
+
+namespace sslbm {
+
+int ensemble_count(const sslbm_ensemble* e) { return e ? e->n : -1; }
+
+int ensemble_grid(const sslbm_ensemble* e, int idx, int64_t* nx, int64_t* ny) {
+  if (!e || idx < 0 || idx >= e->n || !nx || !ny) return SSLBM_ERR_BAD_ARG;
+  *nx = e->sc[idx].nx;
+  *ny = e->sc[idx].ny;
+  return SSLBM_OK;
+}
+
+}  // namespace sslbm

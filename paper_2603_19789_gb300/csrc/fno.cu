@@ -31,6 +31,7 @@
 
 #include "fno_fused.cuh"
 #include "fno_gemm.cuh"
+#include "handles_access.cuh"
 #include "sslbm_internal.cuh"
 
 namespace sslbm {
@@ -151,14 +152,17 @@ __global__ void channel_sum_kernel(const float* __restrict__ src, float* __restr
   }
 }
 
-// y[b, c, p] = sigma_c (x[b, c, p] + (y[b, c, p] + q2[c])) with y holding Q2 p on entry
+// v[b, c, p] = sigma_c max(x[b, c, p] + (y[b, c, p] + q2[c]), 0) with y holding Q2 p on entry:
+// the nonnegative raw prediction.  The clamp keeps a NaN a NaN (fmaxf would turn it into 0,
+// and the rescale would then hide a non-finite prediction from the rollout's checks).
 __global__ void output_kernel(float* __restrict__ y, const float* __restrict__ q2,
                               const float* __restrict__ x, int B, int64_t P) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)B * 5 * P;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / (5 * P), r = t - b * 5 * P;
     const int c = (int)(r / P);
-    const float v = x[b * kCin * P + r] + (y[t] + q2[c]);
+    const float a = x[b * kCin * P + r] + (y[t] + q2[c]);
+    const float v = a < 0.f ? 0.f : a;
     y[t] = (c == 1 || c == 2) ? scale_from_e(x[(b * kCin + 7) * P]) * v : v;
   }
 }
@@ -219,30 +223,19 @@ __device__ __forceinline__ float plane_sum(const float* __restrict__ a, int64_t 
   return acc;
 }
 
-// per sample b = blockIdx.y: sums[2b] += sum_{c,p} a[b, c, p] w[b, c, p], sums[2b+1] += sum u[b, c, p]
-// with u_c = sigma_c x_c the input state and w = 1 (a = the raw prediction v) or w = u
-// (a = dy: the backward pass's sum of dy u)
-__global__ void state_sums_kernel(const float* __restrict__ a, const float* __restrict__ x,
-                                  double* __restrict__ sums, int64_t P, int weight_by_u) {
+// per sample b = blockIdx.y: sums[2b] += sum_{c,p} dy[b, c, p] y[b, c, p], sums[2b+1] += sum y[b, c, p]
+// (y the cached prediction): the backward pass's lambda = sum(dy y) / sum y
+__global__ void seed_sums_kernel(const float* __restrict__ dy, const float* __restrict__ y,
+                                 double* __restrict__ sums, int64_t P5) {
   __shared__ double sh[64];
   const int64_t b = blockIdx.y;
-  const float sg = scale_from_e(x[(b * kCin + 7) * P]);
-  double sa = 0.0, su = 0.0;
-  for (int c = 0; c < 5; ++c) {
-    const float f = (c == 1 || c == 2) ? sg : 1.f;
-    const float* ab = a + (b * 5 + c) * P;
-    const float* xb = x + (b * kCin + c) * P;
-    if (weight_by_u) {
-      float acc = 0.f;
-      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
-        acc = fmaf(ab[i], xb[i], acc);
-      sa += (double)f * acc;
-    } else {
-      sa += plane_sum(ab, P);
-    }
-    su += (double)f * plane_sum(xb, P);
+  float sa = 0.f, sy = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P5; i += (int64_t)gridDim.x * blockDim.x) {
+    const float yv = y[b * P5 + i];
+    sa = fmaf(dy[b * P5 + i], yv, sa);
+    sy += yv;
   }
-  block_add2(sa, su, sums + 2 * b, sh);
+  block_add2((double)sa, (double)sy, sums + 2 * b, sh);
 }
 
 // The forward pass's sums in one sweep (b = blockIdx.y): sums[2b] += sum of the prediction v
@@ -286,58 +279,61 @@ __global__ void pred_sums_kernel(const float* __restrict__ v, const float* __res
   block_add2((double)sv, (double)su_plain + (double)sg * (double)su_scaled, sums + 2 * b, sh);
 }
 
-// y = v - u kappa, kappa = (sum v - sum u) / sum u: the prediction conserves the population
-// (b = blockIdx.y)
-__global__ void conserve_kernel(float* __restrict__ y, const float* __restrict__ x, const double* __restrict__ sums,
-                                int64_t P) {
-  __shared__ float kap;
+// y = v r, r = sum u / sum v (0 if sum v = 0): the prediction holds the input's population and
+// stays nonnegative (b = blockIdx.y).  ratio[b] = r for the backward pass, and with ycache
+// != NULL a copy of y, whose signs and sums the backward pass needs.
+__global__ void conserve_kernel(float* __restrict__ y, const double* __restrict__ sums, float* __restrict__ ratio,
+                                float* __restrict__ ycache, int64_t P) {
+  __shared__ float rat;
   const int64_t b = blockIdx.y;
   if (threadIdx.x == 0) {
-    const double su = sums[2 * b + 1];
-    kap = su != 0.0 ? (float)((sums[2 * b] - su) / su) : 0.f;
+    const double sv = sums[2 * b], su = sums[2 * b + 1];
+    rat = sv > 0.0 ? (float)(su / sv) : 0.f;
+    if (blockIdx.x == 0) ratio[b] = rat;
   }
   __syncthreads();
-  const float kappa = kap, sg = scale_from_e(x[(b * kCin + 7) * P]);
+  const float r = rat;
   float* yb = y + b * 5 * P;
-  const float* xb = x + b * kCin * P;
+  float* cb = ycache ? ycache + b * 5 * P : nullptr;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x, i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if ((P & 3) == 0 && (reinterpret_cast<uintptr_t>(yb) & 15) == 0 && (reinterpret_cast<uintptr_t>(xb) & 15) == 0) {
-    for (int64_t i = i0; i < P / 4; i += stride) {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        const float k = (c == 1 || c == 2) ? sg * kappa : kappa;
-        float4 v = reinterpret_cast<float4*>(yb + c * P)[i];
-        const float4 u = reinterpret_cast<const float4*>(xb + c * P)[i];
-        v.x = fmaf(-u.x, k, v.x), v.y = fmaf(-u.y, k, v.y), v.z = fmaf(-u.z, k, v.z), v.w = fmaf(-u.w, k, v.w);
-        reinterpret_cast<float4*>(yb + c * P)[i] = v;
-      }
+  if (((5 * P) & 3) == 0 && (reinterpret_cast<uintptr_t>(yb) & 15) == 0 &&
+      (cb == nullptr || (reinterpret_cast<uintptr_t>(cb) & 15) == 0)) {
+    for (int64_t i = i0; i < 5 * P / 4; i += stride) {
+      float4 v = reinterpret_cast<float4*>(yb)[i];
+      v.x *= r, v.y *= r, v.z *= r, v.w *= r;
+      reinterpret_cast<float4*>(yb)[i] = v;
+      if (cb) reinterpret_cast<float4*>(cb)[i] = v;
     }
   } else {
-    for (int c = 0; c < 5; ++c) {
-      const float k = (c == 1 || c == 2) ? sg * kappa : kappa;
-      for (int64_t i = i0; i < P; i += stride) yb[c * P + i] = fmaf(-xb[c * P + i], k, yb[c * P + i]);
+    for (int64_t i = i0; i < 5 * P; i += stride) {
+      const float v = yb[i] * r;
+      yb[i] = v;
+      if (cb) cb[i] = v;
     }
   }
 }
 
-// dd = sigma (dy - lambda_b), lambda_b = sum(dy u) / sum u: the derivative with respect to
-// delta = Q2 p + q2 through y = v - u kappa and v_c = sigma_c (x_c + delta_c)  (b = blockIdx.y)
+// dd = sigma r [y > 0] (dy - lambda), lambda = sum(dy y) / sum y: the derivative with respect to
+// delta = Q2 p + q2 through y = r v, r = sum u / sum v, v_c = sigma_c max(x_c + delta_c, 0)
+// (dL/dv = r (dy - sum(dy v) / sum v), and sum(dy v) / sum v = sum(dy y) / sum y)  (b = blockIdx.y)
 __global__ void scale_dy_kernel(const float* __restrict__ dy, const float* __restrict__ x,
-                                const double* __restrict__ sums, float* __restrict__ dd, int64_t P) {
+                                const float* __restrict__ y, const double* __restrict__ sums,
+                                const float* __restrict__ ratio, float* __restrict__ dd, int64_t P) {
   __shared__ float lm;
   const int64_t b = blockIdx.y;
   if (threadIdx.x == 0) {
-    const double su = sums[2 * b + 1];
-    lm = su != 0.0 ? (float)(sums[2 * b] / su) : 0.f;
+    const double sy = sums[2 * b + 1];
+    lm = sy > 0.0 ? (float)(sums[2 * b] / sy) : 0.f;
   }
   __syncthreads();
-  const float lam = lm, sg = scale_from_e(x[(b * kCin + 7) * P]);
+  const float lam = lm, r = ratio[b], sg = scale_from_e(x[(b * kCin + 7) * P]);
   for (int c = 0; c < 5; ++c) {
-    const float f = (c == 1 || c == 2) ? sg : 1.f;
+    const float f = ((c == 1 || c == 2) ? sg : 1.f) * r;
     const float* g = dy + (b * 5 + c) * P;
+    const float* yc = y + (b * 5 + c) * P;
     float* d = dd + (b * 5 + c) * P;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
-      d[i] = f * (g[i] - lam);
+      d[i] = yc[i] > 0.f ? f * (g[i] - lam) : 0.f;
   }
 }
 
@@ -778,7 +774,7 @@ int make_param_layout(const sslbm_fno_config* c, Layout* L) {
 struct Buffers {
   size_t total;
   size_t theta, theta16, grad, mom, vel, dft, hcat, zcat, zp, p, f32a, f32b, f32p, h1, tt, hat, dg, dd, smax, csum,
-      mask, mscale, loss, res, fault;
+      mask, mscale, loss, res, fault, ratio, ycache;
 };
 
 size_t rup(size_t v) { return (v + 255) / 256 * 256; }
@@ -812,6 +808,8 @@ void make_buffers(const Layout& L, Buffers* b) {
   b->loss = take(8);
   b->res = take(B * 3 * 8);
   b->fault = take(4);  // set by a tensor-core product whose wait ran out
+  b->ratio = take(B * 4);  // per sample: sum u / sum v of the last forward pass
+  b->ycache = take(B * 5 * P * 4);  // the last stored forward pass's prediction
   b->total = o;
 }
 
@@ -1093,14 +1091,16 @@ int forward_fused(sslbm_fno* f, int B, const float* x, float* y, int store) {
   return SSLBM_OK;
 }
 
-// the per-sample conservation step of the output: y = v - u kappa
-int conserve(sslbm_fno* f, int B, const float* x, float* y) {
+// the per-sample conservation step of the output: y = v sum u / sum v; store = keep a copy of
+// y for the backward pass
+int conserve(sslbm_fno* f, int B, const float* x, float* y, int store) {
   double* sums = f->at<double>(f->bu.csum);
   CK(cudaMemsetAsync(sums, 0, (size_t)B * 2 * 8, f->stream), "zero population sums");
   const int64_t P = f->L.P;
   pred_sums_kernel<<<dim3(rows_grid(P), B), kThreads, 0, f->stream>>>(y, x, sums, P);
   CK(cudaGetLastError(), "population sums");
-  conserve_kernel<<<dim3(rows_grid(P), B), kThreads, 0, f->stream>>>(y, x, sums, P);
+  conserve_kernel<<<dim3(rows_grid(P), B), kThreads, 0, f->stream>>>(
+      y, sums, f->at<float>(f->bu.ratio), store ? f->at<float>(f->bu.ycache) : nullptr, P);
   CK(cudaGetLastError(), "conservation");
   return SSLBM_OK;
 }
@@ -1111,8 +1111,9 @@ int forward_impl(sslbm_fno* f, int B, const float* x, float* y, int store) {
     st = forward_fused(f, B, x, y, store);
   else
     st = forward_generic(f, B, x, y);  // always stores
-  if (st == SSLBM_OK) st = conserve(f, B, x, y);
-  f->cached_batch = st == SSLBM_OK && (store || !sslbm::fno_fused::supported(f->L.W, f->L.m, f->L.H, f->L.n)) ? B : 0;
+  const bool keeps = store || !sslbm::fno_fused::supported(f->L.W, f->L.m, f->L.H, f->L.n);
+  if (st == SSLBM_OK) st = conserve(f, B, x, y, keeps ? 1 : 0);
+  f->cached_batch = st == SSLBM_OK && keeps ? B : 0;
   return st;
 }
 
@@ -1123,14 +1124,16 @@ int backward_impl(sslbm_fno* f, int B, const float* x, const float* dy_out) {
   float* g = f->grad();
   int st;
   CK(cudaMemsetAsync(g, 0, L.nparams * sizeof(float), f->stream), "zero gradients");
-  // seed: the derivative with respect to delta = Q2 p + q2 (y_c = sigma_c (x_c + delta_c))
+  // seed: the derivative with respect to delta = Q2 p + q2, through the clamp and the rescale
   float* dy = f->at<float>(f->bu.dd);
   double* sums = f->at<double>(f->bu.csum);
+  const float* ycache = f->at<float>(f->bu.ycache);
   CK(cudaMemsetAsync(sums, 0, (size_t)B * 2 * 8, f->stream), "zero population sums");
   dim3 sgrid((unsigned)std::min<int64_t>(64, (5 * P + kThreads - 1) / kThreads), B);
-  state_sums_kernel<<<sgrid, kThreads, 0, f->stream>>>(dy_out, x, sums, P, 1);
-  CK(cudaGetLastError(), "population sums");
-  scale_dy_kernel<<<dim3(rows_grid(P), B), kThreads, 0, f->stream>>>(dy_out, x, sums, dy, P);
+  seed_sums_kernel<<<sgrid, kThreads, 0, f->stream>>>(dy_out, ycache, sums, 5 * P);
+  CK(cudaGetLastError(), "seed sums");
+  scale_dy_kernel<<<dim3(rows_grid(P), B), kThreads, 0, f->stream>>>(dy_out, x, ycache, sums,
+                                                                    f->at<float>(f->bu.ratio), dy, P);
   CK(cudaGetLastError(), "output scale");
   if ((st = channel_sum(f, dy, g + L.off_q2, B, 5))) return st;
   if ((st = weight_grad(f, dy, 5, f->at<bf16>(f->bu.p), 1, L.H, g + L.off_Q2, B, "dQ2"))) return st;
@@ -1419,3 +1422,16 @@ int sslbm_fno_check_project(sslbm_fno* f, int batch, float* y, const float* u, i
 }
 
 }  // extern "C"
+
+namespace sslbm {
+
+int fno_shape(const sslbm_fno* f, int* n, int* max_batch, int* device, cudaStream_t* stream) {
+  if (!f) return SSLBM_ERR_BAD_ARG;
+  if (n) *n = f->L.n;
+  if (max_batch) *max_batch = f->L.maxB;
+  if (device) *device = f->device;
+  if (stream) *stream = f->stream;
+  return SSLBM_OK;
+}
+
+}  // namespace sslbm

@@ -415,7 +415,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) row_kernel(const RowArgs a) {
         }
       }
       if (gr < 5) {
-        // y_c = sigma_c (x_c + delta_c), sigma_E = sigma_I = 10^(4e - 4) from the scale channel
+        // v_c = sigma_c max(x_c + delta_c, 0), sigma_E = sigma_I = 10^(4e - 4) from the scale
+        // channel: the nonnegative raw prediction (the conservation step rescales it); the
+        // clamp keeps a NaN a NaN, so a non-finite prediction stays visible to the checks
         const int c = gr;
         const float qc = a.q2[c];
         const float sig = (c == 1 || c == 2) ? exp10f(4.f * a.x[((size_t)b * kCin + 7) * n * n] - 4.f) : 1.f;
@@ -426,6 +428,8 @@ __global__ void __launch_bounds__(kRowThreads, 2) row_kernel(const RowArgs a) {
           float2 out;
           out.x = xv.x + (acc4[nt][0] + qc);
           out.y = xv.y + (acc4[nt][1] + qc);
+          out.x = out.x < 0.f ? 0.f : out.x;
+          out.y = out.y < 0.f ? 0.f : out.y;
           if (c == 1 || c == 2) {
             out.x *= sig;
             out.y *= sig;

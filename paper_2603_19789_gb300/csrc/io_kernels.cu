@@ -87,7 +87,7 @@ template <typename T, int LAYOUT>
 __global__ void __launch_bounds__(256) diag_partial_kernel(const GridView g,
                                                            const T* __restrict__ st,
                                                            const T* __restrict__ comp,
-                                                           double* __restrict__ partials) {
+                                                           double* __restrict__ partials, int n_comp) {
   double v[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0, -DBL_MAX};
   for (int64_t y = blockIdx.x; y < g.ny; y += gridDim.x) {
     for (int64_t x = threadIdx.x; x < g.nx; x += blockDim.x) {
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) diag_partial_kernel(const GridView g,
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           r[c] = (double)st[c * g.plane + idx];
-          if (comp) r[c] -= (double)comp[c * g.plane + idx];
+          if (comp && c < n_comp) r[c] -= (double)comp[c * g.plane + idx];
         }
       } else {
 #pragma unroll
@@ -136,9 +136,10 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
 // the plane stride are multiples of 4), keeps its share of the row as a TwoSum pair per
 // compartment and adds that pair to the FP64 partial once per row.  With at most a few dozen
 // cells per thread and row, the pair's own error stays near FP32's unit roundoff squared.
-// The peak of I is taken in FP32 (the same value as in FP64), or in FP64 as value minus
-// compensation when COMP.
-template <int LAYOUT, bool COMP>
+// NCOMP: the first NCOMP compartments carry a compensation plane (0; 1 for the split S; 5 for
+// Kahan), subtracted from the values.  The peak of I is taken in FP32 (the same value as in
+// FP64), or in FP64 as value minus compensation when I has one.
+template <int LAYOUT, int NCOMP>
 __global__ void __launch_bounds__(256) diag_partial_f32x4_kernel(const GridView g, const float* __restrict__ st,
                                                                  const float* __restrict__ comp,
                                                                  double* __restrict__ partials) {
@@ -172,9 +173,9 @@ __global__ void __launch_bounds__(256) diag_partial_f32x4_kernel(const GridView 
         r[4][0] = d.x, r[4][1] = d.y, r[4][2] = d.z, r[4][3] = d.w;
       }
       float q[5][4];
-      if (COMP) {
+      if (NCOMP > 0) {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
+        for (int c = 0; c < NCOMP; ++c) {
           const float4 b = *reinterpret_cast<const float4*>(comp + c * g.plane + idx);
           q[c][0] = b.x, q[c][1] = b.y, q[c][2] = b.z, q[c][3] = b.w;
         }
@@ -185,9 +186,9 @@ __global__ void __launch_bounds__(256) diag_partial_f32x4_kernel(const GridView 
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           two_sum_add(hi[c], lo[c], r[c][j]);
-          if (COMP) two_sum_add(hi[c], lo[c], -q[c][j]);
+          if (c < NCOMP) two_sum_add(hi[c], lo[c], -q[c][j]);
         }
-        if (COMP)
+        if (NCOMP > 2)
           v[5] = fmax(v[5], (double)r[2][j] - (double)q[2][j]);
         else
           pk = fmaxf(pk, r[2][j]);
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(256) diag_partial_f32x4_kernel(const GridView 
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) v[c] += (double)hi[c] + (double)lo[c];
-    if (!COMP) v[5] = fmax(v[5], (double)pk);
+    if (NCOMP <= 2) v[5] = fmax(v[5], (double)pk);
   }
   block_reduce6(v);
   if (threadIdx.x == 0 && SSLBM_IN(blockIdx.x, 1, kDiagBlocks, 31)) {
@@ -272,33 +273,37 @@ cudaError_t launch_plane_read(int precision, const GridView& g, const void* plan
 
 cudaError_t launch_diagnostics(int precision, int layout, const GridView& g, const void* planes,
                                const void* comp_planes, double* partials, double* result,
-                               cudaStream_t s) {
+                               cudaStream_t s, int n_comp) {
+  if (!comp_planes) n_comp = 0;
+  if (n_comp != 0 && n_comp != 1 && n_comp != 5) return cudaErrorInvalidValue;
   int64_t blocks = g.ny < kDiagBlocks ? g.ny : kDiagBlocks;
   if (blocks < 1) blocks = 1;
   if (precision == SSLBM_FP64) {
     if (layout == 0)
       diag_partial_kernel<double, 0><<<(unsigned)blocks, 256, 0, s>>>(
-          g, (const double*)planes, (const double*)comp_planes, partials);
+          g, (const double*)planes, (const double*)comp_planes, partials, n_comp);
     else
       diag_partial_kernel<double, 1><<<(unsigned)blocks, 256, 0, s>>>(g, (const double*)planes,
-                                                                      nullptr, partials);
+                                                                      nullptr, partials, 0);
   } else if (g.pitch % 4 == 0 && g.plane % 4 == 0 && reinterpret_cast<uintptr_t>(planes) % 16 == 0 &&
              reinterpret_cast<uintptr_t>(comp_planes) % 16 == 0) {
     const float* st = (const float*)planes;
     const float* cp = (const float*)comp_planes;
     if (layout == 1)
-      diag_partial_f32x4_kernel<1, false><<<(unsigned)blocks, 256, 0, s>>>(g, st, nullptr, partials);
-    else if (cp)
-      diag_partial_f32x4_kernel<0, true><<<(unsigned)blocks, 256, 0, s>>>(g, st, cp, partials);
+      diag_partial_f32x4_kernel<1, 0><<<(unsigned)blocks, 256, 0, s>>>(g, st, nullptr, partials);
+    else if (n_comp == 5)
+      diag_partial_f32x4_kernel<0, 5><<<(unsigned)blocks, 256, 0, s>>>(g, st, cp, partials);
+    else if (n_comp == 1)
+      diag_partial_f32x4_kernel<0, 1><<<(unsigned)blocks, 256, 0, s>>>(g, st, cp, partials);
     else
-      diag_partial_f32x4_kernel<0, false><<<(unsigned)blocks, 256, 0, s>>>(g, st, nullptr, partials);
+      diag_partial_f32x4_kernel<0, 0><<<(unsigned)blocks, 256, 0, s>>>(g, st, nullptr, partials);
   } else {
     if (layout == 0)
       diag_partial_kernel<float, 0><<<(unsigned)blocks, 256, 0, s>>>(
-          g, (const float*)planes, (const float*)comp_planes, partials);
+          g, (const float*)planes, (const float*)comp_planes, partials, n_comp);
     else
       diag_partial_kernel<float, 1><<<(unsigned)blocks, 256, 0, s>>>(g, (const float*)planes,
-                                                                     nullptr, partials);
+                                                                     nullptr, partials, 0);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

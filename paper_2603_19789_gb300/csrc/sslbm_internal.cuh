@@ -14,7 +14,14 @@
 
 namespace sslbm {
 
-enum Mode { MODE_PLAIN = 0, MODE_DEV = 1, MODE_KAHAN = 2 };
+enum Mode { MODE_PLAIN = 0, MODE_DEV = 1, MODE_KAHAN = 2, MODE_SPLIT = 3 };
+
+// Stored planes per state of a mode: the five compartments, plus the compensation of S
+// (MODE_SPLIT) or of all five (MODE_KAHAN), which follow them.
+template <int MODE>
+constexpr int mode_planes() {
+  return MODE == MODE_KAHAN ? 10 : MODE == MODE_SPLIT ? 6 : 5;
+}
 
 struct GridView {
   int64_t nx, ny, pitch, plane;
@@ -160,6 +167,24 @@ __device__ __forceinline__ void kahan_add(float& v, float& c, float inc) {
   v = t;
 }
 
+// Split storage of S (MODE_SPLIT): S = v - c with v the FP32 value plane and c its FP32
+// compensation plane, a hi/lo pair carrying about twice FP32's precision.  The laplacian of
+// S is lap5_diff(v) - lap5_diff(c); the force uses v; the increment is added to (v, c) with
+// kahan_add; E, I, R and D take the plain update of seird_cell.
+__device__ __forceinline__ void seird_cell_split(const Coeffs<float>& k, float v, float c, float E, float I,
+                                                 float R, float D, float lS, float lE, float lI, float lR,
+                                                 float& nv, float& nc, float& nE, float& nI, float& nR,
+                                                 float& nD) {
+  const float F = force_dt(k, v, E, I, R);
+  nv = v;
+  nc = c;
+  kahan_add(nv, nc, fma_rn(k.dl[0], lS, -F));
+  nE = add_rn(fma_rn(k.dl[1], lE, E), fma_rn(-k.adt, E, F));
+  nI = add_rn(fma_rn(k.dl[2], lI, I), fma_rn(k.adt, E, -mul_rn(k.gdt, I)));
+  nR = fma_rn(k.rdt, I, fma_rn(k.dl[3], lR, R));
+  nD = fma_rn(k.ddt, I, D);
+}
+
 // Increments of S, E, I, R, D for the Kahan variant (same expressions as seird_cell).
 __device__ __forceinline__ void seird_increments(const Coeffs<float>& k, float S, float E, float I,
                                                  float R, float lS, float lE, float lI, float lR,
@@ -196,6 +221,36 @@ __device__ __forceinline__ float2 force_dt2(const Coeffs<float>& k, float2 S, fl
   return mul2(num, r);
 }
 
+// lap5_diff on two cells: l, r the left and right neighbours (formed by the caller), u, d the
+// rows above and below; the same operations, in the same order, as lap5_diff.
+__device__ __forceinline__ float2 lap5diff_x2(float2 c, float2 l, float2 r, float2 u, float2 d) {
+  const float2 nc = neg2(c);
+  return add2(add2(add2(l, nc), add2(r, nc)), add2(add2(u, nc), add2(d, nc)));
+}
+
+// kahan_add on two cells.
+__device__ __forceinline__ void kahan_add2(float2& v, float2& c, float2 inc) {
+  const float2 y = add2(inc, neg2(c));
+  const float2 t = add2(v, y);
+  c = add2(add2(t, neg2(v)), neg2(y));
+  v = t;
+}
+
+// seird_cell_split on two cells (x0 = v, xc = c of S; l0 the laplacian of S).
+__device__ __forceinline__ void seird_cell2_split(const Coeffs<float>& k, float2 x0, float2 xc, float2 E, float2 I,
+                                                  float2 R, float2 D, float2 l0, float2 lE, float2 lI, float2 lR,
+                                                  float2& n0, float2& nc, float2& nE, float2& nI, float2& nR,
+                                                  float2& nD) {
+  const float2 F = force_dt2(k, x0, E, I, R);
+  n0 = x0;
+  nc = xc;
+  kahan_add2(n0, nc, fma2(splat2(k.dl[0]), l0, neg2(F)));
+  nE = add2(fma2(splat2(k.dl[1]), lE, E), fma2(splat2(-k.adt), E, F));
+  nI = add2(fma2(splat2(k.dl[2]), lI, I), fma2(splat2(k.adt), E, neg2(mul2(splat2(k.gdt), I))));
+  nR = fma2(splat2(k.rdt), I, fma2(splat2(k.dl[3]), lR, R));
+  nD = fma2(splat2(k.ddt), I, D);
+}
+
 // MODE 0: plain storage (x0 = S); MODE 1: deviation storage (x0 = sigma = s_ref - S).
 template <int DEV>
 __device__ __forceinline__ void seird_cell2(const Coeffs<float>& k, float2 x0, float2 E, float2 I,
@@ -212,14 +267,17 @@ __device__ __forceinline__ void seird_cell2(const Coeffs<float>& k, float2 x0, f
 }
 
 // ---- launchers (defined in the kernel translation units) --------------------------
-// SSLBM: one step per launch (every precision) and K fused steps per launch (FP32 and
-// FP32 deviation-S).  seg_rows > 0 is the blocked kernel's row-segment length.
+// SSLBM: one step per launch (every precision) and K fused steps per launch (FP32, FP32
+// deviation-S and FP32 split-S).  seg_rows > 0 is the blocked kernel's row-segment length.
 cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coeffs, const void* in,
                                void* out, cudaStream_t s);
 cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* coeffs,
                                  const void* in, void* out, int depth, int seg_rows,
                                  cudaStream_t s);
 bool blocked_supported(int precision, const GridView& g);
+// Whether a fused launch gave up waiting on its row handoff since the last call (reads the
+// device flag, synchronises s, and clears it).
+cudaError_t pipe_fault_read_and_clear(unsigned* out, cudaStream_t s);
 // Segment length that makes one blocked launch a single wave of resident warps.
 int blocked_default_seg_rows(int precision, const GridView& g, int depth);
 // BGK: one collide-and-stream step; equilibrium initialisation and density of one
@@ -230,8 +288,9 @@ cudaError_t launch_bgk_init(int precision, const GridView& g, int comp, const vo
                             int rho_dtype, void* f, cudaStream_t s);
 cudaError_t launch_bgk_density(int precision, const GridView& g, int comp, const void* f, void* rho,
                                int rho_dtype, cudaStream_t s);
-// plane <-> contiguous user layout (dev_S: deviation storage of S; comp_plane: Kahan
-// compensation, reset on write and subtracted on read)
+// plane <-> contiguous user layout (dev_S: deviation storage of S; comp_plane: compensation
+// of the Kahan or split storage, the FP32 rounding residue of the value on write (so that
+// value - compensation reproduces the input) and subtracted on read)
 cudaError_t launch_plane_write(int precision, const GridView& g, const void* src, int src_dtype,
                                void* plane, void* comp_plane, int dev_S, double s_ref,
                                cudaStream_t s);
@@ -243,8 +302,10 @@ cudaError_t launch_plane_read(int precision, const GridView& g, const void* plan
 // layout 0: SSLBM planes; layout 1: BGK populations.
 constexpr int kDiagBlocks = 1024;
 constexpr int kDiagSlots = 6;
+// comp_planes: the compensation planes of the first n_comp compartments (5 for the Kahan
+// storage, 1 for the split storage of S), subtracted from the values; NULL for none.
 cudaError_t launch_diagnostics(int precision, int layout, const GridView& g, const void* planes,
                                const void* comp_planes, double* partials, double* result,
-                               cudaStream_t s);
+                               cudaStream_t s, int n_comp = 5);
 
 }  // namespace sslbm

@@ -3,11 +3,11 @@
 //
 // Two kernels advance the same update:
 //   step1_kernel    one step per launch, every precision (FP64, FP32, FP32 deviation-S,
-//                   FP32 Kahan).  Each thread updates V consecutive cells of a row with
+//                   FP32 split-S, FP32 Kahan).  Each thread updates V consecutive cells of a row with
 //                   16-byte vector loads (float4 / double2) of the centre, upper and lower
 //                   rows and two scalar edge loads; neighbouring rows come from L1/L2.
-//   pipe_kernel     K steps per launch (temporal blocking, K = 2..8) for the FP32
-//                   variants, as a pipeline of K warps per CTA: warp s computes level s+1
+//   pipe_kernel     K steps per launch (temporal blocking, K = 2..8) for FP32, FP32
+//                   deviation-S and FP32 split-S (a sixth plane), as a pipeline of K warps per CTA: warp s computes level s+1
 //                   of the time-step wavefront.  A CTA owns a 128-column strip (4 columns
 //                   per lane, 16-byte accesses) with a K-column halo on each side and
 //                   streams down a segment of rows, two rows per step of the pipeline.
@@ -25,6 +25,7 @@
 // Both use the same per-cell expressions (sslbm_internal.cuh), so a blocked launch gives
 // the same bits as K one-step launches.
 #include <atomic>
+#include <cstdlib>
 
 #include "bounds.cuh"
 #include "sslbm_internal.cuh"
@@ -105,12 +106,12 @@ __global__ void __launch_bounds__(256, MODE == MODE_KAHAN ? 2 : 1) step1_kernel(
         if (j + 1 < V) {
           if (j + 1 < nvalid) r = c[f][j + 1 < V ? j + 1 : j];
         }
-        if constexpr (MODE == MODE_KAHAN)
+        if (MODE == MODE_KAHAN || (MODE == MODE_SPLIT && f == 0))
           lap[f][j] = lap5_diff(c[f][j], l, r, u[j], d[j]);
         else
           lap[f][j] = lap5(c[f][j], l, r, u[j], d[j]);
       }
-      if constexpr (MODE == MODE_KAHAN) {
+      if (MODE == MODE_KAHAN || (MODE == MODE_SPLIT && f == 0)) {
         // the represented value is value - compensation: subtract the compensation's laplacian
         const T* Q = in + (5 + f) * g.plane;
         T qc[V], qu[V], qd[V];
@@ -133,7 +134,21 @@ __global__ void __launch_bounds__(256, MODE == MODE_KAHAN ? 2 : 1) step1_kernel(
     T D[V];
     Vec<T, V>::load(in + 4 * g.plane + rc + x0, D);
     T n[5][V];
-    if constexpr (MODE == MODE_KAHAN) {
+    if constexpr (MODE == MODE_SPLIT) {
+      T cmp[V], ncmp[V];
+      Vec<T, V>::load(in + 5 * g.plane + rc + x0, cmp);
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+        seird_cell_split(k, c[0][j], cmp[j], c[1][j], c[2][j], c[3][j], D[j], lap[0][j], lap[1][j], lap[2][j],
+                         lap[3][j], n[0][j], ncmp[j], n[1][j], n[2][j], n[3][j], n[4][j]);
+      if (nvalid == V) {
+        Vec<T, V>::store(out + 5 * g.plane + rc + x0, ncmp);
+      } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+          if (j < nvalid) out[5 * g.plane + rc + x0 + j] = ncmp[j];
+      }
+    } else if constexpr (MODE == MODE_KAHAN) {
       T cmp[5][V];
 #pragma unroll
       for (int f = 0; f < 5; ++f) Vec<T, V>::load(in + (5 + f) * g.plane + rc + x0, cmp[f]);
@@ -185,17 +200,28 @@ __global__ void __launch_bounds__(256, MODE == MODE_KAHAN ? 2 : 1) step1_kernel(
   }
 }
 
-template <int MODE, int K>
+// set by a fused launch whose row handoff wait ran out (read and cleared by the diagnostics)
+__device__ unsigned int g_pipe_fault = 0;
+
+template <int MODE, int K, bool MB>
 __global__ void __launch_bounds__(32 * K, 16 / K) pipe_kernel(const GridView g, const Coeffs<float> k,
                                                              const float* __restrict__ in,
                                                              float* __restrict__ out,
                                                              const int seg_rows, const int nstrips) {
   extern __shared__ __align__(16) unsigned char pipe_smem[];
-  PipeSmem<K>& sm = *reinterpret_cast<PipeSmem<K>*>(pipe_smem);
+  PipeSmem<K, mode_planes<MODE>()>& sm = *reinterpret_cast<PipeSmem<K, mode_planes<MODE>()>*>(pipe_smem);
   const int strip = (int)(blockIdx.x % (unsigned)nstrips);
   const int64_t y0 = (int64_t)(blockIdx.x / (unsigned)nstrips) * seg_rows;
   const int64_t y1 = (y0 + seg_rows < g.ny) ? y0 + seg_rows : g.ny;
-  pipe_tile<MODE, K>(sm, g, k, in, out, strip, y0, y1);
+  pipe_tile<MODE, K, false, MB>(sm, g, k, in, out, strip, y0, y1, &g_pipe_fault);
+}
+
+bool pipe_mbar() {
+  static const bool on = [] {
+    const char* v = std::getenv("SSLBM_PIPE_MBAR");
+    return v && v[0] == '1';
+  }();
+  return on;
 }
 
 template <typename T, int V, int MODE>
@@ -220,9 +246,13 @@ void prefer_shared() {
   if (cudaGetDevice(&dev) != cudaSuccess) return;
   const unsigned long long bit = 1ull << (dev & 63);
   if (done.load(std::memory_order_acquire) & bit) return;
-  cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       cudaSharedmemCarveoutMaxShared);
-  cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<K>));
+  auto set = [](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(PipeSmem<K, mode_planes<MODE>()>));
+  };
+  set(pipe_kernel<MODE, K, false>);
+  if constexpr (MODE != MODE_SPLIT) set(pipe_kernel<MODE, K, true>);
   done.fetch_or(bit, std::memory_order_release);
 }
 
@@ -237,7 +267,10 @@ cudaError_t launch_blocked_t(const GridView& g, const void* coeffs, const void* 
   const int64_t nseg = (g.ny + seg_rows - 1) / seg_rows;
   const int64_t blocks = nstrips * nseg;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  pipe_kernel<MODE, K><<<(unsigned)blocks, 32 * K, sizeof(PipeSmem<K>), s>>>(
+  auto kern = pipe_kernel<MODE, K, false>;
+  if constexpr (MODE != MODE_SPLIT)  // the split storage's sixth plane leaves no registers for it
+    if (pipe_mbar()) kern = pipe_kernel<MODE, K, true>;
+  kern<<<(unsigned)blocks, 32 * K, sizeof(PipeSmem<K, mode_planes<MODE>()>), s>>>(
       g, *static_cast<const Coeffs<float>*>(coeffs), static_cast<const float*>(in),
       static_cast<float*>(out), seg_rows, (int)nstrips);
   return cudaGetLastError();
@@ -252,7 +285,8 @@ int default_seg_rows_t(const GridView& g) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_kernel<MODE, K>, 32 * K, sizeof(PipeSmem<K>));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_kernel<MODE, K, false>, 32 * K,
+                                                sizeof(PipeSmem<K, mode_planes<MODE>()>));
   // one wave: as many CTAs as fit on the device at once, split into row segments
   const int64_t resident = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
   int64_t nseg = resident / nstrips;
@@ -297,11 +331,12 @@ int default_seg_rows_mode(const GridView& g, int depth) {
 int blocked_default_seg_rows(int precision, const GridView& g, int depth) {
   if (precision == SSLBM_FP32) return default_seg_rows_mode<MODE_PLAIN>(g, depth);
   if (precision == SSLBM_FP32_DEV) return default_seg_rows_mode<MODE_DEV>(g, depth);
+  if (precision == SSLBM_FP32_SPLIT) return default_seg_rows_mode<MODE_SPLIT>(g, depth);
   return 0;
 }
 
 bool blocked_supported(int precision, const GridView&) {
-  return precision == SSLBM_FP32 || precision == SSLBM_FP32_DEV;
+  return precision == SSLBM_FP32 || precision == SSLBM_FP32_DEV || precision == SSLBM_FP32_SPLIT;
 }
 
 cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coeffs, const void* in,
@@ -310,10 +345,21 @@ cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coe
     case SSLBM_FP64: return launch_step1_t<double, 2, MODE_PLAIN>(g, coeffs, in, out, s);
     case SSLBM_FP32: return launch_step1_t<float, 4, MODE_PLAIN>(g, coeffs, in, out, s);
     case SSLBM_FP32_DEV: return launch_step1_t<float, 4, MODE_DEV>(g, coeffs, in, out, s);
+    case SSLBM_FP32_SPLIT: return launch_step1_t<float, 4, MODE_SPLIT>(g, coeffs, in, out, s);
     // two cells per thread: the compensated update carries twice the state per cell
     case SSLBM_FP32_KAHAN: return launch_step1_t<float, 2, MODE_KAHAN>(g, coeffs, in, out, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t pipe_fault_read_and_clear(unsigned* out, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_pipe_fault, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && *out) {
+    const unsigned zero = 0;
+    e = cudaMemcpyToSymbolAsync(g_pipe_fault, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s);
+  }
+  return e;
 }
 
 cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* coeffs,
@@ -323,6 +369,8 @@ cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* c
     return launch_blocked_mode<MODE_PLAIN>(g, coeffs, in, out, depth, seg_rows, s);
   if (precision == SSLBM_FP32_DEV)
     return launch_blocked_mode<MODE_DEV>(g, coeffs, in, out, depth, seg_rows, s);
+  if (precision == SSLBM_FP32_SPLIT)
+    return launch_blocked_mode<MODE_SPLIT>(g, coeffs, in, out, depth, seg_rows, s);
   return cudaErrorInvalidValue;
 }
 

@@ -13,8 +13,9 @@
 // row is copied.  x neighbours come from warp shuffles.  Rows and columns outside the domain
 // are loaded as ghost images (periodic wrap or the even mirror extension), which the
 // uniform stencil keeps consistent, so no boundary logic is needed inside the pipeline.
-// The arithmetic is the packed form of seird_cell / seird_cell_dev, bit-identical to the
-// one-step kernel.
+// The arithmetic is the packed form of seird_cell / seird_cell_dev / seird_cell_split,
+// bit-identical to the one-step kernel; the split storage of S carries its compensation as a
+// sixth plane through the pipeline.
 #pragma once
 #include "bounds.cuh"
 #include "sslbm_internal.cuh"
@@ -39,26 +40,69 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Row handoff by mbarriers (the MB form of pipe_tile): every lane of the producing (or
+// consuming) warp arrives, so each barrier completes a phase on 32 arrivals.  Waits are
+// bounded: a lane whose wait runs out raises *fault and carries on, so the launch still
+// ends, with its output marked invalid by the flag.
+constexpr unsigned kPipeWaitLimit = 1u << 22;
+__device__ __forceinline__ void pipe_bar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void pipe_bar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void pipe_bar_wait(unsigned bar, unsigned parity, unsigned* fault) {
+  for (unsigned it = 0; it < kPipeWaitLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return;
+  }
+  if (fault) atomicExch(fault, 1u);
+}
+
 // r0: level-0 rows (warp 0's lanes read back exactly what they copied);
 // rl[s-1]: the pair of level-s rows from warp s-1 to warp s, double-buffered by iteration
 // parity.  Over 48 KB from K = 5 on: the kernels take it as dynamic shared memory.
-template <int K>
+// NF = the planes a state of the mode stores (5, or 6 with the compensation of S).
+template <int K, int NF = 5>
 struct alignas(16) PipeSmem {
-  float r0[kRing0][5][128];
-  float rl[K - 1][2][2][5][128];
+  float r0[kRing0][NF][128];
+  float rl[K - 1][2][2][NF][128];
 };
 
 // Level s+1 of row C (two float2 column pairs per field) from level-s rows P, C, N: x
-// neighbours by shuffles, the packed lap5 and the packed cell update.
-template <int MODE>
-__device__ __forceinline__ void cell_row(const Coeffs<float>& k, const float2 (&P)[5][2], const float2 (&C)[5][2],
-                                         const float2 (&N)[5][2], float2 (&M)[5][2]) {
+// neighbours by shuffles, the packed lap5 and the packed cell update.  MODE_SPLIT: field 5
+// is the compensation of S, and the laplacian of S is lap5_diff(v) - lap5_diff(c).
+template <int MODE, int NF = mode_planes<MODE>()>
+__device__ __forceinline__ void cell_row(const Coeffs<float>& k, const float2 (&P)[NF][2], const float2 (&C)[NF][2],
+                                         const float2 (&N)[NF][2], float2 (&M)[NF][2]) {
   constexpr unsigned kFull = 0xffffffffu;
   float2 lp[4][2];
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     const float L = __shfl_up_sync(kFull, C[f][1].y, 1);
     const float R = __shfl_down_sync(kFull, C[f][0].x, 1);
+    if (MODE == MODE_SPLIT && f == 0) {
+      // the difference form on the value and on the compensation (field Q = NF - 1), columns 0..3
+      constexpr int Q = NF - 1;
+      const float LC = __shfl_up_sync(kFull, C[Q][1].y, 1);
+      const float RC = __shfl_down_sync(kFull, C[Q][0].x, 1);
+      const float2 v0 = lap5diff_x2(C[0][0], make_float2(L, C[0][0].x), make_float2(C[0][0].y, C[0][1].x),
+                                    P[0][0], N[0][0]);
+      const float2 v1 = lap5diff_x2(C[0][1], make_float2(C[0][0].y, C[0][1].x), make_float2(C[0][1].y, R),
+                                    P[0][1], N[0][1]);
+      const float2 c0 = lap5diff_x2(C[Q][0], make_float2(LC, C[Q][0].x), make_float2(C[Q][0].y, C[Q][1].x),
+                                    P[Q][0], N[Q][0]);
+      const float2 c1 = lap5diff_x2(C[Q][1], make_float2(C[Q][0].y, C[Q][1].x), make_float2(C[Q][1].y, RC),
+                                    P[Q][1], N[Q][1]);
+      lp[0][0] = add2(v0, neg2(c0));
+      lp[0][1] = add2(v1, neg2(c1));
+      continue;
+    }
     // left + right neighbour of columns 0..3, then the packed rest of lap5
     const float2 lr0 = make_float2(__fadd_rn(L, C[f][0].y), __fadd_rn(C[f][0].x, C[f][1].x));
     const float2 lr1 = make_float2(__fadd_rn(C[f][0].y, C[f][1].y), __fadd_rn(C[f][1].x, R));
@@ -66,34 +110,39 @@ __device__ __forceinline__ void cell_row(const Coeffs<float>& k, const float2 (&
     lp[f][1] = lap5x2(C[f][1], lr1, P[f][1], N[f][1]);
   }
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
-    seird_cell2<MODE == MODE_DEV>(k, C[0][h], C[1][h], C[2][h], C[3][h], C[4][h], lp[0][h], lp[1][h], lp[2][h],
-                                  lp[3][h], M[0][h], M[1][h], M[2][h], M[3][h], M[4][h]);
+  for (int h = 0; h < 2; ++h) {
+    if constexpr (MODE == MODE_SPLIT)
+      seird_cell2_split(k, C[0][h], C[NF - 1][h], C[1][h], C[2][h], C[3][h], C[4][h], lp[0][h], lp[1][h], lp[2][h],
+                        lp[3][h], M[0][h], M[NF - 1][h], M[1][h], M[2][h], M[3][h], M[4][h]);
+    else
+      seird_cell2<MODE == MODE_DEV>(k, C[0][h], C[1][h], C[2][h], C[3][h], C[4][h], lp[0][h], lp[1][h], lp[2][h],
+                                    lp[3][h], M[0][h], M[1][h], M[2][h], M[3][h], M[4][h]);
+  }
 }
 
 // Hand level-(s+1) row M to the next warp (slot row `which` of parity par) or, for the last
 // warp, write it to row r of the output.
-template <int K>
-__device__ __forceinline__ void emit_row(PipeSmem<K>& sm, const GridView& g, const float2 (&M)[5][2],
+template <int K, int NF>
+__device__ __forceinline__ void emit_row(PipeSmem<K, NF>& sm, const GridView& g, const float2 (&M)[NF][2],
                                          float* __restrict__ out, const int s, const int lane, const int par,
                                          const int which, const bool writer, const int64_t xs, const int64_t r,
                                          const int64_t y0, const int64_t y1) {
   if (s < K - 1) {
     float* dst = &sm.rl[s < K - 1 ? s : 0][par][which][0][4 * lane];
 #pragma unroll
-    for (int f = 0; f < 5; ++f)
+    for (int f = 0; f < NF; ++f)
       *reinterpret_cast<float4*>(dst + 128 * f) = make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
   } else if (writer && r >= y0 && r < y1 && SSLBM_IN(r, 1, g.ny, 5)) {
     float* o = out + r * g.pitch + xs;
     if (xs + 3 < g.nx) {
       if (SSLBM_IN(xs, 4, g.nx, 6)) {
 #pragma unroll
-        for (int f = 0; f < 5; ++f)
+        for (int f = 0; f < NF; ++f)
           *reinterpret_cast<float4*>(o + f * g.plane) = make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
       }
     } else {
 #pragma unroll
-      for (int f = 0; f < 5; ++f) {
+      for (int f = 0; f < NF; ++f) {
         const float v[4] = {M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y};
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj)
@@ -104,39 +153,55 @@ __device__ __forceinline__ void emit_row(PipeSmem<K>& sm, const GridView& g, con
 }
 
 // One iteration of warp s: read the pair of level-s rows b, b+1 (N0, N1) from src (row b+1
-// 640 floats further), compute level-(s+1) rows b-1 (from A = b-2, B = b-1, N0) and b (from
+// 128 NF floats further), compute level-(s+1) rows b-1 (from A = b-2, B = b-1, N0) and b (from
 // B, N0, N1), hand them on or write them as rows r, r+1.  Ends with the CTA barrier.
-template <int MODE, int K>
-__device__ __forceinline__ void pipe_pair(PipeSmem<K>& sm, const GridView& g, const Coeffs<float>& k,
-                                          const float* src, const float2 (&A)[5][2], const float2 (&B)[5][2],
-                                          float2 (&N0)[5][2], float2 (&N1)[5][2], float* __restrict__ out,
+// Without MB the iteration ends with the CTA barrier.  With MB (the caller has already
+// waited for the slot it reads and the slot it writes), the handoff is per slot: `in_bar`
+// (when nonzero) is the consumer's "empty" barrier of the slot just read, arrived on once
+// the pair is in registers, and `out_bar` the producer's "full" barrier of the slot just
+// written, arrived on after both rows are in it.
+template <int MODE, int K, bool MB = false, int NF = mode_planes<MODE>()>
+__device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g, const Coeffs<float>& k,
+                                          const float* src, const float2 (&A)[NF][2], const float2 (&B)[NF][2],
+                                          float2 (&N0)[NF][2], float2 (&N1)[NF][2], float* __restrict__ out,
                                           const int s, const int lane, const int par, const bool writer,
-                                          const int64_t xs, const int64_t r, const int64_t y0, const int64_t y1) {
+                                          const int64_t xs, const int64_t r, const int64_t y0, const int64_t y1,
+                                          const unsigned in_bar = 0, const unsigned out_bar = 0) {
 #pragma unroll
-  for (int f = 0; f < 5; ++f) {
+  for (int f = 0; f < NF; ++f) {
     const float4 t0 = *reinterpret_cast<const float4*>(src + 128 * f);
-    const float4 t1 = *reinterpret_cast<const float4*>(src + 640 + 128 * f);
+    const float4 t1 = *reinterpret_cast<const float4*>(src + 128 * NF + 128 * f);
     N0[f][0] = make_float2(t0.x, t0.y);
     N0[f][1] = make_float2(t0.z, t0.w);
     N1[f][0] = make_float2(t1.x, t1.y);
     N1[f][1] = make_float2(t1.z, t1.w);
   }
-  float2 M[5][2];
+  if (MB && in_bar) pipe_bar_arrive(in_bar);
+  float2 M[NF][2];
   cell_row<MODE>(k, A, B, N0, M);
-  emit_row<K>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
+  emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
   cell_row<MODE>(k, B, N0, N1, M);
-  emit_row<K>(sm, g, M, out, s, lane, par, 1, writer, xs, r + 1, y0, y1);
-  __syncthreads();
+  emit_row<K, NF>(sm, g, M, out, s, lane, par, 1, writer, xs, r + 1, y0, y1);
+  if (MB) {
+    if (out_bar) pipe_bar_arrive(out_bar);
+  } else {
+    __syncthreads();
+  }
 }
 
 // WRAP16: periodic grid with nx a multiple of 4 -- every lane's four columns, ghosts
 // included, are one contiguous 16-byte group at the wrapped position, so all loads are
 // L2-only cp.async.cg (required when other CTAs of the same launch wrote the input, since
 // L1 is not coherent).
-template <int MODE, int K, bool WRAP16 = false>
-__device__ __forceinline__ void pipe_tile(PipeSmem<K>& sm, const GridView& g, const Coeffs<float>& k,
+// MB: hand rows between neighbouring warps by mbarriers (two per slot: full, empty) instead
+// of one CTA barrier per pair, so a warp waits only for its producer and its consumer and
+// can run up to an iteration ahead of them.  Used once per CTA (the barriers' phases start
+// at zero); a wait that runs out sets *fault (see pipe_bar_wait).
+template <int MODE, int K, bool WRAP16 = false, bool MB = false, int NF = mode_planes<MODE>()>
+__device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g, const Coeffs<float>& k,
                                           const float* __restrict__ in, float* __restrict__ out,
-                                          const int strip, const int64_t y0, const int64_t y1) {
+                                          const int strip, const int64_t y0, const int64_t y1,
+                                          unsigned* fault = nullptr) {
   constexpr int HL = (K + 3) / 4;   // halo lanes on each side of the strip
   constexpr int WV = 128 - 8 * HL;  // columns written per strip
   const int lane = threadIdx.x & 31;
@@ -159,8 +224,14 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K>& sm, const GridView& g, co
   const int nt = (int)(((y1 - y0) + 4 * K - 4 + 1) / 2) + 1;
   const int64_t rbase = qa - 3 * (K - 1) - 1;  // the first row the last warp emits (iteration 0)
 
-  for (int i = threadIdx.x; i < kRing0 * 5 * 128; i += 32 * K) (&sm.r0[0][0][0])[i] = 0.f;
-  for (int i = threadIdx.x; i < (K - 1) * 2 * 2 * 5 * 128; i += 32 * K) (&sm.rl[0][0][0][0][0])[i] = 0.f;
+  for (int i = threadIdx.x; i < kRing0 * NF * 128; i += 32 * K) (&sm.r0[0][0][0])[i] = 0.f;
+  for (int i = threadIdx.x; i < (K - 1) * 2 * 2 * NF * 128; i += 32 * K) (&sm.rl[0][0][0][0][0])[i] = 0.f;
+  // full[l][p] = bars[2l + p], empty[l][p] = bars[2(K-1) + 2l + p] for the link l -> l+1
+  __shared__ __align__(8) unsigned long long bars[MB ? 4 * (K - 1) : 1];
+  if (MB && threadIdx.x == 0) {
+    for (int i = 0; i < 4 * (K - 1); ++i) pipe_bar_init(smem_addr(&bars[i]), 32u);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
   __syncthreads();
 
   auto issue = [&](int64_t q) {  // warp 0: copy level-0 row q into its ring slot
@@ -170,7 +241,7 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K>& sm, const GridView& g, co
     if (!SSLBM_IN(yq, 1, g.ny, 1)) return;
     const int64_t row = yq * g.pitch;
 #pragma unroll
-    for (int f = 0; f < 5; ++f) {
+    for (int f = 0; f < NF; ++f) {
       const float* src = in + f * g.plane + row;
       float* dst = &sm.r0[slot][f][4 * lane];
       if (WRAP16) {
@@ -196,9 +267,9 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K>& sm, const GridView& g, co
 
   // Four row buffers: A, B hold rows b-2, b-1; the pair b, b+1 arrives in the other two, and
   // the roles swap every iteration (unrolled two ways, so no row is copied between registers).
-  float2 RA[5][2], RB[5][2], RC[5][2], RD[5][2];
+  float2 RA[NF][2], RB[NF][2], RC[NF][2], RD[NF][2];
 #pragma unroll
-  for (int f = 0; f < 5; ++f)
+  for (int f = 0; f < NF; ++f)
 #pragma unroll
     for (int h = 0; h < 2; ++h) RA[f][h] = RB[f][h] = make_float2(0.f, 0.f);
   // source of the pair of iteration t: warp 0's ring slots, or the previous warp's slot
@@ -212,14 +283,42 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K>& sm, const GridView& g, co
     }
     return &sm.rl[s - 1][(t + 1) & 1][0][0][4 * lane];
   };
-  int t = 0;
-  for (; t + 2 <= nt; t += 2) {
-    pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0, y1);
-    pipe_pair<MODE, K>(sm, g, k, fetch(t + 1), RC, RD, RA, RB, out, s, lane, (t + 1) & 1, writer, xs,
-                       rbase + 2 * t + 2, y0, y1);
+  if constexpr (MB) {
+    // Iteration t: warp s (s >= 1) reads slot q = (t+1) & 1 of link s-1, which warp s-1
+    // wrote at iteration t-1 (at t = 0 the zeroed slot 1); warp s (s < K-1) writes slot
+    // p = t & 1 of link s.  Slot 1 is read at t = 0, 2, 4 ... (the read at t = 2j is that
+    // slot's j-th, of the data written at t = 2j-1) and written at t = 1, 3 ...; slot 0 is
+    // written at t = 0, 2 ... and read at t = 1, 3 ....  Hence the phases below.
+    // one base per warp: full of its output link at lb, of its input link at lb - 16, and
+    // the empty barriers 16 (K - 1) bytes further
+    const unsigned lb = smem_addr(&bars[0]) + 16u * (unsigned)s;
+    constexpr unsigned kEmpty = 16u * (K - 1);
+    const bool cons = s >= 1, prod = s < K - 1;
+    auto step = [&](int t, float2 (&a)[NF][2], float2 (&b)[NF][2], float2 (&c)[NF][2], float2 (&d)[NF][2]) {
+      const unsigned q = (unsigned)(t + 1) & 1u, p = (unsigned)t & 1u, h = (unsigned)(t >> 1);
+      // both waits before any row is loaded: the pair to read is in, the slot to write is free
+      if (cons && t >= 1) pipe_bar_wait(lb - 16u + 8u * q, (q ? h - 1u : h) & 1u, fault);
+      if (prod && t >= 1) pipe_bar_wait(lb + kEmpty + 8u * p, (p ? h : h + 1u) & 1u, fault);
+      pipe_pair<MODE, K, true>(sm, g, k, fetch(t), a, b, c, d, out, s, lane, (int)p, writer, xs, rbase + 2 * t, y0,
+                               y1, cons ? lb - 16u + kEmpty + 8u * q : 0u, prod ? lb + 8u * p : 0u);
+    };
+    int t = 0;
+    for (; t + 2 <= nt; t += 2) {
+      step(t, RA, RB, RC, RD);
+      step(t + 1, RC, RD, RA, RB);
+    }
+    if (t < nt) step(t, RA, RB, RC, RD);
+  } else {
+    int t = 0;
+    for (; t + 2 <= nt; t += 2) {
+      pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0, y1);
+      pipe_pair<MODE, K>(sm, g, k, fetch(t + 1), RC, RD, RA, RB, out, s, lane, (t + 1) & 1, writer, xs,
+                         rbase + 2 * t + 2, y0, y1);
+    }
+    if (t < nt)
+      pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0,
+                         y1);
   }
-  if (t < nt)
-    pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0, y1);
   if (s == 0) cp_async_wait<0>();
 }
 

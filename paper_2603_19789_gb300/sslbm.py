@@ -25,7 +25,7 @@ SSLBM_OK = 0
 (SSLBM_ERR_BAD_ARG, SSLBM_ERR_UNSTABLE, SSLBM_ERR_CUDA, SSLBM_ERR_TIMEOUT, SSLBM_ERR_NONFINITE,
  SSLBM_ERR_WORKSPACE, SSLBM_ERR_UNSUPPORTED, SSLBM_ERR_STATE) = (-1, -2, -3, -4, -5, -6, -7, -8)
 BC_PERIODIC, BC_NOFLUX = 0, 1
-FP64, FP32, FP32_DEV, FP32_KAHAN = 0, 1, 2, 3
+FP64, FP32, FP32_DEV, FP32_KAHAN, FP32_SPLIT = 0, 1, 2, 3, 4
 SCHEME_SSLBM, SCHEME_BGK = 0, 1
 S, E, I, R, D, NCOMP = 0, 1, 2, 3, 4, 5
 ALL = -1
@@ -33,7 +33,7 @@ DT_F64, DT_F32 = 0, 1
 WANT_SSLBM, WANT_BGK = 1, 2
 LATTICE_D2Q5, LATTICE_D2Q9, LATTICE_D2Q5_SLBM, LATTICE_D2Q5_VARD = 0, 1, 2, 3
 MAX_DEPTH = 8
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP32_KAHAN}
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP32_KAHAN, "fp32_split": FP32_SPLIT}
 
 # every symbol include/sslbm.h declares
 EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspace_bytes",
@@ -54,9 +54,15 @@ EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspa
            "sslbm_fno_forward", "sslbm_fno_backward", "sslbm_fno_set_adam", "sslbm_fno_set_loss_weights",
            "sslbm_fno_set_wait_limit",
            "sslbm_fno_infer", "sslbm_fno_fused",
-           "sslbm_fno_train_step", "sslbm_fno_check_project",
+           "sslbm_fno_train_step", "sslbm_fno_check_project", "sslbm_surrogate_rollout",
            "sslbm_fd4_workspace_bytes", "sslbm_fd4_create", "sslbm_fd4_destroy", "sslbm_fd4_write",
            "sslbm_fd4_read", "sslbm_fd4_step", "sslbm_fd4_steps_done", "sslbm_fd4_set_order")
+
+
+class RolloutStats(ctypes.Structure):
+    _fields_ = [("surrogate_steps", ctypes.c_int64), ("fallbacks", ctypes.c_int64),
+                ("failed_conservation", ctypes.c_int64), ("failed_nonnegativity", ctypes.c_int64),
+                ("max_mass_residual", ctypes.c_double), ("max_neg_residual", ctypes.c_double)]
 
 
 class SslbmError(RuntimeError):
@@ -176,6 +182,8 @@ def load(path: str = LIB_PATH):
             "sslbm_fno_train_step": (i32, [_vp, i32, _vp, _vp, _vp, _vp, ctypes.c_float,
                                            ctypes.POINTER(ctypes.c_double)]),
             "sslbm_fno_check_project": (i32, [_vp, i32, _vp, _vp, i32, ctypes.POINTER(ctypes.c_double)]),
+            "sslbm_surrogate_rollout": (i32, [_vp, _vp, i32, i32, i32, _vp, _vp, _vp, _vp, _vp, ctypes.c_double,
+                                              ctypes.c_double, i32, _vp, _vp, ctypes.POINTER(RolloutStats)]),
             "sslbm_diagnostics_noalloc": (i32, [_vp, i32, i64, i64, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_double), _vp]),
         }
@@ -834,6 +842,23 @@ def sslbm_fno_train_step(f, batch, x, target, y_scratch, dy_scratch, lr, want_lo
                                        float(lr), ctypes.byref(loss) if want_loss else None),
            "sslbm_fno_train_step")
     return float(loss.value) if want_loss else None
+
+
+def sslbm_surrogate_rollout(f, e, batch, steps, k_steps, u, r0, logd, x_scratch, y_scratch,
+                            mass_threshold=1e-4, neg_threshold=0.0, reach=0, want_residuals=True):
+    """The C-ABI rollout (argument marshalling only): u (device, [batch, 5, n, n] float32) is
+    advanced in place.  Returns (stats dict, residuals [steps, batch, 2] or None,
+    fell_back [steps, batch] bool or None)."""
+    res = np.empty((steps, batch, 2), np.float64) if want_residuals else None
+    fb = np.empty((steps, batch), np.uint8) if want_residuals else None
+    st = RolloutStats()
+    _check(load().sslbm_surrogate_rollout(
+        f, e, int(batch), int(steps), int(k_steps), _dptr(u), _dptr(r0), _dptr(logd), _dptr(x_scratch),
+        _dptr(y_scratch), float(mass_threshold), float(neg_threshold), int(reach),
+        res.ctypes.data_as(_vp) if res is not None else None, fb.ctypes.data_as(_vp) if fb is not None else None,
+        ctypes.byref(st)), "sslbm_surrogate_rollout")
+    stats = {k: getattr(st, k) for k, _ in RolloutStats._fields_}
+    return stats, res, (fb.astype(bool) if fb is not None else None)
 
 
 def sslbm_fno_check_project(f, batch, y, u, reach=0):

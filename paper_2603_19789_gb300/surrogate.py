@@ -7,19 +7,14 @@ d ~ logU[1e-3, 1e-1], 1..8 Gaussian seeds) on n x n grids, produced by the persi
 ensemble launch; from each trajectory, snapshots at stratified random multiples of 20 steps
 over the rollout horizon (one per stratum), each paired with the state 20 steps later.
 
-Rollout: each surrogate step advances a batch of scenarios by 20 SSLBM steps.  The raw
-prediction y is checked against the input state u: the conservation residual
-|sum y - sum u| / sum u and the nonnegativity residual sum max(-y, 0) / sum u.  A scenario
-whose conservation residual exceeds the threshold (1e-4), or whose negative mass exceeds
-neg_threshold (by default the same 1e-4: negatives that the projection below removes
-while moving the state by no more than the conservation tolerance), takes the SSLBM's 20
-steps instead (the fallback, run by the ensemble kernel).  Accepted predictions are
-projected onto the admissible set: E, I, R and D zeroed outside the domain of dependence
-of the input's infection (20 steps of the 5-point stencil move information at most 20
-cells), clamped at zero, rescaled to the input's total.  With neg_threshold=0 any negative
-value triggers the fallback.  The rollout also counts the scenario-steps with any
-negative value at all.  The SSLBM also judges the rollout: a reference ensemble advanced
-in lock step gives the error every ten surrogate steps.
+Rollout (the library's sslbm_surrogate_rollout): each surrogate step advances a batch of
+scenarios by 20 SSLBM steps.  The network's output is nonnegative and holds its input's
+population by construction; the prediction y is still checked against the input state u --
+the conservation residual |sum y - sum u| / sum u and the negative mass sum max(-y, 0) / sum u,
+infinite for a non-finite prediction -- and a scenario whose conservation residual exceeds
+1e-4 or that has any negative density (neg_threshold = 0) takes the SSLBM's 20 steps instead
+(the fallback, run by the ensemble kernel).  The SSLBM also judges the rollout: a reference
+ensemble advanced in lock step between the rollout calls gives the error.
 """
 from __future__ import annotations
 
@@ -180,16 +175,20 @@ def evaluate(sur, X, Y, r0, logd, idx, batch):
     return tot / cnt
 
 
-def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_threshold=1e-4,
-            reference=True, err_every=10, reach=K_STEPS):
-    """Surrogate rollout with residual checks and SSLBM fallback.  Returns timings, the
-    fallback count and (with reference=True) the error against an SSLBM run in lock step."""
+def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_threshold=0.0,
+            reference=True, err_every=10, reach=0):
+    """Surrogate rollout with residual checks and SSLBM fallback, run by the library's
+    sslbm_surrogate_rollout in calls of err_every surrogate steps.  Returns timings, the
+    fallback counts and (with reference=True) the error against an SSLBM ensemble advanced in
+    lock step between the calls (the judge; not timed)."""
     import torch
     sc, specs, r0, logd = scenario_specs(scenarios, n, seed)
     u = torch.empty((scenarios, 5, n, n), dtype=torch.float32, device="cuda")
     for i, s in enumerate(sc):
         u[i].copy_(torch.from_numpy(inputs.ensemble_state(s).astype(np.float32)))
     tr0, tlogd = torch.from_numpy(r0).cuda(), torch.from_numpy(logd).cuda()
+    xs = torch.empty((scenarios, 8, n, n), dtype=torch.float32, device="cuda")
+    ys = torch.empty_like(u)
     fb = L.Ensemble(specs)          # runs the fallback steps
     fb.set_tiling(4, 64)
     ref = L.Ensemble(specs) if reference else None
@@ -198,63 +197,96 @@ def rollout(sur, n=256, scenarios=64, steps=100, seed=11, threshold=1e-4, neg_th
         for i in range(scenarios):
             L.sslbm_ensemble_write(ref.e, i, u[i])
     total0 = u.double().sum(dim=(1, 2, 3))
-    fallbacks = 0
-    fail_mass = fail_neg = 0
+    tot = {"surrogate_steps": 0, "fallbacks": 0, "failed_conservation": 0, "failed_nonnegativity": 0,
+           "max_mass_residual": 0.0, "max_neg_residual": 0.0}
     any_negative = 0
     t_sur = 0.0
     err_hist = []
     last_ref = None
-    for step in range(steps):
+    done = 0
+    while done < steps:
+        k = min(err_every, steps - done)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        x = sur.make_input(u, tr0, tlogd)
-        y = sur.infer(x)
-        res = sur.check_project(y, u, reach)
-        any_negative += int((res[:, 1] > 0).sum())
-        fail_mass += int((res[:, 0] > threshold).sum())
-        fail_neg += int((res[:, 1] > neg_threshold).sum())
-        # written so that a NaN residual (a non-finite prediction) fails the test
-        bad = np.nonzero(~((res[:, 0] <= threshold) & (res[:, 1] <= neg_threshold)))[0]
-        if bad.size:
-            fallbacks += int(bad.size)
-            for i in bad:
-                L.sslbm_ensemble_write(fb.e, int(i), u[int(i)])
-            fb.run(K_STEPS)
-            for i in bad:
-                L.sslbm_ensemble_read(fb.e, int(i), y[int(i)])
-        u = y
+        st, res, fell = L.sslbm_surrogate_rollout(sur.f, fb.e, scenarios, k, K_STEPS, u, tr0, tlogd, xs, ys,
+                                                  threshold, neg_threshold, reach)
         torch.cuda.synchronize()
         t_sur += time.perf_counter() - t0
+        for key in ("surrogate_steps", "fallbacks", "failed_conservation", "failed_nonnegativity"):
+            tot[key] += st[key]
+        for key in ("max_mass_residual", "max_neg_residual"):
+            tot[key] = max(tot[key], st[key])
+        any_negative += int((res[:, :, 1] > 0).sum())
+        done += k
         if ref is not None:
-            ref.run(K_STEPS)
-            if (step + 1) % err_every == 0 or step == steps - 1:
-                r = torch.empty_like(u)
-                for i in range(scenarios):
-                    L.sslbm_ensemble_read(ref.e, i, r[i])
-                d2 = ((u.double() - r.double()) ** 2).sum(dim=(0, 2, 3))
-                rms = (d2 / (scenarios * n * n)).sqrt().cpu().numpy()
-                rel = (d2 / (r.double() ** 2).sum(dim=(0, 2, 3))).sqrt().cpu().numpy()
-                # the epidemic curves: each compartment's share of the population, per scenario
-                fu = u.double().mean(dim=(2, 3)) / u.double().mean(dim=(2, 3)).sum(dim=1, keepdim=True)
-                fr = r.double().mean(dim=(2, 3)) / r.double().mean(dim=(2, 3)).sum(dim=1, keepdim=True)
-                frac = (fu - fr).abs()
-                peak = (u[:, 2].amax(dim=(1, 2)).double() / r[:, 2].amax(dim=(1, 2)).double().clamp_min(1e-30) - 1).abs()
-                err_hist.append({"step": step + 1, "rms": rms.tolist(), "rel_l2": rel.tolist(),
-                                 "share_abs_err_mean": frac.mean(dim=0).cpu().numpy().tolist(),
-                                 "share_abs_err_max": frac.amax(dim=0).cpu().numpy().tolist(),
-                                 "peak_I_rel_err_median": float(peak.median())})
-                last_ref = r
+            ref.run(K_STEPS * k)
+            r = torch.empty_like(u)
+            for i in range(scenarios):
+                L.sslbm_ensemble_read(ref.e, i, r[i])
+            d2 = ((u.double() - r.double()) ** 2).sum(dim=(0, 2, 3))
+            rms = (d2 / (scenarios * n * n)).sqrt().cpu().numpy()
+            rel = (d2 / (r.double() ** 2).sum(dim=(0, 2, 3))).sqrt().cpu().numpy()
+            # the epidemic curves: each compartment's share of the population, per scenario
+            fu = u.double().mean(dim=(2, 3)) / u.double().mean(dim=(2, 3)).sum(dim=1, keepdim=True)
+            fr = r.double().mean(dim=(2, 3)) / r.double().mean(dim=(2, 3)).sum(dim=1, keepdim=True)
+            frac = (fu - fr).abs()
+            peak = (u[:, 2].amax(dim=(1, 2)).double() / r[:, 2].amax(dim=(1, 2)).double().clamp_min(1e-30) - 1).abs()
+            err_hist.append({"step": done, "rms": rms.tolist(), "rel_l2": rel.tolist(),
+                             "share_abs_err_mean": frac.mean(dim=0).cpu().numpy().tolist(),
+                             "share_abs_err_max": frac.amax(dim=0).cpu().numpy().tolist(),
+                             "peak_I_rel_err_median": float(peak.median())})
+            last_ref = r
     drift = float(((u.double().sum(dim=(1, 2, 3)) - total0).abs() / total0).max())
     fb.close()
     if ref is not None:
         ref.close()
     return {"scenarios": scenarios, "surrogate_steps": steps, "sslbm_steps_equivalent": steps * K_STEPS,
             "seconds": t_sur, "scenario_steps_per_s": scenarios * steps * K_STEPS / t_sur,
-            "fallbacks": fallbacks, "fallback_rate": fallbacks / (scenarios * steps),
-            "failed_conservation": fail_mass, "failed_nonnegativity": fail_neg,
-            "scenario_steps_with_any_negative": any_negative,
+            "fallbacks": tot["fallbacks"], "fallback_rate": tot["fallbacks"] / (scenarios * steps),
+            "failed_conservation": tot["failed_conservation"], "failed_nonnegativity": tot["failed_nonnegativity"],
+            "max_mass_residual": tot["max_mass_residual"], "max_neg_residual": tot["max_neg_residual"],
+            "scenario_steps_with_any_negative": any_negative, "thresholds": [threshold, neg_threshold],
             "rms_error_vs_sslbm": err_hist, "max_population_drift": drift,
             "min_value": float(u.min()), "state": u, "reference_state": last_ref}
+
+
+def fp64_batched_scenario_steps_per_s(n=256, scenarios=64, steps=20, seed=11):
+    """Plain FP64 SSLBM on the rollout's batch: one solver per scenario (the same scenarios,
+    n x n periodic), all on one stream, each advanced `steps` lattice steps per timed round."""
+    import torch
+    sc, specs, _, _ = scenario_specs(scenarios, n, seed)
+    solvers = [L.Solver(n, n, sp["rates"], d=sp["d"], bc=L.BC_PERIODIC, precision=L.FP64) for sp in specs]
+    for s, c in zip(solvers, sc):
+        s.write(inputs.ensemble_state(c))
+    for s in solvers:
+        s.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in solvers:
+        s.step(steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for s in solvers:
+        s.close()
+    return scenarios * steps / dt
+
+
+def fp32_ensemble_scenario_steps_per_s(n=256, scenarios=64, steps=2000, seed=11):
+    """The FP32 SSLBM ensemble (one persistent launch per run) on the rollout's batch."""
+    import torch
+    sc, specs, _, _ = scenario_specs(scenarios, n, seed)
+    ens = L.Ensemble(specs)
+    ens.set_tiling(4, 64)
+    for i, c in enumerate(sc):
+        ens.write(i, inputs.ensemble_state(c).astype(np.float32))
+    ens.run(K_STEPS)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ens.run(steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ens.close()
+    return scenarios * steps / dt
 
 
 def fp64_scenario_steps_per_s(n=256, steps=40, seed=11):

@@ -39,7 +39,7 @@ def _same_bits(a, b):
 
 
 @pytest.mark.parametrize("on_device", [False, True])
-@pytest.mark.parametrize("precision", [L.FP64, L.FP32, L.FP32_DEV, L.FP32_KAHAN])
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32, L.FP32_DEV, L.FP32_KAHAN, L.FP32_SPLIT])
 def test_resume_gives_the_bits_of_the_uninterrupted_run(precision, on_device):
     nx, ny = 133, 97
     st = inputs.epidemic_state(nx, ny, 7)

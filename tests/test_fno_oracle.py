@@ -1,8 +1,11 @@
 """Pins of the FP64 surrogate oracle (oracle/fno.py).
 
-The spectral convolution evaluated as real DFT products (the factorisation the GPU uses)
-must equal the same operator through numpy's FFT; every parameter gradient of the
-hand-derived backward pass must equal a central finite difference of the forward pass.
+The spectral convolution, as the oracle writes it (numpy's 2D FFT, the kept modes, the real
+part of the inverse FFT), must equal a direct double sum of its definition on small grids,
+and the real-DFT-product factorisation the GPU evaluates (written out here, as a subject
+under test) must equal it; every parameter gradient of the hand-derived backward pass must
+equal a central finite difference of the forward pass; the prediction is nonnegative and
+conserves its input's population for any parameters.
 """
 import numpy as np
 import pytest
@@ -10,14 +13,100 @@ import pytest
 from oracle import fno
 
 
+def _direct_spectral(h, R, n, m):
+    """K(h) as the double sum of its definition: forward sums over every cell for each kept
+    mode, then the inverse sum over the kept modes for every cell (pure loops over modes)."""
+    B, Ci = h.shape[:2]
+    Co = R.shape[1]
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    out = np.zeros((B, Co, n, n))
+    for a, kx in enumerate(fno.kx_modes(n, m)):
+        for ky in range(m):
+            e = np.exp(-2j * np.pi * (kx * x + ky * y) / n)
+            hat = (h * e).sum(axis=(2, 3))                        # [B, Ci]
+            g = hat @ (R[:, :, a, ky, 0] + 1j * R[:, :, a, ky, 1])  # [B, Co]
+            c = 1.0 if ky == 0 else 2.0
+            out += c * (g[:, :, None, None] * np.conj(e)[None, None]).real
+    return out / (n * n)
+
+
+# ---- the GPU's factorisation of the same operator (subject under test) -------------------
+
+def _dft_mats(n, m):
+    """Real DFT factors: Fx (n x 4m: cos, -sin per kept kx), Fy (2m x n: cos, -sin per ky),
+    Fyi (n x 2m: cos, sin) and Fxi (4m x n: cos, -sin)."""
+    x = np.arange(n)
+    thx = 2 * np.pi * np.outer(x, fno.kx_modes(n, m)) / n
+    thy = 2 * np.pi * np.outer(np.arange(m), x) / n
+    Fx = np.empty((n, 4 * m))
+    Fx[:, 0::2], Fx[:, 1::2] = np.cos(thx), -np.sin(thx)
+    Fy = np.empty((2 * m, n))
+    Fy[0::2], Fy[1::2] = np.cos(thy), -np.sin(thy)
+    Fyi = np.empty((n, 2 * m))
+    Fyi[:, 0::2], Fyi[:, 1::2] = np.cos(thy).T, np.sin(thy).T
+    Fxi = np.empty((4 * m, n))
+    Fxi[0::2], Fxi[1::2] = np.cos(thx).T, -np.sin(thx).T
+    return Fx, Fy, Fyi, Fxi
+
+
+def _factorised_spectral(h, R, n, m):
+    """H1 = h Fx, T = Fy H1, hat_h = combine(T), hat_g = mix(hat_h, R), U = expand(hat_g),
+    K(h) = Fyi U Fxi / n^2: the order of the GPU's products."""
+    Fx, Fy, Fyi, Fxi = _dft_mats(n, m)
+    T = Fy @ (h @ Fx)                                     # [B, Ci, 2m, 4m]
+    Tc, Ts = T[..., 0::2, :], T[..., 1::2, :]
+    hat_h = np.swapaxes((Tc[..., 0::2] - Ts[..., 1::2]) + 1j * (Tc[..., 1::2] + Ts[..., 0::2]), -1, -2)
+    hat_g = np.einsum("bikq,iokq->bokq", hat_h, R[..., 0] + 1j * R[..., 1])
+    c = np.where(np.arange(m) == 0, 1.0, 2.0)
+    gT = np.swapaxes(hat_g, -1, -2) * c[:, None]          # [B, Co, m, 2m]
+    U = np.zeros(gT.shape[:-2] + (2 * m, 4 * m))
+    U[..., 0::2, 0::2], U[..., 1::2, 0::2] = gT.real, -gT.imag
+    U[..., 0::2, 1::2], U[..., 1::2, 1::2] = gT.imag, gT.real
+    return (Fyi @ U) @ Fxi / (n * n), hat_h
+
+
+@pytest.mark.parametrize("n,m", [(6, 2), (7, 3), (8, 2)])
+def test_spectral_equals_the_direct_double_sum(n, m):
+    g = np.random.default_rng(10 * n + m)
+    h = g.standard_normal((2, 3, n, n))
+    R = g.standard_normal((3, 4, 2 * m, m, 2))
+    a, hat = fno.spectral(h, R, n, m)
+    b = _direct_spectral(h, R, n, m)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-12 * np.abs(b).max())
+    # hat_h is the forward sum itself
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    kx = fno.kx_modes(n, m)
+    direct = (h[0, 1] * np.exp(-2j * np.pi * (kx[-1] * x + (m - 1) * y) / n)).sum()
+    assert abs(hat[0, 1, -1, m - 1] - direct) <= 1e-12 * np.abs(h).sum()
+
+
 @pytest.mark.parametrize("n,m", [(16, 4), (32, 6), (24, 5)])
-def test_spectral_dft_products_equal_numpy_fft(n, m):
+def test_gpu_factorisation_equals_the_definition(n, m):
     g = np.random.default_rng(n + m)
     h = g.standard_normal((2, 3, n, n))
     R = g.standard_normal((3, 4, 2 * m, m, 2))
-    a, _ = fno.spectral(h, R, n, m)
-    b = fno.spectral_fft(h, R, n, m)
-    np.testing.assert_allclose(a, b, rtol=0, atol=1e-12 * np.abs(b).max())
+    a, ha = fno.spectral(h, R, n, m)
+    b, hb = _factorised_spectral(h, R, n, m)
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-12 * np.abs(a).max())
+    np.testing.assert_allclose(hb, ha, rtol=0, atol=1e-12 * np.abs(ha).max())
+
+
+def test_spectral_backward_is_the_adjoint():
+    """<K(h), w> = <h, K^T w> for random h, w (dh of spectral_backward), and dR equals the
+    derivative of <K(h), w> with respect to R (finite differences of a linear map)."""
+    n, m = 12, 3
+    g = np.random.default_rng(2)
+    h = g.standard_normal((2, 3, n, n))
+    w = g.standard_normal((2, 4, n, n))
+    R = g.standard_normal((3, 4, 2 * m, m, 2))
+    out, hat = fno.spectral(h, R, n, m)
+    dh, dR = fno.spectral_backward(w, hat, R, n, m)
+    assert abs((out * w).sum() - (h * dh).sum()) <= 1e-11 * np.abs(out * w).sum()
+    for idx in [(0, 0, 0, 0, 0), (2, 3, 2 * m - 1, m - 1, 1), (1, 2, m, 1, 0), (0, 1, m - 1, 0, 1)]:
+        Rp = R.copy()
+        Rp[idx] += 1.0
+        delta = (fno.spectral(h, Rp, n, m)[0] * w).sum() - (out * w).sum()
+        assert delta == pytest.approx(dR[idx], rel=1e-9, abs=1e-9)
 
 
 def test_spectral_keeps_only_the_retained_modes():
@@ -132,28 +221,43 @@ def test_loss_gradient_matches_finite_differences(mass_weight, neg_weight):
     assert fno.loss(y, t, x)[0] == pytest.approx(ref, rel=1e-13)
 
 
-def test_prediction_conserves_the_population_exactly():
+@pytest.mark.parametrize("spread", [0.3, 3.0])
+def test_prediction_is_nonnegative_and_conserves_the_population_exactly(spread):
+    """For any parameters (here random, with large ones that push many values below zero
+    before the clamp) the prediction is nonnegative and holds its input's population."""
     W, m, L, H, n = 4, 2, 2, 6, 8
     g = np.random.default_rng(8)
     params = fno.init_params(2, W, m, L, H)
     for k in params:
-        params[k] = params[k] + 0.3 * g.standard_normal(params[k].shape)
+        params[k] = params[k] + spread * g.standard_normal(params[k].shape)
     u = g.uniform(0, 1, (3, 5, n, n))
     u[2, 1:3] *= 1e-5
     x = fno.make_input(u, np.array([1.5, 3.0, 2.0]), np.array([-1.5, -2.5, -2.0]))
-    y, _ = fno.forward(params, x, W, m, L, H)
+    y, cache = fno.forward(params, x, W, m, L, H)
+    assert y.min() >= 0.0
     np.testing.assert_allclose(y.reshape(3, -1).sum(axis=1), u.reshape(3, -1).sum(axis=1), rtol=1e-13)
-    # the raw prediction does not conserve: the correction is doing the work
+    # with the large parameters the clamp acts (some pre-clamp values are negative); either way
+    # the raw prediction does not conserve: the rescale is doing the work
+    assert (cache["a"] < 0).any() or spread < 1
     sig = fno.out_scale(x)[:, :, None, None]
-    v = sig * (x[:, :5] + fno.pointwise(params["Q2"], fno.gelu(fno.pointwise(params["Q1"],
-                                                                           _last_hidden(params, x, W, m, L, H),
-                                                                           params["q1"])), params["q2"]))
+    v = sig * np.maximum(cache["a"], 0.0)
     assert np.abs(v.reshape(3, -1).sum(axis=1) - u.reshape(3, -1).sum(axis=1)).max() > 1e-3
+    # y = v scaled by the ratio of the populations, per sample
+    ratio = u.reshape(3, -1).sum(axis=1) / v.reshape(3, -1).sum(axis=1)
+    np.testing.assert_allclose(y, v * ratio[:, None, None, None], rtol=1e-13, atol=0)
 
 
-def _last_hidden(params, x, W, m, L, H):
-    _, cache = fno.forward(params, x, W, m, L, H)
-    return cache[f"h{L}"]
+def test_all_clamped_prediction_is_zero():
+    """If every value of a sample is clamped (sum v = 0) the prediction is 0: its conservation
+    residual is then 1, so the rollout's check sends it to the SSLBM."""
+    W, m, L, H, n = 4, 2, 1, 6, 8
+    params = fno.init_params(3, W, m, L, H)
+    params["Q2"][:] = 0.0
+    params["q2"][:] = -1e6
+    u = np.random.default_rng(1).uniform(0, 1, (1, 5, n, n))
+    x = fno.make_input(u, np.array([2.0]), np.array([-2.0]))
+    y, _ = fno.forward(params, x, W, m, L, H)
+    assert not y.any()
 
 
 def test_gelu_tanh_form_against_the_erf_definition_and_its_derivative():

@@ -115,7 +115,7 @@ def test_zero_steps_is_identity_and_roundtrip_exact():
 # FP32 variants
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_KAHAN])
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_KAHAN, L.FP32_SPLIT])
 def test_centre_bump_fp32_variants_within_tolerance(precision):
     """Errors are normalised by each compartment's peak over the run: after the epidemic
     wave E and I decay below FP32's smallest subnormal (1.4e-45) while FP64 keeps
@@ -141,7 +141,7 @@ def test_centre_bump_fp32_variants_within_tolerance(precision):
         assert (e2 <= FP32_LONG_TOL).all() and (einf <= FP32_LONG_TOL).all(), (t, e2, einf)
 
 
-@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV])
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_SPLIT])
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("nx,ny", [(5, 3), (130, 1), (1, 70), (37, 23), (1000, 333), (250, 260)])
 def test_blocked_depths_give_identical_bits(precision, bc, nx, ny):
@@ -153,26 +153,28 @@ def test_blocked_depths_give_identical_bits(precision, bc, nx, ny):
     ref.write(wl["state"])
     ref.set_blocking(1)
     refs = {}
+    # every stored plane (the checkpoint holds them as stored: the split S's compensation too)
     for n in range(1, 17):
         ref.step(1)
-        refs[n] = ref.read(dtype=np.float32)
+        refs[n] = ref.checkpoint()[128:].view(np.uint32)
+        if n == 11:
+            base = ref.read()
     for k in range(2, 9):
         s = solver_for(wl, precision)
         s.write(wl["state"])
         s.set_blocking(k)
         s.step(2 * k)
-        got = s.read(dtype=np.float32)
-        assert np.array_equal(got.view(np.uint32), refs[2 * k].view(np.uint32)), (k, nx, ny, bc)
+        got = s.checkpoint()[128:].view(np.uint32)
+        assert np.array_equal(got, refs[2 * k]), (k, nx, ny, bc)
     for k in (3, 8):
         s = solver_for(wl, precision)
         s.write(wl["state"])
         s.set_blocking(k)
         s.step(11)
-        assert np.array_equal(s.read(dtype=np.float32).view(np.uint32), refs[11].view(np.uint32)), (k, 11)
-    base = refs[11]
+        assert np.array_equal(s.checkpoint()[128:].view(np.uint32), refs[11]), (k, 11)
     # and a short run agrees with the FP64 oracle to FP32 accuracy
     want = oracle.sslbm_run(wl["state"], taus(wl["d"]), wl["rates"].as_tuple(), 1.0, bc, 11)
-    assert (rel_max(base.astype(np.float64), want) <= FP32_SHORT_TOL).all()
+    assert (rel_max(base, want) <= FP32_SHORT_TOL).all()
 
 
 @pytest.mark.parametrize("depth,seg_rows", [(3, 12), (3, 16), (3, 50), (3, 333), (8, 32), (8, 41), (6, 100),
@@ -233,7 +235,7 @@ def test_bgk_fp32_centre_bump_within_tolerance():
 # Diagnostics, I/O paths, errors
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_KAHAN])
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_KAHAN, L.FP32_SPLIT])
 def test_diagnostics_match_oracle_on_read_back_state(precision):
     wl = small_workload(517, 211, 0, seed=8)
     s = solver_for(wl, precision)
@@ -247,7 +249,8 @@ def test_diagnostics_match_oracle_on_read_back_state(precision):
 
 
 @pytest.mark.parametrize("precision,scheme", [(L.FP32, L.SCHEME_SSLBM), (L.FP32_DEV, L.SCHEME_SSLBM),
-                                              (L.FP32_KAHAN, L.SCHEME_SSLBM), (L.FP32, L.SCHEME_BGK)])
+                                              (L.FP32_KAHAN, L.SCHEME_SSLBM), (L.FP32_SPLIT, L.SCHEME_SSLBM),
+                                              (L.FP32, L.SCHEME_BGK)])
 def test_diagnostics_on_wide_rows(precision, scheme):
     """Rows of 4099 cells: a thread of the FP32 reduction adds several 4-cell groups of a row
     in its TwoSum pair, and the row's last group holds three cells."""
@@ -272,6 +275,22 @@ def test_nonfinite_state_is_reported_not_trapped():
     with pytest.raises(L.SslbmError) as ei:
         s.diagnostics()
     assert ei.value.status == -5
+
+
+def test_split_storage_holds_s_to_twice_fp32_precision():
+    """FP32_SPLIT keeps S as a value and a compensation plane: a written FP64 S reads back to
+    about 2^-48 relative (FP32 keeps 2^-24), the other compartments as FP32 values."""
+    wl = small_workload(61, 37, 1, seed=31)
+    st = wl["state"].copy()
+    st[0] = 0.9 + 1e-9 * np.arange(61 * 37).reshape(37, 61)  # S with increments below an FP32 ulp
+    s = solver_for(wl, L.FP32_SPLIT)
+    s.write(st)
+    back = s.read()
+    assert np.abs(back[0] - st[0]).max() <= 2.0 ** -47 * np.abs(st[0]).max()
+    assert np.array_equal(back[1:], st[1:].astype(np.float32).astype(np.float64))
+    p = solver_for(wl, L.FP32)
+    p.write(st)
+    assert np.abs(p.read()[0] - st[0]).max() > 1e3 * np.abs(back[0] - st[0]).max()
 
 
 def test_device_tensor_io_and_f32_dtype():
@@ -307,7 +326,7 @@ def test_error_statuses_on_gpu():
     assert ei.value.status == -1
 
 
-@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP64])
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_SPLIT, L.FP64])
 def test_autotune_leaves_state_and_picks_a_valid_configuration(precision):
     wl = small_workload(600, 333, 1, seed=12)
     s = solver_for(wl, precision)

@@ -85,7 +85,7 @@ def test_bgk_fp64_matches_oracle_in_physical_units(bc):
     assert (err <= FP64_TOL).all(), err
 
 
-@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_KAHAN])
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_KAHAN, L.FP32_SPLIT])
 def test_fp32_variants_in_physical_units(precision):
     wl = inputs.paper_test_case(bc=L.BC_NOFLUX)
     s = _solver(wl, precision, s_ref=wl["density"])
@@ -108,7 +108,7 @@ def test_fp32_variants_in_physical_units(precision):
         assert (e2 <= FP32_TOL).all() and (einf <= FP32_TOL).all(), (t, e2, einf)
 
 
-@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV])
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_SPLIT])
 def test_blocked_kernel_gives_one_step_bits_near_tau_one_half(precision):
     """With tau - 1/2 of 1e-3 and 3e-6 the update's diffusion weight is tiny; every blocking
     depth must still give the bits of the one-step kernel."""
@@ -117,10 +117,10 @@ def test_blocked_kernel_gives_one_step_bits_near_tau_one_half(precision):
     ref.write(wl["state"])
     ref.set_blocking(1)
     ref.step(16)
-    base = ref.read(dtype=np.float32)
+    base = ref.checkpoint()[128:]  # every stored plane, as stored
     for k in (2, 4, 8):
         s = _solver(wl, precision, s_ref=wl["density"])
         s.write(wl["state"])
         s.set_blocking(k)
         s.step(16)
-        assert np.array_equal(s.read(dtype=np.float32).view(np.uint32), base.view(np.uint32)), k
+        assert np.array_equal(s.checkpoint()[128:], base), k
