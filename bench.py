@@ -42,6 +42,7 @@ NX = NY = 8192
 LATTICE_STEPS_PER_STEP = 100
 BYTES_PER_CELL_FP32 = 40  # read + write of five FP32 planes per launch
 BYTES_PER_CELL_FP64 = 80
+FP64_FLOPS_PER_CELL = 46  # the SSLBM update per cell-step: four laplacians, sources, update
 BGK_BYTES_PER_CELL_FP32 = 168  # 20 populations + D, read and write
 FD4_PLANES_PER_CELL = 85  # RK4 stage kernels: 15 + 25 + 25 + 20 plane reads and writes per step
 
@@ -512,6 +513,26 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
     g, ms = glups_of(L.FP64, 20, 2)
     out["fp64_glups"] = g
     out["fp64_hbm_frac"] = BYTES_PER_CELL_FP64 * cells / (ms * 1e-3) / 1e9 / hbm
+    # the FP64 kernels are bound by the FP64 arithmetic rate, not by HBM: their roofline is a
+    # measured FP64 rate (cuBLAS DGEMM, 4096^3, best of 5), against the update's 46 FP64
+    # flops per cell-step (an FMA counts 2)
+    A = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    Bm = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    torch.matmul(A, Bm)
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.matmul(A, Bm)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    del A, Bm
+    torch.cuda.empty_cache()
+    out["fp64_measured_peak_tflops"] = 2 * 4096 ** 3 / (best * 1e-3) / 1e12
+    out["fp64_tflops"] = FP64_FLOPS_PER_CELL * g / 1e3
+    out["fp64_frac_of_measured_fp64"] = out["fp64_tflops"] / out["fp64_measured_peak_tflops"]
     g, ms = glups_of(L.FP32, 20, 2, schemes=L.WANT_BGK, bgk=True)
     out["bgk_fp32_glups"] = g
     out["bgk_fp32_hbm_frac"] = BGK_BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm

@@ -757,10 +757,6 @@ int sslbm_diagnostics(sslbm_handle* h, int scheme, double* totals, double* peak_
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(diagnostics)");
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(diagnostics)");
-  unsigned pipe_fault = 0;
-  e = sslbm::pipe_fault_read_and_clear(&pipe_fault, h->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "fused-kernel status");
-  if (pipe_fault) return fail(SSLBM_ERR_TIMEOUT, "a fused launch gave up waiting on its row handoff (state invalid)");
   if (!bgk && h->g.precision == SSLBM_FP32_DEV)
     r[0] = h->p.s_ref * (double)h->g.nx * (double)h->g.ny - r[0];
   if (totals)

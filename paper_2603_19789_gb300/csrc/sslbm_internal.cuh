@@ -275,9 +275,6 @@ cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* c
                                  const void* in, void* out, int depth, int seg_rows,
                                  cudaStream_t s);
 bool blocked_supported(int precision, const GridView& g);
-// Whether a fused launch gave up waiting on its row handoff since the last call (reads the
-// device flag, synchronises s, and clears it).
-cudaError_t pipe_fault_read_and_clear(unsigned* out, cudaStream_t s);
 // Segment length that makes one blocked launch a single wave of resident warps.
 int blocked_default_seg_rows(int precision, const GridView& g, int depth);
 // BGK: one collide-and-stream step; equilibrium initialisation and density of one

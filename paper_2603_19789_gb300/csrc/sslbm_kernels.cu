@@ -2,8 +2,9 @@
 // sources of Eq. sources and the deceased update of Eq. rhoD).
 //
 // Two kernels advance the same update:
-//   step1_kernel    one step per launch, every precision (FP64, FP32, FP32 deviation-S,
-//                   FP32 split-S, FP32 Kahan).  Each thread updates V consecutive cells of a row with
+//   step1_kernel    one step per launch (FP64, FP32, FP32 deviation-S, FP32 split-S).
+//   kahan_stream_kernel  one step per launch of the Kahan storage (ten planes): warps stream
+//                   down column strips through a cp.async ring of rows in shared memory.  Each thread updates V consecutive cells of a row with
 //                   16-byte vector loads (float4 / double2) of the centre, upper and lower
 //                   rows and two scalar edge loads; neighbouring rows come from L1/L2.
 //   pipe_kernel     K steps per launch (temporal blocking, K = 2..8) for FP32, FP32
@@ -25,7 +26,6 @@
 // Both use the same per-cell expressions (sslbm_internal.cuh), so a blocked launch gives
 // the same bits as K one-step launches.
 #include <atomic>
-#include <cstdlib>
 
 #include "bounds.cuh"
 #include "sslbm_internal.cuh"
@@ -50,16 +50,6 @@ struct Vec<float, 4> {
   }
 };
 template <>
-struct Vec<float, 2> {
-  static __device__ __forceinline__ void load(const float* p, float (&v)[2]) {
-    const float2 t = *reinterpret_cast<const float2*>(p);
-    v[0] = t.x; v[1] = t.y;
-  }
-  static __device__ __forceinline__ void store(float* p, const float (&v)[2]) {
-    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
-  }
-};
-template <>
 struct Vec<double, 2> {
   static __device__ __forceinline__ void load(const double* p, double (&v)[2]) {
     const double2 t = *reinterpret_cast<const double2*>(p);
@@ -71,7 +61,7 @@ struct Vec<double, 2> {
 };
 
 template <typename T, int V, int MODE>
-__global__ void __launch_bounds__(256, MODE == MODE_KAHAN ? 2 : 1) step1_kernel(const GridView g, const Coeffs<T> k,
+__global__ void __launch_bounds__(256, 1) step1_kernel(const GridView g, const Coeffs<T> k,
                                                     const T* __restrict__ in, T* __restrict__ out) {
   const int64_t nvec = (g.nx + V - 1) / V;
   const int64_t vx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -106,12 +96,12 @@ __global__ void __launch_bounds__(256, MODE == MODE_KAHAN ? 2 : 1) step1_kernel(
         if (j + 1 < V) {
           if (j + 1 < nvalid) r = c[f][j + 1 < V ? j + 1 : j];
         }
-        if (MODE == MODE_KAHAN || (MODE == MODE_SPLIT && f == 0))
+        if (MODE == MODE_SPLIT && f == 0)
           lap[f][j] = lap5_diff(c[f][j], l, r, u[j], d[j]);
         else
           lap[f][j] = lap5(c[f][j], l, r, u[j], d[j]);
       }
-      if (MODE == MODE_KAHAN || (MODE == MODE_SPLIT && f == 0)) {
+      if (MODE == MODE_SPLIT && f == 0) {
         // the represented value is value - compensation: subtract the compensation's laplacian
         const T* Q = in + (5 + f) * g.plane;
         T qc[V], qu[V], qd[V];
@@ -148,33 +138,6 @@ __global__ void __launch_bounds__(256, MODE == MODE_KAHAN ? 2 : 1) step1_kernel(
         for (int j = 0; j < V; ++j)
           if (j < nvalid) out[5 * g.plane + rc + x0 + j] = ncmp[j];
       }
-    } else if constexpr (MODE == MODE_KAHAN) {
-      T cmp[5][V];
-#pragma unroll
-      for (int f = 0; f < 5; ++f) Vec<T, V>::load(in + (5 + f) * g.plane + rc + x0, cmp[f]);
-#pragma unroll
-      for (int j = 0; j < V; ++j) {
-        float inc[5];
-        seird_increments(k, c[0][j], c[1][j], c[2][j], c[3][j], lap[0][j], lap[1][j], lap[2][j],
-                         lap[3][j], inc);
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          n[f][j] = c[f][j];
-          kahan_add(n[f][j], cmp[f][j], inc[f]);
-        }
-        n[4][j] = D[j];
-        kahan_add(n[4][j], cmp[4][j], inc[4]);
-      }
-      if (nvalid == V) {
-#pragma unroll
-        for (int f = 0; f < 5; ++f) Vec<T, V>::store(out + (5 + f) * g.plane + rc + x0, cmp[f]);
-      } else {
-#pragma unroll
-        for (int f = 0; f < 5; ++f)
-#pragma unroll
-          for (int j = 0; j < V; ++j)
-            if (j < nvalid) out[(5 + f) * g.plane + rc + x0 + j] = cmp[f][j];
-      }
     } else {
 #pragma unroll
       for (int j = 0; j < V; ++j) {
@@ -200,10 +163,115 @@ __global__ void __launch_bounds__(256, MODE == MODE_KAHAN ? 2 : 1) step1_kernel(
   }
 }
 
-// set by a fused launch whose row handoff wait ran out (read and cleared by the diagnostics)
-__device__ unsigned int g_pipe_fault = 0;
+// ---- streaming one-step kernel of the Kahan storage -------------------------------------
+// Each warp owns a strip of kKsCols columns and a segment of kKsSeg rows and walks down it.
+// The rows of the ten planes (values and compensations, one halo column on each side,
+// periodic wrap or mirror at the domain's edges) arrive by cp.async in a ring of kKsRing
+// rows in shared memory, kKsRing - 3 rows ahead of the rows being read; every plane is read
+// from global memory once per step.  Lane l updates columns xs + l and xs + 32 + l with the
+// compensated update: lap5_diff of values minus that of compensations, seird_increments,
+// kahan_add (the per-cell expressions of the earlier two-cells-per-thread Kahan kernel, so
+// results are unchanged; it ran at 38.6 GLUPS on the 8192^2 grid, 46% of HBM).  Ring row
+// layout per plane: index i holds column xs - 4 + i; the 64 interior columns start at
+// index 4 (16-byte aligned for the vector copies), the halos sit at 3 and 68.
+// Ring depth and warps per CTA measured at 8192^2: 8 rows (five in flight) and 2 warps
+// (four CTAs, eight warps per SM) 77.3 GLUPS; 8 and 4 warps 76.5; 7 and 3 warps 68.3;
+// 6 and 4 warps 61.3; 10 and 2 warps (three CTAs per SM) 66.6.
+constexpr int kKsCols = 64, kKsStride = 72, kKsRing = 8, kKsSeg = 128, kKsWarps = 2;
+constexpr int kKsWarpFloats = kKsRing * 10 * kKsStride;
 
-template <int MODE, int K, bool MB>
+__device__ __forceinline__ int64_t ks_col(int64_t x, const GridView& g) {
+  if (x >= 0 && x < g.nx) return x;
+  if (x == -1 || x == g.nx) return link_index(x, g.nx, g.bc);
+  return x < 0 ? 0 : g.nx - 1;  // never a neighbour of a written cell
+}
+
+__global__ void __launch_bounds__(32 * kKsWarps, 4) kahan_stream_kernel(const GridView g, const Coeffs<float> k,
+                                                                       const float* __restrict__ in,
+                                                                       float* __restrict__ out, const int nstrips,
+                                                                       const int nitems) {
+  extern __shared__ __align__(16) float ks_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int item = blockIdx.x * kKsWarps + warp;
+  if (item >= nitems) return;
+  float* ring = ks_smem + (size_t)warp * kKsWarpFloats;
+  const int strip = item % nstrips;
+  const int64_t xs = (int64_t)strip * kKsCols;
+  const int64_t y0 = (int64_t)(item / nstrips) * kKsSeg;
+  const int64_t y1 = y0 + kKsSeg < g.ny ? y0 + kKsSeg : g.ny;
+  const bool vec = xs + kKsCols <= g.nx;
+  const int64_t xl = ks_col(xs - 1, g), xr = ks_col(xs + kKsCols, g);
+  const int64_t q0 = y0 - 1;  // first logical row in the ring
+  auto issue = [&](int64_t q) {  // rows q0 .. y1 (one beyond the segment on each side)
+    const int64_t yq = link_index(q, g.ny, g.bc);
+    if (q <= y1 && SSLBM_IN(yq, 1, g.ny, 15)) {
+      const int64_t row = yq * g.pitch;
+      float* dst = ring + (int)((q - q0) % kKsRing) * (10 * kKsStride);
+      if (vec) {
+        for (int u = lane; u < 10 * 16; u += 32) {
+          const int f = u >> 4, part = u & 15;
+          if (SSLBM_IN(xs + 4 * part, 4, g.nx, 16))
+            cp_async16(dst + f * kKsStride + 4 + 4 * part, in + f * g.plane + row + xs + 4 * part);
+        }
+        if (lane < 20) {
+          const int f = lane % 10;
+          const int64_t xh = lane < 10 ? xl : xr;
+          if (SSLBM_IN(xh, 1, g.nx, 17)) cp_async4(dst + f * kKsStride + (lane < 10 ? 3 : 68), in + f * g.plane + row + xh);
+        }
+      } else {
+        for (int u = lane; u < 10 * 66; u += 32) {
+          const int f = u / 66, i = 3 + u % 66;
+          const int64_t xc = ks_col(xs - 4 + i, g);
+          if (SSLBM_IN(xc, 1, g.nx, 18)) cp_async4(dst + f * kKsStride + i, in + f * g.plane + row + xc);
+        }
+      }
+    }
+    cp_async_commit();  // one group per row, empty beyond the segment
+  };
+  // rows y - 1, y, y + 1 are in use, kKsRing - 3 further rows are in flight
+  for (int64_t q = q0; q < q0 + kKsRing - 1; ++q) issue(q);
+  for (int64_t y = y0; y < y1; ++y) {
+    __syncwarp();  // every lane is done with the slot that row y + kKsRing - 2 takes over
+    issue(y + kKsRing - 2);
+    cp_async_wait<kKsRing - 3>();  // rows up to y + 1 are in
+    __syncwarp();
+    const float* U = ring + (int)((y - 1 - q0) % kKsRing) * (10 * kKsStride);
+    const float* C = ring + (int)((y - q0) % kKsRing) * (10 * kKsStride);
+    const float* N = ring + (int)((y + 1 - q0) % kKsRing) * (10 * kKsStride);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t x = xs + lane + 32 * h;
+      if (x >= g.nx || !SSLBM_IN(y, 1, g.ny, 19)) continue;
+      const int i = 4 + lane + 32 * h;
+      float c[5], cmp[5], lap[4];
+#pragma unroll
+      for (int f = 0; f < 5; ++f) {
+        const float* P = C + f * kKsStride;
+        const float* Q = C + (5 + f) * kKsStride;
+        c[f] = P[i];
+        cmp[f] = Q[i];
+        if (f < 4) {
+          lap[f] = lap5_diff(P[i], P[i - 1], P[i + 1], U[f * kKsStride + i], N[f * kKsStride + i]);
+          lap[f] = sub_rn(lap[f], lap5_diff(Q[i], Q[i - 1], Q[i + 1], U[(5 + f) * kKsStride + i],
+                                            N[(5 + f) * kKsStride + i]));
+        }
+      }
+      float inc[5];
+      seird_increments(k, c[0], c[1], c[2], c[3], lap[0], lap[1], lap[2], lap[3], inc);
+      float* o = out + y * g.pitch + x;
+#pragma unroll
+      for (int f = 0; f < 5; ++f) {
+        float v = c[f], q = cmp[f];
+        kahan_add(v, q, inc[f]);
+        o[f * g.plane] = v;
+        o[(5 + f) * g.plane] = q;
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <int MODE, int K>
 __global__ void __launch_bounds__(32 * K, 16 / K) pipe_kernel(const GridView g, const Coeffs<float> k,
                                                              const float* __restrict__ in,
                                                              float* __restrict__ out,
@@ -213,15 +281,7 @@ __global__ void __launch_bounds__(32 * K, 16 / K) pipe_kernel(const GridView g, 
   const int strip = (int)(blockIdx.x % (unsigned)nstrips);
   const int64_t y0 = (int64_t)(blockIdx.x / (unsigned)nstrips) * seg_rows;
   const int64_t y1 = (y0 + seg_rows < g.ny) ? y0 + seg_rows : g.ny;
-  pipe_tile<MODE, K, false, MB>(sm, g, k, in, out, strip, y0, y1, &g_pipe_fault);
-}
-
-bool pipe_mbar() {
-  static const bool on = [] {
-    const char* v = std::getenv("SSLBM_PIPE_MBAR");
-    return v && v[0] == '1';
-  }();
-  return on;
+  pipe_tile<MODE, K>(sm, g, k, in, out, strip, y0, y1);
 }
 
 template <typename T, int V, int MODE>
@@ -246,13 +306,10 @@ void prefer_shared() {
   if (cudaGetDevice(&dev) != cudaSuccess) return;
   const unsigned long long bit = 1ull << (dev & 63);
   if (done.load(std::memory_order_acquire) & bit) return;
-  auto set = [](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(PipeSmem<K, mode_planes<MODE>()>));
-  };
-  set(pipe_kernel<MODE, K, false>);
-  if constexpr (MODE != MODE_SPLIT) set(pipe_kernel<MODE, K, true>);
+  cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(PipeSmem<K, mode_planes<MODE>()>));
   done.fetch_or(bit, std::memory_order_release);
 }
 
@@ -267,12 +324,27 @@ cudaError_t launch_blocked_t(const GridView& g, const void* coeffs, const void* 
   const int64_t nseg = (g.ny + seg_rows - 1) / seg_rows;
   const int64_t blocks = nstrips * nseg;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  auto kern = pipe_kernel<MODE, K, false>;
-  if constexpr (MODE != MODE_SPLIT)  // the split storage's sixth plane leaves no registers for it
-    if (pipe_mbar()) kern = pipe_kernel<MODE, K, true>;
-  kern<<<(unsigned)blocks, 32 * K, sizeof(PipeSmem<K, mode_planes<MODE>()>), s>>>(
+  pipe_kernel<MODE, K><<<(unsigned)blocks, 32 * K, sizeof(PipeSmem<K, mode_planes<MODE>()>), s>>>(
       g, *static_cast<const Coeffs<float>*>(coeffs), static_cast<const float*>(in),
       static_cast<float*>(out), seg_rows, (int)nstrips);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kahan_stream(const GridView& g, const void* coeffs, const void* in, void* out,
+                                cudaStream_t s) {
+  constexpr size_t smem = sizeof(float) * kKsWarpFloats * kKsWarps;
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && !(done.load(std::memory_order_acquire) & (1ull << (dev & 63)))) {
+    cudaFuncSetAttribute(kahan_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    done.fetch_or(1ull << (dev & 63), std::memory_order_release);
+  }
+  const int64_t nstrips = (g.nx + kKsCols - 1) / kKsCols;
+  const int64_t items = nstrips * ((g.ny + kKsSeg - 1) / kKsSeg);
+  if (items > 0x7fffffffLL - kKsWarps) return cudaErrorInvalidConfiguration;
+  kahan_stream_kernel<<<(unsigned)((items + kKsWarps - 1) / kKsWarps), 32 * kKsWarps, smem, s>>>(
+      g, *static_cast<const Coeffs<float>*>(coeffs), static_cast<const float*>(in), static_cast<float*>(out),
+      (int)nstrips, (int)items);
   return cudaGetLastError();
 }
 
@@ -285,7 +357,7 @@ int default_seg_rows_t(const GridView& g) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_kernel<MODE, K, false>, 32 * K,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_kernel<MODE, K>, 32 * K,
                                                 sizeof(PipeSmem<K, mode_planes<MODE>()>));
   // one wave: as many CTAs as fit on the device at once, split into row segments
   const int64_t resident = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
@@ -346,20 +418,9 @@ cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coe
     case SSLBM_FP32: return launch_step1_t<float, 4, MODE_PLAIN>(g, coeffs, in, out, s);
     case SSLBM_FP32_DEV: return launch_step1_t<float, 4, MODE_DEV>(g, coeffs, in, out, s);
     case SSLBM_FP32_SPLIT: return launch_step1_t<float, 4, MODE_SPLIT>(g, coeffs, in, out, s);
-    // two cells per thread: the compensated update carries twice the state per cell
-    case SSLBM_FP32_KAHAN: return launch_step1_t<float, 2, MODE_KAHAN>(g, coeffs, in, out, s);
+    case SSLBM_FP32_KAHAN: return launch_kahan_stream(g, coeffs, in, out, s);
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t pipe_fault_read_and_clear(unsigned* out, cudaStream_t s) {
-  cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_pipe_fault, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess && *out) {
-    const unsigned zero = 0;
-    e = cudaMemcpyToSymbolAsync(g_pipe_fault, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s);
-  }
-  return e;
 }
 
 cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* coeffs,

@@ -40,30 +40,6 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Row handoff by mbarriers (the MB form of pipe_tile): every lane of the producing (or
-// consuming) warp arrives, so each barrier completes a phase on 32 arrivals.  Waits are
-// bounded: a lane whose wait runs out raises *fault and carries on, so the launch still
-// ends, with its output marked invalid by the flag.
-constexpr unsigned kPipeWaitLimit = 1u << 22;
-__device__ __forceinline__ void pipe_bar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void pipe_bar_arrive(unsigned bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void pipe_bar_wait(unsigned bar, unsigned parity, unsigned* fault) {
-  for (unsigned it = 0; it < kPipeWaitLimit; ++it) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return;
-  }
-  if (fault) atomicExch(fault, 1u);
-}
-
 // r0: level-0 rows (warp 0's lanes read back exactly what they copied);
 // rl[s-1]: the pair of level-s rows from warp s-1 to warp s, double-buffered by iteration
 // parity.  Over 48 KB from K = 5 on: the kernels take it as dynamic shared memory.
@@ -155,18 +131,12 @@ __device__ __forceinline__ void emit_row(PipeSmem<K, NF>& sm, const GridView& g,
 // One iteration of warp s: read the pair of level-s rows b, b+1 (N0, N1) from src (row b+1
 // 128 NF floats further), compute level-(s+1) rows b-1 (from A = b-2, B = b-1, N0) and b (from
 // B, N0, N1), hand them on or write them as rows r, r+1.  Ends with the CTA barrier.
-// Without MB the iteration ends with the CTA barrier.  With MB (the caller has already
-// waited for the slot it reads and the slot it writes), the handoff is per slot: `in_bar`
-// (when nonzero) is the consumer's "empty" barrier of the slot just read, arrived on once
-// the pair is in registers, and `out_bar` the producer's "full" barrier of the slot just
-// written, arrived on after both rows are in it.
-template <int MODE, int K, bool MB = false, int NF = mode_planes<MODE>()>
+template <int MODE, int K, int NF = mode_planes<MODE>()>
 __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g, const Coeffs<float>& k,
                                           const float* src, const float2 (&A)[NF][2], const float2 (&B)[NF][2],
                                           float2 (&N0)[NF][2], float2 (&N1)[NF][2], float* __restrict__ out,
                                           const int s, const int lane, const int par, const bool writer,
-                                          const int64_t xs, const int64_t r, const int64_t y0, const int64_t y1,
-                                          const unsigned in_bar = 0, const unsigned out_bar = 0) {
+                                          const int64_t xs, const int64_t r, const int64_t y0, const int64_t y1) {
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     const float4 t0 = *reinterpret_cast<const float4*>(src + 128 * f);
@@ -176,32 +146,22 @@ __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g
     N1[f][0] = make_float2(t1.x, t1.y);
     N1[f][1] = make_float2(t1.z, t1.w);
   }
-  if (MB && in_bar) pipe_bar_arrive(in_bar);
   float2 M[NF][2];
   cell_row<MODE>(k, A, B, N0, M);
   emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
   cell_row<MODE>(k, B, N0, N1, M);
   emit_row<K, NF>(sm, g, M, out, s, lane, par, 1, writer, xs, r + 1, y0, y1);
-  if (MB) {
-    if (out_bar) pipe_bar_arrive(out_bar);
-  } else {
-    __syncthreads();
-  }
+  __syncthreads();
 }
 
 // WRAP16: periodic grid with nx a multiple of 4 -- every lane's four columns, ghosts
 // included, are one contiguous 16-byte group at the wrapped position, so all loads are
 // L2-only cp.async.cg (required when other CTAs of the same launch wrote the input, since
 // L1 is not coherent).
-// MB: hand rows between neighbouring warps by mbarriers (two per slot: full, empty) instead
-// of one CTA barrier per pair, so a warp waits only for its producer and its consumer and
-// can run up to an iteration ahead of them.  Used once per CTA (the barriers' phases start
-// at zero); a wait that runs out sets *fault (see pipe_bar_wait).
-template <int MODE, int K, bool WRAP16 = false, bool MB = false, int NF = mode_planes<MODE>()>
+template <int MODE, int K, bool WRAP16 = false, int NF = mode_planes<MODE>()>
 __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g, const Coeffs<float>& k,
                                           const float* __restrict__ in, float* __restrict__ out,
-                                          const int strip, const int64_t y0, const int64_t y1,
-                                          unsigned* fault = nullptr) {
+                                          const int strip, const int64_t y0, const int64_t y1) {
   constexpr int HL = (K + 3) / 4;   // halo lanes on each side of the strip
   constexpr int WV = 128 - 8 * HL;  // columns written per strip
   const int lane = threadIdx.x & 31;
@@ -226,12 +186,6 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g
 
   for (int i = threadIdx.x; i < kRing0 * NF * 128; i += 32 * K) (&sm.r0[0][0][0])[i] = 0.f;
   for (int i = threadIdx.x; i < (K - 1) * 2 * 2 * NF * 128; i += 32 * K) (&sm.rl[0][0][0][0][0])[i] = 0.f;
-  // full[l][p] = bars[2l + p], empty[l][p] = bars[2(K-1) + 2l + p] for the link l -> l+1
-  __shared__ __align__(8) unsigned long long bars[MB ? 4 * (K - 1) : 1];
-  if (MB && threadIdx.x == 0) {
-    for (int i = 0; i < 4 * (K - 1); ++i) pipe_bar_init(smem_addr(&bars[i]), 32u);
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
   __syncthreads();
 
   auto issue = [&](int64_t q) {  // warp 0: copy level-0 row q into its ring slot
@@ -283,42 +237,14 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g
     }
     return &sm.rl[s - 1][(t + 1) & 1][0][0][4 * lane];
   };
-  if constexpr (MB) {
-    // Iteration t: warp s (s >= 1) reads slot q = (t+1) & 1 of link s-1, which warp s-1
-    // wrote at iteration t-1 (at t = 0 the zeroed slot 1); warp s (s < K-1) writes slot
-    // p = t & 1 of link s.  Slot 1 is read at t = 0, 2, 4 ... (the read at t = 2j is that
-    // slot's j-th, of the data written at t = 2j-1) and written at t = 1, 3 ...; slot 0 is
-    // written at t = 0, 2 ... and read at t = 1, 3 ....  Hence the phases below.
-    // one base per warp: full of its output link at lb, of its input link at lb - 16, and
-    // the empty barriers 16 (K - 1) bytes further
-    const unsigned lb = smem_addr(&bars[0]) + 16u * (unsigned)s;
-    constexpr unsigned kEmpty = 16u * (K - 1);
-    const bool cons = s >= 1, prod = s < K - 1;
-    auto step = [&](int t, float2 (&a)[NF][2], float2 (&b)[NF][2], float2 (&c)[NF][2], float2 (&d)[NF][2]) {
-      const unsigned q = (unsigned)(t + 1) & 1u, p = (unsigned)t & 1u, h = (unsigned)(t >> 1);
-      // both waits before any row is loaded: the pair to read is in, the slot to write is free
-      if (cons && t >= 1) pipe_bar_wait(lb - 16u + 8u * q, (q ? h - 1u : h) & 1u, fault);
-      if (prod && t >= 1) pipe_bar_wait(lb + kEmpty + 8u * p, (p ? h : h + 1u) & 1u, fault);
-      pipe_pair<MODE, K, true>(sm, g, k, fetch(t), a, b, c, d, out, s, lane, (int)p, writer, xs, rbase + 2 * t, y0,
-                               y1, cons ? lb - 16u + kEmpty + 8u * q : 0u, prod ? lb + 8u * p : 0u);
-    };
-    int t = 0;
-    for (; t + 2 <= nt; t += 2) {
-      step(t, RA, RB, RC, RD);
-      step(t + 1, RC, RD, RA, RB);
-    }
-    if (t < nt) step(t, RA, RB, RC, RD);
-  } else {
-    int t = 0;
-    for (; t + 2 <= nt; t += 2) {
-      pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0, y1);
-      pipe_pair<MODE, K>(sm, g, k, fetch(t + 1), RC, RD, RA, RB, out, s, lane, (t + 1) & 1, writer, xs,
-                         rbase + 2 * t + 2, y0, y1);
-    }
-    if (t < nt)
-      pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0,
-                         y1);
+  int t = 0;
+  for (; t + 2 <= nt; t += 2) {
+    pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0, y1);
+    pipe_pair<MODE, K>(sm, g, k, fetch(t + 1), RC, RD, RA, RB, out, s, lane, (t + 1) & 1, writer, xs,
+                       rbase + 2 * t + 2, y0, y1);
   }
+  if (t < nt)
+    pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0, y1);
   if (s == 0) cp_async_wait<0>();
 }
 
