@@ -618,8 +618,11 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
 def surrogate_timing(L, torch, stream, hbm, batch=64, n=256, reps=10):
     """The learned surrogate's kernels at the rollout's batch (64 scenarios, 256 x 256): one
     surrogate step = make_input + inference + residual check/projection, with seeded initial
-    parameters (the time does not depend on their values).  Without fallbacks a step
-    advances every scenario by 20 lattice steps."""
+    parameters (the time does not depend on their values); then the library's rollout call
+    on the same scenarios under the workload's fallback rule, against the plain FP64 SSLBM
+    batched over the scenarios and the FP32 ensemble.  A surrogate step advances every
+    scenario by 20 lattice steps."""
+    from paper_2603_19789_gb300 import inputs
     from paper_2603_19789_gb300 import surrogate as S
     sur = L.Surrogate(n=n, max_batch=batch)
     sur.set_params(S.initial_params())
@@ -647,13 +650,37 @@ def surrogate_timing(L, torch, stream, hbm, batch=64, n=256, reps=10):
     step_ms = timed(lambda: (sur.make_input(u, r0, ld), sur.infer(x, y), sur.check_project(y, u)))
     flops = batch * S.forward_flops(n)
     nbytes = batch * S.forward_bytes(n)
+    # the library's rollout call on the workload's scenarios, under the workload's rule
+    # (conservation residual <= 1e-4, no negative density), 10 surrogate steps per call
+    sc, specs, sr0, slogd = S.scenario_specs(batch, n, 11)
+    us = torch.stack([torch.from_numpy(inputs.ensemble_state(c).astype(np.float32)) for c in sc]).cuda()
+    tr0, tld = torch.from_numpy(sr0).cuda(), torch.from_numpy(slogd).cuda()
+    xs = torch.empty((batch, 8, n, n), dtype=torch.float32, device="cuda")
+    ys = torch.empty_like(us)
+    fb = L.Ensemble(specs)
+    fb.set_tiling(4, 64)
+    L.sslbm_surrogate_rollout(sur.f, fb.e, batch, 2, S.K_STEPS, us, tr0, tld, xs, ys, 1e-4, 0.0, 0, False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, _, _ = L.sslbm_surrogate_rollout(sur.f, fb.e, batch, 10, S.K_STEPS, us, tr0, tld, xs, ys, 1e-4, 0.0, 0,
+                                         False)
+    torch.cuda.synchronize()
+    roll_s = time.perf_counter() - t0
+    fb.close()
     sur.close()
+    roll = batch * 10 * S.K_STEPS / roll_s
+    fp64_b = S.fp64_batched_scenario_steps_per_s(n, batch)
+    fp32_e = S.fp32_ensemble_scenario_steps_per_s(n, batch, steps=400)
     return {"batch": batch, "n": n, "params": S.initial_params().size, "fused": True,
             "infer_ms": infer_ms, "gflop_per_inference": flops / 1e9, "tflops": flops / (infer_ms * 1e-3) / 1e12,
             "hbm_bytes_per_inference": nbytes, "hbm_frac": nbytes / (infer_ms * 1e-3) / 1e9 / hbm,
             "surrogate_step_ms": step_ms,
-            "scenario_steps_per_s_without_fallback": batch * 20 / (step_ms * 1e-3),
-            "note": "trained rollout with checks, fallbacks and the SSLBM judge: studies.py surrogate"}
+            "rollout_scenario_steps_per_s": roll, "rollout_fallbacks": st["fallbacks"],
+            "rollout_rule": "conservation residual <= 1e-4 and no negative density",
+            "fp64_batched_scenario_steps_per_s": fp64_b, "rollout_vs_fp64_batched": roll / fp64_b,
+            "fp32_ensemble_scenario_steps_per_s": fp32_e, "rollout_vs_fp32_ensemble": roll / fp32_e,
+            "note": "seeded initial parameters (the time does not depend on them); the trained network's "
+                    "fallback rate and error against the SSLBM: studies.py surrogate"}
 
 
 def ensemble_timing(L, torch, stream, n_scen=512, steps=5000, err_scen=6, fp64_steps=40, tiling=None):
