@@ -278,6 +278,7 @@ def loss(y, target, x, mass_weight=0.0, neg_weight=0.0):
 # ---- per-element error scale of a BF16 evaluation ----------------------------------------
 
 U_BF16 = 2.0 ** -8      # unit roundoff of BF16 (8 significant bits)
+TANH_ERR = 2.0 ** -9    # bound on the absolute error of an approximate tanh inside an evaluated GELU
 
 
 def sq_spectral(v, R, n, m):
@@ -365,18 +366,21 @@ def rounding_variances(params, x, cache, W=32, m=12, L=4, H=64, u=U_BF16):
     activations in BF16 and evaluates each spectral convolution as factorised DFT products
     (along x, then y, and back) whose operands and partial transforms are rounded to BF16,
     with FP32 accumulation (neglected) and the same parameters.  Each rounding is modelled as
-    an independent relative error of variance q = u^2/3 (uniform in [-u, u]), carried forward
-    to first order by a second pass over the definition on squares:
+    an independent relative error of variance q = u^2/3 (uniform in [-u, u]), and the tanh
+    inside each GELU as one with absolute error uniform in [-TANH_ERR, TANH_ERR] (variance
+    qt = TANH_ERR^2/3, entering the GELU as 0.5 z dt), carried forward to first order by a
+    second pass over the definition on squares:
         V(h0) = q h0^2
         V(z_l) = Ks_l(V(h_{l-1})) + B_l^2 V(h_{l-1}) + Sr_l(h_{l-1})
-        V(h_l) = gelu'(z_l)^2 V(z_l) + q h_l^2          (h_L = z_L: no gelu')
-        V(zp) = Q1^2 V(h_L),  V(p) = gelu'(zp)^2 V(zp) + q p^2,   V(delta) = Q2^2 V(p)
+        V(h_l) = gelu'(z_l)^2 V(z_l) + qt (z_l/2)^2 + q h_l^2     (h_L = z_L: no gelu)
+        V(zp) = Q1^2 V(h_L),  V(p) = gelu'(zp)^2 V(zp) + qt (zp/2)^2 + q p^2,  V(delta) = Q2^2 V(p)
         V(v) = sigma^2 V(delta),   V(y) = r^2 V(v) + y^2 sum V(v) / (sum v)^2
     with Ks = sq_spectral, Sr = spectral_rounding_var (the product's own roundings) and
     squares of matrices taken elementwise (V(h_l) etc. with q for u^2/3 as above).  Returns
     a dict with these variances (keys h0..hL, z1..zL, zp, p, delta, y)."""
     n = x.shape[-1]
     q = u * u / 3.0
+    qt = TANH_ERR * TANH_ERR / 3.0
     h = cache["h0"]
     out = {"h0": q * h * h}
     V = out["h0"]
@@ -385,12 +389,16 @@ def rounding_variances(params, x, cache, W=32, m=12, L=4, H=64, u=U_BF16):
         Vz = (sq_spectral(V, R, n, m) + pointwise(Bl * Bl, V)
               + spectral_rounding_var(h, cache[f"hat{l}"], R, n, m, q))
         h = cache[f"h{l}"]
-        gz = gelu_grad(cache[f"z{l}"]) if l < L else 1.0
-        V = gz * gz * Vz + q * h * h
+        if l < L:
+            zl = cache[f"z{l}"]
+            gz = gelu_grad(zl)
+            V = gz * gz * Vz + qt * (0.5 * zl) ** 2 + q * h * h
+        else:
+            V = Vz + q * h * h
         out[f"z{l}"], out[f"h{l}"] = Vz, V
     out["zp"] = pointwise(params["Q1"] ** 2, V)
     gp = gelu_grad(cache["zp"])
-    out["p"] = gp * gp * out["zp"] + q * cache["p"] ** 2
+    out["p"] = gp * gp * out["zp"] + qt * (0.5 * cache["zp"]) ** 2 + q * cache["p"] ** 2
     out["delta"] = pointwise(params["Q2"] ** 2, out["p"])
     sig = out_scale(x)[:, :, None, None]
     Vv = sig * sig * out["delta"]
