@@ -89,7 +89,8 @@ def test_workspace_bytes_layout(lib):
 
 @pytest.mark.parametrize("kw", [dict(nx=0, ny=5), dict(nx=5, ny=-1), dict(nx=4, ny=4, dx=0.0),
                                 dict(nx=4, ny=4, dt=float("nan")), dict(nx=4, ny=4, bc=2),
-                                dict(nx=4, ny=4, precision=7), dict(nx=4, ny=4, schemes=0),
+                                dict(nx=4, ny=4, precision=7), dict(nx=4, ny=4, precision=5),
+                                dict(nx=4, ny=4, schemes=0),
                                 dict(nx=1 << 31, ny=1)])
 def test_invalid_grids_rejected(lib, kw):
     args = dict(nx=4, ny=4)
@@ -100,11 +101,28 @@ def test_invalid_grids_rejected(lib, kw):
     assert ei.value.status == -1
 
 
-def test_bgk_in_deviation_precision_unsupported(lib):
-    g = L.make_grid(8, 8, precision=L.FP32_DEV, schemes=L.WANT_BGK)
+@pytest.mark.parametrize("precision", [L.FP32_DEV, L.FP32_SPLIT, L.FP32_KAHAN])
+def test_bgk_in_the_fp32_storage_variants_unsupported(lib, precision):
+    g = L.make_grid(8, 8, precision=precision, schemes=L.WANT_BGK)
     with pytest.raises(L.SslbmError) as ei:
         L.sslbm_workspace_bytes(g)
     assert ei.value.status == -7
+
+
+@pytest.mark.parametrize("lattice", [L.LATTICE_D2Q9, L.LATTICE_D2Q5_SLBM, L.LATTICE_D2Q5_VARD])
+def test_split_storage_only_on_d2q5(lib, lattice):
+    g = L.make_grid(8, 8, precision=L.FP32_SPLIT, lattice=lattice)
+    with pytest.raises(L.SslbmError) as ei:
+        L.sslbm_workspace_bytes(g)
+    assert ei.value.status == -7
+
+
+def test_split_storage_workspace_holds_six_planes(lib):
+    pitch = 128
+    g = L.make_grid(100, 7, precision=L.FP32_SPLIT)
+    n = L.sslbm_workspace_bytes(g)
+    assert n >= 2 * 6 * pitch * 7 * 4
+    assert n < L.sslbm_workspace_bytes(L.make_grid(100, 7, precision=L.FP32_KAHAN))
 
 
 def _create_status(grid, params, ws=0, nbytes=0):
