@@ -271,6 +271,10 @@ __device__ __forceinline__ void seird_cell2(const Coeffs<float>& k, float2 x0, f
 // deviation-S and FP32 split-S).  seg_rows > 0 is the blocked kernel's row-segment length.
 cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coeffs, const void* in,
                                void* out, cudaStream_t s);
+// The streaming one-step kernel (stream.cu) of the FP32 storages: FP32, FP32 deviation-S,
+// FP32 split-S and the Kahan storage.
+cudaError_t launch_stream_d2q5(int precision, const GridView& g, const void* coeffs, const void* in, void* out,
+                               cudaStream_t s);
 cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* coeffs,
                                  const void* in, void* out, int depth, int seg_rows,
                                  cudaStream_t s);

@@ -8,9 +8,10 @@
 // planes of 1 give Eq. (sslbm_final_clean).  Neighbours: the periodic wrap, or the cell
 // itself, whose difference is zero (no flux through a wall).
 //
-// One step per launch, V cells of a row per thread as in the one-step D2Q5 kernel: vector
-// loads of the cell's row and of the rows above and below, two scalar loads for the columns
-// left and right of the group.  The four link coefficients of a cell are formed once and
+// FP64: one step per launch, V = 2 cells of a row per thread: vector loads of the cell's row
+// and of the rows above and below, two scalar loads for the columns left and right of the
+// group.  FP32 runs the same per-cell operations in the streaming one-step kernel
+// (stream.cu).  The four link coefficients of a cell are formed once and
 // serve all four mobile compartments; the flux sum follows the link order c_1 .. c_4
 // (+x, +y, -x, -y), each term rounded on its own.
 #include <cuda_runtime.h>
@@ -23,16 +24,6 @@ namespace {
 
 template <typename T, int V>
 struct VRow;
-template <>
-struct VRow<float, 4> {
-  static __device__ __forceinline__ void load(const float* p, float (&v)[4]) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
-  }
-  static __device__ __forceinline__ void store(float* p, const float (&v)[4]) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  }
-};
 template <>
 struct VRow<double, 2> {
   static __device__ __forceinline__ void load(const double* p, double (&v)[2]) {
@@ -194,7 +185,7 @@ cudaError_t launch_sslbm_vard_step(int precision, const GridView& g, const void*
                                    const void* ky, const void* in, void* out, cudaStream_t s) {
   switch (precision) {
     case SSLBM_FP64: return launch_t<double, 2>(g, coeffs, kx, ky, in, out, s);
-    case SSLBM_FP32: return launch_t<float, 4>(g, coeffs, kx, ky, in, out, s);
+    case SSLBM_FP32: return launch_stream_vard(g, coeffs, kx, ky, in, out, s);
     default: return cudaErrorInvalidValue;
   }
 }

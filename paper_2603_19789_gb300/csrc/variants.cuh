@@ -9,6 +9,11 @@ namespace sslbm {
 // one SSLBM step on the D2Q9 lattice (FP64 or FP32)
 cudaError_t launch_sslbm9_step1(int precision, const GridView& g, const void* coeffs, const void* in, void* out,
                                 cudaStream_t s);
+// the FP32 D2Q9 step and the FP32 varying-diffusion step through the streaming one-step
+// kernel (stream.cu)
+cudaError_t launch_stream_d2q9(const GridView& g, const void* coeffs, const void* in, void* out, cudaStream_t s);
+cudaError_t launch_stream_vard(const GridView& g, const void* coeffs, const void* kx, const void* ky, const void* in,
+                               void* out, cudaStream_t s);
 
 // one step of the two-pass SLBM (FP64 or FP32): predictor into pred (4 planes of the state's
 // layout), then the corrector into out; tm1[c] = tau_c - 1

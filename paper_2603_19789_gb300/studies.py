@@ -29,6 +29,11 @@ timing     -- the cost comparison of Sec. IV (Table tab:timing): time per step o
 
 train-step -- time of one surrogate training step (B = 16, 256 x 256, default network).
 
+variant    -- one update variant (lattice x storage, one step per launch or the default
+              blocking) on the n x n multi-seed no-flux workload: GLUPS and the fraction of
+              the measured HBM bandwidth its algorithmic bytes per cell-step reach; the
+              profiling command of the one-step kernels.
+
 Usage:  python -m paper_2603_19789_gb300.studies precision [--n 4096] [--steps 50000]
         [--checkpoints 5] [--out FILE]
         python -m paper_2603_19789_gb300.studies surrogate [--n 256] [--trajectories 2000]
@@ -36,6 +41,8 @@ Usage:  python -m paper_2603_19789_gb300.studies precision [--n 4096] [--steps 5
         python -m paper_2603_19789_gb300.studies accuracy [--out FILE]
         python -m paper_2603_19789_gb300.studies timing [--out FILE]
         python -m paper_2603_19789_gb300.studies train-step [--n 256] [--out FILE]
+        python -m paper_2603_19789_gb300.studies variant --lattice d2q9 --precision fp32
+        [--n 8192] [--steps 20] [--depth 1] [--out FILE]
 """
 from __future__ import annotations
 
@@ -295,9 +302,68 @@ def train_step_timing(n=256, batch=16, steps=50):
     return {"n": n, "batch": batch, "steps": steps, "ms_per_step": a.elapsed_time(b) / steps, "loss": loss}
 
 
+# algorithmic bytes per cell-step of each (lattice, precision) at one step per launch: every
+# plane the update reads, read once, and every plane it writes, written once
+_ESIZE = {L.FP64: 8, L.FP32: 4, L.FP32_DEV: 4, L.FP32_SPLIT: 4, L.FP32_KAHAN: 4}
+_PLANES = {L.FP32_SPLIT: 6, L.FP32_KAHAN: 10}
+LATTICES = {"d2q5": L.LATTICE_D2Q5, "d2q9": L.LATTICE_D2Q9, "vard": L.LATTICE_D2Q5_VARD}
+PRECISION_NAMES = {"fp64": L.FP64, "fp32": L.FP32, "fp32_dev": L.FP32_DEV, "fp32_split": L.FP32_SPLIT,
+                   "fp32_kahan": L.FP32_KAHAN}
+
+
+def _measured_hbm_gbs():
+    """The measured copy bandwidth of the GPU (MEASURED_PEAKS.json at the repository root), or None."""
+    import os
+    try:
+        with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def variant_timing(lattice="d2q9", precision="fp32", n=8192, steps=20, depth=1):
+    """GLUPS of one update variant on the n x n multi-seed no-flux workload (inputs larger than
+    L2 at the default size): 4 warm-up steps, then `steps` steps timed with CUDA events on the
+    solver's stream.  depth applies to the D2Q5 storages (1 = one step per launch, 0 = the
+    default blocking).  hbm_frac = algorithmic bytes per cell-step (every plane read once and
+    written once; the two scale planes read once on the varying-diffusion lattice) over the
+    step time, divided by the measured HBM bandwidth; it is reported for one-step launches only."""
+    import torch
+    lat, prec = LATTICES[lattice], PRECISION_NAMES[precision]
+    wl = inputs.roofline_workload(n, n)
+    st = wl["state"] if prec == L.FP64 else np.ascontiguousarray(wl["state"].astype(np.float32))
+    s = L.Solver(n, n, wl["rates"].as_tuple(), d=wl["d"], bc=wl["bc"], precision=prec, lattice=lat)
+    if lat == L.LATTICE_D2Q5_VARD:
+        s.set_diffusivity_scale(*inputs.mobility_fields(n, n, 7))
+    s.write(st)
+    if lat == L.LATTICE_D2Q5 and depth:
+        s.set_blocking(depth)
+    s.step(4)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s.stream)
+    s.step(steps)
+    b.record(s.stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / steps
+    s.close()
+    planes = _PLANES.get(prec, 5)
+    nbytes = _ESIZE[prec] * (2 * planes + (2 if lat == L.LATTICE_D2Q5_VARD else 0))
+    out = {"lattice": lattice, "precision": precision, "n": n, "steps": steps, "ms_per_step": ms,
+           "glups": n * n / (ms * 1e-3) / 1e9, "bytes_per_cell_step": nbytes}
+    one_step = lat != L.LATTICE_D2Q5 or depth == 1 or prec in (L.FP64, L.FP32_KAHAN)
+    peak = _measured_hbm_gbs()
+    if one_step and peak:
+        out["hbm_frac"] = nbytes * n * n / (ms * 1e-3) / 1e9 / peak
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["precision", "surrogate", "accuracy", "timing", "train-step"])
+    ap.add_argument("study", choices=["precision", "surrogate", "accuracy", "timing", "train-step", "variant"])
+    ap.add_argument("--lattice", default="d2q9", choices=sorted(LATTICES))
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISION_NAMES))
+    ap.add_argument("--depth", type=int, default=1)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--steps", type=int, default=50000)
     ap.add_argument("--checkpoints", type=int, default=6)
@@ -308,9 +374,12 @@ def main(argv=None):
     args = ap.parse_args(argv)
     from . import build
     build.build()
-    if args.study in ("accuracy", "timing", "train-step"):
+    if args.study in ("accuracy", "timing", "train-step", "variant"):
         res = (accuracy_study() if args.study == "accuracy" else
-               timing_study() if args.study == "timing" else train_step_timing(n=args.n or 256))
+               timing_study() if args.study == "timing" else
+               variant_timing(args.lattice, args.precision, n=args.n or 8192,
+                              steps=args.steps if args.steps != 50000 else 20, depth=args.depth)
+               if args.study == "variant" else train_step_timing(n=args.n or 256))
         text = json.dumps(res, indent=1)
         if args.out:
             with open(args.out, "w") as fh:

@@ -2,12 +2,13 @@
 
 compute-sanitizer is not available on these GPUs, so the library has a build in which the
 hot-path kernels -- the fused pipeline tile (single grid and ensemble), the one-step
-kernel, the BGK step and the diagnostics -- test every row and column index of their global
-loads and stores before using it, skip and record any that is out of range.  This test
-compiles that build and, in a child process that loads it, drives a sweep of tiny, odd and
-non-multiple-of-tile grids through every precision, every blocking depth with default and
-short odd segments, both boundary conditions, BGK, the diagnostics and a mixed-size
-ensemble.  The checks must record nothing.  A probe first proves the recording path: one
+kernels (the streaming kernel of the FP32 storages, the D2Q9 lattice and the varying
+diffusion among them), the BGK step and the diagnostics -- test every row and column index
+of their global loads and stores before using it, skip and record any that is out of range.
+This test compiles that build and, in a child process that loads it, drives a sweep of tiny,
+odd and non-multiple-of-tile grids through every precision, every blocking depth with
+default and short odd segments, both boundary conditions, BGK, the FP32 D2Q9 and
+varying-diffusion steps, the diagnostics and a mixed-size ensemble.  The checks must record nothing.  A probe first proves the recording path: one
 check of an index past its limit (no memory access behind it) is counted and reported with
 its value, limit and site; one inside is not.
 """
@@ -63,6 +64,14 @@ for nx, ny in sizes:
                 s.write(st, scheme=L.SCHEME_BGK)
                 s.bgk_step(3)
                 s.diagnostics(L.SCHEME_BGK)
+            s.close()
+        for lat in (L.LATTICE_D2Q9, L.LATTICE_D2Q5_VARD):
+            s = L.Solver(nx, ny, rates, d=d, bc=bc, precision=L.FP32, lattice=lat)
+            if lat == L.LATTICE_D2Q5_VARD:
+                s.set_diffusivity_scale(*inputs.mobility_fields(nx, ny, 3))
+            s.write(st)
+            s.step(3)
+            runs += 1
             s.close()
 out["runs"] = runs
 
