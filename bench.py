@@ -536,10 +536,11 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
     g, ms = glups_of(L.FP32, 20, 2, schemes=L.WANT_BGK, bgk=True)
     out["bgk_fp32_glups"] = g
     out["bgk_fp32_hbm_frac"] = BGK_BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm
-    # the D2Q9 lattice (one step per launch, shared-memory tiles): 40 / 80 B per cell-step
+    # the D2Q9 lattice, one step per launch: 40 / 80 B per cell-step
     for prec, name, nbytes in ((L.FP32, "fp32", BYTES_PER_CELL_FP32), (L.FP64, "fp64", BYTES_PER_CELL_FP64)):
         s9 = L.Solver(NX, NY, rates, d=wl["d"], bc=wl["bc"], precision=prec, lattice=L.LATTICE_D2Q9)
         s9.write(state32 if prec == L.FP32 else state64)
+        s9.set_blocking(1)
         s9.step(2)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -551,6 +552,17 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
         ms = a.elapsed_time(b) / reps
         out[f"d2q9_{name}_glups"] = cells / (ms * 1e-3) / 1e9
         out[f"d2q9_{name}_hbm_frac"] = nbytes * cells / (ms * 1e-3) / 1e9 / hbm
+        if prec == L.FP32:
+            # the temporal-blocked D2Q9 kernel at the autotuned depth, 48 steps per measurement
+            depth, seg, _ = s9.autotune()
+            s9.step(depth)
+            torch.cuda.synchronize()
+            a.record(stream)
+            s9.step(48)
+            b.record(stream)
+            b.synchronize()
+            out["d2q9_fp32_blocked_glups"] = cells * 48 / (a.elapsed_time(b) * 1e-3) / 1e9
+            out["d2q9_fp32_blocked_depth"] = depth
         s9.close()
         del s9
         torch.cuda.empty_cache()

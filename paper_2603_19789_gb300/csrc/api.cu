@@ -192,6 +192,29 @@ int sslbm_workspace_bytes(const sslbm_grid* g, size_t* bytes) {
   return SSLBM_OK;
 }
 
+// The D2Q5 FP32 storages and the FP32 D2Q9 lattice have the temporal-blocked kernel.
+static bool can_block(const sslbm_handle* h) {
+  if (h->g.lattice == SSLBM_LATTICE_D2Q5) return sslbm::blocked_supported(h->g.precision, h->gv);
+  return h->g.lattice == SSLBM_LATTICE_D2Q9 && h->g.precision == SSLBM_FP32;
+}
+
+// One pass of k steps (k = 1: the one-step kernel) from the current buffer into the spare one,
+// on the D2Q5 or D2Q9 lattice.
+static cudaError_t launch_pass(sslbm_handle* h, int k, int seg) {
+  const bool q9 = h->g.lattice == SSLBM_LATTICE_D2Q9;
+  void* out = h->s_buf[1 - h->s_cur];
+  if (k == 1)
+    return q9 ? sslbm::launch_sslbm9_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur], out, h->stream)
+              : sslbm::launch_sslbm_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur], out, h->stream);
+  return q9 ? sslbm::launch_sslbm9_blocked(h->gv, &h->cf, h->s_buf[h->s_cur], out, k, seg, h->stream)
+            : sslbm::launch_sslbm_blocked(h->g.precision, h->gv, &h->cf, h->s_buf[h->s_cur], out, k, seg, h->stream);
+}
+
+static int default_seg(const sslbm_handle* h, int k) {
+  return h->g.lattice == SSLBM_LATTICE_D2Q9 ? sslbm::blocked9_default_seg_rows(h->gv, k)
+                                            : sslbm::blocked_default_seg_rows(h->g.precision, h->gv, k);
+}
+
 int sslbm_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_t ws_bytes,
                  void* stream, sslbm_handle** out) {
   if (!out) return fail(SSLBM_ERR_BAD_ARG, "out is NULL");
@@ -287,7 +310,7 @@ int sslbm_create(const sslbm_grid* g, const sslbm_params* p, void* dev_ws, size_
     for (int b = 0; b < 2; ++b) h->b_buf[b] = h->ws + L.off_b[b];
   if (g->lattice == SSLBM_LATTICE_D2Q5_SLBM) h->pred = h->ws + L.off_pred;
   if (g->lattice == SSLBM_LATTICE_D2Q5_VARD) h->kappa = h->ws + L.off_kappa;
-  h->depth = sslbm::blocked_supported(g->precision, h->gv) ? 4 : 1;
+  h->depth = can_block(h) ? 4 : 1;
   DeviceGuard dg(h->device);
   // zero state buffers (and their row padding) so every scheme starts from a defined state
   e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);
@@ -505,17 +528,7 @@ int sslbm_step(sslbm_handle* h, int64_t n) {
     }
     return SSLBM_OK;
   }
-  if (h->g.lattice == SSLBM_LATTICE_D2Q9) {
-    for (; n > 0; --n) {
-      cudaError_t e = sslbm::launch_sslbm9_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur],
-                                                 h->s_buf[1 - h->s_cur], h->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "D2Q9 step launch");
-      h->s_cur = 1 - h->s_cur;
-      h->s_steps += 1;
-    }
-    return SSLBM_OK;
-  }
-  const bool blocked = sslbm::blocked_supported(h->g.precision, h->gv);
+  const bool blocked = can_block(h);
   while (n > 0) {
     int k = 1;
     cudaError_t e;
@@ -528,14 +541,12 @@ int sslbm_step(sslbm_handle* h, int64_t n) {
       k = (int)((n + passes - 1) / passes);
       int seg = h->seg_rows;
       if (seg <= 0) {
-        if (!h->seg_cache[k]) h->seg_cache[k] = sslbm::blocked_default_seg_rows(h->g.precision, h->gv, k);
+        if (!h->seg_cache[k]) h->seg_cache[k] = default_seg(h, k);
         seg = h->seg_cache[k];
       }
-      e = sslbm::launch_sslbm_blocked(h->g.precision, h->gv, &h->cf, h->s_buf[h->s_cur],
-                                      h->s_buf[1 - h->s_cur], k, seg, h->stream);
+      e = launch_pass(h, k, seg);
     } else {
-      e = sslbm::launch_sslbm_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur],
-                                    h->s_buf[1 - h->s_cur], h->stream);
+      e = launch_pass(h, 1, 0);
     }
     if (e != cudaSuccess) return cuda_fail(e, "SSLBM step launch");
     h->s_cur = 1 - h->s_cur;
@@ -771,9 +782,10 @@ int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows) {
   if (!h) return fail(SSLBM_ERR_BAD_ARG, "handle is NULL");
   if (k < 0 || k > SSLBM_MAX_DEPTH) return fail(SSLBM_ERR_BAD_ARG, "k=%d", k);
   if (seg_rows < 0) return fail(SSLBM_ERR_BAD_ARG, "seg_rows=%d", seg_rows);
-  const bool blocked = sslbm::blocked_supported(h->g.precision, h->gv) && h->g.lattice == SSLBM_LATTICE_D2Q5;
+  const bool blocked = can_block(h);
   if (!blocked && k > 1)
-    return fail(SSLBM_ERR_UNSUPPORTED, "temporal blocking is provided for FP32, FP32_DEV and FP32_SPLIT on D2Q5");
+    return fail(SSLBM_ERR_UNSUPPORTED,
+                "temporal blocking is provided for FP32, FP32_DEV and FP32_SPLIT on D2Q5 and for FP32 on D2Q9");
   h->depth = k == 0 ? (blocked ? 4 : 1) : k;
   if (seg_rows > 0 && seg_rows < 4 * h->depth) seg_rows = 4 * h->depth;
   h->seg_rows = seg_rows;
@@ -782,10 +794,11 @@ int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows) {
 
 namespace {
 struct TuneKey {
-  int device, precision, bc;
+  int device, precision, lattice, bc;
   int64_t nx, ny;
   bool operator<(const TuneKey& o) const {
-    return std::tie(device, precision, bc, nx, ny) < std::tie(o.device, o.precision, o.bc, o.nx, o.ny);
+    return std::tie(device, precision, lattice, bc, nx, ny) <
+           std::tie(o.device, o.precision, o.lattice, o.bc, o.nx, o.ny);
   }
 };
 struct TuneResult {
@@ -795,14 +808,6 @@ struct TuneResult {
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneResult> g_tune_cache;
 
-// Launch one pass of (depth, seg) from the current buffer into the spare one.
-cudaError_t tune_launch(sslbm_handle* h, int depth, int seg) {
-  if (depth == 1)
-    return sslbm::launch_sslbm_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur],
-                                     h->s_buf[1 - h->s_cur], h->stream);
-  return sslbm::launch_sslbm_blocked(h->g.precision, h->gv, &h->cf, h->s_buf[h->s_cur],
-                                     h->s_buf[1 - h->s_cur], depth, seg, h->stream);
-}
 }  // namespace
 
 int sslbm_autotune(sslbm_handle* h, double budget_ms, int* depth_out, int* seg_out,
@@ -811,9 +816,10 @@ int sslbm_autotune(sslbm_handle* h, double budget_ms, int* depth_out, int* seg_o
   if (st) return st;
   if (!(budget_ms >= 0)) return fail(SSLBM_ERR_BAD_ARG, "budget_ms must be >= 0");
   if (budget_ms == 0) budget_ms = 300.0;
-  if (h->g.lattice != SSLBM_LATTICE_D2Q5) return fail(SSLBM_ERR_UNSUPPORTED, "the autotuner tunes the D2Q5 kernels");
+  if (h->g.lattice != SSLBM_LATTICE_D2Q5 && h->g.lattice != SSLBM_LATTICE_D2Q9)
+    return fail(SSLBM_ERR_UNSUPPORTED, "the autotuner tunes the D2Q5 and D2Q9 kernels");
   DeviceGuard dg(h->device);
-  const TuneKey key{h->device, h->g.precision, h->g.bc, h->g.nx, h->g.ny};
+  const TuneKey key{h->device, h->g.precision, h->g.lattice, h->g.bc, h->g.nx, h->g.ny};
   TuneResult best{1, 0, 0.0};
   bool cached = false;
   {
@@ -827,9 +833,9 @@ int sslbm_autotune(sslbm_handle* h, double budget_ms, int* depth_out, int* seg_o
   if (!cached) {
     std::vector<std::pair<int, int>> cand;
     cand.push_back({1, 0});
-    if (sslbm::blocked_supported(h->g.precision, h->gv)) {
+    if (can_block(h)) {
       for (int d = 2; d <= SSLBM_MAX_DEPTH; ++d) {
-        const int base = sslbm::blocked_default_seg_rows(h->g.precision, h->gv, d);
+        const int base = default_seg(h, d);
         int segs[3] = {base, base / 2, base * 2};
         for (int sg : segs) {
           if (sg < 4 * d) sg = 4 * d;
@@ -852,7 +858,7 @@ int sslbm_autotune(sslbm_handle* h, double budget_ms, int* depth_out, int* seg_o
     for (auto& c : cand) {
       // one untimed launch (also sizes the repetition count), then the timed repetitions
       e = cudaEventRecord(e0, h->stream);
-      if (e == cudaSuccess) e = tune_launch(h, c.first, c.second);
+      if (e == cudaSuccess) e = launch_pass(h, c.first, c.second);
       if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms1 = 0.f;
@@ -861,7 +867,7 @@ int sslbm_autotune(sslbm_handle* h, double budget_ms, int* depth_out, int* seg_o
       if (reps < 2) reps = 2;
       if (reps > 50) reps = 50;
       if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = tune_launch(h, c.first, c.second);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_pass(h, c.first, c.second);
       if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;

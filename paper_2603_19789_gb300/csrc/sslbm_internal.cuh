@@ -14,7 +14,9 @@
 
 namespace sslbm {
 
-enum Mode { MODE_PLAIN = 0, MODE_DEV = 1, MODE_KAHAN = 2, MODE_SPLIT = 3 };
+// MODE_D2Q9 / MODE_D2Q9_NOFLUX: the plain FP32 storage on the D2Q9 lattice (the nine-point
+// laplacian), periodic or with bounce-back walls, for the temporal-blocked pipeline.
+enum Mode { MODE_PLAIN = 0, MODE_DEV = 1, MODE_KAHAN = 2, MODE_SPLIT = 3, MODE_D2Q9 = 4, MODE_D2Q9_NOFLUX = 5 };
 
 // Stored planes per state of a mode: the five compartments, plus the compensation of S
 // (MODE_SPLIT) or of all five (MODE_KAHAN), which follow them.
@@ -279,6 +281,10 @@ cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* c
                                  const void* in, void* out, int depth, int seg_rows,
                                  cudaStream_t s);
 bool blocked_supported(int precision, const GridView& g);
+// The D2Q9 lattice (plain FP32 storage): K fused steps per launch, and its default segment.
+cudaError_t launch_sslbm9_blocked(const GridView& g, const void* coeffs, const void* in, void* out, int depth,
+                                  int seg_rows, cudaStream_t s);
+int blocked9_default_seg_rows(const GridView& g, int depth);
 // Segment length that makes one blocked launch a single wave of resident warps.
 int blocked_default_seg_rows(int precision, const GridView& g, int depth);
 // BGK: one collide-and-stream step; equilibrium initialisation and density of one

@@ -6,7 +6,9 @@
 //                   and two scalar edge loads; neighbouring rows come from L1/L2.  The FP32
 //                   storages advance one step per launch in the streaming kernel (stream.cu).
 //   pipe_kernel     K steps per launch (temporal blocking, K = 2..8) for FP32, FP32
-//                   deviation-S and FP32 split-S (a sixth plane), as a pipeline of K warps per
+//                   deviation-S and FP32 split-S (a sixth plane), and FP32 on the D2Q9 lattice
+//                   (periodic, or no-flux with the bounce-back substituted into the row
+//                   update), as a pipeline of K warps per
 //                   CTA: warp s computes level s+1 of the time-step wavefront.  A CTA owns a
 //                   128-column strip (4 columns per lane, 16-byte accesses) with a K-column halo
 //                   on each side and streams down a segment of rows, two rows per step of the
@@ -98,7 +100,10 @@ __global__ void __launch_bounds__(32 * K, 16 / K) pipe_kernel(const GridView g, 
   const int strip = (int)(blockIdx.x % (unsigned)nstrips);
   const int64_t y0 = (int64_t)(blockIdx.x / (unsigned)nstrips) * seg_rows;
   const int64_t y1 = (y0 + seg_rows < g.ny) ? y0 + seg_rows : g.ny;
-  pipe_tile<MODE, K>(sm, g, k, in, out, strip, y0, y1);
+  if (MODE == MODE_D2Q9_NOFLUX && strip != 0 && strip != nstrips - 1)
+    pipe_tile<MODE, K, false, false>(sm, g, k, in, out, strip, y0, y1);  // no wall column in this strip
+  else
+    pipe_tile<MODE, K>(sm, g, k, in, out, strip, y0, y1);
 }
 
 cudaError_t launch_step1_fp64(const GridView& g, const void* coeffs, const void* in, void* out, cudaStream_t s) {
@@ -202,6 +207,16 @@ int blocked_default_seg_rows(int precision, const GridView& g, int depth) {
   if (precision == SSLBM_FP32_DEV) return default_seg_rows_mode<MODE_DEV>(g, depth);
   if (precision == SSLBM_FP32_SPLIT) return default_seg_rows_mode<MODE_SPLIT>(g, depth);
   return 0;
+}
+
+int blocked9_default_seg_rows(const GridView& g, int depth) {
+  return g.bc != 0 ? default_seg_rows_mode<MODE_D2Q9_NOFLUX>(g, depth) : default_seg_rows_mode<MODE_D2Q9>(g, depth);
+}
+
+cudaError_t launch_sslbm9_blocked(const GridView& g, const void* coeffs, const void* in, void* out, int depth,
+                                  int seg_rows, cudaStream_t s) {
+  if (g.bc != 0) return launch_blocked_mode<MODE_D2Q9_NOFLUX>(g, coeffs, in, out, depth, seg_rows, s);
+  return launch_blocked_mode<MODE_D2Q9>(g, coeffs, in, out, depth, seg_rows, s);
 }
 
 bool blocked_supported(int precision, const GridView&) {

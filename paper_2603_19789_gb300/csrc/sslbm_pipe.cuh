@@ -15,7 +15,9 @@
 // uniform stencil keeps consistent, so no boundary logic is needed inside the pipeline.
 // The arithmetic is the packed form of seird_cell / seird_cell_dev / seird_cell_split,
 // bit-identical to the one-step kernel; the split storage of S carries its compensation as a
-// sixth plane through the pipeline.
+// sixth plane through the pipeline.  On the D2Q9 lattice (cell_row9) the row update is the
+// nine-point one of the one-step D2Q9 kernel; its no-flux walls (bounce-back) are not a ghost
+// image, so they are substituted into the row update instead.
 #pragma once
 #include "bounds.cuh"
 #include "sslbm_internal.cuh"
@@ -96,6 +98,76 @@ __device__ __forceinline__ void cell_row(const Coeffs<float>& k, const float2 (&
   }
 }
 
+// Level s+1 of row C on the D2Q9 lattice (plain FP32 storage) from level-s rows P, C, N: the
+// nine-point laplacian (4 ((l + r) + (u + d)) + ((ne + nw) + (se + sw)) - 20 c) / 6 of S, E,
+// I, R, each pair sum formed as row[x-1] + row[x+1] (equal bits: the sums commute), then the
+// packed cell update -- the operations of the one-step D2Q9 kernel.  One column pair at a
+// time (h = 0: columns 0, 1 with the left neighbours shuffled in; h = 1: columns 2, 3 with the
+// right ones), which keeps the live registers within the pipeline's budget.
+//
+// WALLS (no-flux): a link that leaves the domain sees the cell's own value (halfway
+// bounce-back).  At x = 0 (column 0 of the lane with xs = 0) the shuffled-in left neighbours
+// of the three rows are replaced by the centre; at x = nx - 1 (column jr of its lane) the right
+// neighbours, in-lane or shuffled in, likewise.  ROWWALL (row 0 or ny - 1, warp-uniform): the
+// row beyond the wall enters as the centre, its pair sum as centre + centre.  Cells outside the
+// domain are never read by an in-domain cell, so their values do not matter.
+template <bool ROWWALL, bool WALLS>
+__device__ __forceinline__ void cell_row9(const Coeffs<float>& k, const GridView& g, const float2 (&P)[5][2],
+                                          const float2 (&C)[5][2], const float2 (&N)[5][2], float2 (&M)[5][2],
+                                          const int64_t xs, const int64_t row) {
+  constexpr unsigned kFull = 0xffffffffu;
+  const bool wl = WALLS && xs == 0;                            // column 0 is x = 0
+  const int jr = WALLS ? (int)(g.nx - 1 - xs) : -1;           // column of x = nx - 1, if in [0, 3]
+  const bool wd = ROWWALL && row == 0, wu = ROWWALL && row == g.ny - 1;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float2 lp[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      // the neighbour beyond the pair: from the lane on the left (h = 0) or on the right (h = 1)
+      float XP = h == 0 ? __shfl_up_sync(kFull, P[f][1].y, 1) : __shfl_down_sync(kFull, P[f][0].x, 1);
+      float XC = h == 0 ? __shfl_up_sync(kFull, C[f][1].y, 1) : __shfl_down_sync(kFull, C[f][0].x, 1);
+      float XN = h == 0 ? __shfl_up_sync(kFull, N[f][1].y, 1) : __shfl_down_sync(kFull, N[f][0].x, 1);
+      // right neighbours of the pair's columns inside the lane (h = 0: columns 1, 2; h = 1:
+      // column 3), the centre where that column is x = nx - 1
+      float RP, RC, RN;
+      if (h == 0) {
+        if (WALLS && wl) XP = XC = XN = C[f][0].x;
+        const bool w0 = WALLS && jr == 0;
+        RP = w0 ? C[f][0].x : P[f][0].y;
+        RC = w0 ? C[f][0].x : C[f][0].y;
+        RN = w0 ? C[f][0].x : N[f][0].y;
+      } else {
+        if (WALLS && jr == 3) XP = XC = XN = C[f][1].y;
+        const bool w2 = WALLS && jr == 2;
+        RP = w2 ? C[f][1].x : P[f][1].y;
+        RC = w2 ? C[f][1].x : C[f][1].y;
+        RN = w2 ? C[f][1].x : N[f][1].y;
+      }
+      float2 hP, hC, hN;
+      if (h == 0) {
+        const bool w1 = WALLS && jr == 1;
+        hP = make_float2(__fadd_rn(XP, RP), __fadd_rn(P[f][0].x, w1 ? C[f][0].y : P[f][1].x));
+        hC = make_float2(__fadd_rn(XC, RC), __fadd_rn(C[f][0].x, w1 ? C[f][0].y : C[f][1].x));
+        hN = make_float2(__fadd_rn(XN, RN), __fadd_rn(N[f][0].x, w1 ? C[f][0].y : N[f][1].x));
+      } else {
+        hP = make_float2(__fadd_rn(P[f][0].y, RP), __fadd_rn(P[f][1].x, XP));
+        hC = make_float2(__fadd_rn(C[f][0].y, RC), __fadd_rn(C[f][1].x, XC));
+        hN = make_float2(__fadd_rn(N[f][0].y, RN), __fadd_rn(N[f][1].x, XN));
+      }
+      float2 Pv = P[f][h], Nv = N[f][h];
+      if (ROWWALL) {
+        if (wd) Pv = C[f][h], hP = add2(C[f][h], C[f][h]);
+        if (wu) Nv = C[f][h], hN = add2(C[f][h], C[f][h]);
+      }
+      lp[f] = mul2(fma2(splat2(-20.f), C[f][h], fma2(splat2(4.f), add2(hC, add2(Nv, Pv)), add2(hN, hP))),
+                   splat2(1.f / 6.f));
+    }
+    seird_cell2<0>(k, C[0][h], C[1][h], C[2][h], C[3][h], C[4][h], lp[0], lp[1], lp[2], lp[3], M[0][h], M[1][h],
+                   M[2][h], M[3][h], M[4][h]);
+  }
+}
+
 // Hand level-(s+1) row M to the next warp (slot row `which` of parity par) or, for the last
 // warp, write it to row r of the output.
 template <int K, int NF>
@@ -131,25 +203,44 @@ __device__ __forceinline__ void emit_row(PipeSmem<K, NF>& sm, const GridView& g,
 // One iteration of warp s: read the pair of level-s rows b, b+1 (N0, N1) from src (row b+1
 // 128 NF floats further), compute level-(s+1) rows b-1 (from A = b-2, B = b-1, N0) and b (from
 // B, N0, N1), hand them on or write them as rows r, r+1.  Ends with the CTA barrier.
-template <int MODE, int K, int NF = mode_planes<MODE>()>
+template <int MODE, int K, bool COLW = true, int NF = mode_planes<MODE>()>
 __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g, const Coeffs<float>& k,
                                           const float* src, const float2 (&A)[NF][2], const float2 (&B)[NF][2],
                                           float2 (&N0)[NF][2], float2 (&N1)[NF][2], float* __restrict__ out,
                                           const int s, const int lane, const int par, const bool writer,
                                           const int64_t xs, const int64_t r, const int64_t y0, const int64_t y1) {
+  auto load_row = [&](const float* p, float2 (&R)[NF][2]) {
 #pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    const float4 t0 = *reinterpret_cast<const float4*>(src + 128 * f);
-    const float4 t1 = *reinterpret_cast<const float4*>(src + 128 * NF + 128 * f);
-    N0[f][0] = make_float2(t0.x, t0.y);
-    N0[f][1] = make_float2(t0.z, t0.w);
-    N1[f][0] = make_float2(t1.x, t1.y);
-    N1[f][1] = make_float2(t1.z, t1.w);
-  }
+    for (int f = 0; f < NF; ++f) {
+      const float4 t = *reinterpret_cast<const float4*>(p + 128 * f);
+      R[f][0] = make_float2(t.x, t.y);
+      R[f][1] = make_float2(t.z, t.w);
+    }
+  };
   float2 M[NF][2];
-  cell_row<MODE>(k, A, B, N0, M);
-  emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
-  cell_row<MODE>(k, B, N0, N1, M);
+  if constexpr (MODE == MODE_D2Q9 || MODE == MODE_D2Q9_NOFLUX) {
+    // the second row of the pair is read after the first is done: fewer live registers for
+    // the nine-point stencil's wider neighbourhood
+    constexpr bool W = MODE == MODE_D2Q9_NOFLUX;
+    const int64_t row = r + 3 * (K - 1 - s);  // the first row this warp computes (r: the last warp's)
+    load_row(src, N0);
+    if (W && (row == 0 || row == g.ny - 1))
+      cell_row9<true, W>(k, g, A, B, N0, M, xs, row);
+    else
+      cell_row9<false, W && COLW>(k, g, A, B, N0, M, xs, row);
+    emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
+    load_row(src + 128 * NF, N1);
+    if (W && (row + 1 == 0 || row + 1 == g.ny - 1))
+      cell_row9<true, W>(k, g, B, N0, N1, M, xs, row + 1);
+    else
+      cell_row9<false, W && COLW>(k, g, B, N0, N1, M, xs, row + 1);
+  } else {
+    load_row(src, N0);
+    load_row(src + 128 * NF, N1);
+    cell_row<MODE>(k, A, B, N0, M);
+    emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
+    cell_row<MODE>(k, B, N0, N1, M);
+  }
   emit_row<K, NF>(sm, g, M, out, s, lane, par, 1, writer, xs, r + 1, y0, y1);
   __syncthreads();
 }
@@ -158,7 +249,9 @@ __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g
 // included, are one contiguous 16-byte group at the wrapped position, so all loads are
 // L2-only cp.async.cg (required when other CTAs of the same launch wrote the input, since
 // L1 is not coherent).
-template <int MODE, int K, bool WRAP16 = false, int NF = mode_planes<MODE>()>
+// COLW = false: the strip holds neither x = 0 nor x = nx - 1 (D2Q9 no-flux: no column wall
+// code in its rows).
+template <int MODE, int K, bool WRAP16 = false, bool COLW = true, int NF = mode_planes<MODE>()>
 __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g, const Coeffs<float>& k,
                                           const float* __restrict__ in, float* __restrict__ out,
                                           const int strip, const int64_t y0, const int64_t y1) {
@@ -239,12 +332,14 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g
   };
   int t = 0;
   for (; t + 2 <= nt; t += 2) {
-    pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0, y1);
-    pipe_pair<MODE, K>(sm, g, k, fetch(t + 1), RC, RD, RA, RB, out, s, lane, (t + 1) & 1, writer, xs,
-                       rbase + 2 * t + 2, y0, y1);
+    pipe_pair<MODE, K, COLW>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0,
+                             y1);
+    pipe_pair<MODE, K, COLW>(sm, g, k, fetch(t + 1), RC, RD, RA, RB, out, s, lane, (t + 1) & 1, writer, xs,
+                             rbase + 2 * t + 2, y0, y1);
   }
   if (t < nt)
-    pipe_pair<MODE, K>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0, y1);
+    pipe_pair<MODE, K, COLW>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0,
+                             y1);
   if (s == 0) cp_async_wait<0>();
 }
 

@@ -42,7 +42,7 @@ Usage:  python -m paper_2603_19789_gb300.studies precision [--n 4096] [--steps 5
         python -m paper_2603_19789_gb300.studies timing [--out FILE]
         python -m paper_2603_19789_gb300.studies train-step [--n 256] [--out FILE]
         python -m paper_2603_19789_gb300.studies variant --lattice d2q9 --precision fp32
-        [--n 8192] [--steps 20] [--depth 1] [--out FILE]
+        [--n 8192] [--steps 20] [--depth 1] [--bc periodic|noflux] [--out FILE]
 """
 from __future__ import annotations
 
@@ -321,22 +321,24 @@ def _measured_hbm_gbs():
         return None
 
 
-def variant_timing(lattice="d2q9", precision="fp32", n=8192, steps=20, depth=1):
+def variant_timing(lattice="d2q9", precision="fp32", n=8192, steps=20, depth=1, bc=None):
     """GLUPS of one update variant on the n x n multi-seed no-flux workload (inputs larger than
     L2 at the default size): 4 warm-up steps, then `steps` steps timed with CUDA events on the
-    solver's stream.  depth applies to the D2Q5 storages (1 = one step per launch, 0 = the
-    default blocking).  hbm_frac = algorithmic bytes per cell-step (every plane read once and
-    written once; the two scale planes read once on the varying-diffusion lattice) over the
-    step time, divided by the measured HBM bandwidth; it is reported for one-step launches only."""
+    solver's stream.  depth applies where a blocked kernel exists (the D2Q5 FP32 storages, FP32
+    D2Q9): 1 = one step per launch, 0 = the default blocking, k = k steps per launch.
+    hbm_frac = algorithmic bytes per cell-step (every plane read once and written once; the
+    two scale planes read once on the varying-diffusion lattice) over the step time, divided
+    by the measured HBM bandwidth; it is reported for one-step launches only."""
     import torch
     lat, prec = LATTICES[lattice], PRECISION_NAMES[precision]
     wl = inputs.roofline_workload(n, n)
     st = wl["state"] if prec == L.FP64 else np.ascontiguousarray(wl["state"].astype(np.float32))
-    s = L.Solver(n, n, wl["rates"].as_tuple(), d=wl["d"], bc=wl["bc"], precision=prec, lattice=lat)
+    bc = wl["bc"] if bc is None else bc
+    s = L.Solver(n, n, wl["rates"].as_tuple(), d=wl["d"], bc=bc, precision=prec, lattice=lat)
     if lat == L.LATTICE_D2Q5_VARD:
         s.set_diffusivity_scale(*inputs.mobility_fields(n, n, 7))
     s.write(st)
-    if lat == L.LATTICE_D2Q5 and depth:
+    if lat in (L.LATTICE_D2Q5, L.LATTICE_D2Q9) and depth:
         s.set_blocking(depth)
     s.step(4)
     torch.cuda.synchronize()
@@ -349,9 +351,10 @@ def variant_timing(lattice="d2q9", precision="fp32", n=8192, steps=20, depth=1):
     s.close()
     planes = _PLANES.get(prec, 5)
     nbytes = _ESIZE[prec] * (2 * planes + (2 if lat == L.LATTICE_D2Q5_VARD else 0))
-    out = {"lattice": lattice, "precision": precision, "n": n, "steps": steps, "ms_per_step": ms,
+    out = {"lattice": lattice, "precision": precision, "n": n, "bc": "periodic" if bc == L.BC_PERIODIC else "no-flux",
+           "depth": depth, "steps": steps, "ms_per_step": ms,
            "glups": n * n / (ms * 1e-3) / 1e9, "bytes_per_cell_step": nbytes}
-    one_step = lat != L.LATTICE_D2Q5 or depth == 1 or prec in (L.FP64, L.FP32_KAHAN)
+    one_step = lat not in (L.LATTICE_D2Q5, L.LATTICE_D2Q9) or depth == 1 or prec in (L.FP64, L.FP32_KAHAN)
     peak = _measured_hbm_gbs()
     if one_step and peak:
         out["hbm_frac"] = nbytes * n * n / (ms * 1e-3) / 1e9 / peak
@@ -364,6 +367,7 @@ def main(argv=None):
     ap.add_argument("--lattice", default="d2q9", choices=sorted(LATTICES))
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISION_NAMES))
     ap.add_argument("--depth", type=int, default=1)
+    ap.add_argument("--bc", default=None, choices=["periodic", "noflux"], help="variant: the workload's (no-flux) if unset")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--steps", type=int, default=50000)
     ap.add_argument("--checkpoints", type=int, default=6)
@@ -378,7 +382,8 @@ def main(argv=None):
         res = (accuracy_study() if args.study == "accuracy" else
                timing_study() if args.study == "timing" else
                variant_timing(args.lattice, args.precision, n=args.n or 8192,
-                              steps=args.steps if args.steps != 50000 else 20, depth=args.depth)
+                              steps=args.steps if args.steps != 50000 else 20, depth=args.depth,
+                              bc=None if args.bc is None else (L.BC_PERIODIC if args.bc == "periodic" else L.BC_NOFLUX))
                if args.study == "variant" else train_step_timing(n=args.n or 256))
         text = json.dumps(res, indent=1)
         if args.out:

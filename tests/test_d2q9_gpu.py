@@ -93,8 +93,91 @@ def test_stability_range_and_what_it_does_not_run():
     assert e.value.status == L.SSLBM_ERR_UNSUPPORTED
     with pytest.raises(L.SslbmError):
         L.Solver(8, 8, RATES, d=D, lattice=L.LATTICE_D2Q9, precision=L.FP32_DEV)
-    s = L.Solver(64, 64, RATES, d=D, lattice=L.LATTICE_D2Q9, precision=L.FP32)
+    # temporal blocking: FP32 only
+    s = L.Solver(64, 64, RATES, d=D, lattice=L.LATTICE_D2Q9, precision=L.FP64)
     with pytest.raises(L.SslbmError) as e:
         s.set_blocking(4)
     assert e.value.status == L.SSLBM_ERR_UNSUPPORTED
     s.close()
+    s = L.Solver(64, 64, RATES, d=D, lattice=L.LATTICE_D2Q9, precision=L.FP32)
+    assert s.get_blocking()[0] == 4  # the default where the blocked kernel exists
+    s.set_blocking(8)
+    s.close()
+
+
+def _checkpoint_bits(s):
+    return s.checkpoint()[128:].view(np.uint32)
+
+
+@pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
+@pytest.mark.parametrize("nx,ny", [(131, 77), (257, 130), (64, 300), (120, 45), (5, 7), (1, 1), (2, 9)])
+def test_fp32_blocked_depths_give_identical_bits(bc, nx, ny):
+    """The temporal-blocked D2Q9 kernel (the pipeline tile with the nine-point stencil and
+    the bounce-back substitution at walls) against the one-step kernel, bit for bit: 2k steps
+    at depth k are two passes of exactly that depth; then 11 steps, which mix depths.  The
+    widths put the strip's halo columns on both sides of the domain and the walls inside a
+    lane's four columns."""
+    st = inputs.epidemic_state(nx, ny, 7 * nx + ny).astype(np.float32)
+    ref = L.Solver(nx, ny, RATES, d=D, bc=bc, precision=L.FP32, lattice=L.LATTICE_D2Q9)
+    ref.write(st)
+    ref.set_blocking(1)
+    refs = {}
+    for n in range(1, 17):
+        ref.step(1)
+        refs[n] = _checkpoint_bits(ref)
+    ref.close()
+    for k in range(2, 9):
+        s = L.Solver(nx, ny, RATES, d=D, bc=bc, precision=L.FP32, lattice=L.LATTICE_D2Q9)
+        s.write(st)
+        s.set_blocking(k)
+        s.step(2 * k)
+        assert np.array_equal(_checkpoint_bits(s), refs[2 * k]), (k, nx, ny, bc)
+        s.close()
+    for k in (3, 8):
+        s = L.Solver(nx, ny, RATES, d=D, bc=bc, precision=L.FP32, lattice=L.LATTICE_D2Q9)
+        s.write(st)
+        s.set_blocking(k)
+        s.step(11)
+        assert np.array_equal(_checkpoint_bits(s), refs[11]), (k, 11)
+        s.close()
+
+
+@pytest.mark.parametrize("depth,seg_rows", [(3, 12), (3, 50), (8, 32), (8, 41), (6, 100), (7, 28), (2, 8)])
+def test_fp32_blocked_segment_lengths_give_identical_bits(depth, seg_rows):
+    """2 x depth steps under no-flux: two passes of this depth with this row-segment length
+    (segment seams inside the grid and next to the walls)."""
+    st = inputs.epidemic_state(300, 333, 5).astype(np.float32)
+    ref = L.Solver(300, 333, RATES, d=D, bc=L.BC_NOFLUX, precision=L.FP32, lattice=L.LATTICE_D2Q9)
+    ref.write(st)
+    ref.set_blocking(1)
+    ref.step(2 * depth)
+    want = _checkpoint_bits(ref)
+    ref.close()
+    s = L.Solver(300, 333, RATES, d=D, bc=L.BC_NOFLUX, precision=L.FP32, lattice=L.LATTICE_D2Q9)
+    s.write(st)
+    s.set_blocking(depth, seg_rows)
+    s.step(2 * depth)
+    assert np.array_equal(_checkpoint_bits(s), want)
+    s.close()
+
+
+def test_fp32_blocked_long_run_matches_oracle_and_conserves():
+    """200 steps at the autotuned blocking against the FP64 oracle (FP32 tolerance), and the
+    population conserved to FP32 rounding under no-flux (bounce-back keeps it exactly in
+    exact arithmetic)."""
+    nx, ny = 96, 70
+    st = inputs.epidemic_state(nx, ny, 21)
+    s = L.Solver(nx, ny, RATES, d=D, bc=L.BC_NOFLUX, precision=L.FP32, lattice=L.LATTICE_D2Q9)
+    s.write(st.astype(np.float32))
+    depth, seg, _ = s.autotune(50.0)
+    assert 1 <= depth <= 8 and (depth == 1 or seg >= 4 * depth)
+    assert np.array_equal(s.read(dtype=np.float32), st.astype(np.float32))  # the tuner left the state
+    s.step(200)
+    got = s.read()
+    tot, _ = s.diagnostics()
+    s.close()
+    tau = [oracle.tau_from_d(d) for d in D[:4]]
+    ref = oracle.sslbm9_run(st.astype(np.float32).astype(np.float64), tau, RATES, 1.0, L.BC_NOFLUX, 200)
+    assert relmax(got, ref) <= 1e-4
+    s0 = float(st.astype(np.float32).astype(np.float64).sum())
+    assert abs(float(tot.sum()) - s0) / s0 < 200 * 4 * 6e-8
