@@ -592,6 +592,7 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
         sv = L.Solver(NX, NY, rates, d=wl["d"], bc=wl["bc"], precision=prec, lattice=L.LATTICE_D2Q5_VARD)
         sv.set_diffusivity_scale(kx, ky)
         sv.write(state32 if prec == L.FP32 else state64)
+        sv.set_blocking(1)
         sv.step(2)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -603,6 +604,17 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
         ms = a.elapsed_time(b) / reps
         out[f"vard_{name}_glups"] = cells / (ms * 1e-3) / 1e9
         out[f"vard_{name}_hbm_frac"] = 12 * esz * cells / (ms * 1e-3) / 1e9 / hbm
+        if prec == L.FP32:
+            # the temporal-blocked kernel at the autotuned depth, 48 steps per measurement
+            depth, seg, _ = sv.autotune()
+            sv.step(depth)
+            torch.cuda.synchronize()
+            a.record(stream)
+            sv.step(48)
+            b.record(stream)
+            b.synchronize()
+            out["vard_fp32_blocked_glups"] = cells * 48 / (a.elapsed_time(b) * 1e-3) / 1e9
+            out["vard_fp32_blocked_depth"] = depth
         sv.close()
         del sv
         torch.cuda.empty_cache()

@@ -209,7 +209,8 @@ int sslbm_set_diffusivity_scale(sslbm_handle* h, const void* kx, const void* ky,
  * On D2Q5 rho_f = rho_b, so the kernels evaluate the algebraically identical
  * rho_c + d_lattice (sum of the four neighbours - 4 rho_c) + Psi dt.
  * Several steps are fused per pass over memory (temporal blocking, depth set by
- * sslbm_set_blocking or sslbm_autotune; D2Q5 in the FP32 storages, D2Q9 in FP32); n steps
+ * sslbm_set_blocking or sslbm_autotune; D2Q5 in the FP32 storages, D2Q9 and varying
+ * diffusion in FP32); n steps
  * take ceil(n / depth) passes whose depths differ by at most one.  Results do not depend on
  * the depth: every depth performs the same floating-point operations in the same order.
  * Enqueues on the handle's stream and returns. */
@@ -309,13 +310,14 @@ int sslbm_diagnostics_noalloc(const void* fields, int dtype, int64_t nx, int64_t
 /* Temporal-blocking depth k (steps fused per pass, 1..SSLBM_MAX_DEPTH) and the
  * kernel's row-segment length seg_rows (0 = automatic).  k = 0 restores the default (4
  * where a blocked kernel exists, else 1).  The blocked kernels cover the D2Q5 lattice in
- * SSLBM_FP32, SSLBM_FP32_DEV and SSLBM_FP32_SPLIT and the D2Q9 lattice in SSLBM_FP32; k > 1
- * elsewhere returns SSLBM_ERR_UNSUPPORTED. */
+ * SSLBM_FP32, SSLBM_FP32_DEV and SSLBM_FP32_SPLIT, and the D2Q9 and varying-diffusion
+ * lattices in SSLBM_FP32; k > 1 elsewhere returns SSLBM_ERR_UNSUPPORTED. */
 #define SSLBM_MAX_DEPTH 8
 int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows);
 
 /* Autotuner: choose the blocking depth (1..SSLBM_MAX_DEPTH) and segment length for this
- * handle's grid, precision and lattice (D2Q5 or D2Q9; others: SSLBM_ERR_UNSUPPORTED) by
+ * handle's grid, precision and lattice (D2Q5, D2Q9 or varying diffusion, whose scale fields
+ * must be set; others: SSLBM_ERR_UNSUPPORTED) by
  * timing candidate launches on the handle's stream.  The candidates read the current state
  * and write the spare buffer, so the state is left unchanged.  budget_ms bounds the search
  * (0 = 300 ms).  The choice is cached per (device, nx, ny, precision, lattice, boundary)

@@ -192,10 +192,12 @@ int sslbm_workspace_bytes(const sslbm_grid* g, size_t* bytes) {
   return SSLBM_OK;
 }
 
-// The D2Q5 FP32 storages and the FP32 D2Q9 lattice have the temporal-blocked kernel.
+// The D2Q5 FP32 storages and the FP32 D2Q9 and varying-diffusion lattices have the
+// temporal-blocked kernel.
 static bool can_block(const sslbm_handle* h) {
   if (h->g.lattice == SSLBM_LATTICE_D2Q5) return sslbm::blocked_supported(h->g.precision, h->gv);
-  return h->g.lattice == SSLBM_LATTICE_D2Q9 && h->g.precision == SSLBM_FP32;
+  return (h->g.lattice == SSLBM_LATTICE_D2Q9 || h->g.lattice == SSLBM_LATTICE_D2Q5_VARD) &&
+         h->g.precision == SSLBM_FP32;
 }
 
 // One pass of k steps (k = 1: the one-step kernel) from the current buffer into the spare one,
@@ -203,6 +205,14 @@ static bool can_block(const sslbm_handle* h) {
 static cudaError_t launch_pass(sslbm_handle* h, int k, int seg) {
   const bool q9 = h->g.lattice == SSLBM_LATTICE_D2Q9;
   void* out = h->s_buf[1 - h->s_cur];
+  if (h->g.lattice == SSLBM_LATTICE_D2Q5_VARD) {  // scale planes kx, ky in the kappa area
+    const char* kx = h->kappa;
+    const char* ky = h->kappa + h->L.plane_bytes;
+    if (k == 1)
+      return sslbm::launch_sslbm_vard_step(h->g.precision, h->gv, h->coeffs(), kx, ky, h->s_buf[h->s_cur], out,
+                                           h->stream);
+    return sslbm::launch_sslbm_vard_blocked(h->gv, &h->cf, kx, ky, h->s_buf[h->s_cur], out, k, seg, h->stream);
+  }
   if (k == 1)
     return q9 ? sslbm::launch_sslbm9_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur], out, h->stream)
               : sslbm::launch_sslbm_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur], out, h->stream);
@@ -211,6 +221,7 @@ static cudaError_t launch_pass(sslbm_handle* h, int k, int seg) {
 }
 
 static int default_seg(const sslbm_handle* h, int k) {
+  if (h->g.lattice == SSLBM_LATTICE_D2Q5_VARD) return sslbm::blocked_vard_default_seg_rows(h->gv, k);
   return h->g.lattice == SSLBM_LATTICE_D2Q9 ? sslbm::blocked9_default_seg_rows(h->gv, k)
                                             : sslbm::blocked_default_seg_rows(h->g.precision, h->gv, k);
 }
@@ -515,19 +526,8 @@ int sslbm_step(sslbm_handle* h, int64_t n) {
     }
     return SSLBM_OK;
   }
-  if (h->g.lattice == SSLBM_LATTICE_D2Q5_VARD) {
-    if (!h->kappa_ok)
-      return fail(SSLBM_ERR_BAD_ARG, "the diffusivity scale fields are not set (sslbm_set_diffusivity_scale)");
-    for (; n > 0; --n) {
-      cudaError_t e = sslbm::launch_sslbm_vard_step(h->g.precision, h->gv, h->coeffs(), h->kappa,
-                                                    h->kappa + h->L.plane_bytes, h->s_buf[h->s_cur],
-                                                    h->s_buf[1 - h->s_cur], h->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "varying-diffusivity step launch");
-      h->s_cur = 1 - h->s_cur;
-      h->s_steps += 1;
-    }
-    return SSLBM_OK;
-  }
+  if (h->g.lattice == SSLBM_LATTICE_D2Q5_VARD && !h->kappa_ok)
+    return fail(SSLBM_ERR_BAD_ARG, "the diffusivity scale fields are not set (sslbm_set_diffusivity_scale)");
   const bool blocked = can_block(h);
   while (n > 0) {
     int k = 1;
@@ -635,12 +635,13 @@ int sslbm_debug_bounds(long long* count, long long* value, long long* limit, int
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize(bounds records)");
   int (*const take[])(sslbm::OobRecord*) = {sslbm::oob_take_kernels, sslbm::oob_take_ensemble, sslbm::oob_take_bgk,
-                                            sslbm::oob_take_io, sslbm::oob_take_stream};
-  const int tu_site[] = {0, 100, 200, 300, 400};  // site numbers are offset by translation unit
+                                            sslbm::oob_take_io, sslbm::oob_take_stream,
+                                            sslbm::oob_take_lattices};
+  const int tu_site[] = {0, 100, 200, 300, 400, 500};  // site numbers are offset by translation unit
   unsigned long long total = 0;
   sslbm::OobRecord first{};
   int first_site = -1;
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < 6; ++i) {
     sslbm::OobRecord r{};
     if (take[i](&r) != 0) return fail(SSLBM_ERR_CUDA, "reading the bounds record of unit %d", i);
     if (r.count && first_site < 0) {
@@ -785,7 +786,8 @@ int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows) {
   const bool blocked = can_block(h);
   if (!blocked && k > 1)
     return fail(SSLBM_ERR_UNSUPPORTED,
-                "temporal blocking is provided for FP32, FP32_DEV and FP32_SPLIT on D2Q5 and for FP32 on D2Q9");
+                "temporal blocking is provided for FP32, FP32_DEV and FP32_SPLIT on D2Q5 and for FP32 on D2Q9 "
+                "and the varying-diffusion lattice");
   h->depth = k == 0 ? (blocked ? 4 : 1) : k;
   if (seg_rows > 0 && seg_rows < 4 * h->depth) seg_rows = 4 * h->depth;
   h->seg_rows = seg_rows;
@@ -816,8 +818,11 @@ int sslbm_autotune(sslbm_handle* h, double budget_ms, int* depth_out, int* seg_o
   if (st) return st;
   if (!(budget_ms >= 0)) return fail(SSLBM_ERR_BAD_ARG, "budget_ms must be >= 0");
   if (budget_ms == 0) budget_ms = 300.0;
-  if (h->g.lattice != SSLBM_LATTICE_D2Q5 && h->g.lattice != SSLBM_LATTICE_D2Q9)
-    return fail(SSLBM_ERR_UNSUPPORTED, "the autotuner tunes the D2Q5 and D2Q9 kernels");
+  if (h->g.lattice != SSLBM_LATTICE_D2Q5 && h->g.lattice != SSLBM_LATTICE_D2Q9 &&
+      h->g.lattice != SSLBM_LATTICE_D2Q5_VARD)
+    return fail(SSLBM_ERR_UNSUPPORTED, "the autotuner tunes the D2Q5, D2Q9 and varying-diffusion kernels");
+  if (h->g.lattice == SSLBM_LATTICE_D2Q5_VARD && !h->kappa_ok)
+    return fail(SSLBM_ERR_BAD_ARG, "the diffusivity scale fields are not set (sslbm_set_diffusivity_scale)");
   DeviceGuard dg(h->device);
   const TuneKey key{h->device, h->g.precision, h->g.lattice, h->g.bc, h->g.nx, h->g.ny};
   TuneResult best{1, 0, 0.0};

@@ -16,7 +16,16 @@ namespace sslbm {
 
 // MODE_D2Q9 / MODE_D2Q9_NOFLUX: the plain FP32 storage on the D2Q9 lattice (the nine-point
 // laplacian), periodic or with bounce-back walls, for the temporal-blocked pipeline.
-enum Mode { MODE_PLAIN = 0, MODE_DEV = 1, MODE_KAHAN = 2, MODE_SPLIT = 3, MODE_D2Q9 = 4, MODE_D2Q9_NOFLUX = 5 };
+// MODE_VARD: the plain FP32 storage with spatially varying diffusion (the flux form).
+enum Mode {
+  MODE_PLAIN = 0,
+  MODE_DEV = 1,
+  MODE_KAHAN = 2,
+  MODE_SPLIT = 3,
+  MODE_D2Q9 = 4,
+  MODE_D2Q9_NOFLUX = 5,
+  MODE_VARD = 6
+};
 
 // Stored planes per state of a mode: the five compartments, plus the compensation of S
 // (MODE_SPLIT) or of all five (MODE_KAHAN), which follow them.
@@ -285,6 +294,11 @@ bool blocked_supported(int precision, const GridView& g);
 cudaError_t launch_sslbm9_blocked(const GridView& g, const void* coeffs, const void* in, void* out, int depth,
                                   int seg_rows, cudaStream_t s);
 int blocked9_default_seg_rows(const GridView& g, int depth);
+// The varying-diffusion lattice (plain FP32 storage, scale planes kx, ky): K fused steps per
+// launch, and its default segment.
+cudaError_t launch_sslbm_vard_blocked(const GridView& g, const void* coeffs, const void* kx, const void* ky,
+                                      const void* in, void* out, int depth, int seg_rows, cudaStream_t s);
+int blocked_vard_default_seg_rows(const GridView& g, int depth);
 // Segment length that makes one blocked launch a single wave of resident warps.
 int blocked_default_seg_rows(int precision, const GridView& g, int depth);
 // BGK: one collide-and-stream step; equilibrium initialisation and density of one

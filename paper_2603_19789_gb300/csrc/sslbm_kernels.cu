@@ -5,10 +5,12 @@
 //                   row with 16-byte vector loads (double2) of the centre, upper and lower rows
 //                   and two scalar edge loads; neighbouring rows come from L1/L2.  The FP32
 //                   storages advance one step per launch in the streaming kernel (stream.cu).
-//   pipe_kernel     K steps per launch (temporal blocking, K = 2..8) for FP32, FP32
-//                   deviation-S and FP32 split-S (a sixth plane), and FP32 on the D2Q9 lattice
-//                   (periodic, or no-flux with the bounce-back substituted into the row
-//                   update), as a pipeline of K warps per
+//   pipe_kernel     (pipe_launch.cuh) K steps per launch (temporal blocking, K = 2..8) for
+//                   FP32, FP32 deviation-S and FP32 split-S (a sixth plane); pipe_lattices.cu
+//                   instantiates it for FP32 on the D2Q9 lattice (periodic, or no-flux with the
+//                   bounce-back substituted into the row update) and on the varying-diffusion
+//                   lattice (the scale rows in a static shared-memory ring), as a pipeline of
+//                   K warps per
 //                   CTA: warp s computes level s+1 of the time-step wavefront.  A CTA owns a
 //                   128-column strip (4 columns per lane, 16-byte accesses) with a K-column halo
 //                   on each side and streams down a segment of rows, two rows per step of the
@@ -29,7 +31,7 @@
 
 #include "bounds.cuh"
 #include "sslbm_internal.cuh"
-#include "sslbm_pipe.cuh"
+#include "pipe_launch.cuh"
 
 SSLBM_OOB_ACCESSOR(kernels)
 
@@ -90,22 +92,6 @@ __global__ void __launch_bounds__(256, 1) step1_kernel(const GridView g, const C
   }
 }
 
-template <int MODE, int K>
-__global__ void __launch_bounds__(32 * K, 16 / K) pipe_kernel(const GridView g, const Coeffs<float> k,
-                                                             const float* __restrict__ in,
-                                                             float* __restrict__ out,
-                                                             const int seg_rows, const int nstrips) {
-  extern __shared__ __align__(16) unsigned char pipe_smem[];
-  PipeSmem<K, mode_planes<MODE>()>& sm = *reinterpret_cast<PipeSmem<K, mode_planes<MODE>()>*>(pipe_smem);
-  const int strip = (int)(blockIdx.x % (unsigned)nstrips);
-  const int64_t y0 = (int64_t)(blockIdx.x / (unsigned)nstrips) * seg_rows;
-  const int64_t y1 = (y0 + seg_rows < g.ny) ? y0 + seg_rows : g.ny;
-  if (MODE == MODE_D2Q9_NOFLUX && strip != 0 && strip != nstrips - 1)
-    pipe_tile<MODE, K, false, false>(sm, g, k, in, out, strip, y0, y1);  // no wall column in this strip
-  else
-    pipe_tile<MODE, K>(sm, g, k, in, out, strip, y0, y1);
-}
-
 cudaError_t launch_step1_fp64(const GridView& g, const void* coeffs, const void* in, void* out, cudaStream_t s) {
   const int64_t nvec = (g.nx + 1) / 2;
   dim3 block(32, 8);
@@ -117,89 +103,6 @@ cudaError_t launch_step1_fp64(const GridView& g, const void* coeffs, const void*
   return cudaGetLastError();
 }
 
-// The fused kernel's shared-memory attributes, set once per device (a bit per device in an
-// atomic mask: host threads may launch concurrently; setting them twice is harmless).
-template <int MODE, int K>
-void prefer_shared() {
-  static std::atomic<unsigned long long> done{0};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return;
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (done.load(std::memory_order_acquire) & bit) return;
-  cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       cudaSharedmemCarveoutMaxShared);
-  cudaFuncSetAttribute(pipe_kernel<MODE, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(PipeSmem<K, mode_planes<MODE>()>));
-  done.fetch_or(bit, std::memory_order_release);
-}
-
-template <int MODE, int K>
-cudaError_t launch_blocked_t(const GridView& g, const void* coeffs, const void* in, void* out,
-                             int seg_rows, cudaStream_t s) {
-  constexpr int HL = (K + 3) / 4;
-  constexpr int WV = 128 - 8 * HL;
-  prefer_shared<MODE, K>();
-  if (seg_rows <= 0) return cudaErrorInvalidValue;
-  const int64_t nstrips = (g.nx + WV - 1) / WV;
-  const int64_t nseg = (g.ny + seg_rows - 1) / seg_rows;
-  const int64_t blocks = nstrips * nseg;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  pipe_kernel<MODE, K><<<(unsigned)blocks, 32 * K, sizeof(PipeSmem<K, mode_planes<MODE>()>), s>>>(
-      g, *static_cast<const Coeffs<float>*>(coeffs), static_cast<const float*>(in),
-      static_cast<float*>(out), seg_rows, (int)nstrips);
-  return cudaGetLastError();
-}
-
-template <int MODE, int K>
-int default_seg_rows_t(const GridView& g) {
-  constexpr int HL = (K + 3) / 4;
-  constexpr int WV = 128 - 8 * HL;
-  prefer_shared<MODE, K>();
-  const int64_t nstrips = (g.nx + WV - 1) / WV;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_kernel<MODE, K>, 32 * K,
-                                                sizeof(PipeSmem<K, mode_planes<MODE>()>));
-  // one wave: as many CTAs as fit on the device at once, split into row segments
-  const int64_t resident = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-  int64_t nseg = resident / nstrips;
-  if (nseg < 1) nseg = 1;
-  int64_t rows = (g.ny + nseg - 1) / nseg;
-  if (rows < 4 * K) rows = 4 * K;
-  if (rows > (1 << 30)) rows = 1 << 30;
-  return (int)rows;
-}
-
-template <int MODE>
-cudaError_t launch_blocked_mode(const GridView& g, const void* coeffs, const void* in, void* out,
-                                int depth, int seg_rows, cudaStream_t s) {
-  switch (depth) {
-    case 2: return launch_blocked_t<MODE, 2>(g, coeffs, in, out, seg_rows, s);
-    case 3: return launch_blocked_t<MODE, 3>(g, coeffs, in, out, seg_rows, s);
-    case 4: return launch_blocked_t<MODE, 4>(g, coeffs, in, out, seg_rows, s);
-    case 5: return launch_blocked_t<MODE, 5>(g, coeffs, in, out, seg_rows, s);
-    case 6: return launch_blocked_t<MODE, 6>(g, coeffs, in, out, seg_rows, s);
-    case 7: return launch_blocked_t<MODE, 7>(g, coeffs, in, out, seg_rows, s);
-    case 8: return launch_blocked_t<MODE, 8>(g, coeffs, in, out, seg_rows, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <int MODE>
-int default_seg_rows_mode(const GridView& g, int depth) {
-  switch (depth) {
-    case 2: return default_seg_rows_t<MODE, 2>(g);
-    case 3: return default_seg_rows_t<MODE, 3>(g);
-    case 4: return default_seg_rows_t<MODE, 4>(g);
-    case 5: return default_seg_rows_t<MODE, 5>(g);
-    case 6: return default_seg_rows_t<MODE, 6>(g);
-    case 7: return default_seg_rows_t<MODE, 7>(g);
-    case 8: return default_seg_rows_t<MODE, 8>(g);
-    default: return 0;
-  }
-}
-
 }  // namespace
 
 int blocked_default_seg_rows(int precision, const GridView& g, int depth) {
@@ -207,16 +110,6 @@ int blocked_default_seg_rows(int precision, const GridView& g, int depth) {
   if (precision == SSLBM_FP32_DEV) return default_seg_rows_mode<MODE_DEV>(g, depth);
   if (precision == SSLBM_FP32_SPLIT) return default_seg_rows_mode<MODE_SPLIT>(g, depth);
   return 0;
-}
-
-int blocked9_default_seg_rows(const GridView& g, int depth) {
-  return g.bc != 0 ? default_seg_rows_mode<MODE_D2Q9_NOFLUX>(g, depth) : default_seg_rows_mode<MODE_D2Q9>(g, depth);
-}
-
-cudaError_t launch_sslbm9_blocked(const GridView& g, const void* coeffs, const void* in, void* out, int depth,
-                                  int seg_rows, cudaStream_t s) {
-  if (g.bc != 0) return launch_blocked_mode<MODE_D2Q9_NOFLUX>(g, coeffs, in, out, depth, seg_rows, s);
-  return launch_blocked_mode<MODE_D2Q9>(g, coeffs, in, out, depth, seg_rows, s);
 }
 
 bool blocked_supported(int precision, const GridView&) {

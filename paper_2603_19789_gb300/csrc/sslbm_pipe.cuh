@@ -168,6 +168,59 @@ __device__ __forceinline__ void cell_row9(const Coeffs<float>& k, const GridView
   }
 }
 
+// Static rows of the varying-diffusion lattice: the scale planes kx, ky of the rows in the
+// pipeline's window, kRingK rows of 128 columns each in shared memory (row q in slot
+// (q - qa) mod kRingK).  A level-s warp reads rows up to 3(K - 1) + 2 behind the level-0
+// rows, which are copied three row pairs ahead, so kRingK >= 3K + 8.
+constexpr int kRingK = 32;
+
+// Level s+1 of row C on the varying-diffusion lattice (plain FP32 storage) from level-s rows
+// P, C, N: the link coefficients (k_a(x) + k_a(x + c_i)) / 2 from the scale rows (kx of the
+// row, x neighbours by shuffles; ky of the rows y-1, y, y+1), the flux terms of S, E, I, R,
+// each rounded on its own, summed as ((+x) + (-x)) + ((+y) + (-y)) in scalar adds, then the
+// packed cell update -- the operations of the one-step kernel.  The sum is unchanged by a
+// mirror image, so the no-flux ghost images evolve as the cells they mirror, as on D2Q5.
+// kxr, kyp, kyc, kyn: this lane's four columns of kx (row y) and ky (rows y-1, y, y+1).
+__device__ __forceinline__ void cell_rowv(const Coeffs<float>& k, const float2 (&P)[5][2], const float2 (&C)[5][2],
+                                          const float2 (&N)[5][2], float2 (&M)[5][2], const float* kxr,
+                                          const float* kyp, const float* kyc, const float* kyn) {
+  constexpr unsigned kFull = 0xffffffffu;
+  const float4 ax = *reinterpret_cast<const float4*>(kxr);
+  const float axL = __shfl_up_sync(kFull, ax.w, 1), axR = __shfl_down_sync(kFull, ax.x, 1);
+  const float4 bc = *reinterpret_cast<const float4*>(kyc);
+  const float4 bp = *reinterpret_cast<const float4*>(kyp);
+  const float4 bn = *reinterpret_cast<const float4*>(kyn);
+  const float2 half = splat2(0.5f);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float2 a = h == 0 ? make_float2(ax.x, ax.y) : make_float2(ax.z, ax.w);
+    const float2 aR = h == 0 ? make_float2(ax.y, ax.z) : make_float2(ax.w, axR);
+    const float2 aL = h == 0 ? make_float2(axL, ax.x) : make_float2(ax.y, ax.z);
+    const float2 b = h == 0 ? make_float2(bc.x, bc.y) : make_float2(bc.z, bc.w);
+    const float2 bN = h == 0 ? make_float2(bn.x, bn.y) : make_float2(bn.z, bn.w);
+    const float2 bP = h == 0 ? make_float2(bp.x, bp.y) : make_float2(bp.z, bp.w);
+    const float2 lxp = mul2(half, add2(a, aR)), lyp = mul2(half, add2(b, bN));
+    const float2 lxm = mul2(half, add2(a, aL)), lym = mul2(half, add2(b, bP));
+    float2 flux[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      // the neighbour beyond the pair: from the lane on the left (h = 0) or on the right (h = 1)
+      const float X = h == 0 ? __shfl_up_sync(kFull, C[f][1].y, 1) : __shfl_down_sync(kFull, C[f][0].x, 1);
+      const float2 cc = C[f][h], ncc = neg2(cc);
+      const float2 right = h == 0 ? make_float2(C[f][0].y, C[f][1].x) : make_float2(C[f][1].y, X);
+      const float2 left = h == 0 ? make_float2(X, C[f][0].x) : make_float2(C[f][0].y, C[f][1].x);
+      const float2 t1 = mul2(lxp, add2(right, ncc));
+      const float2 t2 = mul2(lyp, add2(N[f][h], ncc));
+      const float2 t3 = mul2(lxm, add2(left, ncc));
+      const float2 t4 = mul2(lym, add2(P[f][h], ncc));
+      flux[f] = make_float2(__fadd_rn(__fadd_rn(t1.x, t3.x), __fadd_rn(t2.x, t4.x)),
+                            __fadd_rn(__fadd_rn(t1.y, t3.y), __fadd_rn(t2.y, t4.y)));
+    }
+    seird_cell2<0>(k, C[0][h], C[1][h], C[2][h], C[3][h], C[4][h], flux[0], flux[1], flux[2], flux[3], M[0][h],
+                   M[1][h], M[2][h], M[3][h], M[4][h]);
+  }
+}
+
 // Hand level-(s+1) row M to the next warp (slot row `which` of parity par) or, for the last
 // warp, write it to row r of the output.
 template <int K, int NF>
@@ -208,7 +261,8 @@ __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g
                                           const float* src, const float2 (&A)[NF][2], const float2 (&B)[NF][2],
                                           float2 (&N0)[NF][2], float2 (&N1)[NF][2], float* __restrict__ out,
                                           const int s, const int lane, const int par, const bool writer,
-                                          const int64_t xs, const int64_t r, const int64_t y0, const int64_t y1) {
+                                          const int64_t xs, const int64_t r, const int64_t y0, const int64_t y1,
+                                          const float* rk = nullptr, const int sk = 0) {
   auto load_row = [&](const float* p, float2 (&R)[NF][2]) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -234,6 +288,16 @@ __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g
       cell_row9<true, W>(k, g, B, N0, N1, M, xs, row + 1);
     else
       cell_row9<false, W && COLW>(k, g, B, N0, N1, M, xs, row + 1);
+  } else if constexpr (MODE == MODE_VARD) {
+    // sk: the static-ring slot of the first row this warp computes (row b - 1)
+    auto krow = [&](int d, int plane) {  // this lane's columns of scale plane `plane`, row b - 1 + d
+      return rk + ((sk + d + kRingK) & (kRingK - 1)) * 256 + plane * 128 + 4 * lane;
+    };
+    load_row(src, N0);
+    cell_rowv(k, A, B, N0, M, krow(0, 0), krow(-1, 1), krow(0, 1), krow(1, 1));
+    emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
+    load_row(src + 128 * NF, N1);
+    cell_rowv(k, B, N0, N1, M, krow(1, 0), krow(0, 1), krow(1, 1), krow(2, 1));
   } else {
     load_row(src, N0);
     load_row(src + 128 * NF, N1);
@@ -254,7 +318,9 @@ __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g
 template <int MODE, int K, bool WRAP16 = false, bool COLW = true, int NF = mode_planes<MODE>()>
 __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g, const Coeffs<float>& k,
                                           const float* __restrict__ in, float* __restrict__ out,
-                                          const int strip, const int64_t y0, const int64_t y1) {
+                                          const int strip, const int64_t y0, const int64_t y1,
+                                          const float* __restrict__ kx = nullptr,
+                                          const float* __restrict__ ky = nullptr, float* rk = nullptr) {
   constexpr int HL = (K + 3) / 4;   // halo lanes on each side of the strip
   constexpr int WV = 128 - 8 * HL;  // columns written per strip
   const int lane = threadIdx.x & 31;
@@ -279,6 +345,8 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g
 
   for (int i = threadIdx.x; i < kRing0 * NF * 128; i += 32 * K) (&sm.r0[0][0][0])[i] = 0.f;
   for (int i = threadIdx.x; i < (K - 1) * 2 * 2 * NF * 128; i += 32 * K) (&sm.rl[0][0][0][0][0])[i] = 0.f;
+  if (MODE == MODE_VARD)
+    for (int i = threadIdx.x; i < kRingK * 2 * 128; i += 32 * K) rk[i] = 0.f;
   __syncthreads();
 
   auto issue = [&](int64_t q) {  // warp 0: copy level-0 row q into its ring slot
@@ -287,10 +355,12 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g
     const int64_t yq = ghost_index(q, g.ny, g.bc);
     if (!SSLBM_IN(yq, 1, g.ny, 1)) return;
     const int64_t row = yq * g.pitch;
+    // the state planes, and on the varying-diffusion lattice the two scale planes (static ring)
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const float* src = in + f * g.plane + row;
-      float* dst = &sm.r0[slot][f][4 * lane];
+    for (int f = 0; f < (MODE == MODE_VARD ? NF + 2 : NF); ++f) {
+      const float* src = (f < NF ? in + f * g.plane : f == NF ? kx : ky) + row;
+      float* dst = f < NF ? &sm.r0[slot][f][4 * lane]
+                          : rk + ((int)(q - qa) & (kRingK - 1)) * 256 + (f - NF) * 128 + 4 * lane;
       if (WRAP16) {
         if (SSLBM_IN(xw, 4, g.nx, 2)) cp_async16(dst, src + xw);
       } else if (vec_ok) {
@@ -330,16 +400,18 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g
     }
     return &sm.rl[s - 1][(t + 1) & 1][0][0][4 * lane];
   };
+  // the static-ring slot of the first row warp s computes at iteration t (row qa + 2t - 3s - 1)
+  auto kslot = [&](int t) { return (2 * t - 3 * s - 1) & (kRingK - 1); };
   int t = 0;
   for (; t + 2 <= nt; t += 2) {
     pipe_pair<MODE, K, COLW>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0,
-                             y1);
+                             y1, rk, kslot(t));
     pipe_pair<MODE, K, COLW>(sm, g, k, fetch(t + 1), RC, RD, RA, RB, out, s, lane, (t + 1) & 1, writer, xs,
-                             rbase + 2 * t + 2, y0, y1);
+                             rbase + 2 * t + 2, y0, y1, rk, kslot(t + 1));
   }
   if (t < nt)
     pipe_pair<MODE, K, COLW>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0,
-                             y1);
+                             y1, rk, kslot(t));
   if (s == 0) cp_async_wait<0>();
 }
 

@@ -331,8 +331,8 @@ struct D2q9Cell {
 
 // Spatially varying, axis-anisotropic diffusion in flux form: the link coefficients
 // (k_a(x) + k_a(x + c_i)) / 2 of the links +x, +y, -x, -y, each flux term rounded on its own
-// and summed in that order, then seird_cell.  Ring planes: S, E, I, R, kx (x neighbours),
-// ky, D.
+// and summed as ((+x) + (-x)) + ((+y) + (-y)) (the order of vard.cu), then seird_cell.  Ring
+// planes: S, E, I, R, kx (x neighbours), ky, D.
 struct VardCell {
   static constexpr int kPlanes = 7, kHaloPlanes = 5, kRing = 8, kWarps = 4, kMinBlocks = 3;
   static constexpr bool kPacked = true;
@@ -363,13 +363,13 @@ struct VardCell {
       const float2 t2 = mul2(lyp, add2(ld2(r.N + f * kStStride, i), ncc));
       const float2 t3 = mul2(lxm, add2(ld2(P, i - 1), ncc));
       const float2 t4 = mul2(lym, add2(ld2(r.U + f * kStStride, i), ncc));
-      // the sum in scalar adds: summed with packed adds (the intrinsic or inline PTX) the
-      // results differed in the last bit from the scalar kernel's on 0.1-1% of cells, although
-      // the packed add, multiply and FMA each match their scalar forms bit for bit on 4M
-      // random operand pairs (subnormals included); with scalar adds of the packed products
-      // every bit agrees
-      flux[f] = make_float2(add_rn(add_rn(add_rn(t1.x, t2.x), t3.x), t4.x),
-                            add_rn(add_rn(add_rn(t1.y, t2.y), t3.y), t4.y));
+      // ((+x) + (-x)) + ((+y) + (-y)), in scalar adds: summed with packed adds (the intrinsic
+      // or inline PTX) the results differed in the last bit from the scalar kernel's on 0.1-1%
+      // of cells, although the packed add, multiply and FMA each match their scalar forms bit
+      // for bit on 4M random operand pairs (subnormals included); with scalar adds of the
+      // packed products every bit agrees
+      flux[f] = make_float2(add_rn(add_rn(t1.x, t3.x), add_rn(t2.x, t4.x)),
+                            add_rn(add_rn(t1.y, t3.y), add_rn(t2.y, t4.y)));
       c[f] = cc;
     }
     float2 n[5];

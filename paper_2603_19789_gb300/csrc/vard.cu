@@ -12,8 +12,10 @@
 // and of the rows above and below, two scalar loads for the columns left and right of the
 // group.  FP32 runs the same per-cell operations in the streaming one-step kernel
 // (stream.cu).  The four link coefficients of a cell are formed once and
-// serve all four mobile compartments; the flux sum follows the link order c_1 .. c_4
-// (+x, +y, -x, -y), each term rounded on its own.
+// serve all four mobile compartments; each flux term is rounded on its own and the sum pairs
+// the two x links and the two y links, ((+x) + (-x)) + ((+y) + (-y)), an order that a mirror
+// image leaves unchanged (so the no-flux boundary is exactly a ghost image, which the
+// temporal-blocked kernel relies on).
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(256) vard_step_kernel(const GridView g, const 
         const T t2 = mul_rn(lyp[j], sub_rn(p[j], cc));
         const T t3 = mul_rn(lxm[j], sub_rn(left, cc));
         const T t4 = mul_rn(lym[j], sub_rn(m[j], cc));
-        flux[c][j] = add_rn(add_rn(add_rn(t1, t2), t3), t4);
+        flux[c][j] = add_rn(add_rn(t1, t3), add_rn(t2, t4));
       }
     }
     T D[V];

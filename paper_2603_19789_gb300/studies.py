@@ -325,7 +325,8 @@ def variant_timing(lattice="d2q9", precision="fp32", n=8192, steps=20, depth=1, 
     """GLUPS of one update variant on the n x n multi-seed no-flux workload (inputs larger than
     L2 at the default size): 4 warm-up steps, then `steps` steps timed with CUDA events on the
     solver's stream.  depth applies where a blocked kernel exists (the D2Q5 FP32 storages, FP32
-    D2Q9): 1 = one step per launch, 0 = the default blocking, k = k steps per launch.
+    D2Q9 and varying diffusion): 1 = one step per launch, 0 = the default blocking, k = k steps
+    per launch.
     hbm_frac = algorithmic bytes per cell-step (every plane read once and written once; the
     two scale planes read once on the varying-diffusion lattice) over the step time, divided
     by the measured HBM bandwidth; it is reported for one-step launches only."""
@@ -338,7 +339,8 @@ def variant_timing(lattice="d2q9", precision="fp32", n=8192, steps=20, depth=1, 
     if lat == L.LATTICE_D2Q5_VARD:
         s.set_diffusivity_scale(*inputs.mobility_fields(n, n, 7))
     s.write(st)
-    if lat in (L.LATTICE_D2Q5, L.LATTICE_D2Q9) and depth:
+    blockable = (L.LATTICE_D2Q5, L.LATTICE_D2Q9, L.LATTICE_D2Q5_VARD)
+    if lat in blockable and depth and not (lat != L.LATTICE_D2Q5 and prec != L.FP32):
         s.set_blocking(depth)
     s.step(4)
     torch.cuda.synchronize()
@@ -354,7 +356,7 @@ def variant_timing(lattice="d2q9", precision="fp32", n=8192, steps=20, depth=1, 
     out = {"lattice": lattice, "precision": precision, "n": n, "bc": "periodic" if bc == L.BC_PERIODIC else "no-flux",
            "depth": depth, "steps": steps, "ms_per_step": ms,
            "glups": n * n / (ms * 1e-3) / 1e9, "bytes_per_cell_step": nbytes}
-    one_step = lat not in (L.LATTICE_D2Q5, L.LATTICE_D2Q9) or depth == 1 or prec in (L.FP64, L.FP32_KAHAN)
+    one_step = lat not in blockable or depth == 1 or prec in (L.FP64, L.FP32_KAHAN)
     peak = _measured_hbm_gbs()
     if one_step and peak:
         out["hbm_frac"] = nbytes * n * n / (ms * 1e-3) / 1e9 / peak

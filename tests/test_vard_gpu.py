@@ -2,8 +2,9 @@
 LATTICE_D2Q5_VARD, sslbm_set_diffusivity_scale) against the FP64 oracle
 (oracle.sslbm_vard_run).
 
-The kernel forms the four link coefficients and the flux sum in the oracle's order, each
-operation rounded once; the update itself uses the library's fused form of
+The kernel forms the four link coefficients as the oracle does and sums the flux terms as
+((+x) + (-x)) + ((+y) + (-y)) (the oracle: in link order), each operation rounded once; the
+update itself uses the library's fused form of
 Eq. (sslbm_final_clean) (rho_c + d flux with FMA, sources with dt folded into the rates),
 so FP64 agrees to a few roundings per step: 1e-12 relative max-norm over 25 steps, as for
 the constant-diffusivity kernel.  FP32 evaluates the same expressions in single
@@ -134,7 +135,7 @@ def test_validation_and_what_it_does_not_run():
     s.set_diffusivity_scale(k)
     s.step(2)
     with pytest.raises(L.SslbmError) as e:
-        s.set_blocking(4)
+        s.set_blocking(4)  # temporal blocking: FP32 only
     assert e.value.status == L.SSLBM_ERR_UNSUPPORTED
     s.close()
     # the fields decide stability: tau = 1.4 (d = 0.3) runs with small fields
@@ -152,3 +153,80 @@ def test_validation_and_what_it_does_not_run():
     with pytest.raises(L.SslbmError) as e:
         L.Solver(nx, ny, RATES, d=D, precision=L.FP32_DEV, lattice=L.LATTICE_D2Q5_VARD)
     assert e.value.status == L.SSLBM_ERR_UNSUPPORTED
+
+
+def _vard_fp32(nx, ny, bc, st, kx, ky):
+    s = _solver(nx, ny, bc, L.FP32)
+    s.set_diffusivity_scale(kx, ky)
+    s.write(st)
+    return s
+
+
+@pytest.mark.parametrize("bc", [L.BC_PERIODIC, L.BC_NOFLUX])
+@pytest.mark.parametrize("nx,ny", [(131, 77), (257, 130), (64, 300), (120, 45), (5, 7), (1, 1), (2, 9)])
+def test_fp32_blocked_depths_give_identical_bits(bc, nx, ny):
+    """The temporal-blocked kernel (the pipeline tile with the flux-form row update, the scale
+    rows staged in shared memory) against the one-step kernel, bit for bit: 2k steps at depth k
+    are two passes of exactly that depth; then 11 steps, which mix depths.  Under no-flux the
+    ghost images of the state and of the scale fields evolve as the cells they mirror, since
+    the flux sum ((+x) + (-x)) + ((+y) + (-y)) is unchanged by a mirror image."""
+    st = inputs.epidemic_state(nx, ny, 7 * nx + ny).astype(np.float32)
+    kx, ky = (f.astype(np.float32) for f in inputs.mobility_fields(nx, ny, 3 + nx, "random"))
+    ref = _vard_fp32(nx, ny, bc, st, kx, ky)
+    ref.set_blocking(1)
+    refs = {}
+    for n in range(1, 17):
+        ref.step(1)
+        refs[n] = ref.checkpoint()[128:].view(np.uint32)
+    ref.close()
+    for k in range(2, 9):
+        s = _vard_fp32(nx, ny, bc, st, kx, ky)
+        s.set_blocking(k)
+        s.step(2 * k)
+        assert np.array_equal(s.checkpoint()[128:].view(np.uint32), refs[2 * k]), (k, nx, ny, bc)
+        s.close()
+    for k in (3, 8):
+        s = _vard_fp32(nx, ny, bc, st, kx, ky)
+        s.set_blocking(k)
+        s.step(11)
+        assert np.array_equal(s.checkpoint()[128:].view(np.uint32), refs[11]), (k, 11)
+        s.close()
+
+
+@pytest.mark.parametrize("depth,seg_rows", [(3, 12), (3, 50), (8, 32), (8, 41), (6, 100), (7, 28), (2, 8)])
+def test_fp32_blocked_segment_lengths_give_identical_bits(depth, seg_rows):
+    """2 x depth steps under no-flux: two passes of this depth with this row-segment length."""
+    nx, ny = 300, 333
+    st = inputs.epidemic_state(nx, ny, 5).astype(np.float32)
+    kx, ky = (f.astype(np.float32) for f in inputs.mobility_fields(nx, ny, 9, "regions"))
+    ref = _vard_fp32(nx, ny, L.BC_NOFLUX, st, kx, ky)
+    ref.set_blocking(1)
+    ref.step(2 * depth)
+    want = ref.checkpoint()[128:].view(np.uint32)
+    ref.close()
+    s = _vard_fp32(nx, ny, L.BC_NOFLUX, st, kx, ky)
+    s.set_blocking(depth, seg_rows)
+    s.step(2 * depth)
+    assert np.array_equal(s.checkpoint()[128:].view(np.uint32), want)
+    s.close()
+
+
+def test_fp32_blocked_autotuned_long_run_matches_oracle():
+    """200 steps at the autotuned blocking against the FP64 oracle (FP32 tolerance), with the
+    population conserved to FP32 rounding."""
+    nx, ny = 96, 70
+    st = inputs.epidemic_state(nx, ny, 21).astype(np.float32)
+    kx, ky = (f.astype(np.float32) for f in inputs.mobility_fields(nx, ny, 13, "regions"))
+    s = _vard_fp32(nx, ny, L.BC_NOFLUX, st, kx, ky)
+    depth, seg, _ = s.autotune(50.0)
+    assert 1 <= depth <= 8 and (depth == 1 or seg >= 4 * depth)
+    assert np.array_equal(s.read(dtype=np.float32), st)  # the tuner left the state
+    s.step(200)
+    got = s.read()
+    tot, _ = s.diagnostics()
+    s.close()
+    ref = oracle.sslbm_vard_run(st.astype(np.float64), TAU, RATES, kx.astype(np.float64), ky.astype(np.float64),
+                                1.0, L.BC_NOFLUX, 200)
+    assert relmax(got, ref) <= 1e-4
+    s0 = float(st.astype(np.float64).sum())
+    assert abs(float(tot.sum()) - s0) / s0 < 200 * 4 * 6e-8
