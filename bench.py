@@ -48,7 +48,7 @@ FD4_PLANES_PER_CELL = 85  # RK4 stage kernels: 15 + 25 + 25 + 20 plane reads and
 
 
 PIPE_SOURCES = ("paper_2603_19789_gb300/csrc/sslbm_pipe.cuh", "paper_2603_19789_gb300/csrc/sslbm_internal.cuh",
-                "paper_2603_19789_gb300/csrc/sslbm_kernels.cu")
+                "paper_2603_19789_gb300/csrc/sslbm_kernels.cu", "paper_2603_19789_gb300/csrc/pipe_launch.cuh")
 
 
 def captured_traffic(depth: int, cells: int):
