@@ -636,12 +636,12 @@ int sslbm_debug_bounds(long long* count, long long* value, long long* limit, int
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize(bounds records)");
   int (*const take[])(sslbm::OobRecord*) = {sslbm::oob_take_kernels, sslbm::oob_take_ensemble, sslbm::oob_take_bgk,
                                             sslbm::oob_take_io, sslbm::oob_take_stream,
-                                            sslbm::oob_take_lattices};
-  const int tu_site[] = {0, 100, 200, 300, 400, 500};  // site numbers are offset by translation unit
+                                            sslbm::oob_take_d2q9, sslbm::oob_take_d2q9a, sslbm::oob_take_vard};
+  const int tu_site[] = {0, 100, 200, 300, 400, 500, 600, 700};  // site numbers are offset by translation unit
   unsigned long long total = 0;
   sslbm::OobRecord first{};
   int first_site = -1;
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < 8; ++i) {
     sslbm::OobRecord r{};
     if (take[i](&r) != 0) return fail(SSLBM_ERR_CUDA, "reading the bounds record of unit %d", i);
     if (r.count && first_site < 0) {

@@ -1,7 +1,8 @@
 // pipe_launch.cuh -- the kernel and the host launchers of the temporal-blocked pipeline tile
 // (sslbm_pipe.cuh), instantiated per mode by the translation units that launch it:
-// sslbm_kernels.cu for the D2Q5 storages, pipe_lattices.cu for the D2Q9 and varying-diffusion
-// lattices (two units so that the builds compile in parallel).
+// sslbm_kernels.cu for the D2Q5 storages, pipe_d2q9.cu, pipe_d2q9_aligned.cu and pipe_vard.cu
+// for the D2Q9 and varying-diffusion lattices (separate units, so that the build compiles them
+// in parallel).
 #pragma once
 #include <atomic>
 
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(32 * K, 16 / K) pipe_kernel(const GridView g, 
   const int strip = (int)(blockIdx.x % (unsigned)nstrips);
   const int64_t y0 = (int64_t)(blockIdx.x / (unsigned)nstrips) * seg_rows;
   const int64_t y1 = (y0 + seg_rows < g.ny) ? y0 + seg_rows : g.ny;
-  if (MODE == MODE_D2Q9_NOFLUX && strip != 0 && strip != nstrips - 1)
+  if ((MODE == MODE_D2Q9_NOFLUX || MODE == MODE_D2Q9_NOFLUX4) && strip != 0 && strip != nstrips - 1)
     pipe_tile<MODE, K, false, false>(sm, g, k, in, out, strip, y0, y1);  // no wall column in this strip
   else
     pipe_tile<MODE, K>(sm, g, k, in, out, strip, y0, y1, kx, ky, rk);
@@ -86,7 +87,7 @@ int default_seg_rows_t(const GridView& g) {
   // one wave: as many CTAs as fit on the device at once, split into row segments.  D2Q9
   // no-flux: two waves, since the first and last strips (wall code) take longer than the rest
   const int64_t resident = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-  int64_t nseg = (MODE == MODE_D2Q9_NOFLUX ? 2 : 1) * resident / nstrips;
+  int64_t nseg = (MODE == MODE_D2Q9_NOFLUX || MODE == MODE_D2Q9_NOFLUX4 ? 2 : 1) * resident / nstrips;
   if (nseg < 1) nseg = 1;
   int64_t rows = (g.ny + nseg - 1) / nseg;
   if (rows < 4 * K) rows = 4 * K;

@@ -24,7 +24,8 @@ enum Mode {
   MODE_SPLIT = 3,
   MODE_D2Q9 = 4,
   MODE_D2Q9_NOFLUX = 5,
-  MODE_VARD = 6
+  MODE_VARD = 6,
+  MODE_D2Q9_NOFLUX4 = 7  // no-flux with nx a multiple of 4: x = nx - 1 ends a lane's four columns
 };
 
 // Stored planes per state of a mode: the five compartments, plus the compensation of S
@@ -294,6 +295,10 @@ bool blocked_supported(int precision, const GridView& g);
 cudaError_t launch_sslbm9_blocked(const GridView& g, const void* coeffs, const void* in, void* out, int depth,
                                   int seg_rows, cudaStream_t s);
 int blocked9_default_seg_rows(const GridView& g, int depth);
+// ... under no-flux with nx a multiple of 4 (pipe_d2q9_aligned.cu)
+cudaError_t launch_sslbm9_aligned_blocked(const GridView& g, const void* coeffs, const void* in, void* out,
+                                          int depth, int seg_rows, cudaStream_t s);
+int blocked9_aligned_default_seg_rows(const GridView& g, int depth);
 // The varying-diffusion lattice (plain FP32 storage, scale planes kx, ky): K fused steps per
 // launch, and its default segment.
 cudaError_t launch_sslbm_vard_blocked(const GridView& g, const void* coeffs, const void* kx, const void* ky,

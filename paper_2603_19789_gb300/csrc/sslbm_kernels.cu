@@ -6,8 +6,8 @@
 //                   and two scalar edge loads; neighbouring rows come from L1/L2.  The FP32
 //                   storages advance one step per launch in the streaming kernel (stream.cu).
 //   pipe_kernel     (pipe_launch.cuh) K steps per launch (temporal blocking, K = 2..8) for
-//                   FP32, FP32 deviation-S and FP32 split-S (a sixth plane); pipe_lattices.cu
-//                   instantiates it for FP32 on the D2Q9 lattice (periodic, or no-flux with the
+//                   FP32, FP32 deviation-S and FP32 split-S (a sixth plane); pipe_d2q9*.cu and
+//                   pipe_vard.cu instantiate it for FP32 on the D2Q9 lattice (periodic, or no-flux with the
 //                   bounce-back substituted into the row update) and on the varying-diffusion
 //                   lattice (the scale rows in a static shared-memory ring), as a pipeline of
 //                   K warps per

@@ -105,13 +105,14 @@ __device__ __forceinline__ void cell_row(const Coeffs<float>& k, const float2 (&
 // time (h = 0: columns 0, 1 with the left neighbours shuffled in; h = 1: columns 2, 3 with the
 // right ones), which keeps the live registers within the pipeline's budget.
 //
+// ALIGNED: nx is a multiple of 4, so x = nx - 1 is column 3 of its lane (jr = 3 or none).
 // WALLS (no-flux): a link that leaves the domain sees the cell's own value (halfway
 // bounce-back).  At x = 0 (column 0 of the lane with xs = 0) the shuffled-in left neighbours
 // of the three rows are replaced by the centre; at x = nx - 1 (column jr of its lane) the right
 // neighbours, in-lane or shuffled in, likewise.  ROWWALL (row 0 or ny - 1, warp-uniform): the
 // row beyond the wall enters as the centre, its pair sum as centre + centre.  Cells outside the
 // domain are never read by an in-domain cell, so their values do not matter.
-template <bool ROWWALL, bool WALLS>
+template <bool ROWWALL, bool WALLS, bool ALIGNED = false>
 __device__ __forceinline__ void cell_row9(const Coeffs<float>& k, const GridView& g, const float2 (&P)[5][2],
                                           const float2 (&C)[5][2], const float2 (&N)[5][2], float2 (&M)[5][2],
                                           const int64_t xs, const int64_t row) {
@@ -133,20 +134,20 @@ __device__ __forceinline__ void cell_row9(const Coeffs<float>& k, const GridView
       float RP, RC, RN;
       if (h == 0) {
         if (WALLS && wl) XP = XC = XN = C[f][0].x;
-        const bool w0 = WALLS && jr == 0;
+        const bool w0 = WALLS && !ALIGNED && jr == 0;
         RP = w0 ? C[f][0].x : P[f][0].y;
         RC = w0 ? C[f][0].x : C[f][0].y;
         RN = w0 ? C[f][0].x : N[f][0].y;
       } else {
         if (WALLS && jr == 3) XP = XC = XN = C[f][1].y;
-        const bool w2 = WALLS && jr == 2;
+        const bool w2 = WALLS && !ALIGNED && jr == 2;
         RP = w2 ? C[f][1].x : P[f][1].y;
         RC = w2 ? C[f][1].x : C[f][1].y;
         RN = w2 ? C[f][1].x : N[f][1].y;
       }
       float2 hP, hC, hN;
       if (h == 0) {
-        const bool w1 = WALLS && jr == 1;
+        const bool w1 = WALLS && !ALIGNED && jr == 1;
         hP = make_float2(__fadd_rn(XP, RP), __fadd_rn(P[f][0].x, w1 ? C[f][0].y : P[f][1].x));
         hC = make_float2(__fadd_rn(XC, RC), __fadd_rn(C[f][0].x, w1 ? C[f][0].y : C[f][1].x));
         hN = make_float2(__fadd_rn(XN, RN), __fadd_rn(N[f][0].x, w1 ? C[f][0].y : N[f][1].x));
@@ -272,22 +273,23 @@ __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g
     }
   };
   float2 M[NF][2];
-  if constexpr (MODE == MODE_D2Q9 || MODE == MODE_D2Q9_NOFLUX) {
+  if constexpr (MODE == MODE_D2Q9 || MODE == MODE_D2Q9_NOFLUX || MODE == MODE_D2Q9_NOFLUX4) {
     // the second row of the pair is read after the first is done: fewer live registers for
     // the nine-point stencil's wider neighbourhood
-    constexpr bool W = MODE == MODE_D2Q9_NOFLUX;
+    constexpr bool W = MODE == MODE_D2Q9_NOFLUX || MODE == MODE_D2Q9_NOFLUX4;
+    constexpr bool AL = MODE == MODE_D2Q9_NOFLUX4;
     const int64_t row = r + 3 * (K - 1 - s);  // the first row this warp computes (r: the last warp's)
     load_row(src, N0);
     if (W && (row == 0 || row == g.ny - 1))
       cell_row9<true, W>(k, g, A, B, N0, M, xs, row);
     else
-      cell_row9<false, W && COLW>(k, g, A, B, N0, M, xs, row);
+      cell_row9<false, W && COLW, AL>(k, g, A, B, N0, M, xs, row);
     emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
     load_row(src + 128 * NF, N1);
     if (W && (row + 1 == 0 || row + 1 == g.ny - 1))
       cell_row9<true, W>(k, g, B, N0, N1, M, xs, row + 1);
     else
-      cell_row9<false, W && COLW>(k, g, B, N0, N1, M, xs, row + 1);
+      cell_row9<false, W && COLW, AL>(k, g, B, N0, N1, M, xs, row + 1);
   } else if constexpr (MODE == MODE_VARD) {
     // sk: the static-ring slot of the first row this warp computes (row b - 1)
     auto krow = [&](int d, int plane) {  // this lane's columns of scale plane `plane`, row b - 1 + d
