@@ -99,7 +99,8 @@ typedef struct sslbm_grid {
   int32_t schemes;     /* SSLBM_WANT_SSLBM | SSLBM_WANT_BGK: which state to hold */
   int32_t lattice;     /* SSLBM_LATTICE_D2Q5 (0), SSLBM_LATTICE_D2Q9 (1),
                           SSLBM_LATTICE_D2Q5_SLBM (2) or SSLBM_LATTICE_D2Q5_VARD (3); 1 to 3:
-                          SSLBM scheme only, FP64 or FP32, no temporal blocking */
+                          SSLBM scheme only, FP64 or FP32; temporal blocking for FP32 on
+                          D2Q9 and D2Q5_VARD (sslbm_set_blocking) */
 } sslbm_grid;
 
 /* Epidemiological parameters in the notation of Table I:
