@@ -713,25 +713,11 @@ def ensemble_timing(L, torch, stream, n_scen=512, steps=5000, err_scen=6, fp64_s
     scenario on the same GPU.  The FP64 time is measured on one scenario of each grid size
     for fp64_steps steps and weighted by the ensemble's size mix; the FP32 error is the
     root-mean-square difference from FP64 per compartment (density units, total ~1) on the
-    first err_scen scenarios after all steps."""
+    first err_scen scenarios after all steps.  The same run with S stored as a hi/lo pair
+    (FP32_SPLIT, autotuned on its own) is reported under "split": its throughput and error."""
     from paper_2603_19789_gb300 import inputs
     scen = inputs.ensemble_scenarios(n_scen)
     specs = [dict(nx=s["nx"], ny=s["ny"], rates=s["rates"].as_tuple(), d=s["d"]) for s in scen]
-    ens = L.Ensemble(specs, precision=L.FP32)
-    if tiling:
-        ens.set_tiling(*tiling)
-        depth, seg = tiling
-    else:
-        depth, seg, _ = ens.autotune(trial_blocks=2)
-    for i, s in enumerate(scen):
-        ens.write(i, inputs.ensemble_state(s).astype(np.float32))
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    ens.run(steps)
-    b.record(stream)
-    b.synchronize()
-    ms = a.elapsed_time(b)
     cells = sum(s["nx"] * s["ny"] for s in scen)
     # plain FP64 SSLBM, one scenario per grid size
     per_size = {}
@@ -750,20 +736,48 @@ def ensemble_timing(L, torch, stream, n_scen=512, steps=5000, err_scen=6, fp64_s
         per_size[s["nx"]] = e0.elapsed_time(e1) / fp64_steps
         f.close()
     fp64_ms = sum(per_size[s["nx"]] * steps for s in scen)
-    # error of the FP32 ensemble against FP64 on a few scenarios
-    rms = np.zeros(5)
+    # FP64 references of the first err_scen scenarios
+    refs = []
     for i in range(min(err_scen, n_scen)):
         s = scen[i]
         f = L.Solver(s["nx"], s["ny"], s["rates"].as_tuple(), d=s["d"], bc=L.BC_PERIODIC, precision=L.FP64)
         f.write(inputs.ensemble_state(s))
         f.step(steps)
-        ref = f.read()
+        refs.append(f.read())
         f.close()
-        got = ens.read(i)
-        rms = np.maximum(rms, np.sqrt(((got - ref) ** 2).reshape(5, -1).mean(axis=1)))
-    ens.close()
-    del ens
-    torch.cuda.empty_cache()
+
+    def run(precision, tile):
+        ens = L.Ensemble(specs, precision=precision)
+        if tile:
+            ens.set_tiling(*tile)
+            depth, seg = tile
+        else:
+            depth, seg, _ = ens.autotune(trial_blocks=2)
+        for i, s in enumerate(scen):
+            ens.write(i, inputs.ensemble_state(s).astype(np.float32))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ens.run(steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        rms = np.zeros(5)
+        for i, ref in enumerate(refs):
+            got = ens.read(i)
+            rms = np.maximum(rms, np.sqrt(((got - ref) ** 2).reshape(5, -1).mean(axis=1)))
+        ens.close()
+        del ens
+        torch.cuda.empty_cache()
+        return depth, seg, ms, rms
+
+    depth, seg, ms, rms = run(L.FP32, tiling)
+    sdepth, sseg, sms, srms = run(L.FP32_SPLIT, None)
+
+    def errs(r):
+        return {"S": r[0], "E": r[1], "I": r[2], "R": r[3], "D": r[4], "scenarios": err_scen,
+                "units": "density (total ~1)"}
+
     return {"scenarios": n_scen, "steps": steps, "cells": cells, "precision": "fp32",
             "tiling": {"depth": depth, "seg_rows": seg, "chosen_by": "--ens-tiling" if tiling else "autotuner"},
             "launch": "one persistent kernel per run, replayed from a CUDA graph",
@@ -773,8 +787,11 @@ def ensemble_timing(L, torch, stream, n_scen=512, steps=5000, err_scen=6, fp64_s
             "fp64_plain_note": f"plain FP64 SSLBM per scenario, {fp64_steps} steps timed on one "
                                "scenario per grid size, weighted by the size mix",
             "speedup_vs_fp64": fp64_ms / ms,
-            "rms_error_vs_fp64": {"S": rms[0], "E": rms[1], "I": rms[2], "R": rms[3], "D": rms[4],
-                                  "scenarios": err_scen, "units": "density (total ~1)"}}
+            "rms_error_vs_fp64": errs(rms),
+            "split": {"precision": "fp32_split", "tiling": {"depth": sdepth, "seg_rows": sseg},
+                      "ms": sms, "scenario_steps_per_s": n_scen * steps / (sms * 1e-3),
+                      "glups": cells * steps / (sms * 1e-3) / 1e9, "speedup_vs_fp64": fp64_ms / sms,
+                      "rms_error_vs_fp64": errs(srms)}}
 
 
 if __name__ == "__main__":

@@ -346,7 +346,9 @@ typedef struct sslbm_scenario {
 
 typedef struct sslbm_ensemble sslbm_ensemble;
 
-/* Workspace bytes for n scenarios in the given precision (SSLBM_FP32 or SSLBM_FP32_DEV). */
+/* Workspace bytes for n scenarios in the given precision (SSLBM_FP32, SSLBM_FP32_DEV or
+ * SSLBM_FP32_SPLIT; the split storage keeps a sixth plane per scenario, the compensation of S;
+ * others: SSLBM_ERR_UNSUPPORTED). */
 int sslbm_ensemble_workspace_bytes(int n, const sslbm_scenario* sc, int precision, size_t* bytes);
 
 /* Create an ensemble (scenarios copied; states zero until written).  dev_ws: caller-owned,
@@ -369,7 +371,8 @@ int sslbm_ensemble_get_tiling(const sslbm_ensemble* e, int* depth, int* seg_rows
 int sslbm_ensemble_set_wait_limit(sslbm_ensemble* e, long long spin_limit, long long stall_item);
 
 /* Set / get all five planes ([5][ny][nx]) of scenario idx, as in sslbm_write / sslbm_read
- * (FP64 or FP32 values; host or device memory).  Both synchronise the stream. */
+ * (FP64 or FP32 values; host or device memory; under FP32_SPLIT a write sets the compensation
+ * of S to zero and a read returns value - compensation).  Both synchronise the stream. */
 int sslbm_ensemble_write(sslbm_ensemble* e, int idx, const void* src, int src_dtype, int on_device);
 int sslbm_ensemble_read(sslbm_ensemble* e, int idx, void* dst, int dst_dtype, int on_device);
 
@@ -394,7 +397,8 @@ int64_t sslbm_ensemble_steps_done(const sslbm_ensemble* e);
 
 /* Checkpoint / resume of an ensemble (not part of the paper's method), as sslbm_checkpoint_*
  * for one grid: the stored FP32
- * planes of every scenario (sigma = s_ref - S under FP32_DEV, as stored) and the step
+ * planes of every scenario (sigma = s_ref - S under FP32_DEV, the sixth plane under
+ * FP32_SPLIT, as stored) and the step
  * counter, so that a resumed run gives the bits of the uninterrupted one.  Layout: a 64-byte
  * header (magic "SSLE", version 2, n, precision, steps), then (nx, ny, s_ref) of every
  * scenario as two int64 and a double, padded to a multiple of 128 bytes, then per scenario

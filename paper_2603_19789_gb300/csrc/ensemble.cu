@@ -14,8 +14,9 @@
 // it runs out the CTA raises an error flag, and all CTAs stop taking work as soon as they
 // see the flag; the host then reports SSLBM_ERR_TIMEOUT.
 //
-// State layout: two buffers; in each, scenario s owns five planes (pitched as in
-// sslbm_internal.cuh) starting at element offset off[s].  Loads use L2-only cp.async.cg
+// State layout: two buffers; in each, scenario s owns the planes of its storage -- five, or
+// six with the compensation of S of the split storage (pitched as in sslbm_internal.cuh) --
+// starting at element offset off[s].  Loads use L2-only cp.async.cg
 // (periodic grids, nx a multiple of 4), because other CTAs of the same launch write them.
 #include <algorithm>
 #include <cmath>
@@ -81,7 +82,8 @@ __global__ void __launch_bounds__(32 * K, 16 / K)
                     EnsControl* ctl, unsigned* done, const long long spin_limit,
                     const long long stall_item) {
   extern __shared__ __align__(16) unsigned char ens_smem[];
-  sslbm::PipeSmem<K>& sm = *reinterpret_cast<sslbm::PipeSmem<K>*>(ens_smem);
+  using Smem = sslbm::PipeSmem<K, sslbm::mode_planes<MODE>()>;
+  Smem& sm = *reinterpret_cast<Smem*>(ens_smem);
   __shared__ long long item_sh;
   __shared__ int go_sh;
   const long long total = (long long)nblocks * total_tiles;
@@ -151,18 +153,23 @@ EnsKernel pick_kernel(int depth) {
   }
 }
 
-// dynamic shared memory of the pipeline tile at this depth
-size_t pipe_smem_bytes(int depth) {
+template <int NF>
+size_t pipe_smem_bytes_nf(int depth) {
   switch (depth) {
-    case 2: return sizeof(sslbm::PipeSmem<2>);
-    case 3: return sizeof(sslbm::PipeSmem<3>);
-    case 4: return sizeof(sslbm::PipeSmem<4>);
-    case 5: return sizeof(sslbm::PipeSmem<5>);
-    case 6: return sizeof(sslbm::PipeSmem<6>);
-    case 7: return sizeof(sslbm::PipeSmem<7>);
-    case 8: return sizeof(sslbm::PipeSmem<8>);
+    case 2: return sizeof(sslbm::PipeSmem<2, NF>);
+    case 3: return sizeof(sslbm::PipeSmem<3, NF>);
+    case 4: return sizeof(sslbm::PipeSmem<4, NF>);
+    case 5: return sizeof(sslbm::PipeSmem<5, NF>);
+    case 6: return sizeof(sslbm::PipeSmem<6, NF>);
+    case 7: return sizeof(sslbm::PipeSmem<7, NF>);
+    case 8: return sizeof(sslbm::PipeSmem<8, NF>);
     default: return 0;
   }
+}
+
+// dynamic shared memory of the pipeline tile at this depth (six planes under the split storage)
+size_t pipe_smem_bytes(int depth, int precision) {
+  return precision == SSLBM_FP32_SPLIT ? pipe_smem_bytes_nf<6>(depth) : pipe_smem_bytes_nf<5>(depth);
 }
 
 constexpr size_t kAlign = 256;
@@ -174,7 +181,10 @@ struct EnsLayout {
   int64_t buf_elems;
 };
 
-int make_layout(int n, const sslbm_scenario* sc, EnsLayout* L) {
+// planes a scenario stores: five, and the compensation of S under the split storage
+int ens_planes(int precision) { return precision == SSLBM_FP32_SPLIT ? 6 : 5; }
+
+int make_layout(int n, const sslbm_scenario* sc, int precision, EnsLayout* L) {
   L->pitch.resize(n);
   L->plane.resize(n);
   L->elem_off.resize(n);
@@ -183,7 +193,7 @@ int make_layout(int n, const sslbm_scenario* sc, EnsLayout* L) {
     L->pitch[i] = (sc[i].nx + 31) / 32 * 32;
     L->plane[i] = (L->pitch[i] * sc[i].ny + 63) / 64 * 64;
     L->elem_off[i] = e;
-    e += 5 * L->plane[i];
+    e += ens_planes(precision) * L->plane[i];
   }
   L->buf_elems = e;
   size_t off = 0;
@@ -209,8 +219,8 @@ int check_scenarios(int n, const sslbm_scenario* sc, int bc, int precision) {
   if (n < 1 || !sc) return err(SSLBM_ERR_BAD_ARG, "need n >= 1 scenarios");
   if (bc != SSLBM_BC_PERIODIC)
     return err(SSLBM_ERR_UNSUPPORTED, "the ensemble launch takes periodic grids");
-  if (precision != SSLBM_FP32 && precision != SSLBM_FP32_DEV)
-    return err(SSLBM_ERR_UNSUPPORTED, "the ensemble launch runs FP32 or FP32_DEV");
+  if (precision != SSLBM_FP32 && precision != SSLBM_FP32_DEV && precision != SSLBM_FP32_SPLIT)
+    return err(SSLBM_ERR_UNSUPPORTED, "the ensemble launch runs FP32, FP32_DEV or FP32_SPLIT");
   for (int i = 0; i < n; ++i) {
     const sslbm_scenario& s = sc[i];
     if (s.nx < 4 || s.ny < 1 || s.nx % 4 || s.nx > (1 << 24) || s.ny > (1 << 24))
@@ -303,7 +313,7 @@ int upload_table(sslbm_ensemble* e) {
   return SSLBM_OK;
 }
 
-int resident_ctas(EnsKernel kern, int depth, int* out) {
+int resident_ctas(EnsKernel kern, int depth, int precision, int* out) {
   int dev = 0, sms = 0, per = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -311,9 +321,10 @@ int resident_ctas(EnsKernel kern, int depth, int* out) {
     ce = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                               cudaSharedmemCarveoutMaxShared);
   if (ce == cudaSuccess)
-    ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe_smem_bytes(depth));
+    ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)pipe_smem_bytes(depth, precision));
   if (ce == cudaSuccess)
-    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * depth, pipe_smem_bytes(depth));
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * depth, pipe_smem_bytes(depth, precision));
   if (ce != cudaSuccess) return cuda_err(ce, "occupancy query");
   *out = sms * (per > 0 ? per : 1);
   return SSLBM_OK;
@@ -323,8 +334,9 @@ int resident_ctas(EnsKernel kern, int depth, int* out) {
 // CUDA graph and replayed.
 int launch_blocks(sslbm_ensemble* e, int nblocks) {
   if (nblocks <= 0) return SSLBM_OK;
-  EnsKernel kern = e->precision == SSLBM_FP32_DEV ? pick_kernel<sslbm::MODE_DEV>(e->depth)
-                                                  : pick_kernel<sslbm::MODE_PLAIN>(e->depth);
+  EnsKernel kern = e->precision == SSLBM_FP32_DEV     ? pick_kernel<sslbm::MODE_DEV>(e->depth)
+                    : e->precision == SSLBM_FP32_SPLIT ? pick_kernel<sslbm::MODE_SPLIT>(e->depth)
+                                                       : pick_kernel<sslbm::MODE_PLAIN>(e->depth);
   if (!kern) return err(SSLBM_ERR_BAD_ARG, "depth %d has no ensemble kernel", e->depth);
   if (!(e->exec && e->exec_blocks == nblocks && e->exec_cur == e->cur && e->exec_depth == e->depth)) {
     if (e->exec) {
@@ -332,7 +344,7 @@ int launch_blocks(sslbm_ensemble* e, int nblocks) {
       e->exec = nullptr;
     }
     int grid = 0;
-    int st = resident_ctas(kern, e->depth, &grid);
+    int st = resident_ctas(kern, e->depth, e->precision, &grid);
     if (st) return st;
     cudaStream_t cap;
     cudaError_t ce = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
@@ -344,7 +356,7 @@ int launch_blocks(sslbm_ensemble* e, int nblocks) {
     if (ce == cudaSuccess) {
       float* b0 = e->buf(e->cur);
       float* b1 = e->buf(1 - e->cur);
-      kern<<<grid, 32 * e->depth, pipe_smem_bytes(e->depth), cap>>>(e->dtab(), e->n, e->total_tiles, nblocks, b0, b1, e->ctl(),
+      kern<<<grid, 32 * e->depth, pipe_smem_bytes(e->depth, e->precision), cap>>>(e->dtab(), e->n, e->total_tiles, nblocks, b0, b1, e->ctl(),
                                             e->done(), e->spin_limit, e->stall_item);
       ce = cudaGetLastError();
     }
@@ -393,7 +405,7 @@ int sslbm_ensemble_workspace_bytes(int n, const sslbm_scenario* sc, int precisio
   int st = check_scenarios(n, sc, SSLBM_BC_PERIODIC, precision);
   if (st) return st;
   EnsLayout L;
-  make_layout(n, sc, &L);
+  make_layout(n, sc, precision, &L);
   *bytes = L.total;
   return SSLBM_OK;
 }
@@ -405,7 +417,7 @@ int sslbm_ensemble_create(int n, const sslbm_scenario* sc, int precision, void* 
   int st = check_scenarios(n, sc, SSLBM_BC_PERIODIC, precision);
   if (st) return st;
   EnsLayout L;
-  make_layout(n, sc, &L);
+  make_layout(n, sc, precision, &L);
   if (!dev_ws || reinterpret_cast<uintptr_t>(dev_ws) % kAlign)
     return err(SSLBM_ERR_WORKSPACE, "workspace missing or not 256-byte aligned");
   if (ws_bytes < L.total)
@@ -493,7 +505,8 @@ int sslbm_ensemble_write(sslbm_ensemble* e, int idx, const void* src, int src_dt
       s = staging;
     }
     const int dev_S = (e->precision == SSLBM_FP32_DEV && c == 0) ? 1 : 0;
-    ce = sslbm::launch_plane_write(SSLBM_FP32, g, s, src_dtype, e->plane(e->cur, idx, c), nullptr, dev_S,
+    void* comp = (e->precision == SSLBM_FP32_SPLIT && c == 0) ? e->plane(e->cur, idx, 5) : nullptr;
+    ce = sslbm::launch_plane_write(SSLBM_FP32, g, s, src_dtype, e->plane(e->cur, idx, c), comp, dev_S,
                                    e->sc[idx].s_ref, e->stream);
     if (ce != cudaSuccess) return cuda_err(ce, "plane write");
   }
@@ -516,7 +529,8 @@ int sslbm_ensemble_read(sslbm_ensemble* e, int idx, void* dst, int dst_dtype, in
   for (int c = 0; c < 5; ++c) {
     char* d = static_cast<char*>(dst) + c * bytes;
     const int dev_S = (e->precision == SSLBM_FP32_DEV && c == 0) ? 1 : 0;
-    cudaError_t ce = sslbm::launch_plane_read(SSLBM_FP32, g, e->plane(e->cur, idx, c), nullptr, dev_S,
+    const void* comp = (e->precision == SSLBM_FP32_SPLIT && c == 0) ? e->plane(e->cur, idx, 5) : nullptr;
+    cudaError_t ce = sslbm::launch_plane_read(SSLBM_FP32, g, e->plane(e->cur, idx, c), comp, dev_S,
                                               e->sc[idx].s_ref, on_device ? d : staging, dst_dtype,
                                               e->stream);
     if (ce != cudaSuccess) return cuda_err(ce, "plane read");
@@ -562,9 +576,10 @@ int sslbm_ensemble_diagnostics(sslbm_ensemble* e, double* totals, double* peak_I
   double* partials = reinterpret_cast<double*>(e->ws + e->L.off_partials);
   double* results = reinterpret_cast<double*>(e->ws + e->L.off_results);
   for (int i = 0; i < e->n; ++i) {
-    cudaError_t ce = sslbm::launch_diagnostics(SSLBM_FP32, 0, e->gv(i), e->plane(e->cur, i, 0), nullptr,
-                                               partials, results + (size_t)i * sslbm::kDiagSlots,
-                                               e->stream);
+    const bool split = e->precision == SSLBM_FP32_SPLIT;  // S = value - compensation (plane 5)
+    cudaError_t ce = sslbm::launch_diagnostics(SSLBM_FP32, 0, e->gv(i), e->plane(e->cur, i, 0),
+                                               split ? e->plane(e->cur, i, 5) : nullptr, partials,
+                                               results + (size_t)i * sslbm::kDiagSlots, e->stream, 1);
     if (ce != cudaSuccess) return cuda_err(ce, "diagnostics");
   }
   std::vector<double> r((size_t)e->n * sslbm::kDiagSlots);
@@ -674,7 +689,7 @@ size_t ens_ckpt_data_offset(int n) {
 
 size_t ens_ckpt_bytes(const sslbm_ensemble* e) {
   size_t b = ens_ckpt_data_offset(e->n);
-  for (int i = 0; i < e->n; ++i) b += (size_t)5 * e->sc[i].nx * e->sc[i].ny * sizeof(float);
+  for (int i = 0; i < e->n; ++i) b += (size_t)ens_planes(e->precision) * e->sc[i].nx * e->sc[i].ny * sizeof(float);
   return b;
 }
 }  // namespace
@@ -720,7 +735,7 @@ int sslbm_ensemble_checkpoint_save(sslbm_ensemble* e, void* dst, size_t bytes, i
   for (int i = 0; i < e->n; ++i) {
     const GridView g = e->gv(i);
     const size_t row = (size_t)g.nx * sizeof(float);
-    for (int c = 0; c < 5; ++c, d += row * (size_t)g.ny) {
+    for (int c = 0; c < ens_planes(e->precision); ++c, d += row * (size_t)g.ny) {
       ce = cudaMemcpy2DAsync(d, row, e->plane(e->cur, i, c), (size_t)g.pitch * sizeof(float), row, (size_t)g.ny,
                              dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, e->stream);
       if (ce != cudaSuccess) return cuda_err(ce, "cudaMemcpy2DAsync(checkpoint save)");
@@ -780,7 +795,7 @@ int sslbm_ensemble_checkpoint_load(sslbm_ensemble* e, const void* src, size_t by
   for (int i = 0; i < e->n; ++i) {
     const GridView g = e->gv(i);
     const size_t row = (size_t)g.nx * sizeof(float);
-    for (int c = 0; c < 5; ++c, s += row * (size_t)g.ny) {
+    for (int c = 0; c < ens_planes(e->precision); ++c, s += row * (size_t)g.ny) {
       ce = cudaMemcpy2DAsync(e->plane(e->cur, i, c), (size_t)g.pitch * sizeof(float), s, row, row, (size_t)g.ny,
                              src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, e->stream);
       if (ce != cudaSuccess) return cuda_err(ce, "cudaMemcpy2DAsync(checkpoint load)");

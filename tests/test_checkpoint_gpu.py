@@ -197,7 +197,7 @@ def _ensemble(specs, precision=L.FP32):
 
 
 @pytest.mark.parametrize("on_device", [False, True])
-@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV])
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_SPLIT])
 def test_ensemble_resume_gives_the_bits_of_the_uninterrupted_run(precision, on_device):
     specs = _ens_specs()
     a = _ensemble(specs, precision)

@@ -1,8 +1,8 @@
 """The persistent ensemble launch against the single-grid solver and the oracle.
 
-Every scenario of an ensemble must give the same bits as a single-grid FP32 solver
-with the same parameters (one-step kernel), and agree with the FP64 oracle to FP32
-accuracy.  The bounded dependency waits are exercised by a host-side fault injection:
+Every scenario of an ensemble must give the same bits as a single-grid solver of the same
+storage (FP32, FP32 deviation-S, FP32 split-S) with the same parameters (one-step kernel),
+and agree with the FP64 oracle to FP32 accuracy.  The bounded dependency waits are exercised by a host-side fault injection:
 one work item never reports completion, so the waits behind it run out and the run
 returns SSLBM_ERR_TIMEOUT; the GPU stays usable afterwards.
 """
@@ -51,7 +51,7 @@ def _single(sp, st, n, precision=L.FP32):
     return out
 
 
-@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV])
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_SPLIT])
 @pytest.mark.parametrize("depth,seg", [(4, 64), (2, 16), (3, 12), (8, 32), (6, 256)])
 def test_ensemble_matches_single_grid_bits(precision, depth, seg):
     specs = _specs()
@@ -143,3 +143,35 @@ def test_ensemble_rejects_what_it_does_not_run():
     with pytest.raises(L.SslbmError):
         L.sslbm_ensemble_workspace_bytes(L.make_scenarios([dict(nx=8, ny=8, rates=(0.3, 0.2, 0.1, 0.1),
                                                                 d=(0.05,) * 4)]), precision=L.FP64)
+
+
+def test_split_ensemble_diagnostics_and_accuracy():
+    """The split storage of S in the ensemble: totals as the single-grid split solver reports
+    them (value - compensation), and S after 400 steps of a small-seed epidemic closer to the
+    FP64 oracle than plain FP32's."""
+    specs = _specs(seed=11)[:3]
+    states = [inputs.epidemic_state(sp["nx"], sp["ny"], 70 + i) for i, sp in enumerate(specs)]
+    errs = {}
+    for prec in (L.FP32, L.FP32_SPLIT):
+        ens = L.Ensemble(specs, precision=prec)
+        ens.set_tiling(4, 32)
+        for i, st in enumerate(states):
+            ens.write(i, st)
+        ens.run(400)
+        tot, _ = ens.diagnostics()
+        worst = 0.0
+        for i, (sp, st) in enumerate(zip(specs, states)):
+            got = ens.read(i)
+            s = L.Solver(sp["nx"], sp["ny"], sp["rates"], d=sp["d"], bc=L.BC_PERIODIC, precision=prec)
+            s.write(st)
+            s.step(400)
+            stot, _ = s.diagnostics()
+            s.close()
+            assert np.array_equal(tot[i], stot), (prec, i)
+            taus = [oracle.tau_from_d(x) for x in sp["d"][:4]]
+            ref = oracle.sslbm_run(st.astype(np.float32).astype(np.float64), taus, sp["rates"], 1.0,
+                                   L.BC_PERIODIC, 400)
+            worst = max(worst, float(np.abs(got[0] - ref[0]).max()))
+        errs[prec] = worst
+        ens.close()
+    assert errs[L.FP32_SPLIT] <= errs[L.FP32], errs
