@@ -474,12 +474,14 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
 
     def glups_of(precision, n_lat, reps, depth=None, schemes=L.WANT_SSLBM, bgk=False):
         s = L.Solver(NX, NY, rates, d=wl["d"], bc=wl["bc"], precision=precision, schemes=schemes)
-        if depth:
-            s.set_blocking(depth)
         if bgk:
             s.write(state64, scheme=L.SCHEME_BGK)
         else:
             s.write(state32 if precision != L.FP64 else state64)
+        if depth == "auto":
+            s.autotune()
+        elif depth:
+            s.set_blocking(depth)
         run = s.bgk_step if bgk else s.step
         run(n_lat)
         torch.cuda.synchronize()
@@ -500,16 +502,19 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
         out[f"fp32_depth{k}_glups"] = g
         if k == 1:
             out["fp32_depth1_hbm_frac"] = BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm
-    g, _ = glups_of(L.FP32_DEV, 48, 4)
+    # the other storages at the autotuned blocking, and one step per launch against HBM
+    g, _ = glups_of(L.FP32_DEV, 48, 4, depth="auto")
     out["fp32_dev_glups"] = g
-    g, _ = glups_of(L.FP32_SPLIT, 48, 4)
+    g, _ = glups_of(L.FP32_SPLIT, 48, 4, depth="auto")
     out["fp32_split_glups"] = g
     g, ms = glups_of(L.FP32_SPLIT, 20, 2, depth=1)
     out["fp32_split_depth1_glups"] = g
     out["fp32_split_depth1_hbm_frac"] = 48 * cells / (ms * 1e-3) / 1e9 / hbm
-    g, ms = glups_of(L.FP32_KAHAN, 20, 2)
+    g, ms = glups_of(L.FP32_KAHAN, 20, 2, depth=1)
     out["fp32_kahan_glups"] = g
     out["fp32_kahan_hbm_frac"] = 80 * cells / (ms * 1e-3) / 1e9 / hbm
+    g, _ = glups_of(L.FP32_KAHAN, 48, 2, depth="auto")
+    out["fp32_kahan_blocked_glups"] = g
     g, ms = glups_of(L.FP64, 20, 2)
     out["fp64_glups"] = g
     out["fp64_hbm_frac"] = BYTES_PER_CELL_FP64 * cells / (ms * 1e-3) / 1e9 / hbm

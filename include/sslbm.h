@@ -210,7 +210,7 @@ int sslbm_set_diffusivity_scale(sslbm_handle* h, const void* kx, const void* ky,
  * On D2Q5 rho_f = rho_b, so the kernels evaluate the algebraically identical
  * rho_c + d_lattice (sum of the four neighbours - 4 rho_c) + Psi dt.
  * Several steps are fused per pass over memory (temporal blocking, depth set by
- * sslbm_set_blocking or sslbm_autotune; D2Q5 in the FP32 storages, D2Q9 and varying
+ * sslbm_set_blocking or sslbm_autotune; D2Q5 in every FP32 storage, D2Q9 and varying
  * diffusion in FP32); n steps
  * take ceil(n / depth) passes whose depths differ by at most one.  Results do not depend on
  * the depth: every depth performs the same floating-point operations in the same order.
@@ -311,8 +311,8 @@ int sslbm_diagnostics_noalloc(const void* fields, int dtype, int64_t nx, int64_t
 /* Temporal-blocking depth k (steps fused per pass, 1..SSLBM_MAX_DEPTH) and the
  * kernel's row-segment length seg_rows (0 = automatic).  k = 0 restores the default (4
  * where a blocked kernel exists, else 1).  The blocked kernels cover the D2Q5 lattice in
- * SSLBM_FP32, SSLBM_FP32_DEV and SSLBM_FP32_SPLIT, and the D2Q9 and varying-diffusion
- * lattices in SSLBM_FP32; k > 1 elsewhere returns SSLBM_ERR_UNSUPPORTED. */
+ * SSLBM_FP32, SSLBM_FP32_DEV, SSLBM_FP32_SPLIT and SSLBM_FP32_KAHAN, and the D2Q9 and
+ * varying-diffusion lattices in SSLBM_FP32; k > 1 elsewhere returns SSLBM_ERR_UNSUPPORTED. */
 #define SSLBM_MAX_DEPTH 8
 int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows);
 

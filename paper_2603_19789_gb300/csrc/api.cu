@@ -636,12 +636,13 @@ int sslbm_debug_bounds(long long* count, long long* value, long long* limit, int
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize(bounds records)");
   int (*const take[])(sslbm::OobRecord*) = {sslbm::oob_take_kernels, sslbm::oob_take_ensemble, sslbm::oob_take_bgk,
                                             sslbm::oob_take_io, sslbm::oob_take_stream,
-                                            sslbm::oob_take_d2q9, sslbm::oob_take_d2q9a, sslbm::oob_take_vard};
-  const int tu_site[] = {0, 100, 200, 300, 400, 500, 600, 700};  // site numbers are offset by translation unit
+                                            sslbm::oob_take_d2q9, sslbm::oob_take_d2q9a, sslbm::oob_take_vard,
+                                            sslbm::oob_take_kahan};
+  const int tu_site[] = {0, 100, 200, 300, 400, 500, 600, 700, 800};  // offset by translation unit
   unsigned long long total = 0;
   sslbm::OobRecord first{};
   int first_site = -1;
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 9; ++i) {
     sslbm::OobRecord r{};
     if (take[i](&r) != 0) return fail(SSLBM_ERR_CUDA, "reading the bounds record of unit %d", i);
     if (r.count && first_site < 0) {
@@ -786,7 +787,7 @@ int sslbm_set_blocking(sslbm_handle* h, int k, int seg_rows) {
   const bool blocked = can_block(h);
   if (!blocked && k > 1)
     return fail(SSLBM_ERR_UNSUPPORTED,
-                "temporal blocking is provided for FP32, FP32_DEV and FP32_SPLIT on D2Q5 and for FP32 on D2Q9 "
+                "temporal blocking is provided for the FP32 storages on D2Q5 and for FP32 on D2Q9 "
                 "and the varying-diffusion lattice");
   h->depth = k == 0 ? (blocked ? 4 : 1) : k;
   if (seg_rows > 0 && seg_rows < 4 * h->depth) seg_rows = 4 * h->depth;

@@ -22,7 +22,7 @@ constexpr size_t pipe_smem_bytes() {
 
 // kx, ky: the scale planes of the varying-diffusion lattice (MODE_VARD), else unused.
 template <int MODE, int K>
-__global__ void __launch_bounds__(32 * K, 16 / K) pipe_kernel(const GridView g, const Coeffs<float> k,
+__global__ void __launch_bounds__(32 * K, MODE == MODE_KAHAN ? 1 : 16 / K) pipe_kernel(const GridView g, const Coeffs<float> k,
                                                              const float* __restrict__ in,
                                                              float* __restrict__ out,
                                                              const int seg_rows, const int nstrips,

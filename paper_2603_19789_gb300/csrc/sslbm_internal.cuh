@@ -280,7 +280,8 @@ __device__ __forceinline__ void seird_cell2(const Coeffs<float>& k, float2 x0, f
 
 // ---- launchers (defined in the kernel translation units) --------------------------
 // SSLBM: one step per launch (every precision) and K fused steps per launch (FP32, FP32
-// deviation-S and FP32 split-S).  seg_rows > 0 is the blocked kernel's row-segment length.
+// deviation-S, FP32 split-S and FP32 Kahan).  seg_rows > 0 is the blocked kernel's row-segment
+// length.
 cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coeffs, const void* in,
                                void* out, cudaStream_t s);
 // The streaming one-step kernel (stream.cu) of the FP32 storages: FP32, FP32 deviation-S,
@@ -291,6 +292,10 @@ cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* c
                                  const void* in, void* out, int depth, int seg_rows,
                                  cudaStream_t s);
 bool blocked_supported(int precision, const GridView& g);
+// The Kahan storage's blocked kernel (pipe_kahan.cu) and its default segment.
+cudaError_t launch_kahan_blocked(const GridView& g, const void* coeffs, const void* in, void* out, int depth,
+                                 int seg_rows, cudaStream_t s);
+int blocked_kahan_default_seg_rows(const GridView& g, int depth);
 // The D2Q9 lattice (plain FP32 storage): K fused steps per launch, and its default segment.
 cudaError_t launch_sslbm9_blocked(const GridView& g, const void* coeffs, const void* in, void* out, int depth,
                                   int seg_rows, cudaStream_t s);

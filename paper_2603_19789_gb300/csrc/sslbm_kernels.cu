@@ -109,11 +109,13 @@ int blocked_default_seg_rows(int precision, const GridView& g, int depth) {
   if (precision == SSLBM_FP32) return default_seg_rows_mode<MODE_PLAIN>(g, depth);
   if (precision == SSLBM_FP32_DEV) return default_seg_rows_mode<MODE_DEV>(g, depth);
   if (precision == SSLBM_FP32_SPLIT) return default_seg_rows_mode<MODE_SPLIT>(g, depth);
+  if (precision == SSLBM_FP32_KAHAN) return blocked_kahan_default_seg_rows(g, depth);
   return 0;
 }
 
 bool blocked_supported(int precision, const GridView&) {
-  return precision == SSLBM_FP32 || precision == SSLBM_FP32_DEV || precision == SSLBM_FP32_SPLIT;
+  return precision == SSLBM_FP32 || precision == SSLBM_FP32_DEV || precision == SSLBM_FP32_SPLIT ||
+         precision == SSLBM_FP32_KAHAN;
 }
 
 cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coeffs, const void* in,
@@ -137,6 +139,7 @@ cudaError_t launch_sslbm_blocked(int precision, const GridView& g, const void* c
     return launch_blocked_mode<MODE_DEV>(g, coeffs, in, out, depth, seg_rows, s);
   if (precision == SSLBM_FP32_SPLIT)
     return launch_blocked_mode<MODE_SPLIT>(g, coeffs, in, out, depth, seg_rows, s);
+  if (precision == SSLBM_FP32_KAHAN) return launch_kahan_blocked(g, coeffs, in, out, depth, seg_rows, s);
   return cudaErrorInvalidValue;
 }
 

@@ -222,6 +222,55 @@ __device__ __forceinline__ void cell_rowv(const Coeffs<float>& k, const float2 (
   }
 }
 
+// Level s+1 of row C in the Kahan storage (ten planes: the values of S, E, I, R, D, then
+// their compensations) from level-s rows P, C, N: per compartment the laplacian
+// lap5_diff(value) - lap5_diff(compensation), the increments of seird_increments (the force
+// from the values), each added to its (value, compensation) pair with kahan_add -- the
+// operations of the one-step Kahan kernel, packed.  The adds whose operand is a packed
+// product, and the product that enters kahan_add directly, stay scalar: packed, the compiler
+// may fuse the product into the add (measured: the compensation of D then differed in its
+// last bits from the one-step kernel's).
+__device__ __forceinline__ void cell_row_kahan(const Coeffs<float>& k, const float2 (&P)[10][2],
+                                               const float2 (&C)[10][2], const float2 (&N)[10][2],
+                                               float2 (&M)[10][2]) {
+  constexpr unsigned kFull = 0xffffffffu;
+  float2 lp[4][2];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    float2 d[2][2];  // [value, compensation][column pair]
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int p = q == 0 ? f : 5 + f;
+      const float L = __shfl_up_sync(kFull, C[p][1].y, 1);
+      const float R = __shfl_down_sync(kFull, C[p][0].x, 1);
+      d[q][0] = lap5diff_x2(C[p][0], make_float2(L, C[p][0].x), make_float2(C[p][0].y, C[p][1].x), P[p][0], N[p][0]);
+      d[q][1] = lap5diff_x2(C[p][1], make_float2(C[p][0].y, C[p][1].x), make_float2(C[p][1].y, R), P[p][1], N[p][1]);
+    }
+    lp[f][0] = add2(d[0][0], neg2(d[1][0]));
+    lp[f][1] = add2(d[0][1], neg2(d[1][1]));
+  }
+  auto sadd = [](float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); };
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float2 S = C[0][h], E = C[1][h], I = C[2][h];
+    const float2 F = force_dt2(k, S, E, I, C[3][h]);
+    float2 inc[5];
+    inc[0] = fma2(splat2(k.dl[0]), lp[0][h], neg2(F));
+    inc[1] = sadd(mul2(splat2(k.dl[1]), lp[1][h]), fma2(splat2(-k.adt), E, F));
+    inc[2] = sadd(mul2(splat2(k.dl[2]), lp[2][h]), fma2(splat2(k.adt), E, neg2(mul2(splat2(k.gdt), I))));
+    inc[3] = fma2(splat2(k.rdt), I, mul2(splat2(k.dl[3]), lp[3][h]));
+    // scalar products: a packed product feeding kahan_add's first add could be fused into it
+    inc[4] = make_float2(__fmul_rn(k.ddt, I.x), __fmul_rn(k.ddt, I.y));
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      float2 v = C[f][h], c = C[5 + f][h];
+      kahan_add2(v, c, inc[f]);
+      M[f][h] = v;
+      M[5 + f][h] = c;
+    }
+  }
+}
+
 // Hand level-(s+1) row M to the next warp (slot row `which` of parity par) or, for the last
 // warp, write it to row r of the output.
 template <int K, int NF>
@@ -290,6 +339,13 @@ __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g
       cell_row9<true, W>(k, g, B, N0, N1, M, xs, row + 1);
     else
       cell_row9<false, W && COLW, AL>(k, g, B, N0, N1, M, xs, row + 1);
+  } else if constexpr (MODE == MODE_KAHAN) {
+    // ten planes: the second row of the pair is read after the first is done
+    load_row(src, N0);
+    cell_row_kahan(k, A, B, N0, M);
+    emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
+    load_row(src + 128 * NF, N1);
+    cell_row_kahan(k, B, N0, N1, M);
   } else if constexpr (MODE == MODE_VARD) {
     // sk: the static-ring slot of the first row this warp computes (row b - 1)
     auto krow = [&](int d, int plane) {  // this lane's columns of scale plane `plane`, row b - 1 + d

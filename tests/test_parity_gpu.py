@@ -141,7 +141,7 @@ def test_centre_bump_fp32_variants_within_tolerance(precision):
         assert (e2 <= FP32_LONG_TOL).all() and (einf <= FP32_LONG_TOL).all(), (t, e2, einf)
 
 
-@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_SPLIT])
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_SPLIT, L.FP32_KAHAN])
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("nx,ny", [(5, 3), (130, 1), (1, 70), (37, 23), (1000, 333), (250, 260)])
 def test_blocked_depths_give_identical_bits(precision, bc, nx, ny):
@@ -326,7 +326,7 @@ def test_error_statuses_on_gpu():
     assert ei.value.status == -1
 
 
-@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_SPLIT, L.FP64])
+@pytest.mark.parametrize("precision", [L.FP32, L.FP32_DEV, L.FP32_SPLIT, L.FP32_KAHAN, L.FP64])
 def test_autotune_leaves_state_and_picks_a_valid_configuration(precision):
     wl = small_workload(600, 333, 1, seed=12)
     s = solver_for(wl, precision)
