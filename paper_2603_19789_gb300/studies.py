@@ -72,7 +72,7 @@ def precision_study(n: int = 4096, steps: int = 50000, checkpoints: int = 6, see
         s = L.Solver(n, n, wl["rates"].as_tuple(), d=wl["d"], bc=wl["bc"], precision=prec,
                      s_ref=1.0)
         s.write(st)
-        if prec in (L.FP32, L.FP32_DEV, L.FP32_SPLIT):
+        if prec != L.FP64:
             s.autotune(200.0)
         solvers[name] = s
     out = {"workload": wl["name"], "n": n, "steps": steps, "seed_amplitude": 1e-6,
