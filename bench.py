@@ -311,7 +311,9 @@ def main():
     total_ms = max_over_ranks(total_ms, world)
     cells = NX * NY
     value = world * cells * LATTICE_STEPS_PER_STEP * args.steps / (total_ms * 1e-3) / 1e9
-    launches_per_step = math.ceil(LATTICE_STEPS_PER_STEP / depth) + 2  # step launches + 2 diagnostics kernels
+    fused_diag = s.get_fused_diagnostics()[1]  # the last pass took the diagnostics
+    # step launches, then the diagnostics: one kernel adding the fused pass's partials, or two
+    launches_per_step = math.ceil(LATTICE_STEPS_PER_STEP / depth) + (1 if fused_diag else 2)
     launch_ms = kern_ms / (args.steps * math.ceil(LATTICE_STEPS_PER_STEP / depth))
     hbm, peak_kind = load_peaks()
     achieved = BYTES_PER_CELL_FP32 * cells / (launch_ms * 1e-3) / 1e9
@@ -355,6 +357,8 @@ def main():
                        "temporal_block_depth": depth, "seg_rows": seg or "auto",
                        "passes_per_step": pass_split(LATTICE_STEPS_PER_STEP, depth),
                        "blocking_chosen_by": "autotuner" if tuned else "--depth",
+                       "diagnostics": "fused into the last pass of each step" if fused_diag
+                                      else "separate reduction after each step",
                        "l2": f"state {20 * cells / 1e9:.2f} GB vs 129 MB L2"
                              + (" (no flush needed)" if 20 * cells > 129e6 else " (fits in L2)"),
                        "parallelism": f"replicas x{world}"},

@@ -281,6 +281,25 @@ int sslbm_checkpoint_load(sslbm_handle* h, const void* src, size_t bytes, int sr
  * SSLBM_ERR_NONFINITE if any total is NaN or Inf (results still written). */
 int sslbm_diagnostics(sslbm_handle* h, int scheme, double* totals, double* peak_I);
 
+/* Fused diagnostics (on = 1; 0 turns them off, the default): the last pass of each
+ * sslbm_step call also reduces its output to the totals and peak of sslbm_diagnostics,
+ * so that a following sslbm_diagnostics(h, SSLBM_SCHEME_SSLBM, ...) reads them without a
+ * pass over the state.  They are taken where that pass is temporally blocked on the D2Q5
+ * lattice in SSLBM_FP32 or SSLBM_FP32_DEV and its grid has at most 1024 tiles (128-column
+ * strips times row segments).  Any other step (also a call whose last pass is a single
+ * step, as at depth 2 with an odd n), and any write or checkpoint load of the SSLBM state,
+ * leaves sslbm_diagnostics to its own reduction.  The state written is the
+ * same, and so are the results: each tile keeps FP32 TwoSum pairs of its output cells
+ * (about twice FP32's precision per tile) and adds them in FP64 in a fixed order, so the
+ * totals agree with the unfused reduction to rounding in FP64 and the peak exactly.
+ * Returns SSLBM_ERR_BAD_ARG for a NULL handle or on not 0 or 1.  Not part of the paper. */
+int sslbm_set_fused_diagnostics(sslbm_handle* h, int on);
+
+/* Whether fused diagnostics are on (*on) and whether the last pass left those of the current
+ * SSLBM state (*ready = 1: sslbm_diagnostics reads them without a pass over the state).
+ * Either pointer may be NULL.  SSLBM_ERR_BAD_ARG for a NULL handle. */
+int sslbm_get_fused_diagnostics(const sslbm_handle* h, int* on, int* ready);
+
 /* Totals and peak infected of caller-provided fields, allocating no device memory.
  * The paper has no counterpart: this serves callers that hold device buffers but
  * cannot allocate -- e.g. a monitoring hook inside another framework's time loop whose

@@ -151,6 +151,8 @@ struct sslbm_handle {
   int64_t s_steps = 0, b_steps = 0;
   int depth = 1, seg_rows = 0;
   int seg_cache[SSLBM_MAX_DEPTH + 1] = {0};
+  bool fuse_diag = false;   // sslbm_set_fused_diagnostics
+  bool diag_ready = false;  // diag_result() holds the diagnostics of the current SSLBM state
 
   const void* coeffs() const {
     return g.precision == SSLBM_FP64 ? static_cast<const void*>(&cd) : static_cast<const void*>(&cf);
@@ -362,6 +364,7 @@ int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_
   const size_t plane_user = (size_t)h->g.nx * (size_t)h->g.ny * usize;
   const int c0 = comp == SSLBM_ALL ? 0 : comp, c1 = comp == SSLBM_ALL ? 5 : comp + 1;
   const bool bgk = scheme == SSLBM_SCHEME_BGK;
+  if (!bgk) h->diag_ready = false;
   char* staging = bgk ? h->b_buf[1 - h->b_cur] : h->s_buf[1 - h->s_cur];
   const int own_dtype = h->g.precision == SSLBM_FP64 ? SSLBM_DT_F64 : SSLBM_DT_F32;
   for (int c = c0; c < c1; ++c) {
@@ -529,6 +532,7 @@ int sslbm_step(sslbm_handle* h, int64_t n) {
   if (h->g.lattice == SSLBM_LATTICE_D2Q5_VARD && !h->kappa_ok)
     return fail(SSLBM_ERR_BAD_ARG, "the diffusivity scale fields are not set (sslbm_set_diffusivity_scale)");
   const bool blocked = can_block(h);
+  if (n > 0) h->diag_ready = false;
   while (n > 0) {
     int k = 1;
     cudaError_t e;
@@ -544,7 +548,18 @@ int sslbm_step(sslbm_handle* h, int64_t n) {
         if (!h->seg_cache[k]) h->seg_cache[k] = default_seg(h, k);
         seg = h->seg_cache[k];
       }
-      e = launch_pass(h, k, seg);
+      // the last pass of the call takes the diagnostics of its output when they are fused
+      if (h->fuse_diag && n == k && h->g.lattice == SSLBM_LATTICE_D2Q5 &&
+          sslbm::blocked_diag_supported(h->g.precision, h->gv, k, seg)) {
+        e = sslbm::launch_sslbm_blocked_diag(h->g.precision, h->gv, &h->cf, h->s_buf[h->s_cur],
+                                             h->s_buf[1 - h->s_cur], k, seg, h->diag_partials(), h->stream);
+        if (e == cudaSuccess)
+          e = sslbm::launch_diag_final(h->diag_partials(), (int)sslbm::blocked_ctas(h->gv, k, seg),
+                                       h->diag_result(), h->stream);
+        if (e == cudaSuccess) h->diag_ready = true;
+      } else {
+        e = launch_pass(h, k, seg);
+      }
     } else {
       e = launch_pass(h, 1, 0);
     }
@@ -637,12 +652,12 @@ int sslbm_debug_bounds(long long* count, long long* value, long long* limit, int
   int (*const take[])(sslbm::OobRecord*) = {sslbm::oob_take_kernels, sslbm::oob_take_ensemble, sslbm::oob_take_bgk,
                                             sslbm::oob_take_io, sslbm::oob_take_stream,
                                             sslbm::oob_take_d2q9, sslbm::oob_take_d2q9a, sslbm::oob_take_vard,
-                                            sslbm::oob_take_kahan};
-  const int tu_site[] = {0, 100, 200, 300, 400, 500, 600, 700, 800};  // offset by translation unit
+                                            sslbm::oob_take_kahan, sslbm::oob_take_diag};
+  const int tu_site[] = {0, 100, 200, 300, 400, 500, 600, 700, 800, 900};  // offset by translation unit
   unsigned long long total = 0;
   sslbm::OobRecord first{};
   int first_site = -1;
-  for (int i = 0; i < 9; ++i) {
+  for (int i = 0; i < 10; ++i) {
     sslbm::OobRecord r{};
     if (take[i](&r) != 0) return fail(SSLBM_ERR_CUDA, "reading the bounds record of unit %d", i);
     if (r.count && first_site < 0) {
@@ -738,6 +753,7 @@ int sslbm_checkpoint_load(sslbm_handle* h, const void* src, size_t bytes, int sr
   if (bytes < need) return fail(SSLBM_ERR_BAD_ARG, "checkpoint of %zu bytes < %zu", bytes, need);
   const size_t row = (size_t)own.nx * own.esize, plane_user = row * (size_t)own.ny;
   const char* sp = static_cast<const char*>(src) + kCkptData;
+  h->diag_ready = false;
   for (int i = 0; i < own.s_planes + own.b_planes; ++i, sp += plane_user) {
     cudaError_t e = cudaMemcpy2DAsync(ckpt_plane(h, own, i), (size_t)h->L.pitch * h->L.esize, sp, row, row,
                                       (size_t)own.ny, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -758,13 +774,16 @@ int sslbm_diagnostics(sslbm_handle* h, int scheme, double* totals, double* peak_
   if (st) return st;
   DeviceGuard dg(h->device);
   const bool bgk = scheme == SSLBM_SCHEME_BGK;
-  const void* planes = bgk ? (const void*)h->b_buf[h->b_cur] : (const void*)h->s_buf[h->s_cur];
-  const bool comp = !bgk && (h->g.precision == SSLBM_FP32_KAHAN || h->g.precision == SSLBM_FP32_SPLIT);
-  const void* comps = comp ? h->s_plane(h->s_cur, 5) : nullptr;
-  cudaError_t e = sslbm::launch_diagnostics(h->g.precision, bgk ? 1 : 0, h->gv, planes, comps,
-                                            h->diag_partials(), h->diag_result(), h->stream,
-                                            h->g.precision == SSLBM_FP32_SPLIT ? 1 : 5);
-  if (e != cudaSuccess) return cuda_fail(e, "diagnostics launch");
+  cudaError_t e = cudaSuccess;
+  if (bgk || !h->diag_ready) {  // else the last step's fused pass left them in diag_result()
+    const void* planes = bgk ? (const void*)h->b_buf[h->b_cur] : (const void*)h->s_buf[h->s_cur];
+    const bool comp = !bgk && (h->g.precision == SSLBM_FP32_KAHAN || h->g.precision == SSLBM_FP32_SPLIT);
+    const void* comps = comp ? h->s_plane(h->s_cur, 5) : nullptr;
+    h->diag_ready = false;  // the reduction below overwrites the result
+    e = sslbm::launch_diagnostics(h->g.precision, bgk ? 1 : 0, h->gv, planes, comps, h->diag_partials(),
+                                  h->diag_result(), h->stream, h->g.precision == SSLBM_FP32_SPLIT ? 1 : 5);
+    if (e != cudaSuccess) return cuda_fail(e, "diagnostics launch");
+  }
   double r[sslbm::kDiagSlots];
   e = cudaMemcpyAsync(r, h->diag_result(), sizeof(r), cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(diagnostics)");
@@ -777,6 +796,20 @@ int sslbm_diagnostics(sslbm_handle* h, int scheme, double* totals, double* peak_
   if (peak_I) *peak_I = r[5];
   for (int c = 0; c < 5; ++c)
     if (!std::isfinite(r[c])) return fail(SSLBM_ERR_NONFINITE, "total of compartment %d is %g", c, r[c]);
+  return SSLBM_OK;
+}
+
+int sslbm_set_fused_diagnostics(sslbm_handle* h, int on) {
+  if (!h) return fail(SSLBM_ERR_BAD_ARG, "handle is NULL");
+  if (on != 0 && on != 1) return fail(SSLBM_ERR_BAD_ARG, "on=%d (0 or 1)", on);
+  h->fuse_diag = on == 1;
+  return SSLBM_OK;
+}
+
+int sslbm_get_fused_diagnostics(const sslbm_handle* h, int* on, int* ready) {
+  if (!h) return fail(SSLBM_ERR_BAD_ARG, "handle is NULL");
+  if (on) *on = h->fuse_diag ? 1 : 0;
+  if (ready) *ready = h->diag_ready ? 1 : 0;
   return SSLBM_OK;
 }
 

@@ -27,6 +27,7 @@ int oob_take_d2q9(OobRecord* out);
 int oob_take_d2q9a(OobRecord* out);
 int oob_take_vard(OobRecord* out);
 int oob_take_kahan(OobRecord* out);
+int oob_take_diag(OobRecord* out);
 // Evaluate one check of index v against limit on the device, with no access behind it.
 cudaError_t launch_oob_probe(long long v, long long limit, cudaStream_t s);
 

@@ -311,6 +311,12 @@ cudaError_t launch_diagnostics(int precision, int layout, const GridView& g, con
   return cudaGetLastError();
 }
 
+cudaError_t launch_diag_final(const double* partials, int nblocks, double* result, cudaStream_t s) {
+  if (nblocks < 1 || nblocks > kDiagBlocks) return cudaErrorInvalidValue;
+  diag_final_kernel<<<1, 256, 0, s>>>(partials, nblocks, result);
+  return cudaGetLastError();
+}
+
 namespace {
 // One index check with no memory access behind it (site 999).
 __global__ void oob_probe_kernel(long long v, long long limit) { (void)SSLBM_IN(v, 1, limit, 999); }

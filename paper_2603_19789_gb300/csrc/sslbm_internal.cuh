@@ -311,6 +311,14 @@ cudaError_t launch_sslbm_vard_blocked(const GridView& g, const void* coeffs, con
 int blocked_vard_default_seg_rows(const GridView& g, int depth);
 // Segment length that makes one blocked launch a single wave of resident warps.
 int blocked_default_seg_rows(int precision, const GridView& g, int depth);
+// The same pass with the fused diagnostics (FP32 and FP32_DEV storages, at most kDiagBlocks
+// CTAs): partials receives one 6-double partial per CTA (the five totals of the stored planes,
+// then the largest I), which launch_diag_final reduces.  blocked_ctas: the CTAs of such a pass
+// (-1 for an invalid depth or segment length).
+int64_t blocked_ctas(const GridView& g, int depth, int seg_rows);
+bool blocked_diag_supported(int precision, const GridView& g, int depth, int seg_rows);
+cudaError_t launch_sslbm_blocked_diag(int precision, const GridView& g, const void* coeffs, const void* in,
+                                      void* out, int depth, int seg_rows, double* partials, cudaStream_t s);
 // BGK: one collide-and-stream step; equilibrium initialisation and density of one
 // compartment from / to a contiguous ny x nx plane of type rho_dtype.
 cudaError_t launch_bgk_step(int precision, const GridView& g, const void* coeffs, const void* f_in,
@@ -338,5 +346,7 @@ constexpr int kDiagSlots = 6;
 cudaError_t launch_diagnostics(int precision, int layout, const GridView& g, const void* planes,
                                const void* comp_planes, double* partials, double* result,
                                cudaStream_t s, int n_comp = 5);
+// The fixed-order FP64 total of nblocks 6-double partials into result[6] (one CTA).
+cudaError_t launch_diag_final(const double* partials, int nblocks, double* result, cudaStream_t s);
 
 }  // namespace sslbm

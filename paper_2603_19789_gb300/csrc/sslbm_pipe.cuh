@@ -19,6 +19,8 @@
 // nine-point one of the one-step D2Q9 kernel; its no-flux walls (bounce-back) are not a ghost
 // image, so they are substituted into the row update instead.
 #pragma once
+#include <cfloat>
+
 #include "bounds.cuh"
 #include "sslbm_internal.cuh"
 
@@ -51,6 +53,42 @@ struct alignas(16) PipeSmem {
   float r0[kRing0][NF][128];
   float rl[K - 1][2][2][NF][128];
 };
+
+// Fused diagnostics (DIAG): the last warp also stores its output pair here, double-buffered
+// by iteration parity like the level handoff; at the next iteration every warp adds its share
+// (plane-rows j = row * NF + plane, j = (w - 2) mod K + i K for warp w) to running TwoSum
+// pairs, and at the end of the tile the lanes' sums go to FP64, one partial per CTA.
+constexpr int kDiagMaxWarps = 8;
+template <int NF>
+struct alignas(16) DiagSmem {
+  float rows[2][2][NF][128];
+  double part[kDiagMaxWarps][2 * NF];  // per warp and slot: the sum over the warp's lanes
+  float peak;                          // the CTA's largest I (last warp)
+};
+template <int K, int NF>
+constexpr int diag_slots() {
+  return (2 * NF + K - 1) / K;
+}
+
+// a - b for two pairs in one instruction: b * (-1) is exact, so the fused multiply-add rounds
+// a - b once, like the subtraction.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return fma2(b, splat2(-1.f), a); }
+// hi + lo <- hi + x, the rounding error of the addition carried into lo (Knuth's TwoSum),
+// for two independent pairs at once.
+__device__ __forceinline__ void two_sum2(float2& hi, float2& lo, float2 x) {
+  const float2 s = add2(hi, x);
+  const float2 bp = sub2(s, hi);
+  const float2 e = add2(sub2(hi, sub2(s, bp)), sub2(x, bp));
+  hi = s;
+  lo = add2(lo, e);
+}
+// Renormalise (Fast2Sum, |hi| >= |lo|): afterwards |lo| is at most half an ulp of hi, which
+// keeps the rounding errors of later additions to lo at FP32's unit roundoff squared.
+__device__ __forceinline__ void fast_two_sum2(float2& hi, float2& lo) {
+  const float2 s = add2(hi, lo);
+  lo = sub2(lo, sub2(s, hi));
+  hi = s;
+}
 
 // Level s+1 of row C (two float2 column pairs per field) from level-s rows P, C, N: x
 // neighbours by shuffles, the packed lap5 and the packed cell update.  MODE_SPLIT: field 5
@@ -273,17 +311,42 @@ __device__ __forceinline__ void cell_row_kahan(const Coeffs<float>& k, const flo
 
 // Hand level-(s+1) row M to the next warp (slot row `which` of parity par) or, for the last
 // warp, write it to row r of the output.
-template <int K, int NF>
+// DIAG: the last warp also stores the row into slot row `which` of dsl (the parity's
+// diagnostics rows; zeros for cells outside the tile's output) and takes the largest I of
+// the cells it writes into *pk.
+template <int K, int NF, bool DIAG = false>
 __device__ __forceinline__ void emit_row(PipeSmem<K, NF>& sm, const GridView& g, const float2 (&M)[NF][2],
                                          float* __restrict__ out, const int s, const int lane, const int par,
                                          const int which, const bool writer, const int64_t xs, const int64_t r,
-                                         const int64_t y0, const int64_t y1) {
+                                         const int64_t y0, const int64_t y1, float* dsl = nullptr,
+                                         float* pk = nullptr) {
   if (s < K - 1) {
     float* dst = &sm.rl[s < K - 1 ? s : 0][par][which][0][4 * lane];
 #pragma unroll
     for (int f = 0; f < NF; ++f)
       *reinterpret_cast<float4*>(dst + 128 * f) = make_float4(M[f][0].x, M[f][0].y, M[f][1].x, M[f][1].y);
-  } else if (writer && r >= y0 && r < y1 && SSLBM_IN(r, 1, g.ny, 5)) {
+    return;
+  }
+  if constexpr (DIAG) {
+    const bool rv = writer && r >= y0 && r < y1;
+    // columns xs + j that lie in the grid (a writer's first column always does)
+    const bool c1 = xs + 1 < g.nx, c2 = xs + 2 < g.nx, c3 = xs + 3 < g.nx;
+    float* d = dsl + which * (NF * 128) + 4 * lane;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rv) v = make_float4(M[f][0].x, c1 ? M[f][0].y : 0.f, c2 ? M[f][1].x : 0.f, c3 ? M[f][1].y : 0.f);
+      *reinterpret_cast<float4*>(d + 128 * f) = v;
+    }
+    if (rv) {
+      float m = M[2][0].x;
+      if (c1) m = fmaxf(m, M[2][0].y);
+      if (c2) m = fmaxf(m, M[2][1].x);
+      if (c3) m = fmaxf(m, M[2][1].y);
+      *pk = fmaxf(*pk, m);
+    }
+  }
+  if (writer && r >= y0 && r < y1 && SSLBM_IN(r, 1, g.ny, 5)) {
     float* o = out + r * g.pitch + xs;
     if (xs + 3 < g.nx) {
       if (SSLBM_IN(xs, 4, g.nx, 6)) {
@@ -306,13 +369,15 @@ __device__ __forceinline__ void emit_row(PipeSmem<K, NF>& sm, const GridView& g,
 // One iteration of warp s: read the pair of level-s rows b, b+1 (N0, N1) from src (row b+1
 // 128 NF floats further), compute level-(s+1) rows b-1 (from A = b-2, B = b-1, N0) and b (from
 // B, N0, N1), hand them on or write them as rows r, r+1.  Ends with the CTA barrier.
-template <int MODE, int K, bool COLW = true, int NF = mode_planes<MODE>()>
+// DIAG: dsl, pk as in emit_row (dsl: the diagnostics rows of parity par).
+template <int MODE, int K, bool COLW = true, bool DIAG = false, int NF = mode_planes<MODE>()>
 __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g, const Coeffs<float>& k,
                                           const float* src, const float2 (&A)[NF][2], const float2 (&B)[NF][2],
                                           float2 (&N0)[NF][2], float2 (&N1)[NF][2], float* __restrict__ out,
                                           const int s, const int lane, const int par, const bool writer,
                                           const int64_t xs, const int64_t r, const int64_t y0, const int64_t y1,
-                                          const float* rk = nullptr, const int sk = 0) {
+                                          const float* rk = nullptr, const int sk = 0, float* dsl = nullptr,
+                                          float* pk = nullptr) {
   auto load_row = [&](const float* p, float2 (&R)[NF][2]) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -333,7 +398,7 @@ __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g
       cell_row9<true, W>(k, g, A, B, N0, M, xs, row);
     else
       cell_row9<false, W && COLW, AL>(k, g, A, B, N0, M, xs, row);
-    emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
+    emit_row<K, NF, DIAG>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1, dsl, pk);
     load_row(src + 128 * NF, N1);
     if (W && (row + 1 == 0 || row + 1 == g.ny - 1))
       cell_row9<true, W>(k, g, B, N0, N1, M, xs, row + 1);
@@ -343,7 +408,7 @@ __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g
     // ten planes: the second row of the pair is read after the first is done
     load_row(src, N0);
     cell_row_kahan(k, A, B, N0, M);
-    emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
+    emit_row<K, NF, DIAG>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1, dsl, pk);
     load_row(src + 128 * NF, N1);
     cell_row_kahan(k, B, N0, N1, M);
   } else if constexpr (MODE == MODE_VARD) {
@@ -353,17 +418,17 @@ __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g
     };
     load_row(src, N0);
     cell_rowv(k, A, B, N0, M, krow(0, 0), krow(-1, 1), krow(0, 1), krow(1, 1));
-    emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
+    emit_row<K, NF, DIAG>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1, dsl, pk);
     load_row(src + 128 * NF, N1);
     cell_rowv(k, B, N0, N1, M, krow(1, 0), krow(0, 1), krow(1, 1), krow(2, 1));
   } else {
     load_row(src, N0);
     load_row(src + 128 * NF, N1);
     cell_row<MODE>(k, A, B, N0, M);
-    emit_row<K, NF>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1);
+    emit_row<K, NF, DIAG>(sm, g, M, out, s, lane, par, 0, writer, xs, r, y0, y1, dsl, pk);
     cell_row<MODE>(k, B, N0, N1, M);
   }
-  emit_row<K, NF>(sm, g, M, out, s, lane, par, 1, writer, xs, r + 1, y0, y1);
+  emit_row<K, NF, DIAG>(sm, g, M, out, s, lane, par, 1, writer, xs, r + 1, y0, y1, dsl, pk);
   __syncthreads();
 }
 
@@ -373,12 +438,18 @@ __device__ __forceinline__ void pipe_pair(PipeSmem<K, NF>& sm, const GridView& g
 // L1 is not coherent).
 // COLW = false: the strip holds neither x = 0 nor x = nx - 1 (D2Q9 no-flux: no column wall
 // code in its rows).
-template <int MODE, int K, bool WRAP16 = false, bool COLW = true, int NF = mode_planes<MODE>()>
+// DIAG (five planes): also the totals of the five output planes over the tile's output cells
+// and their largest I, written as FP64 partial `diag_slot` of diag (6 doubles: the totals,
+// then the peak), with dsm as the diagnostics' shared memory.
+template <int MODE, int K, bool WRAP16 = false, bool COLW = true, bool DIAG = false, int NF = mode_planes<MODE>()>
 __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g, const Coeffs<float>& k,
                                           const float* __restrict__ in, float* __restrict__ out,
                                           const int strip, const int64_t y0, const int64_t y1,
                                           const float* __restrict__ kx = nullptr,
-                                          const float* __restrict__ ky = nullptr, float* rk = nullptr) {
+                                          const float* __restrict__ ky = nullptr, float* rk = nullptr,
+                                          DiagSmem<NF>* dsm = nullptr, double* __restrict__ diag = nullptr,
+                                          const int diag_slot = 0) {
+  static_assert(!DIAG || (NF == 5 && K <= kDiagMaxWarps), "fused diagnostics: five planes, up to 8 warps");
   constexpr int HL = (K + 3) / 4;   // halo lanes on each side of the strip
   constexpr int WV = 128 - 8 * HL;  // columns written per strip
   const int lane = threadIdx.x & 31;
@@ -405,6 +476,8 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g
   for (int i = threadIdx.x; i < (K - 1) * 2 * 2 * NF * 128; i += 32 * K) (&sm.rl[0][0][0][0][0])[i] = 0.f;
   if (MODE == MODE_VARD)
     for (int i = threadIdx.x; i < kRingK * 2 * 128; i += 32 * K) rk[i] = 0.f;
+  if constexpr (DIAG)
+    for (int i = threadIdx.x; i < 2 * 2 * NF * 128; i += 32 * K) (&dsm->rows[0][0][0][0])[i] = 0.f;
   __syncthreads();
 
   auto issue = [&](int64_t q) {  // warp 0: copy level-0 row q into its ring slot
@@ -460,17 +533,77 @@ __device__ __forceinline__ void pipe_tile(PipeSmem<K, NF>& sm, const GridView& g
   };
   // the static-ring slot of the first row warp s computes at iteration t (row qa + 2t - 3s - 1)
   auto kslot = [&](int t) { return (2 * t - 3 * s - 1) & (kRingK - 1); };
+
+  // Fused diagnostics: this lane's TwoSum pairs, one per plane-row slot of the warp, and (last
+  // warp) the largest I it wrote.  Before iteration t every warp adds its plane-rows of the
+  // last warp's output of iteration t - 1 (parity (t + 1) & 1; zeros at t = 0).
+  constexpr int NS = DIAG ? diag_slots<K, NF>() : 1;
+  const int j0 = (s + 2 * K - 2) % K;  // this warp's first plane-row
+  float2 dh[NS], dl[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) dh[i] = dl[i] = make_float2(0.f, 0.f);
+  float pk = -FLT_MAX;
+  auto dsl = [&](int par) -> float* { return DIAG ? &dsm->rows[par][0][0][0] : nullptr; };
+  auto diag_take = [&](int par) {
+    if constexpr (DIAG) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        const int j = j0 + i * K;
+        if (j < 2 * NF) {
+          const float4 v = *reinterpret_cast<const float4*>(&dsm->rows[par][0][0][0] + j * 128 + 4 * lane);
+          two_sum2(dh[i], dl[i], make_float2(v.x, v.y));
+          two_sum2(dh[i], dl[i], make_float2(v.z, v.w));
+          fast_two_sum2(dh[i], dl[i]);
+        }
+      }
+    }
+  };
+
   int t = 0;
   for (; t + 2 <= nt; t += 2) {
-    pipe_pair<MODE, K, COLW>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0,
-                             y1, rk, kslot(t));
-    pipe_pair<MODE, K, COLW>(sm, g, k, fetch(t + 1), RC, RD, RA, RB, out, s, lane, (t + 1) & 1, writer, xs,
-                             rbase + 2 * t + 2, y0, y1, rk, kslot(t + 1));
+    diag_take((t + 1) & 1);
+    pipe_pair<MODE, K, COLW, DIAG>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t,
+                                   y0, y1, rk, kslot(t), dsl(t & 1), &pk);
+    diag_take(t & 1);
+    pipe_pair<MODE, K, COLW, DIAG>(sm, g, k, fetch(t + 1), RC, RD, RA, RB, out, s, lane, (t + 1) & 1, writer, xs,
+                                   rbase + 2 * t + 2, y0, y1, rk, kslot(t + 1), dsl((t + 1) & 1), &pk);
   }
-  if (t < nt)
-    pipe_pair<MODE, K, COLW>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t, y0,
-                             y1, rk, kslot(t));
+  if (t < nt) {
+    diag_take((t + 1) & 1);
+    pipe_pair<MODE, K, COLW, DIAG>(sm, g, k, fetch(t), RA, RB, RC, RD, out, s, lane, t & 1, writer, xs, rbase + 2 * t,
+                                   y0, y1, rk, kslot(t), dsl(t & 1), &pk);
+  }
   if (s == 0) cp_async_wait<0>();
+  if constexpr (DIAG) {
+    diag_take((nt - 1) & 1);  // the last iteration's output (the last pipe_pair ended with a barrier)
+    constexpr unsigned kFull = 0xffffffffu;
+    double acc[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      acc[i] = ((double)dh[i].x + (double)dl[i].x) + ((double)dh[i].y + (double)dl[i].y);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(kFull, acc[i], o);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pk = fmaxf(pk, __shfl_xor_sync(kFull, pk, o));
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) dsm->part[s][i] = acc[i];
+      if (s == K - 1) dsm->peak = pk;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && SSLBM_IN(diag_slot, 1, kDiagBlocks, 8)) {
+      double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int w = 0; w < K; ++w)  // fixed order: the partial does not depend on timing
+        for (int i = 0; i < NS; ++i) {
+          const int j = (w + 2 * K - 2) % K + i * K;
+          if (j < 2 * NF) tot[j % NF] += dsm->part[w][i];
+        }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) diag[diag_slot * kDiagSlots + c] = tot[c];
+      diag[diag_slot * kDiagSlots + 5] = (double)dsm->peak;
+    }
+  }
 }
 
 }  // namespace sslbm

@@ -41,7 +41,8 @@ EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspa
            "sslbm_set_diffusivity_scale", "sslbm_step", "bgk_step", "sslbm_steps_done",
            "sslbm_checkpoint_bytes", "sslbm_checkpoint_save", "sslbm_checkpoint_load",
            "sslbm_debug_bounds", "sslbm_debug_bounds_probe",
-           "sslbm_diagnostics", "sslbm_set_blocking",
+           "sslbm_diagnostics", "sslbm_set_fused_diagnostics",
+           "sslbm_get_fused_diagnostics", "sslbm_set_blocking",
            "sslbm_get_blocking", "sslbm_diagnostics_noalloc", "sslbm_autotune",
            "sslbm_ensemble_workspace_bytes", "sslbm_ensemble_create", "sslbm_ensemble_destroy",
            "sslbm_ensemble_set_tiling", "sslbm_ensemble_get_tiling",
@@ -134,6 +135,8 @@ def load(path: str = LIB_PATH):
             "sslbm_checkpoint_load": (i32, [_vp, _vp, ctypes.c_size_t, i32]),
             "sslbm_diagnostics": (i32, [_vp, i32, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]),
+            "sslbm_set_fused_diagnostics": (i32, [_vp, i32]),
+            "sslbm_get_fused_diagnostics": (i32, [_vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "sslbm_set_blocking": (i32, [_vp, i32, i32]),
             "sslbm_get_blocking": (i32, [_vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "sslbm_autotune": (i32, [_vp, ctypes.c_double, ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -382,6 +385,18 @@ def sslbm_diagnostics_noalloc(fields, stream: int = 0):
     return np.array(tot[:]), float(pk.value)
 
 
+def sslbm_set_fused_diagnostics(h, on: bool):
+    _check(load().sslbm_set_fused_diagnostics(h, 1 if on else 0), "sslbm_set_fused_diagnostics")
+
+
+def sslbm_get_fused_diagnostics(h):
+    """(on, ready): fused diagnostics on, and the current state's diagnostics left by the last pass."""
+    on, ready = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().sslbm_get_fused_diagnostics(h, ctypes.byref(on), ctypes.byref(ready)),
+           "sslbm_get_fused_diagnostics")
+    return bool(on.value), bool(ready.value)
+
+
 def sslbm_set_blocking(h, k: int, seg_rows: int = 0):
     _check(load().sslbm_set_blocking(h, int(k), int(seg_rows)), "sslbm_set_blocking")
 
@@ -457,6 +472,12 @@ class Solver:
 
     def diagnostics(self, scheme=SCHEME_SSLBM):
         return sslbm_diagnostics(self.h, scheme)
+
+    def set_fused_diagnostics(self, on=True):
+        sslbm_set_fused_diagnostics(self.h, on)
+
+    def get_fused_diagnostics(self):
+        return sslbm_get_fused_diagnostics(self.h)
 
     def set_blocking(self, k, seg_rows=0):
         sslbm_set_blocking(self.h, k, seg_rows)

@@ -79,10 +79,18 @@ def _check_autotuned_like_the_bench(wl, s):
     windows against the oracle, and the whole grid against the one-step kernel bit for bit.
     Tolerance per value: 2e-5 relative plus 1e-5 of the compartment's largest value on the
     grid (n u = 100 x 6e-8 bounds the accumulated rounding; a cell far smaller than its
-    neighbours carries their rounding, hence the absolute part, as in the FP32 parity tests)."""
+    neighbours carries their rounding, hence the absolute part, as in the FP32 parity tests).
+    The diagnostics are fused into the last pass, as in the benchmark: their totals agree with
+    the oracle's totals of the read-back state to 1e-12 and with the separate reduction of the
+    same state to 1e-13, and the peak of I is the same value."""
     s.write(wl["state"])
+    s.set_fused_diagnostics(True)
     s.step(BENCH_STEPS)
+    tot_f, pk_f = s.diagnostics()
     got = s.read(dtype=np.float32)
+    otot, opk = oracle.diagnostics(got.astype(np.float64))
+    np.testing.assert_allclose(tot_f, otot, rtol=1e-12)
+    assert pk_f == pytest.approx(opk, rel=1e-7)
     g64 = got.astype(np.float64)
     scale = np.abs(g64).reshape(5, -1).max(axis=1)
     st = wl["state"]
@@ -94,10 +102,14 @@ def _check_autotuned_like_the_bench(wl, s):
             bound = 2e-5 * np.abs(want[c]) + 1e-5 * scale[c]
             assert (np.abs(part[c] - want[c]) <= bound).all(), (x0, y0, c, np.abs(part[c] - want[c]).max())
     s.write(wl["state"])
+    s.set_fused_diagnostics(False)
     s.set_blocking(1)
     s.step(BENCH_STEPS)
     ref = s.read(dtype=np.float32)
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    tot, pk = s.diagnostics()
+    np.testing.assert_allclose(tot_f, tot, rtol=1e-13)
+    assert pk_f == pk
 
 
 def test_roofline_grid_fp32_autotuned_config(workload):
