@@ -8,8 +8,8 @@ of their global loads and stores before using it, skip and record any that is ou
 This test compiles that build and, in a child process that loads it, drives a sweep of tiny,
 odd and non-multiple-of-tile grids through every precision, every blocking depth with
 default and short odd segments, both boundary conditions, BGK, the FP32 D2Q9 and
-varying-diffusion steps (one-step and blocked at every depth), the diagnostics and a
-mixed-size ensemble.  The checks must record nothing.  A probe first proves the recording path: one
+varying-diffusion steps (one-step and blocked at every depth), the diagnostics (separate, and
+fused into the last pass at every depth) and a mixed-size ensemble.  The checks must record nothing.  A probe first proves the recording path: one
 check of an index past its limit (no memory access behind it) is counted and reported with
 its value, limit and site; one inside is not.
 """
@@ -61,6 +61,15 @@ for nx, ny in sizes:
                     s.step(2 * k + 1)
                     runs += 1
             s.diagnostics()
+            if prec in (L.FP32, L.FP32_DEV):  # the pipeline with the fused diagnostics
+                s.set_fused_diagnostics(True)
+                for k in range(2, 9):
+                    for seg in (0, 4 * k + 1):
+                        s.set_blocking(k, seg)
+                        s.step(2 * k)
+                        s.diagnostics()
+                        runs += 1
+                s.set_fused_diagnostics(False)
             if both:
                 s.write(st, scheme=L.SCHEME_BGK)
                 s.bgk_step(3)
