@@ -467,6 +467,42 @@ def e2e_timing(L, torch, s, state32, stream, world, wl, steps=3, jobs=8, infligh
             "serial": {"value": serial, "steps": steps, "ms_per_step": el_serial / steps * 1e3}}
 
 
+def fused_diagnostics_timing(L, wl, state32, stream, reps=20):
+    """One blocked FP32 pass (1024-row segments) with and without the diagnostics fused into
+    it, and the separate diagnostics reduction, in ms per call at depths 2, 4 and 8."""
+    import torch
+    s = L.Solver(NX, NY, wl["rates"].as_tuple(), d=wl["d"], bc=wl["bc"], precision=L.FP32)
+    s.write(state32)
+
+    def per_call(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = {}
+    for k in (2, 4, 8):
+        s.set_blocking(k, 1024)
+        s.set_fused_diagnostics(False)
+        plain = per_call(lambda: s.step(k))
+        separate = per_call(lambda: s.diagnostics())
+        s.set_fused_diagnostics(True)
+        fused = per_call(lambda: s.step(k))
+        if not s.get_fused_diagnostics()[1]:
+            raise RuntimeError("the fused diagnostics were not taken")
+        out[f"K{k}"] = {"plain_pass_ms": plain, "fused_pass_ms": fused, "separate_reduction_ms": separate}
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return out
+
+
 def secondary_timings(L, wl, state64, state32, stream, hbm):
     """Other variants on the same grid: FP64, deviation-S, split-S, Kahan, depth sweep, BGK,
     D2Q9, two-pass SLBM, varying diffusivity, FD4."""
@@ -481,7 +517,7 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
         if bgk:
             s.write(state64, scheme=L.SCHEME_BGK)
         else:
-            s.write(state32 if precision != L.FP64 else state64)
+            s.write(state64 if precision in (L.FP64, L.FP64_DW) else state32)
         if depth == "auto":
             s.autotune()
         elif depth:
@@ -506,6 +542,7 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
         out[f"fp32_depth{k}_glups"] = g
         if k == 1:
             out["fp32_depth1_hbm_frac"] = BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm
+    out["fused_diagnostics"] = fused_diagnostics_timing(L, wl, state32, stream)
     # the other storages at the autotuned blocking, and one step per launch against HBM
     g, _ = glups_of(L.FP32_DEV, 48, 4, depth="auto")
     out["fp32_dev_glups"] = g
@@ -542,6 +579,12 @@ def secondary_timings(L, wl, state64, state32, stream, hbm):
     out["fp64_measured_peak_tflops"] = 2 * 4096 ** 3 / (best * 1e-3) / 1e12
     out["fp64_tflops"] = FP64_FLOPS_PER_CELL * g / 1e3
     out["fp64_frac_of_measured_fp64"] = out["fp64_tflops"] / out["fp64_measured_peak_tflops"]
+    # FP64 accuracy in FP32 arithmetic: the double-word storage (hi + lo float pairs, 80 B per
+    # cell-step), one step per launch
+    g, ms = glups_of(L.FP64_DW, 20, 2)
+    out["fp64_dw_glups"] = g
+    out["fp64_dw_hbm_frac"] = 80 * cells / (ms * 1e-3) / 1e9 / hbm
+    out["fp64_dw_vs_fp64"] = g / out["fp64_glups"]
     g, ms = glups_of(L.FP32, 20, 2, schemes=L.WANT_BGK, bgk=True)
     out["bgk_fp32_glups"] = g
     out["bgk_fp32_hbm_frac"] = BGK_BYTES_PER_CELL_FP32 * cells / (ms * 1e-3) / 1e9 / hbm

@@ -67,8 +67,17 @@ enum { SSLBM_BC_PERIODIC = 0, SSLBM_BC_NOFLUX = 1 };
  *                precision at every value of S (the deviation storage keeps it only while
  *                S is near s_ref).  S's laplacian is taken in difference form on v minus
  *                that of c, and S's increment is added with Kahan summation; E, I, R, D
- *                are plain FP32.  Six planes: 48 bytes per cell-step. */
-enum { SSLBM_FP64 = 0, SSLBM_FP32 = 1, SSLBM_FP32_DEV = 2, SSLBM_FP32_KAHAN = 3, SSLBM_FP32_SPLIT = 4 };
+ *                are plain FP32.  Six planes: 48 bytes per cell-step.
+ *   FP64_DW    : FP64-accurate fields in FP32 arithmetic: every value is a double word
+ *                hi + lo of two floats (about 48 significant bits), stored as the Kahan
+ *                storage's ten planes (hi, and the compensation -lo), and the update of
+ *                FP64 is carried out in double-word arithmetic (the error-free building
+ *                blocks of Joldes, Muller and Popescu, ACM TOMS 2017: relative error of
+ *                order 2^-46 per operation), with the laplacian in difference form.  The
+ *                exponent range is FP32's (values below 1e-38 lose precision).  D2Q5 SSLBM,
+ *                one step per launch; 80 bytes per cell-step. */
+enum { SSLBM_FP64 = 0, SSLBM_FP32 = 1, SSLBM_FP32_DEV = 2, SSLBM_FP32_KAHAN = 3, SSLBM_FP32_SPLIT = 4,
+       SSLBM_FP64_DW = 5 };
 enum { SSLBM_SCHEME_SSLBM = 0, SSLBM_SCHEME_BGK = 1 };
 enum { SSLBM_S = 0, SSLBM_E = 1, SSLBM_I = 2, SSLBM_R = 3, SSLBM_D = 4, SSLBM_NCOMP = 5 };
 enum { SSLBM_ALL = -1 }; /* comp argument: all five planes, consecutive */
@@ -95,7 +104,7 @@ typedef struct sslbm_grid {
   double dx, dt;       /* lattice spacing and time step (> 0); lattice units: 1, 1 */
   int32_t bc;          /* SSLBM_BC_PERIODIC or SSLBM_BC_NOFLUX (homogeneous Neumann,
                           cell-centred mirror; BGK: halfway bounce-back) */
-  int32_t precision;   /* SSLBM_FP64 .. SSLBM_FP32_SPLIT (BGK supports FP64 and FP32) */
+  int32_t precision;   /* SSLBM_FP64 .. SSLBM_FP64_DW (BGK supports FP64 and FP32) */
   int32_t schemes;     /* SSLBM_WANT_SSLBM | SSLBM_WANT_BGK: which state to hold */
   int32_t lattice;     /* SSLBM_LATTICE_D2Q5 (0), SSLBM_LATTICE_D2Q9 (1),
                           SSLBM_LATTICE_D2Q5_SLBM (2) or SSLBM_LATTICE_D2Q5_VARD (3); 1 to 3:

@@ -61,7 +61,7 @@ int check_grid(const sslbm_grid* g) {
     return fail(SSLBM_ERR_BAD_ARG, "dx and dt must be finite and > 0");
   if (g->bc != SSLBM_BC_PERIODIC && g->bc != SSLBM_BC_NOFLUX)
     return fail(SSLBM_ERR_BAD_ARG, "bc=%d is not a boundary code", g->bc);
-  if (g->precision < SSLBM_FP64 || g->precision > SSLBM_FP32_SPLIT)
+  if (g->precision < SSLBM_FP64 || g->precision > SSLBM_FP64_DW)
     return fail(SSLBM_ERR_BAD_ARG, "precision=%d is not a precision code", g->precision);
   if (g->schemes < 1 || g->schemes > 3)
     return fail(SSLBM_ERR_BAD_ARG, "schemes=%d must be a nonzero mask of 1 (SSLBM) and 2 (BGK)",
@@ -87,7 +87,10 @@ int make_layout(const sslbm_grid* g, Layout* L) {
   const double bytes_est = (double)L->plane * (double)L->esize * (10.0 + 2 * kBgkPlanes) * 2.0;
   if (bytes_est > 9.0e18) return fail(SSLBM_ERR_BAD_ARG, "grid too large");
   L->plane_bytes = round_up((size_t)L->plane * L->esize, kAlign);
-  L->s_planes = g->precision == SSLBM_FP32_KAHAN ? 10 : g->precision == SSLBM_FP32_SPLIT ? 6 : 5;
+  // the double-word storage keeps the Kahan storage's ten planes (hi, and -lo as compensation)
+  L->s_planes = (g->precision == SSLBM_FP32_KAHAN || g->precision == SSLBM_FP64_DW) ? 10
+                : g->precision == SSLBM_FP32_SPLIT                                  ? 6
+                                                                                    : 5;
   size_t off = 0;
   L->off_diag = off;
   off += round_up((sslbm::kDiagBlocks * sslbm::kDiagSlots + 8) * sizeof(double), kAlign);
@@ -154,8 +157,10 @@ struct sslbm_handle {
   bool fuse_diag = false;   // sslbm_set_fused_diagnostics
   bool diag_ready = false;  // diag_result() holds the diagnostics of the current SSLBM state
 
+  // Coeffs<double> for FP64 and for the double-word storage (which splits them into pairs)
   const void* coeffs() const {
-    return g.precision == SSLBM_FP64 ? static_cast<const void*>(&cd) : static_cast<const void*>(&cf);
+    return (g.precision == SSLBM_FP64 || g.precision == SSLBM_FP64_DW) ? static_cast<const void*>(&cd)
+                                                                       : static_cast<const void*>(&cf);
   }
   char* s_plane(int buf, int c) const { return s_buf[buf] + (size_t)c * L.plane_bytes; }
   double* diag_partials() const { return reinterpret_cast<double*>(ws + L.off_diag); }
@@ -192,6 +197,12 @@ int sslbm_workspace_bytes(const sslbm_grid* g, size_t* bytes) {
   if (st) return st;
   *bytes = L.total;
   return SSLBM_OK;
+}
+
+// The storages of ten planes: values and compensations (Kahan), or high parts and minus the
+// low parts (double word); both are read as value - compensation.
+static bool ten_planes(const sslbm_handle* h) {
+  return h->g.precision == SSLBM_FP32_KAHAN || h->g.precision == SSLBM_FP64_DW;
 }
 
 // The D2Q5 FP32 storages and the FP32 D2Q9 and varying-diffusion lattices have the
@@ -371,7 +382,7 @@ int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_
     const char* s = static_cast<const char*>(src) + (size_t)(c - c0) * plane_user;
     // values stored as given (same type, no deviation or compensation plane): one strided copy
     // into the pitched plane, without staging or a conversion pass
-    if (!bgk && src_dtype == own_dtype && h->g.precision != SSLBM_FP32_KAHAN &&
+    if (!bgk && src_dtype == own_dtype && !ten_planes(h) &&
         !((h->g.precision == SSLBM_FP32_DEV || h->g.precision == SSLBM_FP32_SPLIT) && c == SSLBM_S)) {
       cudaError_t e = cudaMemcpy2DAsync(h->s_plane(h->s_cur, c), (size_t)h->L.pitch * usize, s,
                                         (size_t)h->g.nx * usize, (size_t)h->g.nx * usize, (size_t)h->g.ny,
@@ -390,7 +401,7 @@ int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_
       e = sslbm::launch_bgk_init(h->g.precision, h->gv, c, s, src_dtype, h->b_buf[h->b_cur],
                                  h->stream);
     } else {
-      const bool kahan = h->g.precision == SSLBM_FP32_KAHAN;
+      const bool kahan = ten_planes(h);
       const bool split = h->g.precision == SSLBM_FP32_SPLIT && c == SSLBM_S;
       const int dev_S = (h->g.precision == SSLBM_FP32_DEV && c == SSLBM_S) ? 1 : 0;
       e = sslbm::launch_plane_write(h->g.precision, h->gv, s, src_dtype, h->s_plane(h->s_cur, c),
@@ -477,7 +488,7 @@ int sslbm_read(sslbm_handle* h, int scheme, int comp, void* dst, int dst_dtype, 
   for (int c = c0; c < c1; ++c) {
     char* d = static_cast<char*>(dst) + (size_t)(c - c0) * plane_user;
     // values stored as they are returned: one strided copy out of the pitched plane
-    if (!bgk && dst_dtype == own_dtype && h->g.precision != SSLBM_FP32_KAHAN &&
+    if (!bgk && dst_dtype == own_dtype && !ten_planes(h) &&
         !((h->g.precision == SSLBM_FP32_DEV || h->g.precision == SSLBM_FP32_SPLIT) && c == SSLBM_S)) {
       cudaError_t e = cudaMemcpy2DAsync(d, (size_t)h->g.nx * usize, h->s_plane(h->s_cur, c),
                                         (size_t)h->L.pitch * usize, (size_t)h->g.nx * usize, (size_t)h->g.ny,
@@ -492,7 +503,7 @@ int sslbm_read(sslbm_handle* h, int scheme, int comp, void* dst, int dst_dtype, 
       e = sslbm::launch_bgk_density(h->g.precision, h->gv, c, h->b_buf[h->b_cur], target,
                                     dst_dtype, h->stream);
     } else {
-      const bool kahan = h->g.precision == SSLBM_FP32_KAHAN;
+      const bool kahan = ten_planes(h);
       const bool split = h->g.precision == SSLBM_FP32_SPLIT && c == SSLBM_S;
       const int dev_S = (h->g.precision == SSLBM_FP32_DEV && c == SSLBM_S) ? 1 : 0;
       e = sslbm::launch_plane_read(h->g.precision, h->gv, h->s_plane(h->s_cur, c),
@@ -777,7 +788,7 @@ int sslbm_diagnostics(sslbm_handle* h, int scheme, double* totals, double* peak_
   cudaError_t e = cudaSuccess;
   if (bgk || !h->diag_ready) {  // else the last step's fused pass left them in diag_result()
     const void* planes = bgk ? (const void*)h->b_buf[h->b_cur] : (const void*)h->s_buf[h->s_cur];
-    const bool comp = !bgk && (h->g.precision == SSLBM_FP32_KAHAN || h->g.precision == SSLBM_FP32_SPLIT);
+    const bool comp = !bgk && (ten_planes(h) || h->g.precision == SSLBM_FP32_SPLIT);
     const void* comps = comp ? h->s_plane(h->s_cur, 5) : nullptr;
     h->diag_ready = false;  // the reduction below overwrites the result
     e = sslbm::launch_diagnostics(h->g.precision, bgk ? 1 : 0, h->gv, planes, comps, h->diag_partials(),

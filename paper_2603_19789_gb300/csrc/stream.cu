@@ -26,6 +26,7 @@
 #include <atomic>
 
 #include "bounds.cuh"
+#include "dword.cuh"
 #include "sslbm_internal.cuh"
 #include "sslbm_pipe.cuh"
 #include "variants.cuh"
@@ -186,6 +187,69 @@ __device__ __forceinline__ void st2(float* o, int64_t plane_off, float2 v, bool 
   o[plane_off] = v.x;
   if (second) o[plane_off + 32] = v.y;
 }
+
+// The FP64-accurate double-word storage (SSLBM_FP64_DW): the Kahan storage's ten planes, read
+// as values hi and lo = -(compensation plane), and the update of seird_cell (the FP64
+// kernel's operations, in its order) in double-word arithmetic (dword.cuh), except the
+// laplacian, taken as ((l - c) + (r - c)) + ((u - c) + (d - c)): for a smooth field every
+// difference is small and carries the double-word precision of the values, where the sum of
+// the neighbours minus 4c would lose their high part's magnitude.  Ring planes: the high
+// parts of S, E, I, R, their compensations (the planes with x neighbours), then D's two.
+// The additions are the 11-flop form (add_abs), whose absolute error bound is what a
+// max-norm against the fields' peak needs: 37.5 GLUPS at 8192^2 against 27.8 with the
+// 20-flop accurate sum, with the same errors against the oracle (1.6e-13 after 2000 steps of
+// the paper's case).  Ring rows and warps, 8192^2: 4 rows, 4 warps, 4 CTAs (16 warps per SM)
+// 40.7 GLUPS; 4 rows, 2 warps, 8 CTAs 40.7; 5 rows, 4 warps, 3 CTAs 37.5; 6 rows, 2 warps,
+// 6 CTAs 37.7 (the native FP64 kernel: 11.9).
+struct DwCell {
+  static constexpr int kPlanes = 10, kHaloPlanes = 8, kRing = 4, kWarps = 4, kMinBlocks = 4;
+  static constexpr bool kPacked = true;
+  const float* in;
+  float* out;
+  DwCoeffs k;
+  __device__ __forceinline__ const float* src(int f, const GridView& g) const {
+    return in + (f < 4 ? f : f < 8 ? f + 1 : f == 8 ? 4 : 9) * g.plane;
+  }
+  using State = NoState;
+  __device__ __forceinline__ void update(const GridView& g, const Rows& r, int i, int64_t x, int64_t y, State&,
+                                         bool) const {
+    using dw::W;
+    // the pair of ring plane f (high part) and f + off (compensation) at ring index j of row p
+    auto val = [&](const float* p, int f, int off, int j) {
+      return W{ld2(p + f * kStStride, j), neg2(ld2(p + (f + off) * kStStride, j))};
+    };
+    W c[5], lap[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      c[f] = val(r.C, f, 4, i);
+      const W dl = dw::sub_abs(val(r.C, f, 4, i - 1), c[f]), dr = dw::sub_abs(val(r.C, f, 4, i + 1), c[f]);
+      const W du = dw::sub_abs(val(r.U, f, 4, i), c[f]), dd = dw::sub_abs(val(r.N, f, 4, i), c[f]);
+      lap[f] = dw::add_abs(dw::add_abs(dl, dr), dw::add_abs(du, dd));
+    }
+    c[4] = val(r.C, 8, 1, i);
+    const W &S = c[0], &E = c[1], &I = c[2], &R = c[3], &D = c[4];
+    // force of infection times dt, beta S I / N_c dt, against max(N_c, smallest normal)
+    W Nc = dw::add_abs(dw::add_abs(S, E), dw::add_abs(I, R));
+    if (!(Nc.h.x >= 1.17549435e-38f)) Nc.h.x = 1.17549435e-38f, Nc.l.x = 0.f;
+    if (!(Nc.h.y >= 1.17549435e-38f)) Nc.h.y = 1.17549435e-38f, Nc.l.y = 0.f;
+    const W F = dw::div(dw::mul(dw::mul(dw::splat(k.bdt), S), I), Nc);
+    const W adt = dw::splat(k.adt);
+    W n[5];
+    n[0] = dw::sub_abs(dw::add_abs(dw::mul(dw::splat(k.dl[0]), lap[0]), S), F);
+    n[1] = dw::add_abs(dw::add_abs(dw::mul(dw::splat(k.dl[1]), lap[1]), E), dw::add_abs(dw::mul(dw::neg(adt), E), F));
+    n[2] = dw::add_abs(dw::add_abs(dw::mul(dw::splat(k.dl[2]), lap[2]), I),
+                   dw::sub_abs(dw::mul(adt, E), dw::mul(dw::splat(k.gdt), I)));
+    n[3] = dw::add_abs(dw::mul(dw::splat(k.rdt), I), dw::add_abs(dw::mul(dw::splat(k.dl[3]), lap[3]), R));
+    n[4] = dw::add_abs(dw::mul(dw::splat(k.ddt), I), D);
+    float* o = out + y * g.pitch + x;
+    const bool second = x + 32 < g.nx;
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      st2(o, f * g.plane, n[f].h, second);
+      st2(o, (5 + f) * g.plane, neg2(n[f].l), second);
+    }
+  }
+};
 
 // The D2Q5 one-step update of the plain (MODE_PLAIN), deviation (MODE_DEV) and split
 // (MODE_SPLIT) storages, as step1_kernel computes it: lap5 of S, E, I, R (lap5_diff of the
@@ -420,6 +484,18 @@ cudaError_t launch_stream_d2q5(int precision, const GridView& g, const void* coe
     case SSLBM_FP32_KAHAN: return launch_stream(g, KahanCell{src, dst, k}, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_stream_dw(const GridView& g, const void* coeffs, const void* in, void* out, cudaStream_t s) {
+  const Coeffs<double>& c = *static_cast<const Coeffs<double>*>(coeffs);
+  auto pair = [](double v) {  // hi = v rounded to float, lo = the rest rounded to float
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  };
+  DwCoeffs k;
+  for (int f = 0; f < 4; ++f) k.dl[f] = pair(c.dl[f]);
+  k.bdt = pair(c.bdt), k.adt = pair(c.adt), k.gdt = pair(c.gdt), k.rdt = pair(c.rdt), k.ddt = pair(c.ddt);
+  return launch_stream(g, DwCell{static_cast<const float*>(in), static_cast<float*>(out), k}, s);
 }
 
 cudaError_t launch_stream_d2q9(const GridView& g, const void* coeffs, const void* in, void* out, cudaStream_t s) {

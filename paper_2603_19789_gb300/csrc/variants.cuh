@@ -12,6 +12,8 @@ cudaError_t launch_sslbm9_step1(int precision, const GridView& g, const void* co
 // the FP32 D2Q9 step and the FP32 varying-diffusion step through the streaming one-step
 // kernel (stream.cu)
 cudaError_t launch_stream_d2q9(const GridView& g, const void* coeffs, const void* in, void* out, cudaStream_t s);
+// The FP64-accurate double-word storage (SSLBM_FP64_DW), one step: coeffs is a Coeffs<double>.
+cudaError_t launch_stream_dw(const GridView& g, const void* coeffs, const void* in, void* out, cudaStream_t s);
 cudaError_t launch_stream_vard(const GridView& g, const void* coeffs, const void* kx, const void* ky, const void* in,
                                void* out, cudaStream_t s);
 

@@ -25,7 +25,7 @@ SSLBM_OK = 0
 (SSLBM_ERR_BAD_ARG, SSLBM_ERR_UNSTABLE, SSLBM_ERR_CUDA, SSLBM_ERR_TIMEOUT, SSLBM_ERR_NONFINITE,
  SSLBM_ERR_WORKSPACE, SSLBM_ERR_UNSUPPORTED, SSLBM_ERR_STATE) = (-1, -2, -3, -4, -5, -6, -7, -8)
 BC_PERIODIC, BC_NOFLUX = 0, 1
-FP64, FP32, FP32_DEV, FP32_KAHAN, FP32_SPLIT = 0, 1, 2, 3, 4
+FP64, FP32, FP32_DEV, FP32_KAHAN, FP32_SPLIT, FP64_DW = 0, 1, 2, 3, 4, 5
 SCHEME_SSLBM, SCHEME_BGK = 0, 1
 S, E, I, R, D, NCOMP = 0, 1, 2, 3, 4, 5
 ALL = -1
@@ -33,7 +33,8 @@ DT_F64, DT_F32 = 0, 1
 WANT_SSLBM, WANT_BGK = 1, 2
 LATTICE_D2Q5, LATTICE_D2Q9, LATTICE_D2Q5_SLBM, LATTICE_D2Q5_VARD = 0, 1, 2, 3
 MAX_DEPTH = 8
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP32_KAHAN, "fp32_split": FP32_SPLIT}
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_dev": FP32_DEV, "fp32_kahan": FP32_KAHAN, "fp32_split": FP32_SPLIT,
+              "fp64_dw": FP64_DW}
 
 # every symbol include/sslbm.h declares
 EXPORTS = ("sslbm_strerror", "sslbm_last_error", "sslbm_version", "sslbm_workspace_bytes",

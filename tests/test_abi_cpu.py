@@ -85,11 +85,14 @@ def test_workspace_bytes_layout(lib):
     assert n >= (2 * 5 + 2 * 21) * pitch * 7 * 8
     g = L.make_grid(100, 7, precision=L.FP32_KAHAN)
     assert L.sslbm_workspace_bytes(g) >= 2 * 10 * 128 * 7 * 4
+    # the double-word storage: ten FP32 planes (high parts and minus the low parts)
+    g = L.make_grid(100, 7, precision=L.FP64_DW)
+    assert L.sslbm_workspace_bytes(g) == L.sslbm_workspace_bytes(L.make_grid(100, 7, precision=L.FP32_KAHAN))
 
 
 @pytest.mark.parametrize("kw", [dict(nx=0, ny=5), dict(nx=5, ny=-1), dict(nx=4, ny=4, dx=0.0),
                                 dict(nx=4, ny=4, dt=float("nan")), dict(nx=4, ny=4, bc=2),
-                                dict(nx=4, ny=4, precision=7), dict(nx=4, ny=4, precision=5),
+                                dict(nx=4, ny=4, precision=7), dict(nx=4, ny=4, precision=6),
                                 dict(nx=4, ny=4, schemes=0),
                                 dict(nx=1 << 31, ny=1)])
 def test_invalid_grids_rejected(lib, kw):
@@ -101,7 +104,7 @@ def test_invalid_grids_rejected(lib, kw):
     assert ei.value.status == -1
 
 
-@pytest.mark.parametrize("precision", [L.FP32_DEV, L.FP32_SPLIT, L.FP32_KAHAN])
+@pytest.mark.parametrize("precision", [L.FP32_DEV, L.FP32_SPLIT, L.FP32_KAHAN, L.FP64_DW])
 def test_bgk_in_the_fp32_storage_variants_unsupported(lib, precision):
     g = L.make_grid(8, 8, precision=precision, schemes=L.WANT_BGK)
     with pytest.raises(L.SslbmError) as ei:
@@ -109,9 +112,10 @@ def test_bgk_in_the_fp32_storage_variants_unsupported(lib, precision):
     assert ei.value.status == -7
 
 
+@pytest.mark.parametrize("precision", [L.FP32_SPLIT, L.FP64_DW])
 @pytest.mark.parametrize("lattice", [L.LATTICE_D2Q9, L.LATTICE_D2Q5_SLBM, L.LATTICE_D2Q5_VARD])
-def test_split_storage_only_on_d2q5(lib, lattice):
-    g = L.make_grid(8, 8, precision=L.FP32_SPLIT, lattice=lattice)
+def test_split_and_double_word_storages_only_on_d2q5(lib, lattice, precision):
+    g = L.make_grid(8, 8, precision=precision, lattice=lattice)
     with pytest.raises(L.SslbmError) as ei:
         L.sslbm_workspace_bytes(g)
     assert ei.value.status == -7

@@ -46,7 +46,7 @@ runs = 0
 for nx, ny in sizes:
     st = inputs.epidemic_state(nx, ny, 7 * nx + ny)
     for bc in (L.BC_PERIODIC, L.BC_NOFLUX):
-        for prec in (L.FP64, L.FP32, L.FP32_DEV, L.FP32_KAHAN, L.FP32_SPLIT):
+        for prec in (L.FP64, L.FP32, L.FP32_DEV, L.FP32_KAHAN, L.FP32_SPLIT, L.FP64_DW):
             both = prec in (L.FP64, L.FP32)
             s = L.Solver(nx, ny, rates, d=d, bc=bc, precision=prec,
                          schemes=(L.WANT_SSLBM | L.WANT_BGK) if both else L.WANT_SSLBM)
