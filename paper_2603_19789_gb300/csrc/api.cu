@@ -226,6 +226,8 @@ static cudaError_t launch_pass(sslbm_handle* h, int k, int seg) {
                                            h->stream);
     return sslbm::launch_sslbm_vard_blocked(h->gv, &h->cf, kx, ky, h->s_buf[h->s_cur], out, k, seg, h->stream);
   }
+  if (k == 1 && h->g.precision == SSLBM_FP64_DW)  // the double word: its own streaming cell
+    return sslbm::launch_stream_dw(h->gv, h->coeffs(), h->s_buf[h->s_cur], out, h->stream);
   if (k == 1)
     return q9 ? sslbm::launch_sslbm9_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur], out, h->stream)
               : sslbm::launch_sslbm_step1(h->g.precision, h->gv, h->coeffs(), h->s_buf[h->s_cur], out, h->stream);

@@ -32,7 +32,6 @@
 #include "bounds.cuh"
 #include "sslbm_internal.cuh"
 #include "pipe_launch.cuh"
-#include "variants.cuh"
 
 SSLBM_OOB_ACCESSOR(kernels)
 
@@ -127,7 +126,6 @@ cudaError_t launch_sslbm_step1(int precision, const GridView& g, const void* coe
     case SSLBM_FP32_DEV:
     case SSLBM_FP32_SPLIT:
     case SSLBM_FP32_KAHAN: return launch_stream_d2q5(precision, g, coeffs, in, out, s);
-    case SSLBM_FP64_DW: return launch_stream_dw(g, coeffs, in, out, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,11 +1,12 @@
 """Measurement studies built on the library (run on a GPU).
 
 precision  -- the small-increment precision study: the multi-seed no-flux workload at
-              4096 x 4096 with every infected seed at amplitude 1e-6, 50,000 steps, in five
+              4096 x 4096 with every infected seed at amplitude 1e-6, 50,000 steps, in six
               storage/arithmetic variants: FP64, FP32, FP32 with S stored as its deviation
               from the total density, FP32 with S stored as a hi/lo pair, FP32 with
-              compensated (Kahan) accumulation of every compartment.  Reports,
-              at log-spaced checkpoints, each FP32 variant's per-compartment root-mean-square
+              compensated (Kahan) accumulation of every compartment, and FP64 accuracy in
+              double-word FP32 arithmetic.  Reports,
+              at log-spaced checkpoints, each other variant's per-compartment root-mean-square
               and max-norm error against the FP64 run, divided by the compartment's peak so
               far (E and I decay to ~0 after the wave), the relative L2 error of the infected
               fraction 1 - S, and every variant's drift of the total population (FP64
@@ -57,7 +58,7 @@ from . import inputs
 from . import sslbm as L
 
 VARIANTS = (("fp64", L.FP64), ("fp32", L.FP32), ("fp32_dev", L.FP32_DEV), ("fp32_split", L.FP32_SPLIT),
-            ("fp32_kahan", L.FP32_KAHAN))
+            ("fp32_kahan", L.FP32_KAHAN), ("fp64_dw", L.FP64_DW))
 
 
 def precision_study(n: int = 4096, steps: int = 50000, checkpoints: int = 6, seed: int = inputs.DEFAULT_SEED):
