@@ -74,8 +74,10 @@ enum { SSLBM_BC_PERIODIC = 0, SSLBM_BC_NOFLUX = 1 };
  *                FP64 is carried out in double-word arithmetic (the error-free building
  *                blocks of Joldes, Muller and Popescu, ACM TOMS 2017: relative error of
  *                order 2^-46 per operation), with the laplacian in difference form.  The
- *                exponent range is FP32's (values below 1e-38 lose precision).  D2Q5 SSLBM,
- *                one step per launch; 80 bytes per cell-step. */
+ *                exponent range is FP32's: values below 1e-38 lose precision, and an
+ *                infection front whose leading edge lies below the smallest float (1.4e-45)
+ *                in FP64 arrives shifted, as in every FP32 storage.  D2Q5 SSLBM, one step
+ *                per launch; 80 bytes per cell-step. */
 enum { SSLBM_FP64 = 0, SSLBM_FP32 = 1, SSLBM_FP32_DEV = 2, SSLBM_FP32_KAHAN = 3, SSLBM_FP32_SPLIT = 4,
        SSLBM_FP64_DW = 5 };
 enum { SSLBM_SCHEME_SSLBM = 0, SSLBM_SCHEME_BGK = 1 };
