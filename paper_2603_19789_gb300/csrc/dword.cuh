@@ -64,6 +64,19 @@ __device__ __forceinline__ W add_abs(const W& x, const W& y) {
 }
 __device__ __forceinline__ W sub_abs(const W& x, const W& y) { return add_abs(x, neg(y)); }
 
+// ((l - c) + (r - c)) + ((u - c) + (d - c)) of double words, with one normalisation: the high
+// parts' differences and their sums are exact (TwoSum), and their errors and the low parts'
+// differences are added in FP32 once, so the result's absolute error stays of order
+// u^2 (|c| + the neighbours), like a chain of add_abs (59 flops against 77).
+__device__ __forceinline__ W lap5_diff(const W& c, const W& l, const W& r, const W& up, const W& dn) {
+  const W d1 = two_sum(l.h, neg2(c.h)), d2 = two_sum(r.h, neg2(c.h));
+  const W d3 = two_sum(up.h, neg2(c.h)), d4 = two_sum(dn.h, neg2(c.h));
+  const W a = two_sum(d1.h, d2.h), b = two_sum(d3.h, d4.h), e = two_sum(a.h, b.h);
+  const float2 lows = add2(add2(sub(l.l, c.l), sub(r.l, c.l)), add2(sub(up.l, c.l), sub(dn.l, c.l)));
+  const float2 errs = add2(add2(add2(d1.l, d2.l), add2(d3.l, d4.l)), add2(add2(a.l, b.l), e.l));
+  return fast_two_sum(e.h, add2(lows, errs));
+}
+
 // x y (relative error <= 4u^2).
 __device__ __forceinline__ W mul(const W& x, const W& y) {
   const W c = two_prod(x.h, y.h);
