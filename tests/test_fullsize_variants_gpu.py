@@ -63,3 +63,34 @@ def test_autotuned_blocking_gives_the_one_step_bits_at_full_size(workload, preci
     ref = s.checkpoint(on_device=True)
     assert torch.equal(blocked, ref)
     s.close()
+
+
+def test_double_word_at_full_size_matches_the_oracle_on_windows(workload):
+    """The FP64-accurate double word (bench.py's fp64_dw_glups), 8 steps of the 8192^2 grid:
+    sampled 8 x 8 windows against the oracle, which evaluates each on its domain of dependence.
+    Errors are measured against each compartment's largest value on the grid: outside the
+    seeds I and E fall below FP32's exponent range, which a double word of floats shares."""
+    wl = workload
+    steps = 8
+    s = L.Solver(N, N, wl["rates"].as_tuple(), d=wl["d"], bc=wl["bc"], precision=L.FP64_DW)
+    s.write(wl["state"])
+    s.step(steps)
+    got = s.read()
+    scale = np.abs(got).reshape(5, -1).max(axis=1)
+    tau = [oracle.tau_from_d(v) for v in wl["d"][:4]]
+    g = np.random.default_rng(5)
+    pts = [(0, 0), (N - 8, 0), (0, N - 8), (N - 8, N - 8), (N // 2, N // 3)]
+    pts += [(int(g.integers(0, N - 8)), int(g.integers(0, N - 8))) for _ in range(20)]
+    # on the seeds: the largest initial I in each quadrant
+    I0 = wl["state"][2]
+    h = N // 2
+    for qy in (0, h):
+        for qx in (0, h):
+            y, x = np.unravel_index(np.argmax(I0[qy:qy + h, qx:qx + h]), (h, h))
+            pts.append((min(max(qx + x - 4, 0), N - 8), min(max(qy + y - 4, 0), N - 8)))
+    for x0, y0 in pts:
+        want = oracle.sslbm_window(wl["state"], x0, y0, 8, 8, tau, wl["rates"].as_tuple(), 1.0, wl["bc"], steps)
+        part = got[:, y0:y0 + 8, x0:x0 + 8]
+        for c in range(5):
+            assert np.abs(part[c] - want[c]).max() <= 1e-12 * scale[c], (x0, y0, c)
+    s.close()
