@@ -305,11 +305,11 @@ def train_step_timing(n=256, batch=16, steps=50):
 
 # algorithmic bytes per cell-step of each (lattice, precision) at one step per launch: every
 # plane the update reads, read once, and every plane it writes, written once
-_ESIZE = {L.FP64: 8, L.FP32: 4, L.FP32_DEV: 4, L.FP32_SPLIT: 4, L.FP32_KAHAN: 4}
-_PLANES = {L.FP32_SPLIT: 6, L.FP32_KAHAN: 10}
+_ESIZE = {L.FP64: 8, L.FP32: 4, L.FP32_DEV: 4, L.FP32_SPLIT: 4, L.FP32_KAHAN: 4, L.FP64_DW: 4}
+_PLANES = {L.FP32_SPLIT: 6, L.FP32_KAHAN: 10, L.FP64_DW: 10}
 LATTICES = {"d2q5": L.LATTICE_D2Q5, "d2q9": L.LATTICE_D2Q9, "vard": L.LATTICE_D2Q5_VARD}
 PRECISION_NAMES = {"fp64": L.FP64, "fp32": L.FP32, "fp32_dev": L.FP32_DEV, "fp32_split": L.FP32_SPLIT,
-                   "fp32_kahan": L.FP32_KAHAN}
+                   "fp32_kahan": L.FP32_KAHAN, "fp64_dw": L.FP64_DW}
 
 
 def _measured_hbm_gbs():
@@ -334,7 +334,7 @@ def variant_timing(lattice="d2q9", precision="fp32", n=8192, steps=20, depth=1, 
     import torch
     lat, prec = LATTICES[lattice], PRECISION_NAMES[precision]
     wl = inputs.roofline_workload(n, n)
-    st = wl["state"] if prec == L.FP64 else np.ascontiguousarray(wl["state"].astype(np.float32))
+    st = wl["state"] if prec in (L.FP64, L.FP64_DW) else np.ascontiguousarray(wl["state"].astype(np.float32))
     bc = wl["bc"] if bc is None else bc
     s = L.Solver(n, n, wl["rates"].as_tuple(), d=wl["d"], bc=bc, precision=prec, lattice=lat)
     if lat == L.LATTICE_D2Q5_VARD:
