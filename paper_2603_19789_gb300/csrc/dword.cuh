@@ -21,7 +21,9 @@ struct W {
   float2 h, l;
 };
 
-__device__ __forceinline__ float2 sub(float2 a, float2 b) { return add2(a, neg2(b)); }
+// a - b in one instruction: b * (-1) is exact, so the fused multiply-add rounds a - b once,
+// like the subtraction (the same bits as adding -b).
+__device__ __forceinline__ float2 sub(float2 a, float2 b) { return fma2(b, splat2(-1.f), a); }
 
 // Knuth's TwoSum: s + e = a + b exactly, s = fl(a + b); no condition on a, b.
 __device__ __forceinline__ W two_sum(float2 a, float2 b) {
