@@ -176,15 +176,16 @@ void sslbm_destroy(sslbm_handle* h);
  * pinned) or the device (src_on_device = 1).  Values are rounded to the solver's
  * precision.  For BGK the populations of the written compartments are set to the
  * equilibrium f_i = w_i rho (Sec. II.B; the initial populations are not stated in
- * the paper).  FP32_KAHAN keeps the rounding residue of each written value in its
- * compensation plane, so FP64 input is represented to ~1e-15.  When comp is SSLBM_ALL
+ * the paper).  FP32_KAHAN and FP64_DW keep the rounding residue of each written value in
+ * its compensation plane, so FP64 input is represented to 2^-48 relative (within FP32's
+ * exponent range).  When comp is SSLBM_ALL
  * the scheme's step counter is reset.  Host sources are consumed before the call returns. */
 int sslbm_write(sslbm_handle* h, int scheme, int comp, const void* src, int src_dtype,
                 int src_on_device);
 
 /* Copy compartment comp (or SSLBM_ALL) of scheme `scheme` to dst in dst_dtype; for
- * BGK the density rho = sum_i f_i.  FP32_DEV returns S = s_ref - sigma and
- * FP32_KAHAN the compensated value, both evaluated in double precision.
+ * BGK the density rho = sum_i f_i.  FP32_DEV returns S = s_ref - sigma, FP32_KAHAN the
+ * compensated value and FP64_DW hi + lo, each evaluated in double precision.
  * A host destination synchronises the stream; a device destination is stream-ordered. */
 int sslbm_read(sslbm_handle* h, int scheme, int comp, void* dst, int dst_dtype, int dst_on_device);
 
@@ -241,11 +242,13 @@ int64_t sslbm_steps_done(const sslbm_handle* h, int scheme);
  * A checkpoint is the solver's state exactly as stored, so that a run resumed from it
  * gives the bits of the uninterrupted run.  sslbm_read / sslbm_write cannot do that for
  * every configuration: FP32_DEV returns S rebuilt from the stored deviation, FP32_KAHAN
- * the compensated value, and a BGK write sets equilibrium populations.  Layout (a flat
+ * the compensated value, FP64_DW hi + lo rounded to a double, and a BGK write sets
+ * equilibrium populations.  Layout (a flat
  * byte buffer, host or device, owned by the caller): a 128-byte header (magic "SSLC",
  * version 2, nx, ny, precision, lattice, bc, schemes, the two step counters, the plane
  * counts, the element size and s_ref), then every stored plane in the solver's precision, each
- * ny*nx values row-major: the SSLBM planes (5, or 10 with the Kahan compensations) when
+ * ny*nx values row-major: the SSLBM planes (5; 6 for FP32_SPLIT; 10 with the Kahan
+ * compensations or the double word's negated low parts) when
  * the handle holds that scheme, then the 21 BGK planes (20 populations, D) when it holds
  * BGK.  Parameters, blocking and the diffusivity scale fields are the handle's own and
  * are not part of a checkpoint. */
