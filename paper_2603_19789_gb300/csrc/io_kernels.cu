@@ -133,9 +133,12 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
 
 // The FP32 partials of diag_partial_kernel without per-cell FP64 arithmetic (few FP64 units
 // on this GPU): each thread reads 4 cells per plane at a time (16-byte loads; the pitch and
-// the plane stride are multiples of 4), keeps its share of the row as a TwoSum pair per
-// compartment and adds that pair to the FP64 partial once per row.  With at most a few dozen
-// cells per thread and row, the pair's own error stays near FP32's unit roundoff squared.
+// the plane stride are multiples of 4) and keeps its share of the rows as a TwoSum pair per
+// compartment, renormalised (Fast2Sum) after every 4 cells and added to the FP64 partial every
+// kFlushRows rows and at the end.  After a renormalisation the pair's low part is at most half
+// an ulp of its high part, so the pair's own rounding stays near FP32's unit roundoff squared
+// per group of 4 cells.  (Adding the pair to FP64 after every row, the earlier form, took
+// 265 us per 8192^2 call against 255 us now: GB300 has few FP64 units.)
 // NCOMP: the first NCOMP compartments carry a compensation plane (0; 1 for the split S; 5 for
 // Kahan), subtracted from the values.  The peak of I is taken in FP32 (the same value as in
 // FP64), or in FP64 as value minus compensation when I has one.
@@ -143,10 +146,19 @@ template <int LAYOUT, int NCOMP>
 __global__ void __launch_bounds__(256) diag_partial_f32x4_kernel(const GridView g, const float* __restrict__ st,
                                                                  const float* __restrict__ comp,
                                                                  double* __restrict__ partials) {
+  constexpr int kFlushRows = 16;
   double v[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0, -DBL_MAX};
+  float hi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float pk = -FLT_MAX;
+  int rows = 0;
+  auto flush = [&]() {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      v[c] += (double)hi[c] + (double)lo[c];
+      hi[c] = lo[c] = 0.f;
+    }
+  };
   for (int64_t y = blockIdx.x; y < g.ny; y += gridDim.x) {
-    float hi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    float pk = -FLT_MAX;
     for (int64_t x = 4 * (int64_t)threadIdx.x; x < g.nx; x += 4 * (int64_t)blockDim.x) {
       if (!SSLBM_IN(x, 4, g.pitch, 30)) continue;
       const int64_t idx = y * g.pitch + x;
@@ -193,11 +205,20 @@ __global__ void __launch_bounds__(256) diag_partial_f32x4_kernel(const GridView 
         else
           pk = fmaxf(pk, r[2][j]);
       }
-    }
 #pragma unroll
-    for (int c = 0; c < 5; ++c) v[c] += (double)hi[c] + (double)lo[c];
-    if (NCOMP <= 2) v[5] = fmax(v[5], (double)pk);
+      for (int c = 0; c < 5; ++c) {  // Fast2Sum: |lo| <= ulp(hi) / 2 again
+        const float t = __fadd_rn(hi[c], lo[c]);
+        lo[c] = __fsub_rn(lo[c], __fsub_rn(t, hi[c]));
+        hi[c] = t;
+      }
+    }
+    if (++rows == kFlushRows) {
+      flush();
+      rows = 0;
+    }
   }
+  flush();
+  if (NCOMP <= 2) v[5] = fmax(v[5], (double)pk);
   block_reduce6(v);
   if (threadIdx.x == 0 && SSLBM_IN(blockIdx.x, 1, kDiagBlocks, 31)) {
 #pragma unroll
