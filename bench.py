@@ -264,6 +264,8 @@ def main():
     ap.add_argument("--ens-scenarios", type=int, default=512, help="ensemble size (profiling cases)")
     ap.add_argument("--ens-steps", type=int, default=5000, help="ensemble steps (profiling cases)")
     ap.add_argument("--ens-tiling", default="", help="depth,seg_rows instead of the autotuner")
+    ap.add_argument("--fused-diagnostics", action="store_true",
+                    help="take the diagnostics in the last pass of each step (sslbm_set_fused_diagnostics)")
     ap.add_argument("--nx", type=int, default=NX, help="grid width (profiling cases; default 8192)")
     ap.add_argument("--ny", type=int, default=NY, help="grid height (profiling cases; default 8192)")
     args = ap.parse_args()
@@ -290,6 +292,8 @@ def main():
 
     s = L.Solver(NX, NY, rates, d=wl["d"], bc=wl["bc"], precision=L.FP32)
     s.write(state32)
+    if args.fused_diagnostics:
+        s.set_fused_diagnostics(True)
     tuned = None
     if args.depth:
         s.set_blocking(args.depth)
